@@ -1,0 +1,49 @@
+"""Writes tests/golden/tiny_oracle.json: the FP64 oracle's results on the
+32x12x12 tiny workload (4 boxes 16x12x12, 6 states each, seed 0).
+
+Calls only oracle/ and the seeded input generator.  The stored numbers are
+the oracle's, not the paper's (the paper prints no worked example: its
+figures are not part of the available text).
+Run from the repository root:  python tests/golden/make_golden.py
+"""
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from ofm_inputs import make_workload  # noqa: E402
+from oracle import ofm_oracle as O  # noqa: E402
+
+
+def main():
+    wl = make_workload("tiny", seed=0)
+    r = O.run_ofm(wl)
+    lo, hi = O.window_bounds(r["E"], wl.window)
+    win = r["E"][(r["E"] >= lo) & (r["E"] <= hi)]
+    exact = np.linalg.eigvalsh(r["H"].toarray())
+    out = {
+        "workload": wl.name,
+        "seed": 0,
+        "source": "oracle/ofm_oracle.py run_ofm (FP64), tests/golden/make_golden.py",
+        "fragment_eps": [list(map(float, e)) for e in r["eps"]],
+        "pairs": [list(p) for p in r["pairs"]],
+        "ofm_spectrum": list(map(float, r["E"])),
+        "window": [lo, hi],
+        "window_eigs": list(map(float, win)),
+        "exact_lowest": list(map(float, exact[:len(r["E"])])),
+        "S_min_eig": float(np.linalg.eigvalsh(r["Sd"])[0]),
+        "H_01_corner": [[float(x) for x in row] for row in r["blocks"][(0, 1)][0][:3, :3]],
+        "S_01_corner": [[float(x) for x in row] for row in r["blocks"][(0, 1)][1][:3, :3]],
+    }
+    path = os.path.join(ROOT, "tests", "golden", "tiny_oracle.json")
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1)
+    print("wrote", path)
+
+
+if __name__ == "__main__":
+    main()
