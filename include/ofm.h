@@ -1,0 +1,202 @@
+/*
+ * ofm.h -- C ABI of the GB300 overlapping-fragments-method (OFM) library.
+ *
+ * The method (Vukmirovic & Wang, "Overlapping fragments method for
+ * electronic structure calculation of large systems", Sec. II): the system is
+ * divided into mutually overlapping fragments; the lowest eigenstates of each
+ * fragment form a basis; the whole-system Hamiltonian H and the overlap S are
+ * represented in that basis,
+ *     H_{ij,mn} = <phi_i^(j)| H |phi_m^(n)>,   S_{ij,mn} = <phi_i^(j)|phi_m^(n)>,
+ * and the generalized eigenproblem sum_mn (H - E S) C = 0 (Eq. 2) is solved for
+ * the states in an energy window.
+ *
+ * Discretisation used by every entry point:
+ *   - periodic grid of n[0] x n[1] x n[2] points, spacing h (bohr); point
+ *     (x,y,z) has linear index x + n0*(y + n1*z) (x fastest);
+ *   - H = -1/2 Laplacian + V (Eq. 1 in atomic units), Laplacian = 7-point
+ *     finite difference (sum of the six neighbours - 6 phi) / h^2;
+ *   - fragment a is the box off + [0, ext) (mod n); its Hamiltonian is the
+ *     principal submatrix of H on the box (zero outside; periodic wrap kept
+ *     in a dimension that the box spans completely);
+ *   - the dilated box B_a+ grows the box by one point on each side in every
+ *     dimension with ext < n; H phi_a is non-zero only there;
+ *   - states are unit-norm in the plain Euclidean grid sum; basis order is
+ *     fragment-major, states ascending in fragment energy;
+ *   - a pair a <= b is kept when box a meets the dilated box of b.
+ *
+ * Conventions:
+ *   - Every call returns an ofm_status.  On failure a message is kept in the
+ *     context (ofm_last_error) and the context stays valid for ofm_destroy.
+ *     Calls out of order return OFM_ERR_STATE.  No exception crosses the ABI.
+ *   - The context owns every device buffer it allocates.  The caller owns all
+ *     pointers it passes; inputs are copied before the call returns (or, for
+ *     device inputs, before work enqueued on the context stream reads them).
+ *   - All device work is ordered on the context's CUDA stream.  Calls that
+ *     return host data synchronise that stream before returning.
+ *   - A "device" pointer is a CUDA global-memory address on the context's
+ *     current device; a "host" pointer is ordinary (pageable or pinned) memory.
+ */
+#ifndef OFM_H
+#define OFM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  OFM_OK = 0,
+  OFM_ERR_INVALID = 1,        /* bad argument or geometry */
+  OFM_ERR_OOM = 2,            /* device allocation failed */
+  OFM_ERR_CUDA = 3,           /* a CUDA runtime call failed */
+  OFM_ERR_NOT_CONVERGED = 4,  /* iteration cap reached (residuals reported) */
+  OFM_ERR_NOT_POSDEF = 5,     /* Cholesky of S met a non-positive pivot */
+  OFM_ERR_TIMEOUT = 6,        /* a bounded device-side wait gave up */
+  OFM_ERR_STATE = 7           /* call out of order */
+} ofm_status;
+
+/* Arithmetic of the pair contraction (Sec. II, the H_ab / S_ab dot products). */
+typedef enum {
+  OFM_PREC_FP64 = 0,    /* FP64 products and sums (CUDA cores) */
+  OFM_PREC_FP32 = 1,    /* FP32 products and sums (CUDA cores) */
+  OFM_PREC_TF32 = 2,    /* tcgen05 kind::tf32, FP32 accumulation in TMEM */
+  OFM_PREC_BF16 = 3,    /* tcgen05 kind::f16 (bf16 operands), FP32 accumulation */
+  OFM_PREC_BF16X3 = 4   /* bf16 hi+lo split: hi*hi + hi*lo + lo*hi, FP32 accumulation */
+} ofm_precision;
+
+/* Storage type of the fragment states and of H phi in device memory. */
+typedef enum { OFM_STORE_FP64 = 0, OFM_STORE_FP32 = 1 } ofm_storage;
+
+typedef enum { OFM_HOST = 0, OFM_DEVICE = 1 } ofm_location;
+
+typedef struct { int n[3]; double h; } ofm_grid;
+typedef struct { int off[3]; int ext[3]; int n_states; } ofm_fragment;
+
+/* Options of the batched fragment eigensolver (Chebyshev-filtered subspace
+ * iteration with Rayleigh-Ritz).  Zero fields take the defaults in brackets. */
+typedef struct {
+  double tol;            /* stop when every max_i ||H phi_i - eps_i phi_i|| <= tol [1e-5 FP32, 1e-9 FP64] */
+  int max_iter;          /* outer iterations [60] */
+  int degree;            /* Chebyshev degree per iteration [12] */
+  int extra_states;      /* guard vectors beyond n_states [max(4, n/4)] */
+  uint64_t seed;         /* start vectors from a counter-based generator [0] */
+} ofm_eig_opts;
+
+/* Options of the assembly.  NULL means defaults. */
+typedef struct {
+  int chunk_points;      /* target points per contraction work item [0 = planner's choice] */
+  int keep_hphi;         /* keep H phi resident after the call (1) [1] */
+} ofm_assemble_opts;
+
+/* Counts describing the planned work (after ofm_build_fragments). */
+typedef struct {
+  int n_frag;
+  int n_pairs;
+  int basis_size;                 /* sum of n_states */
+  int n_work_items;               /* contraction work items of the current plan */
+  long long pair_flops;           /* sum_{a<=b} 2 n_a n_b (|B_a ∩ B_b| + |B_a ∩ B_b+|) */
+  long long overlap_points_s;     /* sum_{a<=b} |B_a ∩ B_b| */
+  long long overlap_points_h;     /* sum_{a<=b} |B_a ∩ B_b+| */
+  long long state_bytes;          /* device bytes of the fragment states (one copy) */
+  long long hphi_bytes;           /* device bytes of H phi */
+  long long apply_points;         /* sum_a |B_a+| * n_a (point-states written by the H apply) */
+} ofm_plan_info;
+
+typedef struct ofm_ctx ofm_ctx;
+
+/* Create a context on the current CUDA device.  stream: a cudaStream_t to
+ * order all work on, or NULL for a context-owned non-blocking stream. */
+ofm_status ofm_create(ofm_ctx** ctx, void* cuda_stream);
+void ofm_destroy(ofm_ctx* ctx);
+const char* ofm_last_error(const ofm_ctx* ctx);
+const char* ofm_status_string(ofm_status s);
+
+/* Sec. II (input: the potential on a real-space grid, and fragments = boxes).
+ * Validates the grid and boxes, copies V (n0*n1*n2 doubles, x fastest; host
+ * or device per v_loc) into the context in the storage type, plans the pair
+ * list and the per-pair overlap geometry, and allocates every device buffer
+ * the later calls use (re-using them when a new geometry fits).
+ * Returns OFM_ERR_INVALID for: h <= 0; any n < 1; ext_d < 1 or ext_d > n_d;
+ * ext_d == n_d - 1 (the dilated box would wrap onto itself);
+ * n_states < 1 or n_states > P_a - 1. */
+ofm_status ofm_build_fragments(ofm_ctx* ctx, const ofm_grid* grid, const double* V,
+                               ofm_location v_loc, const ofm_fragment* frags, int n_frag,
+                               ofm_storage storage);
+
+/* Sec. II, "calculation of basis wave functions": the lowest n_a eigenpairs
+ * of every fragment Hamiltonian, all fragments in one batch.  eps_out: host,
+ * basis_size doubles (fragment-major, ascending); resid_out: host, basis_size
+ * residual norms ||H phi - eps phi|| or NULL.  OFM_ERR_NOT_CONVERGED leaves
+ * the best states found in place (usable) and fills both outputs. */
+ofm_status ofm_fragment_eigs(ofm_ctx* ctx, const ofm_eig_opts* opts,
+                             double* eps_out, double* resid_out);
+
+/* Import / export the states of fragment a: phi is P_a x n_a, column-major
+ * (state i is phi[i*P_a .. (i+1)*P_a), box points x fastest), doubles, on the
+ * host or device per loc.  Import marks the states as the current basis. */
+ofm_status ofm_set_fragment_states(ofm_ctx* ctx, int a, const double* phi, ofm_location loc);
+ofm_status ofm_get_fragment_states(ofm_ctx* ctx, int a, double* phi_out, ofm_location loc);
+
+/* Sec. II, the main part of the calculation: H phi_b on every dilated box
+ * (whole-system H), then for every pair a <= b
+ *     S_ab = Phi_a^T Phi_b  over B_a ∩ B_b,   H_ab = Phi_a^T (H Phi_b) over B_a ∩ B_b+,
+ * in the requested arithmetic, summed in a fixed order (deterministic), and
+ * stored as FP64 blocks; a diagonal block is symmetrised as (X + X^T)/2.
+ * FP64 arithmetic is allowed with either storage; the others need FP32
+ * storage.  Enqueued on the context stream; does not synchronise. */
+ofm_status ofm_assemble_HS(ofm_ctx* ctx, ofm_precision prec, const ofm_assemble_opts* opts);
+
+/* The pair list: *n_pairs always; pair_ab (2*n_pairs ints, a then b, a<=b,
+ * sorted by a then b) when not NULL. */
+ofm_status ofm_get_pairs(ofm_ctx* ctx, int* n_pairs, int* pair_ab);
+ofm_status ofm_get_plan_info(ofm_ctx* ctx, ofm_plan_info* info);
+
+/* Block of the pair (a, b) (either order): n_a x n_b row-major doubles,
+ * host.  A pair not in the list yields zeros.  H_ab / S_ab may be NULL. */
+ofm_status ofm_get_block(ofm_ctx* ctx, int a, int b, double* H_ab, double* S_ab);
+
+/* Dense n x n (n = basis_size) row-major H and S in basis order, host or
+ * device per loc.  Either pointer may be NULL. */
+ofm_status ofm_get_dense_HS(ofm_ctx* ctx, double* H, double* S, ofm_location loc);
+
+/* H phi_b of fragment b on its dilated box as |B_b+| x n_b column-major
+ * doubles (host), available after ofm_assemble_HS. */
+ofm_status ofm_get_hphi(ofm_ctx* ctx, int b, double* hphi_out);
+
+/* Eq. 2 restricted to an energy window, FP64 on the device: Cholesky
+ * S = L L^T, A = L^-1 H L^-T, Householder tridiagonalisation, Sturm-count
+ * bisection for the eigenvalues in [E_lo, E_hi] (inclusive).  E_out: host,
+ * max_out doubles, ascending; *n_out = number found (may exceed max_out, in
+ * which case only max_out are written).  C_out: host, n x min(n_out,max_out)
+ * column-major S-orthonormal eigenvectors, or NULL.
+ * OFM_ERR_NOT_POSDEF when S is not positive definite. */
+ofm_status ofm_window_eigs(ofm_ctx* ctx, double E_lo, double E_hi, int max_out,
+                           double* E_out, int* n_out, double* C_out);
+
+/* Eigenvalues with 0-based ascending indices [i_lo, i_hi) of Eq. 2 (host
+ * output), from the same factorisation as ofm_window_eigs.  Used to place
+ * an energy window relative to a gap. */
+ofm_status ofm_eigs_by_index(ofm_ctx* ctx, int i_lo, int i_hi, double* E_out);
+
+/* Eq. 2 for caller-supplied dense n x n row-major H (symmetric) and S
+ * (symmetric positive definite), host pointers, solved by the same device
+ * path as ofm_window_eigs (replaces the assembled matrices). */
+ofm_status ofm_set_dense_HS(ofm_ctx* ctx, int n, const double* H, const double* S);
+
+/* Host-only planner query (needs no GPU and no context): validates the
+ * geometry like ofm_build_fragments and returns the pair list (Sec. II,
+ * pairs of fragments that share grid points through the stencil) with the
+ * overlap sizes.  *n_pairs always; when pair_ab is not NULL, up to
+ * max_pairs pairs (a, b) with a <= b; when counts is not NULL, 2 per written
+ * pair: |B_a ∩ B_b| then |B_a ∩ B_b+|.  *pair_flops (nullable) receives the
+ * algorithmic flop count sum 2 n_a n_b (|B_a ∩ B_b| + |B_a ∩ B_b+|). */
+ofm_status ofm_plan_pairs(const ofm_grid* grid, const ofm_fragment* frags, int n_frag,
+                          int* n_pairs, int* pair_ab, long long* counts, int max_pairs,
+                          long long* pair_flops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OFM_H */

@@ -1,0 +1,466 @@
+// C ABI entry points of the OFM library (include/ofm.h): context handling,
+// argument validation, buffer management and the order of device work.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "ofm_internal.h"
+
+using namespace ofm;
+
+// ------------------------------------------------------------- helpers -----
+
+ofm_status ofm_fail(ofm_ctx* c, ofm_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+ofm_status ofm_cuda_check(ofm_ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return OFM_OK;
+  std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  if (e == cudaErrorMemoryAllocation) return ofm_fail(c, OFM_ERR_OOM, m);
+  return ofm_fail(c, OFM_ERR_CUDA, m);
+}
+
+ofm_status ofm_ensure(ofm_ctx* c, DevBuf& b, size_t bytes, const char* what) {
+  if (bytes == 0) bytes = 16;
+  if (b.cap >= bytes) return OFM_OK;
+  if (b.p) {
+    cudaError_t e = cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+    if (e != cudaSuccess) return ofm_cuda_check(c, e, "cudaFree");
+  }
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e != cudaSuccess) {
+    b.p = nullptr;
+    cudaGetLastError();
+    char buf[160];
+    snprintf(buf, sizeof buf, "cudaMalloc of %zu bytes for %s failed", bytes, what);
+    return ofm_fail(c, e == cudaErrorMemoryAllocation ? OFM_ERR_OOM : OFM_ERR_CUDA, buf);
+  }
+  b.cap = bytes;
+  return OFM_OK;
+}
+
+static void free_buf(DevBuf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.cap = 0;
+}
+
+static ofm_status check_launch(ofm_ctx* c, const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return ofm_cuda_check(c, e, what);
+  return OFM_OK;
+}
+
+static ofm_status sync(ofm_ctx* c, const char* what) {
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return ofm_cuda_check(c, e, what);
+  return OFM_OK;
+}
+
+static size_t elem_size(const ofm_ctx* c) { return c->storage == OFM_STORE_FP64 ? 8 : 4; }
+
+static int find_pair(const ofm_ctx* c, int a, int b) {
+  // pairs are sorted by (a, b) with a <= b
+  int lo = 0, hi = (int)c->pairs.size() - 1;
+  while (lo <= hi) {
+    int mid = (lo + hi) / 2;
+    const HostPair& p = c->pairs[mid];
+    if (p.a == a && p.b == b) return mid;
+    if (p.a < a || (p.a == a && p.b < b)) lo = mid + 1; else hi = mid - 1;
+  }
+  return -1;
+}
+
+// ------------------------------------------------------------- lifecycle ---
+
+extern "C" const char* ofm_status_string(ofm_status s) {
+  switch (s) {
+    case OFM_OK: return "OFM_OK";
+    case OFM_ERR_INVALID: return "OFM_ERR_INVALID";
+    case OFM_ERR_OOM: return "OFM_ERR_OOM";
+    case OFM_ERR_CUDA: return "OFM_ERR_CUDA";
+    case OFM_ERR_NOT_CONVERGED: return "OFM_ERR_NOT_CONVERGED";
+    case OFM_ERR_NOT_POSDEF: return "OFM_ERR_NOT_POSDEF";
+    case OFM_ERR_TIMEOUT: return "OFM_ERR_TIMEOUT";
+    case OFM_ERR_STATE: return "OFM_ERR_STATE";
+  }
+  return "OFM_ERR_UNKNOWN";
+}
+
+extern "C" ofm_status ofm_create(ofm_ctx** out, void* cuda_stream) {
+  if (!out) return OFM_ERR_INVALID;
+  *out = nullptr;
+  ofm_ctx* c = new (std::nothrow) ofm_ctx();
+  if (!c) return OFM_ERR_OOM;
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e != cudaSuccess) {
+    delete c;
+    cudaGetLastError();
+    return OFM_ERR_CUDA;
+  }
+  if (cuda_stream) {
+    c->stream = (cudaStream_t)cuda_stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      delete c;
+      cudaGetLastError();
+      return OFM_ERR_CUDA;
+    }
+    c->own_stream = true;
+  }
+  if (ofm_ensure(c, c->flag, 64, "error flags") != OFM_OK) {
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return OFM_ERR_OOM;
+  }
+  *out = c;
+  return OFM_OK;
+}
+
+extern "C" void ofm_destroy(ofm_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  DevBuf* bufs[] = {&c->V, &c->states, &c->hphi, &c->d_frags, &c->d_apply_start, &c->d_pairs,
+                    &c->d_pieces, &c->d_items, &c->partials, &c->blocks, &c->dense_H,
+                    &c->dense_S, &c->staging, &c->flag, &c->w_A, &c->w_L, &c->w_d, &c->w_e,
+                    &c->w_tau, &c->w_tmp, &c->w_eval};
+  for (DevBuf* b : bufs) free_buf(*b);
+  ofm_free_extra(c);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+extern "C" const char* ofm_last_error(const ofm_ctx* c) {
+  if (!c) return "null context";
+  return c->err.c_str();
+}
+
+// ------------------------------------------------------------- build -------
+
+extern "C" ofm_status ofm_build_fragments(ofm_ctx* c, const ofm_grid* grid, const double* V,
+                                          ofm_location v_loc, const ofm_fragment* frags,
+                                          int n_frag, ofm_storage storage) {
+  if (!c) return OFM_ERR_INVALID;
+  if (!grid || !V) return ofm_fail(c, OFM_ERR_INVALID, "grid and V must not be NULL");
+  if (storage != OFM_STORE_FP32 && storage != OFM_STORE_FP64)
+    return ofm_fail(c, OFM_ERR_INVALID, "unknown storage type");
+  if (v_loc != OFM_HOST && v_loc != OFM_DEVICE)
+    return ofm_fail(c, OFM_ERR_INVALID, "unknown V location");
+  std::string msg;
+  if (!validate_geometry(*grid, frags, n_frag, msg)) return ofm_fail(c, OFM_ERR_INVALID, msg);
+
+  c->built = c->have_states = c->assembled = c->dense_ready = c->factored = false;
+  c->grid = *grid;
+  c->storage = storage;
+  c->nfrag = n_frag;
+  c->in_frags.assign(frags, frags + n_frag);
+  make_frag_table(*grid, frags, n_frag, c->frags, c->state_elems);
+  make_pairs(*grid, c->frags, c->pairs);
+  c->basis = 0;
+  c->apply_points = 0;
+  for (auto& f : c->frags) {
+    c->basis += f.n;
+    c->apply_points += f.Pd * f.n;
+  }
+  c->flops = c->ks = c->kh = 0;
+  for (auto& p : c->pairs) {
+    c->ks += p.ks;
+    c->kh += p.kh;
+    c->flops += 2LL * c->frags[p.a].n * c->frags[p.b].n * (p.ks + p.kh);
+  }
+  c->frag_set.assign(n_frag, 0);
+
+  const size_t es = elem_size(c);
+  const long long npts = (long long)grid->n[0] * grid->n[1] * grid->n[2];
+  OFM_TRY(ofm_ensure(c, c->V, npts * es, "potential"));
+  if (v_loc == OFM_HOST) {
+    OFM_TRY(ofm_ensure(c, c->staging, npts * sizeof(double), "staging"));
+    OFM_CUDA(c, cudaMemcpyAsync(c->staging.p, V, npts * sizeof(double), cudaMemcpyHostToDevice,
+                                c->stream));
+    launch_convert_V((const double*)c->staging.p, c->V.p, npts, es == 8, c->stream);
+  } else {
+    launch_convert_V(V, c->V.p, npts, es == 8, c->stream);
+  }
+  OFM_TRY(check_launch(c, "convert V"));
+
+  OFM_TRY(ofm_ensure(c, c->states, c->state_elems * es, "fragment states"));
+  OFM_TRY(ofm_ensure(c, c->hphi, c->state_elems * es, "H phi"));
+  OFM_CUDA(c, cudaMemsetAsync(c->states.p, 0, c->state_elems * es, c->stream));
+  OFM_CUDA(c, cudaMemsetAsync(c->hphi.p, 0, c->state_elems * es, c->stream));
+  OFM_TRY(ofm_ensure(c, c->d_frags, sizeof(DevFrag) * n_frag, "fragment table"));
+  OFM_CUDA(c, cudaMemcpyAsync(c->d_frags.p, c->frags.data(), sizeof(DevFrag) * n_frag,
+                              cudaMemcpyHostToDevice, c->stream));
+
+  // H-apply launch table: one thread per 16 bytes of states of a point
+  const int vn = es == 8 ? 2 : 4;
+  c->apply_cta_start.resize(n_frag);
+  long long tot = 0;
+  for (int a = 0; a < n_frag; ++a) {
+    c->apply_cta_start[a] = (int)tot;
+    tot += (c->frags[a].Pd * (c->frags[a].ld / vn) + 255) / 256;
+  }
+  if (tot > 0x7fffffff) return ofm_fail(c, OFM_ERR_INVALID, "H-apply grid too large");
+  c->apply_total_ctas = (int)tot;
+  OFM_TRY(ofm_ensure(c, c->d_apply_start, sizeof(int) * n_frag, "apply table"));
+  OFM_CUDA(c, cudaMemcpyAsync(c->d_apply_start.p, c->apply_cta_start.data(), sizeof(int) * n_frag,
+                              cudaMemcpyHostToDevice, c->stream));
+
+  // SIMT contraction plan: about 8 work items per SM
+  long long chunk = std::max<long long>(256, c->kh / (8 * 152));
+  chunk = std::min<long long>(chunk, 16384);
+  c->simt_chunk = chunk;
+  make_items_simt(c->frags, c->pairs, c->simt_tile, chunk, c->simt_pairs, c->simt_pieces,
+                  c->simt_items, c->simt_partial_elems);
+  const int np = (int)c->simt_pairs.size();
+  OFM_TRY(ofm_ensure(c, c->d_pairs, sizeof(DevPair) * std::max(1, np), "pair table"));
+  OFM_TRY(ofm_ensure(c, c->d_pieces, sizeof(Piece) * std::max<size_t>(1, c->simt_pieces.size()), "piece table"));
+  OFM_TRY(ofm_ensure(c, c->d_items, sizeof(WorkItem) * std::max<size_t>(1, c->simt_items.size()), "work items"));
+  OFM_TRY(ofm_ensure(c, c->partials, sizeof(double) * c->simt_partial_elems, "partials"));
+  OFM_CUDA(c, cudaMemcpyAsync(c->d_pairs.p, c->simt_pairs.data(), sizeof(DevPair) * np,
+                              cudaMemcpyHostToDevice, c->stream));
+  OFM_CUDA(c, cudaMemcpyAsync(c->d_pieces.p, c->simt_pieces.data(),
+                              sizeof(Piece) * c->simt_pieces.size(), cudaMemcpyHostToDevice, c->stream));
+  OFM_CUDA(c, cudaMemcpyAsync(c->d_items.p, c->simt_items.data(),
+                              sizeof(WorkItem) * c->simt_items.size(), cudaMemcpyHostToDevice, c->stream));
+  c->blk_elems = 0;
+  for (auto& p : c->simt_pairs) c->blk_elems = std::max<long long>(c->blk_elems, p.blk_off + 2LL * c->frags[p.a].n * c->frags[p.b].n);
+  OFM_TRY(ofm_ensure(c, c->blocks, sizeof(double) * c->blk_elems, "blocks"));
+  OFM_TRY(ofm_plan_extra(c));
+  // host copies of tables are read back by later calls: wait for the uploads
+  OFM_TRY(sync(c, "build_fragments"));
+  c->built = true;
+  return OFM_OK;
+}
+
+// ------------------------------------------------------------- states ------
+
+extern "C" ofm_status ofm_set_fragment_states(ofm_ctx* c, int a, const double* phi, ofm_location loc) {
+  if (!c) return OFM_ERR_INVALID;
+  if (!c->built) return ofm_fail(c, OFM_ERR_STATE, "ofm_build_fragments must come first");
+  if (a < 0 || a >= c->nfrag || !phi) return ofm_fail(c, OFM_ERR_INVALID, "bad fragment index or NULL states");
+  const DevFrag& F = c->frags[a];
+  const long long P = (long long)F.ext[0] * F.ext[1] * F.ext[2];
+  const double* src = phi;
+  if (loc == OFM_HOST) {
+    OFM_TRY(ofm_ensure(c, c->staging, P * F.n * sizeof(double), "staging"));
+    OFM_CUDA(c, cudaMemcpyAsync(c->staging.p, phi, P * F.n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    src = (const double*)c->staging.p;
+  } else if (loc != OFM_DEVICE) {
+    return ofm_fail(c, OFM_ERR_INVALID, "unknown location");
+  }
+  launch_import_states((const DevFrag*)c->d_frags.p, a, F, src, c->states.p, c->storage == OFM_STORE_FP64, c->stream);
+  OFM_TRY(check_launch(c, "import states"));
+  if (loc == OFM_HOST) OFM_TRY(sync(c, "set_fragment_states"));  // staging is reused
+  c->frag_set[a] = 1;
+  c->have_states = std::all_of(c->frag_set.begin(), c->frag_set.end(), [](char v) { return v != 0; });
+  c->assembled = c->dense_ready = c->factored = false;
+  return OFM_OK;
+}
+
+extern "C" ofm_status ofm_get_fragment_states(ofm_ctx* c, int a, double* out, ofm_location loc) {
+  if (!c) return OFM_ERR_INVALID;
+  if (!c->built || !c->frag_set.size() || !c->frag_set[a < 0 || a >= c->nfrag ? 0 : a])
+    return ofm_fail(c, OFM_ERR_STATE, "states of this fragment are not set");
+  if (a < 0 || a >= c->nfrag || !out) return ofm_fail(c, OFM_ERR_INVALID, "bad fragment index or NULL output");
+  const DevFrag& F = c->frags[a];
+  const long long cnt = (long long)F.ext[0] * F.ext[1] * F.ext[2] * F.n;
+  double* dst = out;
+  if (loc == OFM_HOST) {
+    OFM_TRY(ofm_ensure(c, c->staging, cnt * sizeof(double), "staging"));
+    dst = (double*)c->staging.p;
+  }
+  launch_export_states(F, c->states.p, dst, c->storage == OFM_STORE_FP64, false, c->stream);
+  OFM_TRY(check_launch(c, "export states"));
+  if (loc == OFM_HOST)
+    OFM_CUDA(c, cudaMemcpyAsync(out, dst, cnt * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  return sync(c, "get_fragment_states");
+}
+
+extern "C" ofm_status ofm_get_hphi(ofm_ctx* c, int b, double* out) {
+  if (!c) return OFM_ERR_INVALID;
+  if (!c->assembled) return ofm_fail(c, OFM_ERR_STATE, "ofm_assemble_HS must come first");
+  if (b < 0 || b >= c->nfrag || !out) return ofm_fail(c, OFM_ERR_INVALID, "bad fragment index or NULL output");
+  const DevFrag& F = c->frags[b];
+  const long long cnt = F.Pd * F.n;
+  OFM_TRY(ofm_ensure(c, c->staging, cnt * sizeof(double), "staging"));
+  launch_export_states(F, c->hphi.p, (double*)c->staging.p, c->storage == OFM_STORE_FP64, true, c->stream);
+  OFM_TRY(check_launch(c, "export H phi"));
+  OFM_CUDA(c, cudaMemcpyAsync(out, c->staging.p, cnt * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  return sync(c, "get_hphi");
+}
+
+// ------------------------------------------------------------- assembly ----
+
+ofm_status ofm_apply_h(ofm_ctx* c) {
+  launch_apply_global((const DevFrag*)c->d_frags.p, (const int*)c->d_apply_start.p, c->nfrag,
+                      c->apply_total_ctas, c->V.p, c->states.p, c->hphi.p, c->grid.n, c->grid.h,
+                      c->storage == OFM_STORE_FP64, c->stream);
+  return check_launch(c, "apply H");
+}
+
+extern "C" ofm_status ofm_assemble_HS(ofm_ctx* c, ofm_precision prec, const ofm_assemble_opts* opts) {
+  if (!c) return OFM_ERR_INVALID;
+  if (!c->built) return ofm_fail(c, OFM_ERR_STATE, "ofm_build_fragments must come first");
+  if (!c->have_states) return ofm_fail(c, OFM_ERR_STATE, "fragment states are not set (ofm_fragment_eigs or ofm_set_fragment_states)");
+  if (prec < OFM_PREC_FP64 || prec > OFM_PREC_BF16X3) return ofm_fail(c, OFM_ERR_INVALID, "unknown precision");
+  if (prec != OFM_PREC_FP64 && c->storage == OFM_STORE_FP64)
+    return ofm_fail(c, OFM_ERR_INVALID, "FP32 and tensor-core contractions need FP32 storage");
+  (void)opts;
+  c->assembled = c->dense_ready = c->factored = false;
+  OFM_TRY(ofm_apply_h(c));
+  if (prec == OFM_PREC_FP64 || prec == OFM_PREC_FP32) {
+    launch_contract_simt(prec, c->storage == OFM_STORE_FP64, (const DevFrag*)c->d_frags.p,
+                         (const DevPair*)c->d_pairs.p, (const Piece*)c->d_pieces.p,
+                         (const WorkItem*)c->d_items.p, (int)c->simt_items.size(), c->states.p,
+                         c->hphi.p, c->partials.p, c->simt_tile, c->stream);
+    OFM_TRY(check_launch(c, "contract (CUDA cores)"));
+    launch_finalize_simt(prec, (const DevFrag*)c->d_frags.p, (const DevPair*)c->d_pairs.p,
+                         (int)c->simt_pairs.size(), (const WorkItem*)c->d_items.p, c->partials.p,
+                         c->simt_tile, (double*)c->blocks.p, c->stream);
+    OFM_TRY(check_launch(c, "finalize blocks"));
+  } else {
+    OFM_TRY(ofm_contract_tc(c, prec));
+  }
+  c->assembled = true;
+  return OFM_OK;
+}
+
+extern "C" ofm_status ofm_get_pairs(ofm_ctx* c, int* n_pairs, int* pair_ab) {
+  if (!c) return OFM_ERR_INVALID;
+  if (!c->built) return ofm_fail(c, OFM_ERR_STATE, "ofm_build_fragments must come first");
+  if (!n_pairs) return ofm_fail(c, OFM_ERR_INVALID, "n_pairs must not be NULL");
+  *n_pairs = (int)c->pairs.size();
+  if (pair_ab)
+    for (size_t i = 0; i < c->pairs.size(); ++i) {
+      pair_ab[2 * i] = c->pairs[i].a;
+      pair_ab[2 * i + 1] = c->pairs[i].b;
+    }
+  return OFM_OK;
+}
+
+extern "C" ofm_status ofm_get_plan_info(ofm_ctx* c, ofm_plan_info* info) {
+  if (!c) return OFM_ERR_INVALID;
+  if (!c->built) return ofm_fail(c, OFM_ERR_STATE, "ofm_build_fragments must come first");
+  if (!info) return ofm_fail(c, OFM_ERR_INVALID, "info must not be NULL");
+  info->n_frag = c->nfrag;
+  info->n_pairs = (int)c->pairs.size();
+  info->basis_size = c->basis;
+  info->n_work_items = (int)c->simt_items.size();
+  info->pair_flops = c->flops;
+  info->overlap_points_s = c->ks;
+  info->overlap_points_h = c->kh;
+  info->state_bytes = c->state_elems * (long long)elem_size(c);
+  info->hphi_bytes = c->state_elems * (long long)elem_size(c);
+  info->apply_points = c->apply_points;
+  return OFM_OK;
+}
+
+extern "C" ofm_status ofm_get_block(ofm_ctx* c, int a, int b, double* H_ab, double* S_ab) {
+  if (!c) return OFM_ERR_INVALID;
+  if (!c->assembled) return ofm_fail(c, OFM_ERR_STATE, "ofm_assemble_HS must come first");
+  if (a < 0 || b < 0 || a >= c->nfrag || b >= c->nfrag) return ofm_fail(c, OFM_ERR_INVALID, "bad fragment index");
+  const bool swap = a > b;
+  const int lo = swap ? b : a, hi = swap ? a : b;
+  const int na = c->frags[a].n, nb = c->frags[b].n;
+  const int p = find_pair(c, lo, hi);
+  if (p < 0) {
+    if (H_ab) std::memset(H_ab, 0, sizeof(double) * na * nb);
+    if (S_ab) std::memset(S_ab, 0, sizeof(double) * na * nb);
+    return OFM_OK;
+  }
+  const int nlo = c->frags[lo].n, nhi = c->frags[hi].n;
+  std::vector<double> tmp(2LL * nlo * nhi);
+  OFM_CUDA(c, cudaMemcpyAsync(tmp.data(), (const double*)c->blocks.p + c->simt_pairs[p].blk_off,
+                              sizeof(double) * tmp.size(), cudaMemcpyDeviceToHost, c->stream));
+  OFM_TRY(sync(c, "get_block"));
+  const double* Hs = tmp.data();
+  const double* Ss = tmp.data() + (long long)nlo * nhi;
+  for (int i = 0; i < na; ++i)
+    for (int m = 0; m < nb; ++m) {
+      const long long src = swap ? (long long)m * nhi + i : (long long)i * nhi + m;
+      if (H_ab) H_ab[(long long)i * nb + m] = Hs[src];
+      if (S_ab) S_ab[(long long)i * nb + m] = Ss[src];
+    }
+  return OFM_OK;
+}
+
+ofm_status ofm_make_dense(ofm_ctx* c) {
+  if (c->dense_ready) return OFM_OK;
+  if (!c->assembled) return ofm_fail(c, OFM_ERR_STATE, "ofm_assemble_HS must come first");
+  const long long n = c->basis;
+  OFM_TRY(ofm_ensure(c, c->dense_H, sizeof(double) * n * n, "dense H"));
+  OFM_TRY(ofm_ensure(c, c->dense_S, sizeof(double) * n * n, "dense S"));
+  OFM_CUDA(c, cudaMemsetAsync(c->dense_H.p, 0, sizeof(double) * n * n, c->stream));
+  OFM_CUDA(c, cudaMemsetAsync(c->dense_S.p, 0, sizeof(double) * n * n, c->stream));
+  launch_scatter_dense((const DevFrag*)c->d_frags.p, (const DevPair*)c->d_pairs.p,
+                       (int)c->simt_pairs.size(), (const double*)c->blocks.p, (int)n,
+                       (double*)c->dense_H.p, (double*)c->dense_S.p, c->stream);
+  OFM_TRY(check_launch(c, "scatter dense"));
+  c->dense_n = (int)n;
+  c->dense_ready = true;
+  c->factored = false;
+  return OFM_OK;
+}
+
+extern "C" ofm_status ofm_get_dense_HS(ofm_ctx* c, double* H, double* S, ofm_location loc) {
+  if (!c) return OFM_ERR_INVALID;
+  if (!c->dense_ready) OFM_TRY(ofm_make_dense(c));
+  const size_t bytes = sizeof(double) * (size_t)c->dense_n * c->dense_n;
+  const cudaMemcpyKind k = loc == OFM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (H) OFM_CUDA(c, cudaMemcpyAsync(H, c->dense_H.p, bytes, k, c->stream));
+  if (S) OFM_CUDA(c, cudaMemcpyAsync(S, c->dense_S.p, bytes, k, c->stream));
+  return sync(c, "get_dense_HS");
+}
+
+extern "C" ofm_status ofm_set_dense_HS(ofm_ctx* c, int n, const double* H, const double* S) {
+  if (!c) return OFM_ERR_INVALID;
+  if (n < 1 || !H || !S) return ofm_fail(c, OFM_ERR_INVALID, "need n >= 1 and non-NULL H, S");
+  const size_t bytes = sizeof(double) * (size_t)n * n;
+  OFM_TRY(ofm_ensure(c, c->dense_H, bytes, "dense H"));
+  OFM_TRY(ofm_ensure(c, c->dense_S, bytes, "dense S"));
+  OFM_CUDA(c, cudaMemcpyAsync(c->dense_H.p, H, bytes, cudaMemcpyHostToDevice, c->stream));
+  OFM_CUDA(c, cudaMemcpyAsync(c->dense_S.p, S, bytes, cudaMemcpyHostToDevice, c->stream));
+  OFM_TRY(sync(c, "set_dense_HS"));
+  c->dense_n = n;
+  c->dense_ready = true;
+  c->factored = false;
+  c->assembled = false;  // the dense pencil no longer comes from the blocks
+  return OFM_OK;
+}
+
+// ------------------------------------------------------------- Eq. 2 -------
+
+extern "C" ofm_status ofm_window_eigs(ofm_ctx* c, double E_lo, double E_hi, int max_out,
+                                      double* E_out, int* n_out, double* C_out) {
+  if (!c) return OFM_ERR_INVALID;
+  if (!n_out || (max_out > 0 && !E_out) || max_out < 0 || !(E_lo <= E_hi))
+    return ofm_fail(c, OFM_ERR_INVALID, "bad window arguments");
+  if (!c->dense_ready) OFM_TRY(ofm_make_dense(c));
+  if (!c->factored) OFM_TRY(ofm_window_factor(c));
+  int i_lo = 0, i_hi = 0;
+  OFM_TRY(ofm_window_count(c, E_lo, false, &i_lo));
+  OFM_TRY(ofm_window_count(c, E_hi, true, &i_hi));
+  *n_out = i_hi - i_lo;
+  const int m = std::min(*n_out, max_out);
+  if (m > 0) OFM_TRY(ofm_window_bisect(c, i_lo, i_lo + m, E_out));
+  if (C_out && m > 0) OFM_TRY(ofm_window_vectors(c, m, C_out));
+  return OFM_OK;
+}
+
+extern "C" ofm_status ofm_eigs_by_index(ofm_ctx* c, int i_lo, int i_hi, double* E_out) {
+  if (!c) return OFM_ERR_INVALID;
+  if (!c->dense_ready) OFM_TRY(ofm_make_dense(c));
+  if (i_lo < 0 || i_hi > c->dense_n || i_lo > i_hi || (!E_out && i_hi > i_lo))
+    return ofm_fail(c, OFM_ERR_INVALID, "bad index range");
+  if (!c->factored) OFM_TRY(ofm_window_factor(c));
+  if (i_hi > i_lo) OFM_TRY(ofm_window_bisect(c, i_lo, i_hi, E_out));
+  return OFM_OK;
+}

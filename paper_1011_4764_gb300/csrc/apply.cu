@@ -1,0 +1,181 @@
+// H phi on the dilated fragment boxes (Eq. 1 with the 7-point stencil), and
+// the layout conversions between the caller's column-major states and the
+// library's point-major storage.
+//
+// H phi(r) = (3/h^2) phi(r) - (1/(2 h^2)) sum_{6 neighbours} phi + V(r) phi(r)
+// with phi zero outside its box (Sec. II: H phi_i^(j) with the whole-system
+// H).  It is evaluated on every point of the dilated box, where it can be
+// non-zero.  Storage is point-major (the n states of one point are adjacent),
+// so one thread owns 16 bytes of states of one point and every neighbour
+// access of a warp is a contiguous run: the kernel is a streaming
+// stencil, bound by HBM bandwidth.
+#include <cuda_runtime.h>
+
+#include "ofm_internal.h"
+
+namespace ofm {
+
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; static constexpr int n = 4; };
+template <> struct Vec16<double> { using type = double2; static constexpr int n = 2; };
+
+__device__ __forceinline__ float4 fma4(float a, float4 x, float4 y) {
+  return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+}
+__device__ __forceinline__ double2 fma4(double a, double2 x, double2 y) {
+  return make_double2(fma(a, x.x, y.x), fma(a, x.y, y.y));
+}
+__device__ __forceinline__ float4 add4(float4 a, float4 b) {
+  return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+__device__ __forceinline__ double2 add4(double2 a, double2 b) {
+  return make_double2(a.x + b.x, a.y + b.y);
+}
+__device__ __forceinline__ float4 zero4(float) { return make_float4(0.f, 0.f, 0.f, 0.f); }
+__device__ __forceinline__ double2 zero4(double) { return make_double2(0.0, 0.0); }
+
+__device__ __forceinline__ int find_frag(const int* start, int nfrag, int cta) {
+  int lo = 0, hi = nfrag - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (start[mid] <= cta) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Neighbour offset along one dimension in the storage box: +/-1 step of
+// `stride` points; in a full-span dimension it wraps, otherwise a step out
+// of the storage box reads zero (returns -1).
+__device__ __forceinline__ long long nb_index(long long p, int c, int ext, int full, int dir,
+                                              long long stride) {
+  int c2 = c + dir;
+  if (c2 < 0 || c2 >= ext) {
+    if (!full) return -1;
+    c2 = (c2 + ext) % ext;
+  }
+  return p + (long long)(c2 - c) * stride;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) apply_global_kernel(const DevFrag* __restrict__ fr,
+                                                           const int* __restrict__ cta_start,
+                                                           int nfrag, const T* __restrict__ V,
+                                                           const T* __restrict__ states,
+                                                           T* __restrict__ hphi, int gx, int gy,
+                                                           int gz, T c0, T c1) {
+  using V16 = typename Vec16<T>::type;
+  constexpr int VN = Vec16<T>::n;
+  const int f = find_frag(cta_start, nfrag, blockIdx.x);
+  const DevFrag F = fr[f];
+  const int q_per_pt = F.ld / VN;
+  const long long e = (long long)(blockIdx.x - cta_start[f]) * blockDim.x + threadIdx.x;
+  if (e >= F.Pd * q_per_pt) return;
+  const long long p = e / q_per_pt;
+  const int q = (int)(e - p * q_per_pt);
+  const int ex = F.dext[0], ey = F.dext[1], ez = F.dext[2];
+  const int x = (int)(p % ex);
+  const int y = (int)((p / ex) % ey);
+  const int z = (int)(p / ((long long)ex * ey));
+  const int X = (F.doff[0] + x) % gx, Y = (F.doff[1] + y) % gy, Z = (F.doff[2] + z) % gz;
+  const T v = V[((long long)Z * gy + Y) * gx + X];
+  const V16* S = reinterpret_cast<const V16*>(states + F.off);
+  const long long sx = 1, sy = ex, sz = (long long)ex * ey;
+  V16 ctr = S[p * q_per_pt + q];
+  V16 sum = zero4(T());
+  long long nb;
+  if ((nb = nb_index(p, x, ex, F.full[0], +1, sx)) >= 0) sum = add4(sum, S[nb * q_per_pt + q]);
+  if ((nb = nb_index(p, x, ex, F.full[0], -1, sx)) >= 0) sum = add4(sum, S[nb * q_per_pt + q]);
+  if ((nb = nb_index(p, y, ey, F.full[1], +1, sy)) >= 0) sum = add4(sum, S[nb * q_per_pt + q]);
+  if ((nb = nb_index(p, y, ey, F.full[1], -1, sy)) >= 0) sum = add4(sum, S[nb * q_per_pt + q]);
+  if ((nb = nb_index(p, z, ez, F.full[2], +1, sz)) >= 0) sum = add4(sum, S[nb * q_per_pt + q]);
+  if ((nb = nb_index(p, z, ez, F.full[2], -1, sz)) >= 0) sum = add4(sum, S[nb * q_per_pt + q]);
+  // (c0 + v) * ctr - c1 * sum
+  V16 out = fma4(c0 + v, ctr, zero4(T()));
+  out = fma4(-c1, sum, out);
+  reinterpret_cast<V16*>(hphi + F.off)[p * q_per_pt + q] = out;
+}
+
+void launch_apply_global(const DevFrag* d_fr, const int* d_cta_start, int nfrag, int total_ctas,
+                         const void* V, const void* states, void* hphi, const int gn[3], double h,
+                         bool fp64, cudaStream_t s) {
+  const double c0 = 3.0 / (h * h), c1 = 0.5 / (h * h);
+  if (fp64)
+    apply_global_kernel<double><<<total_ctas, 256, 0, s>>>(
+        d_fr, d_cta_start, nfrag, (const double*)V, (const double*)states, (double*)hphi, gn[0],
+        gn[1], gn[2], c0, c1);
+  else
+    apply_global_kernel<float><<<total_ctas, 256, 0, s>>>(
+        d_fr, d_cta_start, nfrag, (const float*)V, (const float*)states, (float*)hphi, gn[0],
+        gn[1], gn[2], (float)c0, (float)c1);
+}
+
+// ------------------------------------------------------------ conversions --
+
+template <typename T>
+__global__ void convert_V_kernel(const double* __restrict__ src, T* __restrict__ dst, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = (T)src[i];
+}
+
+void launch_convert_V(const double* src, void* dst, long long n, bool fp64, cudaStream_t s) {
+  int blocks = (int)((n + 255) / 256);
+  if (fp64) convert_V_kernel<double><<<blocks, 256, 0, s>>>(src, (double*)dst, n);
+  else convert_V_kernel<float><<<blocks, 256, 0, s>>>(src, (float*)dst, n);
+}
+
+// Column-major box states (P x n, box order) -> point-major dilated storage.
+// Writes every interior point and every state column < ld (pad columns get 0).
+template <typename T>
+__global__ void import_kernel(DevFrag F, const double* __restrict__ src, T* __restrict__ dst) {
+  const long long P = (long long)F.ext[0] * F.ext[1] * F.ext[2];
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P * F.ld) return;
+  const int s = (int)(i / P);
+  const long long p = i - (long long)s * P;
+  const int x = (int)(p % F.ext[0]);
+  const int y = (int)((p / F.ext[0]) % F.ext[1]);
+  const int z = (int)(p / ((long long)F.ext[0] * F.ext[1]));
+  const long long pd = ((long long)(z + F.lo[2]) * F.dext[1] + (y + F.lo[1])) * F.dext[0] + (x + F.lo[0]);
+  dst[F.off + pd * F.ld + s] = (s < F.n) ? (T)src[(long long)s * P + p] : (T)0;
+}
+
+void launch_import_states(const DevFrag* /*d_fr*/, int /*a*/, const DevFrag& fa, const double* src,
+                          void* states, bool fp64, cudaStream_t s) {
+  const long long P = (long long)fa.ext[0] * fa.ext[1] * fa.ext[2];
+  const long long tot = P * fa.ld;
+  int blocks = (int)((tot + 255) / 256);
+  if (fp64) import_kernel<double><<<blocks, 256, 0, s>>>(fa, src, (double*)states);
+  else import_kernel<float><<<blocks, 256, 0, s>>>(fa, src, (float*)states);
+}
+
+// Point-major storage -> column-major doubles.  dilated=false: box points
+// (P_a x n); dilated=true: every point of the dilated box (Pd x n).
+template <typename T>
+__global__ void export_kernel(DevFrag F, const T* __restrict__ srcbuf, double* __restrict__ dst,
+                              int dilated) {
+  const int ex = dilated ? F.dext[0] : F.ext[0];
+  const int ey = dilated ? F.dext[1] : F.ext[1];
+  const int ez = dilated ? F.dext[2] : F.ext[2];
+  const long long P = (long long)ex * ey * ez;
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P * F.n) return;
+  const int s = (int)(i / P);
+  const long long p = i - (long long)s * P;
+  const int x = (int)(p % ex);
+  const int y = (int)((p / ex) % ey);
+  const int z = (int)(p / ((long long)ex * ey));
+  const int ox = dilated ? 0 : F.lo[0], oy = dilated ? 0 : F.lo[1], oz = dilated ? 0 : F.lo[2];
+  const long long pd = ((long long)(z + oz) * F.dext[1] + (y + oy)) * F.dext[0] + (x + ox);
+  dst[(long long)s * P + p] = (double)srcbuf[F.off + pd * F.ld + s];
+}
+
+void launch_export_states(const DevFrag& fa, const void* buf, double* dst, bool fp64,
+                          bool dilated, cudaStream_t s) {
+  const long long P = dilated ? fa.Pd : (long long)fa.ext[0] * fa.ext[1] * fa.ext[2];
+  const long long tot = P * fa.n;
+  int blocks = (int)((tot + 255) / 256);
+  if (fp64) export_kernel<double><<<blocks, 256, 0, s>>>(fa, (const double*)buf, dst, dilated ? 1 : 0);
+  else export_kernel<float><<<blocks, 256, 0, s>>>(fa, (const float*)buf, dst, dilated ? 1 : 0);
+}
+
+}  // namespace ofm

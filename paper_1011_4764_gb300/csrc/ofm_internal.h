@@ -1,0 +1,186 @@
+// Internal declarations of the OFM library: context, plan tables, kernel
+// launchers.  Not part of the public ABI (see include/ofm.h).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "ofm.h"
+
+namespace ofm {
+
+// ---------------------------------------------------------------- geometry --
+
+// One fragment as the kernels see it.  States and H phi are stored
+// point-major on the dilated box: element (p, s) at off + p * ld + s, where p
+// is the dilated-local linear index (x fastest) and s the state.  Halo points
+// of the states are zero.
+struct DevFrag {
+  int doff[3];     // global coordinate of dilated-local 0
+  int dext[3];     // dilated extent (storage box)
+  int lo[3];       // first interior (box) coordinate, dilated-local
+  int ext[3];      // box extent
+  int full[3];     // 1 when the box spans the whole grid in that dimension
+  int n;           // states
+  int ld;          // row stride in elements (n rounded up to 4)
+  int basis0;      // first basis index of this fragment
+  long long Pd;    // points of the dilated box
+  long long off;   // element offset of this fragment in the state / H phi arenas
+};
+
+// A product of per-dimension runs: a sub-box of B_a ∩ B_b+ that is a
+// contiguous box in both fragments' dilated-local coordinates.
+struct Piece {
+  int la[3];       // start, dilated-local coordinates of fragment a
+  int lb[3];       // start, dilated-local coordinates of fragment b
+  int len[3];      // extent
+};
+
+struct DevPair {
+  int a, b;
+  int item0, nitem;     // work items of this pair (contiguous)
+  int nchunk;           // K chunks per output tile
+  int mtiles, ntiles;   // output tiles (SIMT path)
+  long long blk_off;    // element offset of [H_ab | S_ab] in the block arena
+};
+
+// One unit of contraction work: rows [r0, r1) of a piece (a row is one
+// x-run of len[0] points at fixed y, z), for one output tile.
+struct WorkItem {
+  int pair;
+  int piece;
+  int r0, r1;
+  int mt, nt;
+  long long part_off;   // element offset of this item's partial tile
+};
+
+struct HostPair {
+  int a, b;
+  long long ks, kh;           // |B_a ∩ B_b|, |B_a ∩ B_b+|
+  std::vector<Piece> pieces;  // cover B_a ∩ B_b+
+};
+
+// ------------------------------------------------------------ device buffer --
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+};
+
+// ---------------------------------------------------------------- planner --
+
+// Runs of one dimension: positions t of box a (0 <= t < ext_a) that lie in
+// the (dilated) box b, grouped into maximal runs that are contiguous in both
+// fragments' local coordinates.  Returns (t_start, lb_start, len) triples.
+struct Run { int ta, lb, len; };
+std::vector<Run> dim_runs(int n, int offa, int exta, int offb, int extb);
+bool validate_geometry(const ofm_grid& g, const ofm_fragment* f, int nf, std::string& err);
+void make_frag_table(const ofm_grid& g, const ofm_fragment* f, int nf, std::vector<DevFrag>& out,
+                     long long& total_elems);
+void make_pairs(const ofm_grid& g, const std::vector<DevFrag>& fr, std::vector<HostPair>& pairs);
+// SIMT plan: items for output tiles of TILE x TILE, K chunks of ~chunk points.
+void make_items_simt(const std::vector<DevFrag>& fr, const std::vector<HostPair>& pairs,
+                     int tile, long long chunk, std::vector<DevPair>& dpairs,
+                     std::vector<Piece>& pieces, std::vector<WorkItem>& items,
+                     long long& partial_elems);
+
+// ------------------------------------------------------------ kernels ------
+
+void launch_apply_global(const DevFrag* d_fr, const int* d_cta_start, int nfrag, int total_ctas,
+                         const void* V, const void* states, void* hphi, const int gn[3], double h,
+                         bool fp64, cudaStream_t s);
+void launch_import_states(const DevFrag* d_fr, int a, const DevFrag& fa, const double* src,
+                          void* states, bool fp64, cudaStream_t s);
+void launch_export_states(const DevFrag& fa, const void* states, double* dst, bool fp64,
+                          bool dilated_hphi, cudaStream_t s);
+void launch_convert_V(const double* src, void* dst, long long n, bool fp64, cudaStream_t s);
+void launch_contract_simt(int prec, bool store_fp64, const DevFrag* d_fr, const DevPair* d_pairs,
+                          const Piece* d_pieces, const WorkItem* d_items, int nitems,
+                          const void* states, const void* hphi, void* partials, int tile,
+                          cudaStream_t s);
+void launch_finalize_simt(int prec, const DevFrag* d_fr, const DevPair* d_pairs, int npairs,
+                          const WorkItem* d_items, const void* partials, int tile,
+                          double* blocks, cudaStream_t s);
+void launch_scatter_dense(const DevFrag* d_fr, const DevPair* d_pairs, int npairs,
+                          const double* blocks, int n, double* Hd, double* Sd, cudaStream_t s);
+
+}  // namespace ofm
+
+// ------------------------------------------------------------- context ------
+
+struct ofm_ctx {
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0;
+  std::string err;
+
+  // state machine
+  bool built = false;
+  bool have_states = false;
+  bool assembled = false;
+  bool dense_ready = false;   // dense H, S hold the matrices to solve
+  bool factored = false;      // tridiagonal form of the current dense pencil is ready
+
+  ofm_grid grid{};
+  ofm_storage storage = OFM_STORE_FP32;
+  int nfrag = 0;
+  int basis = 0;
+  std::vector<ofm_fragment> in_frags;
+  std::vector<ofm::DevFrag> frags;
+  std::vector<ofm::HostPair> pairs;
+  long long state_elems = 0;
+  long long flops = 0, ks = 0, kh = 0, apply_points = 0;
+
+  // SIMT plan
+  std::vector<ofm::DevPair> simt_pairs;
+  std::vector<ofm::Piece> simt_pieces;
+  std::vector<ofm::WorkItem> simt_items;
+  long long simt_partial_elems = 0;
+  int simt_tile = 64;
+  long long simt_chunk = 0;
+
+  std::vector<long long> blk_off;   // per pair
+  long long blk_elems = 0;
+  std::vector<int> apply_cta_start;
+  int apply_total_ctas = 0;
+
+  // device buffers
+  ofm::DevBuf V, states, hphi, d_frags, d_apply_start, d_pairs, d_pieces, d_items, partials,
+      blocks, dense_H, dense_S, staging, flag;
+  ofm::DevBuf w_A, w_L, w_d, w_e, w_tau, w_tmp, w_eval;   // window-solver workspaces
+  int dense_n = 0;
+  int window_fail_col = -1;
+  std::vector<char> frag_set;       // per fragment: states imported or computed
+  struct Extra* extra = nullptr;    // tensor-core plan and eigensolver buffers
+};
+
+// helpers used by every translation unit
+ofm_status ofm_fail(ofm_ctx* c, ofm_status s, const std::string& msg);
+ofm_status ofm_cuda_check(ofm_ctx* c, cudaError_t e, const char* what);
+ofm_status ofm_ensure(ofm_ctx* c, ofm::DevBuf& b, size_t bytes, const char* what);
+
+// cross-translation-unit steps
+ofm_status ofm_apply_h(ofm_ctx* c);
+ofm_status ofm_make_dense(ofm_ctx* c);
+ofm_status ofm_plan_extra(ofm_ctx* c);        // tensor-core plan after a build
+void ofm_free_extra(ofm_ctx* c);
+ofm_status ofm_contract_tc(ofm_ctx* c, ofm_precision prec);
+ofm_status ofm_window_factor(ofm_ctx* c);
+ofm_status ofm_window_count(ofm_ctx* c, double x, bool inclusive, int* count);
+ofm_status ofm_window_bisect(ofm_ctx* c, int i_lo, int i_hi, double* E_out);
+ofm_status ofm_window_vectors(ofm_ctx* c, int m, double* C_out);
+
+#define OFM_CUDA(ctx, expr)                                             \
+  do {                                                                  \
+    cudaError_t _e = (expr);                                            \
+    if (_e != cudaSuccess) return ofm_cuda_check((ctx), _e, #expr);     \
+  } while (0)
+
+#define OFM_TRY(expr)                           \
+  do {                                          \
+    ofm_status _s = (expr);                     \
+    if (_s != OFM_OK) return _s;                \
+  } while (0)

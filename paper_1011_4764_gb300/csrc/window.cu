@@ -1,0 +1,448 @@
+// FP64 solution of the generalized eigenproblem of Eq. 2,
+//     sum_mn (H - E S) C = 0,
+// for the eigenvalues inside an energy window, on the device:
+//   1. Cholesky S = L L^T (blocked, right-looking, 32-wide panels);
+//   2. A = L^-1 H L^-T by two blocked forward substitutions;
+//   3. Householder reduction of A to a symmetric tridiagonal T (d, e);
+//   4. Sturm-sequence counts and bisection on T, one thread per wanted
+//      eigenvalue index.
+// The paper solves this step with LAPACK on one CPU (Sec. II); this is a
+// GPU route to the same numbers in the same (FP64) arithmetic.  The pivot
+// check of step 1 reports a non-positive-definite S (OFM_ERR_NOT_POSDEF).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+#include <vector>
+
+#include "ofm_internal.h"
+
+namespace ofm {
+
+constexpr int NB = 32;
+
+// ---------------------------------------------------------------- Cholesky --
+
+// Factor the kb x kb diagonal block at (k0, k0) in place (lower triangle).
+__global__ void potrf_diag_kernel(double* W, int n, int k0, int kb, int* fail_col) {
+  __shared__ double a[NB][NB + 1];
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 32
+  if (tx < kb && ty < kb) a[ty][tx] = W[(long long)(k0 + ty) * n + k0 + tx];
+  __syncthreads();
+  for (int j = 0; j < kb; ++j) {
+    if (tx == 0 && ty == 0) {
+      double piv = a[j][j];
+      if (!(piv > 0.0)) {
+        atomicCAS(fail_col, -1, k0 + j);
+        piv = 1.0;  // keep going with finite numbers; the call reports failure
+      }
+      a[j][j] = sqrt(piv);
+    }
+    __syncthreads();
+    if (tx == 0 && ty > j && ty < kb) a[ty][j] /= a[j][j];
+    __syncthreads();
+    if (ty > j && ty < kb && tx > j && tx <= ty) a[ty][tx] -= a[ty][j] * a[tx][j];
+    __syncthreads();
+  }
+  if (tx < kb && ty < kb && tx <= ty) W[(long long)(k0 + ty) * n + k0 + tx] = a[ty][tx];
+}
+
+// Rows i >= k0+kb of the panel: L21 = W21 L11^-T (forward substitution per row).
+__global__ void trsm_panel_kernel(double* W, int n, int k0, int kb) {
+  __shared__ double l[NB][NB + 1];
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    int r = e / NB, cc = e % NB;
+    l[r][cc] = (r < kb && cc <= r) ? W[(long long)(k0 + r) * n + k0 + cc] : 0.0;
+  }
+  __syncthreads();
+  const int i = k0 + kb + blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double x[NB];
+  double* row = W + (long long)i * n + k0;
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    if (j < kb) {
+      double s = row[j];
+      for (int t = 0; t < j; ++t) s -= x[t] * l[j][t];
+      x[j] = s / l[j][j];
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < NB; ++j)
+    if (j < kb) row[j] = x[j];
+}
+
+// Trailing update of the lower triangle: W22 -= L21 L21^T (32x32 tiles).
+__global__ void syrk_update_kernel(double* W, int n, int k0, int kb) {
+  const int t0 = k0 + kb;
+  const int bi = blockIdx.y, bj = blockIdx.x;
+  if (bj > bi) return;
+  __shared__ double li[NB][NB + 1], lj[NB][NB + 1];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i0 = t0 + bi * NB, j0 = t0 + bj * NB;
+  {
+    int r = i0 + ty;
+    li[ty][tx] = (r < n && tx < kb) ? W[(long long)r * n + k0 + tx] : 0.0;
+    r = j0 + ty;
+    lj[ty][tx] = (r < n && tx < kb) ? W[(long long)r * n + k0 + tx] : 0.0;
+  }
+  __syncthreads();
+  const int i = i0 + ty, j = j0 + tx;
+  if (i < n && j < n && j <= i) {
+    double s = 0.0;
+#pragma unroll 8
+    for (int t = 0; t < NB; ++t) s += li[ty][t] * lj[tx][t];
+    W[(long long)i * n + j] -= s;
+  }
+}
+
+// ------------------------------------------------------ triangular solves --
+
+// X_k = L_kk^-1 B_k for the kb rows of block k (one thread per column).
+__global__ void trsm_diag_rows_kernel(const double* L, double* B, int n, int k0, int kb) {
+  __shared__ double l[NB][NB + 1];
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    int r = e / NB, cc = e % NB;
+    l[r][cc] = (r < kb && cc <= r) ? L[(long long)(k0 + r) * n + k0 + cc] : 0.0;
+  }
+  __syncthreads();
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  double x[NB];
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    if (j < kb) {
+      double s = B[(long long)(k0 + j) * n + c];
+      for (int t = 0; t < j; ++t) s -= l[j][t] * x[t];
+      x[j] = s / l[j][j];
+      B[(long long)(k0 + j) * n + c] = x[j];
+    }
+  }
+}
+
+// B[i, :] -= L[i, k0:k0+kb] X_k for rows i >= k0+kb (64 x 64 output tiles).
+__global__ void gemm_update_rows_kernel(const double* L, double* B, int n, int k0, int kb) {
+  __shared__ double ls[64][NB + 1];
+  __shared__ double xs[NB][64 + 1];
+  const int r0 = k0 + kb + blockIdx.y * 64, c0 = blockIdx.x * 64;
+  const int tid = threadIdx.x;  // 256
+  for (int e = tid; e < 64 * NB; e += 256) {
+    int r = e / NB, t = e % NB;
+    ls[r][t] = (r0 + r < n && t < kb) ? L[(long long)(r0 + r) * n + k0 + t] : 0.0;
+  }
+  for (int e = tid; e < NB * 64; e += 256) {
+    int t = e / 64, cc = e % 64;
+    xs[t][cc] = (t < kb && c0 + cc < n) ? B[(long long)(k0 + t) * n + c0 + cc] : 0.0;
+  }
+  __syncthreads();
+  const int tx = tid % 16, ty = tid / 16;
+  double acc[4][4] = {};
+  for (int t = 0; t < NB; ++t) {
+    double a[4], b[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = ls[ty * 4 + i][t];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) b[j] = xs[t][tx * 4 + j];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int r = r0 + ty * 4 + i;
+    if (r >= n) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int cc = c0 + tx * 4 + j;
+      if (cc < n) B[(long long)r * n + cc] -= acc[i][j];
+    }
+  }
+}
+
+__global__ void transpose_kernel(const double* in, double* out, int n) {
+  __shared__ double t[32][33];
+  int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 32 + threadIdx.y;
+  if (x < n && y < n) t[threadIdx.y][threadIdx.x] = in[(long long)y * n + x];
+  __syncthreads();
+  x = blockIdx.y * 32 + threadIdx.x;
+  y = blockIdx.x * 32 + threadIdx.y;
+  if (x < n && y < n) out[(long long)y * n + x] = t[threadIdx.x][threadIdx.y];
+}
+
+__global__ void symmetrize_kernel(double* A, int n) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)n * n) return;
+  int i = (int)(e / n), j = (int)(e % n);
+  if (j >= i) return;
+  double v = 0.5 * (A[(long long)i * n + j] + A[(long long)j * n + i]);
+  A[(long long)i * n + j] = v;
+  A[(long long)j * n + i] = v;
+}
+
+// ------------------------------------------------------- tridiagonalise ----
+
+// Householder vector for column k: x = A[k+1:, k]; v = x - alpha e1 with
+// alpha = -sign(x0) ||x||, tau = 2 / v^T v.  Stores v in vbuf[k+1:] and in
+// A[k+1:, k] (for the back-transformation), d[k], e[k], tau[k].
+__global__ void householder_kernel(double* A, int n, int k, double* vbuf, double* d, double* e,
+                                   double* tau) {
+  __shared__ double red[32];
+  const int m = n - k - 1;
+  double s = 0.0;
+  for (int i = threadIdx.x + 1; i < m; i += blockDim.x) {
+    double x = A[(long long)(k + 1 + i) * n + k];
+    s += x * x;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) red[0] = s;
+  }
+  __syncthreads();
+  const double sig = red[0];  // ||x[1:]||^2
+  const double x0 = A[(long long)(k + 1) * n + k];
+  double alpha, t, v0;
+  if (sig == 0.0) {
+    alpha = x0;
+    t = 0.0;
+    v0 = 1.0;
+  } else {
+    const double nrm = sqrt(x0 * x0 + sig);
+    alpha = (x0 > 0.0) ? -nrm : nrm;
+    v0 = x0 - alpha;
+    t = 2.0 / (v0 * v0 + sig);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    double v = (i == 0) ? v0 : A[(long long)(k + 1 + i) * n + k];
+    vbuf[k + 1 + i] = v;
+    A[(long long)k * n + k + 1 + i] = v;  // row k keeps v for the back-transformation
+  }
+  if (threadIdx.x == 0) {
+    d[k] = A[(long long)k * n + k];
+    e[k] = alpha;
+    tau[k] = t;
+  }
+}
+
+// p = tau * A22 v over rows k+1.. (one warp per row).
+__global__ void symv_kernel(const double* A, int n, int k, const double* vbuf, const double* tau,
+                            double* p) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int i = k + 1 + warp;
+  if (i >= n) return;
+  const double* row = A + (long long)i * n;
+  double s = 0.0;
+  for (int j = k + 1 + lane; j < n; j += 32) s += row[j] * vbuf[j];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) p[i] = tau[k] * s;
+}
+
+// A22 -= v w^T + w v^T with w = p - (tau/2)(v^T p) v; every CTA forms v^T p
+// itself (a short read of two vectors) so the step needs no extra launch.
+__global__ void rank2_kernel(double* A, int n, int k, const double* vbuf, const double* p,
+                             const double* tau) {
+  __shared__ double red[8];
+  __shared__ double Ks;
+  double s = 0.0;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  for (int j = k + 1 + tid; j < n; j += blockDim.x * blockDim.y) s += vbuf[j] * p[j];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((tid & 31) == 0) red[tid >> 5] = s;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x * blockDim.y) / 32; ++w) t += red[w];
+    Ks = 0.5 * tau[k] * t;
+  }
+  __syncthreads();
+  const double K = Ks;
+  const int i = k + 1 + blockIdx.y * blockDim.y + threadIdx.y;
+  const int j0 = k + 1 + blockIdx.x * 64;
+  if (i >= n) return;
+  const double vi = vbuf[i], wi = p[i] - K * vi;
+  for (int jj = threadIdx.x; jj < 64; jj += blockDim.x) {
+    const int j = j0 + jj;
+    if (j >= n) break;
+    const double vj = vbuf[j], wj = p[j] - K * vj;
+    A[(long long)i * n + j] -= vi * wj + wi * vj;
+  }
+}
+
+__global__ void tridiag_tail_kernel(const double* A, int n, double* d, double* e) {
+  if (n >= 2) {
+    d[n - 2] = A[(long long)(n - 2) * n + n - 2];
+    e[n - 2] = A[(long long)(n - 1) * n + n - 2];
+  }
+  d[n - 1] = A[(long long)(n - 1) * n + n - 1];
+}
+
+// ---------------------------------------------------------------- bisection --
+
+// Number of eigenvalues of T below x (negative pivots of T - x I).
+__device__ int sturm_count(const double* d, const double* e, int n, double x, double pivmin) {
+  int c = 0;
+  double q = d[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  if (q < 0) ++c;
+  for (int j = 1; j < n; ++j) {
+    q = d[j] - x - e[j - 1] * e[j - 1] / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    if (q < 0) ++c;
+  }
+  return c;
+}
+
+__device__ void gersh(const double* d, const double* e, int n, double* lo, double* hi) {
+  double a = DBL_MAX, b = -DBL_MAX;
+  for (int j = 0; j < n; ++j) {
+    double r = (j > 0 ? fabs(e[j - 1]) : 0.0) + (j < n - 1 ? fabs(e[j]) : 0.0);
+    a = fmin(a, d[j] - r);
+    b = fmax(b, d[j] + r);
+  }
+  double w = fmax(fabs(a), fabs(b));
+  *lo = a - 2.0 * DBL_EPSILON * w - 1e-300;
+  *hi = b + 2.0 * DBL_EPSILON * w + 1e-300;
+}
+
+__device__ double pivmin_of(const double* e, int n) {
+  double m = 0.0;
+  for (int j = 0; j < n - 1; ++j) m = fmax(m, e[j] * e[j]);
+  return fmax(DBL_MIN, DBL_MIN * m);
+}
+
+__global__ void count_kernel(const double* d, const double* e, int n, double x, int* out) {
+  *out = sturm_count(d, e, n, x, pivmin_of(e, n));
+}
+
+__global__ void bisect_kernel(const double* d, const double* e, int n, int i_lo, int m, double* out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m) return;
+  const int idx = i_lo + t;
+  double lo, hi;
+  gersh(d, e, n, &lo, &hi);
+  const double pm = pivmin_of(e, n);
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + 4.0 * DBL_MIN || mid == lo || mid == hi) break;
+    if (sturm_count(d, e, n, mid, pm) > idx) hi = mid; else lo = mid;
+  }
+  out[t] = 0.5 * (lo + hi);
+}
+
+}  // namespace ofm
+
+using namespace ofm;
+
+static ofm_status sync_ctx(ofm_ctx* c, const char* what) {
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return ofm_cuda_check(c, e, what);
+  return OFM_OK;
+}
+
+// Solve L X = B in place in B (n x n), L lower triangular in Lbuf.
+static void trsm_lower_left(const double* L, double* B, int n, cudaStream_t s) {
+  for (int k0 = 0; k0 < n; k0 += NB) {
+    const int kb = std::min(NB, n - k0);
+    trsm_diag_rows_kernel<<<(n + 127) / 128, 128, 0, s>>>(L, B, n, k0, kb);
+    const int rows = n - k0 - kb;
+    if (rows > 0) {
+      dim3 g((n + 63) / 64, (rows + 63) / 64);
+      gemm_update_rows_kernel<<<g, 256, 0, s>>>(L, B, n, k0, kb);
+    }
+  }
+}
+
+ofm_status ofm_window_factor(ofm_ctx* c) {
+  const int n = c->dense_n;
+  const size_t bytes = sizeof(double) * (size_t)n * n;
+  OFM_TRY(ofm_ensure(c, c->w_L, bytes, "window L"));
+  OFM_TRY(ofm_ensure(c, c->w_A, bytes, "window A"));
+  OFM_TRY(ofm_ensure(c, c->w_d, sizeof(double) * n, "window d"));
+  OFM_TRY(ofm_ensure(c, c->w_e, sizeof(double) * n, "window e"));
+  OFM_TRY(ofm_ensure(c, c->w_tau, sizeof(double) * n, "window tau"));
+  OFM_TRY(ofm_ensure(c, c->w_tmp, sizeof(double) * 2 * n, "window vectors"));
+  double* L = (double*)c->w_L.p;
+  double* A = (double*)c->w_A.p;
+  int* flag = (int*)c->flag.p;
+  cudaStream_t s = c->stream;
+  OFM_CUDA(c, cudaMemcpyAsync(L, c->dense_S.p, bytes, cudaMemcpyDeviceToDevice, s));
+  OFM_CUDA(c, cudaMemsetAsync(flag, 0xff, sizeof(int), s));  // -1: no failure
+  // 1. Cholesky
+  for (int k0 = 0; k0 < n; k0 += NB) {
+    const int kb = std::min(NB, n - k0);
+    potrf_diag_kernel<<<1, dim3(32, 32), 0, s>>>(L, n, k0, kb, flag);
+    const int rows = n - k0 - kb;
+    if (rows > 0) {
+      trsm_panel_kernel<<<(rows + 127) / 128, 128, 0, s>>>(L, n, k0, kb);
+      const int tb = (rows + NB - 1) / NB;
+      syrk_update_kernel<<<dim3(tb, tb), dim3(32, 32), 0, s>>>(L, n, k0, kb);
+    }
+  }
+  OFM_CUDA(c, cudaGetLastError());
+  int fail = -1;
+  OFM_CUDA(c, cudaMemcpyAsync(&fail, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  OFM_TRY(sync_ctx(c, "Cholesky of S"));
+  if (fail >= 0) {
+    c->window_fail_col = fail;
+    char buf[160];
+    snprintf(buf, sizeof buf, "S is not positive definite: Cholesky pivot %d is not positive", fail);
+    return ofm_fail(c, OFM_ERR_NOT_POSDEF, buf);
+  }
+  // 2. A = L^-1 H L^-T: X = L^-1 H, then A = L^-1 X^T
+  double* T = (double*)c->dense_H.p;  // kept intact: work on a copy
+  OFM_CUDA(c, cudaMemcpyAsync(A, T, bytes, cudaMemcpyDeviceToDevice, s));
+  trsm_lower_left(L, A, n, s);
+  OFM_TRY(ofm_ensure(c, c->w_eval, bytes, "window scratch"));
+  double* X = (double*)c->w_eval.p;
+  dim3 tg((n + 31) / 32, (n + 31) / 32);
+  transpose_kernel<<<tg, dim3(32, 32), 0, s>>>(A, X, n);
+  trsm_lower_left(L, X, n, s);
+  symmetrize_kernel<<<(int)(((long long)n * n + 255) / 256), 256, 0, s>>>(X, n);
+  OFM_CUDA(c, cudaMemcpyAsync(A, X, bytes, cudaMemcpyDeviceToDevice, s));
+  OFM_CUDA(c, cudaGetLastError());
+  // 3. tridiagonalise
+  double* d = (double*)c->w_d.p;
+  double* e = (double*)c->w_e.p;
+  double* tau = (double*)c->w_tau.p;
+  double* vbuf = (double*)c->w_tmp.p;
+  double* p = vbuf + n;
+  for (int k = 0; k + 2 < n; ++k) {
+    householder_kernel<<<1, 256, 0, s>>>(A, n, k, vbuf, d, e, tau);
+    const int m = n - k - 1;
+    symv_kernel<<<(m + 7) / 8, 256, 0, s>>>(A, n, k, vbuf, tau, p);
+    rank2_kernel<<<dim3((m + 63) / 64, (m + 7) / 8), dim3(32, 8), 0, s>>>(A, n, k, vbuf, p, tau);
+  }
+  tridiag_tail_kernel<<<1, 1, 0, s>>>(A, n, d, e);
+  OFM_CUDA(c, cudaGetLastError());
+  OFM_TRY(sync_ctx(c, "tridiagonalisation"));
+  c->factored = true;
+  return OFM_OK;
+}
+
+ofm_status ofm_window_count(ofm_ctx* c, double x, bool inclusive, int* count) {
+  if (inclusive) x = std::nextafter(x, HUGE_VAL);
+  int* dc = (int*)c->flag.p + 1;
+  count_kernel<<<1, 1, 0, c->stream>>>((const double*)c->w_d.p, (const double*)c->w_e.p,
+                                       c->dense_n, x, dc);
+  OFM_CUDA(c, cudaGetLastError());
+  OFM_CUDA(c, cudaMemcpyAsync(count, dc, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  return sync_ctx(c, "Sturm count");
+}
+
+ofm_status ofm_window_bisect(ofm_ctx* c, int i_lo, int i_hi, double* E_out) {
+  const int m = i_hi - i_lo;
+  double* out = (double*)c->w_tmp.p;  // 2n doubles, m <= n
+  bisect_kernel<<<(m + 127) / 128, 128, 0, c->stream>>>((const double*)c->w_d.p,
+                                                       (const double*)c->w_e.p, c->dense_n, i_lo,
+                                                       m, out);
+  OFM_CUDA(c, cudaGetLastError());
+  OFM_CUDA(c, cudaMemcpyAsync(E_out, out, sizeof(double) * m, cudaMemcpyDeviceToHost, c->stream));
+  return sync_ctx(c, "bisection");
+}

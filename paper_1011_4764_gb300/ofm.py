@@ -1,0 +1,304 @@
+"""Thin ctypes binding of libofm.so (include/ofm.h).
+
+Every function marshals arguments and calls the C ABI of the same name; all
+computation runs in the library's CUDA kernels.  There is no fallback: if
+the library is missing or fails to load, the import of the entry points
+raises.  PyTorch is used only to hand device pointers and streams across.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libofm.so")
+
+OFM_OK, OFM_ERR_INVALID, OFM_ERR_OOM, OFM_ERR_CUDA = 0, 1, 2, 3
+OFM_ERR_NOT_CONVERGED, OFM_ERR_NOT_POSDEF, OFM_ERR_TIMEOUT, OFM_ERR_STATE = 4, 5, 6, 7
+PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3, "bf16x3": 4}
+STORE = {"fp64": 0, "fp32": 1}
+HOST, DEVICE = 0, 1
+
+# every symbol the header declares (checked by the CPU tests)
+EXPORTS = [
+    "ofm_create", "ofm_destroy", "ofm_last_error", "ofm_status_string", "ofm_build_fragments",
+    "ofm_fragment_eigs", "ofm_set_fragment_states", "ofm_get_fragment_states",
+    "ofm_assemble_HS", "ofm_get_pairs", "ofm_get_plan_info", "ofm_get_block",
+    "ofm_get_dense_HS", "ofm_get_hphi", "ofm_window_eigs", "ofm_eigs_by_index",
+    "ofm_set_dense_HS", "ofm_plan_pairs",
+]
+
+
+class ofm_grid(C.Structure):
+    _fields_ = [("n", C.c_int * 3), ("h", C.c_double)]
+
+
+class ofm_fragment(C.Structure):
+    _fields_ = [("off", C.c_int * 3), ("ext", C.c_int * 3), ("n_states", C.c_int)]
+
+
+class ofm_eig_opts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("degree", C.c_int),
+                ("extra_states", C.c_int), ("seed", C.c_uint64)]
+
+
+class ofm_assemble_opts(C.Structure):
+    _fields_ = [("chunk_points", C.c_int), ("keep_hphi", C.c_int)]
+
+
+class ofm_plan_info(C.Structure):
+    _fields_ = [("n_frag", C.c_int), ("n_pairs", C.c_int), ("basis_size", C.c_int),
+                ("n_work_items", C.c_int), ("pair_flops", C.c_longlong),
+                ("overlap_points_s", C.c_longlong), ("overlap_points_h", C.c_longlong),
+                ("state_bytes", C.c_longlong), ("hphi_bytes", C.c_longlong),
+                ("apply_points", C.c_longlong)]
+
+
+_LIB = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libofm.so once and declare the signatures.  Raises when absent."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libofm.so not found at {path}; build it with "
+                           "paper_1011_4764_gb300.build.build() (no CPU fallback exists)")
+    lib = C.CDLL(path)
+    P, I, D = C.c_void_p, C.c_int, C.c_double
+    DP, IP = C.POINTER(C.c_double), C.POINTER(C.c_int)
+    sig = {
+        "ofm_create": ([C.POINTER(C.c_void_p), P], I),
+        "ofm_destroy": ([P], None),
+        "ofm_last_error": ([P], C.c_char_p),
+        "ofm_status_string": ([I], C.c_char_p),
+        "ofm_build_fragments": ([P, C.POINTER(ofm_grid), P, I, C.POINTER(ofm_fragment), I, I], I),
+        "ofm_fragment_eigs": ([P, C.POINTER(ofm_eig_opts), DP, DP], I),
+        "ofm_set_fragment_states": ([P, I, P, I], I),
+        "ofm_get_fragment_states": ([P, I, P, I], I),
+        "ofm_assemble_HS": ([P, I, C.POINTER(ofm_assemble_opts)], I),
+        "ofm_get_pairs": ([P, IP, IP], I),
+        "ofm_get_plan_info": ([P, C.POINTER(ofm_plan_info)], I),
+        "ofm_get_block": ([P, I, I, DP, DP], I),
+        "ofm_get_dense_HS": ([P, P, P, I], I),
+        "ofm_get_hphi": ([P, I, DP], I),
+        "ofm_window_eigs": ([P, D, D, I, DP, IP, DP], I),
+        "ofm_eigs_by_index": ([P, I, I, DP], I),
+        "ofm_set_dense_HS": ([P, I, DP, DP], I),
+        "ofm_plan_pairs": ([C.POINTER(ofm_grid), C.POINTER(ofm_fragment), I, IP, IP,
+                            C.POINTER(C.c_longlong), I, C.POINTER(C.c_longlong)], I),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _LIB = lib
+    return lib
+
+
+class OFMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{status_name(status)}: {msg}")
+        self.status = status
+
+
+def status_name(s: int) -> str:
+    return load_library().ofm_status_string(s).decode()
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _iptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int))
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _c_geometry(grid, frags):
+    g = ofm_grid((C.c_int * 3)(*grid.n), float(grid.h))
+    fa = (ofm_fragment * len(frags))()
+    for i, f in enumerate(frags):
+        fa[i].off = (C.c_int * 3)(*f.off)
+        fa[i].ext = (C.c_int * 3)(*f.ext)
+        fa[i].n_states = int(f.n_states)
+    return g, fa
+
+
+def plan_pairs(grid, frags):
+    """Host-only planner query: (pairs, counts (P, 2): |B_a∩B_b|, |B_a∩B_b+|, flops)."""
+    lib = load_library()
+    g, fa = _c_geometry(grid, frags)
+    n = C.c_int()
+    s = lib.ofm_plan_pairs(C.byref(g), fa, len(frags), C.byref(n), None, None, 0, None)
+    if s != OFM_OK:
+        raise OFMError(s, "invalid geometry")
+    ab = np.zeros(2 * n.value, dtype=np.int32)
+    cnt = np.zeros(2 * n.value, dtype=np.int64)
+    F = C.c_longlong()
+    lib.ofm_plan_pairs(C.byref(g), fa, len(frags), C.byref(n), _iptr(ab),
+                       cnt.ctypes.data_as(C.POINTER(C.c_longlong)), n.value, C.byref(F))
+    return [tuple(map(int, ab[2 * i:2 * i + 2])) for i in range(n.value)], cnt.reshape(-1, 2), F.value
+
+
+class Context:
+    """One library context (ofm_ctx) bound to a CUDA stream."""
+
+    def __init__(self, stream=None):
+        self.lib = load_library()
+        h = C.c_void_p()
+        st = None
+        if stream is not None:
+            st = C.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+        s = self.lib.ofm_create(C.byref(h), st)
+        if s != OFM_OK:
+            raise OFMError(s, "ofm_create failed")
+        self.h = h
+        self.frags = []
+        self.grid = None
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.ofm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, s, allow=()):
+        if s != OFM_OK and s not in allow:
+            raise OFMError(s, self.lib.ofm_last_error(self.h).decode())
+        return s
+
+    # -- ofm_build_fragments
+    def build_fragments(self, grid, V, frags, storage="fp32"):
+        """grid: object with .n (nx, ny, nz) and .h; V: float64 array (nz, ny, nx)
+        as numpy (host) or a CUDA torch tensor (device); frags: objects with
+        .off, .ext, .n_states."""
+        g, fa = _c_geometry(grid, frags)
+        if _is_torch(V):
+            assert V.is_cuda and str(V.dtype) == "torch.float64" and V.is_contiguous()
+            ptr, loc = C.c_void_p(V.data_ptr()), DEVICE
+            keep = V
+        else:
+            keep = np.ascontiguousarray(V, dtype=np.float64)
+            ptr, loc = C.c_void_p(keep.ctypes.data), HOST
+        self._check(self.lib.ofm_build_fragments(self.h, C.byref(g), ptr, loc, fa, len(frags),
+                                                 STORE[storage]))
+        del keep
+        self.frags = list(frags)
+        self.grid = grid
+        return self
+
+    # -- ofm_fragment_eigs
+    def fragment_eigs(self, tol=0.0, max_iter=0, degree=0, extra_states=0, seed=0,
+                      allow_not_converged=False):
+        n = sum(f.n_states for f in self.frags)
+        eps = np.zeros(n)
+        res = np.zeros(n)
+        o = ofm_eig_opts(tol, max_iter, degree, extra_states, seed)
+        s = self._check(self.lib.ofm_fragment_eigs(self.h, C.byref(o), _dptr(eps), _dptr(res)),
+                        allow=(OFM_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+        return eps, res, s
+
+    # -- ofm_set_fragment_states / ofm_get_fragment_states
+    def set_fragment_states(self, a, phi):
+        """phi: numpy (P_a, n_a) float64 array of box states (column j = state
+        j), or a CUDA float64 torch tensor of shape (n_a, P_a), contiguous
+        (the same column-major memory)."""
+        if _is_torch(phi):
+            assert phi.is_cuda and phi.is_contiguous() and str(phi.dtype) == "torch.float64"
+            self._check(self.lib.ofm_set_fragment_states(self.h, a, C.c_void_p(phi.data_ptr()), DEVICE))
+            return
+        arr = np.asfortranarray(phi, dtype=np.float64)
+        self._check(self.lib.ofm_set_fragment_states(self.h, a, C.c_void_p(arr.ctypes.data), HOST))
+
+    def get_fragment_states(self, a):
+        f = self.frags[a]
+        P = f.ext[0] * f.ext[1] * f.ext[2]
+        out = np.zeros((f.n_states, P))
+        self._check(self.lib.ofm_get_fragment_states(self.h, a, C.c_void_p(out.ctypes.data), HOST))
+        return out.T
+
+    # -- ofm_assemble_HS
+    def assemble(self, precision="fp32", chunk_points=0):
+        o = ofm_assemble_opts(chunk_points, 1)
+        self._check(self.lib.ofm_assemble_HS(self.h, PREC[precision], C.byref(o)))
+
+    def pairs(self):
+        n = C.c_int()
+        self._check(self.lib.ofm_get_pairs(self.h, C.byref(n), None))
+        out = np.zeros(2 * n.value, dtype=np.int32)
+        self._check(self.lib.ofm_get_pairs(self.h, C.byref(n), _iptr(out)))
+        return [tuple(map(int, out[2 * i:2 * i + 2])) for i in range(n.value)]
+
+    def plan_info(self):
+        info = ofm_plan_info()
+        self._check(self.lib.ofm_get_plan_info(self.h, C.byref(info)))
+        return {k: getattr(info, k) for k, _ in ofm_plan_info._fields_}
+
+    def block(self, a, b):
+        na, nb = self.frags[a].n_states, self.frags[b].n_states
+        H = np.zeros((na, nb))
+        S = np.zeros((na, nb))
+        self._check(self.lib.ofm_get_block(self.h, a, b, _dptr(H), _dptr(S)))
+        return H, S
+
+    def dense_HS(self, out_H=None, out_S=None):
+        """Host numpy arrays, or CUDA torch tensors when out_H/out_S are given."""
+        if out_H is not None or out_S is not None:
+            pH = C.c_void_p(out_H.data_ptr()) if out_H is not None else None
+            pS = C.c_void_p(out_S.data_ptr()) if out_S is not None else None
+            self._check(self.lib.ofm_get_dense_HS(self.h, pH, pS, DEVICE))
+            return out_H, out_S
+        n = sum(f.n_states for f in self.frags)
+        H = np.zeros((n, n))
+        S = np.zeros((n, n))
+        self._check(self.lib.ofm_get_dense_HS(self.h, C.c_void_p(H.ctypes.data),
+                                              C.c_void_p(S.ctypes.data), HOST))
+        return H, S
+
+    def hphi(self, b):
+        f = self.frags[b]
+        Pd = 1
+        for d in range(3):
+            Pd *= f.ext[d] + 2 if f.ext[d] < self.grid.n[d] else f.ext[d]
+        out = np.zeros((f.n_states, Pd))
+        self._check(self.lib.ofm_get_hphi(self.h, b, _dptr(out)))
+        return out.T
+
+    # -- ofm_window_eigs / ofm_eigs_by_index / ofm_set_dense_HS
+    def window_eigs(self, E_lo, E_hi, max_out=None, vectors=False, n_basis=None):
+        if max_out is None:
+            max_out = n_basis or sum(f.n_states for f in self.frags) or 1
+        E = np.zeros(max(1, max_out))
+        nout = C.c_int()
+        Cv = None
+        if vectors:
+            n = n_basis or sum(f.n_states for f in self.frags)
+            Cv = np.zeros((max_out, n))
+        self._check(self.lib.ofm_window_eigs(self.h, float(E_lo), float(E_hi), max_out, _dptr(E),
+                                             C.byref(nout), _dptr(Cv) if vectors else None))
+        m = min(nout.value, max_out)
+        if vectors:
+            return E[:m], Cv[:m].T, nout.value
+        return E[:m], nout.value
+
+    def eigs_by_index(self, i_lo, i_hi):
+        E = np.zeros(max(1, i_hi - i_lo))
+        self._check(self.lib.ofm_eigs_by_index(self.h, i_lo, i_hi, _dptr(E)))
+        return E[:i_hi - i_lo]
+
+    def set_dense_HS(self, H, S):
+        H = np.ascontiguousarray(H, dtype=np.float64)
+        S = np.ascontiguousarray(S, dtype=np.float64)
+        self._check(self.lib.ofm_set_dense_HS(self.h, H.shape[0], _dptr(H), _dptr(S)))
