@@ -78,6 +78,11 @@ static int find_pair(const ofm_ctx* c, int a, int b) {
   return -1;
 }
 
+void ofm_free_extra(ofm_ctx* c) {
+  ofm_eig_free(c);
+  ofm_tc_free(c);
+}
+
 // ------------------------------------------------------------- lifecycle ---
 
 extern "C" const char* ofm_status_string(ofm_status s) {

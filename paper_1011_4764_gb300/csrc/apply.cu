@@ -109,6 +109,69 @@ void launch_apply_global(const DevFrag* d_fr, const int* d_cta_start, int nfrag,
         gn[1], gn[2], (float)c0, (float)c1);
 }
 
+// Fragment-mode apply for the eigensolver: the fragment Hamiltonian is the
+// principal submatrix of H on the box, so only interior points are written
+// (the zero halo stays zero) and the stencil reads zeros beyond the box.
+// One fused step of the scaled Chebyshev three-term recurrence:
+//     out = alpha_f * (H_f in - c_f in) + beta_f * prev
+// with per-fragment coefficients coef[f] = (alpha, beta, c); prev may be
+// null when beta is zero.
+template <typename T>
+__global__ void __launch_bounds__(256) apply_filter_kernel(
+    const DevFrag* __restrict__ fr, const int* __restrict__ cta_start, int nfrag,
+    const T* __restrict__ V, const T* __restrict__ in, const T* __restrict__ prev,
+    T* __restrict__ out, const double* __restrict__ coef, int gx, int gy, int gz, T c0, T c1) {
+  using V16 = typename Vec16<T>::type;
+  constexpr int VN = Vec16<T>::n;
+  const int f = find_frag(cta_start, nfrag, blockIdx.x);
+  const DevFrag F = fr[f];
+  const int q_per_pt = F.ld / VN;
+  const long long e = (long long)(blockIdx.x - cta_start[f]) * blockDim.x + threadIdx.x;
+  if (e >= F.Pd * q_per_pt) return;
+  const long long p = e / q_per_pt;
+  const int q = (int)(e - p * q_per_pt);
+  const int ex = F.dext[0], ey = F.dext[1], ez = F.dext[2];
+  const int x = (int)(p % ex);
+  const int y = (int)((p / ex) % ey);
+  const int z = (int)(p / ((long long)ex * ey));
+  if (x < F.lo[0] || x >= F.lo[0] + F.ext[0] || y < F.lo[1] || y >= F.lo[1] + F.ext[1] ||
+      z < F.lo[2] || z >= F.lo[2] + F.ext[2])
+    return;
+  const int X = (F.doff[0] + x) % gx, Y = (F.doff[1] + y) % gy, Z = (F.doff[2] + z) % gz;
+  const T alpha = (T)coef[3 * f], beta = (T)coef[3 * f + 1], shift = (T)coef[3 * f + 2];
+  const T v = V[((long long)Z * gy + Y) * gx + X];
+  const V16* S = reinterpret_cast<const V16*>(in + F.off);
+  const long long sx = 1, sy = ex, sz = (long long)ex * ey;
+  V16 ctr = S[p * q_per_pt + q];
+  V16 sum = zero4(T());
+  long long nb;
+  if ((nb = nb_index(p, x, ex, F.full[0], +1, sx)) >= 0) sum = add4(sum, S[nb * q_per_pt + q]);
+  if ((nb = nb_index(p, x, ex, F.full[0], -1, sx)) >= 0) sum = add4(sum, S[nb * q_per_pt + q]);
+  if ((nb = nb_index(p, y, ey, F.full[1], +1, sy)) >= 0) sum = add4(sum, S[nb * q_per_pt + q]);
+  if ((nb = nb_index(p, y, ey, F.full[1], -1, sy)) >= 0) sum = add4(sum, S[nb * q_per_pt + q]);
+  if ((nb = nb_index(p, z, ez, F.full[2], +1, sz)) >= 0) sum = add4(sum, S[nb * q_per_pt + q]);
+  if ((nb = nb_index(p, z, ez, F.full[2], -1, sz)) >= 0) sum = add4(sum, S[nb * q_per_pt + q]);
+  V16 hy = fma4(c0 + v - shift, ctr, zero4(T()));
+  hy = fma4(-c1, sum, hy);
+  V16 o = fma4(alpha, hy, zero4(T()));
+  if (prev != nullptr) o = fma4(beta, reinterpret_cast<const V16*>(prev + F.off)[p * q_per_pt + q], o);
+  reinterpret_cast<V16*>(out + F.off)[p * q_per_pt + q] = o;
+}
+
+void launch_apply_filter(const DevFrag* d_fr, const int* d_cta_start, int nfrag, int total_ctas,
+                         const void* V, const void* in, const void* prev, void* out,
+                         const double* coef, const int gn[3], double h, bool fp64, cudaStream_t s) {
+  const double c0 = 3.0 / (h * h), c1 = 0.5 / (h * h);
+  if (fp64)
+    apply_filter_kernel<double><<<total_ctas, 256, 0, s>>>(
+        d_fr, d_cta_start, nfrag, (const double*)V, (const double*)in, (const double*)prev,
+        (double*)out, coef, gn[0], gn[1], gn[2], c0, c1);
+  else
+    apply_filter_kernel<float><<<total_ctas, 256, 0, s>>>(
+        d_fr, d_cta_start, nfrag, (const float*)V, (const float*)in, (const float*)prev,
+        (float*)out, coef, gn[0], gn[1], gn[2], (float)c0, (float)c1);
+}
+
 // ------------------------------------------------------------ conversions --
 
 template <typename T>

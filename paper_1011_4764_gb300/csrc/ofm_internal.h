@@ -96,6 +96,9 @@ void launch_import_states(const DevFrag* d_fr, int a, const DevFrag& fa, const d
                           void* states, bool fp64, cudaStream_t s);
 void launch_export_states(const DevFrag& fa, const void* states, double* dst, bool fp64,
                           bool dilated_hphi, cudaStream_t s);
+void launch_apply_filter(const DevFrag* d_fr, const int* d_cta_start, int nfrag, int total_ctas,
+                         const void* V, const void* in, const void* prev, void* out,
+                         const double* coef, const int gn[3], double h, bool fp64, cudaStream_t s);
 void launch_convert_V(const double* src, void* dst, long long n, bool fp64, cudaStream_t s);
 void launch_contract_simt(int prec, bool store_fp64, const DevFrag* d_fr, const DevPair* d_pairs,
                           const Piece* d_pieces, const WorkItem* d_items, int nitems,
@@ -154,7 +157,9 @@ struct ofm_ctx {
   int dense_n = 0;
   int window_fail_col = -1;
   std::vector<char> frag_set;       // per fragment: states imported or computed
-  struct Extra* extra = nullptr;    // tensor-core plan and eigensolver buffers
+  int last_eig_iters = 0;           // filter iterations of the last fragment eigensolve
+  struct EigWork* eig = nullptr;    // fragment-eigensolver buffers and plan
+  struct TcPlan* tc = nullptr;      // tensor-core contraction plan
 };
 
 // helpers used by every translation unit
@@ -166,7 +171,9 @@ ofm_status ofm_ensure(ofm_ctx* c, ofm::DevBuf& b, size_t bytes, const char* what
 ofm_status ofm_apply_h(ofm_ctx* c);
 ofm_status ofm_make_dense(ofm_ctx* c);
 ofm_status ofm_plan_extra(ofm_ctx* c);        // tensor-core plan after a build
-void ofm_free_extra(ofm_ctx* c);
+void ofm_free_extra(ofm_ctx* c);              // frees eig and tc
+void ofm_eig_free(ofm_ctx* c);
+void ofm_tc_free(ofm_ctx* c);
 ofm_status ofm_contract_tc(ofm_ctx* c, ofm_precision prec);
 ofm_status ofm_window_factor(ofm_ctx* c);
 ofm_status ofm_window_count(ofm_ctx* c, double x, bool inclusive, int* count);

@@ -16,13 +16,3 @@ def gpu_lib():
     build.build()
     from paper_1011_4764_gb300 import ofm
     return ofm
-
-
-def zero_extend_on_dilated(grid, frag, dil_off, dil_ext, values):
-    """Place box values (P, n) into the dilated box order (Pd, n)."""
-    raise NotImplementedError
-
-
-def sum_abs_products(A, B):
-    """Sigma_r |A_ri| |B_rj| for the error bounds of inner products."""
-    return np.abs(A).T @ np.abs(B)

@@ -9,7 +9,7 @@ import pytest
 from ofm_inputs import Fragment, Grid, make_workload, random_states, small_workload
 from oracle import ofm_oracle as O
 
-from gpu_util import U32, gpu_lib, sum_abs_products
+from gpu_util import U32, gpu_lib
 
 pytestmark = pytest.mark.gpu
 
@@ -17,6 +17,13 @@ pytestmark = pytest.mark.gpu
 @pytest.fixture(scope="module")
 def ofm():
     return gpu_lib()
+
+
+def abs_overlap(grid, fa, Pa, fb, Pb):
+    """sum_r |phi_a(r)| |phi_b(r)| with zero-extended states."""
+    Ea = O.zero_extend(grid, fa, Pa)
+    Eb = O.zero_extend(grid, fb, Pb)
+    return (abs(Ea).T @ abs(Eb)).toarray()
 
 
 def oracle_with_states(wl, Phis):
@@ -90,7 +97,7 @@ def test_random_states_fp64_blocks_exact(ofm, geom):
     assert ctx.pairs() == pairs
     for (a, b), (Hab, Sab) in blocks.items():
         Hg, Sg = ctx.block(a, b)
-        bound_s = 1e-13 * max(1.0, sum_abs_products(Phis[a], Phis[b]).max())
+        bound_s = 1e-13 * max(1.0, abs_overlap(wl.grid, frags[a], Phis[a], frags[b], Phis[b]).max())
         assert np.max(np.abs(Sg - Sab)) < bound_s, (a, b)
         assert np.max(np.abs(Hg - Hab)) < 1e-12 * max(1.0, np.abs(Hab).max()), (a, b)
     for b, f in enumerate(frags):
@@ -162,7 +169,7 @@ def test_fp64_arithmetic_on_fp32_storage(ofm):
     ctx = run_gpu(ofm, wl, Phis, "fp32", "fp64")
     for (a, b), (Hab, Sab) in blocks.items():
         Hg, Sg = ctx.block(a, b)
-        assert np.max(np.abs(Sg - Sab)) < 1e-13 * max(1.0, sum_abs_products(Phis[a], Phis[b]).max())
+        assert np.max(np.abs(Sg - Sab)) < 1e-13 * max(1.0, abs_overlap(wl.grid, frags[a], Phis[a], frags[b], Phis[b]).max())
         Ea = O.zero_extend(wl.grid, frags[a], Phis[a])
         Eb = O.zero_extend(wl.grid, frags[b], Phis[b])
         absH = (abs(Ea).T @ (abs(H) @ abs(Eb))).toarray()
