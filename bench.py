@@ -1,0 +1,434 @@
+#!/usr/bin/env python3
+"""Benchmark of the overlapping-fragments-method hot path on GB300.
+
+One step is one pass of the whole method over the synthetic alkane-chain
+workload (256x32x32 grid, 31 boxes 16x32x32, 32 states each), starting from
+the potential resident in device memory:
+  a2  plan the pairs and overlap geometry (host) and take V    ofm_build_fragments
+  a0  batched fragment eigensolve                                ofm_fragment_eigs
+  a1  H phi on the dilated boxes, a3/a4 pair contraction,
+  a5  symmetrise into blocks                                     ofm_assemble_HS
+  a6  FP64 window solve (index of the gap level, then the
+      eigenvalues in [E_gap, E_gap + 0.3 Ha])                    ofm_eigs_by_index, ofm_window_eigs
+The metric is the pair-block rate: algorithmic pair-block flops of one step
+(sum over pairs a<=b of 2 n_a n_b (|B_a∩B_b| + |B_a∩B_b+|)) times the steps,
+over the device time of the steps.  Per-row device times, the assembly-only
+rate, the roofline of the dominant kernel, the window-eigenvalue error
+against the all-FP64 GPU path and the speedups of the contraction
+arithmetic are reported beside it.
+
+--impl reference times the FP64 CPU oracle on a bounded sample instead.
+Under torchrun every rank runs an independent replica (the method's units
+are independent workloads; no collective on the data path).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FLUSH_BYTES = 512 << 20   # larger than the 129 MB L2
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="alkane")
+    p.add_argument("--precision", default="fp32")
+    p.add_argument("--no-extras", action="store_true", help="skip e2e, FP64 reference and sweeps")
+    return p.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"],
+                "bf16_tflops_sustained": d.get("bf16_tflops_sustained"), "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "source": "fallback"}
+
+
+# ------------------------------------------------------------------ clocks --
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------------ oracle legs --
+
+def _oracle_frag(args):
+    name, a = args
+    from ofm_inputs import make_workload
+    from oracle import ofm_oracle as O
+    wl = make_workload(name)
+    H = O.hamiltonian(wl.grid, wl.V)
+    return O.fragment_eigs(H, wl.grid, wl.frags[a])
+
+
+def oracle_sample(name, k):
+    """The FP64 oracle, as it stands, on the sub-system of the first k
+    fragments of the workload: k fragment eigensolves (one single-threaded
+    process each), their pair blocks and the dense generalized eigensolve.
+    Returns (pair flops of the sub-system, seconds, cores)."""
+    import multiprocessing as mp
+    for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    from ofm_inputs import make_workload
+    from oracle import ofm_oracle as O
+    wl = make_workload(name)
+    frags = wl.frags[:k]
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(k) as pool:
+        res = pool.map(_oracle_frag, [(name, a) for a in range(k)])
+    Phis = [U for _, U in res]
+    H = O.hamiltonian(wl.grid, wl.V)
+    pairs = O.pair_list(wl.grid, frags)
+    blocks = O.pair_blocks(H, wl.grid, frags, Phis, pairs)
+    Hd, Sd = O.assemble_dense(frags, blocks)
+    O.generalized_eigs(Hd, Sd)
+    dt = time.perf_counter() - t0
+    return O.pair_flops(wl.grid, frags, pairs), dt, k
+
+
+def cpu_baseline_leg(name):
+    k = max(1, min(8, os.cpu_count() or 1))
+    F, dt, cores = oracle_sample(name, k)
+    return {"value": F / dt / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+            "sample": f"fragments 0..{k - 1} of the workload as a sub-system: {k} fragment "
+                      f"eigensolves (one single-threaded process each), their pair blocks, "
+                      f"dense generalized eigensolve; {F:.3e} pair flops in {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from ofm_inputs import make_workload
+    wl = make_workload(args.workload)
+    k = 2
+    times = []
+    F = 0
+    for i in range(args.warmup + args.steps):
+        F, dt, cores = oracle_sample(args.workload, k)
+        if i >= args.warmup:
+            times.append(dt)
+    t = sum(times) / len(times)
+    val = F / t / 1e12
+    out = {
+        "impl": "reference", "metric": "H/S pair-block TFLOP/s", "value": val, "unit": "TFLOP/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "sample_fragments": k},
+        "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": k, "kind": "oracle",
+                         "sample": f"fragments 0..{k - 1} of {wl.name} per step (eigensolves, "
+                                   f"pair blocks, dense generalized eigensolve)"},
+        "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------- our arm --
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else torch.cuda.current_device())
+
+    from ofm_inputs import make_workload
+    from paper_1011_4764_gb300 import build
+    build.build()
+    from paper_1011_4764_gb300 import ofm
+
+    wl = make_workload(args.workload)
+    grid, frags, rule = wl.grid, wl.frags, wl.window
+    storage = "fp64" if args.precision == "fp64" else "fp32"
+    stream = torch.cuda.Stream(device=dev)
+    ctx = ofm.Context(stream)
+    V_dev = torch.from_numpy(np.ascontiguousarray(wl.V)).to(dev)
+    V_host = torch.from_numpy(np.ascontiguousarray(wl.V)).pin_memory()
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def window_of(c):
+        if rule.kind == "above_gap":
+            lo = float(c.eigs_by_index(rule.n_occ, rule.n_occ + 1)[0])
+            hi = lo + rule.width
+        elif rule.kind == "from_lowest":
+            lo = float(c.eigs_by_index(0, 1)[0])
+            hi = lo + rule.width
+        else:
+            e = c.eigs_by_index(rule.n_occ - 1, rule.n_occ + 1)
+            lo, hi = float(e[0]) - rule.width, float(e[1]) + rule.width
+        E, n = c.window_eigs(lo, hi)
+        return E, lo, hi
+
+    def step(Vsrc):
+        ctx.build_fragments(grid, Vsrc, frags, storage=storage)
+        eps, res, _ = ctx.fragment_eigs()
+        ctx.assemble(args.precision)
+        E, lo, hi = window_of(ctx)
+        return E, eps
+
+    info = None
+    for _ in range(args.warmup):
+        step(V_dev)
+    info = ctx.plan_info()
+    F = info["pair_flops"]
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    # ---- timed region: K full steps, inputs resident in HBM
+    ctx.set_profiling(True)
+    clocks = ClockSampler(local if world > 1 else dev.index or 0)
+    barrier()
+    clocks.start()
+    t_wall0 = time.perf_counter()
+    step_ms = []
+    host_build_s = 0.0
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        E, eps = step(V_dev)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+    barrier()
+    wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    stats = ctx.kernel_stats()
+    ctx.set_profiling(False)
+    t_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([t_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t.item())
+    K = args.steps
+    ms_per_step = t_ms / K
+    value = world * F * K / (t_ms * 1e-3) / 1e12
+
+    rows = {}
+    for name, s in stats.items():
+        rows.setdefault(s["row"], 0.0)
+        rows[s["row"]] += s["ms"] / K
+    asm_ms = sum(rows.get(r, 0.0) for r in ("a1", "a4", "a5")) - stats.get("scatter", {}).get("ms", 0.0) / K
+    launches = sum(s["launches"] for s in stats.values())
+
+    # dominant kernel class and its roofline
+    pk = peaks()
+    dom_name, dom = max(stats.items(), key=lambda kv: kv[1]["ms"])
+    per_launch_ms = dom["ms"] / max(1, dom["launches"])
+    bytes_per_launch = dom["bytes"] / max(1, dom["launches"])
+    traffic = profiled_traffic(dom_name)
+    roof = {"kernel": dom_name, "row": dom["row"], "bound": "hbm",
+            "achieved": bytes_per_launch / (per_launch_ms * 1e-3) / 1e9,
+            "peak": pk["hbm_gbs"], "unit": "GB/s", "peak_source": pk["source"] + " (copy burst)",
+            "launches": dom["launches"], "ms_per_launch": per_launch_ms,
+            "algorithmic_bytes_per_launch": bytes_per_launch,
+            "traffic": traffic}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+
+    out = {
+        "metric": "H/S pair-block TFLOP/s", "value": value, "unit": "TFLOP/s",
+        "n_gpus": world, "steps": K, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "fp32": "f32", "tf32": "tf32", "bf16": "bf16",
+                  "bf16x3": "bf16x3"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": wl.name, "grid": list(grid.n), "h": grid.h,
+                   "fragments": len(frags), "states": sorted({f.n_states for f in frags}),
+                   "pairs": info["n_pairs"], "basis": info["basis_size"], "pair_flops": F,
+                   "contraction": args.precision, "storage": storage,
+                   "step": "a2 plan + a0 fragment eigensolve + a1 H apply + a3/a4 contraction "
+                           "+ a5 blocks + a6 FP64 window solve",
+                   "window": f"{rule.kind} width {rule.width} Ha",
+                   "l2": "flushed by a 512 MiB device write before every step (untimed)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "rows_ms": {k: round(v, 4) for k, v in sorted(rows.items())},
+        "kernels": {k: {"row": s["row"], "launches": s["launches"] // K, "ms": s["ms"] / K}
+                    for k, s in sorted(stats.items())},
+        "assembly": {"ms": asm_ms, "tflops": F / (asm_ms * 1e-3) / 1e12 if asm_ms > 0 else None},
+        "wall_s": wall,
+        "gpu_launches": launches,
+        "roofline": roof,
+        "clocks": clk,
+        "window_eigs": int(len(E)),
+    }
+
+    if not args.no_extras and rank == 0:
+        out.update(extras(args, ctx, ofm, wl, V_host, step, window_of, stream, storage, F, dev, E))
+    if rank == 0:
+        if world == 1 and not args.no_extras:
+            try:
+                out["cpu_baseline"] = cpu_baseline_leg(args.workload)
+            except Exception as e:  # the baseline must not hide the GPU line
+                out["cpu_baseline"] = {"value": None, "unit": "TFLOP/s", "cores": 0,
+                                       "kind": "oracle", "sample": f"failed: {e}"}
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def profiled_traffic(kernel_class):
+    """DRAM bytes per launch from the committed ncu summary, or None when the
+    summary is absent or was taken on a different version of the kernel."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        d = json.load(open(path))[kernel_class]
+    except Exception:
+        return None
+    import hashlib
+    src = os.path.join(ROOT, "paper_1011_4764_gb300", "csrc", d["source"])
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    if sha != d.get("source_sha"):
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def extras(args, ctx, ofm, wl, V_host, step, window_of, stream, storage, F, dev, E_main):
+    import numpy as np
+    import torch
+    ex = {}
+    # e2e: the same steps through the C ABI from pinned host buffers
+    n_e2e = max(2, min(args.steps, 5))
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        E, eps = step(V_host)
+    torch.cuda.synchronize(dev)
+    dt = (time.perf_counter() - t0) / n_e2e
+    nb = sum(f.n_states for f in wl.frags)
+    ex["e2e"] = {"value": F / dt / 1e12, "unit": "TFLOP/s",
+                 "h2d_bytes_per_step": int(V_host.numel() * 8),
+                 "d2h_bytes_per_step": int((2 * nb + len(E) + 1) * 8),
+                 "steps": n_e2e, "timer": "host wall clock"}
+    # contraction arithmetic on the same states: a1-a5 device time
+    asm = {}
+    for prec in ("fp32", "fp64", "tf32", "bf16", "bf16x3"):
+        if storage == "fp64" and prec != "fp64":
+            continue
+        try:
+            ctx.assemble(prec)
+        except ofm.OFMError:
+            continue
+        ts = []
+        for _ in range(5):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.assemble(prec)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        asm[prec] = min(ts)
+    ex["assembly_ms_by_precision"] = asm
+    if "fp32" in asm:
+        ex["speedup_vs_fp32"] = {p: asm["fp32"] / t for p, t in asm.items()}
+    # window eigenvalues against the all-FP64 GPU path (FP64 states, FP64
+    # contraction), compared index by index
+    try:
+        ref = ofm.Context(stream)
+        ref.build_fragments(wl.grid, V_host, wl.frags, storage="fp64")
+        ref.fragment_eigs()
+        ref.assemble("fp64")
+        Eref, lo, hi = window_of(ref)
+        ctx.assemble(args.precision)
+        n0 = wl.window.n_occ if wl.window.kind != "from_lowest" else 0
+        m = len(Eref)
+        mine = ctx.eigs_by_index(n0, n0 + m)
+        refi = ref.eigs_by_index(n0, n0 + m)
+        ex["window_vs_fp64"] = {"n": m, "max_abs_err_ha": float(np.max(np.abs(mine - refi))) if m else 0.0,
+                                "window_ha": [lo, hi]}
+        ref.close()
+    except Exception as e:
+        ex["window_vs_fp64"] = {"error": str(e)}
+    return ex
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

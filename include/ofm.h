@@ -185,6 +185,24 @@ ofm_status ofm_eigs_by_index(ofm_ctx* ctx, int i_lo, int i_hi, double* E_out);
  * path as ofm_window_eigs (replaces the assembled matrices). */
 ofm_status ofm_set_dense_HS(ofm_ctx* ctx, int n, const double* H, const double* S);
 
+/* Per-kernel-class launch counts and device time.  Counting is always on;
+ * device time is measured with CUDA events recorded on the context stream
+ * around each launch (or launch sequence) while profiling is on.
+ * ofm_set_profiling clears the statistics.  ofm_get_kernel_stats
+ * synchronises the stream, writes up to max entries (one per class that has
+ * launched) and sets *n to the number written. */
+typedef struct {
+  char name[32];          /* kernel class, e.g. "filter", "contract" */
+  char row[8];            /* method step: "a0".."a6" */
+  long long launches;
+  double total_ms;        /* 0 when profiling was off */
+  double bytes;           /* algorithmic bytes moved by these launches (model, not counters) */
+  double flops;           /* algorithmic flops of these launches */
+} ofm_kernel_stat;
+
+ofm_status ofm_set_profiling(ofm_ctx* ctx, int on);
+ofm_status ofm_get_kernel_stats(ofm_ctx* ctx, ofm_kernel_stat* out, int max, int* n);
+
 /* Host-only planner query (needs no GPU and no context): validates the
  * geometry like ofm_build_fragments and returns the pair list (Sec. II,
  * pairs of fragments that share grid points through the stencil) with the

@@ -133,6 +133,7 @@ extern "C" ofm_status ofm_create(ofm_ctx** out, void* cuda_stream) {
 extern "C" void ofm_destroy(ofm_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
+  ofm_prof_release(c);
   DevBuf* bufs[] = {&c->V, &c->states, &c->hphi, &c->d_frags, &c->d_apply_start, &c->d_pairs,
                     &c->d_pieces, &c->d_items, &c->partials, &c->blocks, &c->dense_H,
                     &c->dense_S, &c->staging, &c->flag, &c->w_A, &c->w_L, &c->w_d, &c->w_e,
@@ -184,14 +185,23 @@ extern "C" ofm_status ofm_build_fragments(ofm_ctx* c, const ofm_grid* grid, cons
   c->frag_set.assign(n_frag, 0);
 
   const size_t es = elem_size(c);
+  // algorithmic traffic: the H apply reads every state and V once and writes
+  // H phi once on the dilated boxes; the contraction at its minimum reads
+  // states and H phi once.
+  c->apply_bytes = 0;
+  for (auto& f : c->frags) c->apply_bytes += (double)f.Pd * (2.0 * f.n + 1.0) * es;
+  c->contract_bytes = 0;
+  for (auto& f : c->frags) c->contract_bytes += (double)f.Pd * 2.0 * f.n * es;
   const long long npts = (long long)grid->n[0] * grid->n[1] * grid->n[2];
   OFM_TRY(ofm_ensure(c, c->V, npts * es, "potential"));
   if (v_loc == OFM_HOST) {
     OFM_TRY(ofm_ensure(c, c->staging, npts * sizeof(double), "staging"));
     OFM_CUDA(c, cudaMemcpyAsync(c->staging.p, V, npts * sizeof(double), cudaMemcpyHostToDevice,
                                 c->stream));
+    KTimer t(c, KC_CONVERT);
     launch_convert_V((const double*)c->staging.p, c->V.p, npts, es == 8, c->stream);
   } else {
+    KTimer t(c, KC_CONVERT);
     launch_convert_V(V, c->V.p, npts, es == 8, c->stream);
   }
   OFM_TRY(check_launch(c, "convert V"));
@@ -238,6 +248,7 @@ extern "C" ofm_status ofm_build_fragments(ofm_ctx* c, const ofm_grid* grid, cons
   c->blk_elems = 0;
   for (auto& p : c->simt_pairs) c->blk_elems = std::max<long long>(c->blk_elems, p.blk_off + 2LL * c->frags[p.a].n * c->frags[p.b].n);
   OFM_TRY(ofm_ensure(c, c->blocks, sizeof(double) * c->blk_elems, "blocks"));
+  c->finalize_bytes = (double)c->simt_partial_elems * (es == 8 ? 8 : 4) + 8.0 * c->blk_elems;
   OFM_TRY(ofm_plan_extra(c));
   // host copies of tables are read back by later calls: wait for the uploads
   OFM_TRY(sync(c, "build_fragments"));
@@ -261,7 +272,8 @@ extern "C" ofm_status ofm_set_fragment_states(ofm_ctx* c, int a, const double* p
   } else if (loc != OFM_DEVICE) {
     return ofm_fail(c, OFM_ERR_INVALID, "unknown location");
   }
-  launch_import_states((const DevFrag*)c->d_frags.p, a, F, src, c->states.p, c->storage == OFM_STORE_FP64, c->stream);
+  { KTimer t(c, KC_CONVERT);
+  launch_import_states((const DevFrag*)c->d_frags.p, a, F, src, c->states.p, c->storage == OFM_STORE_FP64, c->stream); }
   OFM_TRY(check_launch(c, "import states"));
   if (loc == OFM_HOST) OFM_TRY(sync(c, "set_fragment_states"));  // staging is reused
   c->frag_set[a] = 1;
@@ -305,6 +317,7 @@ extern "C" ofm_status ofm_get_hphi(ofm_ctx* c, int b, double* out) {
 // ------------------------------------------------------------- assembly ----
 
 ofm_status ofm_apply_h(ofm_ctx* c) {
+  KTimer t(c, KC_APPLY, 1, c->apply_bytes);
   launch_apply_global((const DevFrag*)c->d_frags.p, (const int*)c->d_apply_start.p, c->nfrag,
                       c->apply_total_ctas, c->V.p, c->states.p, c->hphi.p, c->grid.n, c->grid.h,
                       c->storage == OFM_STORE_FP64, c->stream);
@@ -322,14 +335,16 @@ extern "C" ofm_status ofm_assemble_HS(ofm_ctx* c, ofm_precision prec, const ofm_
   c->assembled = c->dense_ready = c->factored = false;
   OFM_TRY(ofm_apply_h(c));
   if (prec == OFM_PREC_FP64 || prec == OFM_PREC_FP32) {
+    { KTimer t(c, KC_CONTRACT, 1, c->contract_bytes, (double)c->flops);
     launch_contract_simt(prec, c->storage == OFM_STORE_FP64, (const DevFrag*)c->d_frags.p,
                          (const DevPair*)c->d_pairs.p, (const Piece*)c->d_pieces.p,
                          (const WorkItem*)c->d_items.p, (int)c->simt_items.size(), c->states.p,
-                         c->hphi.p, c->partials.p, c->simt_tile, c->stream);
+                         c->hphi.p, c->partials.p, c->simt_tile, c->stream); }
     OFM_TRY(check_launch(c, "contract (CUDA cores)"));
+    { KTimer t(c, KC_FINALIZE, 1, c->finalize_bytes);
     launch_finalize_simt(prec, (const DevFrag*)c->d_frags.p, (const DevPair*)c->d_pairs.p,
                          (int)c->simt_pairs.size(), (const WorkItem*)c->d_items.p, c->partials.p,
-                         c->simt_tile, (double*)c->blocks.p, c->stream);
+                         c->simt_tile, (double*)c->blocks.p, c->stream); }
     OFM_TRY(check_launch(c, "finalize blocks"));
   } else {
     OFM_TRY(ofm_contract_tc(c, prec));
@@ -405,9 +420,10 @@ ofm_status ofm_make_dense(ofm_ctx* c) {
   OFM_TRY(ofm_ensure(c, c->dense_S, sizeof(double) * n * n, "dense S"));
   OFM_CUDA(c, cudaMemsetAsync(c->dense_H.p, 0, sizeof(double) * n * n, c->stream));
   OFM_CUDA(c, cudaMemsetAsync(c->dense_S.p, 0, sizeof(double) * n * n, c->stream));
+  { KTimer t(c, KC_SCATTER);
   launch_scatter_dense((const DevFrag*)c->d_frags.p, (const DevPair*)c->d_pairs.p,
                        (int)c->simt_pairs.size(), (const double*)c->blocks.p, (int)n,
-                       (double*)c->dense_H.p, (double*)c->dense_S.p, c->stream);
+                       (double*)c->dense_H.p, (double*)c->dense_S.p, c->stream); }
   OFM_TRY(check_launch(c, "scatter dense"));
   c->dense_n = (int)n;
   c->dense_ready = true;

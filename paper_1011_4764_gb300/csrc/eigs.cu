@@ -53,6 +53,10 @@ struct EigWork {
       d_gitems, d_toff, d_rank, d_vmax;
   double vmax = 0.0;
   bool ready = false;
+  // algorithmic traffic / work per launch: a filter step streams the block
+  // in, the previous block (three-term steps) and the block out, plus V
+  double filter_b2 = 0, filter_b3 = 0, gram_bytes = 0, gram_flops = 0, rot_bytes = 0,
+         rot_flops = 0;
 };
 
 void ofm_eig_free(ofm_ctx* c) {
@@ -533,6 +537,16 @@ static ofm_status eig_setup(ofm_ctx* c, int guard_opt) {
     ctas += (E.Pd * (E.ld / vn) + 255) / 256;
   }
   w->total_ctas = (int)ctas;
+  w->filter_b2 = w->filter_b3 = w->gram_bytes = w->gram_flops = w->rot_bytes = w->rot_flops = 0;
+  for (const DevFrag& E : w->efr) {
+    const double P = (double)E.ext[0] * E.ext[1] * E.ext[2];
+    w->filter_b2 += P * (2.0 * E.n + 1.0) * es;
+    w->filter_b3 += P * (3.0 * E.n + 1.0) * es;
+    w->gram_bytes += P * 2.0 * E.n * es;
+    w->gram_flops += 2.0 * P * E.n * 2.0 * E.n;
+    w->rot_bytes += P * 4.0 * E.n * es;
+    w->rot_flops += 2.0 * 2.0 * P * E.n * E.n;
+  }
   // Gram plan: self pairs over the interior box, chunks of ~1024 points
   std::vector<HostPair> sp(nf);
   for (int a = 0; a < nf; ++a) {
@@ -576,6 +590,7 @@ static ofm_status eig_setup(ofm_ctx* c, int guard_opt) {
   OFM_CUDA(c, cudaMemcpyAsync(w->d_gpieces.p, w->gpieces.data(), sizeof(Piece) * w->gpieces.size(), cudaMemcpyHostToDevice, s));
   OFM_CUDA(c, cudaMemcpyAsync(w->d_gitems.p, w->gitems.data(), sizeof(WorkItem) * w->gitems.size(), cudaMemcpyHostToDevice, s));
   const long long npts = (long long)c->grid.n[0] * c->grid.n[1] * c->grid.n[2];
+  KTimer kt(c, KC_EIG_INIT);
   if (fp64) vmax_kernel<double><<<1, 1024, 0, s>>>((const double*)c->V.p, npts, (double*)w->d_vmax.p);
   else vmax_kernel<float><<<1, 1024, 0, s>>>((const float*)c->V.p, npts, (double*)w->d_vmax.p);
   OFM_CUDA(c, cudaGetLastError());
@@ -595,6 +610,8 @@ static ofm_status eig_rr(ofm_ctx* c, int y, int hy, int xo, int hxo, unsigned lo
   const bool fp64 = c->storage == OFM_STORE_FP64;
   const int nf = c->nfrag;
   cudaStream_t s = c->stream;
+  {
+  KTimer kt(c, KC_GRAM, 2, w->gram_bytes, w->gram_flops);
   launch_contract_simt(fp64 ? OFM_PREC_FP64 : OFM_PREC_FP32, fp64, (const DevFrag*)w->d_efr.p,
                        (const DevPair*)w->d_gpairs.p, (const Piece*)w->d_gpieces.p,
                        (const WorkItem*)w->d_gitems.p, (int)w->gitems.size(), w->buf[y].p,
@@ -602,17 +619,20 @@ static ofm_status eig_rr(ofm_ctx* c, int y, int hy, int xo, int hxo, unsigned lo
   launch_finalize_simt(fp64 ? OFM_PREC_FP64 : OFM_PREC_FP32, (const DevFrag*)w->d_efr.p,
                        (const DevPair*)w->d_gpairs.p, nf, (const WorkItem*)w->d_gitems.p,
                        w->partials.p, 64, (double*)w->blocks.p, s);
+  }
   const long long mm = (long long)w->mmax * w->mmax;
+  { KTimer kt(c, KC_RR);
   rayleigh_ritz_kernel<<<nf, 256, 0, s>>>((const DevFrag*)w->d_efr.p, (const DevPair*)w->d_gpairs.p,
                                           (const double*)w->blocks.p, (double*)w->work.p,
                                           3 * mm + 3 * w->mmax + 8, (double*)w->Cm.p, mm,
                                           (double*)w->theta.p, (const long long*)w->d_toff.p,
-                                          fp64 ? 1e-13 : 1e-6, (int*)w->d_rank.p);
+                                          fp64 ? 1e-13 : 1e-6, (int*)w->d_rank.p); }
   const size_t es = fp64 ? 8 : 4;
   const size_t smem = (size_t)w->mmax * w->mmax * es + 32 * (size_t)w->mmax * es;
   long long maxP = 0;
   for (auto& E : w->efr) maxP = std::max<long long>(maxP, (long long)E.ext[0] * E.ext[1] * E.ext[2]);
   dim3 g((unsigned)std::min<long long>((maxP + 31) / 32, 64), nf, 2);
+  KTimer kt(c, KC_ROTATE, 2, w->rot_bytes, w->rot_flops);
   if (fp64)
     rotate_kernel<double><<<g, 256, smem, s>>>((const DevFrag*)w->d_efr.p, (const double*)w->buf[y].p,
                                                (double*)w->buf[xo].p, (const double*)w->buf[hy].p,
@@ -638,6 +658,7 @@ static ofm_status eig_rr(ofm_ctx* c, int y, int hy, int xo, int hxo, unsigned lo
 
 static void apply_block(ofm_ctx* c, int in, int prev, int out, const double* coef) {
   EigWork* w = c->eig;
+  KTimer kt(c, KC_FILTER, 1, prev >= 0 ? w->filter_b3 : w->filter_b2);
   launch_apply_filter((const DevFrag*)w->d_efr.p, (const int*)w->d_cta.p, c->nfrag, w->total_ctas,
                       c->V.p, w->buf[in].p, prev >= 0 ? w->buf[prev].p : nullptr, w->buf[out].p,
                       coef, c->grid.n, c->grid.h, c->storage == OFM_STORE_FP64, c->stream);
@@ -671,10 +692,11 @@ extern "C" ofm_status ofm_fragment_eigs(ofm_ctx* c, const ofm_eig_opts* opts, do
   c->assembled = c->dense_ready = c->factored = false;
 
   // start block in buffer 0
+  { KTimer kt(c, KC_EIG_INIT);
   if (fp64)
     init_random_kernel<double><<<w->total_ctas, 256, 0, s>>>((const DevFrag*)w->d_efr.p, (const int*)w->d_cta.p, nf, (double*)w->buf[0].p, o.seed);
   else
-    init_random_kernel<float><<<w->total_ctas, 256, 0, s>>>((const DevFrag*)w->d_efr.p, (const int*)w->d_cta.p, nf, (float*)w->buf[0].p, o.seed);
+    init_random_kernel<float><<<w->total_ctas, 256, 0, s>>>((const DevFrag*)w->d_efr.p, (const int*)w->d_cta.p, nf, (float*)w->buf[0].p, o.seed); }
   OFM_CUDA(c, cudaGetLastError());
   // coefficient table: degree steps x fragments x (alpha, beta, shift)
   OFM_TRY(ofm_ensure(c, w->coef, sizeof(double) * 3 * nf * (degree + 1), "filter coefficients"));
@@ -750,12 +772,13 @@ extern "C" ofm_status ofm_fragment_eigs(ofm_ctx* c, const ofm_eig_opts* opts, do
   }
   // export the first n_a Ritz vectors with the sign gauge
   dim3 eg(nf, (w->mmax + 31) / 32);
+  { KTimer kt(c, KC_EXPORT);
   if (fp64)
     export_states_kernel<double><<<eg, 256, 0, s>>>((const DevFrag*)w->d_efr.p, (const DevFrag*)c->d_frags.p,
                                                     (const double*)w->buf[xb].p, (double*)c->states.p);
   else
     export_states_kernel<float><<<eg, 256, 0, s>>>((const DevFrag*)w->d_efr.p, (const DevFrag*)c->d_frags.p,
-                                                   (const float*)w->buf[xb].p, (float*)c->states.p);
+                                                   (const float*)w->buf[xb].p, (float*)c->states.p); }
   OFM_CUDA(c, cudaGetLastError());
   OFM_CUDA(c, cudaStreamSynchronize(s));
   double worst = 0.0;

@@ -112,6 +112,31 @@ void launch_scatter_dense(const DevFrag* d_fr, const DevPair* d_pairs, int npair
 
 }  // namespace ofm
 
+// ------------------------------------------------------------- profiling ----
+
+namespace ofm {
+enum KClass {
+  KC_CONVERT, KC_APPLY, KC_CONTRACT, KC_FINALIZE, KC_SCATTER, KC_EIG_INIT, KC_FILTER, KC_GRAM,
+  KC_RR, KC_ROTATE, KC_EXPORT, KC_CHOL, KC_REDUCE, KC_TRIDIAG, KC_BISECT, KC_COUNT
+};
+struct KStat {
+  long long launches = 0;
+  double ms = 0.0;
+  double bytes = 0.0;
+  double flops = 0.0;
+};
+const char* kclass_name(int k);
+const char* kclass_row(int k);
+}  // namespace ofm
+
+struct ofm_prof {
+  bool on = false;
+  ofm::KStat st[ofm::KC_COUNT];
+  std::vector<cudaEvent_t> pool;
+  struct Pending { int k; cudaEvent_t a, b; };
+  std::vector<Pending> pending;
+};
+
 // ------------------------------------------------------------- context ------
 
 struct ofm_ctx {
@@ -158,6 +183,9 @@ struct ofm_ctx {
   int window_fail_col = -1;
   std::vector<char> frag_set;       // per fragment: states imported or computed
   int last_eig_iters = 0;           // filter iterations of the last fragment eigensolve
+  // algorithmic traffic of one launch, set by the planner
+  double apply_bytes = 0, contract_bytes = 0, finalize_bytes = 0;
+  ofm_prof prof;                    // per-kernel-class launch counts and event timing
   struct EigWork* eig = nullptr;    // fragment-eigensolver buffers and plan
   struct TcPlan* tc = nullptr;      // tensor-core contraction plan
 };
@@ -173,12 +201,26 @@ ofm_status ofm_make_dense(ofm_ctx* c);
 ofm_status ofm_plan_extra(ofm_ctx* c);        // tensor-core plan after a build
 void ofm_free_extra(ofm_ctx* c);              // frees eig and tc
 void ofm_eig_free(ofm_ctx* c);
+void ofm_prof_release(ofm_ctx* c);            // waits for and frees timing events
 void ofm_tc_free(ofm_ctx* c);
 ofm_status ofm_contract_tc(ofm_ctx* c, ofm_precision prec);
 ofm_status ofm_window_factor(ofm_ctx* c);
 ofm_status ofm_window_count(ofm_ctx* c, double x, bool inclusive, int* count);
 ofm_status ofm_window_bisect(ofm_ctx* c, int i_lo, int i_hi, double* E_out);
 ofm_status ofm_window_vectors(ofm_ctx* c, int m, double* C_out);
+
+// Counts the launches of one kernel class and, while profiling is on,
+// brackets them with CUDA events on the context stream.
+struct KTimer {
+  ofm_ctx* c;
+  int k;
+  cudaEvent_t a = nullptr;
+  // bytes / flops: algorithmic traffic and work of the launches (for the
+  // roofline figures), not measured counters
+  KTimer(ofm_ctx* c_, int k_, long long nlaunch = 1, double bytes = 0.0, double flops = 0.0);
+  ~KTimer();
+  void add(long long n);
+};
 
 #define OFM_CUDA(ctx, expr)                                             \
   do {                                                                  \

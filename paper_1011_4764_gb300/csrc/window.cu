@@ -375,7 +375,9 @@ ofm_status ofm_window_factor(ofm_ctx* c) {
   OFM_CUDA(c, cudaMemcpyAsync(L, c->dense_S.p, bytes, cudaMemcpyDeviceToDevice, s));
   OFM_CUDA(c, cudaMemsetAsync(flag, 0xff, sizeof(int), s));  // -1: no failure
   // 1. Cholesky
+  { KTimer kt(c, KC_CHOL, 0);
   for (int k0 = 0; k0 < n; k0 += NB) {
+    kt.add(1);
     const int kb = std::min(NB, n - k0);
     potrf_diag_kernel<<<1, dim3(32, 32), 0, s>>>(L, n, k0, kb, flag);
     const int rows = n - k0 - kb;
@@ -383,7 +385,9 @@ ofm_status ofm_window_factor(ofm_ctx* c) {
       trsm_panel_kernel<<<(rows + 127) / 128, 128, 0, s>>>(L, n, k0, kb);
       const int tb = (rows + NB - 1) / NB;
       syrk_update_kernel<<<dim3(tb, tb), dim3(32, 32), 0, s>>>(L, n, k0, kb);
+      kt.add(2);
     }
+  }
   }
   OFM_CUDA(c, cudaGetLastError());
   int fail = -1;
@@ -398,6 +402,8 @@ ofm_status ofm_window_factor(ofm_ctx* c) {
   // 2. A = L^-1 H L^-T: X = L^-1 H, then A = L^-1 X^T
   double* T = (double*)c->dense_H.p;  // kept intact: work on a copy
   OFM_CUDA(c, cudaMemcpyAsync(A, T, bytes, cudaMemcpyDeviceToDevice, s));
+  {
+  KTimer kt(c, KC_REDUCE, 2 + 4 * ((n + NB - 1) / NB));
   trsm_lower_left(L, A, n, s);
   OFM_TRY(ofm_ensure(c, c->w_eval, bytes, "window scratch"));
   double* X = (double*)c->w_eval.p;
@@ -406,6 +412,7 @@ ofm_status ofm_window_factor(ofm_ctx* c) {
   trsm_lower_left(L, X, n, s);
   symmetrize_kernel<<<(int)(((long long)n * n + 255) / 256), 256, 0, s>>>(X, n);
   OFM_CUDA(c, cudaMemcpyAsync(A, X, bytes, cudaMemcpyDeviceToDevice, s));
+  }
   OFM_CUDA(c, cudaGetLastError());
   // 3. tridiagonalise
   double* d = (double*)c->w_d.p;
@@ -413,6 +420,8 @@ ofm_status ofm_window_factor(ofm_ctx* c) {
   double* tau = (double*)c->w_tau.p;
   double* vbuf = (double*)c->w_tmp.p;
   double* p = vbuf + n;
+  {
+  KTimer kt(c, KC_TRIDIAG, 1 + 3LL * std::max(0, n - 2));
   for (int k = 0; k + 2 < n; ++k) {
     householder_kernel<<<1, 256, 0, s>>>(A, n, k, vbuf, d, e, tau);
     const int m = n - k - 1;
@@ -420,6 +429,7 @@ ofm_status ofm_window_factor(ofm_ctx* c) {
     rank2_kernel<<<dim3((m + 63) / 64, (m + 7) / 8), dim3(32, 8), 0, s>>>(A, n, k, vbuf, p, tau);
   }
   tridiag_tail_kernel<<<1, 1, 0, s>>>(A, n, d, e);
+  }
   OFM_CUDA(c, cudaGetLastError());
   OFM_TRY(sync_ctx(c, "tridiagonalisation"));
   c->factored = true;
@@ -429,6 +439,7 @@ ofm_status ofm_window_factor(ofm_ctx* c) {
 ofm_status ofm_window_count(ofm_ctx* c, double x, bool inclusive, int* count) {
   if (inclusive) x = std::nextafter(x, HUGE_VAL);
   int* dc = (int*)c->flag.p + 1;
+  KTimer kt(c, KC_BISECT);
   count_kernel<<<1, 1, 0, c->stream>>>((const double*)c->w_d.p, (const double*)c->w_e.p,
                                        c->dense_n, x, dc);
   OFM_CUDA(c, cudaGetLastError());
@@ -439,6 +450,7 @@ ofm_status ofm_window_count(ofm_ctx* c, double x, bool inclusive, int* count) {
 ofm_status ofm_window_bisect(ofm_ctx* c, int i_lo, int i_hi, double* E_out) {
   const int m = i_hi - i_lo;
   double* out = (double*)c->w_tmp.p;  // 2n doubles, m <= n
+  KTimer kt(c, KC_BISECT);
   bisect_kernel<<<(m + 127) / 128, 128, 0, c->stream>>>((const double*)c->w_d.p,
                                                        (const double*)c->w_e.p, c->dense_n, i_lo,
                                                        m, out);

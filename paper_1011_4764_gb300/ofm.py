@@ -27,7 +27,7 @@ EXPORTS = [
     "ofm_fragment_eigs", "ofm_set_fragment_states", "ofm_get_fragment_states",
     "ofm_assemble_HS", "ofm_get_pairs", "ofm_get_plan_info", "ofm_get_block",
     "ofm_get_dense_HS", "ofm_get_hphi", "ofm_window_eigs", "ofm_eigs_by_index",
-    "ofm_set_dense_HS", "ofm_plan_pairs",
+    "ofm_set_dense_HS", "ofm_plan_pairs", "ofm_set_profiling", "ofm_get_kernel_stats",
 ]
 
 
@@ -54,6 +54,11 @@ class ofm_plan_info(C.Structure):
                 ("overlap_points_s", C.c_longlong), ("overlap_points_h", C.c_longlong),
                 ("state_bytes", C.c_longlong), ("hphi_bytes", C.c_longlong),
                 ("apply_points", C.c_longlong)]
+
+
+class ofm_kernel_stat(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("row", C.c_char * 8), ("launches", C.c_longlong),
+                ("total_ms", C.c_double), ("bytes", C.c_double), ("flops", C.c_double)]
 
 
 _LIB = None
@@ -90,6 +95,8 @@ def load_library(path: str = LIB_PATH):
         "ofm_set_dense_HS": ([P, I, DP, DP], I),
         "ofm_plan_pairs": ([C.POINTER(ofm_grid), C.POINTER(ofm_fragment), I, IP, IP,
                             C.POINTER(C.c_longlong), I, C.POINTER(C.c_longlong)], I),
+        "ofm_set_profiling": ([P, I], I),
+        "ofm_get_kernel_stats": ([P, C.POINTER(ofm_kernel_stat), I, IP], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -186,8 +193,8 @@ class Context:
         .off, .ext, .n_states."""
         g, fa = _c_geometry(grid, frags)
         if _is_torch(V):
-            assert V.is_cuda and str(V.dtype) == "torch.float64" and V.is_contiguous()
-            ptr, loc = C.c_void_p(V.data_ptr()), DEVICE
+            assert str(V.dtype) == "torch.float64" and V.is_contiguous()
+            ptr, loc = C.c_void_p(V.data_ptr()), (DEVICE if V.is_cuda else HOST)
             keep = V
         else:
             keep = np.ascontiguousarray(V, dtype=np.float64)
@@ -297,6 +304,20 @@ class Context:
         E = np.zeros(max(1, i_hi - i_lo))
         self._check(self.lib.ofm_eigs_by_index(self.h, i_lo, i_hi, _dptr(E)))
         return E[:i_hi - i_lo]
+
+    # -- ofm_set_profiling / ofm_get_kernel_stats
+    def set_profiling(self, on=True):
+        self._check(self.lib.ofm_set_profiling(self.h, 1 if on else 0))
+
+    def kernel_stats(self):
+        """{class name: dict(row, launches, ms, bytes, flops)}; synchronises."""
+        out = (ofm_kernel_stat * 64)()
+        n = C.c_int()
+        self._check(self.lib.ofm_get_kernel_stats(self.h, out, 64, C.byref(n)))
+        return {out[i].name.decode(): dict(row=out[i].row.decode(), launches=out[i].launches,
+                                           ms=out[i].total_ms, bytes=out[i].bytes,
+                                           flops=out[i].flops)
+                for i in range(n.value)}
 
     def set_dense_HS(self, H, S):
         H = np.ascontiguousarray(H, dtype=np.float64)
