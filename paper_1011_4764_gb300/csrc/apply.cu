@@ -68,14 +68,16 @@ __global__ void __launch_bounds__(256) apply_global_kernel(const DevFrag* __rest
   const int f = find_frag(cta_start, nfrag, blockIdx.x);
   const DevFrag F = fr[f];
   const int q_per_pt = F.ld / VN;
-  const long long e = (long long)(blockIdx.x - cta_start[f]) * blockDim.x + threadIdx.x;
-  if (e >= F.Pd * q_per_pt) return;
-  const long long p = e / q_per_pt;
-  const int q = (int)(e - p * q_per_pt);
+  // 32-bit index math: the planner keeps Pd * ld below 2^31 per fragment
+  const int e = (int)(blockIdx.x - cta_start[f]) * (int)blockDim.x + (int)threadIdx.x;
+  if (e >= (int)F.Pd * q_per_pt) return;
+  const int p = e / q_per_pt;
+  const int q = e - p * q_per_pt;
   const int ex = F.dext[0], ey = F.dext[1], ez = F.dext[2];
-  const int x = (int)(p % ex);
-  const int y = (int)((p / ex) % ey);
-  const int z = (int)(p / ((long long)ex * ey));
+  const int x = p % ex;
+  const int yz = p / ex;
+  const int y = yz % ey;
+  const int z = yz / ey;
   const int X = (F.doff[0] + x) % gx, Y = (F.doff[1] + y) % gy, Z = (F.doff[2] + z) % gz;
   const T v = V[((long long)Z * gy + Y) * gx + X];
   const V16* S = reinterpret_cast<const V16*>(states + F.off);
@@ -126,14 +128,16 @@ __global__ void __launch_bounds__(256) apply_filter_kernel(
   const int f = find_frag(cta_start, nfrag, blockIdx.x);
   const DevFrag F = fr[f];
   const int q_per_pt = F.ld / VN;
-  const long long e = (long long)(blockIdx.x - cta_start[f]) * blockDim.x + threadIdx.x;
-  if (e >= F.Pd * q_per_pt) return;
-  const long long p = e / q_per_pt;
-  const int q = (int)(e - p * q_per_pt);
+  // 32-bit index math: the planner keeps Pd * ld below 2^31 per fragment
+  const int e = (int)(blockIdx.x - cta_start[f]) * (int)blockDim.x + (int)threadIdx.x;
+  if (e >= (int)F.Pd * q_per_pt) return;
+  const int p = e / q_per_pt;
+  const int q = e - p * q_per_pt;
   const int ex = F.dext[0], ey = F.dext[1], ez = F.dext[2];
-  const int x = (int)(p % ex);
-  const int y = (int)((p / ex) % ey);
-  const int z = (int)(p / ((long long)ex * ey));
+  const int x = p % ex;
+  const int yz = p / ex;
+  const int y = yz % ey;
+  const int z = yz / ey;
   if (x < F.lo[0] || x >= F.lo[0] + F.ext[0] || y < F.lo[1] || y >= F.lo[1] + F.ext[1] ||
       z < F.lo[2] || z >= F.lo[2] + F.ext[2])
     return;

@@ -50,8 +50,10 @@ struct EigWork {
   long long gpart = 0;
   long long gblk = 0;
   DevBuf d_efr, d_cta, buf[4], coef, theta, res, Cm, work, blocks, partials, d_gpairs, d_gpieces,
-      d_gitems, d_toff, d_rank, d_vmax;
+      d_gitems, d_toff, d_rank, d_vmax, rpart;
   double vmax = 0.0;
+  size_t rr_smem = 0, rot_smem = 0;   // dynamic shared memory of the two kernels
+  int rot_blocks = 1;
   bool ready = false;
   // algorithmic traffic / work per launch: a filter step streams the block
   // in, the previous block (three-term steps) and the block out, plus V
@@ -64,7 +66,8 @@ void ofm_eig_free(ofm_ctx* c) {
   EigWork* w = c->eig;
   DevBuf* bufs[] = {&w->d_efr, &w->d_cta, &w->buf[0], &w->buf[1], &w->buf[2], &w->buf[3],
                     &w->coef, &w->theta, &w->res, &w->Cm, &w->work, &w->blocks, &w->partials,
-                    &w->d_gpairs, &w->d_gpieces, &w->d_gitems, &w->d_toff, &w->d_rank, &w->d_vmax};
+                    &w->d_gpairs, &w->d_gpieces, &w->d_gitems, &w->d_toff, &w->d_rank, &w->d_vmax,
+                    &w->rpart};
   for (DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   delete w;
@@ -132,6 +135,8 @@ __global__ void init_random_kernel(const DevFrag* fr, const int* cta_start, int 
 // Cyclic parallel Jacobi on the symmetric n x n matrix A (leading dim lda),
 // accumulating the rotations into V (which must hold the identity or a
 // start basis).  Round-robin pairing: n_even/2 disjoint rotations per round.
+// A and V live in shared memory when they fit, so a round costs three
+// CTA barriers and no global-memory round trips.
 __device__ void cta_jacobi(double* A, double* V, int n, int lda, int* perm, double* cs,
                            double* red) {
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -142,7 +147,7 @@ __device__ void cta_jacobi(double* A, double* V, int n, int lda, int* perm, doub
   for (int sweep = 0; sweep < 40; ++sweep) {
     double off = 0.0, tot = 0.0;
     for (int e = tid; e < n * n; e += nt) {
-      const int i = e / n, j = e % n;
+      const int i = e / n, j = e - (e / n) * n;
       const double a = A[i * lda + j];
       tot += a * a;
       if (i != j) off += a * a;
@@ -188,7 +193,7 @@ __device__ void cta_jacobi(double* A, double* V, int n, int lda, int* perm, doub
       __syncthreads();
       // rows p, q
       for (int w = tid; w < half * n; w += nt) {
-        const int k = w / n, j = w % n;
+        const int k = w / n, j = w - (w / n) * n;
         const int p = perm[k], q = perm[ne - 1 - k];
         if (p >= n || q >= n) continue;
         const double c = cs[2 * k], s = cs[2 * k + 1];
@@ -200,7 +205,7 @@ __device__ void cta_jacobi(double* A, double* V, int n, int lda, int* perm, doub
       __syncthreads();
       // columns p, q of A and V
       for (int w = tid; w < half * n; w += nt) {
-        const int k = w / n, i = w % n;
+        const int k = w / n, i = w - (w / n) * n;
         const int p = perm[k], q = perm[ne - 1 - k];
         if (p >= n || q >= n) continue;
         const double c = cs[2 * k], s = cs[2 * k + 1];
@@ -226,14 +231,17 @@ __device__ void cta_jacobi(double* A, double* V, int n, int lda, int* perm, doub
 // Inputs: blocks of the self pair of fragment f, [K | G] with K = Y^T H Y
 // and G = Y^T Y (m x m each, symmetrised).  Outputs: C (m x m row-major,
 // columns = Ritz vectors in the Y basis, ascending Ritz values; dropped
-// directions give zero columns), theta (m, +inf style fill for dropped),
-// rank (number of kept directions).
+// directions give zero columns), theta (m; dropped directions repeat the
+// largest kept value), rank (number of kept directions).
+// Work matrices A, U, W (row stride ld) and vectors D, sig, idx live in
+// dynamic shared memory (ld = m + 1) or, for large m, in `work` (ld = m).
 __global__ void __launch_bounds__(256) rayleigh_ritz_kernel(const DevFrag* efr, const DevPair* gp,
                                                             const double* blocks, double* work,
                                                             long long wstride, double* Cm,
                                                             long long cstride, double* theta,
                                                             const long long* toff, double rank_tol,
-                                                            int* rank_out) {
+                                                            int* rank_out, int use_smem) {
+  extern __shared__ double rr_smem[];
   __shared__ int perm[520];
   __shared__ double cs[520];
   __shared__ double red[80];
@@ -243,10 +251,11 @@ __global__ void __launch_bounds__(256) rayleigh_ritz_kernel(const DevFrag* efr, 
   const int tid = threadIdx.x, nt = blockDim.x;
   const double* Kb = blocks + gp[f].blk_off;
   const double* Gb = Kb + (long long)m * m;
-  double* A = work + f * wstride;
-  double* U = A + (long long)m * m;
-  double* W = U + (long long)m * m;
-  double* D = W + (long long)m * m;        // m
+  const int ld = use_smem ? m + 1 : m;
+  double* A = use_smem ? rr_smem : work + f * wstride;
+  double* U = A + (long long)m * ld;
+  double* W = U + (long long)m * ld;
+  double* D = W + (long long)m * ld;       // m
   double* sig = D + m;                     // m
   int* idx = (int*)(sig + m);              // m
   double* C = Cm + f * cstride;
@@ -258,19 +267,19 @@ __global__ void __launch_bounds__(256) rayleigh_ritz_kernel(const DevFrag* efr, 
   }
   __syncthreads();
   for (int e = tid; e < m * m; e += nt) {
-    const int i = e / m, j = e % m;
-    A[e] = D[i] * Gb[e] * D[j];
-    U[e] = (i == j) ? 1.0 : 0.0;
+    const int i = e / m, j = e - (e / m) * m;
+    A[i * ld + j] = D[i] * Gb[e] * D[j];
+    U[i * ld + j] = (i == j) ? 1.0 : 0.0;
   }
   __syncthreads();
-  cta_jacobi(A, U, m, m, perm, cs, red);
+  cta_jacobi(A, U, m, ld, perm, cs, red);
   // rank decision on the scaled Gram spectrum
   if (tid == 0) {
     double smax = 0.0;
-    for (int i = 0; i < m; ++i) smax = fmax(smax, A[i * m + i]);
+    for (int i = 0; i < m; ++i) smax = fmax(smax, A[i * ld + i]);
     int r = 0;
     for (int i = 0; i < m; ++i) {
-      const double s = A[i * m + i];
+      const double s = A[i * ld + i];
       if (s > rank_tol * smax) {
         idx[r] = i;
         sig[r] = s;
@@ -281,47 +290,44 @@ __global__ void __launch_bounds__(256) rayleigh_ritz_kernel(const DevFrag* efr, 
   }
   __syncthreads();
   const int r = nkeep;
-  // W = D U_keep sig^-1/2  (m x r, row-major with row stride m)
+  // W = D U_keep sig^-1/2  (m x r)
   for (int e = tid; e < m * r; e += nt) {
-    const int k = e / r, j = e % r;
-    W[k * m + j] = D[k] * U[k * m + idx[j]] / sqrt(sig[j]);
+    const int k = e / r, j = e - (e / r) * r;
+    W[k * ld + j] = D[k] * U[k * ld + idx[j]] / sqrt(sig[j]);
   }
   __syncthreads();
-  // A <- K W (m x r), then U <- W^T (K W) (r x r)
+  // A <- K W (m x r), then U <- W^T (K W) (r x r), symmetrised
   for (int e = tid; e < m * r; e += nt) {
-    const int k = e / r, j = e % r;
+    const int k = e / r, j = e - (e / r) * r;
     double s = 0.0;
-    for (int l = 0; l < m; ++l) s += Kb[(long long)k * m + l] * W[l * m + j];
-    A[k * m + j] = s;
+    for (int l = 0; l < m; ++l) s += Kb[(long long)k * m + l] * W[l * ld + j];
+    A[k * ld + j] = s;
   }
   __syncthreads();
   for (int e = tid; e < r * r; e += nt) {
-    const int i = e / r, j = e % r;
-    double s = 0.0;
-    for (int l = 0; l < m; ++l) s += W[l * m + i] * A[l * m + j];
-    U[i * m + j] = s;
-  }
-  __syncthreads();
-  for (int e = tid; e < r * r; e += nt) {
-    const int i = e / r, j = e % r;
-    if (i < j) {
-      const double v = 0.5 * (U[i * m + j] + U[j * m + i]);
-      U[i * m + j] = v;
-      U[j * m + i] = v;
+    const int i = e / r, j = e - (e / r) * r;
+    if (j < i) continue;
+    double s = 0.0, t = 0.0;
+    for (int l = 0; l < m; ++l) {
+      s += W[l * ld + i] * A[l * ld + j];
+      t += W[l * ld + j] * A[l * ld + i];
     }
-  }
-  for (int e = tid; e < r * r; e += nt) {
-    const int i = e / r, j = e % r;
-    A[i * m + j] = (i == j) ? 1.0 : 0.0;
+    U[i * ld + j] = 0.5 * (s + t);
+    U[j * ld + i] = 0.5 * (s + t);
   }
   __syncthreads();
-  cta_jacobi(U, A, r, m, perm, cs, red);     // U -> diag(theta), A -> Q
+  for (int e = tid; e < r * r; e += nt) {
+    const int i = e / r, j = e - (e / r) * r;
+    A[i * ld + j] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  cta_jacobi(U, A, r, ld, perm, cs, red);     // U -> diag(theta), A -> Q
   // ascending order: rank of each Ritz value
   for (int j = tid; j < r; j += nt) {
-    const double t = U[j * m + j];
+    const double t = U[j * ld + j];
     int rk = 0;
     for (int i = 0; i < r; ++i) {
-      const double ti = U[i * m + i];
+      const double ti = U[i * ld + i];
       rk += (ti < t || (ti == t && i < j)) ? 1 : 0;
     }
     idx[j] = rk;
@@ -331,126 +337,142 @@ __global__ void __launch_bounds__(256) rayleigh_ritz_kernel(const DevFrag* efr, 
   for (int e = tid; e < m * m; e += nt) C[e] = 0.0;
   __syncthreads();
   for (int e = tid; e < m * r; e += nt) {
-    const int k = e / r, j = e % r;
+    const int k = e / r, j = e - (e / r) * r;
     double s = 0.0;
-    for (int l = 0; l < r; ++l) s += W[k * m + l] * A[l * m + j];
+    for (int l = 0; l < r; ++l) s += W[k * ld + l] * A[l * ld + j];
     C[(long long)k * m + idx[j]] = s;
   }
   double tmax = -DBL_MAX;
-  for (int j = 0; j < r; ++j) tmax = fmax(tmax, U[j * m + j]);
+  for (int j = 0; j < r; ++j) tmax = fmax(tmax, U[j * ld + j]);
   for (int j = tid; j < m; j += nt) {
-    if (j < r) th[idx[j]] = U[j * m + j];
+    if (j < r) th[idx[j]] = U[j * ld + j];
     else th[j] = tmax;
   }
   if (tid == 0) rank_out[f] = r;
 }
 
-// out = in C over interior points (columns >= rank: fresh random values).
+// X_new = Y C and HX_new = HY C over the interior points (columns >= rank
+// get fresh random values and H X = 0), plus per-block partial sums of
+// (HX_new - theta X_new)^2 per column for the residual norms.  A thread owns
+// one column j of a group of points, so the partial sums need no atomics.
 template <typename T>
-__global__ void __launch_bounds__(256) rotate_kernel(const DevFrag* efr, const T* in0, T* out0,
-                                                     const T* in1, T* out1, const double* Cm,
+__global__ void __launch_bounds__(256) rotate_kernel(const DevFrag* efr, const T* Y, T* Xo,
+                                                     const T* HY, T* HXo, const double* Cm,
                                                      long long cstride, const int* rank,
+                                                     const double* theta, const long long* toff,
+                                                     double* partial, int mstride,
                                                      unsigned long long salt) {
-  extern __shared__ unsigned char smem_raw[];
-  T* Cs = reinterpret_cast<T*>(smem_raw);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int TP = 32;
   const int f = blockIdx.y;
   const DevFrag F = efr[f];
   const int m = F.n;
   const int r = rank[f];
-  const long long P = (long long)F.ext[0] * F.ext[1] * F.ext[2];
-  constexpr int TP = 32;
-  T* rows = Cs + m * m;
+  const int ex = F.ext[0], ey = F.ext[1];
+  const int P = F.ext[0] * F.ext[1] * F.ext[2];
+  double* red = reinterpret_cast<double*>(smem_raw);            // blockDim.x
+  int* pds = reinterpret_cast<int*>(red + blockDim.x);           // TP
+  T* Cs = reinterpret_cast<T*>(pds + TP);                        // m * m
+  T* ys = Cs + m * m;                                            // TP * m
+  T* hs = ys + TP * m;                                           // TP * m
   for (int e = threadIdx.x; e < m * m; e += blockDim.x) Cs[e] = (T)Cm[f * cstride + e];
-  const T* in = blockIdx.z == 0 ? in0 : in1;
-  T* out = blockIdx.z == 0 ? out0 : out1;
-  for (long long t0 = (long long)blockIdx.x * TP; t0 < P; t0 += (long long)gridDim.x * TP) {
+  const int G = blockDim.x / m;
+  const int j = threadIdx.x % m, g = threadIdx.x / m;
+  const bool active = g < G;
+  const double th = active ? theta[toff[f] + j] : 0.0;
+  const unsigned long long s0 = splitmix64(salt);
+  double racc = 0.0;
+  for (int t0 = blockIdx.x * TP; t0 < P; t0 += gridDim.x * TP) {
     __syncthreads();
-    for (int e = threadIdx.x; e < TP * m; e += blockDim.x) {
-      const int pp = e / m, k = e % m;
-      const long long t = t0 + pp;
-      T v = 0;
+    if (threadIdx.x < TP) {
+      const int t = t0 + threadIdx.x;
+      int pd = -1;
       if (t < P) {
-        const int x = (int)(t % F.ext[0]), y = (int)((t / F.ext[0]) % F.ext[1]);
-        const int z = (int)(t / ((long long)F.ext[0] * F.ext[1]));
-        const long long pd = ((long long)(z + F.lo[2]) * F.dext[1] + (y + F.lo[1])) * F.dext[0] + x + F.lo[0];
-        v = in[F.off + pd * F.ld + k];
+        const int x = t % ex, y = (t / ex) % ey, z = t / (ex * ey);
+        pd = ((z + F.lo[2]) * F.dext[1] + (y + F.lo[1])) * F.dext[0] + x + F.lo[0];
       }
-      rows[pp * m + k] = v;
+      pds[threadIdx.x] = pd;
     }
     __syncthreads();
     for (int e = threadIdx.x; e < TP * m; e += blockDim.x) {
-      const int pp = e / m, j = e % m;
-      const long long t = t0 + pp;
-      if (t >= P) continue;
-      const int x = (int)(t % F.ext[0]), y = (int)((t / F.ext[0]) % F.ext[1]);
-      const int z = (int)(t / ((long long)F.ext[0] * F.ext[1]));
-      const long long pd = ((long long)(z + F.lo[2]) * F.dext[1] + (y + F.lo[1])) * F.dext[0] + x + F.lo[0];
-      T s = 0;
-      if (j < r) {
-        for (int k = 0; k < m; ++k) s += rows[pp * m + k] * Cs[k * m + j];
-      } else if (blockIdx.z == 0) {
-        unsigned long long key = ((unsigned long long)f << 44) ^ ((unsigned long long)j << 32) ^ (unsigned long long)pd;
-        unsigned long long rr = splitmix64(key + splitmix64(salt));
-        s = (T)(((double)(rr >> 11) * (2.0 / 9007199254740992.0) - 1.0) / sqrt((double)P));
-      }
-      out[F.off + pd * F.ld + j] = s;
+      const int pp = e / m, k = e - pp * m;
+      const int pd = pds[pp];
+      const long long a = F.off + (long long)pd * F.ld + k;
+      ys[e] = pd >= 0 ? Y[a] : (T)0;
+      hs[e] = pd >= 0 ? HY[a] : (T)0;
     }
+    __syncthreads();
+    if (active) {
+      for (int pp = g; pp < TP; pp += G) {
+        const int pd = pds[pp];
+        if (pd < 0) continue;
+        T x = 0, hx = 0;
+        if (j < r) {
+          const T* yr = ys + pp * m;
+          const T* hr = hs + pp * m;
+          for (int k = 0; k < m; ++k) {
+            const T cc = Cs[k * m + j];
+            x += yr[k] * cc;
+            hx += hr[k] * cc;
+          }
+        } else {
+          const unsigned long long key = ((unsigned long long)f << 44) ^ ((unsigned long long)j << 32) ^ (unsigned long long)pd;
+          const unsigned long long rr = splitmix64(key + s0);
+          x = (T)(((double)(rr >> 11) * (2.0 / 9007199254740992.0) - 1.0) / sqrt((double)P));
+        }
+        const long long a = F.off + (long long)pd * F.ld + j;
+        Xo[a] = x;
+        HXo[a] = hx;
+        const double d = (double)hx - th * (double)x;
+        racc += d * d;
+      }
+    }
+  }
+  __syncthreads();
+  red[threadIdx.x] = racc;
+  __syncthreads();
+  if (threadIdx.x < m) {
+    double s = 0.0;
+    for (int gg = 0; gg < G; ++gg) s += red[gg * m + threadIdx.x];
+    partial[((long long)f * gridDim.x + blockIdx.x) * mstride + threadIdx.x] = s;
   }
 }
 
-// res[i] = || HX_i - theta_i X_i ||  (interior points), lanes = states.
-template <typename T>
-__global__ void __launch_bounds__(256) residual_kernel(const DevFrag* efr, const T* X, const T* HX,
-                                                       const double* theta, const long long* toff,
-                                                       double* res) {
-  __shared__ double part[8][32];
+// res = sqrt(sum of the per-block partials), fixed order.
+__global__ void residual_reduce_kernel(const DevFrag* efr, const double* partial, int nblocks,
+                                       int mstride, const long long* toff, double* res) {
   const int f = blockIdx.x;
-  const DevFrag F = efr[f];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int col = blockIdx.y * 32 + lane;
-  const long long P = (long long)F.ext[0] * F.ext[1] * F.ext[2];
-  double s = 0.0;
-  if (col < F.n) {
-    const double th = theta[toff[f] + col];
-    for (long long t = warp; t < P; t += 8) {
-      const int x = (int)(t % F.ext[0]), y = (int)((t / F.ext[0]) % F.ext[1]);
-      const int z = (int)(t / ((long long)F.ext[0] * F.ext[1]));
-      const long long pd = ((long long)(z + F.lo[2]) * F.dext[1] + (y + F.lo[1])) * F.dext[0] + x + F.lo[0];
-      const double d = (double)HX[F.off + pd * F.ld + col] - th * (double)X[F.off + pd * F.ld + col];
-      s += d * d;
-    }
-  }
-  part[warp][lane] = s;
-  __syncthreads();
-  if (warp == 0 && col < F.n) {
-    double t = 0.0;
-    for (int w = 0; w < 8; ++w) t += part[w][lane];
-    res[toff[f] + col] = sqrt(t);
+  const int m = efr[f].n;
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += partial[((long long)f * nblocks + b) * mstride + j];
+    res[toff[f] + j] = sqrt(s);
   }
 }
 
 // First n columns of the block -> state storage, sign gauge applied.
+// 32 warps stride over the points; lanes are states.
 template <typename T>
-__global__ void __launch_bounds__(256) export_states_kernel(const DevFrag* efr, const DevFrag* fr,
-                                                            const T* X, T* states) {
-  __shared__ double bv[8][32];
-  __shared__ long long bi[8][32];
+__global__ void __launch_bounds__(1024) export_states_kernel(const DevFrag* efr, const DevFrag* fr,
+                                                             const T* X, T* states) {
+  __shared__ double bv[32][32];
+  __shared__ int bi[32][32];
   __shared__ double sgn[32];
   const int f = blockIdx.x;
   const DevFrag E = efr[f];
   const DevFrag F = fr[f];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int col = blockIdx.y * 32 + lane;
-  const long long P = (long long)F.ext[0] * F.ext[1] * F.ext[2];
+  const int ex = F.ext[0], ey = F.ext[1];
+  const int P = F.ext[0] * F.ext[1] * F.ext[2];
   double best = -1.0;
-  long long besti = 0;
+  int besti = 0;
   if (col < F.n) {
-    for (long long t = warp; t < P; t += 8) {
-      const int x = (int)(t % F.ext[0]), y = (int)((t / F.ext[0]) % F.ext[1]);
-      const int z = (int)(t / ((long long)F.ext[0] * F.ext[1]));
-      const long long pd = ((long long)(z + E.lo[2]) * E.dext[1] + (y + E.lo[1])) * E.dext[0] + x + E.lo[0];
-      const double a = fabs((double)X[E.off + pd * E.ld + col]);
-      if (a > best) {  // strictly greater: lowest index wins within a warp's stream
+    for (int t = warp; t < P; t += 32) {
+      const int x = t % ex, y = (t / ex) % ey, z = t / (ex * ey);
+      const int pd = ((z + E.lo[2]) * E.dext[1] + (y + E.lo[1])) * E.dext[0] + x + E.lo[0];
+      const double a = fabs((double)X[E.off + (long long)pd * E.ld + col]);
+      if (a > best) {  // strictly greater: the lowest index wins within a warp's stream
         best = a;
         besti = t;
       }
@@ -461,8 +483,8 @@ __global__ void __launch_bounds__(256) export_states_kernel(const DevFrag* efr, 
   __syncthreads();
   if (warp == 0) {
     double b = bv[0][lane];
-    long long ib = bi[0][lane];
-    for (int w = 1; w < 8; ++w) {
+    int ib = bi[0][lane];
+    for (int w = 1; w < 32; ++w) {
       if (bv[w][lane] > b || (bv[w][lane] == b && bi[w][lane] < ib)) {
         b = bv[w][lane];
         ib = bi[w][lane];
@@ -470,22 +492,20 @@ __global__ void __launch_bounds__(256) export_states_kernel(const DevFrag* efr, 
     }
     double sg = 1.0;
     if (col < F.n) {
-      const int x = (int)(ib % F.ext[0]), y = (int)((ib / F.ext[0]) % F.ext[1]);
-      const int z = (int)(ib / ((long long)F.ext[0] * F.ext[1]));
-      const long long pd = ((long long)(z + E.lo[2]) * E.dext[1] + (y + E.lo[1])) * E.dext[0] + x + E.lo[0];
-      sg = (double)X[E.off + pd * E.ld + col] < 0.0 ? -1.0 : 1.0;
+      const int x = ib % ex, y = (ib / ex) % ey, z = ib / (ex * ey);
+      const int pd = ((z + E.lo[2]) * E.dext[1] + (y + E.lo[1])) * E.dext[0] + x + E.lo[0];
+      sg = (double)X[E.off + (long long)pd * E.ld + col] < 0.0 ? -1.0 : 1.0;
     }
     sgn[lane] = sg;
   }
   __syncthreads();
   if (col >= F.n) return;
   const T s = (T)sgn[lane];
-  for (long long t = warp; t < P; t += 8) {
-    const int x = (int)(t % F.ext[0]), y = (int)((t / F.ext[0]) % F.ext[1]);
-    const int z = (int)(t / ((long long)F.ext[0] * F.ext[1]));
-    const long long pe = ((long long)(z + E.lo[2]) * E.dext[1] + (y + E.lo[1])) * E.dext[0] + x + E.lo[0];
-    const long long pf = ((long long)(z + F.lo[2]) * F.dext[1] + (y + F.lo[1])) * F.dext[0] + x + F.lo[0];
-    states[F.off + pf * F.ld + col] = s * X[E.off + pe * E.ld + col];
+  for (int t = warp; t < P; t += 32) {
+    const int x = t % ex, y = (t / ex) % ey, z = t / (ex * ey);
+    const int pe = ((z + E.lo[2]) * E.dext[1] + (y + E.lo[1])) * E.dext[0] + x + E.lo[0];
+    const int pf = ((z + F.lo[2]) * F.dext[1] + (y + F.lo[1])) * F.dext[0] + x + F.lo[0];
+    states[F.off + (long long)pf * F.ld + col] = s * X[E.off + (long long)pe * E.ld + col];
   }
 }
 
@@ -525,7 +545,7 @@ static ofm_status eig_setup(ofm_ctx* c, int guard_opt) {
     const long long P = (long long)E.ext[0] * E.ext[1] * E.ext[2];
     int g = guard_opt > 0 ? guard_opt : std::max(4, E.n / 4);
     int m = (int)std::min<long long>((long long)E.n + g, P - 1);
-    m = std::min(m, 512);
+    m = std::min(m, 256);
     E.n = m;
     E.ld = (m + 3) / 4 * 4;
     E.off = w->elems;
@@ -596,10 +616,17 @@ static ofm_status eig_setup(ofm_ctx* c, int guard_opt) {
   OFM_CUDA(c, cudaGetLastError());
   OFM_CUDA(c, cudaMemcpyAsync(&w->vmax, w->d_vmax.p, sizeof(double), cudaMemcpyDeviceToHost, s));
   OFM_CUDA(c, cudaStreamSynchronize(s));
-  const size_t smem = (size_t)w->mmax * w->mmax * es + 32 * (size_t)w->mmax * es;
-  if (smem > 227 * 1024) return ofm_fail(c, OFM_ERR_INVALID, "block size too large for the rotation kernel");
-  if (fp64) OFM_CUDA(c, cudaFuncSetAttribute(rotate_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  else OFM_CUDA(c, cudaFuncSetAttribute(rotate_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  long long maxP = 0;
+  for (auto& E : w->efr) maxP = std::max<long long>(maxP, (long long)E.ext[0] * E.ext[1] * E.ext[2]);
+  w->rot_blocks = (int)std::min<long long>((maxP + 31) / 32, 64);
+  OFM_TRY(ofm_ensure(c, w->rpart, sizeof(double) * (size_t)nf * w->rot_blocks * w->mmax, "residual partials"));
+  w->rot_smem = 256 * sizeof(double) + 32 * sizeof(int) + ((size_t)w->mmax * w->mmax + 64 * (size_t)w->mmax) * es;
+  if (w->rot_smem > 227 * 1024) return ofm_fail(c, OFM_ERR_INVALID, "block size too large for the rotation kernel");
+  if (fp64) OFM_CUDA(c, cudaFuncSetAttribute(rotate_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w->rot_smem));
+  else OFM_CUDA(c, cudaFuncSetAttribute(rotate_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w->rot_smem));
+  const size_t rr = (3 * (size_t)w->mmax * (w->mmax + 1) + 3 * (size_t)w->mmax) * sizeof(double);
+  w->rr_smem = rr <= 200 * 1024 ? rr : 0;
+  if (w->rr_smem) OFM_CUDA(c, cudaFuncSetAttribute(rayleigh_ritz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w->rr_smem));
   w->ready = true;
   return OFM_OK;
 }
@@ -622,36 +649,30 @@ static ofm_status eig_rr(ofm_ctx* c, int y, int hy, int xo, int hxo, unsigned lo
   }
   const long long mm = (long long)w->mmax * w->mmax;
   { KTimer kt(c, KC_RR);
-  rayleigh_ritz_kernel<<<nf, 256, 0, s>>>((const DevFrag*)w->d_efr.p, (const DevPair*)w->d_gpairs.p,
+  rayleigh_ritz_kernel<<<nf, 256, w->rr_smem, s>>>((const DevFrag*)w->d_efr.p, (const DevPair*)w->d_gpairs.p,
                                           (const double*)w->blocks.p, (double*)w->work.p,
                                           3 * mm + 3 * w->mmax + 8, (double*)w->Cm.p, mm,
                                           (double*)w->theta.p, (const long long*)w->d_toff.p,
-                                          fp64 ? 1e-13 : 1e-6, (int*)w->d_rank.p); }
-  const size_t es = fp64 ? 8 : 4;
-  const size_t smem = (size_t)w->mmax * w->mmax * es + 32 * (size_t)w->mmax * es;
-  long long maxP = 0;
-  for (auto& E : w->efr) maxP = std::max<long long>(maxP, (long long)E.ext[0] * E.ext[1] * E.ext[2]);
-  dim3 g((unsigned)std::min<long long>((maxP + 31) / 32, 64), nf, 2);
+                                          fp64 ? 1e-13 : 1e-6, (int*)w->d_rank.p, w->rr_smem > 0 ? 1 : 0); }
+  dim3 g(w->rot_blocks, nf);
   KTimer kt(c, KC_ROTATE, 2, w->rot_bytes, w->rot_flops);
   if (fp64)
-    rotate_kernel<double><<<g, 256, smem, s>>>((const DevFrag*)w->d_efr.p, (const double*)w->buf[y].p,
+    rotate_kernel<double><<<g, 256, w->rot_smem, s>>>((const DevFrag*)w->d_efr.p, (const double*)w->buf[y].p,
                                                (double*)w->buf[xo].p, (const double*)w->buf[hy].p,
                                                (double*)w->buf[hxo].p, (const double*)w->Cm.p, mm,
-                                               (const int*)w->d_rank.p, salt);
+                                               (const int*)w->d_rank.p, (const double*)w->theta.p,
+                                               (const long long*)w->d_toff.p, (double*)w->rpart.p,
+                                               w->mmax, salt);
   else
-    rotate_kernel<float><<<g, 256, smem, s>>>((const DevFrag*)w->d_efr.p, (const float*)w->buf[y].p,
+    rotate_kernel<float><<<g, 256, w->rot_smem, s>>>((const DevFrag*)w->d_efr.p, (const float*)w->buf[y].p,
                                               (float*)w->buf[xo].p, (const float*)w->buf[hy].p,
                                               (float*)w->buf[hxo].p, (const double*)w->Cm.p, mm,
-                                              (const int*)w->d_rank.p, salt);
-  dim3 rg(nf, (w->mmax + 31) / 32);
-  if (fp64)
-    residual_kernel<double><<<rg, 256, 0, s>>>((const DevFrag*)w->d_efr.p, (const double*)w->buf[xo].p,
-                                               (const double*)w->buf[hxo].p, (const double*)w->theta.p,
-                                               (const long long*)w->d_toff.p, (double*)w->res.p);
-  else
-    residual_kernel<float><<<rg, 256, 0, s>>>((const DevFrag*)w->d_efr.p, (const float*)w->buf[xo].p,
-                                              (const float*)w->buf[hxo].p, (const double*)w->theta.p,
-                                              (const long long*)w->d_toff.p, (double*)w->res.p);
+                                              (const int*)w->d_rank.p, (const double*)w->theta.p,
+                                              (const long long*)w->d_toff.p, (double*)w->rpart.p,
+                                              w->mmax, salt);
+  residual_reduce_kernel<<<nf, 128, 0, s>>>((const DevFrag*)w->d_efr.p, (const double*)w->rpart.p,
+                                            w->rot_blocks, w->mmax, (const long long*)w->d_toff.p,
+                                            (double*)w->res.p);
   OFM_CUDA(c, cudaGetLastError());
   return OFM_OK;
 }

@@ -178,7 +178,7 @@ struct ofm_ctx {
   // device buffers
   ofm::DevBuf V, states, hphi, d_frags, d_apply_start, d_pairs, d_pieces, d_items, partials,
       blocks, dense_H, dense_S, staging, flag;
-  ofm::DevBuf w_A, w_L, w_d, w_e, w_tau, w_tmp, w_eval;   // window-solver workspaces
+  ofm::DevBuf w_A, w_L, w_d, w_e, w_tau, w_tmp, w_eval, w_bar;   // window-solver workspaces
   int dense_n = 0;
   int window_fail_col = -1;
   std::vector<char> frag_set;       // per fragment: states imported or computed
@@ -208,6 +208,11 @@ ofm_status ofm_window_factor(ofm_ctx* c);
 ofm_status ofm_window_count(ofm_ctx* c, double x, bool inclusive, int* count);
 ofm_status ofm_window_bisect(ofm_ctx* c, int i_lo, int i_hi, double* E_out);
 ofm_status ofm_window_vectors(ofm_ctx* c, int m, double* C_out);
+ofm_status ofm_tridiag_persistent(ofm_ctx* c, double* A, int n, double* d, double* e, double* tau,
+                                  double* pg);
+void launch_count_below(const double* d, const double* e, int n, double x, int* out, cudaStream_t s);
+void launch_multisection(const double* d, const double* e, int n, int i_lo, int m, double* out,
+                         cudaStream_t s);
 
 // Counts the launches of one kernel class and, while profiling is on,
 // brackets them with CUDA events on the context stream.

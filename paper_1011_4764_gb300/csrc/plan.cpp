@@ -70,6 +70,12 @@ bool validate_geometry(const ofm_grid& g, const ofm_fragment* f, int nf, std::st
       }
       P *= e;
     }
+    long long Pd = 1;
+    for (int d = 0; d < 3; ++d) Pd *= (f[a].ext[d] < g.n[d]) ? f[a].ext[d] + 2 : f[a].ext[d];
+    if (Pd * 1024 >= (1LL << 31)) {
+      snprintf(buf, sizeof buf, "fragment %d: box of %lld points is too large (limit 2^21)", a, Pd);
+      err = buf; return false;
+    }
     if (f[a].n_states < 1 || f[a].n_states > P - 1 || f[a].n_states > 1024) {
       snprintf(buf, sizeof buf, "fragment %d: n_states=%d outside [1, min(P-1, 1024)] (P=%lld)", a,
                f[a].n_states, P);

@@ -1,0 +1,277 @@
+// Symmetric tridiagonal reduction and spectrum slicing for the window solve
+// of Eq. 2 (after the reduction A = L^-1 H L^-T).
+//
+// 1. Householder reduction of A to tridiagonal form in ONE persistent
+//    cooperative kernel: per column k, every CTA forms the Householder
+//    vector itself (a short column read), the CTAs compute p = tau A22 v by
+//    rows, meet at a grid barrier, apply A22 -= v w^T + w v^T
+//    (w = p - (tau/2)(v^T p) v) by rows and meet again.  Two barriers per
+//    column instead of three kernel launches.  The barrier spins a bounded
+//    number of times and reports a timeout instead of hanging.
+// 2. Eigenvalues by index with multisection: one warp per wanted
+//    eigenvalue; each lane counts the eigenvalues below one of 32 points of
+//    the current interval (Sturm sequence of T - x I written as the
+//    three-term recurrence of the leading principal minors, rescaled by
+//    powers of two, so a step needs no division), and the interval shrinks
+//    33-fold per round.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+
+#include "ofm_internal.h"
+
+namespace ofm {
+
+struct GridBar {
+  unsigned int count;
+  unsigned int gen;
+  int err;
+  int pad;
+};
+
+// All CTAs of a cooperative launch meet here.  Returns false (and sets
+// bar->err) when the wait exceeded its bound or another CTA gave up.
+__device__ bool grid_sync(GridBar* bar, unsigned int nblocks) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* vgen = &bar->gen;
+    volatile int* verr = &bar->err;
+    const unsigned int g = *vgen;
+    __threadfence();
+    const unsigned int arrived = atomicAdd(&bar->count, 1u);
+    ok = 1;
+    if (arrived == nblocks - 1) {
+      atomicExch(&bar->count, 0u);
+      __threadfence();
+      atomicAdd(&bar->gen, 1u);
+    } else {
+      unsigned int spins = 0;
+      while (*vgen == g) {
+        if (*verr != 0 || ++spins > (1u << 24)) {
+          atomicExch(&bar->err, 1);
+          ok = 0;
+          break;
+        }
+        if (spins > 32) __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+__device__ __forceinline__ double block_sum(double s, double* red) {
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) red[32] = s;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+__global__ void __launch_bounds__(512) tridiag_persistent_kernel(double* A, int n, double* d,
+                                                                 double* e, double* tau,
+                                                                 double* pg, GridBar* bar) {
+  // matrix entries written by other CTAs since the last barrier are read
+  // through L2 (__ldcg): L1 is not coherent across SMs
+  extern __shared__ double sv[];
+  double* v = sv;        // n: Householder vector at indices k+1..n-1
+  double* pw = sv + n;   // n: p at indices k+1..n-1
+  __shared__ double red[40];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
+  const unsigned int nb = gridDim.x;
+  const int gw = blockIdx.x * nwarps + warp, gws = nb * nwarps;
+  for (int k = 0; k + 2 < n; ++k) {
+    const int m = n - k - 1;
+    // Householder vector of column k (every CTA, redundantly)
+    double s = 0.0;
+    for (int i = tid + 1; i < m; i += nt) {
+      const double x = __ldcg(&A[(long long)(k + 1 + i) * n + k]);
+      s += x * x;
+    }
+    const double sig = block_sum(s, red);
+    const double x0 = __ldcg(&A[(long long)(k + 1) * n + k]);
+    double alpha, t, v0;
+    if (sig == 0.0) {
+      alpha = x0;
+      t = 0.0;
+      v0 = 1.0;
+    } else {
+      const double nrm = sqrt(x0 * x0 + sig);
+      alpha = (x0 > 0.0) ? -nrm : nrm;
+      v0 = x0 - alpha;
+      t = 2.0 / (v0 * v0 + sig);
+    }
+    for (int i = tid; i < m; i += nt) {
+      const double vi = (i == 0) ? v0 : __ldcg(&A[(long long)(k + 1 + i) * n + k]);
+      v[k + 1 + i] = vi;
+      if (blockIdx.x == 0) A[(long long)k * n + k + 1 + i] = vi;  // kept for back-transformation
+    }
+    if (blockIdx.x == 0 && tid == 0) {
+      d[k] = __ldcg(&A[(long long)k * n + k]);
+      e[k] = alpha;
+      tau[k] = t;
+    }
+    __syncthreads();
+    // p = t A22 v, one warp per row
+    for (int r = gw; r < m; r += gws) {
+      const int i = k + 1 + r;
+      const double* row = A + (long long)i * n;
+      double acc = 0.0;
+      for (int j = k + 1 + lane; j < n; j += 32) acc += __ldcg(&row[j]) * v[j];
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+      if (lane == 0) pg[i] = t * acc;
+    }
+    if (!grid_sync(bar, nb)) return;
+    for (int j = tid; j < m; j += nt) pw[k + 1 + j] = __ldcg(&pg[k + 1 + j]);
+    __syncthreads();
+    double q = 0.0;
+    for (int j = tid; j < m; j += nt) q += v[k + 1 + j] * pw[k + 1 + j];
+    const double K = 0.5 * t * block_sum(q, red);
+    for (int r = gw; r < m; r += gws) {
+      const int i = k + 1 + r;
+      const double vi = v[i], wi = pw[i] - K * vi;
+      double* row = A + (long long)i * n;
+      for (int j = k + 1 + lane; j < n; j += 32)
+        row[j] = __ldcg(&row[j]) - (vi * (pw[j] - K * v[j]) + wi * v[j]);
+    }
+    if (!grid_sync(bar, nb)) return;
+  }
+  if (blockIdx.x == 0 && tid == 0) {
+    if (n >= 2) {
+      d[n - 2] = __ldcg(&A[(long long)(n - 2) * n + n - 2]);
+      e[n - 2] = __ldcg(&A[(long long)(n - 1) * n + n - 2]);
+    }
+    d[n - 1] = __ldcg(&A[(long long)(n - 1) * n + n - 1]);
+  }
+}
+
+// Number of eigenvalues of the tridiagonal (d, e) below x: sign changes of
+// the leading principal minors p_i of T - x I (p_0 = 1), a zero minor
+// counted as a change; both running minors are rescaled by a power of two
+// when the newest leaves [2^-400, 2^400].
+__device__ int sturm_count(const double* __restrict__ d, const double* __restrict__ e, int n,
+                           double x) {
+  double p0 = 1.0, p1 = d[0] - x;
+  if (p1 == 0.0) p1 = -DBL_MIN;
+  int c = p1 < 0.0 ? 1 : 0;
+  for (int i = 1; i < n; ++i) {
+    const double ei = e[i - 1];
+    double p2 = fma(d[i] - x, p1, -(ei * ei) * p0);
+    if (p2 == 0.0) p2 = (p1 < 0.0) ? DBL_MIN : -DBL_MIN;
+    c += ((p2 < 0.0) != (p1 < 0.0)) ? 1 : 0;
+    const double a = fabs(p2);
+    if (a > 0x1p400 || a < 0x1p-400) {
+      const int ex = ilogb(p2);
+      p2 = scalbn(p2, -ex);
+      p1 = scalbn(p1, -ex);
+    }
+    p0 = p1;
+    p1 = p2;
+  }
+  return c;
+}
+
+__global__ void count_below_kernel(const double* d, const double* e, int n, double x, int* out) {
+  *out = sturm_count(d, e, n, x);
+}
+
+// One warp per eigenvalue index i_lo + warp; out[warp] = the eigenvalue.
+__global__ void __launch_bounds__(256) multisection_kernel(const double* __restrict__ d,
+                                                           const double* __restrict__ e, int n,
+                                                           int i_lo, int m, double* out) {
+  const int lane = threadIdx.x & 31;
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= m) return;
+  const int idx = i_lo + w;
+  // Gershgorin interval
+  double a = DBL_MAX, b = -DBL_MAX;
+  for (int j = lane; j < n; j += 32) {
+    const double r = (j > 0 ? fabs(e[j - 1]) : 0.0) + (j < n - 1 ? fabs(e[j]) : 0.0);
+    a = fmin(a, d[j] - r);
+    b = fmax(b, d[j] + r);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a = fmin(a, __shfl_xor_sync(0xffffffffu, a, o));
+    b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+  }
+  const double wdt = fmax(fabs(a), fabs(b));
+  double lo = a - 2.0 * DBL_EPSILON * wdt - DBL_MIN;
+  double hi = b + 2.0 * DBL_EPSILON * wdt + DBL_MIN;
+  for (int it = 0; it < 64; ++it) {
+    if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + 4.0 * DBL_MIN) break;
+    const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
+    const int cnt = sturm_count(d, e, n, x);
+    const unsigned mask = __ballot_sync(0xffffffffu, cnt > idx);
+    const double xprev = __shfl_up_sync(0xffffffffu, x, 1);
+    if (mask == 0) {
+      lo = __shfl_sync(0xffffffffu, x, 31);
+    } else {
+      const int l = __ffs(mask) - 1;
+      const double nhi = __shfl_sync(0xffffffffu, x, l);
+      const double xl = __shfl_sync(0xffffffffu, xprev, l);
+      const double nlo = (l > 0) ? xl : lo;
+      if (nhi == hi && nlo == lo) break;  // no progress at this precision
+      lo = nlo;
+      hi = nhi;
+    }
+  }
+  if (lane == 0) out[w] = 0.5 * (lo + hi);
+}
+
+}  // namespace ofm
+
+using namespace ofm;
+
+// Returns OFM_OK when the persistent reduction ran; OFM_ERR_INVALID when it
+// cannot be used here (the caller then takes the per-column launch path).
+ofm_status ofm_tridiag_persistent(ofm_ctx* c, double* A, int n, double* d, double* e, double* tau,
+                                  double* pg) {
+  const size_t smem = 2 * (size_t)n * sizeof(double);
+  if (n < 3 || smem > 200 * 1024) return OFM_ERR_INVALID;
+  int dev = 0, coop = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (!coop) return OFM_ERR_INVALID;
+  OFM_CUDA(c, cudaFuncSetAttribute(tridiag_persistent_kernel,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  OFM_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tridiag_persistent_kernel, 512, smem));
+  if (per_sm < 1) return OFM_ERR_INVALID;
+  // enough warps for one row each at the first column, never more than co-resident
+  int nb = std::min(sms * per_sm, std::max(1, (n + 15) / 16));
+  nb = std::min(nb, 128);
+  OFM_TRY(ofm_ensure(c, c->w_bar, sizeof(GridBar), "grid barrier"));
+  OFM_CUDA(c, cudaMemsetAsync(c->w_bar.p, 0, sizeof(GridBar), c->stream));
+  GridBar* bar = (GridBar*)c->w_bar.p;
+  void* args[] = {&A, &n, &d, &e, &tau, &pg, &bar};
+  OFM_CUDA(c, cudaLaunchCooperativeKernel((const void*)tridiag_persistent_kernel, dim3(nb),
+                                          dim3(512), args, smem, c->stream));
+  GridBar hb{};
+  OFM_CUDA(c, cudaMemcpyAsync(&hb, bar, sizeof(GridBar), cudaMemcpyDeviceToHost, c->stream));
+  OFM_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (hb.err) return ofm_fail(c, OFM_ERR_TIMEOUT, "tridiagonal reduction: grid barrier wait exceeded its bound");
+  return OFM_OK;
+}
+
+void launch_count_below(const double* d, const double* e, int n, double x, int* out, cudaStream_t s) {
+  count_below_kernel<<<1, 1, 0, s>>>(d, e, n, x, out);
+}
+
+void launch_multisection(const double* d, const double* e, int n, int i_lo, int m, double* out,
+                         cudaStream_t s) {
+  const int warps_per_block = 8;
+  multisection_kernel<<<(m + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, s>>>(
+      d, e, n, i_lo, m, out);
+}

@@ -421,7 +421,14 @@ ofm_status ofm_window_factor(ofm_ctx* c) {
   double* vbuf = (double*)c->w_tmp.p;
   double* p = vbuf + n;
   {
-  KTimer kt(c, KC_TRIDIAG, 1 + 3LL * std::max(0, n - 2));
+  KTimer kt(c, KC_TRIDIAG, 0);
+  const ofm_status ps = ofm_tridiag_persistent(c, A, n, d, e, tau, p);
+  if (ps == OFM_OK) {
+    kt.add(1);
+  } else if (ps != OFM_ERR_INVALID) {
+    return ps;
+  } else {
+  kt.add(1 + 3LL * std::max(0, n - 2));
   for (int k = 0; k + 2 < n; ++k) {
     householder_kernel<<<1, 256, 0, s>>>(A, n, k, vbuf, d, e, tau);
     const int m = n - k - 1;
@@ -429,6 +436,7 @@ ofm_status ofm_window_factor(ofm_ctx* c) {
     rank2_kernel<<<dim3((m + 63) / 64, (m + 7) / 8), dim3(32, 8), 0, s>>>(A, n, k, vbuf, p, tau);
   }
   tridiag_tail_kernel<<<1, 1, 0, s>>>(A, n, d, e);
+  }
   }
   OFM_CUDA(c, cudaGetLastError());
   OFM_TRY(sync_ctx(c, "tridiagonalisation"));
@@ -440,8 +448,8 @@ ofm_status ofm_window_count(ofm_ctx* c, double x, bool inclusive, int* count) {
   if (inclusive) x = std::nextafter(x, HUGE_VAL);
   int* dc = (int*)c->flag.p + 1;
   KTimer kt(c, KC_BISECT);
-  count_kernel<<<1, 1, 0, c->stream>>>((const double*)c->w_d.p, (const double*)c->w_e.p,
-                                       c->dense_n, x, dc);
+  launch_count_below((const double*)c->w_d.p, (const double*)c->w_e.p, c->dense_n, x, dc,
+                     c->stream);
   OFM_CUDA(c, cudaGetLastError());
   OFM_CUDA(c, cudaMemcpyAsync(count, dc, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   return sync_ctx(c, "Sturm count");
@@ -451,9 +459,8 @@ ofm_status ofm_window_bisect(ofm_ctx* c, int i_lo, int i_hi, double* E_out) {
   const int m = i_hi - i_lo;
   double* out = (double*)c->w_tmp.p;  // 2n doubles, m <= n
   KTimer kt(c, KC_BISECT);
-  bisect_kernel<<<(m + 127) / 128, 128, 0, c->stream>>>((const double*)c->w_d.p,
-                                                       (const double*)c->w_e.p, c->dense_n, i_lo,
-                                                       m, out);
+  launch_multisection((const double*)c->w_d.p, (const double*)c->w_e.p, c->dense_n, i_lo, m, out,
+                      c->stream);
   OFM_CUDA(c, cudaGetLastError());
   OFM_CUDA(c, cudaMemcpyAsync(E_out, out, sizeof(double) * m, cudaMemcpyDeviceToHost, c->stream));
   return sync_ctx(c, "bisection");
