@@ -462,13 +462,14 @@ __global__ void __launch_bounds__(1024) export_states_kernel(const DevFrag* efr,
   const DevFrag E = efr[f];
   const DevFrag F = fr[f];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = (int)(blockDim.x >> 5);   // <= 32 warps (launch bound 1024)
   const int col = blockIdx.y * 32 + lane;
   const int ex = F.ext[0], ey = F.ext[1];
   const int P = F.ext[0] * F.ext[1] * F.ext[2];
   double best = -1.0;
   int besti = 0;
   if (col < F.n) {
-    for (int t = warp; t < P; t += 32) {
+    for (int t = warp; t < P; t += nw) {
       const int x = t % ex, y = (t / ex) % ey, z = t / (ex * ey);
       const int pd = ((z + E.lo[2]) * E.dext[1] + (y + E.lo[1])) * E.dext[0] + x + E.lo[0];
       const double a = fabs((double)X[E.off + (long long)pd * E.ld + col]);
@@ -484,14 +485,14 @@ __global__ void __launch_bounds__(1024) export_states_kernel(const DevFrag* efr,
   if (warp == 0) {
     double b = bv[0][lane];
     int ib = bi[0][lane];
-    for (int w = 1; w < 32; ++w) {
+    for (int w = 1; w < nw; ++w) {
       if (bv[w][lane] > b || (bv[w][lane] == b && bi[w][lane] < ib)) {
         b = bv[w][lane];
         ib = bi[w][lane];
       }
     }
     double sg = 1.0;
-    if (col < F.n) {
+    if (col < F.n && ib >= 0 && ib < P) {
       const int x = ib % ex, y = (ib / ex) % ey, z = ib / (ex * ey);
       const int pd = ((z + E.lo[2]) * E.dext[1] + (y + E.lo[1])) * E.dext[0] + x + E.lo[0];
       sg = (double)X[E.off + (long long)pd * E.ld + col] < 0.0 ? -1.0 : 1.0;
@@ -501,7 +502,7 @@ __global__ void __launch_bounds__(1024) export_states_kernel(const DevFrag* efr,
   __syncthreads();
   if (col >= F.n) return;
   const T s = (T)sgn[lane];
-  for (int t = warp; t < P; t += 32) {
+  for (int t = warp; t < P; t += nw) {
     const int x = t % ex, y = (t / ex) % ey, z = t / (ex * ey);
     const int pe = ((z + E.lo[2]) * E.dext[1] + (y + E.lo[1])) * E.dext[0] + x + E.lo[0];
     const int pf = ((z + F.lo[2]) * F.dext[1] + (y + F.lo[1])) * F.dext[0] + x + F.lo[0];
@@ -795,10 +796,10 @@ extern "C" ofm_status ofm_fragment_eigs(ofm_ctx* c, const ofm_eig_opts* opts, do
   dim3 eg(nf, (w->mmax + 31) / 32);
   { KTimer kt(c, KC_EXPORT);
   if (fp64)
-    export_states_kernel<double><<<eg, 256, 0, s>>>((const DevFrag*)w->d_efr.p, (const DevFrag*)c->d_frags.p,
+    export_states_kernel<double><<<eg, 1024, 0, s>>>((const DevFrag*)w->d_efr.p, (const DevFrag*)c->d_frags.p,
                                                     (const double*)w->buf[xb].p, (double*)c->states.p);
   else
-    export_states_kernel<float><<<eg, 256, 0, s>>>((const DevFrag*)w->d_efr.p, (const DevFrag*)c->d_frags.p,
+    export_states_kernel<float><<<eg, 1024, 0, s>>>((const DevFrag*)w->d_efr.p, (const DevFrag*)c->d_frags.p,
                                                    (const float*)w->buf[xb].p, (float*)c->states.p); }
   OFM_CUDA(c, cudaGetLastError());
   OFM_CUDA(c, cudaStreamSynchronize(s));
