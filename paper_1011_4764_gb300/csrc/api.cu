@@ -214,19 +214,9 @@ extern "C" ofm_status ofm_build_fragments(ofm_ctx* c, const ofm_grid* grid, cons
   OFM_CUDA(c, cudaMemcpyAsync(c->d_frags.p, c->frags.data(), sizeof(DevFrag) * n_frag,
                               cudaMemcpyHostToDevice, c->stream));
 
-  // H-apply launch table: one thread per 16 bytes of states of a point
-  const int vn = es == 8 ? 2 : 4;
-  c->apply_cta_start.resize(n_frag);
-  long long tot = 0;
-  for (int a = 0; a < n_frag; ++a) {
-    c->apply_cta_start[a] = (int)tot;
-    tot += (c->frags[a].Pd * (c->frags[a].ld / vn) + 255) / 256;
-  }
-  if (tot > 0x7fffffff) return ofm_fail(c, OFM_ERR_INVALID, "H-apply grid too large");
-  c->apply_total_ctas = (int)tot;
-  OFM_TRY(ofm_ensure(c, c->d_apply_start, sizeof(int) * n_frag, "apply table"));
-  OFM_CUDA(c, cudaMemcpyAsync(c->d_apply_start.p, c->apply_cta_start.data(), sizeof(int) * n_frag,
-                              cudaMemcpyHostToDevice, c->stream));
+  // H-apply launch: 2-D grid (chunks of the largest fragment x fragments)
+  if (n_frag > 65535) return ofm_fail(c, OFM_ERR_INVALID, "at most 65535 fragments");
+  c->apply_total_ctas = apply_grid_x(c->frags, es == 8);
 
   // SIMT contraction plan: about 8 work items per SM
   long long chunk = std::max<long long>(256, c->kh / (8 * 152));
@@ -318,8 +308,8 @@ extern "C" ofm_status ofm_get_hphi(ofm_ctx* c, int b, double* out) {
 
 ofm_status ofm_apply_h(ofm_ctx* c) {
   KTimer t(c, KC_APPLY, 1, c->apply_bytes);
-  launch_apply_global((const DevFrag*)c->d_frags.p, (const int*)c->d_apply_start.p, c->nfrag,
-                      c->apply_total_ctas, c->V.p, c->states.p, c->hphi.p, c->grid.n, c->grid.h,
+  launch_apply_global((const DevFrag*)c->d_frags.p, c->nfrag, c->apply_total_ctas, c->V.p,
+                      c->states.p, c->hphi.p, c->grid.n, c->grid.h,
                       c->storage == OFM_STORE_FP64, c->stream);
   return check_launch(c, "apply H");
 }

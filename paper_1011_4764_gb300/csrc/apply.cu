@@ -7,9 +7,13 @@
 // H).  It is evaluated on every point of the dilated box, where it can be
 // non-zero.  Storage is point-major (the n states of one point are adjacent),
 // so one thread owns 16 bytes of states of one point and every neighbour
-// access of a warp is a contiguous run: the kernel is a streaming
-// stencil, bound by HBM bandwidth.
+// access of a warp is a contiguous run: the kernel is a streaming stencil,
+// bound by HBM bandwidth.  The launch grid is 2-D: blockIdx.y is the
+// fragment, blockIdx.x a chunk of its (point, 16-byte column group)
+// elements, each thread handling APPLY_EPT of them.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "ofm_internal.h"
 
@@ -34,146 +38,157 @@ __device__ __forceinline__ double2 add4(double2 a, double2 b) {
 __device__ __forceinline__ float4 zero4(float) { return make_float4(0.f, 0.f, 0.f, 0.f); }
 __device__ __forceinline__ double2 zero4(double) { return make_double2(0.0, 0.0); }
 
-__device__ __forceinline__ int find_frag(const int* start, int nfrag, int cta) {
-  int lo = 0, hi = nfrag - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (start[mid] <= cta) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-
-// Neighbour offset along one dimension in the storage box: +/-1 step of
+// Neighbour index along one dimension in the storage box: +/-1 step of
 // `stride` points; in a full-span dimension it wraps, otherwise a step out
 // of the storage box reads zero (returns -1).
-__device__ __forceinline__ long long nb_index(long long p, int c, int ext, int full, int dir,
-                                              long long stride) {
+__device__ __forceinline__ int nb_index(int p, int c, int ext, int full, int dir, int stride) {
   int c2 = c + dir;
   if (c2 < 0 || c2 >= ext) {
     if (!full) return -1;
     c2 = (c2 + ext) % ext;
   }
-  return p + (long long)(c2 - c) * stride;
+  return p + (c2 - c) * stride;
 }
 
+// Stencil sum over the six neighbours of point p (coordinates x, y, z) for
+// the column group q.
+template <typename T>
+__device__ __forceinline__ typename Vec16<T>::type neighbour_sum(
+    const typename Vec16<T>::type* __restrict__ S, const DevFrag& F, int p, int x, int y, int z,
+    int q, int qpp) {
+  using V16 = typename Vec16<T>::type;
+  const int ex = F.dext[0], ey = F.dext[1], ez = F.dext[2];
+  V16 sum = zero4(T());
+  int nb;
+  if ((nb = nb_index(p, x, ex, F.full[0], +1, 1)) >= 0) sum = add4(sum, S[nb * qpp + q]);
+  if ((nb = nb_index(p, x, ex, F.full[0], -1, 1)) >= 0) sum = add4(sum, S[nb * qpp + q]);
+  if ((nb = nb_index(p, y, ey, F.full[1], +1, ex)) >= 0) sum = add4(sum, S[nb * qpp + q]);
+  if ((nb = nb_index(p, y, ey, F.full[1], -1, ex)) >= 0) sum = add4(sum, S[nb * qpp + q]);
+  if ((nb = nb_index(p, z, ez, F.full[2], +1, ex * ey)) >= 0) sum = add4(sum, S[nb * qpp + q]);
+  if ((nb = nb_index(p, z, ez, F.full[2], -1, ex * ey)) >= 0) sum = add4(sum, S[nb * qpp + q]);
+  return sum;
+}
+
+constexpr int APPLY_EPT = 4;   // 16-byte elements per thread
+
+// a1: H phi on every point of the dilated boxes.
 template <typename T>
 __global__ void __launch_bounds__(256) apply_global_kernel(const DevFrag* __restrict__ fr,
-                                                           const int* __restrict__ cta_start,
-                                                           int nfrag, const T* __restrict__ V,
+                                                           const T* __restrict__ V,
                                                            const T* __restrict__ states,
                                                            T* __restrict__ hphi, int gx, int gy,
                                                            int gz, T c0, T c1) {
   using V16 = typename Vec16<T>::type;
   constexpr int VN = Vec16<T>::n;
-  const int f = find_frag(cta_start, nfrag, blockIdx.x);
-  const DevFrag F = fr[f];
-  const int q_per_pt = F.ld / VN;
-  // 32-bit index math: the planner keeps Pd * ld below 2^31 per fragment
-  const int e = (int)(blockIdx.x - cta_start[f]) * (int)blockDim.x + (int)threadIdx.x;
-  if (e >= (int)F.Pd * q_per_pt) return;
-  const int p = e / q_per_pt;
-  const int q = e - p * q_per_pt;
-  const int ex = F.dext[0], ey = F.dext[1], ez = F.dext[2];
-  const int x = p % ex;
-  const int yz = p / ex;
-  const int y = yz % ey;
-  const int z = yz / ey;
-  const int X = (F.doff[0] + x) % gx, Y = (F.doff[1] + y) % gy, Z = (F.doff[2] + z) % gz;
-  const T v = V[((long long)Z * gy + Y) * gx + X];
+  __shared__ DevFrag Fs;
+  if (threadIdx.x == 0) Fs = fr[blockIdx.y];
+  __syncthreads();
+  const DevFrag& F = Fs;
+  const int qpp = F.ld / VN;
+  const int total = (int)F.Pd * qpp;   // < 2^31: checked by the planner
   const V16* S = reinterpret_cast<const V16*>(states + F.off);
-  const long long sx = 1, sy = ex, sz = (long long)ex * ey;
-  V16 ctr = S[p * q_per_pt + q];
-  V16 sum = zero4(T());
-  long long nb;
-  if ((nb = nb_index(p, x, ex, F.full[0], +1, sx)) >= 0) sum = add4(sum, S[nb * q_per_pt + q]);
-  if ((nb = nb_index(p, x, ex, F.full[0], -1, sx)) >= 0) sum = add4(sum, S[nb * q_per_pt + q]);
-  if ((nb = nb_index(p, y, ey, F.full[1], +1, sy)) >= 0) sum = add4(sum, S[nb * q_per_pt + q]);
-  if ((nb = nb_index(p, y, ey, F.full[1], -1, sy)) >= 0) sum = add4(sum, S[nb * q_per_pt + q]);
-  if ((nb = nb_index(p, z, ez, F.full[2], +1, sz)) >= 0) sum = add4(sum, S[nb * q_per_pt + q]);
-  if ((nb = nb_index(p, z, ez, F.full[2], -1, sz)) >= 0) sum = add4(sum, S[nb * q_per_pt + q]);
-  // (c0 + v) * ctr - c1 * sum
-  V16 out = fma4(c0 + v, ctr, zero4(T()));
-  out = fma4(-c1, sum, out);
-  reinterpret_cast<V16*>(hphi + F.off)[p * q_per_pt + q] = out;
+  V16* O = reinterpret_cast<V16*>(hphi + F.off);
+  const int ex = F.dext[0], ey = F.dext[1];
+#pragma unroll
+  for (int u = 0; u < APPLY_EPT; ++u) {
+    const int e = (blockIdx.x * APPLY_EPT + u) * (int)blockDim.x + (int)threadIdx.x;
+    if (e >= total) break;
+    const int p = e / qpp, q = e - p * qpp;
+    const int x = p % ex, yz = p / ex, y = yz % ey, z = yz / ey;
+    const int X = (F.doff[0] + x) % gx, Y = (F.doff[1] + y) % gy, Z = (F.doff[2] + z) % gz;
+    const T v = V[((long long)Z * gy + Y) * gx + X];
+    const V16 ctr = S[e];
+    const V16 sum = neighbour_sum<T>(S, F, p, x, y, z, q, qpp);
+    V16 out = fma4(c0 + v, ctr, zero4(T()));
+    out = fma4(-c1, sum, out);
+    O[e] = out;
+  }
 }
 
-void launch_apply_global(const DevFrag* d_fr, const int* d_cta_start, int nfrag, int total_ctas,
-                         const void* V, const void* states, void* hphi, const int gn[3], double h,
-                         bool fp64, cudaStream_t s) {
+void launch_apply_global(const DevFrag* d_fr, int nfrag, int grid_x, const void* V,
+                         const void* states, void* hphi, const int gn[3], double h, bool fp64,
+                         cudaStream_t s) {
   const double c0 = 3.0 / (h * h), c1 = 0.5 / (h * h);
+  dim3 g(grid_x, nfrag);
   if (fp64)
-    apply_global_kernel<double><<<total_ctas, 256, 0, s>>>(
-        d_fr, d_cta_start, nfrag, (const double*)V, (const double*)states, (double*)hphi, gn[0],
-        gn[1], gn[2], c0, c1);
+    apply_global_kernel<double><<<g, 256, 0, s>>>(d_fr, (const double*)V, (const double*)states,
+                                                  (double*)hphi, gn[0], gn[1], gn[2], c0, c1);
   else
-    apply_global_kernel<float><<<total_ctas, 256, 0, s>>>(
-        d_fr, d_cta_start, nfrag, (const float*)V, (const float*)states, (float*)hphi, gn[0],
-        gn[1], gn[2], (float)c0, (float)c1);
+    apply_global_kernel<float><<<g, 256, 0, s>>>(d_fr, (const float*)V, (const float*)states,
+                                                 (float*)hphi, gn[0], gn[1], gn[2], (float)c0,
+                                                 (float)c1);
 }
 
-// Fragment-mode apply for the eigensolver: the fragment Hamiltonian is the
-// principal submatrix of H on the box, so only interior points are written
-// (the zero halo stays zero) and the stencil reads zeros beyond the box.
-// One fused step of the scaled Chebyshev three-term recurrence:
+// a0, fragment mode: the fragment Hamiltonian is the principal submatrix of
+// H on the box, so only interior points are written (the zero halo stays
+// zero) and the stencil reads zeros beyond the box.  One fused step of the
+// scaled Chebyshev three-term recurrence:
 //     out = alpha_f * (H_f in - c_f in) + beta_f * prev
 // with per-fragment coefficients coef[f] = (alpha, beta, c); prev may be
 // null when beta is zero.
 template <typename T>
 __global__ void __launch_bounds__(256) apply_filter_kernel(
-    const DevFrag* __restrict__ fr, const int* __restrict__ cta_start, int nfrag,
-    const T* __restrict__ V, const T* __restrict__ in, const T* __restrict__ prev,
-    T* __restrict__ out, const double* __restrict__ coef, int gx, int gy, int gz, T c0, T c1) {
+    const DevFrag* __restrict__ fr, const T* __restrict__ V, const T* __restrict__ in,
+    const T* __restrict__ prev, T* __restrict__ out, const double* __restrict__ coef, int gx,
+    int gy, int gz, T c0, T c1) {
   using V16 = typename Vec16<T>::type;
   constexpr int VN = Vec16<T>::n;
-  const int f = find_frag(cta_start, nfrag, blockIdx.x);
-  const DevFrag F = fr[f];
-  const int q_per_pt = F.ld / VN;
-  // 32-bit index math: the planner keeps Pd * ld below 2^31 per fragment
-  const int e = (int)(blockIdx.x - cta_start[f]) * (int)blockDim.x + (int)threadIdx.x;
-  if (e >= (int)F.Pd * q_per_pt) return;
-  const int p = e / q_per_pt;
-  const int q = e - p * q_per_pt;
-  const int ex = F.dext[0], ey = F.dext[1], ez = F.dext[2];
-  const int x = p % ex;
-  const int yz = p / ex;
-  const int y = yz % ey;
-  const int z = yz / ey;
-  if (x < F.lo[0] || x >= F.lo[0] + F.ext[0] || y < F.lo[1] || y >= F.lo[1] + F.ext[1] ||
-      z < F.lo[2] || z >= F.lo[2] + F.ext[2])
-    return;
-  const int X = (F.doff[0] + x) % gx, Y = (F.doff[1] + y) % gy, Z = (F.doff[2] + z) % gz;
-  const T alpha = (T)coef[3 * f], beta = (T)coef[3 * f + 1], shift = (T)coef[3 * f + 2];
-  const T v = V[((long long)Z * gy + Y) * gx + X];
+  __shared__ DevFrag Fs;
+  __shared__ T cf[3];
+  if (threadIdx.x == 0) Fs = fr[blockIdx.y];
+  if (threadIdx.x < 3) cf[threadIdx.x] = (T)coef[3 * blockIdx.y + threadIdx.x];
+  __syncthreads();
+  const DevFrag& F = Fs;
+  const int qpp = F.ld / VN;
+  const int total = (int)F.Pd * qpp;
   const V16* S = reinterpret_cast<const V16*>(in + F.off);
-  const long long sx = 1, sy = ex, sz = (long long)ex * ey;
-  V16 ctr = S[p * q_per_pt + q];
-  V16 sum = zero4(T());
-  long long nb;
-  if ((nb = nb_index(p, x, ex, F.full[0], +1, sx)) >= 0) sum = add4(sum, S[nb * q_per_pt + q]);
-  if ((nb = nb_index(p, x, ex, F.full[0], -1, sx)) >= 0) sum = add4(sum, S[nb * q_per_pt + q]);
-  if ((nb = nb_index(p, y, ey, F.full[1], +1, sy)) >= 0) sum = add4(sum, S[nb * q_per_pt + q]);
-  if ((nb = nb_index(p, y, ey, F.full[1], -1, sy)) >= 0) sum = add4(sum, S[nb * q_per_pt + q]);
-  if ((nb = nb_index(p, z, ez, F.full[2], +1, sz)) >= 0) sum = add4(sum, S[nb * q_per_pt + q]);
-  if ((nb = nb_index(p, z, ez, F.full[2], -1, sz)) >= 0) sum = add4(sum, S[nb * q_per_pt + q]);
-  V16 hy = fma4(c0 + v - shift, ctr, zero4(T()));
-  hy = fma4(-c1, sum, hy);
-  V16 o = fma4(alpha, hy, zero4(T()));
-  if (prev != nullptr) o = fma4(beta, reinterpret_cast<const V16*>(prev + F.off)[p * q_per_pt + q], o);
-  reinterpret_cast<V16*>(out + F.off)[p * q_per_pt + q] = o;
+  const V16* Pv = prev ? reinterpret_cast<const V16*>(prev + F.off) : nullptr;
+  V16* O = reinterpret_cast<V16*>(out + F.off);
+  const T alpha = cf[0], beta = cf[1], shift = cf[2];
+  const int ex = F.dext[0], ey = F.dext[1];
+#pragma unroll
+  for (int u = 0; u < APPLY_EPT; ++u) {
+    const int e = (blockIdx.x * APPLY_EPT + u) * (int)blockDim.x + (int)threadIdx.x;
+    if (e >= total) break;
+    const int p = e / qpp, q = e - p * qpp;
+    const int x = p % ex, yz = p / ex, y = yz % ey, z = yz / ey;
+    if (x < F.lo[0] || x >= F.lo[0] + F.ext[0] || y < F.lo[1] || y >= F.lo[1] + F.ext[1] ||
+        z < F.lo[2] || z >= F.lo[2] + F.ext[2])
+      continue;
+    const int X = (F.doff[0] + x) % gx, Y = (F.doff[1] + y) % gy, Z = (F.doff[2] + z) % gz;
+    const T v = V[((long long)Z * gy + Y) * gx + X];
+    const V16 ctr = S[e];
+    const V16 sum = neighbour_sum<T>(S, F, p, x, y, z, q, qpp);
+    V16 hy = fma4(c0 + v - shift, ctr, zero4(T()));
+    hy = fma4(-c1, sum, hy);
+    V16 o = fma4(alpha, hy, zero4(T()));
+    if (Pv != nullptr) o = fma4(beta, Pv[e], o);
+    O[e] = o;
+  }
 }
 
-void launch_apply_filter(const DevFrag* d_fr, const int* d_cta_start, int nfrag, int total_ctas,
-                         const void* V, const void* in, const void* prev, void* out,
-                         const double* coef, const int gn[3], double h, bool fp64, cudaStream_t s) {
+void launch_apply_filter(const DevFrag* d_fr, int nfrag, int grid_x, const void* V, const void* in,
+                         const void* prev, void* out, const double* coef, const int gn[3],
+                         double h, bool fp64, cudaStream_t s) {
   const double c0 = 3.0 / (h * h), c1 = 0.5 / (h * h);
+  dim3 g(grid_x, nfrag);
   if (fp64)
-    apply_filter_kernel<double><<<total_ctas, 256, 0, s>>>(
-        d_fr, d_cta_start, nfrag, (const double*)V, (const double*)in, (const double*)prev,
-        (double*)out, coef, gn[0], gn[1], gn[2], c0, c1);
+    apply_filter_kernel<double><<<g, 256, 0, s>>>(d_fr, (const double*)V, (const double*)in,
+                                                  (const double*)prev, (double*)out, coef, gn[0],
+                                                  gn[1], gn[2], c0, c1);
   else
-    apply_filter_kernel<float><<<total_ctas, 256, 0, s>>>(
-        d_fr, d_cta_start, nfrag, (const float*)V, (const float*)in, (const float*)prev,
-        (float*)out, coef, gn[0], gn[1], gn[2], (float)c0, (float)c1);
+    apply_filter_kernel<float><<<g, 256, 0, s>>>(d_fr, (const float*)V, (const float*)in,
+                                                 (const float*)prev, (float*)out, coef, gn[0],
+                                                 gn[1], gn[2], (float)c0, (float)c1);
+}
+
+// Grid width for the 2-D stencil launches: enough chunks for the largest
+// fragment.
+int apply_grid_x(const std::vector<DevFrag>& fr, bool fp64) {
+  const int vn = fp64 ? 2 : 4;
+  long long mx = 1;
+  for (const DevFrag& f : fr) mx = std::max<long long>(mx, f.Pd * (f.ld / vn));
+  return (int)((mx + 256LL * APPLY_EPT - 1) / (256LL * APPLY_EPT));
 }
 
 // ------------------------------------------------------------ conversions --

@@ -54,6 +54,7 @@ struct EigWork {
   double vmax = 0.0;
   size_t rr_smem = 0, rot_smem = 0;   // dynamic shared memory of the two kernels
   int rot_blocks = 1;
+  int fgrid = 1;                      // grid width of the filter launches
   bool ready = false;
   // algorithmic traffic / work per launch: a filter step streams the block
   // in, the previous block (three-term steps) and the block out, plus V
@@ -167,7 +168,9 @@ __device__ void cta_jacobi(double* A, double* V, int n, int lda, int* perm, doub
         so += red[2 * w];
         st += red[2 * w + 1];
       }
-      red[64] = (so <= 1e-30 * st || so == 0.0) ? 1.0 : 0.0;
+      red[64] = (so <= 1e-30 * st || so == 0.0 || (sweep > 0 && red[65] == 0.0)) ? 1.0 : 0.0;
+      red[65] = 0.0;   // rotations applied in the coming sweep
+      red[66] = 1e-17 * sqrt(st);   // absolute floor: rounding level of the whole matrix
     }
     __syncthreads();
     const bool done = red[64] != 0.0;
@@ -179,7 +182,10 @@ __device__ void cta_jacobi(double* A, double* V, int n, int lda, int* perm, doub
         double c = 1.0, s = 0.0;
         if (p < n && q < n) {
           const double apq = A[p * lda + q];
-          if (apq != 0.0) {
+          // an element below rounding relative to its diagonal pair is left
+          // alone; a sweep that rotates nothing ends the iteration
+          if (fabs(apq) > fmax(1e-16 * sqrt(fabs(A[p * lda + p] * A[q * lda + q])), red[66])) {
+            red[65] = 1.0;
             const double app = A[p * lda + p], aqq = A[q * lda + q];
             const double th = (aqq - app) / (2.0 * apq);
             const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
@@ -558,7 +564,8 @@ static ofm_status eig_setup(ofm_ctx* c, int guard_opt) {
     ctas += (E.Pd * (E.ld / vn) + 255) / 256;
   }
   w->total_ctas = (int)ctas;
-  w->filter_b2 = w->filter_b3 = w->gram_bytes = w->gram_flops = w->rot_bytes = w->rot_flops = 0;
+  w->fgrid = apply_grid_x(w->efr, fp64);
+  w->filter_b2 =w->filter_b3 = w->gram_bytes = w->gram_flops = w->rot_bytes = w->rot_flops = 0;
   for (const DevFrag& E : w->efr) {
     const double P = (double)E.ext[0] * E.ext[1] * E.ext[2];
     w->filter_b2 += P * (2.0 * E.n + 1.0) * es;
@@ -681,9 +688,9 @@ static ofm_status eig_rr(ofm_ctx* c, int y, int hy, int xo, int hxo, unsigned lo
 static void apply_block(ofm_ctx* c, int in, int prev, int out, const double* coef) {
   EigWork* w = c->eig;
   KTimer kt(c, KC_FILTER, 1, prev >= 0 ? w->filter_b3 : w->filter_b2);
-  launch_apply_filter((const DevFrag*)w->d_efr.p, (const int*)w->d_cta.p, c->nfrag, w->total_ctas,
-                      c->V.p, w->buf[in].p, prev >= 0 ? w->buf[prev].p : nullptr, w->buf[out].p,
-                      coef, c->grid.n, c->grid.h, c->storage == OFM_STORE_FP64, c->stream);
+  launch_apply_filter((const DevFrag*)w->d_efr.p, c->nfrag, w->fgrid, c->V.p, w->buf[in].p,
+                      prev >= 0 ? w->buf[prev].p : nullptr, w->buf[out].p, coef, c->grid.n,
+                      c->grid.h, c->storage == OFM_STORE_FP64, c->stream);
 }
 
 static int other(int a, int b, int c2 = -1) {

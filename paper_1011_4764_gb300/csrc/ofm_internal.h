@@ -89,16 +89,17 @@ void make_items_simt(const std::vector<DevFrag>& fr, const std::vector<HostPair>
 
 // ------------------------------------------------------------ kernels ------
 
-void launch_apply_global(const DevFrag* d_fr, const int* d_cta_start, int nfrag, int total_ctas,
-                         const void* V, const void* states, void* hphi, const int gn[3], double h,
-                         bool fp64, cudaStream_t s);
+void launch_apply_global(const DevFrag* d_fr, int nfrag, int grid_x, const void* V,
+                         const void* states, void* hphi, const int gn[3], double h, bool fp64,
+                         cudaStream_t s);
+int apply_grid_x(const std::vector<DevFrag>& fr, bool fp64);
 void launch_import_states(const DevFrag* d_fr, int a, const DevFrag& fa, const double* src,
                           void* states, bool fp64, cudaStream_t s);
 void launch_export_states(const DevFrag& fa, const void* states, double* dst, bool fp64,
                           bool dilated_hphi, cudaStream_t s);
-void launch_apply_filter(const DevFrag* d_fr, const int* d_cta_start, int nfrag, int total_ctas,
-                         const void* V, const void* in, const void* prev, void* out,
-                         const double* coef, const int gn[3], double h, bool fp64, cudaStream_t s);
+void launch_apply_filter(const DevFrag* d_fr, int nfrag, int grid_x, const void* V, const void* in,
+                         const void* prev, void* out, const double* coef, const int gn[3],
+                         double h, bool fp64, cudaStream_t s);
 void launch_convert_V(const double* src, void* dst, long long n, bool fp64, cudaStream_t s);
 void launch_contract_simt(int prec, bool store_fp64, const DevFrag* d_fr, const DevPair* d_pairs,
                           const Piece* d_pieces, const WorkItem* d_items, int nitems,
@@ -211,7 +212,7 @@ ofm_status ofm_window_vectors(ofm_ctx* c, int m, double* C_out);
 ofm_status ofm_tridiag_persistent(ofm_ctx* c, double* A, int n, double* d, double* e, double* tau,
                                   double* pg);
 void launch_count_below(const double* d, const double* e, int n, double x, int* out, cudaStream_t s);
-void launch_multisection(const double* d, const double* e, int n, int i_lo, int m, double* out,
+bool launch_multisection(const double* d, const double* e, int n, int i_lo, int m, double* out,
                          cudaStream_t s);
 
 // Counts the launches of one kernel class and, while profiling is on,

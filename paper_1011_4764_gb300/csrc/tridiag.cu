@@ -128,7 +128,16 @@ __global__ void __launch_bounds__(512) tridiag_persistent_kernel(double* A, int 
       const int i = k + 1 + r;
       const double* row = A + (long long)i * n;
       double acc = 0.0;
-      for (int j = k + 1 + lane; j < n; j += 32) acc += __ldcg(&row[j]) * v[j];
+      int j = k + 1 + lane;
+      // eight independent loads in flight per lane
+      for (; j + 7 * 32 < n; j += 8 * 32) {
+        double a[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) a[u] = __ldcg(&row[j + 32 * u]);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc += a[u] * v[j + 32 * u];
+      }
+      for (; j < n; j += 32) acc += __ldcg(&row[j]) * v[j];
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
       if (lane == 0) pg[i] = t * acc;
     }
@@ -142,8 +151,18 @@ __global__ void __launch_bounds__(512) tridiag_persistent_kernel(double* A, int 
       const int i = k + 1 + r;
       const double vi = v[i], wi = pw[i] - K * vi;
       double* row = A + (long long)i * n;
-      for (int j = k + 1 + lane; j < n; j += 32)
-        row[j] = __ldcg(&row[j]) - (vi * (pw[j] - K * v[j]) + wi * v[j]);
+      int j = k + 1 + lane;
+      for (; j + 7 * 32 < n; j += 8 * 32) {
+        double a[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) a[u] = __ldcg(&row[j + 32 * u]);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int jj = j + 32 * u;
+          row[jj] = a[u] - (vi * (pw[jj] - K * v[jj]) + wi * v[jj]);
+        }
+      }
+      for (; j < n; j += 32) row[j] = __ldcg(&row[j]) - (vi * (pw[j] - K * v[j]) + wi * v[j]);
     }
     if (!grid_sync(bar, nb)) return;
   }
@@ -160,6 +179,8 @@ __global__ void __launch_bounds__(512) tridiag_persistent_kernel(double* A, int 
 // the leading principal minors p_i of T - x I (p_0 = 1), a zero minor
 // counted as a change; both running minors are rescaled by a power of two
 // when the newest leaves [2^-400, 2^400].
+// SQ: the second array already holds the squared off-diagonals.
+template <bool SQ>
 __device__ int sturm_count(const double* __restrict__ d, const double* __restrict__ e, int n,
                            double x) {
   double p0 = 1.0, p1 = d[0] - x;
@@ -167,7 +188,7 @@ __device__ int sturm_count(const double* __restrict__ d, const double* __restric
   int c = p1 < 0.0 ? 1 : 0;
   for (int i = 1; i < n; ++i) {
     const double ei = e[i - 1];
-    double p2 = fma(d[i] - x, p1, -(ei * ei) * p0);
+    double p2 = fma(d[i] - x, p1, -(SQ ? ei : ei * ei) * p0);
     if (p2 == 0.0) p2 = (p1 < 0.0) ? DBL_MIN : -DBL_MIN;
     c += ((p2 < 0.0) != (p1 < 0.0)) ? 1 : 0;
     const double a = fabs(p2);
@@ -183,13 +204,22 @@ __device__ int sturm_count(const double* __restrict__ d, const double* __restric
 }
 
 __global__ void count_below_kernel(const double* d, const double* e, int n, double x, int* out) {
-  *out = sturm_count(d, e, n, x);
+  *out = sturm_count<false>(d, e, n, x);
 }
 
 // One warp per eigenvalue index i_lo + warp; out[warp] = the eigenvalue.
+// d and the squared off-diagonals are staged in shared memory (2n doubles).
 __global__ void __launch_bounds__(256) multisection_kernel(const double* __restrict__ d,
                                                            const double* __restrict__ e, int n,
                                                            int i_lo, int m, double* out) {
+  extern __shared__ double ms_smem[];
+  double* ds = ms_smem;
+  double* e2s = ms_smem + n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    ds[i] = d[i];
+    e2s[i] = (i < n - 1) ? e[i] * e[i] : 0.0;
+  }
+  __syncthreads();
   const int lane = threadIdx.x & 31;
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (w >= m) return;
@@ -211,7 +241,7 @@ __global__ void __launch_bounds__(256) multisection_kernel(const double* __restr
   for (int it = 0; it < 64; ++it) {
     if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + 4.0 * DBL_MIN) break;
     const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
-    const int cnt = sturm_count(d, e, n, x);
+    const int cnt = sturm_count<true>(ds, e2s, n, x);
     const unsigned mask = __ballot_sync(0xffffffffu, cnt > idx);
     const double xprev = __shfl_up_sync(0xffffffffu, x, 1);
     if (mask == 0) {
@@ -269,9 +299,23 @@ void launch_count_below(const double* d, const double* e, int n, double x, int* 
   count_below_kernel<<<1, 1, 0, s>>>(d, e, n, x, out);
 }
 
-void launch_multisection(const double* d, const double* e, int n, int i_lo, int m, double* out,
+// Returns false when the tridiagonal is too long to stage in shared memory
+// (the caller then bisects from global memory).
+bool launch_multisection(const double* d, const double* e, int n, int i_lo, int m, double* out,
                          cudaStream_t s) {
+  const size_t smem = 2 * (size_t)n * sizeof(double);
+  if (smem > 200 * 1024) return false;
+  static bool attr_set = false;
+  if (!attr_set) {
+    if (cudaFuncSetAttribute(multisection_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    attr_set = true;
+  }
   const int warps_per_block = 8;
-  multisection_kernel<<<(m + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, s>>>(
-      d, e, n, i_lo, m, out);
+  multisection_kernel<<<(m + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, smem,
+                        s>>>(d, e, n, i_lo, m, out);
+  return true;
 }

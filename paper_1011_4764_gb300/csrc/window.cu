@@ -459,8 +459,11 @@ ofm_status ofm_window_bisect(ofm_ctx* c, int i_lo, int i_hi, double* E_out) {
   const int m = i_hi - i_lo;
   double* out = (double*)c->w_tmp.p;  // 2n doubles, m <= n
   KTimer kt(c, KC_BISECT);
-  launch_multisection((const double*)c->w_d.p, (const double*)c->w_e.p, c->dense_n, i_lo, m, out,
-                      c->stream);
+  if (!launch_multisection((const double*)c->w_d.p, (const double*)c->w_e.p, c->dense_n, i_lo, m,
+                           out, c->stream))
+    bisect_kernel<<<(m + 127) / 128, 128, 0, c->stream>>>((const double*)c->w_d.p,
+                                                          (const double*)c->w_e.p, c->dense_n,
+                                                          i_lo, m, out);
   OFM_CUDA(c, cudaGetLastError());
   OFM_CUDA(c, cudaMemcpyAsync(E_out, out, sizeof(double) * m, cudaMemcpyDeviceToHost, c->stream));
   return sync_ctx(c, "bisection");
