@@ -58,14 +58,21 @@ __device__ __forceinline__ typename Vec16<T>::type neighbour_sum(
     int q, int qpp) {
   using V16 = typename Vec16<T>::type;
   const int ex = F.dext[0], ey = F.dext[1], ez = F.dext[2];
+  // branch-free: a neighbour outside the storage box reads the point itself
+  // with weight 0, so all six loads can be in flight at once
+  int nb[6];
+  nb[0] = nb_index(p, x, ex, F.full[0], +1, 1);
+  nb[1] = nb_index(p, x, ex, F.full[0], -1, 1);
+  nb[2] = nb_index(p, y, ey, F.full[1], +1, ex);
+  nb[3] = nb_index(p, y, ey, F.full[1], -1, ex);
+  nb[4] = nb_index(p, z, ez, F.full[2], +1, ex * ey);
+  nb[5] = nb_index(p, z, ez, F.full[2], -1, ex * ey);
+  V16 v[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) v[i] = S[(nb[i] >= 0 ? nb[i] : p) * qpp + q];
   V16 sum = zero4(T());
-  int nb;
-  if ((nb = nb_index(p, x, ex, F.full[0], +1, 1)) >= 0) sum = add4(sum, S[nb * qpp + q]);
-  if ((nb = nb_index(p, x, ex, F.full[0], -1, 1)) >= 0) sum = add4(sum, S[nb * qpp + q]);
-  if ((nb = nb_index(p, y, ey, F.full[1], +1, ex)) >= 0) sum = add4(sum, S[nb * qpp + q]);
-  if ((nb = nb_index(p, y, ey, F.full[1], -1, ex)) >= 0) sum = add4(sum, S[nb * qpp + q]);
-  if ((nb = nb_index(p, z, ez, F.full[2], +1, ex * ey)) >= 0) sum = add4(sum, S[nb * qpp + q]);
-  if ((nb = nb_index(p, z, ez, F.full[2], -1, ex * ey)) >= 0) sum = add4(sum, S[nb * qpp + q]);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) sum = fma4(nb[i] >= 0 ? T(1) : T(0), v[i], sum);
   return sum;
 }
 

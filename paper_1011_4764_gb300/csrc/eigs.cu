@@ -168,9 +168,12 @@ __device__ void cta_jacobi(double* A, double* V, int n, int lda, int* perm, doub
         so += red[2 * w];
         st += red[2 * w + 1];
       }
-      red[64] = (so <= 1e-30 * st || so == 0.0 || (sweep > 0 && red[65] == 0.0)) ? 1.0 : 0.0;
+      // converged when the off-diagonal mass is at the rounding level of an
+      // n x n matrix (n eps relative in norm), or a sweep rotated nothing
+      const double tol = 4.0 * n * 1.1e-16;
+      red[64] = (so <= tol * tol * st || so == 0.0 || (sweep > 0 && red[65] == 0.0)) ? 1.0 : 0.0;
       red[65] = 0.0;   // rotations applied in the coming sweep
-      red[66] = 1e-17 * sqrt(st);   // absolute floor: rounding level of the whole matrix
+      red[66] = 2.2e-16 * sqrt(st / n);   // absolute floor: rounding level of an element
     }
     __syncthreads();
     const bool done = red[64] != 0.0;
@@ -184,7 +187,7 @@ __device__ void cta_jacobi(double* A, double* V, int n, int lda, int* perm, doub
           const double apq = A[p * lda + q];
           // an element below rounding relative to its diagonal pair is left
           // alone; a sweep that rotates nothing ends the iteration
-          if (fabs(apq) > fmax(1e-16 * sqrt(fabs(A[p * lda + p] * A[q * lda + q])), red[66])) {
+          if (fabs(apq) > fmax(2.2e-16 * sqrt(fabs(A[p * lda + p] * A[q * lda + q])), red[66])) {
             red[65] = 1.0;
             const double app = A[p * lda + p], aqq = A[q * lda + q];
             const double th = (aqq - app) / (2.0 * apq);

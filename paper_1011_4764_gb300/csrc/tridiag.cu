@@ -279,9 +279,9 @@ ofm_status ofm_tridiag_persistent(ofm_ctx* c, double* A, int n, double* d, doubl
   int per_sm = 0;
   OFM_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tridiag_persistent_kernel, 512, smem));
   if (per_sm < 1) return OFM_ERR_INVALID;
-  // enough warps for one row each at the first column, never more than co-resident
-  int nb = std::min(sms * per_sm, std::max(1, (n + 15) / 16));
-  nb = std::min(nb, 128);
+  // one CTA per SM: the FP64 pipes of every SM share the rank-2 updates
+  // (FP64 issue rate per SM is low on this part), never more than co-resident
+  const int nb = std::max(1, std::min(sms * per_sm, sms));
   OFM_TRY(ofm_ensure(c, c->w_bar, sizeof(GridBar), "grid barrier"));
   OFM_CUDA(c, cudaMemsetAsync(c->w_bar.p, 0, sizeof(GridBar), c->stream));
   GridBar* bar = (GridBar*)c->w_bar.p;
@@ -314,7 +314,8 @@ bool launch_multisection(const double* d, const double* e, int n, int i_lo, int 
     }
     attr_set = true;
   }
-  const int warps_per_block = 8;
+  // two warps per CTA so that the wanted eigenvalues spread over every SM
+  const int warps_per_block = 2;
   multisection_kernel<<<(m + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, smem,
                         s>>>(d, e, n, i_lo, m, out);
   return true;
