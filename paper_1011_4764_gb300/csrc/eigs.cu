@@ -131,25 +131,38 @@ __global__ void init_random_kernel(const DevFrag* fr, const int* cta_start, int 
   }
 }
 
-// ---- per-fragment dense FP64 Rayleigh-Ritz (one CTA per fragment) --------
+// ---- per-fragment dense Rayleigh-Ritz (one CTA per fragment) -------------
+//
+// T is the arithmetic of the small dense problems: FP64 for FP64 storage;
+// FP32 for FP32 storage, where the states themselves carry FP32 rounding
+// (the FP64 pipe of one SM issues about 2 FMA per clock on this part, so
+// FP64 here would make the eigensolver bound by a handful of SMs).
+
+template <typename T> struct Eps;
+template <> struct Eps<float> { static constexpr double v = 6.0e-8; };
+template <> struct Eps<double> { static constexpr double v = 1.1e-16; };
 
 // Cyclic parallel Jacobi on the symmetric n x n matrix A (leading dim lda),
 // accumulating the rotations into V (which must hold the identity or a
 // start basis).  Round-robin pairing: n_even/2 disjoint rotations per round.
-// A and V live in shared memory when they fit, so a round costs three
-// CTA barriers and no global-memory round trips.
-__device__ void cta_jacobi(double* A, double* V, int n, int lda, int* perm, double* cs,
-                           double* red) {
+// A and V live in shared memory when they fit, so a round costs three CTA
+// barriers and no global-memory round trips.  Stops when the off-diagonal
+// mass is at the rounding level of an n x n matrix or a sweep rotated
+// nothing (elements below rounding relative to their diagonal pair are
+// left alone).
+template <typename T>
+__device__ void cta_jacobi(T* A, T* V, int n, int lda, int* perm, T* cs, double* red) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int ne = n + (n & 1);
   const int half = ne / 2;
+  const double eps = Eps<T>::v;
   for (int i = tid; i < ne; i += nt) perm[i] = i;
   __syncthreads();
   for (int sweep = 0; sweep < 40; ++sweep) {
     double off = 0.0, tot = 0.0;
     for (int e = tid; e < n * n; e += nt) {
       const int i = e / n, j = e - (e / n) * n;
-      const double a = A[i * lda + j];
+      const double a = (double)A[i * lda + j];
       tot += a * a;
       if (i != j) off += a * a;
     }
@@ -168,12 +181,10 @@ __device__ void cta_jacobi(double* A, double* V, int n, int lda, int* perm, doub
         so += red[2 * w];
         st += red[2 * w + 1];
       }
-      // converged when the off-diagonal mass is at the rounding level of an
-      // n x n matrix (n eps relative in norm), or a sweep rotated nothing
-      const double tol = 4.0 * n * 1.1e-16;
+      const double tol = 4.0 * n * eps;
       red[64] = (so <= tol * tol * st || so == 0.0 || (sweep > 0 && red[65] == 0.0)) ? 1.0 : 0.0;
-      red[65] = 0.0;   // rotations applied in the coming sweep
-      red[66] = 2.2e-16 * sqrt(st / n);   // absolute floor: rounding level of an element
+      red[65] = 0.0;                      // rotations applied in the coming sweep
+      red[66] = 2.0 * eps * sqrt(st / n);  // absolute floor: rounding level of an element
     }
     __syncthreads();
     const bool done = red[64] != 0.0;
@@ -182,17 +193,15 @@ __device__ void cta_jacobi(double* A, double* V, int n, int lda, int* perm, doub
     for (int r = 0; r < ne - 1; ++r) {
       for (int k = tid; k < half; k += nt) {
         const int p = perm[k], q = perm[ne - 1 - k];
-        double c = 1.0, s = 0.0;
+        T c = 1, s = 0;
         if (p < n && q < n) {
-          const double apq = A[p * lda + q];
-          // an element below rounding relative to its diagonal pair is left
-          // alone; a sweep that rotates nothing ends the iteration
-          if (fabs(apq) > fmax(2.2e-16 * sqrt(fabs(A[p * lda + p] * A[q * lda + q])), red[66])) {
+          const T apq = A[p * lda + q];
+          const T app = A[p * lda + p], aqq = A[q * lda + q];
+          if (fabs((double)apq) > fmax(2.0 * eps * sqrt(fabs((double)app * (double)aqq)), red[66])) {
             red[65] = 1.0;
-            const double app = A[p * lda + p], aqq = A[q * lda + q];
-            const double th = (aqq - app) / (2.0 * apq);
-            const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-            c = 1.0 / sqrt(t * t + 1.0);
+            const T th = (aqq - app) / (T(2) * apq);
+            const T t = (th >= T(0) ? T(1) : T(-1)) / (fabs(th) + sqrt(th * th + T(1)));
+            c = T(1) / sqrt(t * t + T(1));
             s = t * c;
           }
         }
@@ -205,9 +214,9 @@ __device__ void cta_jacobi(double* A, double* V, int n, int lda, int* perm, doub
         const int k = w / n, j = w - (w / n) * n;
         const int p = perm[k], q = perm[ne - 1 - k];
         if (p >= n || q >= n) continue;
-        const double c = cs[2 * k], s = cs[2 * k + 1];
-        if (s == 0.0) continue;
-        const double ap = A[p * lda + j], aq = A[q * lda + j];
+        const T c = cs[2 * k], s = cs[2 * k + 1];
+        if (s == T(0)) continue;
+        const T ap = A[p * lda + j], aq = A[q * lda + j];
         A[p * lda + j] = c * ap - s * aq;
         A[q * lda + j] = s * ap + c * aq;
       }
@@ -217,12 +226,12 @@ __device__ void cta_jacobi(double* A, double* V, int n, int lda, int* perm, doub
         const int k = w / n, i = w - (w / n) * n;
         const int p = perm[k], q = perm[ne - 1 - k];
         if (p >= n || q >= n) continue;
-        const double c = cs[2 * k], s = cs[2 * k + 1];
-        if (s == 0.0) continue;
-        const double ap = A[i * lda + p], aq = A[i * lda + q];
+        const T c = cs[2 * k], s = cs[2 * k + 1];
+        if (s == T(0)) continue;
+        const T ap = A[i * lda + p], aq = A[i * lda + q];
         A[i * lda + p] = c * ap - s * aq;
         A[i * lda + q] = s * ap + c * aq;
-        const double vp = V[i * lda + p], vq = V[i * lda + q];
+        const T vp = V[i * lda + p], vq = V[i * lda + q];
         V[i * lda + p] = c * vp - s * vq;
         V[i * lda + q] = s * vp + c * vq;
       }
@@ -244,15 +253,16 @@ __device__ void cta_jacobi(double* A, double* V, int n, int lda, int* perm, doub
 // largest kept value), rank (number of kept directions).
 // Work matrices A, U, W (row stride ld) and vectors D, sig, idx live in
 // dynamic shared memory (ld = m + 1) or, for large m, in `work` (ld = m).
+template <typename T>
 __global__ void __launch_bounds__(256) rayleigh_ritz_kernel(const DevFrag* efr, const DevPair* gp,
-                                                            const double* blocks, double* work,
+                                                            const double* blocks, T* work,
                                                             long long wstride, double* Cm,
                                                             long long cstride, double* theta,
                                                             const long long* toff, double rank_tol,
                                                             int* rank_out, int use_smem) {
-  extern __shared__ double rr_smem[];
+  extern __shared__ __align__(16) unsigned char rr_raw[];
   __shared__ int perm[520];
-  __shared__ double cs[520];
+  __shared__ T cs[520];
   __shared__ double red[80];
   __shared__ int nkeep;
   const int f = blockIdx.x;
@@ -261,35 +271,35 @@ __global__ void __launch_bounds__(256) rayleigh_ritz_kernel(const DevFrag* efr, 
   const double* Kb = blocks + gp[f].blk_off;
   const double* Gb = Kb + (long long)m * m;
   const int ld = use_smem ? m + 1 : m;
-  double* A = use_smem ? rr_smem : work + f * wstride;
-  double* U = A + (long long)m * ld;
-  double* W = U + (long long)m * ld;
-  double* D = W + (long long)m * ld;       // m
-  double* sig = D + m;                     // m
-  int* idx = (int*)(sig + m);              // m
+  T* A = use_smem ? reinterpret_cast<T*>(rr_raw) : work + f * wstride;
+  T* U = A + (long long)m * ld;
+  T* W = U + (long long)m * ld;
+  T* D = W + (long long)m * ld;           // m
+  T* sig = D + m;                         // m
+  int* idx = reinterpret_cast<int*>(sig + m);   // m
   double* C = Cm + f * cstride;
   double* th = theta + toff[f];
 
   for (int i = tid; i < m; i += nt) {
     const double g = Gb[(long long)i * m + i];
-    D[i] = g > 0.0 ? 1.0 / sqrt(g) : 0.0;
+    D[i] = g > 0.0 ? (T)(1.0 / sqrt(g)) : T(0);
   }
   __syncthreads();
   for (int e = tid; e < m * m; e += nt) {
     const int i = e / m, j = e - (e / m) * m;
-    A[i * ld + j] = D[i] * Gb[e] * D[j];
-    U[i * ld + j] = (i == j) ? 1.0 : 0.0;
+    A[i * ld + j] = D[i] * (T)Gb[e] * D[j];
+    U[i * ld + j] = (i == j) ? T(1) : T(0);
   }
   __syncthreads();
-  cta_jacobi(A, U, m, ld, perm, cs, red);
+  cta_jacobi<T>(A, U, m, ld, perm, cs, red);
   // rank decision on the scaled Gram spectrum
   if (tid == 0) {
-    double smax = 0.0;
+    T smax = 0;
     for (int i = 0; i < m; ++i) smax = fmax(smax, A[i * ld + i]);
     int r = 0;
     for (int i = 0; i < m; ++i) {
-      const double s = A[i * ld + i];
-      if (s > rank_tol * smax) {
+      const T s = A[i * ld + i];
+      if ((double)s > rank_tol * (double)smax) {
         idx[r] = i;
         sig[r] = s;
         ++r;
@@ -308,35 +318,35 @@ __global__ void __launch_bounds__(256) rayleigh_ritz_kernel(const DevFrag* efr, 
   // A <- K W (m x r), then U <- W^T (K W) (r x r), symmetrised
   for (int e = tid; e < m * r; e += nt) {
     const int k = e / r, j = e - (e / r) * r;
-    double s = 0.0;
-    for (int l = 0; l < m; ++l) s += Kb[(long long)k * m + l] * W[l * ld + j];
+    T s = 0;
+    for (int l = 0; l < m; ++l) s += (T)Kb[(long long)k * m + l] * W[l * ld + j];
     A[k * ld + j] = s;
   }
   __syncthreads();
   for (int e = tid; e < r * r; e += nt) {
     const int i = e / r, j = e - (e / r) * r;
     if (j < i) continue;
-    double s = 0.0, t = 0.0;
+    T s = 0, t = 0;
     for (int l = 0; l < m; ++l) {
       s += W[l * ld + i] * A[l * ld + j];
       t += W[l * ld + j] * A[l * ld + i];
     }
-    U[i * ld + j] = 0.5 * (s + t);
-    U[j * ld + i] = 0.5 * (s + t);
+    U[i * ld + j] = T(0.5) * (s + t);
+    U[j * ld + i] = T(0.5) * (s + t);
   }
   __syncthreads();
   for (int e = tid; e < r * r; e += nt) {
     const int i = e / r, j = e - (e / r) * r;
-    A[i * ld + j] = (i == j) ? 1.0 : 0.0;
+    A[i * ld + j] = (i == j) ? T(1) : T(0);
   }
   __syncthreads();
-  cta_jacobi(U, A, r, ld, perm, cs, red);     // U -> diag(theta), A -> Q
+  cta_jacobi<T>(U, A, r, ld, perm, cs, red);     // U -> diag(theta), A -> Q
   // ascending order: rank of each Ritz value
   for (int j = tid; j < r; j += nt) {
-    const double t = U[j * ld + j];
+    const T t = U[j * ld + j];
     int rk = 0;
     for (int i = 0; i < r; ++i) {
-      const double ti = U[i * ld + i];
+      const T ti = U[i * ld + i];
       rk += (ti < t || (ti == t && i < j)) ? 1 : 0;
     }
     idx[j] = rk;
@@ -347,14 +357,14 @@ __global__ void __launch_bounds__(256) rayleigh_ritz_kernel(const DevFrag* efr, 
   __syncthreads();
   for (int e = tid; e < m * r; e += nt) {
     const int k = e / r, j = e - (e / r) * r;
-    double s = 0.0;
+    T s = 0;
     for (int l = 0; l < r; ++l) s += W[k * ld + l] * A[l * ld + j];
-    C[(long long)k * m + idx[j]] = s;
+    C[(long long)k * m + idx[j]] = (double)s;
   }
   double tmax = -DBL_MAX;
-  for (int j = 0; j < r; ++j) tmax = fmax(tmax, U[j * ld + j]);
+  for (int j = 0; j < r; ++j) tmax = fmax(tmax, (double)U[j * ld + j]);
   for (int j = tid; j < m; j += nt) {
-    if (j < r) th[idx[j]] = U[j * ld + j];
+    if (j < r) th[idx[j]] = (double)U[j * ld + j];
     else th[j] = tmax;
   }
   if (tid == 0) rank_out[f] = r;
@@ -635,9 +645,12 @@ static ofm_status eig_setup(ofm_ctx* c, int guard_opt) {
   if (w->rot_smem > 227 * 1024) return ofm_fail(c, OFM_ERR_INVALID, "block size too large for the rotation kernel");
   if (fp64) OFM_CUDA(c, cudaFuncSetAttribute(rotate_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w->rot_smem));
   else OFM_CUDA(c, cudaFuncSetAttribute(rotate_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w->rot_smem));
-  const size_t rr = (3 * (size_t)w->mmax * (w->mmax + 1) + 3 * (size_t)w->mmax) * sizeof(double);
+  const size_t rr = (3 * (size_t)w->mmax * (w->mmax + 1) + 3 * (size_t)w->mmax) * es;
   w->rr_smem = rr <= 200 * 1024 ? rr : 0;
-  if (w->rr_smem) OFM_CUDA(c, cudaFuncSetAttribute(rayleigh_ritz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w->rr_smem));
+  if (w->rr_smem) {
+    if (fp64) OFM_CUDA(c, cudaFuncSetAttribute(rayleigh_ritz_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w->rr_smem));
+    else OFM_CUDA(c, cudaFuncSetAttribute(rayleigh_ritz_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w->rr_smem));
+  }
   w->ready = true;
   return OFM_OK;
 }
@@ -660,11 +673,17 @@ static ofm_status eig_rr(ofm_ctx* c, int y, int hy, int xo, int hxo, unsigned lo
   }
   const long long mm = (long long)w->mmax * w->mmax;
   { KTimer kt(c, KC_RR);
-  rayleigh_ritz_kernel<<<nf, 256, w->rr_smem, s>>>((const DevFrag*)w->d_efr.p, (const DevPair*)w->d_gpairs.p,
-                                          (const double*)w->blocks.p, (double*)w->work.p,
-                                          3 * mm + 3 * w->mmax + 8, (double*)w->Cm.p, mm,
-                                          (double*)w->theta.p, (const long long*)w->d_toff.p,
-                                          fp64 ? 1e-13 : 1e-6, (int*)w->d_rank.p, w->rr_smem > 0 ? 1 : 0); }
+  if (fp64)
+    rayleigh_ritz_kernel<double><<<nf, 256, w->rr_smem, s>>>(
+        (const DevFrag*)w->d_efr.p, (const DevPair*)w->d_gpairs.p, (const double*)w->blocks.p,
+        (double*)w->work.p, 3 * mm + 3 * w->mmax + 8, (double*)w->Cm.p, mm, (double*)w->theta.p,
+        (const long long*)w->d_toff.p, 1e-13, (int*)w->d_rank.p, w->rr_smem > 0 ? 1 : 0);
+  else
+    rayleigh_ritz_kernel<float><<<nf, 256, w->rr_smem, s>>>(
+        (const DevFrag*)w->d_efr.p, (const DevPair*)w->d_gpairs.p, (const double*)w->blocks.p,
+        (float*)w->work.p, 3 * mm + 3 * w->mmax + 8, (double*)w->Cm.p, mm, (double*)w->theta.p,
+        (const long long*)w->d_toff.p, 1e-5, (int*)w->d_rank.p, w->rr_smem > 0 ? 1 : 0);
+  }
   dim3 g(w->rot_blocks, nf);
   KTimer kt(c, KC_ROTATE, 2, w->rot_bytes, w->rot_flops);
   if (fp64)

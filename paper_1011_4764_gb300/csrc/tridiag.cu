@@ -147,9 +147,12 @@ __global__ void __launch_bounds__(512) tridiag_persistent_kernel(double* A, int 
     double q = 0.0;
     for (int j = tid; j < m; j += nt) q += v[k + 1 + j] * pw[k + 1 + j];
     const double K = 0.5 * t * block_sum(q, red);
+    // w = p - K v, once per CTA, so the update costs two FMA per element
+    for (int j = tid; j < m; j += nt) pw[k + 1 + j] = fma(-K, v[k + 1 + j], pw[k + 1 + j]);
+    __syncthreads();
     for (int r = gw; r < m; r += gws) {
       const int i = k + 1 + r;
-      const double vi = v[i], wi = pw[i] - K * vi;
+      const double vi = v[i], wi = pw[i];
       double* row = A + (long long)i * n;
       int j = k + 1 + lane;
       for (; j + 7 * 32 < n; j += 8 * 32) {
@@ -159,10 +162,10 @@ __global__ void __launch_bounds__(512) tridiag_persistent_kernel(double* A, int 
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           const int jj = j + 32 * u;
-          row[jj] = a[u] - (vi * (pw[jj] - K * v[jj]) + wi * v[jj]);
+          row[jj] = fma(-vi, pw[jj], fma(-wi, v[jj], a[u]));
         }
       }
-      for (; j < n; j += 32) row[j] = __ldcg(&row[j]) - (vi * (pw[j] - K * v[j]) + wi * v[j]);
+      for (; j < n; j += 32) row[j] = fma(-vi, pw[j], fma(-wi, v[j], __ldcg(&row[j])));
     }
     if (!grid_sync(bar, nb)) return;
   }
@@ -183,22 +186,30 @@ __global__ void __launch_bounds__(512) tridiag_persistent_kernel(double* A, int 
 template <bool SQ>
 __device__ int sturm_count(const double* __restrict__ d, const double* __restrict__ e, int n,
                            double x) {
+  // sign and exponent tests on the bit patterns (integer pipe), leaving
+  // three FP64 operations per step
   double p0 = 1.0, p1 = d[0] - x;
   if (p1 == 0.0) p1 = -DBL_MIN;
   int c = p1 < 0.0 ? 1 : 0;
+  long long s1 = __double_as_longlong(p1);
   for (int i = 1; i < n; ++i) {
     const double ei = e[i - 1];
     double p2 = fma(d[i] - x, p1, -(SQ ? ei : ei * ei) * p0);
-    if (p2 == 0.0) p2 = (p1 < 0.0) ? DBL_MIN : -DBL_MIN;
-    c += ((p2 < 0.0) != (p1 < 0.0)) ? 1 : 0;
-    const double a = fabs(p2);
-    if (a > 0x1p400 || a < 0x1p-400) {
-      const int ex = ilogb(p2);
+    long long s2 = __double_as_longlong(p2);
+    if ((s2 << 1) == 0) {  // a zero minor counts as a sign change
+      p2 = (s1 < 0) ? DBL_MIN : -DBL_MIN;
+      s2 = __double_as_longlong(p2);
+    }
+    c += (int)((unsigned long long)(s2 ^ s1) >> 63);
+    const int ex = (int)((s2 >> 52) & 0x7ff) - 1023;
+    if (ex > 400 || ex < -400) {
       p2 = scalbn(p2, -ex);
       p1 = scalbn(p1, -ex);
+      s2 = __double_as_longlong(p2);
     }
     p0 = p1;
     p1 = p2;
+    s1 = s2;
   }
   return c;
 }
@@ -222,8 +233,11 @@ __global__ void __launch_bounds__(256) multisection_kernel(const double* __restr
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (w >= m) return;
-  const int idx = i_lo + w;
+  // four eigenvalues per warp, eight lanes (eight shifts) each
+  const int grp = lane >> 3, sub = lane & 7;
+  if (w * 4 >= m) return;
+  const int t = w * 4 + grp;                 // output slot of this lane group
+  const int idx = i_lo + (t < m ? t : m - 1);
   // Gershgorin interval
   double a = DBL_MAX, b = -DBL_MAX;
   for (int j = lane; j < n; j += 32) {
@@ -238,25 +252,35 @@ __global__ void __launch_bounds__(256) multisection_kernel(const double* __restr
   const double wdt = fmax(fabs(a), fabs(b));
   double lo = a - 2.0 * DBL_EPSILON * wdt - DBL_MIN;
   double hi = b + 2.0 * DBL_EPSILON * wdt + DBL_MIN;
-  for (int it = 0; it < 64; ++it) {
-    if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + 4.0 * DBL_MIN) break;
-    const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
-    const int cnt = sturm_count<true>(ds, e2s, n, x);
-    const unsigned mask = __ballot_sync(0xffffffffu, cnt > idx);
+  // every lane group keeps its own [lo, hi]; the warp loops until all four
+  // groups have converged (or stopped making progress)
+  bool done = false;
+  for (int it = 0; it < 128; ++it) {
+    done = done || (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + 4.0 * DBL_MIN);
+    if (__all_sync(0xffffffffu, done)) break;
+    const double x = lo + (hi - lo) * (double)(sub + 1) / 9.0;
+    const int cnt = done ? 0 : sturm_count<true>(ds, e2s, n, x);
+    const unsigned ball = __ballot_sync(0xffffffffu, cnt > idx);
+    const unsigned mask = (ball >> (grp * 8)) & 0xffu;
     const double xprev = __shfl_up_sync(0xffffffffu, x, 1);
-    if (mask == 0) {
-      lo = __shfl_sync(0xffffffffu, x, 31);
-    } else {
-      const int l = __ffs(mask) - 1;
-      const double nhi = __shfl_sync(0xffffffffu, x, l);
-      const double xl = __shfl_sync(0xffffffffu, xprev, l);
-      const double nlo = (l > 0) ? xl : lo;
-      if (nhi == hi && nlo == lo) break;  // no progress at this precision
+    const int l = mask ? __ffs(mask) - 1 : 7;
+    const double xl = __shfl_sync(0xffffffffu, x, grp * 8 + l);
+    const double xlp = __shfl_sync(0xffffffffu, xprev, grp * 8 + l);
+    if (!done) {
+      double nlo, nhi;
+      if (mask == 0) {
+        nlo = xl;        // above all eight shifts
+        nhi = hi;
+      } else {
+        nhi = xl;
+        nlo = (l > 0) ? xlp : lo;
+      }
+      if (nhi == hi && nlo == lo) done = true;  // no progress at this precision
       lo = nlo;
       hi = nhi;
     }
   }
-  if (lane == 0) out[w] = 0.5 * (lo + hi);
+  if (sub == 0 && t < m) out[t] = 0.5 * (lo + hi);
 }
 
 }  // namespace ofm
@@ -314,9 +338,8 @@ bool launch_multisection(const double* d, const double* e, int n, int i_lo, int 
     }
     attr_set = true;
   }
-  // two warps per CTA so that the wanted eigenvalues spread over every SM
-  const int warps_per_block = 2;
-  multisection_kernel<<<(m + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, smem,
-                        s>>>(d, e, n, i_lo, m, out);
+  // two warps (eight eigenvalues) per CTA so that the work spreads over every SM
+  const int per_block = 8;
+  multisection_kernel<<<(m + per_block - 1) / per_block, 64, smem, s>>>(d, e, n, i_lo, m, out);
   return true;
 }
