@@ -138,6 +138,20 @@ __global__ void init_random_kernel(const DevFrag* fr, const int* cta_start, int 
 // (the FP64 pipe of one SM issues about 2 FMA per clock on this part, so
 // FP64 here would make the eigensolver bound by a handful of SMs).
 
+// Round-robin schedule (circle method): index ne-1 stays, the others
+// rotate; round r pairs (r, ne-1) and ((r+k) mod (ne-1), (r-k) mod (ne-1)).
+// Every pair meets once per sweep and the pairs of a round are disjoint.
+__device__ __forceinline__ void rr_pair(int r, int k, int ne, int& p, int& q) {
+  const int M = ne - 1;
+  if (k == 0) {
+    p = r;
+    q = M;
+  } else {
+    p = (r + k) % M;
+    q = (r - k + M) % M;
+  }
+}
+
 template <typename T> struct Eps;
 template <> struct Eps<float> { static constexpr double v = 6.0e-8; };
 template <> struct Eps<double> { static constexpr double v = 1.1e-16; };
@@ -156,8 +170,7 @@ __device__ void cta_jacobi(T* A, T* V, int n, int lda, int* perm, T* cs, double*
   const int ne = n + (n & 1);
   const int half = ne / 2;
   const double eps = Eps<T>::v;
-  for (int i = tid; i < ne; i += nt) perm[i] = i;
-  __syncthreads();
+  (void)perm;
   for (int sweep = 0; sweep < 40; ++sweep) {
     double off = 0.0, tot = 0.0;
     for (int e = tid; e < n * n; e += nt) {
@@ -192,7 +205,8 @@ __device__ void cta_jacobi(T* A, T* V, int n, int lda, int* perm, T* cs, double*
     if (done) break;
     for (int r = 0; r < ne - 1; ++r) {
       for (int k = tid; k < half; k += nt) {
-        const int p = perm[k], q = perm[ne - 1 - k];
+        int p, q;
+        rr_pair(r, k, ne, p, q);
         T c = 1, s = 0;
         if (p < n && q < n) {
           const T apq = A[p * lda + q];
@@ -212,7 +226,8 @@ __device__ void cta_jacobi(T* A, T* V, int n, int lda, int* perm, T* cs, double*
       // rows p, q
       for (int w = tid; w < half * n; w += nt) {
         const int k = w / n, j = w - (w / n) * n;
-        const int p = perm[k], q = perm[ne - 1 - k];
+        int p, q;
+        rr_pair(r, k, ne, p, q);
         if (p >= n || q >= n) continue;
         const T c = cs[2 * k], s = cs[2 * k + 1];
         if (s == T(0)) continue;
@@ -224,7 +239,8 @@ __device__ void cta_jacobi(T* A, T* V, int n, int lda, int* perm, T* cs, double*
       // columns p, q of A and V
       for (int w = tid; w < half * n; w += nt) {
         const int k = w / n, i = w - (w / n) * n;
-        const int p = perm[k], q = perm[ne - 1 - k];
+        int p, q;
+        rr_pair(r, k, ne, p, q);
         if (p >= n || q >= n) continue;
         const T c = cs[2 * k], s = cs[2 * k + 1];
         if (s == T(0)) continue;
@@ -234,12 +250,6 @@ __device__ void cta_jacobi(T* A, T* V, int n, int lda, int* perm, T* cs, double*
         const T vp = V[i * lda + p], vq = V[i * lda + q];
         V[i * lda + p] = c * vp - s * vq;
         V[i * lda + q] = s * vp + c * vq;
-      }
-      __syncthreads();
-      if (tid == 0) {
-        const int last = perm[ne - 1];
-        for (int i = ne - 1; i > 1; --i) perm[i] = perm[i - 1];
-        perm[1] = last;
       }
       __syncthreads();
     }
@@ -291,6 +301,97 @@ __global__ void __launch_bounds__(256) rayleigh_ritz_kernel(const DevFrag* efr, 
     U[i * ld + j] = (i == j) ? T(1) : T(0);
   }
   __syncthreads();
+  // Fast path: when the scaled Gram is well conditioned (every Cholesky
+  // pivot above chol_tol, the usual case once the iteration has started to
+  // converge), G_s = L L^T, B = L^-1 K_s L^-T, one Jacobi on the nearly
+  // diagonal B, C = D L^-T Q.  Otherwise the canonical orthogonalisation
+  // below drops the near-dependent directions.
+  {
+    __shared__ int chol_ok;
+    const T chol_tol = sizeof(T) == 8 ? T(1e-8) : T(1e-3);
+    if (tid == 0) chol_ok = 1;
+    for (int e = tid; e < m * m; e += nt) {
+      const int i = e / m, j = e - (e / m) * m;
+      W[i * ld + j] = A[i * ld + j];
+    }
+    __syncthreads();
+    for (int j = 0; j < m; ++j) {
+      if (tid == 0) {
+        T piv = W[j * ld + j];
+        if (!(piv > chol_tol)) {
+          chol_ok = 0;
+          piv = T(1);
+        }
+        W[j * ld + j] = sqrt(piv);
+      }
+      __syncthreads();
+      for (int i = j + 1 + tid; i < m; i += nt) W[i * ld + j] /= W[j * ld + j];
+      __syncthreads();
+      const int rest = m - j - 1;
+      for (int e = tid; e < rest * rest; e += nt) {
+        const int i = j + 1 + e / rest, k = j + 1 + e % rest;
+        if (k <= i) W[i * ld + k] -= W[i * ld + j] * W[k * ld + j];
+      }
+      __syncthreads();
+    }
+    if (chol_ok) {
+      // U <- L^-1 (D K D), one thread per column
+      for (int c = tid; c < m; c += nt)
+        for (int i = 0; i < m; ++i) {
+          T s = D[i] * (T)Kb[(long long)i * m + c] * D[c];
+          for (int k = 0; k < i; ++k) s -= W[i * ld + k] * U[k * ld + c];
+          U[i * ld + c] = s / W[i * ld + i];
+        }
+      __syncthreads();
+      // A <- L^-1 U^T = L^-1 (D K D) L^-T
+      for (int c = tid; c < m; c += nt)
+        for (int i = 0; i < m; ++i) {
+          T s = U[c * ld + i];
+          for (int k = 0; k < i; ++k) s -= W[i * ld + k] * A[k * ld + c];
+          A[i * ld + c] = s / W[i * ld + i];
+        }
+      __syncthreads();
+      for (int e = tid; e < m * m; e += nt) {
+        const int i = e / m, j = e - (e / m) * m;
+        if (i < j) {
+          const T v = T(0.5) * (A[i * ld + j] + A[j * ld + i]);
+          A[i * ld + j] = v;
+          A[j * ld + i] = v;
+        }
+      }
+      __syncthreads();
+      for (int e = tid; e < m * m; e += nt) {
+        const int i = e / m, j = e - (e / m) * m;
+        U[i * ld + j] = (i == j) ? T(1) : T(0);
+      }
+      __syncthreads();
+      cta_jacobi<T>(A, U, m, ld, perm, cs, red);   // A -> diag(theta), U -> Q
+      for (int j = tid; j < m; j += nt) {
+        const T t = A[j * ld + j];
+        int rk = 0;
+        for (int i = 0; i < m; ++i) {
+          const T ti = A[i * ld + i];
+          rk += (ti < t || (ti == t && i < j)) ? 1 : 0;
+        }
+        idx[j] = rk;
+      }
+      // U <- L^-T Q, one thread per column (back substitution in place)
+      for (int j = tid; j < m; j += nt)
+        for (int i = m - 1; i >= 0; --i) {
+          T s = U[i * ld + j];
+          for (int k = i + 1; k < m; ++k) s -= W[k * ld + i] * U[k * ld + j];
+          U[i * ld + j] = s / W[i * ld + i];
+        }
+      __syncthreads();
+      for (int e = tid; e < m * m; e += nt) {
+        const int k = e / m, j = e - (e / m) * m;
+        C[(long long)k * m + idx[j]] = (double)(D[k] * U[k * ld + j]);
+      }
+      for (int j = tid; j < m; j += nt) th[idx[j]] = (double)A[j * ld + j];
+      if (tid == 0) rank_out[f] = m;
+      return;
+    }
+  }
   cta_jacobi<T>(A, U, m, ld, perm, cs, red);
   // rank decision on the scaled Gram spectrum
   if (tid == 0) {

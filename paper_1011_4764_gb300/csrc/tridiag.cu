@@ -178,6 +178,101 @@ __global__ void __launch_bounds__(512) tridiag_persistent_kernel(double* A, int 
   }
 }
 
+// The same reduction with the matrix resident in shared memory: CTA b owns
+// the rows i = b, b + nb, b + 2 nb, ... for the whole reduction, so the
+// rank-2 updates and the matrix-vector products never leave the SM; only
+// the current column (colbuf) and p (pg) travel through L2.
+__global__ void __launch_bounds__(512) tridiag_smem_kernel(double* A, int n, double* d, double* e,
+                                                           double* tau, double* colbuf,
+                                                           double* pg, GridBar* bar) {
+  extern __shared__ double sm[];
+  const int nb = (int)gridDim.x, b = (int)blockIdx.x;
+  const int R = (n - b + nb - 1) / nb;      // rows owned by this CTA
+  const int Rmax = (n + nb - 1) / nb;
+  double* rows = sm;                        // Rmax x n
+  double* v = rows + (size_t)Rmax * n;      // n
+  double* pw = v + n;                       // n
+  __shared__ double red[40];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
+  for (int e2 = tid; e2 < R * n; e2 += nt) {
+    const int li = e2 / n, j = e2 - li * n;
+    rows[(size_t)li * n + j] = A[(size_t)(b + li * nb) * n + j];
+  }
+  __syncthreads();
+  for (int li = tid; li < R; li += nt) colbuf[b + li * nb] = rows[(size_t)li * n + 0];
+  if (!grid_sync(bar, nb)) return;
+  for (int k = 0; k + 2 < n; ++k) {
+    const int m = n - k - 1;
+    // Householder vector of column k from colbuf (rows k+1..n-1)
+    double s = 0.0;
+    for (int i = tid + 1; i < m; i += nt) {
+      const double x = __ldcg(&colbuf[k + 1 + i]);
+      s += x * x;
+    }
+    const double sig = block_sum(s, red);
+    const double x0 = __ldcg(&colbuf[k + 1]);
+    double alpha, t, v0;
+    if (sig == 0.0) {
+      alpha = x0;
+      t = 0.0;
+      v0 = 1.0;
+    } else {
+      const double nrm = sqrt(x0 * x0 + sig);
+      alpha = (x0 > 0.0) ? -nrm : nrm;
+      v0 = x0 - alpha;
+      t = 2.0 / (v0 * v0 + sig);
+    }
+    for (int i = tid; i < m; i += nt) {
+      const double vi = (i == 0) ? v0 : __ldcg(&colbuf[k + 1 + i]);
+      v[k + 1 + i] = vi;
+      if (b == 0) A[(size_t)k * n + k + 1 + i] = vi;  // kept for back-transformation
+    }
+    if (tid == 0) {
+      if (k % nb == b) d[k] = rows[(size_t)(k / nb) * n + k];
+      if (b == 0) {
+        e[k] = alpha;
+        tau[k] = t;
+      }
+    }
+    __syncthreads();
+    // p_i = t sum_j A_ij v_j for the owned rows i > k, one warp per row
+    const int li0 = (k + 1 - b + nb - 1) / nb;   // first owned row index > k
+    for (int li = li0 + warp; li < R; li += nwarps) {
+      const double* row = rows + (size_t)li * n;
+      double acc = 0.0;
+      for (int j = k + 1 + lane; j < n; j += 32) acc += row[j] * v[j];
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+      if (lane == 0) pg[b + li * nb] = t * acc;
+    }
+    if (!grid_sync(bar, nb)) return;
+    for (int j = tid; j < m; j += nt) pw[k + 1 + j] = __ldcg(&pg[k + 1 + j]);
+    __syncthreads();
+    double q = 0.0;
+    for (int j = tid; j < m; j += nt) q += v[k + 1 + j] * pw[k + 1 + j];
+    const double K = 0.5 * t * block_sum(q, red);
+    for (int j = tid; j < m; j += nt) pw[k + 1 + j] = fma(-K, v[k + 1 + j], pw[k + 1 + j]);
+    __syncthreads();
+    // rank-2 update of the owned rows; the next column goes to colbuf
+    for (int li = li0 + warp; li < R; li += nwarps) {
+      const int i = b + li * nb;
+      double* row = rows + (size_t)li * n;
+      const double vi = v[i], wi = pw[i];
+      for (int j = k + 1 + lane; j < n; j += 32) row[j] = fma(-vi, pw[j], fma(-wi, v[j], row[j]));
+      __syncwarp();
+      if (lane == 0) colbuf[i] = row[k + 1];
+    }
+    if (!grid_sync(bar, nb)) return;
+  }
+  if (tid == 0) {
+    if (n >= 2) {
+      if ((n - 2) % nb == b) d[n - 2] = rows[(size_t)((n - 2) / nb) * n + n - 2];
+      if ((n - 1) % nb == b) e[n - 2] = rows[(size_t)((n - 1) / nb) * n + n - 2];
+    }
+    if ((n - 1) % nb == b) d[n - 1] = rows[(size_t)((n - 1) / nb) * n + n - 1];
+  }
+}
+
 // Number of eigenvalues of the tridiagonal (d, e) below x: sign changes of
 // the leading principal minors p_i of T - x I (p_0 = 1), a zero minor
 // counted as a change; both running minors are rescaled by a power of two
@@ -298,6 +393,34 @@ ofm_status ofm_tridiag_persistent(ofm_ctx* c, double* A, int n, double* d, doubl
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (!coop) return OFM_ERR_INVALID;
+  // shared-memory-resident variant when every CTA's rows fit (one CTA per SM)
+  {
+    const int nbs = sms;
+    const size_t rmax = (size_t)(n + nbs - 1) / nbs;
+    const size_t smem2 = (rmax * n + 2 * (size_t)n) * sizeof(double);
+    int per_sm2 = 0;
+    if (smem2 <= 200 * 1024 &&
+        cudaFuncSetAttribute(tridiag_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem2) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, tridiag_smem_kernel, 512, smem2) ==
+            cudaSuccess &&
+        per_sm2 >= 1 && c->w_eval.cap >= (size_t)n * sizeof(double)) {
+      OFM_TRY(ofm_ensure(c, c->w_bar, sizeof(GridBar), "grid barrier"));
+      OFM_CUDA(c, cudaMemsetAsync(c->w_bar.p, 0, sizeof(GridBar), c->stream));
+      GridBar* bar = (GridBar*)c->w_bar.p;
+      double* colbuf = (double*)c->w_eval.p;
+      int nn = n;
+      void* args[] = {&A, &nn, &d, &e, &tau, &colbuf, &pg, &bar};
+      OFM_CUDA(c, cudaLaunchCooperativeKernel((const void*)tridiag_smem_kernel, dim3(nbs), dim3(512),
+                                              args, smem2, c->stream));
+      GridBar hb{};
+      OFM_CUDA(c, cudaMemcpyAsync(&hb, bar, sizeof(GridBar), cudaMemcpyDeviceToHost, c->stream));
+      OFM_CUDA(c, cudaStreamSynchronize(c->stream));
+      if (hb.err) return ofm_fail(c, OFM_ERR_TIMEOUT, "tridiagonal reduction: grid barrier wait exceeded its bound");
+      return OFM_OK;
+    }
+    cudaGetLastError();
+  }
   OFM_CUDA(c, cudaFuncSetAttribute(tridiag_persistent_kernel,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
