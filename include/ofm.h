@@ -214,6 +214,37 @@ ofm_status ofm_plan_pairs(const ofm_grid* grid, const ofm_fragment* frags, int n
                           int* n_pairs, int* pair_ab, long long* counts, int max_pairs,
                           long long* pair_flops);
 
+/* Allocation-free pair blocks.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory when they need
+ * a block -- code whose device memory is owned by another framework's pool,
+ * latency-critical paths where cudaMalloc/cudaFree may block or synchronise
+ * the device, or sandboxed code that is handed ready-made device buffers.
+ * It computes, for one pair of fragments on the grid, in FP32 arithmetic,
+ *     HS_ab[0 .. n_a*n_b)        = H_ab = Phi_a^T (H Phi_b), row-major n_a x n_b,
+ *     HS_ab[n_a*n_b .. 2 n_a n_b) = S_ab = Phi_a^T Phi_b,
+ * symmetrised when fa and fb describe the same fragment with the same
+ * buffer, and zeros when the boxes do not interact.
+ * Inputs (device, FP32): phi_a, phi_b, hphi_b in the library's storage
+ * layout -- point-major on the fragment's dilated box (the box grown by one
+ * point on each side in every dimension it does not span), element
+ * (p, s) at p * ld + s with ld = n_states rounded up to a multiple of 4, p
+ * the dilated-box point index (x fastest), halo rows of phi zero.  hphi_b
+ * is H phi_b with the whole-system H on the dilated box, same layout.
+ * The work uses only the caller's buffers and one fixed device array of
+ * OFM_NOALLOC_SCRATCH bytes inside the library (held by every GPU that
+ * loads it until exit); no cudaMalloc, cudaFree or allocating library call
+ * is made.  The first call on a device looks up that array's address and
+ * should come before any stream capture.  Calls share the array: calls
+ * whose GPU work overlaps race.  Work is enqueued on cuda_stream (NULL =
+ * legacy default stream) and not synchronised.  Returns OFM_ERR_INVALID for
+ * bad geometry or pointers, or when the pair's work tables and partial
+ * tiles do not fit the scratch; OFM_ERR_CUDA when a runtime call fails. */
+#define OFM_NOALLOC_SCRATCH (32u * 1024u * 1024u)
+ofm_status ofm_pair_blocks_noalloc(const ofm_grid* grid, const ofm_fragment* fa,
+                                   const ofm_fragment* fb, const float* phi_a,
+                                   const float* phi_b, const float* hphi_b, double* HS_ab,
+                                   void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

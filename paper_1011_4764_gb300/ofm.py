@@ -28,6 +28,7 @@ EXPORTS = [
     "ofm_assemble_HS", "ofm_get_pairs", "ofm_get_plan_info", "ofm_get_block",
     "ofm_get_dense_HS", "ofm_get_hphi", "ofm_window_eigs", "ofm_eigs_by_index",
     "ofm_set_dense_HS", "ofm_plan_pairs", "ofm_set_profiling", "ofm_get_kernel_stats",
+    "ofm_pair_blocks_noalloc",
 ]
 
 
@@ -96,6 +97,8 @@ def load_library(path: str = LIB_PATH):
         "ofm_plan_pairs": ([C.POINTER(ofm_grid), C.POINTER(ofm_fragment), I, IP, IP,
                             C.POINTER(C.c_longlong), I, C.POINTER(C.c_longlong)], I),
         "ofm_set_profiling": ([P, I], I),
+        "ofm_pair_blocks_noalloc": ([C.POINTER(ofm_grid), C.POINTER(ofm_fragment),
+                                     C.POINTER(ofm_fragment), P, P, P, P, P], I),
         "ofm_get_kernel_stats": ([P, C.POINTER(ofm_kernel_stat), I, IP], I),
     }
     for name, (args, res) in sig.items():
@@ -152,6 +155,25 @@ def plan_pairs(grid, frags):
     lib.ofm_plan_pairs(C.byref(g), fa, len(frags), C.byref(n), _iptr(ab),
                        cnt.ctypes.data_as(C.POINTER(C.c_longlong)), n.value, C.byref(F))
     return [tuple(map(int, ab[2 * i:2 * i + 2])) for i in range(n.value)], cnt.reshape(-1, 2), F.value
+
+
+def pair_blocks_noalloc(grid, fa, fb, phi_a, phi_b, hphi_b, out, stream=0):
+    """ofm_pair_blocks_noalloc: for callers that cannot allocate device
+    memory.  phi_a, phi_b, hphi_b: CUDA float32 tensors in the storage layout
+    (point-major on the dilated box, row stride n rounded up to 4); out: CUDA
+    float64 tensor of 2 n_a n_b (H_ab then S_ab).  Enqueued on `stream` (a
+    cudaStream_t handle, 0 = legacy default); not synchronised."""
+    lib = load_library()
+    g, fab = _c_geometry(grid, [fa, fb])
+    for t in (phi_a, phi_b, hphi_b):
+        assert t.is_cuda and str(t.dtype) == "torch.float32" and t.is_contiguous()
+    assert out.is_cuda and str(out.dtype) == "torch.float64" and out.is_contiguous()
+    s = lib.ofm_pair_blocks_noalloc(C.byref(g), C.byref(fab[0]), C.byref(fab[1]),
+                                    C.c_void_p(phi_a.data_ptr()), C.c_void_p(phi_b.data_ptr()),
+                                    C.c_void_p(hphi_b.data_ptr()), C.c_void_p(out.data_ptr()),
+                                    C.c_void_p(stream) if stream else None)
+    if s != OFM_OK:
+        raise OFMError(s, "ofm_pair_blocks_noalloc failed")
 
 
 class Context:
