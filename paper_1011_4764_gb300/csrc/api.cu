@@ -377,6 +377,7 @@ extern "C" ofm_status ofm_get_block(ofm_ctx* c, int a, int b, double* H_ab, doub
   if (!c) return OFM_ERR_INVALID;
   if (!c->assembled) return ofm_fail(c, OFM_ERR_STATE, "ofm_assemble_HS must come first");
   if (a < 0 || b < 0 || a >= c->nfrag || b >= c->nfrag) return ofm_fail(c, OFM_ERR_INVALID, "bad fragment index");
+  OFM_TRY(ofm_tc_status(c));
   const bool swap = a > b;
   const int lo = swap ? b : a, hi = swap ? a : b;
   const int na = c->frags[a].n, nb = c->frags[b].n;
@@ -405,6 +406,7 @@ extern "C" ofm_status ofm_get_block(ofm_ctx* c, int a, int b, double* H_ab, doub
 ofm_status ofm_make_dense(ofm_ctx* c) {
   if (c->dense_ready) return OFM_OK;
   if (!c->assembled) return ofm_fail(c, OFM_ERR_STATE, "ofm_assemble_HS must come first");
+  OFM_TRY(ofm_tc_status(c));
   const long long n = c->basis;
   OFM_TRY(ofm_ensure(c, c->dense_H, sizeof(double) * n * n, "dense H"));
   OFM_TRY(ofm_ensure(c, c->dense_S, sizeof(double) * n * n, "dense S"));

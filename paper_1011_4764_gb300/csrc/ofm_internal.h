@@ -187,6 +187,7 @@ struct ofm_ctx {
   // algorithmic traffic of one launch, set by the planner
   double apply_bytes = 0, contract_bytes = 0, finalize_bytes = 0;
   ofm_prof prof;                    // per-kernel-class launch counts and event timing
+  bool tc_check = false;            // a tensor-core launch's timeout flag is unread
   struct EigWork* eig = nullptr;    // fragment-eigensolver buffers and plan
   struct TcPlan* tc = nullptr;      // tensor-core contraction plan
 };
@@ -205,6 +206,7 @@ void ofm_eig_free(ofm_ctx* c);
 void ofm_prof_release(ofm_ctx* c);            // waits for and frees timing events
 void ofm_tc_free(ofm_ctx* c);
 ofm_status ofm_contract_tc(ofm_ctx* c, ofm_precision prec);
+ofm_status ofm_tc_status(ofm_ctx* c);         // OFM_ERR_TIMEOUT if a tensor-core wait gave up
 ofm_status ofm_window_factor(ofm_ctx* c);
 ofm_status ofm_window_count(ofm_ctx* c, double x, bool inclusive, int* count);
 ofm_status ofm_window_bisect(ofm_ctx* c, int i_lo, int i_hi, double* E_out);
