@@ -46,7 +46,48 @@ def parse_args():
     p.add_argument("--workload", default="alkane")
     p.add_argument("--precision", default="fp32")
     p.add_argument("--no-extras", action="store_true", help="skip e2e, FP64 reference and sweeps")
+    p.add_argument("--eig-degree", type=int, default=0, help="Chebyshev degree (0 = library default)")
+    p.add_argument("--eig-extra", type=int, default=0, help="guard vectors (0 = library default)")
     return p.parse_args()
+
+
+# FP64 issue rate measured by ncu on this part (about 2 FMA per clock per SM;
+# sm__pipe_fp64_cycles_active), times 152 SMs at the 2070 MHz maximum clock:
+# 152 * 2 * 2 * 2.07e9 = 1.26e12 flop/s, the recipe's 1.25 TFLOP/s.
+FP64_PEAK_TFLOPS = 1.25
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e-3   # CUDA-core FMA lanes x clock
+HBM_CLASSES = {"filter", "apply", "convert", "eig_export", "eig_init", "finalize", "scatter"}
+FP64_CLASSES = {"cholesky", "reduce", "tridiag", "bisect"}
+
+
+def roofline_for(name, s, pk, precision):
+    """Roofline of one kernel class from its algorithmic bytes / flops and
+    its event-timed duration."""
+    ms = s["ms"] / max(1, s["launches"])
+    r = {"kernel": name, "row": s["row"], "launches": s["launches"], "ms_per_launch": ms}
+    if name in HBM_CLASSES or (s["flops"] == 0 and s["bytes"] > 0):
+        per = s["bytes"] / max(1, s["launches"])
+        r.update(bound="hbm", unit="GB/s", achieved=per / (ms * 1e-3) / 1e9, peak=pk["hbm_gbs"],
+                 peak_source=pk["source"] + " copy bandwidth", algorithmic_bytes_per_launch=per)
+    elif name in FP64_CLASSES:
+        per = s["flops"] / max(1, s["launches"])
+        r.update(bound="alu", unit="TFLOP/s", achieved=per / (ms * 1e-3) / 1e12,
+                 peak=FP64_PEAK_TFLOPS, peak_source="FP64 issue rate x SMs x max clock",
+                 algorithmic_flops_per_launch=per)
+    elif name == "contract" and precision in ("tf32", "bf16", "bf16x3"):
+        per = s["flops"] / max(1, s["launches"])
+        bf16 = pk["bf16_tflops"]
+        peak = {"bf16": bf16, "bf16x3": bf16 / 3.0, "tf32": bf16 * 1.1 / 2.25}[precision]
+        r.update(bound="tensor", unit="TFLOP/s", achieved=per / (ms * 1e-3) / 1e12, peak=peak,
+                 peak_source=pk["source"] + " bf16 burst x dtype ratio (tf32 1.1/2.25, hi+lo 1/3)",
+                 algorithmic_flops_per_launch=per)
+    else:
+        per = s["flops"] / max(1, s["launches"])
+        r.update(bound="alu", unit="TFLOP/s", achieved=per / (ms * 1e-3) / 1e12,
+                 peak=FP32_PEAK_TFLOPS, peak_source="FP32 lanes x SMs x max clock",
+                 algorithmic_flops_per_launch=per)
+    r["frac"] = r["achieved"] / r["peak"] if r["peak"] else None
+    return r
 
 
 def peaks():
@@ -232,7 +273,7 @@ def run_ours(args):
 
     def step(Vsrc):
         ctx.build_fragments(grid, Vsrc, frags, storage=storage)
-        eps, res, _ = ctx.fragment_eigs()
+        eps, res, _ = ctx.fragment_eigs(degree=args.eig_degree, extra_states=args.eig_extra)
         ctx.assemble(args.precision)
         E, lo, hi = window_of(ctx)
         return E, eps
@@ -290,16 +331,10 @@ def run_ours(args):
     # dominant kernel class and its roofline
     pk = peaks()
     dom_name, dom = max(stats.items(), key=lambda kv: kv[1]["ms"])
-    per_launch_ms = dom["ms"] / max(1, dom["launches"])
-    bytes_per_launch = dom["bytes"] / max(1, dom["launches"])
-    traffic = profiled_traffic(dom_name)
-    roof = {"kernel": dom_name, "row": dom["row"], "bound": "hbm",
-            "achieved": bytes_per_launch / (per_launch_ms * 1e-3) / 1e9,
-            "peak": pk["hbm_gbs"], "unit": "GB/s", "peak_source": pk["source"] + " (copy burst)",
-            "launches": dom["launches"], "ms_per_launch": per_launch_ms,
-            "algorithmic_bytes_per_launch": bytes_per_launch,
-            "traffic": traffic}
-    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof = roofline_for(dom_name, dom, pk, args.precision)
+    roof["traffic"] = profiled_traffic(dom_name)
+    others = {k: roofline_for(k, s, pk, args.precision) for k, s in stats.items()
+              if k in ("filter", "apply", "contract", "tridiag")}
 
     out = {
         "metric": "H/S pair-block TFLOP/s", "value": value, "unit": "TFLOP/s",
@@ -324,6 +359,7 @@ def run_ours(args):
         "wall_s": wall,
         "gpu_launches": launches,
         "roofline": roof,
+        "rooflines": others,
         "clocks": clk,
         "window_eigs": int(len(E)),
     }

@@ -24,11 +24,16 @@
 
 namespace ofm {
 
+// Two-level barrier state: CTAs arrive on one of BAR_GROUPS counters (each
+// on its own 128-byte line); the last arrival of a group arrives on the root
+// counter; the last root arrival advances the generation everyone waits on.
+constexpr int BAR_GROUPS = 4;
 struct GridBar {
-  unsigned int count;
   unsigned int gen;
   int err;
-  int pad;
+  unsigned int root;
+  unsigned int pad0[29];
+  unsigned int group[BAR_GROUPS][32];
 };
 
 // All CTAs of a cooperative launch meet here.  Returns false (and sets
@@ -41,10 +46,18 @@ __device__ bool grid_sync(GridBar* bar, unsigned int nblocks) {
     volatile int* verr = &bar->err;
     const unsigned int g = *vgen;
     __threadfence();
-    const unsigned int arrived = atomicAdd(&bar->count, 1u);
+    const unsigned int grp = blockIdx.x % BAR_GROUPS;
+    const unsigned int ngroups = nblocks < (unsigned)BAR_GROUPS ? nblocks : (unsigned)BAR_GROUPS;
+    const unsigned int gsize = (nblocks - grp + BAR_GROUPS - 1) / BAR_GROUPS;
+    bool last = false;
+    if (atomicAdd(&bar->group[grp][0], 1u) == gsize - 1) {
+      atomicExch(&bar->group[grp][0], 0u);
+      __threadfence();
+      last = atomicAdd(&bar->root, 1u) == ngroups - 1;
+    }
     ok = 1;
-    if (arrived == nblocks - 1) {
-      atomicExch(&bar->count, 0u);
+    if (last) {
+      atomicExch(&bar->root, 0u);
       __threadfence();
       atomicAdd(&bar->gen, 1u);
     } else {
@@ -205,13 +218,18 @@ __global__ void __launch_bounds__(512) tridiag_smem_kernel(double* A, int n, dou
   for (int k = 0; k + 2 < n; ++k) {
     const int m = n - k - 1;
     // Householder vector of column k from colbuf (rows k+1..n-1)
+    // one pass over the column: x into v (shared), its squared norm
     double s = 0.0;
-    for (int i = tid + 1; i < m; i += nt) {
+    for (int i = tid; i < m; i += nt) {
       const double x = __ldcg(&colbuf[k + 1 + i]);
-      s += x * x;
+      v[k + 1 + i] = x;
+      if (i > 0) {
+        s += x * x;
+        if (b == 0) A[(size_t)k * n + k + 1 + i] = x;  // kept for back-transformation
+      }
     }
     const double sig = block_sum(s, red);
-    const double x0 = __ldcg(&colbuf[k + 1]);
+    const double x0 = v[k + 1];
     double alpha, t, v0;
     if (sig == 0.0) {
       alpha = x0;
@@ -223,10 +241,10 @@ __global__ void __launch_bounds__(512) tridiag_smem_kernel(double* A, int n, dou
       v0 = x0 - alpha;
       t = 2.0 / (v0 * v0 + sig);
     }
-    for (int i = tid; i < m; i += nt) {
-      const double vi = (i == 0) ? v0 : __ldcg(&colbuf[k + 1 + i]);
-      v[k + 1 + i] = vi;
-      if (b == 0) A[(size_t)k * n + k + 1 + i] = vi;  // kept for back-transformation
+    __syncthreads();   // every thread has read x0 before it is replaced by v0
+    if (tid == 0) {
+      v[k + 1] = v0;
+      if (b == 0) A[(size_t)k * n + k + 1] = v0;
     }
     if (tid == 0) {
       if (k % nb == b) d[k] = rows[(size_t)(k / nb) * n + k];

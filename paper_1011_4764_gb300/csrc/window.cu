@@ -375,7 +375,7 @@ ofm_status ofm_window_factor(ofm_ctx* c) {
   OFM_CUDA(c, cudaMemcpyAsync(L, c->dense_S.p, bytes, cudaMemcpyDeviceToDevice, s));
   OFM_CUDA(c, cudaMemsetAsync(flag, 0xff, sizeof(int), s));  // -1: no failure
   // 1. Cholesky
-  { KTimer kt(c, KC_CHOL, 0);
+  { KTimer kt(c, KC_CHOL, 0, 0.0, (double)n * n * n / 3.0);  // algorithmic n^3/3 flops
   for (int k0 = 0; k0 < n; k0 += NB) {
     kt.add(1);
     const int kb = std::min(NB, n - k0);
@@ -403,7 +403,7 @@ ofm_status ofm_window_factor(ofm_ctx* c) {
   double* T = (double*)c->dense_H.p;  // kept intact: work on a copy
   OFM_CUDA(c, cudaMemcpyAsync(A, T, bytes, cudaMemcpyDeviceToDevice, s));
   {
-  KTimer kt(c, KC_REDUCE, 2 + 4 * ((n + NB - 1) / NB));
+  KTimer kt(c, KC_REDUCE, 2 + 4 * ((n + NB - 1) / NB), 0.0, (double)n * n * n);  // algorithmic (dsygst) n^3 flops
   trsm_lower_left(L, A, n, s);
   OFM_TRY(ofm_ensure(c, c->w_eval, bytes, "window scratch"));
   double* X = (double*)c->w_eval.p;
@@ -421,7 +421,7 @@ ofm_status ofm_window_factor(ofm_ctx* c) {
   double* vbuf = (double*)c->w_tmp.p;
   double* p = vbuf + n;
   {
-  KTimer kt(c, KC_TRIDIAG, 0);
+  KTimer kt(c, KC_TRIDIAG, 0, 0.0, 4.0 / 3.0 * n * n * n);  // algorithmic (dsytrd) 4n^3/3 flops
   const ofm_status ps = ofm_tridiag_persistent(c, A, n, d, e, tau, p);
   if (ps == OFM_OK) {
     kt.add(1);
