@@ -44,7 +44,8 @@ def parse_args():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="alkane")
-    p.add_argument("--precision", default="fp32")
+    p.add_argument("--precision", default="bf16x3",
+                   help="pair-contraction arithmetic: fp64 fp32 tf32 bf16 bf16x3")
     p.add_argument("--no-extras", action="store_true", help="skip e2e, FP64 reference and sweeps")
     p.add_argument("--eig-degree", type=int, default=0, help="Chebyshev degree (0 = library default)")
     p.add_argument("--eig-extra", type=int, default=0, help="guard vectors (0 = library default)")

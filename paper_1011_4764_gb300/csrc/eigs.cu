@@ -832,7 +832,7 @@ extern "C" ofm_status ofm_fragment_eigs(ofm_ctx* c, const ofm_eig_opts* opts, do
   const bool fp64 = c->storage == OFM_STORE_FP64;
   const double tol = o.tol > 0 ? o.tol : (fp64 ? 1e-9 : 1e-5);
   const int max_iter = o.max_iter > 0 ? o.max_iter : 60;
-  const int degree = o.degree > 0 ? o.degree : 12;
+  const int degree = o.degree > 0 ? o.degree : 32;
   if (o.tol < 0 || o.max_iter < 0 || o.degree < 0 || o.extra_states < 0 || degree > 200)
     return ofm_fail(c, OFM_ERR_INVALID, "bad eigensolver options");
   if (!c->eig || !c->eig->ready || c->eig->efr.size() != (size_t)c->nfrag || o.extra_states > 0) {

@@ -24,54 +24,39 @@
 
 namespace ofm {
 
-// Two-level barrier state: CTAs arrive on one of BAR_GROUPS counters (each
-// on its own 128-byte line); the last arrival of a group arrives on the root
-// counter; the last root arrival advances the generation everyone waits on.
-constexpr int BAR_GROUPS = 4;
+// Barrier state: a counter that only grows (one arrival per CTA per
+// barrier), so the k-th barrier completes when the counter reaches
+// k * nblocks; no reset is ever needed.
 struct GridBar {
-  unsigned int gen;
+  unsigned int count;
   int err;
-  unsigned int root;
-  unsigned int pad0[29];
-  unsigned int group[BAR_GROUPS][32];
+  unsigned int pad[30];
 };
 
-// All CTAs of a cooperative launch meet here.  Returns false (and sets
-// bar->err) when the wait exceeded its bound or another CTA gave up.
+// All CTAs of a cooperative launch meet here: one release atomic per CTA
+// and acquire polls of the counter.  Returns false (and sets bar->err) when
+// the wait exceeded its bound or another CTA gave up.
 __device__ bool grid_sync(GridBar* bar, unsigned int nblocks) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned int* vgen = &bar->gen;
     volatile int* verr = &bar->err;
-    const unsigned int g = *vgen;
-    __threadfence();
-    const unsigned int grp = blockIdx.x % BAR_GROUPS;
-    const unsigned int ngroups = nblocks < (unsigned)BAR_GROUPS ? nblocks : (unsigned)BAR_GROUPS;
-    const unsigned int gsize = (nblocks - grp + BAR_GROUPS - 1) / BAR_GROUPS;
-    bool last = false;
-    if (atomicAdd(&bar->group[grp][0], 1u) == gsize - 1) {
-      atomicExch(&bar->group[grp][0], 0u);
-      __threadfence();
-      last = atomicAdd(&bar->root, 1u) == ngroups - 1;
-    }
+    unsigned int old;
+    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], 1;" : "=r"(old) : "l"(&bar->count) : "memory");
+    const unsigned int target = (old / nblocks + 1u) * nblocks;
     ok = 1;
-    if (last) {
-      atomicExch(&bar->root, 0u);
-      __threadfence();
-      atomicAdd(&bar->gen, 1u);
-    } else {
-      unsigned int spins = 0;
-      while (*vgen == g) {
-        if (*verr != 0 || ++spins > (1u << 24)) {
-          atomicExch(&bar->err, 1);
-          ok = 0;
-          break;
-        }
-        if (spins > 32) __nanosleep(64);
+    unsigned int spins = 0;
+    while (true) {
+      unsigned int cur;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(&bar->count) : "memory");
+      if ((int)(cur - target) >= 0) break;
+      if (*verr != 0 || ++spins > (1u << 24)) {
+        atomicExch(&bar->err, 1);
+        ok = 0;
+        break;
       }
+      if (spins > 64) __nanosleep(32);
     }
-    __threadfence();
   }
   __syncthreads();
   return ok != 0;
