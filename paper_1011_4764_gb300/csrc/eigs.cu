@@ -51,7 +51,7 @@ struct EigWork {
   long long gblk = 0;
   DevBuf d_efr, d_cta, buf[4], coef, theta, res, Cm, work, blocks, partials, d_gpairs, d_gpieces,
       d_gitems, d_toff, d_rank, d_vmax, rpart;
-  double vmax = 0.0;
+  double vlim[2] = {0.0, 0.0};        // max V, min V
   size_t rr_smem = 0, rot_smem = 0;   // dynamic shared memory of the two kernels
   int rot_blocks = 1;
   int fgrid = 1;                      // grid width of the filter launches
@@ -630,18 +630,32 @@ __global__ void __launch_bounds__(1024) export_states_kernel(const DevFrag* efr,
   }
 }
 
+// out[0] = max V, out[1] = min V
 template <typename T>
 __global__ void vmax_kernel(const T* V, long long n, double* out) {
-  __shared__ double red[32];
-  double m = -DBL_MAX;
-  for (long long i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, (double)V[i]);
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __shared__ double red[32], redm[32];
+  double m = -DBL_MAX, mn = DBL_MAX;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+    m = fmax(m, (double)V[i]);
+    mn = fmin(mn, (double)V[i]);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    mn = fmin(mn, __shfl_down_sync(0xffffffffu, mn, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5] = m;
+    redm[threadIdx.x >> 5] = mn;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t = -DBL_MAX;
-    for (int w = 0; w < (int)blockDim.x / 32; ++w) t = fmax(t, red[w]);
-    *out = t;
+    double t = -DBL_MAX, tm = DBL_MAX;
+    for (int w = 0; w < (int)blockDim.x / 32; ++w) {
+      t = fmax(t, red[w]);
+      tm = fmin(tm, redm[w]);
+    }
+    out[0] = t;
+    out[1] = tm;
   }
 }
 
@@ -715,7 +729,7 @@ static ofm_status eig_setup(ofm_ctx* c, int guard_opt) {
   OFM_TRY(ofm_ensure(c, w->theta, sizeof(double) * w->tsum, "Ritz values"));
   OFM_TRY(ofm_ensure(c, w->res, sizeof(double) * w->tsum, "residuals"));
   OFM_TRY(ofm_ensure(c, w->d_rank, sizeof(int) * nf, "ranks"));
-  OFM_TRY(ofm_ensure(c, w->d_vmax, sizeof(double), "max V"));
+  OFM_TRY(ofm_ensure(c, w->d_vmax, 2 * sizeof(double), "max and min V"));
   const long long mm = (long long)w->mmax * w->mmax;
   OFM_TRY(ofm_ensure(c, w->Cm, sizeof(double) * mm * nf, "Ritz coefficients"));
   OFM_TRY(ofm_ensure(c, w->work, sizeof(double) * (3 * mm + 3 * w->mmax + 8) * nf, "Rayleigh-Ritz work"));
@@ -736,7 +750,7 @@ static ofm_status eig_setup(ofm_ctx* c, int guard_opt) {
   if (fp64) vmax_kernel<double><<<1, 1024, 0, s>>>((const double*)c->V.p, npts, (double*)w->d_vmax.p);
   else vmax_kernel<float><<<1, 1024, 0, s>>>((const float*)c->V.p, npts, (double*)w->d_vmax.p);
   OFM_CUDA(c, cudaGetLastError());
-  OFM_CUDA(c, cudaMemcpyAsync(&w->vmax, w->d_vmax.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+  OFM_CUDA(c, cudaMemcpyAsync(w->vlim, w->d_vmax.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
   OFM_CUDA(c, cudaStreamSynchronize(s));
   long long maxP = 0;
   for (auto& E : w->efr) maxP = std::max<long long>(maxP, (long long)E.ext[0] * E.ext[1] * E.ext[2]);
@@ -867,7 +881,10 @@ extern "C" ofm_status ofm_fragment_eigs(ofm_ctx* c, const ofm_eig_opts* opts, do
   OFM_TRY(eig_rr(c, 0, 3, 1, 2, 0x1234ULL + o.seed));
   int xb = 1;
   std::vector<double> th(w->tsum), rs(w->tsum);
-  const double bup = 6.0 / (c->grid.h * c->grid.h) + w->vmax;
+  const double bup = 6.0 / (c->grid.h * c->grid.h) + w->vlim[0];
+  // the filter may spread the wanted part of the block by at most this
+  // factor (relative to the arithmetic's resolution), which caps the degree
+  const double spread_max = std::log(fp64 ? 1e8 : 1e4);
   bool converged = false;
   int it = 0;
   for (; it <= max_iter; ++it) {
@@ -882,6 +899,26 @@ extern "C" ofm_status ofm_fragment_eigs(ofm_ctx* c, const ofm_eig_opts* opts, do
           break;
         }
     if (converged || it == max_iter) break;
+    // degree of this iteration: T_d grows like exp(d acosh(t)) below the
+    // damped interval, so the ratio between the bottom of the spectrum
+    // (min V on the first pass, the lowest Ritz value after) and the last
+    // wanted Ritz value is about exp(d (acosh(t_low) - acosh(t_want)));
+    // keep it within spread_max for every fragment
+    int deg = degree;
+    for (int f = 0; f < nf; ++f) {
+      const int m = w->efr[f].n;
+      const double* t = &th[w->toff[f]];
+      double blo = t[m - 1], a0 = t[0];
+      double bu = std::max(bup, blo + 1e-3);
+      if (!(blo > a0)) blo = a0 + 1e-3 * (bu - a0);
+      const double e = 0.5 * (bu - blo), cc = 0.5 * (bu + blo);
+      const double low = (it == 0) ? std::min(w->vlim[1], a0) : a0;
+      const double tl = (cc - low) / e, tw = (cc - t[c->frags[f].n - 1]) / e;
+      if (tl > 1.0) {
+        const double gap = std::acosh(tl) - (tw > 1.0 ? std::acosh(tw) : 0.0);
+        if (gap > 0.0) deg = std::min(deg, std::max(4, (int)(spread_max / gap)));
+      }
+    }
     // filter coefficients from the current Ritz values
     for (int f = 0; f < nf; ++f) {
       const int m = w->efr[f].n;
@@ -893,7 +930,7 @@ extern "C" ofm_status ofm_fragment_eigs(ofm_ctx* c, const ofm_eig_opts* opts, do
       const double sigma1 = e / (a0 - cc);
       double sigma = sigma1;
       const double tau = 2.0 / sigma1;
-      for (int k = 0; k < degree; ++k) {
+      for (int k = 0; k < deg; ++k) {
         double* cf = &coef[3 * ((size_t)k * nf + f)];
         if (k == 0) {
           cf[0] = sigma1 / e;
@@ -907,9 +944,9 @@ extern "C" ofm_status ofm_fragment_eigs(ofm_ctx* c, const ofm_eig_opts* opts, do
         cf[2] = cc;
       }
     }
-    OFM_CUDA(c, cudaMemcpyAsync(w->coef.p, coef.data(), sizeof(double) * 3 * nf * degree, cudaMemcpyHostToDevice, s));
+    OFM_CUDA(c, cudaMemcpyAsync(w->coef.p, coef.data(), sizeof(double) * 3 * nf * deg, cudaMemcpyHostToDevice, s));
     int prev = -1, cur = xb;
-    for (int k = 0; k < degree; ++k) {
+    for (int k = 0; k < deg; ++k) {
       const int nxt = other(prev, cur);
       apply_block(c, cur, prev, nxt, d_coef + 3 * (size_t)k * nf);
       prev = cur;
