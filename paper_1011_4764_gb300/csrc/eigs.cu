@@ -883,8 +883,10 @@ extern "C" ofm_status ofm_fragment_eigs(ofm_ctx* c, const ofm_eig_opts* opts, do
   std::vector<double> th(w->tsum), rs(w->tsum);
   const double bup = 6.0 / (c->grid.h * c->grid.h) + w->vlim[0];
   // the filter may spread the wanted part of the block by at most this
-  // factor (relative to the arithmetic's resolution), which caps the degree
-  const double spread_max = std::log(fp64 ? 1e8 : 1e4);
+  // factor: components shrunk by s relative to the largest carry rounding
+  // of unit roundoff x s, which is the residual floor (FP32: 6e-8 x 100,
+  // below the default tolerance 1e-5; FP64: 1e-16 x 1e6), so s caps the degree
+  const double spread_max = std::log(fp64 ? 1e6 : 1e2);
   bool converged = false;
   int it = 0;
   for (; it <= max_iter; ++it) {
