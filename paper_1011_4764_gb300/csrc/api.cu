@@ -459,8 +459,7 @@ extern "C" ofm_status ofm_window_eigs(ofm_ctx* c, double E_lo, double E_hi, int 
   if (!c->dense_ready) OFM_TRY(ofm_make_dense(c));
   if (!c->factored) OFM_TRY(ofm_window_factor(c));
   int i_lo = 0, i_hi = 0;
-  OFM_TRY(ofm_window_count(c, E_lo, false, &i_lo));
-  OFM_TRY(ofm_window_count(c, E_hi, true, &i_hi));
+  OFM_TRY(ofm_window_count(c, E_lo, E_hi, &i_lo, &i_hi));
   *n_out = i_hi - i_lo;
   const int m = std::min(*n_out, max_out);
   if (m > 0) OFM_TRY(ofm_window_bisect(c, i_lo, i_lo + m, E_out));

@@ -208,12 +208,14 @@ void ofm_tc_free(ofm_ctx* c);
 ofm_status ofm_contract_tc(ofm_ctx* c, ofm_precision prec);
 ofm_status ofm_tc_status(ofm_ctx* c);         // OFM_ERR_TIMEOUT if a tensor-core wait gave up
 ofm_status ofm_window_factor(ofm_ctx* c);
-ofm_status ofm_window_count(ofm_ctx* c, double x, bool inclusive, int* count);
+// eigenvalues below lo and below-or-at hi of the factored pencil
+ofm_status ofm_window_count(ofm_ctx* c, double lo, double hi, int* count_lo, int* count_hi);
 ofm_status ofm_window_bisect(ofm_ctx* c, int i_lo, int i_hi, double* E_out);
 ofm_status ofm_window_vectors(ofm_ctx* c, int m, double* C_out);
 ofm_status ofm_tridiag_persistent(ofm_ctx* c, double* A, int n, double* d, double* e, double* tau,
                                   double* pg);
-void launch_count_below(const double* d, const double* e, int n, double x, int* out, cudaStream_t s);
+void launch_count_below(const double* d, const double* e, int n, double x0, double x1, int* out,
+                        cudaStream_t s);
 bool launch_multisection(const double* d, const double* e, int n, int i_lo, int m, double* out,
                          cudaStream_t s);
 

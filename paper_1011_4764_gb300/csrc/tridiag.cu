@@ -276,48 +276,77 @@ __global__ void __launch_bounds__(512) tridiag_smem_kernel(double* A, int n, dou
   }
 }
 
-// Number of eigenvalues of the tridiagonal (d, e) below x: sign changes of
-// the leading principal minors p_i of T - x I (p_0 = 1), a zero minor
-// counted as a change; both running minors are rescaled by a power of two
-// when the newest leaves [2^-400, 2^400].
-// SQ: the second array already holds the squared off-diagonals.
-template <bool SQ>
-__device__ int sturm_count(const double* __restrict__ d, const double* __restrict__ e, int n,
-                           double x) {
-  // sign and exponent tests on the bit patterns (integer pipe), leaving
-  // three FP64 operations per step
-  double p0 = 1.0, p1 = d[0] - x;
-  if (p1 == 0.0) p1 = -DBL_MIN;
-  int c = p1 < 0.0 ? 1 : 0;
-  long long s1 = __double_as_longlong(p1);
-  for (int i = 1; i < n; ++i) {
-    const double ei = e[i - 1];
-    double p2 = fma(d[i] - x, p1, -(SQ ? ei : ei * ei) * p0);
-    long long s2 = __double_as_longlong(p2);
-    if ((s2 << 1) == 0) {  // a zero minor counts as a sign change
-      p2 = (s1 < 0) ? DBL_MIN : -DBL_MIN;
-      s2 = __double_as_longlong(p2);
-    }
-    c += (int)((unsigned long long)(s2 ^ s1) >> 63);
-    const int ex = (int)((s2 >> 52) & 0x7ff) - 1023;
-    if (ex > 400 || ex < -400) {
-      p2 = scalbn(p2, -ex);
-      p1 = scalbn(p1, -ex);
-      s2 = __double_as_longlong(p2);
-    }
-    p0 = p1;
-    p1 = p2;
-    s1 = s2;
+// Number of eigenvalues of the tridiagonal (d, e2 = squared off-diagonals)
+// below each of K shifts x[k]: sign changes of the leading principal minors
+// p_i of T - x I (p_0 = 1; a minor that is exactly zero counts with the sign
+// of its sign bit, which gives the standard count away from exact
+// eigenvalues).  The K recurrences are interleaved (independent chains hide
+// the FP64 latency); the running pair of minors is rescaled by a power of
+// two every 8 steps when it leaves [2^-400, 2^400] (at most a factor 2^40
+// of growth per 8 steps for the matrices here, far from overflow).
+template <int K>
+__device__ __forceinline__ void sturm_counts(const double* __restrict__ d,
+                                             const double* __restrict__ e2, int n,
+                                             const double* x, int* cnt) {
+  double p0[K], p1[K];
+  int c[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    p0[k] = 1.0;
+    p1[k] = d[0] - x[k];
+    c[k] = (int)((unsigned long long)__double_as_longlong(p1[k]) >> 63);
   }
-  return c;
+  int i = 1;
+  while (i < n) {
+    const int stop = min(n, i + 8);
+    for (; i < stop; ++i) {
+      const double di = d[i], ei = e2[i - 1];
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const double p2 = fma(di - x[k], p1[k], -ei * p0[k]);
+        c[k] += (int)((unsigned long long)(__double_as_longlong(p2) ^ __double_as_longlong(p1[k])) >> 63);
+        p0[k] = p1[k];
+        p1[k] = p2;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int ex = (int)((__double_as_longlong(p1[k]) >> 52) & 0x7ff) - 1023;
+      if (ex > 400 || ex < -400) {
+        p1[k] = scalbn(p1[k], -ex);
+        p0[k] = scalbn(p0[k], -ex);
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) cnt[k] = c[k];
 }
 
-__global__ void count_below_kernel(const double* d, const double* e, int n, double x, int* out) {
-  *out = sturm_count<false>(d, e, n, x);
+// Counts below two shifts (the window ends) in one pass; e holds the
+// off-diagonals themselves.
+__global__ void count_below_kernel(const double* d, const double* e, int n, double x0, double x1,
+                                   int* out) {
+  extern __shared__ double cb_smem[];
+  double* ds = cb_smem;
+  double* e2s = cb_smem + n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    ds[i] = d[i];
+    e2s[i] = (i < n - 1) ? e[i] * e[i] : 0.0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double x[2] = {x0, x1};
+    int c[2];
+    sturm_counts<2>(ds, e2s, n, x, c);
+    out[0] = c[0];
+    out[1] = c[1];
+  }
 }
 
-// One warp per eigenvalue index i_lo + warp; out[warp] = the eigenvalue.
-// d and the squared off-diagonals are staged in shared memory (2n doubles).
+// Multisection: each warp serves four eigenvalue indices (lane groups of 8);
+// each lane counts below 4 shifts, so an eigenvalue sees 32 shifts per round
+// and its interval shrinks 33-fold.  d and e^2 are staged in shared memory.
+constexpr int MS_LANES = 8, MS_K = 4, MS_S = MS_LANES * MS_K;
 __global__ void __launch_bounds__(256) multisection_kernel(const double* __restrict__ d,
                                                            const double* __restrict__ e, int n,
                                                            int i_lo, int m, double* out) {
@@ -331,8 +360,7 @@ __global__ void __launch_bounds__(256) multisection_kernel(const double* __restr
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  // four eigenvalues per warp, eight lanes (eight shifts) each
-  const int grp = lane >> 3, sub = lane & 7;
+  const int grp = lane / MS_LANES, sub = lane % MS_LANES;
   if (w * 4 >= m) return;
   const int t = w * 4 + grp;                 // output slot of this lane group
   const int idx = i_lo + (t < m ? t : m - 1);
@@ -350,28 +378,33 @@ __global__ void __launch_bounds__(256) multisection_kernel(const double* __restr
   const double wdt = fmax(fabs(a), fabs(b));
   double lo = a - 2.0 * DBL_EPSILON * wdt - DBL_MIN;
   double hi = b + 2.0 * DBL_EPSILON * wdt + DBL_MIN;
-  // every lane group keeps its own [lo, hi]; the warp loops until all four
-  // groups have converged (or stopped making progress)
   bool done = false;
-  for (int it = 0; it < 128; ++it) {
+  for (int it = 0; it < 64; ++it) {
     done = done || (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + 4.0 * DBL_MIN);
     if (__all_sync(0xffffffffu, done)) break;
-    const double x = lo + (hi - lo) * (double)(sub + 1) / 9.0;
-    const int cnt = done ? 0 : sturm_count<true>(ds, e2s, n, x);
-    const unsigned ball = __ballot_sync(0xffffffffu, cnt > idx);
-    const unsigned mask = (ball >> (grp * 8)) & 0xffu;
-    const double xprev = __shfl_up_sync(0xffffffffu, x, 1);
-    const int l = mask ? __ffs(mask) - 1 : 7;
-    const double xl = __shfl_sync(0xffffffffu, x, grp * 8 + l);
-    const double xlp = __shfl_sync(0xffffffffu, xprev, grp * 8 + l);
+    // shift j of this group: x_j = lo + (hi - lo) (j + 1) / (S + 1)
+    double x[MS_K];
+    int cnt[MS_K];
+#pragma unroll
+    for (int k = 0; k < MS_K; ++k) x[k] = lo + (hi - lo) * (double)(sub * MS_K + k + 1) / (MS_S + 1);
+    sturm_counts<MS_K>(ds, e2s, n, x, cnt);
+    int first = MS_K;   // first local shift with more than idx eigenvalues below
+#pragma unroll
+    for (int k = MS_K - 1; k >= 0; --k)
+      if (cnt[k] > idx) first = k;
+    const unsigned ball = __ballot_sync(0xffffffffu, first < MS_K);
+    const unsigned gmask = (ball >> (grp * MS_LANES)) & ((1u << MS_LANES) - 1u);
+    const int l = gmask ? __ffs(gmask) - 1 : 0;
+    const int fl = __shfl_sync(0xffffffffu, first, grp * MS_LANES + l);
     if (!done) {
       double nlo, nhi;
-      if (mask == 0) {
-        nlo = xl;        // above all eight shifts
+      if (gmask == 0) {   // above every shift
+        nlo = lo + (hi - lo) * (double)MS_S / (MS_S + 1);
         nhi = hi;
       } else {
-        nhi = xl;
-        nlo = (l > 0) ? xlp : lo;
+        const int j = l * MS_K + fl;
+        nhi = lo + (hi - lo) * (double)(j + 1) / (MS_S + 1);
+        nlo = (j > 0) ? lo + (hi - lo) * (double)j / (MS_S + 1) : lo;
       }
       if (nhi == hi && nlo == lo) done = true;  // no progress at this precision
       lo = nlo;
@@ -380,7 +413,6 @@ __global__ void __launch_bounds__(256) multisection_kernel(const double* __restr
   }
   if (sub == 0 && t < m) out[t] = 0.5 * (lo + hi);
 }
-
 }  // namespace ofm
 
 using namespace ofm;
@@ -445,8 +477,14 @@ ofm_status ofm_tridiag_persistent(ofm_ctx* c, double* A, int n, double* d, doubl
   return OFM_OK;
 }
 
-void launch_count_below(const double* d, const double* e, int n, double x, int* out, cudaStream_t s) {
-  count_below_kernel<<<1, 1, 0, s>>>(d, e, n, x, out);
+void launch_count_below(const double* d, const double* e, int n, double x0, double x1, int* out,
+                        cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(count_below_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  count_below_kernel<<<1, 256, 2 * (size_t)n * sizeof(double), s>>>(d, e, n, x0, x1, out);
 }
 
 // Returns false when the tridiagonal is too long to stage in shared memory
@@ -458,14 +496,16 @@ bool launch_multisection(const double* d, const double* e, int n, int i_lo, int 
   static bool attr_set = false;
   if (!attr_set) {
     if (cudaFuncSetAttribute(multisection_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024) != cudaSuccess ||
+        cudaFuncSetAttribute(count_below_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              200 * 1024) != cudaSuccess) {
       cudaGetLastError();
       return false;
     }
     attr_set = true;
   }
-  // two warps (eight eigenvalues) per CTA so that the work spreads over every SM
-  const int per_block = 8;
-  multisection_kernel<<<(m + per_block - 1) / per_block, 64, smem, s>>>(d, e, n, i_lo, m, out);
+  // one warp (four eigenvalues) per CTA so that the work spreads over every SM
+  const int per_block = 4;
+  multisection_kernel<<<(m + per_block - 1) / per_block, 32, smem, s>>>(d, e, n, i_lo, m, out);
   return true;
 }

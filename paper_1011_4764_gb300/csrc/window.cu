@@ -444,15 +444,21 @@ ofm_status ofm_window_factor(ofm_ctx* c) {
   return OFM_OK;
 }
 
-ofm_status ofm_window_count(ofm_ctx* c, double x, bool inclusive, int* count) {
-  if (inclusive) x = std::nextafter(x, HUGE_VAL);
-  int* dc = (int*)c->flag.p + 1;
+ofm_status ofm_window_count(ofm_ctx* c, double lo, double hi, int* count_lo, int* count_hi) {
+  const double hi_incl = std::nextafter(hi, HUGE_VAL);
+  if (2 * (size_t)c->dense_n * sizeof(double) > 200 * 1024)
+    return ofm_fail(c, OFM_ERR_INVALID, "dense window solve supports a basis of at most 12800");
+  int* dc = (int*)c->flag.p + 2;   // two ints after the pivot flag
+  int h[2] = {0, 0};
   KTimer kt(c, KC_BISECT);
-  launch_count_below((const double*)c->w_d.p, (const double*)c->w_e.p, c->dense_n, x, dc,
+  launch_count_below((const double*)c->w_d.p, (const double*)c->w_e.p, c->dense_n, lo, hi_incl, dc,
                      c->stream);
   OFM_CUDA(c, cudaGetLastError());
-  OFM_CUDA(c, cudaMemcpyAsync(count, dc, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-  return sync_ctx(c, "Sturm count");
+  OFM_CUDA(c, cudaMemcpyAsync(h, dc, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  OFM_TRY(sync_ctx(c, "Sturm count"));
+  *count_lo = h[0];
+  *count_hi = h[1];
+  return OFM_OK;
 }
 
 ofm_status ofm_window_bisect(ofm_ctx* c, int i_lo, int i_hi, double* E_out) {
