@@ -343,10 +343,16 @@ __global__ void count_below_kernel(const double* d, const double* e, int n, doub
   }
 }
 
-// Multisection: each warp serves four eigenvalue indices (lane groups of 8);
-// each lane counts below 4 shifts, so an eigenvalue sees 32 shifts per round
-// and its interval shrinks 33-fold.  d and e^2 are staged in shared memory.
-constexpr int MS_LANES = 8, MS_K = 4, MS_S = MS_LANES * MS_K;
+// Multisection: lane groups of MS_LANES serve one eigenvalue index each and
+// every lane counts below MS_K shifts, so an eigenvalue sees MS_S shifts per
+// round and its interval shrinks (MS_S + 1)-fold.  One eigenvalue per warp
+// (32 lanes, one shift each): a warp's FP64 instructions occupy the FP64
+// pipe of its SM sub-partition for about 64 cycles each on this part, so
+// the work is spread over as many warps (sub-partitions) as there are
+// eigenvalues.  d and e^2 are staged in shared memory.
+constexpr int MS_LANES = 32, MS_K = 1, MS_S = MS_LANES * MS_K;
+constexpr int MS_GPW = 32 / MS_LANES;   // eigenvalues per warp
+constexpr unsigned MS_GMASK = MS_LANES == 32 ? 0xffffffffu : ((1u << MS_LANES) - 1u);
 __global__ void __launch_bounds__(256) multisection_kernel(const double* __restrict__ d,
                                                            const double* __restrict__ e, int n,
                                                            int i_lo, int m, double* out) {
@@ -361,8 +367,8 @@ __global__ void __launch_bounds__(256) multisection_kernel(const double* __restr
   const int lane = threadIdx.x & 31;
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int grp = lane / MS_LANES, sub = lane % MS_LANES;
-  if (w * 4 >= m) return;
-  const int t = w * 4 + grp;                 // output slot of this lane group
+  if (w * MS_GPW >= m) return;
+  const int t = w * MS_GPW + grp;            // output slot of this lane group
   const int idx = i_lo + (t < m ? t : m - 1);
   // Gershgorin interval
   double a = DBL_MAX, b = -DBL_MAX;
@@ -393,7 +399,7 @@ __global__ void __launch_bounds__(256) multisection_kernel(const double* __restr
     for (int k = MS_K - 1; k >= 0; --k)
       if (cnt[k] > idx) first = k;
     const unsigned ball = __ballot_sync(0xffffffffu, first < MS_K);
-    const unsigned gmask = (ball >> (grp * MS_LANES)) & ((1u << MS_LANES) - 1u);
+    const unsigned gmask = (ball >> (grp * MS_LANES)) & MS_GMASK;
     const int l = gmask ? __ffs(gmask) - 1 : 0;
     const int fl = __shfl_sync(0xffffffffu, first, grp * MS_LANES + l);
     if (!done) {
@@ -504,8 +510,8 @@ bool launch_multisection(const double* d, const double* e, int n, int i_lo, int 
     }
     attr_set = true;
   }
-  // one warp (four eigenvalues) per CTA so that the work spreads over every SM
-  const int per_block = 4;
-  multisection_kernel<<<(m + per_block - 1) / per_block, 32, smem, s>>>(d, e, n, i_lo, m, out);
+  // four warps per CTA, MS_GPW eigenvalues per warp
+  const int per_block = 4 * MS_GPW;
+  multisection_kernel<<<(m + per_block - 1) / per_block, 128, smem, s>>>(d, e, n, i_lo, m, out);
   return true;
 }

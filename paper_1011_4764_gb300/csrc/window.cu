@@ -350,7 +350,9 @@ static ofm_status sync_ctx(ofm_ctx* c, const char* what) {
 static void trsm_lower_left(const double* L, double* B, int n, cudaStream_t s) {
   for (int k0 = 0; k0 < n; k0 += NB) {
     const int kb = std::min(NB, n - k0);
-    trsm_diag_rows_kernel<<<(n + 127) / 128, 128, 0, s>>>(L, B, n, k0, kb);
+    // one warp per CTA: each thread runs a serial FP64 substitution, so the
+    // columns are spread over as many SMs as possible
+    trsm_diag_rows_kernel<<<(n + 31) / 32, 32, 0, s>>>(L, B, n, k0, kb);
     const int rows = n - k0 - kb;
     if (rows > 0) {
       dim3 g((n + 63) / 64, (rows + 63) / 64);
@@ -382,7 +384,7 @@ ofm_status ofm_window_factor(ofm_ctx* c) {
     potrf_diag_kernel<<<1, dim3(32, 32), 0, s>>>(L, n, k0, kb, flag);
     const int rows = n - k0 - kb;
     if (rows > 0) {
-      trsm_panel_kernel<<<(rows + 127) / 128, 128, 0, s>>>(L, n, k0, kb);
+      trsm_panel_kernel<<<(rows + 31) / 32, 32, 0, s>>>(L, n, k0, kb);
       const int tb = (rows + NB - 1) / NB;
       syrk_update_kernel<<<dim3(tb, tb), dim3(32, 32), 0, s>>>(L, n, k0, kb);
       kt.add(2);
