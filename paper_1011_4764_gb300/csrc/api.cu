@@ -134,7 +134,7 @@ extern "C" void ofm_destroy(ofm_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
   ofm_prof_release(c);
-  DevBuf* bufs[] = {&c->V, &c->states, &c->hphi, &c->d_frags, &c->d_apply_start, &c->d_pairs,
+  DevBuf* bufs[] = {&c->V, &c->states, &c->hphi, &c->d_frags, &c->d_pairs,
                     &c->d_pieces, &c->d_items, &c->partials, &c->blocks, &c->dense_H,
                     &c->dense_S, &c->staging, &c->flag, &c->w_A, &c->w_L, &c->w_d, &c->w_e,
                     &c->w_tau, &c->w_tmp, &c->w_eval, &c->w_bar};
@@ -216,7 +216,7 @@ extern "C" ofm_status ofm_build_fragments(ofm_ctx* c, const ofm_grid* grid, cons
 
   // H-apply launch: 2-D grid (chunks of the largest fragment x fragments)
   if (n_frag > 65535) return ofm_fail(c, OFM_ERR_INVALID, "at most 65535 fragments");
-  c->apply_total_ctas = apply_grid_x(c->frags, es == 8);
+  c->agrid = apply_grid(c->frags, es == 8, false);
 
   // SIMT contraction plan: about 8 work items per SM
   long long chunk = std::max<long long>(256, c->kh / (8 * 152));
@@ -308,7 +308,7 @@ extern "C" ofm_status ofm_get_hphi(ofm_ctx* c, int b, double* out) {
 
 ofm_status ofm_apply_h(ofm_ctx* c) {
   KTimer t(c, KC_APPLY, 1, c->apply_bytes);
-  launch_apply_global((const DevFrag*)c->d_frags.p, c->nfrag, c->apply_total_ctas, c->V.p,
+  launch_apply_global((const DevFrag*)c->d_frags.p, c->nfrag, c->agrid, c->V.p,
                       c->states.p, c->hphi.p, c->grid.n, c->grid.h,
                       c->storage == OFM_STORE_FP64, c->stream);
   return check_launch(c, "apply H");

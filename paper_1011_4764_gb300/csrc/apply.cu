@@ -8,9 +8,9 @@
 // non-zero.  Storage is point-major (the n states of one point are adjacent),
 // so one thread owns 16 bytes of states of one point and every neighbour
 // access of a warp is a contiguous run: the kernel is a streaming stencil,
-// bound by HBM bandwidth.  The launch grid is 2-D: blockIdx.y is the
-// fragment, blockIdx.x a chunk of its (point, 16-byte column group)
-// elements, each thread handling APPLY_EPT of them.
+// bound by HBM bandwidth.  The launch grid is 3-D: blockIdx.y is the
+// fragment, blockIdx.x a chunk of its (x, y, 16-byte column group) elements
+// and blockIdx.z a chunk of z planes that each thread marches through.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -50,80 +50,128 @@ __device__ __forceinline__ int nb_index(int p, int c, int ext, int full, int dir
   return p + (c2 - c) * stride;
 }
 
-// Stencil sum over the six neighbours of point p (coordinates x, y, z) for
-// the column group q.
-template <typename T>
-__device__ __forceinline__ typename Vec16<T>::type neighbour_sum(
-    const typename Vec16<T>::type* __restrict__ S, const DevFrag& F, int p, int x, int y, int z,
-    int q, int qpp) {
-  using V16 = typename Vec16<T>::type;
-  const int ex = F.dext[0], ey = F.dext[1], ez = F.dext[2];
-  // branch-free: a neighbour outside the storage box reads the point itself
-  // with weight 0, so all six loads can be in flight at once
-  int nb[6];
-  nb[0] = nb_index(p, x, ex, F.full[0], +1, 1);
-  nb[1] = nb_index(p, x, ex, F.full[0], -1, 1);
-  nb[2] = nb_index(p, y, ey, F.full[1], +1, ex);
-  nb[3] = nb_index(p, y, ey, F.full[1], -1, ex);
-  nb[4] = nb_index(p, z, ez, F.full[2], +1, ex * ey);
-  nb[5] = nb_index(p, z, ez, F.full[2], -1, ex * ey);
-  V16 v[6];
-#pragma unroll
-  for (int i = 0; i < 6; ++i) v[i] = S[(nb[i] >= 0 ? nb[i] : p) * qpp + q];
-  V16 sum = zero4(T());
-#pragma unroll
-  for (int i = 0; i < 6; ++i) sum = fma4(nb[i] >= 0 ? T(1) : T(0), v[i], sum);
-  return sum;
-}
-
-constexpr int APPLY_EPT = 4;   // 16-byte elements per thread
-
-// a1: H phi on every point of the dilated boxes.
-template <typename T>
-__global__ void __launch_bounds__(256) apply_global_kernel(const DevFrag* __restrict__ fr,
-                                                           const T* __restrict__ V,
-                                                           const T* __restrict__ states,
-                                                           T* __restrict__ hphi, int gx, int gy,
-                                                           int gz, T c0, T c1) {
+// z-marching form of both stencils: a thread owns one (x, y, 16-byte column)
+// of a fragment and walks along z, keeping the planes z-1, z, z+1 of its
+// column in registers; only the plane ahead, the four in-plane neighbours
+// (cache hits: the neighbouring threads load them as their own centre),
+// V and (filter) the previous block are loaded per output.
+// FILTER: fragment mode (interior points only, Chebyshev step);
+// otherwise the a1 apply on every point of the dilated box.
+template <typename T, bool FILTER>
+__global__ void __launch_bounds__(256) apply_zmarch_kernel(
+    const DevFrag* __restrict__ fr, const T* __restrict__ V, const T* __restrict__ in,
+    const T* __restrict__ prev, T* __restrict__ out, const double* __restrict__ coef, int gx,
+    int gy, int gz, T c0, T c1, int zc) {
   using V16 = typename Vec16<T>::type;
   constexpr int VN = Vec16<T>::n;
   __shared__ DevFrag Fs;
+  __shared__ T cf[3];
   if (threadIdx.x == 0) Fs = fr[blockIdx.y];
+  if (FILTER && threadIdx.x < 3) cf[threadIdx.x] = (T)coef[3 * blockIdx.y + threadIdx.x];
   __syncthreads();
   const DevFrag& F = Fs;
   const int qpp = F.ld / VN;
-  const int total = (int)F.Pd * qpp;   // < 2^31: checked by the planner
-  const V16* S = reinterpret_cast<const V16*>(states + F.off);
-  V16* O = reinterpret_cast<V16*>(hphi + F.off);
-  const int ex = F.dext[0], ey = F.dext[1];
+  const int ex = F.dext[0], ey = F.dext[1], ez = F.dext[2];
+  const int e = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (e >= ex * ey * qpp) return;
+  const int pxy = e / qpp, q = e - pxy * qpp;
+  const int x = pxy % ex, y = pxy / ex;
+  if (FILTER && (x < F.lo[0] || x >= F.lo[0] + F.ext[0] || y < F.lo[1] || y >= F.lo[1] + F.ext[1]))
+    return;
+  const int plane = ex * ey;
+  // in-plane neighbours (branch-free: outside the storage box -> self, weight 0)
+  int nb[4];
+  nb[0] = nb_index(pxy, x, ex, F.full[0], +1, 1);
+  nb[1] = nb_index(pxy, x, ex, F.full[0], -1, 1);
+  nb[2] = nb_index(pxy, y, ey, F.full[1], +1, ex);
+  nb[3] = nb_index(pxy, y, ey, F.full[1], -1, ex);
+  T w[4];
 #pragma unroll
-  for (int u = 0; u < APPLY_EPT; ++u) {
-    const int e = (blockIdx.x * APPLY_EPT + u) * (int)blockDim.x + (int)threadIdx.x;
-    if (e >= total) break;
-    const int p = e / qpp, q = e - p * qpp;
-    const int x = p % ex, yz = p / ex, y = yz % ey, z = yz / ey;
-    const int X = (F.doff[0] + x) % gx, Y = (F.doff[1] + y) % gy, Z = (F.doff[2] + z) % gz;
-    const T v = V[((long long)Z * gy + Y) * gx + X];
-    const V16 ctr = S[e];
-    const V16 sum = neighbour_sum<T>(S, F, p, x, y, z, q, qpp);
-    V16 out = fma4(c0 + v, ctr, zero4(T()));
-    out = fma4(-c1, sum, out);
-    O[e] = out;
+  for (int i = 0; i < 4; ++i) {
+    w[i] = nb[i] >= 0 ? T(1) : T(0);
+    if (nb[i] < 0) nb[i] = pxy;
+  }
+  const V16* S = reinterpret_cast<const V16*>(in + F.off);
+  const V16* Pv = (FILTER && prev) ? reinterpret_cast<const V16*>(prev + F.off) : nullptr;
+  V16* O = reinterpret_cast<V16*>(out + F.off);
+  const T alpha = FILTER ? cf[0] : T(1), beta = FILTER ? cf[1] : T(0), shift = FILTER ? cf[2] : T(0);
+  // this CTA's chunk of planes (blockIdx.z): zc planes of the marched range
+  const int zb = FILTER ? F.lo[2] : 0, ze = FILTER ? F.lo[2] + F.ext[2] : ez;
+  const int z0 = zb + (int)blockIdx.z * zc;
+  const int z1 = min(ze, z0 + zc);
+  if (z0 >= z1) return;
+  const int X = (F.doff[0] + x) % gx, Y = (F.doff[1] + y) % gy;
+  const T* Vrow = V + (long long)Y * gx + X;
+  const long long vstride = (long long)gx * gy;
+  // planes below and at the start
+  auto plane_val = [&](int z) -> V16 {
+    int zz = z;
+    if (zz < 0 || zz >= ez) {
+      if (!F.full[2]) return zero4(T());
+      zz = (zz + ez) % ez;
+    }
+    return S[(zz * plane + pxy) * qpp + q];
+  };
+  V16 below = plane_val(z0 - 1);
+  V16 ctr = plane_val(z0);
+  for (int z = z0; z < z1; ++z) {
+    const V16 above = plane_val(z + 1);
+    const int base = z * plane;
+    V16 sum = add4(below, above);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) sum = fma4(w[i], S[(base + nb[i]) * qpp + q], sum);
+    const T v = Vrow[(long long)((F.doff[2] + z) % gz) * vstride];
+    V16 hy = fma4(c0 + v - shift, ctr, zero4(T()));
+    hy = fma4(-c1, sum, hy);
+    V16 o = fma4(alpha, hy, zero4(T()));
+    const int idx = (base + pxy) * qpp + q;
+    if (Pv != nullptr) o = fma4(beta, Pv[idx], o);
+    O[idx] = o;
+    below = ctr;
+    ctr = above;
   }
 }
 
-void launch_apply_global(const DevFrag* d_fr, int nfrag, int grid_x, const void* V,
+// Launch shape of the stencils: x covers the (x, y, column group) elements of
+// the largest fragment plane, y the fragments, z chunks of zc planes.  The
+// chunk count is chosen so the grid holds about two resident waves of the
+// GB300 (152 SMs x 2048 threads); each chunk re-reads only its two boundary
+// planes.
+ApplyGrid apply_grid(const std::vector<DevFrag>& fr, bool fp64, bool filter) {
+  const int vn = fp64 ? 2 : 4;
+  long long mx = 1, threads = 0;
+  int zmax = 1;
+  for (const DevFrag& f : fr) {
+    const long long xy = (long long)f.dext[0] * f.dext[1] * (f.ld / vn);
+    mx = std::max(mx, xy);
+    threads += filter ? (long long)f.ext[0] * f.ext[1] * (f.ld / vn) : xy;
+    zmax = std::max(zmax, filter ? f.ext[2] : f.dext[2]);
+  }
+  ApplyGrid g;
+  g.x = (int)((mx + 255) / 256);
+  const long long want = 2LL * 152 * 2048;
+  const long long nch = std::max(1LL, std::min<long long>(zmax, (want + threads - 1) / std::max(1LL, threads)));
+  g.zc = (int)((zmax + nch - 1) / nch);
+  g.z = (zmax + g.zc - 1) / g.zc;
+  return g;
+}
+
+template <typename T, bool FILTER>
+static void zmarch(const ApplyGrid& ag, int nfrag, const DevFrag* d_fr, const void* V,
+                   const void* in, const void* prev, void* out, const double* coef,
+                   const int gn[3], double h, cudaStream_t s) {
+  const double c0 = 3.0 / (h * h), c1 = 0.5 / (h * h);
+  dim3 g(ag.x, nfrag, ag.z);
+  apply_zmarch_kernel<T, FILTER><<<g, 256, 0, s>>>(d_fr, (const T*)V, (const T*)in,
+                                                   (const T*)prev, (T*)out, coef, gn[0], gn[1],
+                                                   gn[2], (T)c0, (T)c1, ag.zc);
+}
+
+void launch_apply_global(const DevFrag* d_fr, int nfrag, const ApplyGrid& g, const void* V,
                          const void* states, void* hphi, const int gn[3], double h, bool fp64,
                          cudaStream_t s) {
-  const double c0 = 3.0 / (h * h), c1 = 0.5 / (h * h);
-  dim3 g(grid_x, nfrag);
-  if (fp64)
-    apply_global_kernel<double><<<g, 256, 0, s>>>(d_fr, (const double*)V, (const double*)states,
-                                                  (double*)hphi, gn[0], gn[1], gn[2], c0, c1);
-  else
-    apply_global_kernel<float><<<g, 256, 0, s>>>(d_fr, (const float*)V, (const float*)states,
-                                                 (float*)hphi, gn[0], gn[1], gn[2], (float)c0,
-                                                 (float)c1);
+  if (fp64) zmarch<double, false>(g, nfrag, d_fr, V, states, nullptr, hphi, nullptr, gn, h, s);
+  else zmarch<float, false>(g, nfrag, d_fr, V, states, nullptr, hphi, nullptr, gn, h, s);
 }
 
 // a0, fragment mode: the fragment Hamiltonian is the principal submatrix of
@@ -133,69 +181,11 @@ void launch_apply_global(const DevFrag* d_fr, int nfrag, int grid_x, const void*
 //     out = alpha_f * (H_f in - c_f in) + beta_f * prev
 // with per-fragment coefficients coef[f] = (alpha, beta, c); prev may be
 // null when beta is zero.
-template <typename T>
-__global__ void __launch_bounds__(256) apply_filter_kernel(
-    const DevFrag* __restrict__ fr, const T* __restrict__ V, const T* __restrict__ in,
-    const T* __restrict__ prev, T* __restrict__ out, const double* __restrict__ coef, int gx,
-    int gy, int gz, T c0, T c1) {
-  using V16 = typename Vec16<T>::type;
-  constexpr int VN = Vec16<T>::n;
-  __shared__ DevFrag Fs;
-  __shared__ T cf[3];
-  if (threadIdx.x == 0) Fs = fr[blockIdx.y];
-  if (threadIdx.x < 3) cf[threadIdx.x] = (T)coef[3 * blockIdx.y + threadIdx.x];
-  __syncthreads();
-  const DevFrag& F = Fs;
-  const int qpp = F.ld / VN;
-  const int total = (int)F.Pd * qpp;
-  const V16* S = reinterpret_cast<const V16*>(in + F.off);
-  const V16* Pv = prev ? reinterpret_cast<const V16*>(prev + F.off) : nullptr;
-  V16* O = reinterpret_cast<V16*>(out + F.off);
-  const T alpha = cf[0], beta = cf[1], shift = cf[2];
-  const int ex = F.dext[0], ey = F.dext[1];
-#pragma unroll
-  for (int u = 0; u < APPLY_EPT; ++u) {
-    const int e = (blockIdx.x * APPLY_EPT + u) * (int)blockDim.x + (int)threadIdx.x;
-    if (e >= total) break;
-    const int p = e / qpp, q = e - p * qpp;
-    const int x = p % ex, yz = p / ex, y = yz % ey, z = yz / ey;
-    if (x < F.lo[0] || x >= F.lo[0] + F.ext[0] || y < F.lo[1] || y >= F.lo[1] + F.ext[1] ||
-        z < F.lo[2] || z >= F.lo[2] + F.ext[2])
-      continue;
-    const int X = (F.doff[0] + x) % gx, Y = (F.doff[1] + y) % gy, Z = (F.doff[2] + z) % gz;
-    const T v = V[((long long)Z * gy + Y) * gx + X];
-    const V16 ctr = S[e];
-    const V16 sum = neighbour_sum<T>(S, F, p, x, y, z, q, qpp);
-    V16 hy = fma4(c0 + v - shift, ctr, zero4(T()));
-    hy = fma4(-c1, sum, hy);
-    V16 o = fma4(alpha, hy, zero4(T()));
-    if (Pv != nullptr) o = fma4(beta, Pv[e], o);
-    O[e] = o;
-  }
-}
-
-void launch_apply_filter(const DevFrag* d_fr, int nfrag, int grid_x, const void* V, const void* in,
-                         const void* prev, void* out, const double* coef, const int gn[3],
-                         double h, bool fp64, cudaStream_t s) {
-  const double c0 = 3.0 / (h * h), c1 = 0.5 / (h * h);
-  dim3 g(grid_x, nfrag);
-  if (fp64)
-    apply_filter_kernel<double><<<g, 256, 0, s>>>(d_fr, (const double*)V, (const double*)in,
-                                                  (const double*)prev, (double*)out, coef, gn[0],
-                                                  gn[1], gn[2], c0, c1);
-  else
-    apply_filter_kernel<float><<<g, 256, 0, s>>>(d_fr, (const float*)V, (const float*)in,
-                                                 (const float*)prev, (float*)out, coef, gn[0],
-                                                 gn[1], gn[2], (float)c0, (float)c1);
-}
-
-// Grid width for the 2-D stencil launches: enough chunks for the largest
-// fragment.
-int apply_grid_x(const std::vector<DevFrag>& fr, bool fp64) {
-  const int vn = fp64 ? 2 : 4;
-  long long mx = 1;
-  for (const DevFrag& f : fr) mx = std::max<long long>(mx, f.Pd * (f.ld / vn));
-  return (int)((mx + 256LL * APPLY_EPT - 1) / (256LL * APPLY_EPT));
+void launch_apply_filter(const DevFrag* d_fr, int nfrag, const ApplyGrid& g, const void* V,
+                         const void* in, const void* prev, void* out, const double* coef,
+                         const int gn[3], double h, bool fp64, cudaStream_t s) {
+  if (fp64) zmarch<double, true>(g, nfrag, d_fr, V, in, prev, out, coef, gn, h, s);
+  else zmarch<float, true>(g, nfrag, d_fr, V, in, prev, out, coef, gn, h, s);
 }
 
 // ------------------------------------------------------------ conversions --

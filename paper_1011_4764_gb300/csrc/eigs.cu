@@ -54,7 +54,7 @@ struct EigWork {
   double vlim[2] = {0.0, 0.0};        // max V, min V
   size_t rr_smem = 0, rot_smem = 0;   // dynamic shared memory of the two kernels
   int rot_blocks = 1;
-  int fgrid = 1;                      // grid width of the filter launches
+  ApplyGrid fgrid;                    // launch shape of the filter steps
   bool ready = false;
   // algorithmic traffic / work per launch: a filter step streams the block
   // in, the previous block (three-term steps) and the block out, plus V
@@ -692,7 +692,7 @@ static ofm_status eig_setup(ofm_ctx* c, int guard_opt) {
     ctas += (E.Pd * (E.ld / vn) + 255) / 256;
   }
   w->total_ctas = (int)ctas;
-  w->fgrid = apply_grid_x(w->efr, fp64);
+  w->fgrid = apply_grid(w->efr, fp64, true);
   w->filter_b2 =w->filter_b3 = w->gram_bytes = w->gram_flops = w->rot_bytes = w->rot_flops = 0;
   for (const DevFrag& E : w->efr) {
     const double P = (double)E.ext[0] * E.ext[1] * E.ext[2];

@@ -89,17 +89,19 @@ void make_items_simt(const std::vector<DevFrag>& fr, const std::vector<HostPair>
 
 // ------------------------------------------------------------ kernels ------
 
-void launch_apply_global(const DevFrag* d_fr, int nfrag, int grid_x, const void* V,
+// launch shape of the z-marching stencils (x: plane elements, z: plane chunks)
+struct ApplyGrid { int x = 1, z = 1, zc = 1; };
+ApplyGrid apply_grid(const std::vector<DevFrag>& fr, bool fp64, bool filter);
+void launch_apply_global(const DevFrag* d_fr, int nfrag, const ApplyGrid& g, const void* V,
                          const void* states, void* hphi, const int gn[3], double h, bool fp64,
                          cudaStream_t s);
-int apply_grid_x(const std::vector<DevFrag>& fr, bool fp64);
 void launch_import_states(const DevFrag* d_fr, int a, const DevFrag& fa, const double* src,
                           void* states, bool fp64, cudaStream_t s);
 void launch_export_states(const DevFrag& fa, const void* states, double* dst, bool fp64,
                           bool dilated_hphi, cudaStream_t s);
-void launch_apply_filter(const DevFrag* d_fr, int nfrag, int grid_x, const void* V, const void* in,
-                         const void* prev, void* out, const double* coef, const int gn[3],
-                         double h, bool fp64, cudaStream_t s);
+void launch_apply_filter(const DevFrag* d_fr, int nfrag, const ApplyGrid& g, const void* V,
+                         const void* in, const void* prev, void* out, const double* coef,
+                         const int gn[3], double h, bool fp64, cudaStream_t s);
 void launch_convert_V(const double* src, void* dst, long long n, bool fp64, cudaStream_t s);
 void launch_contract_simt(int prec, bool store_fp64, const DevFrag* d_fr, const DevPair* d_pairs,
                           const Piece* d_pieces, const WorkItem* d_items, int nitems,
@@ -173,11 +175,10 @@ struct ofm_ctx {
 
   std::vector<long long> blk_off;   // per pair
   long long blk_elems = 0;
-  std::vector<int> apply_cta_start;
-  int apply_total_ctas = 0;
+  ofm::ApplyGrid agrid;                // launch shape of the a1 stencil
 
   // device buffers
-  ofm::DevBuf V, states, hphi, d_frags, d_apply_start, d_pairs, d_pieces, d_items, partials,
+  ofm::DevBuf V, states, hphi, d_frags, d_pairs, d_pieces, d_items, partials,
       blocks, dense_H, dense_S, staging, flag;
   ofm::DevBuf w_A, w_L, w_d, w_e, w_tau, w_tmp, w_eval, w_bar;   // window-solver workspaces
   int dense_n = 0;
