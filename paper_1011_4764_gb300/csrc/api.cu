@@ -121,9 +121,12 @@ extern "C" ofm_status ofm_create(ofm_ctx** out, void* cuda_stream) {
     }
     c->own_stream = true;
   }
-  if (ofm_ensure(c, c->flag, 64, "error flags") != OFM_OK) {
+  if (ofm_ensure(c, c->flag, 64, "error flags") != OFM_OK ||
+      cudaMemsetAsync(c->flag.p, 0, 64, c->stream) != cudaSuccess) {
+    if (c->flag.p) cudaFree(c->flag.p);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
+    cudaGetLastError();
     return OFM_ERR_OOM;
   }
   *out = c;
@@ -310,7 +313,8 @@ ofm_status ofm_apply_h(ofm_ctx* c) {
   KTimer t(c, KC_APPLY, 1, c->apply_bytes);
   launch_apply_global((const DevFrag*)c->d_frags.p, c->nfrag, c->agrid, c->V.p,
                       c->states.p, c->hphi.p, c->grid.n, c->grid.h,
-                      c->storage == OFM_STORE_FP64, c->stream);
+                      c->storage == OFM_STORE_FP64, (int*)c->flag.p + OFM_FLAG_STENCIL, c->stream);
+  c->stencil_check = true;
   return check_launch(c, "apply H");
 }
 
@@ -377,7 +381,7 @@ extern "C" ofm_status ofm_get_block(ofm_ctx* c, int a, int b, double* H_ab, doub
   if (!c) return OFM_ERR_INVALID;
   if (!c->assembled) return ofm_fail(c, OFM_ERR_STATE, "ofm_assemble_HS must come first");
   if (a < 0 || b < 0 || a >= c->nfrag || b >= c->nfrag) return ofm_fail(c, OFM_ERR_INVALID, "bad fragment index");
-  OFM_TRY(ofm_tc_status(c));
+  OFM_TRY(ofm_wait_status(c));
   const bool swap = a > b;
   const int lo = swap ? b : a, hi = swap ? a : b;
   const int na = c->frags[a].n, nb = c->frags[b].n;
@@ -406,7 +410,7 @@ extern "C" ofm_status ofm_get_block(ofm_ctx* c, int a, int b, double* H_ab, doub
 ofm_status ofm_make_dense(ofm_ctx* c) {
   if (c->dense_ready) return OFM_OK;
   if (!c->assembled) return ofm_fail(c, OFM_ERR_STATE, "ofm_assemble_HS must come first");
-  OFM_TRY(ofm_tc_status(c));
+  OFM_TRY(ofm_wait_status(c));
   const long long n = c->basis;
   OFM_TRY(ofm_ensure(c, c->dense_H, sizeof(double) * n * n, "dense H"));
   OFM_TRY(ofm_ensure(c, c->dense_S, sizeof(double) * n * n, "dense S"));

@@ -14,8 +14,11 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
+#include <cstring>
 
 #include "ofm_internal.h"
+#include "ptx_util.h"
 
 namespace ofm {
 
@@ -132,24 +135,270 @@ __global__ void __launch_bounds__(256) apply_zmarch_kernel(
   }
 }
 
-// Launch shape of the stencils: x covers the (x, y, column group) elements of
-// the largest fragment plane, y the fragments, z chunks of zc planes.  The
-// chunk count is chosen so the grid holds about two resident waves of the
-// GB300 (152 SMs x 2048 threads); each chunk re-reads only its two boundary
-// planes.
+// Shared-memory staged form (the default where a tile fits): a CTA owns
+// rows [y0, y1) of one fragment (every x) for a chunk of z planes.  For each
+// plane it needs, one thread issues at most three bulk copies (the staged
+// rows y0-1 .. y1 are contiguous in storage except where a full-span
+// dimension wraps) into a ring of STG_BUF plane buffers, completing on the
+// buffer's mbarrier; a slot is refilled as soon as its plane is no longer
+// needed, so up to three planes per CTA are in flight while it computes.  All six neighbours then
+// come from shared memory; V and (filter) the previous block stream from
+// global memory into registers one plane ahead of their use.  Staged rows outside a non-periodic storage box are zeroed
+// once; planes outside it complete their barrier phase without a copy and
+// are skipped in the sum.
+constexpr int STG_BUF = 5;
+constexpr int STG_THREADS = 256;
+constexpr int STG_EPT = 4;   // tile elements per thread (16 bytes each)
+
+template <typename T, bool FILTER>
+__global__ void __launch_bounds__(STG_THREADS) apply_staged_kernel(
+    const DevFrag* __restrict__ fr, const T* __restrict__ V, const T* __restrict__ in,
+    const T* __restrict__ prev, T* __restrict__ out, const double* __restrict__ coef, int gx,
+    int gy, int gz, T c0, T c1, int ty, int zc, int* flag) {
+  using namespace ptx;
+  using V16 = typename Vec16<T>::type;
+  constexpr int VN = Vec16<T>::n;
+  extern __shared__ __align__(128) unsigned char stg_smem[];
+  __shared__ DevFrag Fs;
+  __shared__ T cf[3];
+  __shared__ __align__(8) unsigned long long mbar[STG_BUF];
+  const int tid = threadIdx.x;
+  if (tid == 0) Fs = fr[blockIdx.y];
+  if (FILTER && tid < 3) cf[tid] = (T)coef[3 * blockIdx.y + tid];
+  __syncthreads();
+  const DevFrag& F = Fs;
+  const int ex = F.dext[0], ey = F.dext[1], ez = F.dext[2];
+  const int yb = FILTER ? F.lo[1] : 0, ye = FILTER ? F.lo[1] + F.ext[1] : ey;
+  const int zb = FILTER ? F.lo[2] : 0, ze = FILTER ? F.lo[2] + F.ext[2] : ez;
+  const int y0 = yb + (int)blockIdx.x * ty, y1 = min(ye, y0 + ty);
+  const int z0 = zb + (int)blockIdx.z * zc, z1 = min(ze, z0 + zc);
+  if (y0 >= y1 || z0 >= z1) return;   // uniform over the CTA
+  const int qpp = F.ld / VN;
+  const int rows = y1 - y0 + 2;                 // staged rows y0-1 .. y1
+  const long long rowE = (long long)ex * F.ld;  // elements of one storage row
+  const long long planeE = rows * rowE;         // elements of one staged plane
+  T* buf = reinterpret_cast<T*>(stg_smem);
+  if (tid == 0) {
+    for (int i = 0; i < STG_BUF; ++i) mbar_init(smem_u32(&mbar[i]), 1);
+    fence_mbar_init();
+  }
+  // Staged row r holds storage row y0-1+r (wrapped in a full-span dimension);
+  // only the first and the last staged row can fall outside the storage box.
+  auto srow = [&](int r) { return ((y0 - 1 + r) % ey + ey) % ey; };
+  auto zero_row = [&](int r) { return !F.full[1] && (y0 - 1 + r < 0 || y0 - 1 + r >= ey); };
+  // those rows read zero: written once, never the target of a copy
+  for (int k = 0; k < 2; ++k) {
+    const int r = k ? rows - 1 : 0;
+    if (zero_row(r))
+      for (int i = 0; i < STG_BUF; ++i)
+        for (long long e = tid; e < rowE; e += STG_THREADS) buf[i * planeE + r * rowE + e] = T(0);
+  }
+  fence_async_smem();
+  __syncthreads();
+
+  const T* src = in + F.off;
+  // end of the run of staged rows from r that is contiguous in storage
+  auto run_end = [&](int r) {
+    int r2 = r + 1;
+    if (zero_row(r)) return r2;
+    while (r2 < rows && !zero_row(r2) && srow(r2) == srow(r2 - 1) + 1) ++r2;
+    return r2;
+  };
+  auto plane_ok = [&](int p) { return F.full[2] || (p >= 0 && p < ez); };
+  // thread 0: fetch plane p (z0-1 <= p <= z1) into ring slot (p-z0+1) % STG_BUF
+  auto issue = [&](int p) {
+    const int j = p - (z0 - 1);
+    const uint32_t mb = smem_u32(&mbar[j % STG_BUF]);
+    if (!plane_ok(p)) {
+      mbar_arrive(mb);   // the phase completes without a copy; the plane is skipped
+      return;
+    }
+    const int zz = (p % ez + ez) % ez;
+    T* dst = buf + (long long)(j % STG_BUF) * planeE;
+    uint32_t bytes = 0;
+    for (int r = 0; r < rows; ++r)
+      if (!zero_row(r)) bytes += (uint32_t)(rowE * sizeof(T));
+    mbar_arrive_expect(mb, bytes);
+    for (int r = 0; r < rows;) {
+      const int r2 = run_end(r);
+      if (!zero_row(r))
+        bulk_g2s(smem_u32(dst + r * rowE), src + ((long long)zz * ey + srow(r)) * rowE,
+                 (uint32_t)((r2 - r) * rowE * sizeof(T)), mb);
+      r = r2;
+    }
+  };
+  auto wait_plane = [&](int p) {
+    const int j = p - (z0 - 1);
+    return mbar_wait(smem_u32(&mbar[j % STG_BUF]), (uint32_t)((j / STG_BUF) & 1), flag);
+  };
+  // prologue: fill the ring with planes z0-1 .. z0+STG_BUF-2; afterwards the
+  // end of iteration z refills the slot of plane z-1 with plane z+STG_BUF-1
+  const int plast = z1;   // last plane needed
+  int pnext = min(plast, z0 + STG_BUF - 2) + 1;   // next plane to issue
+  if (tid == 0)
+    for (int p = z0 - 1; p < pnext; ++p) issue(p);
+  int pwait = z0 - 1;     // planes < pwait have been waited for
+
+  const int nx = FILTER ? F.ext[0] : ex, xo = FILTER ? F.lo[0] : 0;
+  const int per_row = nx * qpp;
+  const int nel = (y1 - y0) * per_row;   // <= STG_THREADS * STG_EPT (host's tile choice)
+  const T alpha = FILTER ? cf[0] : T(1), beta = FILTER ? cf[1] : T(0), shift = FILTER ? cf[2] : T(0);
+  const V16* Pv = (FILTER && prev) ? reinterpret_cast<const V16*>(prev + F.off) : nullptr;
+  V16* O = reinterpret_cast<V16*>(out + F.off);
+  const long long vplane = (long long)gx * gy;
+  const int rowq = ex * qpp;   // 16-byte elements of one staged row
+  // per element of this thread: staged index, global index within a plane, V index within a plane
+  int sidx[STG_EPT], xs[STG_EPT], gidx[STG_EPT], vidx[STG_EPT];   // all < 2^31 (planner)
+#pragma unroll
+  for (int u = 0; u < STG_EPT; ++u) {
+    const int e = tid + u * STG_THREADS;
+    const int ee = e < nel ? e : 0;
+    const int yl = ee / per_row;
+    const int rem = ee - yl * per_row;
+    const int xl = rem / qpp, q = rem - xl * qpp;
+    const int x = xo + xl, y = y0 + yl;
+    xs[u] = x;
+    sidx[u] = (yl + 1) * rowq + x * qpp + q;
+    gidx[u] = (y * ex + x) * qpp + q;
+    vidx[u] = ((F.doff[1] + y) % gy) * gx + (F.doff[0] + x) % gx;
+  }
+  const long long gplane = (long long)ey * ex * qpp;   // 16-byte elements of one storage plane
+  // the previous block and V of the plane being computed, loaded one iteration ahead
+  V16 pv[STG_EPT];
+  T vv[STG_EPT];
+  auto prefetch = [&](int z) {
+    const long long zo = (long long)z * gplane;
+    const long long zv = (long long)((F.doff[2] + z) % gz) * vplane;
+#pragma unroll
+    for (int u = 0; u < STG_EPT; ++u) {
+      if (tid + u * STG_THREADS < nel) {
+        vv[u] = V[zv + vidx[u]];
+        if (Pv != nullptr) pv[u] = Pv[zo + gidx[u]];
+      }
+    }
+  };
+  prefetch(z0);
+  bool ok = true;
+  for (int z = z0; z < z1; ++z) {
+    V16 pvc[STG_EPT];
+    T vc[STG_EPT];
+#pragma unroll
+    for (int u = 0; u < STG_EPT; ++u) {
+      pvc[u] = pv[u];
+      vc[u] = vv[u];
+    }
+    if (z + 1 < z1) prefetch(z + 1);
+    // planes z-1, z, z+1 must have landed
+    while (ok && pwait <= z + 1) {
+      ok = wait_plane(pwait);
+      if (ok) ++pwait;
+    }
+    if (!__syncthreads_and(ok)) {
+      ok = false;
+      break;
+    }
+    const int jb = z - 1 - (z0 - 1), jc = jb + 1, ja = jb + 2;
+    const V16* Bb = reinterpret_cast<const V16*>(buf + (long long)(jb % STG_BUF) * planeE);
+    const V16* Bc = reinterpret_cast<const V16*>(buf + (long long)(jc % STG_BUF) * planeE);
+    const V16* Ba = reinterpret_cast<const V16*>(buf + (long long)(ja % STG_BUF) * planeE);
+    const bool has_b = plane_ok(z - 1), has_a = plane_ok(z + 1);
+    const long long zo = (long long)z * gplane;
+#pragma unroll
+    for (int u = 0; u < STG_EPT; ++u) {
+      if (tid + u * STG_THREADS >= nel) continue;
+      const int sc = sidx[u], x = xs[u];
+      V16 sum = add4(Bc[sc + rowq], Bc[sc - rowq]);
+      const int xp = nb_index(x, x, ex, F.full[0], +1, 1), xm = nb_index(x, x, ex, F.full[0], -1, 1);
+      if (xp >= 0) sum = add4(sum, Bc[sc + (xp - x) * qpp]);
+      if (xm >= 0) sum = add4(sum, Bc[sc + (xm - x) * qpp]);
+      if (has_b) sum = add4(sum, Bb[sc]);
+      if (has_a) sum = add4(sum, Ba[sc]);
+      V16 hy = fma4(c0 + vc[u] - shift, Bc[sc], zero4(T()));
+      hy = fma4(-c1, sum, hy);
+      if constexpr (FILTER) {
+        V16 o = fma4(alpha, hy, zero4(T()));
+        if (Pv != nullptr) o = fma4(beta, pvc[u], o);
+        O[zo + gidx[u]] = o;
+      } else {
+        O[zo + gidx[u]] = hy;
+      }
+    }
+    __syncthreads();   // slot of plane z-1 is free
+    if (tid == 0 && pnext <= plast) issue(pnext);
+    ++pnext;
+  }
+  if (!ok) {
+    // drain: every issued copy must land before the CTA's shared memory is released
+    for (; pwait < min(pnext, plast + 1); ++pwait) wait_plane(pwait);
+    __syncthreads();
+  }
+}
+
+// Launch shape of the stencils.  Staged form: x = row tiles of ty rows, y =
+// fragments, z = chunks of zc planes; ty minimises the staged rows (tile plus
+// two halo rows) per output row within the shared-memory budget (two CTAs per
+// SM, else one) and at most STG_EPT elements per thread, and the chunk count
+// fills about two resident waves of the GB300 (152 SMs).  Register form (fallback when even one row does not fit):
+// x covers the (x, y, column group) elements of the largest plane.
 ApplyGrid apply_grid(const std::vector<DevFrag>& fr, bool fp64, bool filter) {
   const int vn = fp64 ? 2 : 4;
-  long long mx = 1, threads = 0;
-  int zmax = 1;
+  const int es = fp64 ? 8 : 4;
+  const int sms = 152;
+  long long mx = 1, threads = 0, rowB = 0, rowQ = 0;
+  int zmax = 1, ymax = 1;
   for (const DevFrag& f : fr) {
     const long long xy = (long long)f.dext[0] * f.dext[1] * (f.ld / vn);
     mx = std::max(mx, xy);
     threads += filter ? (long long)f.ext[0] * f.ext[1] * (f.ld / vn) : xy;
     zmax = std::max(zmax, filter ? f.ext[2] : f.dext[2]);
+    ymax = std::max(ymax, filter ? f.ext[1] : f.dext[1]);
+    rowB = std::max(rowB, (long long)f.dext[0] * f.ld * es);
+    rowQ = std::max(rowQ, (long long)(filter ? f.ext[0] : f.dext[0]) * (f.ld / vn));
   }
   ApplyGrid g;
+  // staged form, where OFM_STENCIL=staged asks for it
+  const char* form = std::getenv("OFM_STENCIL");
+  const bool try_staged = form != nullptr && std::strcmp(form, "staged") == 0;
+  const long long budgets[2] = {110 * 1024, 200 * 1024};
+  for (int bi = 0; bi < 2 && try_staged && !g.staged; ++bi) {
+    int best = 0;
+    long long best_cost = 0;
+    for (int ty = 1; ty <= ymax; ++ty) {
+      if ((long long)STG_BUF * (ty + 2) * rowB > budgets[bi]) break;
+      if ((long long)ty * rowQ > (long long)STG_THREADS * STG_EPT) break;
+      const long long cost = (long long)((ymax + ty - 1) / ty) * (ty + 2);
+      if (best == 0 || cost <= best_cost) {
+        best = ty;
+        best_cost = cost;
+      }
+    }
+    if (best > 0) {
+      g.staged = true;
+      g.ty = best;
+      g.smem = (int)((long long)STG_BUF * (best + 2) * rowB);
+      const int per_sm = bi == 0 ? 2 : 1;
+      long long per_chunk = 0;
+      for (const DevFrag& f : fr) per_chunk += ((filter ? f.ext[1] : f.dext[1]) + best - 1) / best;
+      const long long nch = std::max(1LL, std::min<long long>(zmax, (2LL * sms * per_sm + per_chunk - 1) / per_chunk));
+      g.zc = (int)((zmax + nch - 1) / nch);
+      g.z = (zmax + g.zc - 1) / g.zc;
+      g.x = (ymax + best - 1) / best;
+    }
+  }
+  if (g.staged) {
+    // once per plan (the call is not free: kept out of the launch path)
+    const void* k = fp64 ? (filter ? (const void*)apply_staged_kernel<double, true>
+                                   : (const void*)apply_staged_kernel<double, false>)
+                         : (filter ? (const void*)apply_staged_kernel<float, true>
+                                   : (const void*)apply_staged_kernel<float, false>);
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, g.smem) == cudaSuccess)
+      return g;
+    cudaGetLastError();   // not available: the register form below
+    g = ApplyGrid();
+  }
+  // register form
   g.x = (int)((mx + 255) / 256);
-  const long long want = 2LL * 152 * 2048;
+  const long long want = 2LL * sms * 2048;
   const long long nch = std::max(1LL, std::min<long long>(zmax, (want + threads - 1) / std::max(1LL, threads)));
   g.zc = (int)((zmax + nch - 1) / nch);
   g.z = (zmax + g.zc - 1) / g.zc;
@@ -159,19 +408,25 @@ ApplyGrid apply_grid(const std::vector<DevFrag>& fr, bool fp64, bool filter) {
 template <typename T, bool FILTER>
 static void zmarch(const ApplyGrid& ag, int nfrag, const DevFrag* d_fr, const void* V,
                    const void* in, const void* prev, void* out, const double* coef,
-                   const int gn[3], double h, cudaStream_t s) {
+                   const int gn[3], double h, int* flag, cudaStream_t s) {
   const double c0 = 3.0 / (h * h), c1 = 0.5 / (h * h);
   dim3 g(ag.x, nfrag, ag.z);
-  apply_zmarch_kernel<T, FILTER><<<g, 256, 0, s>>>(d_fr, (const T*)V, (const T*)in,
-                                                   (const T*)prev, (T*)out, coef, gn[0], gn[1],
-                                                   gn[2], (T)c0, (T)c1, ag.zc);
+  if (ag.staged) {
+    apply_staged_kernel<T, FILTER><<<g, STG_THREADS, ag.smem, s>>>(
+        d_fr, (const T*)V, (const T*)in, (const T*)prev, (T*)out, coef, gn[0], gn[1], gn[2],
+        (T)c0, (T)c1, ag.ty, ag.zc, flag);
+  } else {
+    apply_zmarch_kernel<T, FILTER><<<g, 256, 0, s>>>(d_fr, (const T*)V, (const T*)in,
+                                                     (const T*)prev, (T*)out, coef, gn[0], gn[1],
+                                                     gn[2], (T)c0, (T)c1, ag.zc);
+  }
 }
 
 void launch_apply_global(const DevFrag* d_fr, int nfrag, const ApplyGrid& g, const void* V,
                          const void* states, void* hphi, const int gn[3], double h, bool fp64,
-                         cudaStream_t s) {
-  if (fp64) zmarch<double, false>(g, nfrag, d_fr, V, states, nullptr, hphi, nullptr, gn, h, s);
-  else zmarch<float, false>(g, nfrag, d_fr, V, states, nullptr, hphi, nullptr, gn, h, s);
+                         int* flag, cudaStream_t s) {
+  if (fp64) zmarch<double, false>(g, nfrag, d_fr, V, states, nullptr, hphi, nullptr, gn, h, flag, s);
+  else zmarch<float, false>(g, nfrag, d_fr, V, states, nullptr, hphi, nullptr, gn, h, flag, s);
 }
 
 // a0, fragment mode: the fragment Hamiltonian is the principal submatrix of
@@ -183,9 +438,9 @@ void launch_apply_global(const DevFrag* d_fr, int nfrag, const ApplyGrid& g, con
 // null when beta is zero.
 void launch_apply_filter(const DevFrag* d_fr, int nfrag, const ApplyGrid& g, const void* V,
                          const void* in, const void* prev, void* out, const double* coef,
-                         const int gn[3], double h, bool fp64, cudaStream_t s) {
-  if (fp64) zmarch<double, true>(g, nfrag, d_fr, V, in, prev, out, coef, gn, h, s);
-  else zmarch<float, true>(g, nfrag, d_fr, V, in, prev, out, coef, gn, h, s);
+                         const int gn[3], double h, bool fp64, int* flag, cudaStream_t s) {
+  if (fp64) zmarch<double, true>(g, nfrag, d_fr, V, in, prev, out, coef, gn, h, flag, s);
+  else zmarch<float, true>(g, nfrag, d_fr, V, in, prev, out, coef, gn, h, flag, s);
 }
 
 // ------------------------------------------------------------ conversions --

@@ -827,7 +827,9 @@ static void apply_block(ofm_ctx* c, int in, int prev, int out, const double* coe
   KTimer kt(c, KC_FILTER, 1, prev >= 0 ? w->filter_b3 : w->filter_b2);
   launch_apply_filter((const DevFrag*)w->d_efr.p, c->nfrag, w->fgrid, c->V.p, w->buf[in].p,
                       prev >= 0 ? w->buf[prev].p : nullptr, w->buf[out].p, coef, c->grid.n,
-                      c->grid.h, c->storage == OFM_STORE_FP64, c->stream);
+                      c->grid.h, c->storage == OFM_STORE_FP64,
+                      (int*)c->flag.p + OFM_FLAG_STENCIL, c->stream);
+  c->stencil_check = true;
 }
 
 static int other(int a, int b, int c2 = -1) {
@@ -882,11 +884,16 @@ extern "C" ofm_status ofm_fragment_eigs(ofm_ctx* c, const ofm_eig_opts* opts, do
   int xb = 1;
   std::vector<double> th(w->tsum), rs(w->tsum);
   const double bup = 6.0 / (c->grid.h * c->grid.h) + w->vlim[0];
-  // the filter may spread the wanted part of the block by at most this
-  // factor: components shrunk by s relative to the largest carry rounding
-  // of unit roundoff x s, which is the residual floor (FP32: 6e-8 x 100,
-  // below the default tolerance 1e-5; FP64: 1e-16 x 1e6), so s caps the degree
-  const double spread_max = std::log(fp64 ? 1e6 : 1e2);
+  // The filter may spread the wanted part of the block by at most a factor
+  // s: a component shrunk by s relative to the largest one in its vector
+  // carries rounding of unit roundoff u x s.  For a random block every
+  // vector mixes every state, so s <= 0.1 tol / u keeps that floor below
+  // the tolerance (FP32: 1e2, FP64: 1e6).  Once the block holds Ritz
+  // vectors, the lower states enter vector i only through its error,
+  // about the largest residual r of the fragment, so the floor is u s r
+  // and s may grow to 0.1 tol / (u r), up to 1e6 (FP32) / 1e12 (FP64).
+  const double u_round = fp64 ? 1.1e-16 : 6e-8;
+  const double s_min = fp64 ? 1e6 : 1e2, s_max = fp64 ? 1e12 : 1e6;
   bool converged = false;
   int it = 0;
   for (; it <= max_iter; ++it) {
@@ -905,11 +912,17 @@ extern "C" ofm_status ofm_fragment_eigs(ofm_ctx* c, const ofm_eig_opts* opts, do
     // damped interval, so the ratio between the bottom of the spectrum
     // (min V on the first pass, the lowest Ritz value after) and the last
     // wanted Ritz value is about exp(d (acosh(t_low) - acosh(t_want)));
-    // keep it within spread_max for every fragment
+    // keep it within the fragment's spread cap for every fragment
     int deg = degree;
     for (int f = 0; f < nf; ++f) {
       const int m = w->efr[f].n;
       const double* t = &th[w->toff[f]];
+      double rmax = 0.0;
+      for (int i = 0; i < c->frags[f].n; ++i) rmax = std::max(rmax, rs[w->toff[f] + i]);
+      const double smax = (it == 0 || !(rmax > 0.0))
+                              ? s_min
+                              : std::min(s_max, std::max(s_min, 0.1 * tol / (u_round * rmax)));
+      const double spread_max = std::log(smax);
       double blo = t[m - 1], a0 = t[0];
       double bu = std::max(bup, blo + 1e-3);
       if (!(blo > a0)) blo = a0 + 1e-3 * (bu - a0);
@@ -979,6 +992,7 @@ extern "C" ofm_status ofm_fragment_eigs(ofm_ctx* c, const ofm_eig_opts* opts, do
       if (resid_out) resid_out[c->frags[f].basis0 + i] = rs[w->toff[f] + i];
       worst = std::max(worst, rs[w->toff[f] + i]);
     }
+  OFM_TRY(ofm_wait_status(c));
   std::fill(c->frag_set.begin(), c->frag_set.end(), 1);
   c->have_states = true;
   c->last_eig_iters = it;

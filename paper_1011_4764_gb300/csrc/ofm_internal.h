@@ -89,19 +89,24 @@ void make_items_simt(const std::vector<DevFrag>& fr, const std::vector<HostPair>
 
 // ------------------------------------------------------------ kernels ------
 
-// launch shape of the z-marching stencils (x: plane elements, z: plane chunks)
-struct ApplyGrid { int x = 1, z = 1, zc = 1; };
+// launch shape of the stencils: shared-memory staged (row tiles of ty rows,
+// smem bytes per CTA) or register z-marching; z = chunks of zc planes
+struct ApplyGrid {
+  bool staged = false;
+  int x = 1, z = 1, zc = 1, ty = 1, smem = 0;
+};
 ApplyGrid apply_grid(const std::vector<DevFrag>& fr, bool fp64, bool filter);
+// flag: set to 1 when a bounded wait of the staged form gives up
 void launch_apply_global(const DevFrag* d_fr, int nfrag, const ApplyGrid& g, const void* V,
                          const void* states, void* hphi, const int gn[3], double h, bool fp64,
-                         cudaStream_t s);
+                         int* flag, cudaStream_t s);
 void launch_import_states(const DevFrag* d_fr, int a, const DevFrag& fa, const double* src,
                           void* states, bool fp64, cudaStream_t s);
 void launch_export_states(const DevFrag& fa, const void* states, double* dst, bool fp64,
                           bool dilated_hphi, cudaStream_t s);
 void launch_apply_filter(const DevFrag* d_fr, int nfrag, const ApplyGrid& g, const void* V,
                          const void* in, const void* prev, void* out, const double* coef,
-                         const int gn[3], double h, bool fp64, cudaStream_t s);
+                         const int gn[3], double h, bool fp64, int* flag, cudaStream_t s);
 void launch_convert_V(const double* src, void* dst, long long n, bool fp64, cudaStream_t s);
 void launch_contract_simt(int prec, bool store_fp64, const DevFrag* d_fr, const DevPair* d_pairs,
                           const Piece* d_pieces, const WorkItem* d_items, int nitems,
@@ -189,9 +194,14 @@ struct ofm_ctx {
   double apply_bytes = 0, contract_bytes = 0, finalize_bytes = 0;
   ofm_prof prof;                    // per-kernel-class launch counts and event timing
   bool tc_check = false;            // a tensor-core launch's timeout flag is unread
+  bool stencil_check = false;       // a stencil launch's timeout flag is unread
   struct EigWork* eig = nullptr;    // fragment-eigensolver buffers and plan
   struct TcPlan* tc = nullptr;      // tensor-core contraction plan
 };
+
+// words of the context's 16-int flag buffer: 0 pivot flag and 2..3 window
+// counts (window solver), 8 staged-stencil wait timeout
+constexpr int OFM_FLAG_STENCIL = 8;
 
 // helpers used by every translation unit
 ofm_status ofm_fail(ofm_ctx* c, ofm_status s, const std::string& msg);
@@ -207,7 +217,7 @@ void ofm_eig_free(ofm_ctx* c);
 void ofm_prof_release(ofm_ctx* c);            // waits for and frees timing events
 void ofm_tc_free(ofm_ctx* c);
 ofm_status ofm_contract_tc(ofm_ctx* c, ofm_precision prec);
-ofm_status ofm_tc_status(ofm_ctx* c);         // OFM_ERR_TIMEOUT if a tensor-core wait gave up
+ofm_status ofm_wait_status(ofm_ctx* c);       // OFM_ERR_TIMEOUT if a bounded wait gave up
 ofm_status ofm_window_factor(ofm_ctx* c);
 // eigenvalues below lo and below-or-at hi of the factored pencil
 ofm_status ofm_window_count(ofm_ctx* c, double lo, double hi, int* count_lo, int* count_hi);

@@ -30,8 +30,10 @@
 #include <vector>
 
 #include "ofm_internal.h"
+#include "ptx_util.h"
 
 using namespace ofm;
+using namespace ofm::ptx;
 
 namespace {
 
@@ -57,35 +59,6 @@ enum { TC_TF32 = 0, TC_BF16 = 1, TC_BF16X3 = 2 };
 
 // ----------------------------------------------------------- PTX helpers --
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t addr, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_test(uint32_t addr, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred P;\n mbarrier.test_wait.parity.shared::cta.b64 P, [%1], %2;\n"
-      " selp.b32 %0, 1, 0, P;\n}\n"
-      : "=r"(ok)
-      : "r"(addr), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait for completion `parity` of an mbarrier.
-__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity, int* flag) {
-  for (int i = 0; i < (1 << 24); ++i) {
-    if (mbar_test(addr, parity)) return true;
-    if (i > 64) __nanosleep(32);
-  }
-  atomicExch(flag, 1);
-  return false;
-}
-
 __device__ __forceinline__ void cp_async16(uint32_t saddr, const void* g) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr), "l"(g) : "memory");
 }
@@ -95,9 +68,6 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-__device__ __forceinline__ void fence_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -222,7 +192,7 @@ __global__ void __launch_bounds__(TC_THREADS) tc_contract_kernel(
   if (tid == 0) {
     mbar_init(smem_u32(&mbar[0]), 1);
     mbar_init(smem_u32(&mbar[1]), 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    fence_mbar_init();
   }
   // tensor memory: one column per accumulator column (power of two >= 32)
   uint32_t ncols = 32;
@@ -589,16 +559,29 @@ ofm_status ofm_contract_tc(ofm_ctx* c, ofm_precision prec) {
   return OFM_OK;
 }
 
-// Reports a bounded-wait timeout of an earlier tensor-core launch.
-ofm_status ofm_tc_status(ofm_ctx* c) {
-  if (!c->tc_check || !c->tc || !c->tc->flag.p) return OFM_OK;
-  int h = 0;
-  OFM_CUDA(c, cudaMemcpyAsync(&h, c->tc->flag.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-  OFM_CUDA(c, cudaStreamSynchronize(c->stream));
-  c->tc_check = false;
-  if (h) {
-    cudaMemsetAsync(c->tc->flag.p, 0, sizeof(int), c->stream);
-    return ofm_fail(c, OFM_ERR_TIMEOUT, "tensor-core contraction: an mbarrier wait exceeded its bound");
+// Reports a bounded-wait timeout of an earlier tensor-core or staged-stencil
+// launch (each sets its flag word; the flags are read once and cleared).
+ofm_status ofm_wait_status(ofm_ctx* c) {
+  if (c->tc_check && c->tc && c->tc->flag.p) {
+    int h = 0;
+    OFM_CUDA(c, cudaMemcpyAsync(&h, c->tc->flag.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    OFM_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->tc_check = false;
+    if (h) {
+      cudaMemsetAsync(c->tc->flag.p, 0, sizeof(int), c->stream);
+      return ofm_fail(c, OFM_ERR_TIMEOUT, "tensor-core contraction: an mbarrier wait exceeded its bound");
+    }
+  }
+  if (c->stencil_check) {
+    int h = 0;
+    int* f = (int*)c->flag.p + OFM_FLAG_STENCIL;
+    OFM_CUDA(c, cudaMemcpyAsync(&h, f, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    OFM_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->stencil_check = false;
+    if (h) {
+      cudaMemsetAsync(f, 0, sizeof(int), c->stream);
+      return ofm_fail(c, OFM_ERR_TIMEOUT, "stencil: a staged-plane wait exceeded its bound");
+    }
   }
   return OFM_OK;
 }

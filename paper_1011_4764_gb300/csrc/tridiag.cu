@@ -3,10 +3,11 @@
 //
 // 1. Householder reduction of A to tridiagonal form in ONE persistent
 //    cooperative kernel: per column k, every CTA forms the Householder
-//    vector itself (a short column read), the CTAs compute p = tau A22 v by
-//    rows, meet at a grid barrier, apply A22 -= v w^T + w v^T
-//    (w = p - (tau/2)(v^T p) v) by rows and meet again.  Two barriers per
-//    column instead of three kernel launches.  The barrier spins a bounded
+//    vector itself, the CTAs compute p = tau A22 v by rows, meet at a grid
+//    barrier and apply A22 -= v w^T + w v^T (w = p - (tau/2)(v^T p) v) by
+//    rows.  With the matrix rows resident in shared memory one barrier per
+//    column suffices (the next column travels with p as a published row);
+//    the global-memory fallback meets twice.  The barrier spins a bounded
 //    number of times and reports a timeout instead of hanging.
 // 2. Eigenvalues by index with multisection: one warp per wanted
 //    eigenvalue; each lane counts the eigenvalues below one of 32 points of
@@ -176,20 +177,30 @@ __global__ void __launch_bounds__(512) tridiag_persistent_kernel(double* A, int 
   }
 }
 
-// The same reduction with the matrix resident in shared memory: CTA b owns
-// the rows i = b, b + nb, b + 2 nb, ... for the whole reduction, so the
-// rank-2 updates and the matrix-vector products never leave the SM; only
-// the current column (colbuf) and p (pg) travel through L2.
+// The same reduction with the matrix resident in shared memory and ONE
+// grid barrier per column.  CTA b owns the rows i = b, b + nb, b + 2 nb, ...
+// for the whole reduction.  At step k every CTA holds the whole column k of
+// A_k and forms v itself; it computes p_i = tau (A_k v)_i for its rows, and
+// the owner of row k+1 also publishes that row of A_k.  After the barrier
+// every CTA has p and row k+1, forms w = p - (tau/2)(v.p) v, updates its own
+// rows, and obtains column k+1 of A_{k+1} from row k+1 by symmetry:
+//     A_{k+1}[k+1, i] = A_k[k+1, i] - v_{k+1} w_i - w_{k+1} v_i,
+// the same expression (same rounding) the owner applies to its copy of the
+// row.  So the next Householder vector needs no second exchange.  p and the
+// published row are double-buffered by the parity of k: a CTA that runs
+// ahead into step k+1 writes the other half while slower CTAs still read.
 __global__ void __launch_bounds__(512) tridiag_smem_kernel(double* A, int n, double* d, double* e,
-                                                           double* tau, double* colbuf,
-                                                           double* pg, GridBar* bar) {
+                                                           double* tau, double* xbuf,
+                                                           GridBar* bar) {
   extern __shared__ double sm[];
   const int nb = (int)gridDim.x, b = (int)blockIdx.x;
   const int R = (n - b + nb - 1) / nb;      // rows owned by this CTA
   const int Rmax = (n + nb - 1) / nb;
   double* rows = sm;                        // Rmax x n
-  double* v = rows + (size_t)Rmax * n;      // n
-  double* pw = v + n;                       // n
+  double* v = rows + (size_t)Rmax * n;      // n: Householder vector (indices k+1..n-1)
+  double* w = v + n;                        // n: p, then w
+  double* col = w + n;                      // n: column k of A_k (indices k+1..n-1)
+  double* rk = col + n;                     // n: row k+1 of A_k (indices k+1..n-1)
   __shared__ double red[40];
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
@@ -197,24 +208,15 @@ __global__ void __launch_bounds__(512) tridiag_smem_kernel(double* A, int n, dou
     const int li = e2 / n, j = e2 - li * n;
     rows[(size_t)li * n + j] = A[(size_t)(b + li * nb) * n + j];
   }
-  __syncthreads();
-  for (int li = tid; li < R; li += nt) colbuf[b + li * nb] = rows[(size_t)li * n + 0];
+  for (int j = tid; j < n; j += nt) col[j] = A[j];   // column 0 = row 0 (A is symmetric)
+  // nobody reads A after this barrier; CTA 0 then stores the Householder vectors in it
   if (!grid_sync(bar, nb)) return;
   for (int k = 0; k + 2 < n; ++k) {
     const int m = n - k - 1;
-    // Householder vector of column k from colbuf (rows k+1..n-1)
-    // one pass over the column: x into v (shared), its squared norm
     double s = 0.0;
-    for (int i = tid; i < m; i += nt) {
-      const double x = __ldcg(&colbuf[k + 1 + i]);
-      v[k + 1 + i] = x;
-      if (i > 0) {
-        s += x * x;
-        if (b == 0) A[(size_t)k * n + k + 1 + i] = x;  // kept for back-transformation
-      }
-    }
+    for (int i = k + 2 + tid; i < n; i += nt) s += col[i] * col[i];
     const double sig = block_sum(s, red);
-    const double x0 = v[k + 1];
+    const double x0 = col[k + 1];
     double alpha, t, v0;
     if (sig == 0.0) {
       alpha = x0;
@@ -226,10 +228,10 @@ __global__ void __launch_bounds__(512) tridiag_smem_kernel(double* A, int n, dou
       v0 = x0 - alpha;
       t = 2.0 / (v0 * v0 + sig);
     }
-    __syncthreads();   // every thread has read x0 before it is replaced by v0
-    if (tid == 0) {
-      v[k + 1] = v0;
-      if (b == 0) A[(size_t)k * n + k + 1] = v0;
+    for (int i = k + 1 + tid; i < n; i += nt) {
+      const double vi = (i == k + 1) ? v0 : col[i];
+      v[i] = vi;
+      if (b == 0) A[(size_t)k * n + i] = vi;   // kept for back-transformation
     }
     if (tid == 0) {
       if (k % nb == b) d[k] = rows[(size_t)(k / nb) * n + k];
@@ -239,6 +241,8 @@ __global__ void __launch_bounds__(512) tridiag_smem_kernel(double* A, int n, dou
       }
     }
     __syncthreads();
+    double* pb = xbuf + (size_t)(k & 1) * n;
+    double* rb = xbuf + 2 * (size_t)n + (size_t)(k & 1) * n;
     // p_i = t sum_j A_ij v_j for the owned rows i > k, one warp per row
     const int li0 = (k + 1 - b + nb - 1) / nb;   // first owned row index > k
     for (int li = li0 + warp; li < R; li += nwarps) {
@@ -246,26 +250,36 @@ __global__ void __launch_bounds__(512) tridiag_smem_kernel(double* A, int n, dou
       double acc = 0.0;
       for (int j = k + 1 + lane; j < n; j += 32) acc += row[j] * v[j];
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-      if (lane == 0) pg[b + li * nb] = t * acc;
+      if (lane == 0) pb[b + li * nb] = t * acc;
+    }
+    if ((k + 1) % nb == b) {
+      const double* row = rows + (size_t)((k + 1) / nb) * n;
+      for (int j = k + 1 + tid; j < n; j += nt) rb[j] = row[j];
     }
     if (!grid_sync(bar, nb)) return;
-    for (int j = tid; j < m; j += nt) pw[k + 1 + j] = __ldcg(&pg[k + 1 + j]);
+    for (int j = k + 1 + tid; j < n; j += nt) {
+      w[j] = __ldcg(&pb[j]);
+      rk[j] = __ldcg(&rb[j]);
+    }
     __syncthreads();
     double q = 0.0;
-    for (int j = tid; j < m; j += nt) q += v[k + 1 + j] * pw[k + 1 + j];
+    for (int j = k + 1 + tid; j < n; j += nt) q += v[j] * w[j];
     const double K = 0.5 * t * block_sum(q, red);
-    for (int j = tid; j < m; j += nt) pw[k + 1 + j] = fma(-K, v[k + 1 + j], pw[k + 1 + j]);
+    for (int j = k + 1 + tid; j < n; j += nt) w[j] = fma(-K, v[j], w[j]);
     __syncthreads();
-    // rank-2 update of the owned rows; the next column goes to colbuf
+    // rank-2 update of the owned rows i > k
     for (int li = li0 + warp; li < R; li += nwarps) {
       const int i = b + li * nb;
       double* row = rows + (size_t)li * n;
-      const double vi = v[i], wi = pw[i];
-      for (int j = k + 1 + lane; j < n; j += 32) row[j] = fma(-vi, pw[j], fma(-wi, v[j], row[j]));
-      __syncwarp();
-      if (lane == 0) colbuf[i] = row[k + 1];
+      const double vi = v[i], wi = w[i];
+      for (int j = k + 1 + lane; j < n; j += 32) row[j] = fma(-vi, w[j], fma(-wi, v[j], row[j]));
     }
-    if (!grid_sync(bar, nb)) return;
+    // column k+1 of A_{k+1} from row k+1 (same expression as the owner's update)
+    {
+      const double vk = v[k + 1], wk = w[k + 1];
+      for (int i = k + 2 + tid; i < n; i += nt) col[i] = fma(-vk, w[i], fma(-wk, v[i], rk[i]));
+    }
+    __syncthreads();
   }
   if (tid == 0) {
     if (n >= 2) {
@@ -438,20 +452,20 @@ ofm_status ofm_tridiag_persistent(ofm_ctx* c, double* A, int n, double* d, doubl
   {
     const int nbs = sms;
     const size_t rmax = (size_t)(n + nbs - 1) / nbs;
-    const size_t smem2 = (rmax * n + 2 * (size_t)n) * sizeof(double);
+    const size_t smem2 = (rmax * n + 4 * (size_t)n) * sizeof(double);
     int per_sm2 = 0;
     if (smem2 <= 200 * 1024 &&
         cudaFuncSetAttribute(tridiag_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem2) == cudaSuccess &&
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, tridiag_smem_kernel, 512, smem2) ==
             cudaSuccess &&
-        per_sm2 >= 1 && c->w_eval.cap >= (size_t)n * sizeof(double)) {
+        per_sm2 >= 1 && c->w_eval.cap >= 4 * (size_t)n * sizeof(double)) {
       OFM_TRY(ofm_ensure(c, c->w_bar, sizeof(GridBar), "grid barrier"));
       OFM_CUDA(c, cudaMemsetAsync(c->w_bar.p, 0, sizeof(GridBar), c->stream));
       GridBar* bar = (GridBar*)c->w_bar.p;
-      double* colbuf = (double*)c->w_eval.p;
+      double* xbuf = (double*)c->w_eval.p;   // p and the published row, two halves each
       int nn = n;
-      void* args[] = {&A, &nn, &d, &e, &tau, &colbuf, &pg, &bar};
+      void* args[] = {&A, &nn, &d, &e, &tau, &xbuf, &bar};
       OFM_CUDA(c, cudaLaunchCooperativeKernel((const void*)tridiag_smem_kernel, dim3(nbs), dim3(512),
                                               args, smem2, c->stream));
       GridBar hb{};

@@ -25,8 +25,12 @@ constexpr int NB = 32;
 // ---------------------------------------------------------------- Cholesky --
 
 // Factor the kb x kb diagonal block at (k0, k0) in place (lower triangle).
+// The pivot's square root and its reciprocal are formed once per column,
+// so the column is scaled by a multiplication (FP64 division and square
+// root are long instruction sequences on a part with few FP64 units).
 __global__ void potrf_diag_kernel(double* W, int n, int k0, int kb, int* fail_col) {
   __shared__ double a[NB][NB + 1];
+  __shared__ double rinv;
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 32
   if (tx < kb && ty < kb) a[ty][tx] = W[(long long)(k0 + ty) * n + k0 + tx];
   __syncthreads();
@@ -37,10 +41,12 @@ __global__ void potrf_diag_kernel(double* W, int n, int k0, int kb, int* fail_co
         atomicCAS(fail_col, -1, k0 + j);
         piv = 1.0;  // keep going with finite numbers; the call reports failure
       }
-      a[j][j] = sqrt(piv);
+      const double r = sqrt(piv);
+      a[j][j] = r;
+      rinv = 1.0 / r;
     }
     __syncthreads();
-    if (tx == 0 && ty > j && ty < kb) a[ty][j] /= a[j][j];
+    if (tx == 0 && ty > j && ty < kb) a[ty][j] *= rinv;
     __syncthreads();
     if (ty > j && ty < kb && tx > j && tx <= ty) a[ty][tx] -= a[ty][j] * a[tx][j];
     __syncthreads();
@@ -51,10 +57,13 @@ __global__ void potrf_diag_kernel(double* W, int n, int k0, int kb, int* fail_co
 // Rows i >= k0+kb of the panel: L21 = W21 L11^-T (forward substitution per row).
 __global__ void trsm_panel_kernel(double* W, int n, int k0, int kb) {
   __shared__ double l[NB][NB + 1];
+  __shared__ double dinv[NB];
   for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
     int r = e / NB, cc = e % NB;
     l[r][cc] = (r < kb && cc <= r) ? W[(long long)(k0 + r) * n + k0 + cc] : 0.0;
   }
+  __syncthreads();
+  for (int j = threadIdx.x; j < kb; j += blockDim.x) dinv[j] = 1.0 / l[j][j];
   __syncthreads();
   const int i = k0 + kb + blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -65,7 +74,7 @@ __global__ void trsm_panel_kernel(double* W, int n, int k0, int kb) {
     if (j < kb) {
       double s = row[j];
       for (int t = 0; t < j; ++t) s -= x[t] * l[j][t];
-      x[j] = s / l[j][j];
+      x[j] = s * dinv[j];
     }
   }
 #pragma unroll
@@ -102,10 +111,13 @@ __global__ void syrk_update_kernel(double* W, int n, int k0, int kb) {
 // X_k = L_kk^-1 B_k for the kb rows of block k (one thread per column).
 __global__ void trsm_diag_rows_kernel(const double* L, double* B, int n, int k0, int kb) {
   __shared__ double l[NB][NB + 1];
+  __shared__ double dinv[NB];
   for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
     int r = e / NB, cc = e % NB;
     l[r][cc] = (r < kb && cc <= r) ? L[(long long)(k0 + r) * n + k0 + cc] : 0.0;
   }
+  __syncthreads();
+  for (int j = threadIdx.x; j < kb; j += blockDim.x) dinv[j] = 1.0 / l[j][j];
   __syncthreads();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n) return;
@@ -115,7 +127,7 @@ __global__ void trsm_diag_rows_kernel(const double* L, double* B, int n, int k0,
     if (j < kb) {
       double s = B[(long long)(k0 + j) * n + c];
       for (int t = 0; t < j; ++t) s -= l[j][t] * x[t];
-      x[j] = s / l[j][j];
+      x[j] = s * dinv[j];
       B[(long long)(k0 + j) * n + c] = x[j];
     }
   }
