@@ -322,6 +322,15 @@ def window_eigs(Hd, Sd, E_lo, E_hi):
     return E[(E >= E_lo) & (E <= E_hi)]
 
 
+def window_vectors(Hd, Sd, E_lo, E_hi):
+    """Eigenpairs of Eq. 2 inside [E_lo, E_hi] (inclusive): eigenvalues
+    ascending and the coefficient vectors C (columns, S-orthonormal:
+    C^T S C = I), from LAPACK's symmetric-definite solver."""
+    E, C = scipy.linalg.eigh(Hd, Sd)
+    keep = (E >= E_lo) & (E <= E_hi)
+    return E[keep], C[:, keep]
+
+
 # ------------------------------------------------------------- pipeline -----
 
 def run_ofm(workload, Phis=None, pairs=None):

@@ -467,7 +467,7 @@ extern "C" ofm_status ofm_window_eigs(ofm_ctx* c, double E_lo, double E_hi, int 
   *n_out = i_hi - i_lo;
   const int m = std::min(*n_out, max_out);
   if (m > 0) OFM_TRY(ofm_window_bisect(c, i_lo, i_lo + m, E_out));
-  if (C_out && m > 0) OFM_TRY(ofm_window_vectors(c, m, C_out));
+  if (C_out && m > 0) OFM_TRY(ofm_window_vectors(c, m, E_out, C_out));
   return OFM_OK;
 }
 

@@ -125,7 +125,7 @@ void launch_scatter_dense(const DevFrag* d_fr, const DevPair* d_pairs, int npair
 namespace ofm {
 enum KClass {
   KC_CONVERT, KC_APPLY, KC_CONTRACT, KC_FINALIZE, KC_SCATTER, KC_EIG_INIT, KC_FILTER, KC_GRAM,
-  KC_RR, KC_ROTATE, KC_EXPORT, KC_CHOL, KC_REDUCE, KC_TRIDIAG, KC_BISECT, KC_COUNT
+  KC_RR, KC_ROTATE, KC_EXPORT, KC_CHOL, KC_REDUCE, KC_TRIDIAG, KC_BISECT, KC_VECTORS, KC_COUNT
 };
 struct KStat {
   long long launches = 0;
@@ -222,7 +222,8 @@ ofm_status ofm_window_factor(ofm_ctx* c);
 // eigenvalues below lo and below-or-at hi of the factored pencil
 ofm_status ofm_window_count(ofm_ctx* c, double lo, double hi, int* count_lo, int* count_hi);
 ofm_status ofm_window_bisect(ofm_ctx* c, int i_lo, int i_hi, double* E_out);
-ofm_status ofm_window_vectors(ofm_ctx* c, int m, double* C_out);
+// eigenvectors for the m eigenvalues E (host, ascending) of the last bisection
+ofm_status ofm_window_vectors(ofm_ctx* c, int m, const double* E, double* C_out);
 ofm_status ofm_tridiag_persistent(ofm_ctx* c, double* A, int n, double* d, double* e, double* tau,
                                   double* pg);
 void launch_count_below(const double* d, const double* e, int n, double x0, double x1, int* out,

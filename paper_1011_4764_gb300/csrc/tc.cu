@@ -586,8 +586,3 @@ ofm_status ofm_wait_status(ofm_ctx* c) {
   return OFM_OK;
 }
 
-ofm_status ofm_window_vectors(ofm_ctx* c, int m, double* C_out) {
-  (void)m;
-  (void)C_out;
-  return ofm_fail(c, OFM_ERR_INVALID, "window eigenvectors are not built yet");
-}

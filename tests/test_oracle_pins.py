@@ -265,6 +265,33 @@ def test_generalized_solver_two_independent_routes():
     assert np.max(np.abs(O.generalized_eigs(Hd, np.eye(n)) - np.linalg.eigvalsh(Hd))) < 1e-12
 
 
+def test_window_vectors_two_by_two_and_properties():
+    """Eq. 2 vectors: for the 2x2 pencil the eigenvector of E solves
+    (a - E) c0 + (b - E s) c1 = 0 with c^T S c = 1; for a random pencil the
+    vectors satisfy H C = S C diag(E) and C^T S C = I, with the eigenvalues
+    of the hand-written Cholesky + Jacobi route."""
+    a, b, c, s = -0.7, 0.21, -0.3, 0.35
+    Hd = np.array([[a, b], [b, c]])
+    Sd = np.array([[1.0, s], [s, 1.0]])
+    E, C = O.window_vectors(Hd, Sd, -10.0, 10.0)
+    for k in range(2):
+        v = np.array([-(b - E[k] * s), a - E[k]])
+        v /= math.sqrt(v @ Sd @ v)
+        assert min(np.max(np.abs(C[:, k] - v)), np.max(np.abs(C[:, k] + v))) < 1e-13
+    rng = np.random.default_rng(12)
+    n = 16
+    X = rng.standard_normal((n, n))
+    Sd = X @ X.T / n + 0.5 * np.eye(n)
+    Y = rng.standard_normal((n, n))
+    Hd = 0.5 * (Y + Y.T)
+    Eall = O.generalized_eigs_jacobi(Hd, Sd)
+    lo, hi = Eall[3] - 1e-9, Eall[9] + 1e-9
+    E, C = O.window_vectors(Hd, Sd, lo, hi)
+    assert len(E) == 7 and np.max(np.abs(E - Eall[3:10])) < 1e-11
+    assert np.max(np.abs(Hd @ C - Sd @ C * E)) < 1e-12
+    assert np.max(np.abs(C.T @ Sd @ C - np.eye(7))) < 1e-12
+
+
 def test_jacobi_rejects_indefinite_overlap():
     with pytest.raises(np.linalg.LinAlgError):
         O.generalized_eigs_jacobi(np.eye(2), np.array([[1.0, 2.0], [2.0, 1.0]]))
