@@ -9,12 +9,12 @@
 //    column suffices (the next column travels with p as a published row);
 //    the global-memory fallback meets twice.  The barrier spins a bounded
 //    number of times and reports a timeout instead of hanging.
-// 2. Eigenvalues by index with multisection: one warp per wanted
-//    eigenvalue; each lane counts the eigenvalues below one of 32 points of
-//    the current interval (Sturm sequence of T - x I written as the
-//    three-term recurrence of the leading principal minors, rescaled by
-//    powers of two, so a step needs no division), and the interval shrinks
-//    33-fold per round.
+// 2. Eigenvalues by index with multisection: one CTA of one to four warps
+//    per wanted eigenvalue; each thread counts the eigenvalues below one of
+//    32-128 points of the current interval (Sturm sequence of T - x I
+//    written as the three-term recurrence of the leading principal minors,
+//    rescaled by powers of two, so a step needs no division), and the
+//    interval shrinks 33- to 129-fold per round.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -75,6 +75,22 @@ __device__ __forceinline__ double block_sum(double s, double* red) {
   }
   __syncthreads();
   return red[32];
+}
+
+// Sum over the first four warps (one per SM sub-partition; their partial
+// sums cover the whole range), in a fixed order.  Fewer warps than the whole
+// CTA because each FP64 instruction of a warp occupies a sub-partition's
+// FP64 pipe for many cycles: sixteen warps' shuffle trees cost more than
+// the additions they save.
+__device__ __forceinline__ double sum4(double s, double* red) {
+  if (threadIdx.x < 128) {
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  }
+  __syncthreads();
+  const double t = (red[0] + red[1]) + (red[2] + red[3]);
+  __syncthreads();
+  return t;
 }
 
 __global__ void __launch_bounds__(512) tridiag_persistent_kernel(double* A, int n, double* d,
@@ -211,23 +227,31 @@ __global__ void __launch_bounds__(512) tridiag_smem_kernel(double* A, int n, dou
   for (int j = tid; j < n; j += nt) col[j] = A[j];   // column 0 = row 0 (A is symmetric)
   // nobody reads A after this barrier; CTA 0 then stores the Householder vectors in it
   if (!grid_sync(bar, nb)) return;
+  __shared__ double hh[3];   // alpha, tau, v0 of the current column
   for (int k = 0; k + 2 < n; ++k) {
-    const int m = n - k - 1;
     double s = 0.0;
-    for (int i = k + 2 + tid; i < n; i += nt) s += col[i] * col[i];
-    const double sig = block_sum(s, red);
-    const double x0 = col[k + 1];
-    double alpha, t, v0;
-    if (sig == 0.0) {
-      alpha = x0;
-      t = 0.0;
-      v0 = 1.0;
-    } else {
-      const double nrm = sqrt(x0 * x0 + sig);
-      alpha = (x0 > 0.0) ? -nrm : nrm;
-      v0 = x0 - alpha;
-      t = 2.0 / (v0 * v0 + sig);
+    if (tid < 128)
+      for (int i = k + 2 + tid; i < n; i += 128) s += col[i] * col[i];
+    const double sig = sum4(s, red);
+    // the scalar part once (FP64 square root and division are long
+    // sequences), broadcast through shared memory
+    if (tid == 0) {
+      const double x0 = col[k + 1];
+      if (sig == 0.0) {
+        hh[0] = x0;
+        hh[1] = 0.0;
+        hh[2] = 1.0;
+      } else {
+        const double nrm = sqrt(x0 * x0 + sig);
+        const double al = (x0 > 0.0) ? -nrm : nrm;
+        const double vv = x0 - al;
+        hh[0] = al;
+        hh[1] = 2.0 / (vv * vv + sig);
+        hh[2] = vv;
+      }
     }
+    __syncthreads();
+    const double alpha = hh[0], t = hh[1], v0 = hh[2];
     for (int i = k + 1 + tid; i < n; i += nt) {
       const double vi = (i == k + 1) ? v0 : col[i];
       v[i] = vi;
@@ -263,8 +287,9 @@ __global__ void __launch_bounds__(512) tridiag_smem_kernel(double* A, int n, dou
     }
     __syncthreads();
     double q = 0.0;
-    for (int j = k + 1 + tid; j < n; j += nt) q += v[j] * w[j];
-    const double K = 0.5 * t * block_sum(q, red);
+    if (tid < 128)
+      for (int j = k + 1 + tid; j < n; j += 128) q += v[j] * w[j];
+    const double K = 0.5 * t * sum4(q, red);
     for (int j = k + 1 + tid; j < n; j += nt) w[j] = fma(-K, v[j], w[j]);
     __syncthreads();
     // rank-2 update of the owned rows i > k
@@ -348,90 +373,92 @@ __global__ void count_below_kernel(const double* d, const double* e, int n, doub
     e2s[i] = (i < n - 1) ? e[i] * e[i] : 0.0;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    const double x[2] = {x0, x1};
-    int c[2];
-    sturm_counts<2>(ds, e2s, n, x, c);
-    out[0] = c[0];
-    out[1] = c[1];
+  // one shift per warp (separate SM sub-partitions)
+  if ((threadIdx.x & 31) == 0 && threadIdx.x < 64) {
+    const int k = threadIdx.x >> 5;
+    double x[1] = {k ? x1 : x0};
+    int c[1];
+    sturm_counts<1>(ds, e2s, n, x, c);
+    out[k] = c[0];
   }
 }
 
-// Multisection: lane groups of MS_LANES serve one eigenvalue index each and
-// every lane counts below MS_K shifts, so an eigenvalue sees MS_S shifts per
-// round and its interval shrinks (MS_S + 1)-fold.  One eigenvalue per warp
-// (32 lanes, one shift each): a warp's FP64 instructions occupy the FP64
-// pipe of its SM sub-partition for about 64 cycles each on this part, so
-// the work is spread over as many warps (sub-partitions) as there are
-// eigenvalues.  d and e^2 are staged in shared memory.
-constexpr int MS_LANES = 32, MS_K = 1, MS_S = MS_LANES * MS_K;
-constexpr int MS_GPW = 32 / MS_LANES;   // eigenvalues per warp
-constexpr unsigned MS_GMASK = MS_LANES == 32 ? 0xffffffffu : ((1u << MS_LANES) - 1u);
-__global__ void __launch_bounds__(256) multisection_kernel(const double* __restrict__ d,
-                                                           const double* __restrict__ e, int n,
-                                                           int i_lo, int m, double* out) {
+// Multisection: one CTA of MS_W warps per wanted eigenvalue index; thread j
+// counts the eigenvalues below the shift x_j = lo + (hi - lo)(j + 1)/(S + 1)
+// (S = 32 MS_W shifts), and the interval shrinks to the (S + 1)-th part
+// holding the eigenvalue.  On this part one warp issues an FP64 instruction
+// every 64 cycles at best while an SM retires one warp-wide FP64
+// instruction about every 19 cycles: up to four warps per SM cost little
+// more time per round than one, beyond that time grows with the warp
+// count.  So few wanted eigenvalues take four warps each (129-section,
+// fewest rounds); many take one (33-section, least work).  d and e^2 are
+// staged in shared memory.
+template <int MS_W>
+__global__ void __launch_bounds__(32 * MS_W) multisection_kernel(const double* __restrict__ d,
+                                                                 const double* __restrict__ e,
+                                                                 int n, int i_lo, int m,
+                                                                 double* out) {
+  constexpr int MS_S = 32 * MS_W;
   extern __shared__ double ms_smem[];
+  __shared__ int firstw[MS_W];
+  __shared__ double gl[2 * MS_W];
   double* ds = ms_smem;
   double* e2s = ms_smem + n;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int t = blockIdx.x;
+  if (t >= m) return;   // uniform over the CTA
+  const int idx = i_lo + t;
+  // staged d, e^2 and the Gershgorin interval
+  double a = DBL_MAX, b = -DBL_MAX;
+  for (int i = tid; i < n; i += blockDim.x) {
     ds[i] = d[i];
     e2s[i] = (i < n - 1) ? e[i] * e[i] : 0.0;
-  }
-  __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int grp = lane / MS_LANES, sub = lane % MS_LANES;
-  if (w * MS_GPW >= m) return;
-  const int t = w * MS_GPW + grp;            // output slot of this lane group
-  const int idx = i_lo + (t < m ? t : m - 1);
-  // Gershgorin interval
-  double a = DBL_MAX, b = -DBL_MAX;
-  for (int j = lane; j < n; j += 32) {
-    const double r = (j > 0 ? fabs(e[j - 1]) : 0.0) + (j < n - 1 ? fabs(e[j]) : 0.0);
-    a = fmin(a, d[j] - r);
-    b = fmax(b, d[j] + r);
+    const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < n - 1 ? fabs(e[i]) : 0.0);
+    a = fmin(a, d[i] - r);
+    b = fmax(b, d[i] + r);
   }
   for (int o = 16; o > 0; o >>= 1) {
     a = fmin(a, __shfl_xor_sync(0xffffffffu, a, o));
     b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
   }
+  if (lane == 0) {
+    gl[warp] = a;
+    gl[MS_W + warp] = b;
+  }
+  __syncthreads();
+  for (int w = 0; w < MS_W; ++w) {
+    a = fmin(a, gl[w]);
+    b = fmax(b, gl[MS_W + w]);
+  }
   const double wdt = fmax(fabs(a), fabs(b));
   double lo = a - 2.0 * DBL_EPSILON * wdt - DBL_MIN;
   double hi = b + 2.0 * DBL_EPSILON * wdt + DBL_MIN;
-  bool done = false;
   for (int it = 0; it < 64; ++it) {
-    done = done || (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + 4.0 * DBL_MIN);
-    if (__all_sync(0xffffffffu, done)) break;
-    // shift j of this group: x_j = lo + (hi - lo) (j + 1) / (S + 1)
-    double x[MS_K];
-    int cnt[MS_K];
-#pragma unroll
-    for (int k = 0; k < MS_K; ++k) x[k] = lo + (hi - lo) * (double)(sub * MS_K + k + 1) / (MS_S + 1);
-    sturm_counts<MS_K>(ds, e2s, n, x, cnt);
-    int first = MS_K;   // first local shift with more than idx eigenvalues below
-#pragma unroll
-    for (int k = MS_K - 1; k >= 0; --k)
-      if (cnt[k] > idx) first = k;
-    const unsigned ball = __ballot_sync(0xffffffffu, first < MS_K);
-    const unsigned gmask = (ball >> (grp * MS_LANES)) & MS_GMASK;
-    const int l = gmask ? __ffs(gmask) - 1 : 0;
-    const int fl = __shfl_sync(0xffffffffu, first, grp * MS_LANES + l);
-    if (!done) {
-      double nlo, nhi;
-      if (gmask == 0) {   // above every shift
-        nlo = lo + (hi - lo) * (double)MS_S / (MS_S + 1);
-        nhi = hi;
-      } else {
-        const int j = l * MS_K + fl;
-        nhi = lo + (hi - lo) * (double)(j + 1) / (MS_S + 1);
-        nlo = (j > 0) ? lo + (hi - lo) * (double)j / (MS_S + 1) : lo;
-      }
-      if (nhi == hi && nlo == lo) done = true;  // no progress at this precision
-      lo = nlo;
-      hi = nhi;
+    if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + 4.0 * DBL_MIN) break;
+    double x[1];
+    int cnt[1];
+    x[0] = lo + (hi - lo) * (double)(tid + 1) / (MS_S + 1);
+    sturm_counts<1>(ds, e2s, n, x, cnt);
+    const unsigned ball = __ballot_sync(0xffffffffu, cnt[0] > idx);
+    if (lane == 0) firstw[warp] = ball ? __ffs(ball) - 1 : 32;
+    __syncthreads();
+    int j = MS_S;   // first shift with more than idx eigenvalues below
+    for (int w = MS_W - 1; w >= 0; --w)
+      if (firstw[w] < 32) j = w * 32 + firstw[w];
+    __syncthreads();   // firstw is rewritten next round
+    double nlo, nhi;
+    if (j == MS_S) {   // above every shift
+      nlo = lo + (hi - lo) * (double)MS_S / (MS_S + 1);
+      nhi = hi;
+    } else {
+      nhi = lo + (hi - lo) * (double)(j + 1) / (MS_S + 1);
+      nlo = (j > 0) ? lo + (hi - lo) * (double)j / (MS_S + 1) : lo;
     }
+    if (nhi == hi && nlo == lo) break;   // no progress at this precision
+    lo = nlo;
+    hi = nhi;
   }
-  if (sub == 0 && t < m) out[t] = 0.5 * (lo + hi);
+  if (tid == 0) out[t] = 0.5 * (lo + hi);
 }
 }  // namespace ofm
 
@@ -515,7 +542,11 @@ bool launch_multisection(const double* d, const double* e, int n, int i_lo, int 
   if (smem > 200 * 1024) return false;
   static bool attr_set = false;
   if (!attr_set) {
-    if (cudaFuncSetAttribute(multisection_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(multisection_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024) != cudaSuccess ||
+        cudaFuncSetAttribute(multisection_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024) != cudaSuccess ||
+        cudaFuncSetAttribute(multisection_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              200 * 1024) != cudaSuccess ||
         cudaFuncSetAttribute(count_below_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              200 * 1024) != cudaSuccess) {
@@ -524,8 +555,13 @@ bool launch_multisection(const double* d, const double* e, int n, int i_lo, int 
     }
     attr_set = true;
   }
-  // four warps per CTA, MS_GPW eigenvalues per warp
-  const int per_block = 4 * MS_GPW;
-  multisection_kernel<<<(m + per_block - 1) / per_block, 128, smem, s>>>(d, e, n, i_lo, m, out);
+  // about four warps per SM of the GB300 (152 SMs) in total
+  const long long slots = 4LL * 152;
+  if ((long long)m * 4 <= slots)
+    multisection_kernel<4><<<m, 128, smem, s>>>(d, e, n, i_lo, m, out);
+  else if ((long long)m * 2 <= slots)
+    multisection_kernel<2><<<m, 64, smem, s>>>(d, e, n, i_lo, m, out);
+  else
+    multisection_kernel<1><<<m, 32, smem, s>>>(d, e, n, i_lo, m, out);
   return true;
 }
