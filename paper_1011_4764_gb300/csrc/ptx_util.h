@@ -35,6 +35,19 @@ __device__ __forceinline__ bool mbar_test(uint32_t addr, uint32_t parity) {
   return ok != 0;
 }
 
+// Like mbar_test, but the hardware may suspend the thread for a while before
+// reporting "not yet" (fewer issue slots spent while waiting).
+__device__ __forceinline__ bool mbar_try(uint32_t addr, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n"
+      " selp.b32 %0, 1, 0, P;\n}\n"
+      : "=r"(ok)
+      : "r"(addr), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
 // Bounded wait for the completion of phase `parity` of an mbarrier.
 __device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity, int* flag) {
   for (int i = 0; i < (1 << 24); ++i) {

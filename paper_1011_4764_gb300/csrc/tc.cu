@@ -2,25 +2,19 @@
 //     [S_ab | H_ab] = Phi_a[R]^T [Phi_b[R] | HPhi_b[R]]   (Sec. II),
 // M = n_a (padded to 128), N = 2 n_b (padded to a multiple of 16), K = |R|.
 //
-// One CTA (4 warps) per work item = (pair, rows [r0, r1) of a piece).  Per
-// K step of 32 grid points:
-//   1. cp.async brings the FP32 rows (states of a point are contiguous) of
-//      the 32 points into a raw staging buffer (two stages in flight);
-//   2. the CTA converts the raw rows into the operand tiles in the
-//      K-major, no-swizzle canonical layout of the MMA (core matrices of
-//      8 rows x 16 bytes, K-adjacent cores 128 bytes apart, 8-row groups
-//      one K-tile apart): TF32 (round to nearest), BF16 (round to nearest
-//      even), or the BF16 pair hi = bf16(x), lo = bf16(x - hi);
-//   3. one thread issues tcgen05.mma (kind::tf32 or kind::f16 with bf16
-//      operands, FP32 accumulation in tensor memory); the hi+lo split issues
-//      hi*hi + hi*lo + lo*hi into the same accumulator (lo*lo dropped);
-//      tcgen05.commit arrives on the stage's mbarrier when the MMAs finish,
-//      which frees that operand stage for the step after next.
-// The epilogue reads the accumulator with tcgen05.ld (warp w owns TMEM
-// lanes 32w..32w+31 = rows of the tile) and writes an FP32 partial tile;
-// a finalize kernel sums the partials of each pair in a fixed order.
-// Every wait is bounded: on timeout the CTA sets an error flag, drains its
-// copies, frees its tensor memory and returns.
+// The work is cut into items (pair, rows of a piece); a persistent CTA per SM
+// streams its items through a warp-specialised pipeline (one thread issues
+// bulk copies of the K step's point rows into a ring of raw stages; four
+// warps convert them into the K-major, no-swizzle canonical operand layout
+// of the MMA -- core matrices of 8 rows x 16 bytes, K-adjacent cores 128
+// bytes apart, 8-row groups one K-tile apart -- as TF32 (round to nearest),
+// BF16 (round to nearest even) or the BF16 pair hi = bf16(x),
+// lo = bf16(x - hi); one thread issues tcgen05.mma with FP32 accumulation in
+// tensor memory, hi*hi + hi*lo + lo*hi for the split (lo*lo dropped); four
+// warps read the accumulator with tcgen05.ld and write the item's FP32
+// partial tile).  A finalize kernel sums the partials of each pair in a
+// fixed order.  Every wait is bounded: on timeout the CTA sets an error
+// flag, drains its copies and MMAs, frees its tensor memory and returns.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -51,22 +45,10 @@ struct TcItem {
   long long part_off;   // FP32 partial tile of n_a x N
 };
 
-constexpr int KT = 32;          // grid points per K step
-constexpr int TC_THREADS = 128;
-constexpr int TILE_PAD = 2048;  // slack after every operand tile (bytes)
 
 enum { TC_TF32 = 0, TC_BF16 = 1, TC_BF16X3 = 2 };
 
 // ----------------------------------------------------------- PTX helpers --
-
-__device__ __forceinline__ void cp_async16(uint32_t saddr, const void* g) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr), "l"(g) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
 
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -142,65 +124,99 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 
 // ----------------------------------------------------------- the kernel ---
 
+// Fixed per plan: the largest row strides (floats), operand tile rows,
+// ring sizes and tile bytes.
 struct SmemLayout {
   int ldA, ldB;        // raw row strides (floats), the largest of the plan
   int Rb;              // B tile rows (largest Npad)
-  int raw_stage;       // bytes of one raw stage
-  int tileA, tileB;    // bytes of one operand tile (+ slack)
+  int kt;              // grid points per K step (operand stage): 64, or 32 where 64 does not fit
+  int raw_stage;       // bytes of one raw stage: rsteps x kt points x (ldA + 2 ldB) floats
+  int nraw;            // raw stages in the ring
+  int nop;             // operand stages in the ring (2..TS_NOP)
+  int rsteps;          // K steps per raw stage
+  int tileA, tileB;    // bytes of one operand tile
   int ntiles;          // operand tiles per operand (1, or 2 for hi+lo)
+  int nitems;          // work items of the plan
 };
 
-template <int KIND>
-__global__ void __launch_bounds__(TC_THREADS) tc_contract_kernel(
+constexpr int TS_THREADS = 448;  // warp 0 copies, 1 MMA, 2-9 convert, 10-13 epilogue
+constexpr int TS_NOP = 4;        // largest operand ring
+constexpr int TS_CONV = 8;       // converter warps
+constexpr int TS_MAXRAW = 8;
+constexpr int TS_ACC_COLS = 256; // columns of one accumulator (N <= 256); two of them
+
+// Persistent, warp-specialised contraction: CTA c takes items c, c + grid,
+// c + 2 grid, ...; every role walks the same item sequence, so a global step
+// counter g indexes the rings.
+//   warp 0   : its lanes issue bulk copies of the K step's point rows (a
+//              contiguous x-run of a piece is contiguous in both fragments'
+//              storage: one copy per run and operand, one run per lane) into
+//              raw stage g % nraw;
+//   warps 2-9: convert raw stage -> operand stage g % nop (canonical K-major
+//              layout, TF32 / BF16 / BF16 hi+lo), zero past the item's end;
+//   warp 1   : one thread issues the MMAs of the stage into the item's
+//              accumulator (two in tensor memory, alternating per item) and
+//              commits them to the stage's "empty" barrier, and after the
+//              item's last stage to the accumulator's "full" barrier;
+//   warps 10-13: read the accumulator (warp w owns lanes 32 (w % 4)..), write
+//              the item's FP32 partial tile, release the accumulator.
+// mbarriers: raw full (copy bytes) / empty (8 converter warps), operand
+// full (8 converter warps) / empty (MMA commit), accumulator full (MMA
+// commit) / empty (4 epilogue warps).  Every wait is bounded and also stops
+// when another role gave up; the CTA then waits (bounded) for its copies and
+// MMAs in flight, frees its tensor memory and returns.
+template <int KIND, int KT>
+__global__ void __launch_bounds__(TS_THREADS, 1) tc_contract_kernel(
     const DevFrag* __restrict__ fr, const TcPair* __restrict__ prs, const Piece* __restrict__ pcs,
     const TcItem* __restrict__ items, const float* __restrict__ states,
     const float* __restrict__ hphi, float* __restrict__ partials, int* flag, SmemLayout L) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) unsigned long long mbar[2];
+  __shared__ __align__(8) unsigned long long raw_full[TS_MAXRAW], raw_empty[TS_MAXRAW];
+  __shared__ __align__(8) unsigned long long op_full[TS_NOP], op_empty[TS_NOP], acc_full[2], acc_empty[2];
   __shared__ uint32_t tmem_slot;
+  __shared__ int abort_s, issued_s, mma_steps_s;
 
-  const TcItem it = items[blockIdx.x];
-  const TcPair pr = prs[it.pair];
-  const DevFrag A = fr[pr.a];
-  const DevFrag B = fr[pr.b];
-  const Piece pc = pcs[it.piece];
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int lenx = pc.len[0], leny = pc.len[1];
-  const int npts = (it.r1 - it.r0) * lenx;
-  const int niter = (npts + KT - 1) / KT;
-  const int N = pr.N, Npad = pr.Npad;
   constexpr int ESZ = (KIND == TC_TF32) ? 4 : 2;
   constexpr int E = 16 / ESZ;                 // elements per core row
   constexpr uint32_t LBO = 128;               // K-adjacent cores
   constexpr uint32_t SBO = (KT / E) * 128;    // next 8-row group
   constexpr int KSTEPS = (KT * ESZ) / 32;     // MMAs per K step (32 bytes of K each)
-
-  float* raw = reinterpret_cast<float*>(smem);
-  unsigned char* ops = smem + 2 * L.raw_stage;
-  // operand tile t of stage s: A tiles first, then B tiles
-  auto tileA = [&](int s, int t) { return ops + (size_t)s * L.ntiles * (L.tileA + L.tileB) + (size_t)t * L.tileA; };
-  auto tileB = [&](int s, int t) {
-    return ops + (size_t)s * L.ntiles * (L.tileA + L.tileB) + (size_t)L.ntiles * L.tileA + (size_t)t * L.tileB;
+  constexpr int NG = KT / E;                  // core groups along K
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nraw = L.nraw, nop = L.nop;
+  const int span = L.rsteps * KT;   // points per raw stage
+  unsigned char* raw = smem;
+  unsigned char* ops = smem + (size_t)nraw * L.raw_stage;
+  auto tileA = [&](int o, int t) {
+    return ops + (size_t)o * L.ntiles * (L.tileA + L.tileB) + (size_t)t * L.tileA;
+  };
+  auto tileB = [&](int o, int t) {
+    return ops + (size_t)o * L.ntiles * (L.tileA + L.tileB) + (size_t)L.ntiles * L.tileA +
+           (size_t)t * L.tileB;
   };
 
-  // zero every operand tile once: padding rows stay zero afterwards
-  {
-    const int total = 2 * L.ntiles * (L.tileA + L.tileB);
-    uint4* p = reinterpret_cast<uint4*>(ops);
-    for (int i = tid; i < total / 16; i += TC_THREADS) p[i] = make_uint4(0, 0, 0, 0);
-  }
   if (tid == 0) {
-    mbar_init(smem_u32(&mbar[0]), 1);
-    mbar_init(smem_u32(&mbar[1]), 1);
+    for (int i = 0; i < nraw; ++i) {
+      mbar_init(smem_u32(&raw_full[i]), 1);
+      mbar_init(smem_u32(&raw_empty[i]), TS_CONV);
+    }
+    for (int i = 0; i < L.nop; ++i) {
+      mbar_init(smem_u32(&op_full[i]), TS_CONV);
+      mbar_init(smem_u32(&op_empty[i]), 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(smem_u32(&acc_full[i]), 1);
+      mbar_init(smem_u32(&acc_empty[i]), 4);
+    }
     fence_mbar_init();
+    abort_s = 0;
+    issued_s = 0;
+    mma_steps_s = 0;
   }
-  // tensor memory: one column per accumulator column (power of two >= 32)
-  uint32_t ncols = 32;
-  while ((int)ncols < Npad) ncols <<= 1;
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tmem_slot)),
-                 "r"(ncols)
+                 "r"(2 * TS_ACC_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -208,179 +224,259 @@ __global__ void __launch_bounds__(TC_THREADS) tc_contract_kernel(
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
-  fence_async_smem();
 
-  const float* Pa = states + A.off;
-  const float* Pb = states + B.off;
-  const float* Hb = hphi + B.off;
-  const int qa = A.ld / 4, qb = B.ld / 4;           // 16-byte chunks per row
-  const int per_pt = qa + 2 * qb;
-  float* rawA0 = raw;                               // [KT][ldA]
-  const int rawAB = KT * L.ldA;                     // floats
+  // bounded wait that also ends when another role gave up
+  auto wait = [&](unsigned long long* bar, uint32_t parity) -> bool {
+    const uint32_t a = smem_u32(bar);
+    for (int i = 0; i < (1 << 20); ++i) {
+      if (mbar_try(a, parity)) return true;
+      if (*(volatile int*)&abort_s) return false;
+    }
+    atomicExch(flag, 1);
+    *(volatile int*)&abort_s = 1;
+    return false;
+  };
+  const int nitems = L.nitems;
 
-  // issue the cp.async copies of K step `step` into raw stage s
-  auto load_stage = [&](int step, int s) {
-    float* base = raw + (size_t)s * (L.raw_stage / 4);
-    float* rA = base;
-    float* rB = base + rawAB;
-    float* rH = rB + KT * L.ldB;
-    for (int c = tid; c < KT * per_pt; c += TC_THREADS) {
-      const int kk = c / per_pt, q = c - kk * per_pt;
-      const int k = step * KT + kk;
-      float* dst;
-      const float* src = nullptr;
-      if (q < qa) dst = rA + kk * L.ldA + 4 * q;
-      else if (q < qa + qb) dst = rB + kk * L.ldB + 4 * (q - qa);
-      else dst = rH + kk * L.ldB + 4 * (q - qa - qb);
-      if (k < npts) {
-        const int r = it.r0 + k / lenx, x = k - (k / lenx) * lenx;
-        const int y = r % leny, z = r / leny;
-        if (q < qa) {
-          const long long pa = ((long long)(pc.la[2] + z) * A.dext[1] + (pc.la[1] + y)) * A.dext[0] + pc.la[0] + x;
-          src = Pa + pa * A.ld + 4 * q;
-        } else {
-          const long long pb = ((long long)(pc.lb[2] + z) * B.dext[1] + (pc.lb[1] + y)) * B.dext[0] + pc.lb[0] + x;
-          src = (q < qa + qb) ? (Pb + pb * B.ld + 4 * (q - qa)) : (Hb + pb * B.ld + 4 * (q - qa - qb));
+  if (warp == 0) {
+    // ------------------------------------------------------------ copies
+    // one raw stage holds `span` points of the item (rsteps K steps); lane j
+    // issues the copies of runs j, j + 32, ...: run 0 starts at the stage's
+    // first point, run i > 0 at the start of the i-th following row
+    int gr = 0;
+    bool ok = true;
+    for (int ii = blockIdx.x; ii < nitems && ok; ii += gridDim.x) {
+      const TcItem it = items[ii];
+      const TcPair pr = prs[it.pair];
+      const DevFrag A = fr[pr.a], B = fr[pr.b];
+      const Piece pc = pcs[it.piece];
+      const int lenx = pc.len[0], leny = pc.len[1];
+      const int npts = (it.r1 - it.r0) * lenx;
+      for (int k0 = 0; k0 < npts; k0 += span, ++gr) {
+        const int s = gr % nraw, u = gr / nraw;
+        if (u > 0) {   // lane 0 waits; the verdict is the warp's (uniform control flow)
+          bool w = true;
+          if (lane == 0) w = wait(&raw_empty[s], (uint32_t)((u - 1) & 1));
+          ok = __shfl_sync(0xffffffffu, w ? 1 : 0, 0) != 0;
+          if (!ok) break;
         }
-        cp_async16(smem_u32(dst), src);
-      } else {
-        *reinterpret_cast<float4*>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int nk = min(span, npts - k0);
+        const uint32_t mb = smem_u32(&raw_full[s]);
+        if (lane == 0) mbar_arrive_expect(mb, (uint32_t)(nk * (A.ld + 2 * B.ld) * 4));
+        __syncwarp();
+        const int row0 = k0 / lenx, x0 = k0 - row0 * lenx;
+        const int nruns = (k0 + nk - 1) / lenx - row0 + 1;   // <= span
+        unsigned char* rA = raw + (size_t)s * L.raw_stage;
+        unsigned char* rB = rA + (size_t)span * L.ldA * 4;
+        unsigned char* rH = rB + (size_t)span * L.ldB * 4;
+        for (int j = lane; j < nruns; j += 32) {
+          const int x = j == 0 ? x0 : 0;
+          const int kstart = j == 0 ? k0 : (row0 + j) * lenx;
+          const int run = min(lenx - x, k0 + nk - kstart);
+          const int r = it.r0 + row0 + j;
+          const int y = r % leny, z = r / leny;
+          const long long pa =
+              ((long long)(pc.la[2] + z) * A.dext[1] + (pc.la[1] + y)) * A.dext[0] + pc.la[0] + x;
+          const long long pb =
+              ((long long)(pc.lb[2] + z) * B.dext[1] + (pc.lb[1] + y)) * B.dext[0] + pc.lb[0] + x;
+          const int kk = kstart - k0;
+          bulk_g2s(smem_u32(rA + (size_t)kk * A.ld * 4), states + A.off + pa * A.ld,
+                   (uint32_t)(run * A.ld * 4), mb);
+          bulk_g2s(smem_u32(rB + (size_t)kk * B.ld * 4), states + B.off + pb * B.ld,
+                   (uint32_t)(run * B.ld * 4), mb);
+          bulk_g2s(smem_u32(rH + (size_t)kk * B.ld * 4), hphi + B.off + pb * B.ld,
+                   (uint32_t)(run * B.ld * 4), mb);
+        }
+        if (lane == 0) *(volatile int*)&issued_s = gr + 1;
       }
     }
-    cp_async_commit();
-  };
-
-  // raw stage s -> operand tiles of stage s
-  auto convert_stage = [&](int s) {
-    const float* base = raw + (size_t)s * (L.raw_stage / 4);
-    const float* rA = base;
-    const float* rB = base + rawAB;
-    const float* rH = rB + KT * L.ldB;
-    // A rows = states of fragment a (rows >= n_a stay zero)
-    for (int row = tid; row < A.n; row += TC_THREADS) {
-      for (int g = 0; g < KT / E; ++g) {
-        const size_t off = (size_t)(row >> 3) * SBO + (size_t)g * LBO + (size_t)(row & 7) * 16;
-        float v[E];
+  } else if (warp == 1) {
+    // -------------------------------------------------------------- MMAs
+    if (lane == 0) {
+      constexpr uint32_t FMT = (KIND == TC_TF32) ? 2u : 1u;
+      int g = 0, item_no = 0;
+      bool ok = true;
+      for (int ii = blockIdx.x; ii < nitems && ok; ii += gridDim.x, ++item_no) {
+        const TcItem it = items[ii];
+        const TcPair pr = prs[it.pair];
+        const Piece pc = pcs[it.piece];
+        const int npts = (it.r1 - it.r0) * pc.len[0];
+        const int b = item_no & 1, ub = item_no >> 1;
+        if (ub > 0 && !(ok = wait(&acc_empty[b], (uint32_t)((ub - 1) & 1)))) break;
+        tc_fence_after();
+        const uint32_t idesc = instr_desc(FMT, 128, (uint32_t)pr.Npad);
+        const uint32_t dacc = tmem + (uint32_t)(b * TS_ACC_COLS);
+        for (int k0 = 0; k0 < npts; k0 += KT, ++g) {
+          const int o = g % nop, uo = g / nop;
+          if (!(ok = wait(&op_full[o], (uint32_t)(uo & 1)))) break;
+          tc_fence_after();
+          // descriptors of the stage's tiles; a K sub-step advances the
+          // start address by two core matrices (the field holds address >> 4)
+          const uint64_t ah0 = smem_desc(smem_u32(tileA(o, 0)), LBO, SBO);
+          const uint64_t bh0 = smem_desc(smem_u32(tileB(o, 0)), LBO, SBO);
+          uint64_t al0 = 0, bl0 = 0;
+          if constexpr (KIND == TC_BF16X3) {
+            al0 = smem_desc(smem_u32(tileA(o, 1)), LBO, SBO);
+            bl0 = smem_desc(smem_u32(tileB(o, 1)), LBO, SBO);
+          }
 #pragma unroll
-        for (int j = 0; j < E; ++j) v[j] = rA[(g * E + j) * L.ldA + row];
-        if constexpr (KIND == TC_TF32) {
-          uint4 w = make_uint4(f32_to_tf32(v[0]), f32_to_tf32(v[1]), f32_to_tf32(v[2]), f32_to_tf32(v[3]));
-          *reinterpret_cast<uint4*>(tileA(s, 0) + off) = w;
-        } else {
-          uint32_t hi[4], lo[4];
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            hi[j] = pack_bf16(v[2 * j], v[2 * j + 1]);
+          for (int ks = 0; ks < KSTEPS; ++ks) {
+            const uint64_t off = (uint64_t)((ks * 2 * LBO) >> 4);
+            mma<KIND>(dacc, ah0 + off, bh0 + off, idesc, (k0 > 0 || ks > 0) ? 1u : 0u);
             if constexpr (KIND == TC_BF16X3) {
-              __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162*>(&hi[j]);
-              const float2 hf = __bfloat1622float2(h);
-              lo[j] = pack_bf16(v[2 * j] - hf.x, v[2 * j + 1] - hf.y);
+              mma<KIND>(dacc, ah0 + off, bl0 + off, idesc, 1u);
+              mma<KIND>(dacc, al0 + off, bh0 + off, idesc, 1u);
             }
           }
-          *reinterpret_cast<uint4*>(tileA(s, 0) + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-          if constexpr (KIND == TC_BF16X3)
-            *reinterpret_cast<uint4*>(tileA(s, 1) + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+          mma_commit(smem_u32(&op_empty[o]));
+          *(volatile int*)&mma_steps_s = g + 1;
         }
+        if (!ok) break;
+        mma_commit(smem_u32(&acc_full[b]));
       }
     }
-    // B rows: columns 0..n_b-1 from Phi_b, n_b..2n_b-1 from H Phi_b
-    for (int row = tid; row < N; row += TC_THREADS) {
-      const bool h = row >= B.n;
-      const float* src = h ? rH : rB;
-      const int col = h ? row - B.n : row;
-      for (int g = 0; g < KT / E; ++g) {
-        const size_t off = (size_t)(row >> 3) * SBO + (size_t)g * LBO + (size_t)(row & 7) * 16;
-        float v[E];
+  } else if (warp < 2 + TS_CONV) {
+    // -------------------------------------------------------- conversion
+    const int ct = tid - 64;   // 0 .. 32 TS_CONV - 1
+    int gr = 0, go = 0;
+    bool ok = true;
+    for (int ii = blockIdx.x; ii < nitems && ok; ii += gridDim.x) {
+      const TcItem it = items[ii];
+      const TcPair pr = prs[it.pair];
+      const DevFrag A = fr[pr.a], B = fr[pr.b];
+      const Piece pc = pcs[it.piece];
+      const int npts = (it.r1 - it.r0) * pc.len[0];
+      const int N = pr.N;
+      // e -> (row, k group) without integer division: e / rows from a float
+      // reciprocal, corrected by one (exact for e < 2^24)
+      const float inv_a = 1.0f / (float)A.n, inv_n = 1.0f / (float)N;
+      for (int k0 = 0; k0 < npts && ok; k0 += span, ++gr) {
+        const int s = gr % nraw, u = gr / nraw;
+        // every lane waits (it reads the copied data); the verdict is the warp's
+        ok = __all_sync(0xffffffffu, wait(&raw_full[s], (uint32_t)(u & 1)));
+        if (!ok) break;
+        const int nkr = min(span, npts - k0);
+        const float* rA = reinterpret_cast<const float*>(raw + (size_t)s * L.raw_stage);
+        const float* rB = rA + (size_t)span * L.ldA;
+        const float* rH = rB + (size_t)span * L.ldB;
+        for (int j0 = 0; j0 < nkr; j0 += KT, ++go) {
+          const int o = go % nop, uo = go / nop;
+          if (uo > 0) {
+            ok = __all_sync(0xffffffffu, wait(&op_empty[o], (uint32_t)((uo - 1) & 1)));
+            if (!ok) break;
+          }
+          const int nk = min(KT, nkr - j0);
+          // operand rows: A = states of fragment a; B = columns 0..n_b-1 from
+          // Phi_b, n_b..2n_b-1 from H Phi_b
+          for (int e = ct; e < (A.n + N) * NG; e += 32 * TS_CONV) {
+            const bool isA = e < A.n * NG;
+            const int e2 = isA ? e : e - A.n * NG;
+            const int rows = isA ? A.n : N;
+            int gq = (int)((float)e2 * (isA ? inv_a : inv_n));
+            if (gq * rows > e2) --gq;
+            else if ((gq + 1) * rows <= e2) ++gq;
+            const int row = e2 - gq * rows;
+            const float* src;
+            int col, ld;
+            if (isA) {
+              src = rA;
+              col = row;
+              ld = A.ld;
+            } else {
+              const bool h = row >= B.n;
+              src = h ? rH : rB;
+              col = h ? row - B.n : row;
+              ld = B.ld;
+            }
+            src += (size_t)j0 * ld + col;
+            float v[E];
 #pragma unroll
-        for (int j = 0; j < E; ++j) v[j] = src[(g * E + j) * L.ldB + col];
-        if constexpr (KIND == TC_TF32) {
-          uint4 w = make_uint4(f32_to_tf32(v[0]), f32_to_tf32(v[1]), f32_to_tf32(v[2]), f32_to_tf32(v[3]));
-          *reinterpret_cast<uint4*>(tileB(s, 0) + off) = w;
-        } else {
-          uint32_t hi[4], lo[4];
+            for (int j = 0; j < E; ++j) {
+              const int kk = gq * E + j;
+              v[j] = kk < nk ? src[kk * ld] : 0.f;
+            }
+            const size_t off = (size_t)(row >> 3) * SBO + (size_t)gq * LBO + (size_t)(row & 7) * 16;
+            unsigned char* t0 = isA ? tileA(o, 0) : tileB(o, 0);
+            if constexpr (KIND == TC_TF32) {
+              *reinterpret_cast<uint4*>(t0 + off) =
+                  make_uint4(f32_to_tf32(v[0]), f32_to_tf32(v[1]), f32_to_tf32(v[2]), f32_to_tf32(v[3]));
+            } else {
+              uint32_t hi[4], lo[4];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            hi[j] = pack_bf16(v[2 * j], v[2 * j + 1]);
-            if constexpr (KIND == TC_BF16X3) {
-              __nv_bfloat162 hh = *reinterpret_cast<__nv_bfloat162*>(&hi[j]);
-              const float2 hf = __bfloat1622float2(hh);
-              lo[j] = pack_bf16(v[2 * j] - hf.x, v[2 * j + 1] - hf.y);
+              for (int j = 0; j < 4; ++j) {
+                hi[j] = pack_bf16(v[2 * j], v[2 * j + 1]);
+                if constexpr (KIND == TC_BF16X3) {
+                  __nv_bfloat162 hh = *reinterpret_cast<__nv_bfloat162*>(&hi[j]);
+                  const float2 hf = __bfloat1622float2(hh);
+                  lo[j] = pack_bf16(v[2 * j] - hf.x, v[2 * j + 1] - hf.y);
+                }
+              }
+              *reinterpret_cast<uint4*>(t0 + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+              if constexpr (KIND == TC_BF16X3) {
+                unsigned char* t1 = isA ? tileA(o, 1) : tileB(o, 1);
+                *reinterpret_cast<uint4*>(t1 + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+              }
             }
           }
-          *reinterpret_cast<uint4*>(tileB(s, 0) + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-          if constexpr (KIND == TC_BF16X3)
-            *reinterpret_cast<uint4*>(tileB(s, 1) + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+          fence_async_smem();   // generic-proxy writes -> tensor-core reads
+          __syncwarp();
+          if (lane == 0) mbar_arrive(smem_u32(&op_full[o]));
         }
+        if (!ok) break;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&raw_empty[s]));   // every K step of the stage read
       }
     }
-  };
-
-  constexpr uint32_t FMT = (KIND == TC_TF32) ? 2u : 1u;
-  const uint32_t idesc = instr_desc(FMT, 128, (uint32_t)Npad);
-  bool ok = true;
-  if (niter > 0) load_stage(0, 0);
-  for (int step = 0; step < niter && ok; ++step) {
-    const int s = step & 1;
-    if (step + 1 < niter) load_stage(step + 1, s ^ 1);
-    else cp_async_commit();                     // keep the group count uniform
-    cp_async_wait<1>();
-    __syncthreads();                            // raw stage s visible to all threads
-    if (step >= 2) ok = mbar_wait(smem_u32(&mbar[s]), (uint32_t)(((step - 2) >> 1) & 1), flag);
-    if (!__syncthreads_and(ok)) {
-      ok = false;
-      break;
-    }
-    convert_stage(s);
-    fence_async_smem();                         // generic-proxy writes -> tensor-core reads
-    __syncthreads();
-    if (tid == 0) {
+  } else {
+    // ---------------------------------------------------------- epilogue
+    const int q = warp & 3;   // tensor-memory lane quadrant of this warp
+    int item_no = 0;
+    bool ok = true;
+    for (int ii = blockIdx.x; ii < nitems && ok; ii += gridDim.x, ++item_no) {
+      const TcItem it = items[ii];
+      const TcPair pr = prs[it.pair];
+      const int na = fr[pr.a].n, N = pr.N, Npad = pr.Npad;
+      const int b = item_no & 1, ub = item_no >> 1;
+      ok = __all_sync(0xffffffffu, wait(&acc_full[b], (uint32_t)(ub & 1)));
+      if (!ok) break;
       tc_fence_after();
+      float* out = partials + it.part_off;
+      const int row = q * 32 + lane;
+      for (int c0 = 0; c0 < Npad; c0 += 8) {
+        float v[8];
+        tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * TS_ACC_COLS + c0), v);
+        if (row < na) {
 #pragma unroll
-      for (int ks = 0; ks < KSTEPS; ++ks) {
-        const uint32_t aoff = ks * 2 * LBO, boff = ks * 2 * LBO;
-        const uint64_t ah = smem_desc(smem_u32(tileA(s, 0)) + aoff, LBO, SBO);
-        const uint64_t bh = smem_desc(smem_u32(tileB(s, 0)) + boff, LBO, SBO);
-        const uint32_t acc0 = (step > 0 || ks > 0) ? 1u : 0u;
-        mma<KIND>(tmem, ah, bh, idesc, acc0);
-        if constexpr (KIND == TC_BF16X3) {
-          const uint64_t al = smem_desc(smem_u32(tileA(s, 1)) + aoff, LBO, SBO);
-          const uint64_t bl = smem_desc(smem_u32(tileB(s, 1)) + boff, LBO, SBO);
-          mma<KIND>(tmem, ah, bl, idesc, 1u);
-          mma<KIND>(tmem, al, bh, idesc, 1u);
+          for (int j = 0; j < 8; ++j)
+            if (c0 + j < N) out[(long long)row * N + c0 + j] = v[j];
         }
       }
-      mma_commit(smem_u32(&mbar[s]));
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&acc_empty[b]));
     }
   }
-  cp_async_wait<0>();
-  // wait for the last committed MMAs, then read the accumulator
-  if (ok && niter > 0) {
-    const int last = niter - 1;
-    ok = mbar_wait(smem_u32(&mbar[last & 1]), (uint32_t)((last >> 1) & 1), flag);
-  }
-  ok = __syncthreads_and(ok);
-  tc_fence_after();
-  if (ok) {
-    float* out = partials + it.part_off;
-    const int row = warp * 32 + lane;
-    for (int c0 = 0; c0 < Npad; c0 += 8) {
-      float v[8];
-      tmem_ld8(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-      if (row < A.n && niter > 0) {
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-          if (c0 + j < N) out[(long long)row * N + c0 + j] = v[j];
-      } else if (row < A.n) {
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-          if (c0 + j < N) out[(long long)row * N + c0 + j] = 0.f;
-      }
-    }
+
+  __syncthreads();
+  if (abort_s && tid == 0) {
+    // drain before the shared and tensor memory are released: the copies of
+    // the last issued stages and the MMAs of the last committed stage
+    auto drain = [&](unsigned long long* bar, uint32_t parity) {
+      const uint32_t a = smem_u32(bar);
+      for (int i = 0; i < (1 << 24) && !mbar_test(a, parity); ++i)
+        if (i > 64) __nanosleep(64);
+    };
+    const int issued = issued_s;
+    for (int g = max(0, issued - nraw); g < issued; ++g)
+      drain(&raw_full[g % nraw], (uint32_t)((g / nraw) & 1));
+    const int ms = mma_steps_s;
+    if (ms > 0) drain(&op_empty[(ms - 1) % nop], (uint32_t)(((ms - 1) / nop) & 1));
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols)
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(2 * TS_ACC_COLS)
                  : "memory");
 }
 
@@ -494,16 +590,32 @@ ofm_status ofm_plan_extra(ofm_ctx* c) {
     L.ldA = ldA;
     L.ldB = ldB;
     L.Rb = Rb;
-    L.raw_stage = KT * (ldA + 2 * ldB) * 4;
     const int esz = (k == TC_TF32) ? 4 : 2;
-    L.tileA = 128 * KT * esz + TILE_PAD;
-    L.tileB = Rb * KT * esz + TILE_PAD;
     L.ntiles = (k == TC_BF16X3) ? 2 : 1;
-    t->smem[k] = 2 * (size_t)L.raw_stage + 2 * (size_t)L.ntiles * (L.tileA + L.tileB);
-  }
-  if (t->smem[TC_BF16X3] > 220 * 1024 || t->smem[TC_TF32] > 220 * 1024) {
-    t->why = "tensor-core staging does not fit shared memory for these state counts";
-    return OFM_OK;
+    L.nitems = (int)t->items.size();
+    // the longest K step, then the largest raw stages (fewest per-stage
+    // costs), then the deepest operand ring, that leave two raw stages
+    const long long budget = 216 * 1024;
+    L.nraw = 0;
+    for (L.kt = 64; L.kt >= 32 && L.nraw < 2; L.kt /= 2) {
+      L.tileA = (128 * L.kt * esz + 1023) / 1024 * 1024;
+      L.tileB = (Rb * L.kt * esz + 1023) / 1024 * 1024;
+      for (L.rsteps = 128 / L.kt; L.rsteps >= 1; L.rsteps /= 2) {
+        L.raw_stage = (L.rsteps * L.kt * (ldA + 2 * ldB) * 4 + 1023) / 1024 * 1024;
+        for (L.nop = TS_NOP; L.nop >= 2; --L.nop) {
+          const long long ops = (long long)L.nop * L.ntiles * (L.tileA + L.tileB);
+          L.nraw = (int)std::min<long long>(TS_MAXRAW, (budget - ops) / L.raw_stage);
+          if (L.nraw >= 2) break;
+        }
+        if (L.nraw >= 2) break;
+      }
+      if (L.nraw >= 2) break;
+    }
+    if (L.nraw < 2) {
+      t->why = "tensor-core staging does not fit shared memory for these state counts";
+      return OFM_OK;
+    }
+    t->smem[k] = (size_t)L.nraw * L.raw_stage + (size_t)L.nop * L.ntiles * (L.tileA + L.tileB);
   }
   OFM_TRY(ofm_ensure(c, t->d_pairs, sizeof(TcPair) * std::max<size_t>(1, t->pairs.size()), "tc pairs"));
   OFM_TRY(ofm_ensure(c, t->d_items, sizeof(TcItem) * std::max<size_t>(1, t->items.size()), "tc items"));
@@ -514,9 +626,12 @@ ofm_status ofm_plan_extra(ofm_ctx* c) {
   OFM_CUDA(c, cudaMemcpyAsync(t->d_items.p, t->items.data(), sizeof(TcItem) * t->items.size(), cudaMemcpyHostToDevice, c->stream));
   OFM_CUDA(c, cudaMemcpyAsync(t->d_pieces.p, t->pieces.data(), sizeof(Piece) * t->pieces.size(), cudaMemcpyHostToDevice, c->stream));
   OFM_CUDA(c, cudaMemsetAsync(t->flag.p, 0, sizeof(int), c->stream));
-  OFM_CUDA(c, cudaFuncSetAttribute(tc_contract_kernel<TC_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem[TC_TF32]));
-  OFM_CUDA(c, cudaFuncSetAttribute(tc_contract_kernel<TC_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem[TC_BF16]));
-  OFM_CUDA(c, cudaFuncSetAttribute(tc_contract_kernel<TC_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem[TC_BF16X3]));
+  OFM_CUDA(c, cudaFuncSetAttribute(tc_contract_kernel<TC_TF32, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 216 * 1024));
+  OFM_CUDA(c, cudaFuncSetAttribute(tc_contract_kernel<TC_BF16, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 216 * 1024));
+  OFM_CUDA(c, cudaFuncSetAttribute(tc_contract_kernel<TC_BF16X3, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 216 * 1024));
+  OFM_CUDA(c, cudaFuncSetAttribute(tc_contract_kernel<TC_TF32, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 216 * 1024));
+  OFM_CUDA(c, cudaFuncSetAttribute(tc_contract_kernel<TC_BF16, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 216 * 1024));
+  OFM_CUDA(c, cudaFuncSetAttribute(tc_contract_kernel<TC_BF16X3, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 216 * 1024));
   t->ok = true;
   return OFM_OK;
 }
@@ -529,21 +644,32 @@ ofm_status ofm_contract_tc(ofm_ctx* c, ofm_precision prec) {
   {
     KTimer kt(c, KC_CONTRACT, 1, c->contract_bytes, (double)c->flops);
     if (nit > 0) {
-      if (kind == TC_TF32)
-        tc_contract_kernel<TC_TF32><<<nit, TC_THREADS, t->smem[kind], c->stream>>>(
-            (const DevFrag*)c->d_frags.p, (const TcPair*)t->d_pairs.p, (const Piece*)t->d_pieces.p,
-            (const TcItem*)t->d_items.p, (const float*)c->states.p, (const float*)c->hphi.p,
-            (float*)t->partials.p, (int*)t->flag.p, t->lay[kind]);
-      else if (kind == TC_BF16)
-        tc_contract_kernel<TC_BF16><<<nit, TC_THREADS, t->smem[kind], c->stream>>>(
-            (const DevFrag*)c->d_frags.p, (const TcPair*)t->d_pairs.p, (const Piece*)t->d_pieces.p,
-            (const TcItem*)t->d_items.p, (const float*)c->states.p, (const float*)c->hphi.p,
-            (float*)t->partials.p, (int*)t->flag.p, t->lay[kind]);
-      else
-        tc_contract_kernel<TC_BF16X3><<<nit, TC_THREADS, t->smem[kind], c->stream>>>(
-            (const DevFrag*)c->d_frags.p, (const TcPair*)t->d_pairs.p, (const Piece*)t->d_pieces.p,
-            (const TcItem*)t->d_items.p, (const float*)c->states.p, (const float*)c->hphi.p,
-            (float*)t->partials.p, (int*)t->flag.p, t->lay[kind]);
+      const int grid = std::min(nit, 152);   // one persistent CTA per SM
+      const SmemLayout& L = t->lay[kind];
+      const DevFrag* fr = (const DevFrag*)c->d_frags.p;
+      const TcPair* pr = (const TcPair*)t->d_pairs.p;
+      const Piece* pc = (const Piece*)t->d_pieces.p;
+      const TcItem* itm = (const TcItem*)t->d_items.p;
+      const float* st = (const float*)c->states.p;
+      const float* hp = (const float*)c->hphi.p;
+      float* part = (float*)t->partials.p;
+      int* fl = (int*)t->flag.p;
+      const size_t sm = t->smem[kind];
+      if (L.kt == 64) {
+        if (kind == TC_TF32)
+          tc_contract_kernel<TC_TF32, 64><<<grid, TS_THREADS, sm, c->stream>>>(fr, pr, pc, itm, st, hp, part, fl, L);
+        else if (kind == TC_BF16)
+          tc_contract_kernel<TC_BF16, 64><<<grid, TS_THREADS, sm, c->stream>>>(fr, pr, pc, itm, st, hp, part, fl, L);
+        else
+          tc_contract_kernel<TC_BF16X3, 64><<<grid, TS_THREADS, sm, c->stream>>>(fr, pr, pc, itm, st, hp, part, fl, L);
+      } else {
+        if (kind == TC_TF32)
+          tc_contract_kernel<TC_TF32, 32><<<grid, TS_THREADS, sm, c->stream>>>(fr, pr, pc, itm, st, hp, part, fl, L);
+        else if (kind == TC_BF16)
+          tc_contract_kernel<TC_BF16, 32><<<grid, TS_THREADS, sm, c->stream>>>(fr, pr, pc, itm, st, hp, part, fl, L);
+        else
+          tc_contract_kernel<TC_BF16X3, 32><<<grid, TS_THREADS, sm, c->stream>>>(fr, pr, pc, itm, st, hp, part, fl, L);
+      }
     }
     OFM_CUDA(c, cudaGetLastError());
   }
