@@ -76,12 +76,23 @@ def roofline_for(name, s, pk, precision):
                  peak=FP64_PEAK_TFLOPS, peak_source="FP64 issue rate x SMs x max clock",
                  algorithmic_flops_per_launch=per)
     elif name == "contract" and precision in ("tf32", "bf16", "bf16x3"):
+        # attainable = min(tensor peak of the precision, intensity x HBM); the
+        # binding one is the bound reported
         per = s["flops"] / max(1, s["launches"])
+        per_b = s["bytes"] / max(1, s["launches"])
         bf16 = pk["bf16_tflops"]
-        peak = {"bf16": bf16, "bf16x3": bf16 / 3.0, "tf32": bf16 * 1.1 / 2.25}[precision]
-        r.update(bound="tensor", unit="TFLOP/s", achieved=per / (ms * 1e-3) / 1e12, peak=peak,
-                 peak_source=pk["source"] + " bf16 burst x dtype ratio (tf32 1.1/2.25, hi+lo 1/3)",
-                 algorithmic_flops_per_launch=per)
+        tpeak = {"bf16": bf16, "bf16x3": bf16 / 3.0, "tf32": bf16 * 1.1 / 2.25}[precision]
+        intensity = per / per_b if per_b > 0 else float("inf")
+        if intensity * pk["hbm_gbs"] / 1e3 < tpeak:
+            r.update(bound="hbm", unit="GB/s", achieved=per_b / (ms * 1e-3) / 1e9, peak=pk["hbm_gbs"],
+                     peak_source=pk["source"] + " copy bandwidth (intensity %.1f flop/B is below "
+                     "the tensor ridge)" % intensity,
+                     algorithmic_bytes_per_launch=per_b, algorithmic_flops_per_launch=per,
+                     tflops=per / (ms * 1e-3) / 1e12, tensor_peak_tflops=tpeak)
+        else:
+            r.update(bound="tensor", unit="TFLOP/s", achieved=per / (ms * 1e-3) / 1e12, peak=tpeak,
+                     peak_source=pk["source"] + " bf16 burst x dtype ratio (tf32 1.1/2.25, hi+lo 1/3)",
+                     algorithmic_flops_per_launch=per)
     else:
         per = s["flops"] / max(1, s["launches"])
         r.update(bound="alu", unit="TFLOP/s", achieved=per / (ms * 1e-3) / 1e12,

@@ -55,6 +55,7 @@ struct EigWork {
   size_t rr_smem = 0, rot_smem = 0;   // dynamic shared memory of the two kernels
   int rot_blocks = 1;
   ApplyGrid fgrid;                    // launch shape of the filter steps
+  struct TcPlan* gtc = nullptr;       // Gram on tensor cores (TF32 hi+lo), FP32 storage
   bool ready = false;
   // algorithmic traffic / work per launch: a filter step streams the block
   // in, the previous block (three-term steps) and the block out, plus V
@@ -71,6 +72,7 @@ void ofm_eig_free(ofm_ctx* c) {
                     &w->rpart};
   for (DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
+  ofm_tc_plan_free(w->gtc);
   delete w;
   c->eig = nullptr;
 }
@@ -720,6 +722,17 @@ static ofm_status eig_setup(ofm_ctx* c, int guard_opt) {
   make_items_simt(w->efr, sp, 64, 1024, w->gpairs, w->gpieces, w->gitems, w->gpart);
   w->gblk = 0;
   for (auto& p : w->gpairs) w->gblk = std::max<long long>(w->gblk, p.blk_off + 2LL * w->efr[p.a].n * w->efr[p.b].n);
+  // FP32 storage: the same Gram on tensor cores with TF32 hi+lo operands
+  // (products to about 2^-22, FP32 accumulation), when the blocks fit
+  if (!fp64) {
+    std::vector<long long> goff(nf);
+    long long gk = 0;
+    for (int a = 0; a < nf; ++a) {
+      goff[a] = w->gpairs[a].blk_off;
+      gk += sp[a].kh;
+    }
+    OFM_TRY(ofm_tc_plan_build(c, &w->gtc, w->efr, sp, goff, gk));
+  }
 
   for (int i = 0; i < 4; ++i) OFM_TRY(ofm_ensure(c, w->buf[i], w->elems * es, "eigensolver block"));
   for (int i = 0; i < 4; ++i) OFM_CUDA(c, cudaMemsetAsync(w->buf[i].p, 0, w->elems * es, c->stream));
@@ -776,7 +789,11 @@ static ofm_status eig_rr(ofm_ctx* c, int y, int hy, int xo, int hxo, unsigned lo
   const bool fp64 = c->storage == OFM_STORE_FP64;
   const int nf = c->nfrag;
   cudaStream_t s = c->stream;
-  {
+  if (!fp64 && ofm_tc_plan_ok(w->gtc, OFM_TC_TF32X3)) {
+    OFM_TRY(ofm_tc_run(c, w->gtc, OFM_TC_TF32X3, (const DevFrag*)w->d_efr.p, w->buf[y].p,
+                       w->buf[hy].p, (double*)w->blocks.p, KC_GRAM, KC_GRAM, w->gram_bytes,
+                       w->gram_flops));
+  } else {
   KTimer kt(c, KC_GRAM, 2, w->gram_bytes, w->gram_flops);
   launch_contract_simt(fp64 ? OFM_PREC_FP64 : OFM_PREC_FP32, fp64, (const DevFrag*)w->d_efr.p,
                        (const DevPair*)w->d_gpairs.p, (const Piece*)w->d_gpieces.p,

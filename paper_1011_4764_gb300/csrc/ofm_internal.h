@@ -200,8 +200,10 @@ struct ofm_ctx {
 };
 
 // words of the context's 16-int flag buffer: 0 pivot flag and 2..3 window
-// counts (window solver), 8 staged-stencil wait timeout
+// counts (window solver), 8 staged-stencil wait timeout, 9 tensor-core wait
+// timeout
 constexpr int OFM_FLAG_STENCIL = 8;
+constexpr int OFM_FLAG_TC = 9;
 
 // helpers used by every translation unit
 ofm_status ofm_fail(ofm_ctx* c, ofm_status s, const std::string& msg);
@@ -217,6 +219,16 @@ void ofm_eig_free(ofm_ctx* c);
 void ofm_prof_release(ofm_ctx* c);            // waits for and frees timing events
 void ofm_tc_free(ofm_ctx* c);
 ofm_status ofm_contract_tc(ofm_ctx* c, ofm_precision prec);
+// tensor-core plans over any fragment table (assembly, eigensolver Gram)
+enum { OFM_TC_TF32 = 0, OFM_TC_BF16 = 1, OFM_TC_BF16X3 = 2, OFM_TC_TF32X3 = 3 };
+ofm_status ofm_tc_plan_build(ofm_ctx* c, struct TcPlan** tp, const std::vector<ofm::DevFrag>& fr,
+                             const std::vector<ofm::HostPair>& pairs,
+                             const std::vector<long long>& blk_off, long long kh);
+ofm_status ofm_tc_run(ofm_ctx* c, struct TcPlan* t, int kind, const ofm::DevFrag* d_frags,
+                      const void* states, const void* hphi, double* blocks, int kclass_contract,
+                      int kclass_finalize, double bytes, double flops);
+bool ofm_tc_plan_ok(const struct TcPlan* t, int kind);   // the kind's staging fits
+void ofm_tc_plan_free(struct TcPlan* t);
 ofm_status ofm_wait_status(ofm_ctx* c);       // OFM_ERR_TIMEOUT if a bounded wait gave up
 ofm_status ofm_window_factor(ofm_ctx* c);
 // eigenvalues below lo and below-or-at hi of the factored pencil

@@ -46,7 +46,12 @@ struct TcItem {
 };
 
 
-enum { TC_TF32 = 0, TC_BF16 = 1, TC_BF16X3 = 2 };
+// operand kinds: TF32, BF16, BF16 hi+lo, TF32 hi+lo (the last for FP32-class
+// Gram matrices: hi = tf32(x), lo = tf32(x - hi), products to about 2^-22)
+enum { TC_TF32 = 0, TC_BF16 = 1, TC_BF16X3 = 2, TC_TF32X3 = 3, TC_NKIND = 4 };
+
+template <int KIND> constexpr bool is_tf32() { return KIND == TC_TF32 || KIND == TC_TF32X3; }
+template <int KIND> constexpr bool is_split() { return KIND == TC_BF16X3 || KIND == TC_TF32X3; }
 
 // ----------------------------------------------------------- PTX helpers --
 
@@ -78,7 +83,7 @@ __host__ __device__ constexpr uint32_t instr_desc(uint32_t fmt, uint32_t M, uint
 template <int KIND>
 __device__ __forceinline__ void mma(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                     uint32_t accum) {
-  if constexpr (KIND == TC_TF32) {
+  if constexpr (is_tf32<KIND>()) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
@@ -176,7 +181,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1) tc_contract_kernel(
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_s, issued_s, mma_steps_s;
 
-  constexpr int ESZ = (KIND == TC_TF32) ? 4 : 2;
+  constexpr int ESZ = is_tf32<KIND>() ? 4 : 2;
   constexpr int E = 16 / ESZ;                 // elements per core row
   constexpr uint32_t LBO = 128;               // K-adjacent cores
   constexpr uint32_t SBO = (KT / E) * 128;    // next 8-row group
@@ -293,7 +298,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1) tc_contract_kernel(
   } else if (warp == 1) {
     // -------------------------------------------------------------- MMAs
     if (lane == 0) {
-      constexpr uint32_t FMT = (KIND == TC_TF32) ? 2u : 1u;
+      constexpr uint32_t FMT = is_tf32<KIND>() ? 2u : 1u;
       int g = 0, item_no = 0;
       bool ok = true;
       for (int ii = blockIdx.x; ii < nitems && ok; ii += gridDim.x, ++item_no) {
@@ -315,7 +320,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1) tc_contract_kernel(
           const uint64_t ah0 = smem_desc(smem_u32(tileA(o, 0)), LBO, SBO);
           const uint64_t bh0 = smem_desc(smem_u32(tileB(o, 0)), LBO, SBO);
           uint64_t al0 = 0, bl0 = 0;
-          if constexpr (KIND == TC_BF16X3) {
+          if constexpr (is_split<KIND>()) {
             al0 = smem_desc(smem_u32(tileA(o, 1)), LBO, SBO);
             bl0 = smem_desc(smem_u32(tileB(o, 1)), LBO, SBO);
           }
@@ -323,7 +328,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1) tc_contract_kernel(
           for (int ks = 0; ks < KSTEPS; ++ks) {
             const uint64_t off = (uint64_t)((ks * 2 * LBO) >> 4);
             mma<KIND>(dacc, ah0 + off, bh0 + off, idesc, (k0 > 0 || ks > 0) ? 1u : 0u);
-            if constexpr (KIND == TC_BF16X3) {
+            if constexpr (is_split<KIND>()) {
               mma<KIND>(dacc, ah0 + off, bl0 + off, idesc, 1u);
               mma<KIND>(dacc, al0 + off, bh0 + off, idesc, 1u);
             }
@@ -397,9 +402,18 @@ __global__ void __launch_bounds__(TS_THREADS, 1) tc_contract_kernel(
             }
             const size_t off = (size_t)(row >> 3) * SBO + (size_t)gq * LBO + (size_t)(row & 7) * 16;
             unsigned char* t0 = isA ? tileA(o, 0) : tileB(o, 0);
-            if constexpr (KIND == TC_TF32) {
-              *reinterpret_cast<uint4*>(t0 + off) =
-                  make_uint4(f32_to_tf32(v[0]), f32_to_tf32(v[1]), f32_to_tf32(v[2]), f32_to_tf32(v[3]));
+            if constexpr (is_tf32<KIND>()) {
+              uint32_t hi[4];
+#pragma unroll
+              for (int j = 0; j < 4; ++j) hi[j] = f32_to_tf32(v[j]);
+              *reinterpret_cast<uint4*>(t0 + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+              if constexpr (KIND == TC_TF32X3) {
+                uint32_t lo[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) lo[j] = f32_to_tf32(v[j] - __uint_as_float(hi[j]));
+                unsigned char* t1 = isA ? tileA(o, 1) : tileB(o, 1);
+                *reinterpret_cast<uint4*>(t1 + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+              }
             } else {
               uint32_t hi[4], lo[4];
 #pragma unroll
@@ -513,40 +527,55 @@ struct TcPlan {
   std::vector<TcItem> items;
   std::vector<Piece> pieces;
   long long part_elems = 0;
-  SmemLayout lay[3];
-  size_t smem[3] = {0, 0, 0};
-  DevBuf d_pairs, d_items, d_pieces, partials, flag;
+  SmemLayout lay[TC_NKIND];
+  size_t smem[TC_NKIND] = {0, 0, 0, 0};
+  DevBuf d_pairs, d_items, d_pieces, partials;
   bool ok = false;
   std::string why;
 };
 
-void ofm_tc_free(ofm_ctx* c) {
-  if (!c->tc) return;
-  DevBuf* bufs[] = {&c->tc->d_pairs, &c->tc->d_items, &c->tc->d_pieces, &c->tc->partials, &c->tc->flag};
+void ofm_tc_plan_free(TcPlan* t) {
+  if (!t) return;
+  DevBuf* bufs[] = {&t->d_pairs, &t->d_items, &t->d_pieces, &t->partials};
   for (DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
-  delete c->tc;
+  delete t;
+}
+
+void ofm_tc_free(ofm_ctx* c) {
+  ofm_tc_plan_free(c->tc);
   c->tc = nullptr;
 }
 
-// Plan of the tensor-core contraction after a build: one item per row chunk
-// of a piece, chunks sized for about four items per SM.
-ofm_status ofm_plan_extra(ofm_ctx* c) {
-  if (!c->tc) c->tc = new TcPlan();
-  TcPlan* t = c->tc;
+bool ofm_tc_plan_ok(const TcPlan* t, int kind) {
+  return t && t->ok && kind >= 0 && kind < TC_NKIND && t->lay[kind].nraw >= 2;
+}
+
+template <int KIND, int KTT>
+static void set_smem_attr() {
+  cudaFuncSetAttribute(tc_contract_kernel<KIND, KTT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       216 * 1024);
+}
+
+// Tensor-core plan for the pairs over the fragment table fr (FP32 storage,
+// row strides fr[].ld): one item per row chunk of a piece, chunks sized for
+// about four items per SM; blk_off[p] is pair p's offset in the FP64 block
+// arena.  The plan is marked not usable (with the reason) when a fragment
+// has more than 128 states or the staging does not fit shared memory.
+ofm_status ofm_tc_plan_build(ofm_ctx* c, TcPlan** tp, const std::vector<DevFrag>& fr,
+                             const std::vector<HostPair>& prs, const std::vector<long long>& blk_off,
+                             long long kh) {
+  if (!*tp) *tp = new TcPlan();
+  TcPlan* t = *tp;
   t->pairs.clear();
   t->items.clear();
   t->pieces.clear();
   t->part_elems = 0;
   t->ok = false;
-  if (c->storage != OFM_STORE_FP32) {
-    t->why = "tensor-core contraction needs FP32 storage";
-    return OFM_OK;
-  }
   int ldA = 4, ldB = 4, Rb = 16;
-  for (const HostPair& hp : c->pairs) {
-    const DevFrag& A = c->frags[hp.a];
-    const DevFrag& B = c->frags[hp.b];
+  for (const HostPair& hp : prs) {
+    const DevFrag& A = fr[hp.a];
+    const DevFrag& B = fr[hp.b];
     if (A.n > 128 || 2 * B.n > 256) {
       t->why = "tensor-core contraction supports at most 128 states per fragment";
       return OFM_OK;
@@ -555,17 +584,17 @@ ofm_status ofm_plan_extra(ofm_ctx* c) {
     ldB = std::max(ldB, B.ld);
     Rb = std::max(Rb, (2 * B.n + 15) / 16 * 16);
   }
-  const long long target = std::max<long long>(1024, c->kh / (4 * 152));
-  for (size_t p = 0; p < c->pairs.size(); ++p) {
-    const HostPair& hp = c->pairs[p];
-    const DevFrag& B = c->frags[hp.b];
-    TcPair tp;
-    tp.a = hp.a;
-    tp.b = hp.b;
-    tp.N = 2 * B.n;
-    tp.Npad = (tp.N + 15) / 16 * 16;
-    tp.blk_off = c->simt_pairs[p].blk_off;
-    tp.item0 = (int)t->items.size();
+  const long long target = std::max<long long>(1024, kh / (4 * 152));
+  for (size_t p = 0; p < prs.size(); ++p) {
+    const HostPair& hp = prs[p];
+    const DevFrag& B = fr[hp.b];
+    TcPair tq;
+    tq.a = hp.a;
+    tq.b = hp.b;
+    tq.N = 2 * B.n;
+    tq.Npad = (tq.N + 15) / 16 * 16;
+    tq.blk_off = blk_off[p];
+    tq.item0 = (int)t->items.size();
     for (const Piece& pc : hp.pieces) {
       const int pid = (int)t->pieces.size();
       t->pieces.push_back(pc);
@@ -578,20 +607,20 @@ ofm_status ofm_plan_extra(ofm_ctx* c) {
         it.r0 = r0;
         it.r1 = std::min(rows, r0 + per);
         it.part_off = t->part_elems;
-        t->part_elems += (long long)c->frags[hp.a].n * tp.N;
+        t->part_elems += (long long)fr[hp.a].n * tq.N;
         t->items.push_back(it);
       }
     }
-    tp.nitem = (int)t->items.size() - tp.item0;
-    t->pairs.push_back(tp);
+    tq.nitem = (int)t->items.size() - tq.item0;
+    t->pairs.push_back(tq);
   }
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < TC_NKIND; ++k) {
     SmemLayout& L = t->lay[k];
     L.ldA = ldA;
     L.ldB = ldB;
     L.Rb = Rb;
-    const int esz = (k == TC_TF32) ? 4 : 2;
-    L.ntiles = (k == TC_BF16X3) ? 2 : 1;
+    const int esz = (k == TC_TF32 || k == TC_TF32X3) ? 4 : 2;
+    L.ntiles = (k == TC_BF16X3 || k == TC_TF32X3) ? 2 : 1;
     L.nitems = (int)t->items.size();
     // the longest K step, then the largest raw stages (fewest per-stage
     // costs), then the deepest operand ring, that leave two raw stages
@@ -611,90 +640,114 @@ ofm_status ofm_plan_extra(ofm_ctx* c) {
       }
       if (L.nraw >= 2) break;
     }
-    if (L.nraw < 2) {
-      t->why = "tensor-core staging does not fit shared memory for these state counts";
-      return OFM_OK;
-    }
-    t->smem[k] = (size_t)L.nraw * L.raw_stage + (size_t)L.nop * L.ntiles * (L.tileA + L.tileB);
+    // a kind whose staging does not fit stays unusable (nraw < 2); the others run
+    t->smem[k] = L.nraw >= 2 ? (size_t)L.nraw * L.raw_stage + (size_t)L.nop * L.ntiles * (L.tileA + L.tileB) : 0;
   }
   OFM_TRY(ofm_ensure(c, t->d_pairs, sizeof(TcPair) * std::max<size_t>(1, t->pairs.size()), "tc pairs"));
   OFM_TRY(ofm_ensure(c, t->d_items, sizeof(TcItem) * std::max<size_t>(1, t->items.size()), "tc items"));
   OFM_TRY(ofm_ensure(c, t->d_pieces, sizeof(Piece) * std::max<size_t>(1, t->pieces.size()), "tc pieces"));
   OFM_TRY(ofm_ensure(c, t->partials, sizeof(float) * std::max<long long>(1, t->part_elems), "tc partials"));
-  OFM_TRY(ofm_ensure(c, t->flag, sizeof(int), "tc flag"));
   OFM_CUDA(c, cudaMemcpyAsync(t->d_pairs.p, t->pairs.data(), sizeof(TcPair) * t->pairs.size(), cudaMemcpyHostToDevice, c->stream));
   OFM_CUDA(c, cudaMemcpyAsync(t->d_items.p, t->items.data(), sizeof(TcItem) * t->items.size(), cudaMemcpyHostToDevice, c->stream));
   OFM_CUDA(c, cudaMemcpyAsync(t->d_pieces.p, t->pieces.data(), sizeof(Piece) * t->pieces.size(), cudaMemcpyHostToDevice, c->stream));
-  OFM_CUDA(c, cudaMemsetAsync(t->flag.p, 0, sizeof(int), c->stream));
-  OFM_CUDA(c, cudaFuncSetAttribute(tc_contract_kernel<TC_TF32, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 216 * 1024));
-  OFM_CUDA(c, cudaFuncSetAttribute(tc_contract_kernel<TC_BF16, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 216 * 1024));
-  OFM_CUDA(c, cudaFuncSetAttribute(tc_contract_kernel<TC_BF16X3, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 216 * 1024));
-  OFM_CUDA(c, cudaFuncSetAttribute(tc_contract_kernel<TC_TF32, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 216 * 1024));
-  OFM_CUDA(c, cudaFuncSetAttribute(tc_contract_kernel<TC_BF16, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 216 * 1024));
-  OFM_CUDA(c, cudaFuncSetAttribute(tc_contract_kernel<TC_BF16X3, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 216 * 1024));
+  static bool attr = false;   // the kernels' shared-memory limit, once per process
+  if (!attr) {
+    set_smem_attr<TC_TF32, 32>();
+    set_smem_attr<TC_BF16, 32>();
+    set_smem_attr<TC_BF16X3, 32>();
+    set_smem_attr<TC_TF32X3, 32>();
+    set_smem_attr<TC_TF32, 64>();
+    set_smem_attr<TC_BF16, 64>();
+    set_smem_attr<TC_BF16X3, 64>();
+    set_smem_attr<TC_TF32X3, 64>();
+    OFM_CUDA(c, cudaGetLastError());
+    attr = true;
+  }
   t->ok = true;
   return OFM_OK;
 }
 
-ofm_status ofm_contract_tc(ofm_ctx* c, ofm_precision prec) {
-  TcPlan* t = c->tc;
+// Plan of the pair contraction after a build.
+ofm_status ofm_plan_extra(ofm_ctx* c) {
+  if (c->storage != OFM_STORE_FP32) {
+    if (!c->tc) c->tc = new TcPlan();
+    c->tc->ok = false;
+    c->tc->why = "tensor-core contraction needs FP32 storage";
+    return OFM_OK;
+  }
+  std::vector<long long> off(c->pairs.size());
+  for (size_t p = 0; p < c->pairs.size(); ++p) off[p] = c->simt_pairs[p].blk_off;
+  return ofm_tc_plan_build(c, &c->tc, c->frags, c->pairs, off, c->kh);
+}
+
+template <int KIND>
+static void launch_kind(const TcPlan* t, int kt, int grid, size_t sm, cudaStream_t s,
+                        const DevFrag* fr, const float* st, const float* hp, int* fl) {
+  const SmemLayout& L = t->lay[KIND];
+  const TcPair* pr = (const TcPair*)t->d_pairs.p;
+  const Piece* pc = (const Piece*)t->d_pieces.p;
+  const TcItem* itm = (const TcItem*)t->d_items.p;
+  float* part = (float*)t->partials.p;
+  if (kt == 64)
+    tc_contract_kernel<KIND, 64><<<grid, TS_THREADS, sm, s>>>(fr, pr, pc, itm, st, hp, part, fl, L);
+  else
+    tc_contract_kernel<KIND, 32><<<grid, TS_THREADS, sm, s>>>(fr, pr, pc, itm, st, hp, part, fl, L);
+}
+
+// Runs a plan: contraction into FP32 partials, then the fixed-order sum into
+// the FP64 block arena.  kind: TC_TF32 .. TC_TF32X3.
+ofm_status ofm_tc_run(ofm_ctx* c, TcPlan* t, int kind, const DevFrag* d_frags, const void* states,
+                      const void* hphi, double* blocks, int kclass_contract, int kclass_finalize,
+                      double bytes, double flops) {
   if (!t || !t->ok) return ofm_fail(c, OFM_ERR_INVALID, t ? t->why : "no tensor-core plan");
-  const int kind = prec == OFM_PREC_TF32 ? TC_TF32 : prec == OFM_PREC_BF16 ? TC_BF16 : TC_BF16X3;
+  if (!ofm_tc_plan_ok(t, kind))
+    return ofm_fail(c, OFM_ERR_INVALID, "tensor-core staging does not fit shared memory for these state counts");
   const int nit = (int)t->items.size();
+  int* fl = (int*)c->flag.p + OFM_FLAG_TC;
   {
-    KTimer kt(c, KC_CONTRACT, 1, c->contract_bytes, (double)c->flops);
+    KTimer kt(c, kclass_contract, 1, bytes, flops);
     if (nit > 0) {
       const int grid = std::min(nit, 152);   // one persistent CTA per SM
-      const SmemLayout& L = t->lay[kind];
-      const DevFrag* fr = (const DevFrag*)c->d_frags.p;
-      const TcPair* pr = (const TcPair*)t->d_pairs.p;
-      const Piece* pc = (const Piece*)t->d_pieces.p;
-      const TcItem* itm = (const TcItem*)t->d_items.p;
-      const float* st = (const float*)c->states.p;
-      const float* hp = (const float*)c->hphi.p;
-      float* part = (float*)t->partials.p;
-      int* fl = (int*)t->flag.p;
+      const int ktl = t->lay[kind].kt;
       const size_t sm = t->smem[kind];
-      if (L.kt == 64) {
-        if (kind == TC_TF32)
-          tc_contract_kernel<TC_TF32, 64><<<grid, TS_THREADS, sm, c->stream>>>(fr, pr, pc, itm, st, hp, part, fl, L);
-        else if (kind == TC_BF16)
-          tc_contract_kernel<TC_BF16, 64><<<grid, TS_THREADS, sm, c->stream>>>(fr, pr, pc, itm, st, hp, part, fl, L);
-        else
-          tc_contract_kernel<TC_BF16X3, 64><<<grid, TS_THREADS, sm, c->stream>>>(fr, pr, pc, itm, st, hp, part, fl, L);
-      } else {
-        if (kind == TC_TF32)
-          tc_contract_kernel<TC_TF32, 32><<<grid, TS_THREADS, sm, c->stream>>>(fr, pr, pc, itm, st, hp, part, fl, L);
-        else if (kind == TC_BF16)
-          tc_contract_kernel<TC_BF16, 32><<<grid, TS_THREADS, sm, c->stream>>>(fr, pr, pc, itm, st, hp, part, fl, L);
-        else
-          tc_contract_kernel<TC_BF16X3, 32><<<grid, TS_THREADS, sm, c->stream>>>(fr, pr, pc, itm, st, hp, part, fl, L);
-      }
+      const float* st = (const float*)states;
+      const float* hp = (const float*)hphi;
+      if (kind == TC_TF32) launch_kind<TC_TF32>(t, ktl, grid, sm, c->stream, d_frags, st, hp, fl);
+      else if (kind == TC_BF16) launch_kind<TC_BF16>(t, ktl, grid, sm, c->stream, d_frags, st, hp, fl);
+      else if (kind == TC_BF16X3) launch_kind<TC_BF16X3>(t, ktl, grid, sm, c->stream, d_frags, st, hp, fl);
+      else launch_kind<TC_TF32X3>(t, ktl, grid, sm, c->stream, d_frags, st, hp, fl);
     }
     OFM_CUDA(c, cudaGetLastError());
   }
   {
-    KTimer kt(c, KC_FINALIZE, 1, (double)t->part_elems * 4 + 8.0 * c->blk_elems);
+    KTimer kt(c, kclass_finalize, 1, (double)t->part_elems * 4);
     if (!t->pairs.empty())
       tc_finalize_kernel<<<(int)t->pairs.size(), 256, 0, c->stream>>>(
-          (const DevFrag*)c->d_frags.p, (const TcPair*)t->d_pairs.p, (const TcItem*)t->d_items.p,
-          (const float*)t->partials.p, (double*)c->blocks.p);
+          d_frags, (const TcPair*)t->d_pairs.p, (const TcItem*)t->d_items.p,
+          (const float*)t->partials.p, blocks);
     OFM_CUDA(c, cudaGetLastError());
   }
   c->tc_check = true;
   return OFM_OK;
 }
 
+ofm_status ofm_contract_tc(ofm_ctx* c, ofm_precision prec) {
+  const int kind = prec == OFM_PREC_TF32 ? TC_TF32 : prec == OFM_PREC_BF16 ? TC_BF16 : TC_BF16X3;
+  return ofm_tc_run(c, c->tc, kind, (const DevFrag*)c->d_frags.p, c->states.p, c->hphi.p,
+                    (double*)c->blocks.p, KC_CONTRACT, KC_FINALIZE, c->contract_bytes, (double)c->flops);
+}
+
 // Reports a bounded-wait timeout of an earlier tensor-core or staged-stencil
 // launch (each sets its flag word; the flags are read once and cleared).
 ofm_status ofm_wait_status(ofm_ctx* c) {
-  if (c->tc_check && c->tc && c->tc->flag.p) {
+  if (c->tc_check) {
     int h = 0;
-    OFM_CUDA(c, cudaMemcpyAsync(&h, c->tc->flag.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    int* f = (int*)c->flag.p + OFM_FLAG_TC;
+    OFM_CUDA(c, cudaMemcpyAsync(&h, f, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     OFM_CUDA(c, cudaStreamSynchronize(c->stream));
     c->tc_check = false;
     if (h) {
-      cudaMemsetAsync(c->tc->flag.p, 0, sizeof(int), c->stream);
+      cudaMemsetAsync(f, 0, sizeof(int), c->stream);
       return ofm_fail(c, OFM_ERR_TIMEOUT, "tensor-core contraction: an mbarrier wait exceeded its bound");
     }
   }
