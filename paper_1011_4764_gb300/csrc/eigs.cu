@@ -127,7 +127,12 @@ __global__ void init_random_kernel(const DevFrag* fr, const int* cta_start, int 
       unsigned long long key = ((unsigned long long)f << 44) ^ ((unsigned long long)col << 32) ^
                                (unsigned long long)p;
       unsigned long long r = splitmix64(key + s0);
-      v = (T)((double)(r >> 11) * (2.0 / 9007199254740992.0) - 1.0);
+      // uniform in [-1, 1): 53 random bits for FP64 storage, 24 for FP32
+      // (FP32 arithmetic there: the FP64 units of this part are few)
+      if (sizeof(T) == 8)
+        v = (T)((double)(r >> 11) * (2.0 / 9007199254740992.0) - 1.0);
+      else
+        v = (T)((float)(r >> 40) * (2.0f / 16777216.0f) - 1.0f);
     }
     buf[F.off + p * F.ld + col] = v;
   }
@@ -172,12 +177,15 @@ __device__ void cta_jacobi(T* A, T* V, int n, int lda, int* perm, T* cs, double*
   const int ne = n + (n & 1);
   const int half = ne / 2;
   const double eps = Eps<T>::v;
+  const T eps_t = (T)Eps<T>::v;
   (void)perm;
+  // norms, reductions and thresholds in the working precision T: the FP64
+  // units of this part are few, and a stopping test needs no more
   for (int sweep = 0; sweep < 40; ++sweep) {
-    double off = 0.0, tot = 0.0;
+    T off = 0, tot = 0;
     for (int e = tid; e < n * n; e += nt) {
       const int i = e / n, j = e - (e / n) * n;
-      const double a = (double)A[i * lda + j];
+      const T a = A[i * lda + j];
       tot += a * a;
       if (i != j) off += a * a;
     }
@@ -186,8 +194,8 @@ __device__ void cta_jacobi(T* A, T* V, int n, int lda, int* perm, T* cs, double*
       tot += __shfl_down_sync(0xffffffffu, tot, o);
     }
     if ((tid & 31) == 0) {
-      red[2 * (tid >> 5)] = off;
-      red[2 * (tid >> 5) + 1] = tot;
+      red[2 * (tid >> 5)] = (double)off;
+      red[2 * (tid >> 5) + 1] = (double)tot;
     }
     __syncthreads();
     if (tid == 0) {
@@ -203,6 +211,7 @@ __device__ void cta_jacobi(T* A, T* V, int n, int lda, int* perm, T* cs, double*
     }
     __syncthreads();
     const bool done = red[64] != 0.0;
+    const T floor_t = (T)red[66];
     __syncthreads();
     if (done) break;
     for (int r = 0; r < ne - 1; ++r) {
@@ -213,7 +222,7 @@ __device__ void cta_jacobi(T* A, T* V, int n, int lda, int* perm, T* cs, double*
         if (p < n && q < n) {
           const T apq = A[p * lda + q];
           const T app = A[p * lda + p], aqq = A[q * lda + q];
-          if (fabs((double)apq) > fmax(2.0 * eps * sqrt(fabs((double)app * (double)aqq)), red[66])) {
+          if (fabs(apq) > fmax(T(2) * eps_t * sqrt(fabs(app * aqq)), floor_t)) {
             red[65] = 1.0;
             const T th = (aqq - app) / (T(2) * apq);
             const T t = (th >= T(0) ? T(1) : T(-1)) / (fabs(th) + sqrt(th * th + T(1)));
@@ -501,9 +510,11 @@ __global__ void __launch_bounds__(256) rotate_kernel(const DevFrag* efr, const T
   const int G = blockDim.x / m;
   const int j = threadIdx.x % m, g = threadIdx.x / m;
   const bool active = g < G;
-  const double th = active ? theta[toff[f] + j] : 0.0;
+  const T th = active ? (T)theta[toff[f] + j] : T(0);
   const unsigned long long s0 = splitmix64(salt);
-  double racc = 0.0;
+  // residual partial sums in the working precision (FP64 is scarce on this
+  // part); they are combined in FP64 below
+  T racc = 0;
   for (int t0 = blockIdx.x * TP; t0 < P; t0 += gridDim.x * TP) {
     __syncthreads();
     if (threadIdx.x < TP) {
@@ -545,13 +556,13 @@ __global__ void __launch_bounds__(256) rotate_kernel(const DevFrag* efr, const T
         const long long a = F.off + (long long)pd * F.ld + j;
         Xo[a] = x;
         HXo[a] = hx;
-        const double d = (double)hx - th * (double)x;
+        const T d = hx - th * x;
         racc += d * d;
       }
     }
   }
   __syncthreads();
-  red[threadIdx.x] = racc;
+  red[threadIdx.x] = (double)racc;
   __syncthreads();
   if (threadIdx.x < m) {
     double s = 0.0;
@@ -577,9 +588,10 @@ __global__ void residual_reduce_kernel(const DevFrag* efr, const double* partial
 template <typename T>
 __global__ void __launch_bounds__(1024) export_states_kernel(const DevFrag* efr, const DevFrag* fr,
                                                              const T* X, T* states) {
-  __shared__ double bv[32][32];
+  // magnitudes compared in the storage type: the same order as in FP64
+  __shared__ T bv[32][32];
   __shared__ int bi[32][32];
-  __shared__ double sgn[32];
+  __shared__ T sgn[32];
   const int f = blockIdx.x;
   const DevFrag E = efr[f];
   const DevFrag F = fr[f];
@@ -588,13 +600,13 @@ __global__ void __launch_bounds__(1024) export_states_kernel(const DevFrag* efr,
   const int col = blockIdx.y * 32 + lane;
   const int ex = F.ext[0], ey = F.ext[1];
   const int P = F.ext[0] * F.ext[1] * F.ext[2];
-  double best = -1.0;
+  T best = T(-1);
   int besti = 0;
   if (col < F.n) {
     for (int t = warp; t < P; t += nw) {
       const int x = t % ex, y = (t / ex) % ey, z = t / (ex * ey);
       const int pd = ((z + E.lo[2]) * E.dext[1] + (y + E.lo[1])) * E.dext[0] + x + E.lo[0];
-      const double a = fabs((double)X[E.off + (long long)pd * E.ld + col]);
+      const T a = fabs(X[E.off + (long long)pd * E.ld + col]);
       if (a > best) {  // strictly greater: the lowest index wins within a warp's stream
         best = a;
         besti = t;
@@ -605,7 +617,7 @@ __global__ void __launch_bounds__(1024) export_states_kernel(const DevFrag* efr,
   bi[warp][lane] = besti;
   __syncthreads();
   if (warp == 0) {
-    double b = bv[0][lane];
+    T b = bv[0][lane];
     int ib = bi[0][lane];
     for (int w = 1; w < nw; ++w) {
       if (bv[w][lane] > b || (bv[w][lane] == b && bi[w][lane] < ib)) {
@@ -613,17 +625,17 @@ __global__ void __launch_bounds__(1024) export_states_kernel(const DevFrag* efr,
         ib = bi[w][lane];
       }
     }
-    double sg = 1.0;
+    T sg = T(1);
     if (col < F.n && ib >= 0 && ib < P) {
       const int x = ib % ex, y = (ib / ex) % ey, z = ib / (ex * ey);
       const int pd = ((z + E.lo[2]) * E.dext[1] + (y + E.lo[1])) * E.dext[0] + x + E.lo[0];
-      sg = (double)X[E.off + (long long)pd * E.ld + col] < 0.0 ? -1.0 : 1.0;
+      sg = X[E.off + (long long)pd * E.ld + col] < T(0) ? T(-1) : T(1);
     }
     sgn[lane] = sg;
   }
   __syncthreads();
   if (col >= F.n) return;
-  const T s = (T)sgn[lane];
+  const T s = sgn[lane];
   for (int t = warp; t < P; t += nw) {
     const int x = t % ex, y = (t / ex) % ey, z = t / (ex * ey);
     const int pe = ((z + E.lo[2]) * E.dext[1] + (y + E.lo[1])) * E.dext[0] + x + E.lo[0];

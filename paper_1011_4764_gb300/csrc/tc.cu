@@ -508,7 +508,8 @@ __global__ void tc_finalize_kernel(const DevFrag* __restrict__ fr, const TcPair*
     for (int k = 0; k < pr.nitem; ++k) s += (double)partials[items[pr.item0 + k].part_off + (long long)i * N + c];
     return s;
   };
-  for (int e = threadIdx.x; e < na * nb; e += blockDim.x) {
+  // blockIdx.y: a chunk of outputs (the FP64 sums spread over many SMs)
+  for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < na * nb; e += gridDim.y * blockDim.x) {
     const int i = e / nb, m = e % nb;
     double s = sum(i, m), h = sum(i, nb + m);
     if (pr.a == pr.b) {
@@ -721,8 +722,12 @@ ofm_status ofm_tc_run(ofm_ctx* c, TcPlan* t, int kind, const DevFrag* d_frags, c
   }
   {
     KTimer kt(c, kclass_finalize, 1, (double)t->part_elems * 4);
+    // enough output chunks for the largest block (n_a <= 128, n_b = N / 2)
+    int nmax = 1;
+    for (const TcPair& q : t->pairs) nmax = std::max(nmax, q.N / 2);
+    const int chunks = std::max(1, (128 * nmax + 255) / 256);
     if (!t->pairs.empty())
-      tc_finalize_kernel<<<(int)t->pairs.size(), 256, 0, c->stream>>>(
+      tc_finalize_kernel<<<dim3((int)t->pairs.size(), chunks), 256, 0, c->stream>>>(
           d_frags, (const TcPair*)t->d_pairs.p, (const TcItem*)t->d_items.p,
           (const float*)t->partials.p, blocks);
     OFM_CUDA(c, cudaGetLastError());
