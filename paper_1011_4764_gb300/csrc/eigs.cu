@@ -178,7 +178,6 @@ __device__ void cta_jacobi(T* A, T* V, int n, int lda, int* perm, T* cs, double*
   const int half = ne / 2;
   const double eps = Eps<T>::v;
   const T eps_t = (T)Eps<T>::v;
-  (void)perm;
   // norms, reductions and thresholds in the working precision T: the FP64
   // units of this part are few, and a stopping test needs no more
   for (int sweep = 0; sweep < 40; ++sweep) {
@@ -214,10 +213,14 @@ __device__ void cta_jacobi(T* A, T* V, int n, int lda, int* perm, T* cs, double*
     const T floor_t = (T)red[66];
     __syncthreads();
     if (done) break;
+    const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
     for (int r = 0; r < ne - 1; ++r) {
+      // angles of the round's disjoint pairs; the pairs go to perm[] so the
+      // updates below need no index arithmetic
       for (int k = tid; k < half; k += nt) {
         int p, q;
         rr_pair(r, k, ne, p, q);
+        perm[k] = p | (q << 16);
         T c = 1, s = 0;
         if (p < n && q < n) {
           const T apq = A[p * lda + q];
@@ -234,33 +237,31 @@ __device__ void cta_jacobi(T* A, T* V, int n, int lda, int* perm, T* cs, double*
         cs[2 * k + 1] = s;
       }
       __syncthreads();
-      // rows p, q
-      for (int w = tid; w < half * n; w += nt) {
-        const int k = w / n, j = w - (w / n) * n;
-        int p, q;
-        rr_pair(r, k, ne, p, q);
-        if (p >= n || q >= n) continue;
+      // rows p, q: one warp per pair, lanes along the row
+      for (int k = warp; k < half; k += nwarps) {
+        const int pq = perm[k], p = pq & 0xffff, q = pq >> 16;
         const T c = cs[2 * k], s = cs[2 * k + 1];
-        if (s == T(0)) continue;
-        const T ap = A[p * lda + j], aq = A[q * lda + j];
-        A[p * lda + j] = c * ap - s * aq;
-        A[q * lda + j] = s * ap + c * aq;
+        if (p >= n || q >= n || s == T(0)) continue;   // uniform over the warp
+        for (int j = lane; j < n; j += 32) {
+          const T ap = A[p * lda + j], aq = A[q * lda + j];
+          A[p * lda + j] = c * ap - s * aq;
+          A[q * lda + j] = s * ap + c * aq;
+        }
       }
       __syncthreads();
-      // columns p, q of A and V
-      for (int w = tid; w < half * n; w += nt) {
-        const int k = w / n, i = w - (w / n) * n;
-        int p, q;
-        rr_pair(r, k, ne, p, q);
-        if (p >= n || q >= n) continue;
+      // columns p, q of A and V: one warp per pair, lanes down the column
+      for (int k = warp; k < half; k += nwarps) {
+        const int pq = perm[k], p = pq & 0xffff, q = pq >> 16;
         const T c = cs[2 * k], s = cs[2 * k + 1];
-        if (s == T(0)) continue;
-        const T ap = A[i * lda + p], aq = A[i * lda + q];
-        A[i * lda + p] = c * ap - s * aq;
-        A[i * lda + q] = s * ap + c * aq;
-        const T vp = V[i * lda + p], vq = V[i * lda + q];
-        V[i * lda + p] = c * vp - s * vq;
-        V[i * lda + q] = s * vp + c * vq;
+        if (p >= n || q >= n || s == T(0)) continue;
+        for (int i = lane; i < n; i += 32) {
+          const T ap = A[i * lda + p], aq = A[i * lda + q];
+          A[i * lda + p] = c * ap - s * aq;
+          A[i * lda + q] = s * ap + c * aq;
+          const T vp = V[i * lda + p], vq = V[i * lda + q];
+          V[i * lda + p] = c * vp - s * vq;
+          V[i * lda + q] = s * vp + c * vq;
+        }
       }
       __syncthreads();
     }
@@ -338,10 +339,10 @@ __global__ void __launch_bounds__(256) rayleigh_ritz_kernel(const DevFrag* efr, 
       __syncthreads();
       for (int i = j + 1 + tid; i < m; i += nt) W[i * ld + j] /= W[j * ld + j];
       __syncthreads();
-      const int rest = m - j - 1;
-      for (int e = tid; e < rest * rest; e += nt) {
-        const int i = j + 1 + e / rest, k = j + 1 + e % rest;
-        if (k <= i) W[i * ld + k] -= W[i * ld + j] * W[k * ld + j];
+      // trailing update, one warp per row, lanes along the row (no index division)
+      for (int i = j + 1 + (tid >> 5); i < m; i += nt >> 5) {
+        const T lij = W[i * ld + j];
+        for (int k = j + 1 + (tid & 31); k <= i; k += 32) W[i * ld + k] -= lij * W[k * ld + j];
       }
       __syncthreads();
     }
