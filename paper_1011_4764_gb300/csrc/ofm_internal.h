@@ -185,7 +185,7 @@ struct ofm_ctx {
   // device buffers
   ofm::DevBuf V, states, hphi, d_frags, d_pairs, d_pieces, d_items, partials,
       blocks, dense_H, dense_S, staging, flag;
-  ofm::DevBuf w_A, w_L, w_d, w_e, w_tau, w_tmp, w_eval, w_bar;   // window-solver workspaces
+  ofm::DevBuf w_A, w_L, w_d, w_e, w_tau, w_tmp, w_eval, w_bar, w_Q;   // window-solver workspaces
   int dense_n = 0;
   int window_fail_col = -1;
   std::vector<char> frag_set;       // per fragment: states imported or computed

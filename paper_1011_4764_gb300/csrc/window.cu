@@ -2,7 +2,8 @@
 //     sum_mn (H - E S) C = 0,
 // for the eigenvalues inside an energy window, on the device:
 //   1. Cholesky S = L L^T (blocked, right-looking, 32-wide panels);
-//   2. A = L^-1 H L^-T by two blocked forward substitutions;
+//   2. A = L^-1 H L^-T by two blocked forward substitutions with the
+//      block multipliers L_jj^-1 and L_ij L_jj^-1 formed once;
 //   3. Householder reduction of A to a symmetric tridiagonal T (d, e);
 //   4. Sturm-sequence counts and bisection on T, one thread per wanted
 //      eigenvalue index.
@@ -25,9 +26,10 @@ constexpr int NB = 32;
 // ---------------------------------------------------------------- Cholesky --
 
 // Factor the kb x kb diagonal block at (k0, k0) in place (lower triangle).
-// The pivot's square root and its reciprocal are formed once per column,
-// so the column is scaled by a multiplication (FP64 division and square
-// root are long instruction sequences on a part with few FP64 units).
+// The pivot's reciprocal square root is formed once per column (one call;
+// L_jj = piv / sqrt(piv)), so the column is scaled by a multiplication (FP64
+// division and square root are long instruction sequences on a part with
+// few FP64 units).
 __global__ void potrf_diag_kernel(double* W, int n, int k0, int kb, int* fail_col) {
   __shared__ double a[NB][NB + 1];
   __shared__ double rinv;
@@ -41,9 +43,9 @@ __global__ void potrf_diag_kernel(double* W, int n, int k0, int kb, int* fail_co
         atomicCAS(fail_col, -1, k0 + j);
         piv = 1.0;  // keep going with finite numbers; the call reports failure
       }
-      const double r = sqrt(piv);
-      a[j][j] = r;
-      rinv = 1.0 / r;
+      const double ri = rsqrt(piv);   // one call instead of a square root and a division
+      a[j][j] = piv * ri;
+      rinv = ri;
     }
     __syncthreads();
     if (tx == 0 && ty > j && ty < kb) a[ty][j] *= rinv;
@@ -107,69 +109,98 @@ __global__ void syrk_update_kernel(double* W, int n, int k0, int kb) {
 }
 
 // ------------------------------------------------------ triangular solves --
+//
+// L X = B is solved by blocks of NB rows with precomputed multipliers
+// Q_jj = L_jj^-1 (diagonal blocks) and Q_ij = L_ij L_jj^-1 (i > j): step j
+// writes X_j = Q_jj B_j and updates B_i -= Q_ij B_j (= L_ij X_j) for i > j,
+// one independent NB x NB x NB product per CTA.  The serial substitutions are
+// confined to the NB x NB diagonal inverses, computed once per factorisation
+// for all blocks in one launch.
 
-// X_k = L_kk^-1 B_k for the kb rows of block k (one thread per column).
-__global__ void trsm_diag_rows_kernel(const double* L, double* B, int n, int k0, int kb) {
+// Q_jj = L_jj^-1: one CTA of NB threads per diagonal block, thread c solves
+// L_jj x = e_c by forward substitution (reciprocal pivots); the strictly
+// upper part of the block is written as zero.
+__global__ void inv_diag_kernel(const double* L, double* Q, int n) {
   __shared__ double l[NB][NB + 1];
   __shared__ double dinv[NB];
-  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-    int r = e / NB, cc = e % NB;
-    l[r][cc] = (r < kb && cc <= r) ? L[(long long)(k0 + r) * n + k0 + cc] : 0.0;
-  }
+  const int k0 = blockIdx.x * NB, kb = min(NB, n - k0);
+  const int c = threadIdx.x;
+  for (int r = 0; r < NB; ++r) l[r][c] = (r < kb && c <= r) ? L[(long long)(k0 + r) * n + k0 + c] : 0.0;
   __syncthreads();
-  for (int j = threadIdx.x; j < kb; j += blockDim.x) dinv[j] = 1.0 / l[j][j];
+  if (c < kb) dinv[c] = 1.0 / l[c][c];
   __syncthreads();
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= n) return;
+  if (c >= kb) return;
   double x[NB];
 #pragma unroll
-  for (int j = 0; j < NB; ++j) {
-    if (j < kb) {
-      double s = B[(long long)(k0 + j) * n + c];
-      for (int t = 0; t < j; ++t) s -= l[j][t] * x[t];
-      x[j] = s * dinv[j];
-      B[(long long)(k0 + j) * n + c] = x[j];
+  for (int r = 0; r < NB; ++r) {
+    double v = 0.0;
+    if (r == c) {
+      v = dinv[c];
+    } else if (r > c && r < kb) {
+      double s = 0.0;
+      for (int k = c; k < r; ++k) s -= l[r][k] * x[k];
+      v = s * dinv[r];
     }
+    x[r] = v;
+  }
+#pragma unroll
+  for (int r = 0; r < NB; ++r)
+    if (r < kb) Q[(long long)(k0 + r) * n + k0 + c] = x[r];
+}
+
+// Q_ij = L_ij Q_jj for the blocks below the diagonal (grid: j, i).
+__global__ void panel_mul_kernel(const double* L, double* Q, int n) {
+  const int j = blockIdx.x, i = blockIdx.y;
+  if (i <= j) return;
+  __shared__ double a[NB][NB + 1], q[NB][NB + 1];
+  const int r0 = i * NB, k0 = j * NB;
+  const int rb = min(NB, n - r0), kb = min(NB, n - k0);
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int r = e / NB, cc = e % NB;
+    a[r][cc] = (r < rb && cc < kb) ? L[(long long)(r0 + r) * n + k0 + cc] : 0.0;
+    q[r][cc] = (r < kb && cc < kb) ? Q[(long long)(k0 + r) * n + k0 + cc] : 0.0;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int r = e / NB, cc = e % NB;
+    double s = 0.0;
+#pragma unroll 8
+    for (int k = 0; k < NB; ++k) s = fma(a[r][k], q[k][cc], s);
+    if (r < rb && cc < kb) Q[(long long)(r0 + r) * n + k0 + cc] = s;
   }
 }
 
-// B[i, :] -= L[i, k0:k0+kb] X_k for rows i >= k0+kb (64 x 64 output tiles).
-__global__ void gemm_update_rows_kernel(const double* L, double* B, int n, int k0, int kb) {
-  __shared__ double ls[64][NB + 1];
-  __shared__ double xs[NB][64 + 1];
-  const int r0 = k0 + kb + blockIdx.y * 64, c0 = blockIdx.x * 64;
-  const int tid = threadIdx.x;  // 256
-  for (int e = tid; e < 64 * NB; e += 256) {
-    int r = e / NB, t = e % NB;
-    ls[r][t] = (r0 + r < n && t < kb) ? L[(long long)(r0 + r) * n + k0 + t] : 0.0;
-  }
-  for (int e = tid; e < NB * 64; e += 256) {
-    int t = e / 64, cc = e % 64;
-    xs[t][cc] = (t < kb && c0 + cc < n) ? B[(long long)(k0 + t) * n + c0 + cc] : 0.0;
+// Step j: block row i = j + blockIdx.y, columns c0 = NB blockIdx.x ..
+//   i == j: X_j = Q_jj B_j;   i > j: B_i -= Q_ij B_j.
+__global__ void __launch_bounds__(256) trsm_step_kernel(const double* Q, double* B, double* X,
+                                                        int n, int j) {
+  __shared__ double q[NB][NB + 1], bj[NB][NB + 1];
+  const int i = j + blockIdx.y, c0 = blockIdx.x * NB;
+  const int r0 = i * NB, k0 = j * NB;
+  const int rb = min(NB, n - r0), kb = min(NB, n - k0), cb = min(NB, n - c0);
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int r = e / NB, cc = e % NB;
+    q[r][cc] = (r < rb && cc < kb) ? Q[(long long)(r0 + r) * n + k0 + cc] : 0.0;
+    bj[r][cc] = (r < kb && cc < cb) ? B[(long long)(k0 + r) * n + c0 + cc] : 0.0;
   }
   __syncthreads();
-  const int tx = tid % 16, ty = tid / 16;
-  double acc[4][4] = {};
-  for (int t = 0; t < NB; ++t) {
-    double a[4], b[4];
+  // four outputs per thread: rows ty, ty + 8, ty + 16, ty + 24 of column tx
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll 8
+  for (int k = 0; k < NB; ++k) {
+    const double b = bj[k][tx];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) a[i] = ls[ty * 4 + i][t];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) b[j] = xs[t][tx * 4 + j];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    for (int u = 0; u < 4; ++u) acc[u] = fma(q[ty + 8 * u][k], b, acc[u]);
   }
+  if (tx >= cb) return;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    int r = r0 + ty * 4 + i;
-    if (r >= n) continue;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      int cc = c0 + tx * 4 + j;
-      if (cc < n) B[(long long)r * n + cc] -= acc[i][j];
-    }
+  for (int u = 0; u < 4; ++u) {
+    const int r = ty + 8 * u;
+    if (r >= rb) continue;
+    const long long o = (long long)(r0 + r) * n + c0 + tx;
+    if (i == j) X[o] = acc[u];
+    else B[o] -= acc[u];
   }
 }
 
@@ -358,19 +389,11 @@ static ofm_status sync_ctx(ofm_ctx* c, const char* what) {
   return OFM_OK;
 }
 
-// Solve L X = B in place in B (n x n), L lower triangular in Lbuf.
-static void trsm_lower_left(const double* L, double* B, int n, cudaStream_t s) {
-  for (int k0 = 0; k0 < n; k0 += NB) {
-    const int kb = std::min(NB, n - k0);
-    // one warp per CTA: each thread runs a serial FP64 substitution, so the
-    // columns are spread over as many SMs as possible
-    trsm_diag_rows_kernel<<<(n + 31) / 32, 32, 0, s>>>(L, B, n, k0, kb);
-    const int rows = n - k0 - kb;
-    if (rows > 0) {
-      dim3 g((n + 63) / 64, (rows + 63) / 64);
-      gemm_update_rows_kernel<<<g, 256, 0, s>>>(L, B, n, k0, kb);
-    }
-  }
+// X = L^-1 B (n x n) with the multipliers Q of L; B is overwritten.
+static void trsm_lower_left(const double* Q, double* B, double* X, int n, cudaStream_t s) {
+  const int nblk = (n + NB - 1) / NB;
+  for (int j = 0; j < nblk; ++j)
+    trsm_step_kernel<<<dim3(nblk, nblk - j), 256, 0, s>>>(Q, B, X, n, j);
 }
 
 ofm_status ofm_window_factor(ofm_ctx* c) {
@@ -413,17 +436,22 @@ ofm_status ofm_window_factor(ofm_ctx* c) {
     snprintf(buf, sizeof buf, "S is not positive definite: Cholesky pivot %d is not positive", fail);
     return ofm_fail(c, OFM_ERR_NOT_POSDEF, buf);
   }
-  // 2. A = L^-1 H L^-T: X = L^-1 H, then A = L^-1 X^T
+  // 2. A = L^-1 H L^-T: multipliers Q of L, X = L^-1 H, then A = L^-1 X^T
   double* T = (double*)c->dense_H.p;  // kept intact: work on a copy
   OFM_CUDA(c, cudaMemcpyAsync(A, T, bytes, cudaMemcpyDeviceToDevice, s));
   {
-  KTimer kt(c, KC_REDUCE, 2 + 4 * ((n + NB - 1) / NB), 0.0, (double)n * n * n);  // algorithmic (dsygst) n^3 flops
-  trsm_lower_left(L, A, n, s);
+  const int nblk = (n + NB - 1) / NB;
+  KTimer kt(c, KC_REDUCE, 5 + 2LL * nblk, 0.0, (double)n * n * n);  // algorithmic (dsygst) n^3 flops
   OFM_TRY(ofm_ensure(c, c->w_eval, bytes, "window scratch"));
+  OFM_TRY(ofm_ensure(c, c->w_Q, bytes, "window multipliers"));
   double* X = (double*)c->w_eval.p;
+  double* Q = (double*)c->w_Q.p;
+  inv_diag_kernel<<<nblk, NB, 0, s>>>(L, Q, n);
+  panel_mul_kernel<<<dim3(nblk, nblk), 256, 0, s>>>(L, Q, n);
+  trsm_lower_left(Q, A, X, n, s);          // X = L^-1 H (A is consumed)
   dim3 tg((n + 31) / 32, (n + 31) / 32);
-  transpose_kernel<<<tg, dim3(32, 32), 0, s>>>(A, X, n);
-  trsm_lower_left(L, X, n, s);
+  transpose_kernel<<<tg, dim3(32, 32), 0, s>>>(X, A, n);
+  trsm_lower_left(Q, A, X, n, s);          // X = L^-1 (L^-1 H)^T
   symmetrize_kernel<<<(int)(((long long)n * n + 255) / 256), 256, 0, s>>>(X, n);
   OFM_CUDA(c, cudaMemcpyAsync(A, X, bytes, cudaMemcpyDeviceToDevice, s));
   }
