@@ -82,15 +82,17 @@ __device__ __forceinline__ double block_sum(double s, double* red) {
 // CTA because each FP64 instruction of a warp occupies a sub-partition's
 // FP64 pipe for many cycles: sixteen warps' shuffle trees cost more than
 // the additions they save.
-__device__ __forceinline__ double sum4(double s, double* red) {
+__device__ __forceinline__ double sum4(double s, double* red, double scale = 1.0) {
   if (threadIdx.x < 128) {
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
   }
   __syncthreads();
-  const double t = (red[0] + red[1]) + (red[2] + red[3]);
+  // one thread adds the four partials (the SM's FP64 unit is shared: the
+  // same three additions in every warp would queue behind each other)
+  if (threadIdx.x == 0) red[4] = scale * ((red[0] + red[1]) + (red[2] + red[3]));
   __syncthreads();
-  return t;
+  return red[4];
 }
 
 __global__ void __launch_bounds__(512) tridiag_persistent_kernel(double* A, int n, double* d,
@@ -227,7 +229,7 @@ __global__ void __launch_bounds__(512) tridiag_smem_kernel(double* A, int n, dou
   for (int j = tid; j < n; j += nt) col[j] = A[j];   // column 0 = row 0 (A is symmetric)
   // nobody reads A after this barrier; CTA 0 then stores the Householder vectors in it
   if (!grid_sync(bar, nb)) return;
-  __shared__ double hh[3];   // alpha, tau, v0 of the current column
+  __shared__ double hh[4];   // alpha, tau, v0, tau / 2 of the current column
   for (int k = 0; k + 2 < n; ++k) {
     double s = 0.0;
     if (tid < 128)
@@ -249,6 +251,7 @@ __global__ void __launch_bounds__(512) tridiag_smem_kernel(double* A, int n, dou
         hh[1] = 2.0 / (vv * vv + sig);
         hh[2] = vv;
       }
+      hh[3] = 0.5 * hh[1];
     }
     __syncthreads();
     const double alpha = hh[0], t = hh[1], v0 = hh[2];
@@ -289,7 +292,7 @@ __global__ void __launch_bounds__(512) tridiag_smem_kernel(double* A, int n, dou
     double q = 0.0;
     if (tid < 128)
       for (int j = k + 1 + tid; j < n; j += 128) q += v[j] * w[j];
-    const double K = 0.5 * t * sum4(q, red);
+    const double K = sum4(q, red, hh[3]);   // (tau / 2) v.p
     for (int j = k + 1 + tid; j < n; j += nt) w[j] = fma(-K, v[j], w[j]);
     __syncthreads();
     // rank-2 update of the owned rows i > k
