@@ -86,8 +86,13 @@ typedef struct {
 
 /* Options of the assembly.  NULL means defaults. */
 typedef struct {
-  int chunk_points;      /* target points per contraction work item [0 = planner's choice] */
-  int keep_hphi;         /* keep H phi resident after the call (1) [1] */
+  int chunk_points;      /* target points per contraction work item [0 = planner's choice];
+                            a value different from the current plan's re-plans */
+  int use_graph;         /* [1] capture the assembly's launches for this precision as a
+                            CUDA graph on first use and replay it; used only while
+                            profiling is off (per-launch timing needs separate launches)
+                            and on a stream that can be captured (not the legacy default
+                            stream); 0 launches the kernels one by one */
 } ofm_assemble_opts;
 
 /* Counts describing the planned work (after ofm_build_fragments). */

@@ -66,6 +66,16 @@ static ofm_status sync(ofm_ctx* c, const char* what) {
 
 static size_t elem_size(const ofm_ctx* c) { return c->storage == OFM_STORE_FP64 ? 8 : 4; }
 
+// Captured assembly graphs refer to the plans and buffers of the moment.
+static void drop_graphs(ofm_ctx* c) {
+  for (auto& g : c->asm_exec)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+}
+
+
 static int find_pair(const ofm_ctx* c, int a, int b) {
   // pairs are sorted by (a, b) with a <= b
   int lo = 0, hi = (int)c->pairs.size() - 1;
@@ -136,6 +146,7 @@ extern "C" ofm_status ofm_create(ofm_ctx** out, void* cuda_stream) {
 extern "C" void ofm_destroy(ofm_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
+  drop_graphs(c);
   ofm_prof_release(c);
   DevBuf* bufs[] = {&c->V, &c->states, &c->hphi, &c->d_frags, &c->d_pairs,
                     &c->d_pieces, &c->d_items, &c->partials, &c->blocks, &c->dense_H,
@@ -153,6 +164,36 @@ extern "C" const char* ofm_last_error(const ofm_ctx* c) {
 }
 
 // ------------------------------------------------------------- build -------
+
+// Contraction plans (CUDA-core and tensor-core) for the current fragments,
+// with work items of about c->asm_chunk points (0: the planner's choice,
+// about 8 items per SM on CUDA cores, 4 per SM on tensor cores).  Any
+// captured assembly graph refers to the old plan and is dropped.
+static ofm_status plan_contraction(ofm_ctx* c) {
+  drop_graphs(c);
+  const size_t es = elem_size(c);
+  long long chunk = c->asm_chunk > 0 ? c->asm_chunk : std::max<long long>(256, c->kh / (8 * 152));
+  if (c->asm_chunk <= 0) chunk = std::min<long long>(chunk, 16384);
+  c->simt_chunk = chunk;
+  make_items_simt(c->frags, c->pairs, c->simt_tile, chunk, c->simt_pairs, c->simt_pieces,
+                  c->simt_items, c->simt_partial_elems);
+  const int np = (int)c->simt_pairs.size();
+  OFM_TRY(ofm_ensure(c, c->d_pairs, sizeof(DevPair) * std::max(1, np), "pair table"));
+  OFM_TRY(ofm_ensure(c, c->d_pieces, sizeof(Piece) * std::max<size_t>(1, c->simt_pieces.size()), "piece table"));
+  OFM_TRY(ofm_ensure(c, c->d_items, sizeof(WorkItem) * std::max<size_t>(1, c->simt_items.size()), "work items"));
+  OFM_TRY(ofm_ensure(c, c->partials, sizeof(double) * c->simt_partial_elems, "partials"));
+  OFM_CUDA(c, cudaMemcpyAsync(c->d_pairs.p, c->simt_pairs.data(), sizeof(DevPair) * np,
+                              cudaMemcpyHostToDevice, c->stream));
+  OFM_CUDA(c, cudaMemcpyAsync(c->d_pieces.p, c->simt_pieces.data(),
+                              sizeof(Piece) * c->simt_pieces.size(), cudaMemcpyHostToDevice, c->stream));
+  OFM_CUDA(c, cudaMemcpyAsync(c->d_items.p, c->simt_items.data(),
+                              sizeof(WorkItem) * c->simt_items.size(), cudaMemcpyHostToDevice, c->stream));
+  c->blk_elems = 0;
+  for (auto& p : c->simt_pairs) c->blk_elems = std::max<long long>(c->blk_elems, p.blk_off + 2LL * c->frags[p.a].n * c->frags[p.b].n);
+  OFM_TRY(ofm_ensure(c, c->blocks, sizeof(double) * c->blk_elems, "blocks"));
+  c->finalize_bytes = (double)c->simt_partial_elems * (es == 8 ? 8 : 4) + 8.0 * c->blk_elems;
+  return ofm_plan_extra(c);
+}
 
 extern "C" ofm_status ofm_build_fragments(ofm_ctx* c, const ofm_grid* grid, const double* V,
                                           ofm_location v_loc, const ofm_fragment* frags,
@@ -221,28 +262,8 @@ extern "C" ofm_status ofm_build_fragments(ofm_ctx* c, const ofm_grid* grid, cons
   if (n_frag > 65535) return ofm_fail(c, OFM_ERR_INVALID, "at most 65535 fragments");
   c->agrid = apply_grid(c->frags, es == 8, false);
 
-  // SIMT contraction plan: about 8 work items per SM
-  long long chunk = std::max<long long>(256, c->kh / (8 * 152));
-  chunk = std::min<long long>(chunk, 16384);
-  c->simt_chunk = chunk;
-  make_items_simt(c->frags, c->pairs, c->simt_tile, chunk, c->simt_pairs, c->simt_pieces,
-                  c->simt_items, c->simt_partial_elems);
-  const int np = (int)c->simt_pairs.size();
-  OFM_TRY(ofm_ensure(c, c->d_pairs, sizeof(DevPair) * std::max(1, np), "pair table"));
-  OFM_TRY(ofm_ensure(c, c->d_pieces, sizeof(Piece) * std::max<size_t>(1, c->simt_pieces.size()), "piece table"));
-  OFM_TRY(ofm_ensure(c, c->d_items, sizeof(WorkItem) * std::max<size_t>(1, c->simt_items.size()), "work items"));
-  OFM_TRY(ofm_ensure(c, c->partials, sizeof(double) * c->simt_partial_elems, "partials"));
-  OFM_CUDA(c, cudaMemcpyAsync(c->d_pairs.p, c->simt_pairs.data(), sizeof(DevPair) * np,
-                              cudaMemcpyHostToDevice, c->stream));
-  OFM_CUDA(c, cudaMemcpyAsync(c->d_pieces.p, c->simt_pieces.data(),
-                              sizeof(Piece) * c->simt_pieces.size(), cudaMemcpyHostToDevice, c->stream));
-  OFM_CUDA(c, cudaMemcpyAsync(c->d_items.p, c->simt_items.data(),
-                              sizeof(WorkItem) * c->simt_items.size(), cudaMemcpyHostToDevice, c->stream));
-  c->blk_elems = 0;
-  for (auto& p : c->simt_pairs) c->blk_elems = std::max<long long>(c->blk_elems, p.blk_off + 2LL * c->frags[p.a].n * c->frags[p.b].n);
-  OFM_TRY(ofm_ensure(c, c->blocks, sizeof(double) * c->blk_elems, "blocks"));
-  c->finalize_bytes = (double)c->simt_partial_elems * (es == 8 ? 8 : 4) + 8.0 * c->blk_elems;
-  OFM_TRY(ofm_plan_extra(c));
+  c->asm_chunk = 0;
+  OFM_TRY(plan_contraction(c));
   // host copies of tables are read back by later calls: wait for the uploads
   OFM_TRY(sync(c, "build_fragments"));
   c->built = true;
@@ -318,15 +339,9 @@ ofm_status ofm_apply_h(ofm_ctx* c) {
   return check_launch(c, "apply H");
 }
 
-extern "C" ofm_status ofm_assemble_HS(ofm_ctx* c, ofm_precision prec, const ofm_assemble_opts* opts) {
-  if (!c) return OFM_ERR_INVALID;
-  if (!c->built) return ofm_fail(c, OFM_ERR_STATE, "ofm_build_fragments must come first");
-  if (!c->have_states) return ofm_fail(c, OFM_ERR_STATE, "fragment states are not set (ofm_fragment_eigs or ofm_set_fragment_states)");
-  if (prec < OFM_PREC_FP64 || prec > OFM_PREC_BF16X3) return ofm_fail(c, OFM_ERR_INVALID, "unknown precision");
-  if (prec != OFM_PREC_FP64 && c->storage == OFM_STORE_FP64)
-    return ofm_fail(c, OFM_ERR_INVALID, "FP32 and tensor-core contractions need FP32 storage");
-  (void)opts;
-  c->assembled = c->dense_ready = c->factored = false;
+// The launches of one assembly (a1 apply, a3/a4 contraction, a5 blocks) on
+// the context stream; no host synchronisation, so it can be captured.
+static ofm_status enqueue_assembly(ofm_ctx* c, ofm_precision prec) {
   OFM_TRY(ofm_apply_h(c));
   if (prec == OFM_PREC_FP64 || prec == OFM_PREC_FP32) {
     { KTimer t(c, KC_CONTRACT, 1, c->contract_bytes, (double)c->flops);
@@ -343,6 +358,74 @@ extern "C" ofm_status ofm_assemble_HS(ofm_ctx* c, ofm_precision prec, const ofm_
   } else {
     OFM_TRY(ofm_contract_tc(c, prec));
   }
+  return OFM_OK;
+}
+
+// Captures enqueue_assembly for `prec` as a CUDA graph.  A stream that cannot
+// be captured (the legacy default stream, for one) turns graphs off for the
+// context; the assembly is then launched directly.
+static ofm_status capture_assembly(ofm_ctx* c, ofm_precision prec) {
+  ofm::KStat before[KC_COUNT];
+  for (int k = 0; k < KC_COUNT; ++k) before[k] = c->prof.st[k];
+  if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    c->graphs_off = true;
+    return OFM_OK;
+  }
+  const ofm_status st = enqueue_assembly(c, prec);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+  // nothing ran yet: the counters take what one replay adds
+  for (int k = 0; k < KC_COUNT; ++k) {
+    c->asm_cost[prec][k].launches = c->prof.st[k].launches - before[k].launches;
+    c->asm_cost[prec][k].bytes = c->prof.st[k].bytes - before[k].bytes;
+    c->asm_cost[prec][k].flops = c->prof.st[k].flops - before[k].flops;
+    c->prof.st[k] = before[k];
+  }
+  c->asm_tc[prec] = c->tc_check;
+  c->tc_check = false;
+  c->stencil_check = false;
+  if (st != OFM_OK || e != cudaSuccess || !g ||
+      cudaGraphInstantiate(&c->asm_exec[prec], g, 0) != cudaSuccess) {
+    cudaGetLastError();
+    c->asm_exec[prec] = nullptr;
+    c->graphs_off = true;
+  }
+  if (g) cudaGraphDestroy(g);
+  return OFM_OK;
+}
+
+extern "C" ofm_status ofm_assemble_HS(ofm_ctx* c, ofm_precision prec, const ofm_assemble_opts* opts) {
+  if (!c) return OFM_ERR_INVALID;
+  if (!c->built) return ofm_fail(c, OFM_ERR_STATE, "ofm_build_fragments must come first");
+  if (!c->have_states) return ofm_fail(c, OFM_ERR_STATE, "fragment states are not set (ofm_fragment_eigs or ofm_set_fragment_states)");
+  if (prec < OFM_PREC_FP64 || prec > OFM_PREC_BF16X3) return ofm_fail(c, OFM_ERR_INVALID, "unknown precision");
+  if (prec != OFM_PREC_FP64 && c->storage == OFM_STORE_FP64)
+    return ofm_fail(c, OFM_ERR_INVALID, "FP32 and tensor-core contractions need FP32 storage");
+  const long long chunk = opts ? opts->chunk_points : 0;
+  const bool use_graph = opts ? opts->use_graph != 0 : true;
+  if (chunk < 0) return ofm_fail(c, OFM_ERR_INVALID, "chunk_points must be >= 0");
+  if (chunk != c->asm_chunk) {
+    c->asm_chunk = chunk;
+    OFM_TRY(plan_contraction(c));
+  }
+  c->assembled = c->dense_ready = c->factored = false;
+  if (use_graph && !c->prof.on && !c->graphs_off) {
+    if (!c->asm_exec[prec]) OFM_TRY(capture_assembly(c, prec));
+    if (c->asm_exec[prec]) {
+      OFM_CUDA(c, cudaGraphLaunch(c->asm_exec[prec], c->stream));
+      for (int k = 0; k < KC_COUNT; ++k) {
+        c->prof.st[k].launches += c->asm_cost[prec][k].launches;
+        c->prof.st[k].bytes += c->asm_cost[prec][k].bytes;
+        c->prof.st[k].flops += c->asm_cost[prec][k].flops;
+      }
+      c->stencil_check = true;
+      if (c->asm_tc[prec]) c->tc_check = true;
+      c->assembled = true;
+      return OFM_OK;
+    }
+  }
+  OFM_TRY(enqueue_assembly(c, prec));
   c->assembled = true;
   return OFM_OK;
 }

@@ -744,7 +744,7 @@ static ofm_status eig_setup(ofm_ctx* c, int guard_opt) {
       goff[a] = w->gpairs[a].blk_off;
       gk += sp[a].kh;
     }
-    OFM_TRY(ofm_tc_plan_build(c, &w->gtc, w->efr, sp, goff, gk));
+    OFM_TRY(ofm_tc_plan_build(c, &w->gtc, w->efr, sp, goff, gk, 0));
   }
 
   for (int i = 0; i < 4; ++i) OFM_TRY(ofm_ensure(c, w->buf[i], w->elems * es, "eigensolver block"));

@@ -193,6 +193,13 @@ struct ofm_ctx {
   // algorithmic traffic of one launch, set by the planner
   double apply_bytes = 0, contract_bytes = 0, finalize_bytes = 0;
   ofm_prof prof;                    // per-kernel-class launch counts and event timing
+  // assembly as CUDA graphs (one per precision, captured on first use with
+  // profiling off); what one replay adds to the per-class counters
+  long long asm_chunk = 0;          // contraction work-item points of the current plans (0: planner)
+  cudaGraphExec_t asm_exec[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  ofm::KStat asm_cost[5][ofm::KC_COUNT];
+  bool asm_tc[5] = {false, false, false, false, false};
+  bool graphs_off = false;          // capture failed once on this stream: launch directly
   bool tc_check = false;            // a tensor-core launch's timeout flag is unread
   bool stencil_check = false;       // a stencil launch's timeout flag is unread
   struct EigWork* eig = nullptr;    // fragment-eigensolver buffers and plan
@@ -223,7 +230,7 @@ ofm_status ofm_contract_tc(ofm_ctx* c, ofm_precision prec);
 enum { OFM_TC_TF32 = 0, OFM_TC_BF16 = 1, OFM_TC_BF16X3 = 2, OFM_TC_TF32X3 = 3 };
 ofm_status ofm_tc_plan_build(ofm_ctx* c, struct TcPlan** tp, const std::vector<ofm::DevFrag>& fr,
                              const std::vector<ofm::HostPair>& pairs,
-                             const std::vector<long long>& blk_off, long long kh);
+                             const std::vector<long long>& blk_off, long long kh, long long chunk);
 ofm_status ofm_tc_run(ofm_ctx* c, struct TcPlan* t, int kind, const ofm::DevFrag* d_frags,
                       const void* states, const void* hphi, double* blocks, int kclass_contract,
                       int kclass_finalize, double bytes, double flops);

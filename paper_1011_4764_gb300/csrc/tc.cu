@@ -559,13 +559,14 @@ static void set_smem_attr() {
 }
 
 // Tensor-core plan for the pairs over the fragment table fr (FP32 storage,
-// row strides fr[].ld): one item per row chunk of a piece, chunks sized for
-// about four items per SM; blk_off[p] is pair p's offset in the FP64 block
+// row strides fr[].ld): one item per row chunk of a piece, chunks of about
+// `chunk` points (0: sized for about four items per SM); blk_off[p] is pair
+// p's offset in the FP64 block
 // arena.  The plan is marked not usable (with the reason) when a fragment
 // has more than 128 states or the staging does not fit shared memory.
 ofm_status ofm_tc_plan_build(ofm_ctx* c, TcPlan** tp, const std::vector<DevFrag>& fr,
                              const std::vector<HostPair>& prs, const std::vector<long long>& blk_off,
-                             long long kh) {
+                             long long kh, long long chunk) {
   if (!*tp) *tp = new TcPlan();
   TcPlan* t = *tp;
   t->pairs.clear();
@@ -585,7 +586,7 @@ ofm_status ofm_tc_plan_build(ofm_ctx* c, TcPlan** tp, const std::vector<DevFrag>
     ldB = std::max(ldB, B.ld);
     Rb = std::max(Rb, (2 * B.n + 15) / 16 * 16);
   }
-  const long long target = std::max<long long>(1024, kh / (4 * 152));
+  const long long target = chunk > 0 ? chunk : std::max<long long>(1024, kh / (4 * 152));
   for (size_t p = 0; p < prs.size(); ++p) {
     const HostPair& hp = prs[p];
     const DevFrag& B = fr[hp.b];
@@ -678,7 +679,7 @@ ofm_status ofm_plan_extra(ofm_ctx* c) {
   }
   std::vector<long long> off(c->pairs.size());
   for (size_t p = 0; p < c->pairs.size(); ++p) off[p] = c->simt_pairs[p].blk_off;
-  return ofm_tc_plan_build(c, &c->tc, c->frags, c->pairs, off, c->kh);
+  return ofm_tc_plan_build(c, &c->tc, c->frags, c->pairs, off, c->kh, c->asm_chunk);
 }
 
 template <int KIND>

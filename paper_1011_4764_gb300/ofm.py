@@ -46,7 +46,7 @@ class ofm_eig_opts(C.Structure):
 
 
 class ofm_assemble_opts(C.Structure):
-    _fields_ = [("chunk_points", C.c_int), ("keep_hphi", C.c_int)]
+    _fields_ = [("chunk_points", C.c_int), ("use_graph", C.c_int)]
 
 
 class ofm_plan_info(C.Structure):
@@ -259,8 +259,8 @@ class Context:
         return out.T
 
     # -- ofm_assemble_HS
-    def assemble(self, precision="fp32", chunk_points=0):
-        o = ofm_assemble_opts(chunk_points, 1)
+    def assemble(self, precision="fp32", chunk_points=0, use_graph=True):
+        o = ofm_assemble_opts(chunk_points, 1 if use_graph else 0)
         self._check(self.lib.ofm_assemble_HS(self.h, PREC[precision], C.byref(o)))
 
     def pairs(self):
