@@ -485,8 +485,16 @@ __global__ void __launch_bounds__(256) rayleigh_ritz_kernel(const DevFrag* efr, 
 
 // X_new = Y C and HX_new = HY C over the interior points (columns >= rank
 // get fresh random values and H X = 0), plus per-block partial sums of
-// (HX_new - theta X_new)^2 per column for the residual norms.  A thread owns
-// one column j of a group of points, so the partial sums need no atomics.
+// (HX_new - theta X_new)^2 per column for the residual norms.
+// A CTA takes tiles of RT points: their rows of Y and H Y are staged in
+// shared memory (row stride m + 1: conflict-free column reads); thread
+// (point lane pl, column group jg) accumulates the columns j = jb + jg + 4 i
+// (i < RJ) of its point in registers, so each coefficient read is a warp
+// broadcast and feeds two FMAs per point.  Results go back through shared
+// memory and leave as whole point rows (coalesced).
+constexpr int RT = 64;   // points per tile
+constexpr int RJ = 10;   // columns per thread and column block (4 groups x 10 = 40)
+
 template <typename T>
 __global__ void __launch_bounds__(256) rotate_kernel(const DevFrag* efr, const T* Y, T* Xo,
                                                      const T* HY, T* HXo, const double* Cm,
@@ -495,84 +503,115 @@ __global__ void __launch_bounds__(256) rotate_kernel(const DevFrag* efr, const T
                                                      double* partial, int mstride,
                                                      unsigned long long salt) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int TP = 32;
   const int f = blockIdx.y;
   const DevFrag F = efr[f];
-  const int m = F.n;
+  const int m = F.n, ms = m + 1;
   const int r = rank[f];
   const int ex = F.ext[0], ey = F.ext[1];
   const int P = F.ext[0] * F.ext[1] * F.ext[2];
-  double* red = reinterpret_cast<double*>(smem_raw);            // blockDim.x
-  int* pds = reinterpret_cast<int*>(red + blockDim.x);           // TP
-  T* Cs = reinterpret_cast<T*>(pds + TP);                        // m * m
-  T* ys = Cs + m * m;                                            // TP * m
-  T* hs = ys + TP * m;                                           // TP * m
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x) Cs[e] = (T)Cm[f * cstride + e];
-  const int G = blockDim.x / m;
-  const int j = threadIdx.x % m, g = threadIdx.x / m;
-  const bool active = g < G;
-  const T th = active ? (T)theta[toff[f] + j] : T(0);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int pl = tid & (RT - 1), jg = tid / RT;   // point lane, column group (0..3)
+  constexpr int JB = 4 * RJ;                       // columns per block
+  int* pds = reinterpret_cast<int*>(smem_raw);                   // RT
+  T* rs = reinterpret_cast<T*>(smem_raw + 16 * ((RT * sizeof(int) + 15) / 16));    // JB residual sums
+  T* Cs = rs + 4 * RJ;                                           // m * m
+  T* ys = Cs + m * m;                                            // RT * ms
+  T* hs = ys + RT * ms;                                          // RT * ms
+  for (int e = tid; e < m * m; e += blockDim.x) Cs[e] = (T)Cm[f * cstride + e];
   const unsigned long long s0 = splitmix64(salt);
-  // residual partial sums in the working precision (FP64 is scarce on this
-  // part); they are combined in FP64 below
-  T racc = 0;
-  for (int t0 = blockIdx.x * TP; t0 < P; t0 += gridDim.x * TP) {
-    __syncthreads();
-    if (threadIdx.x < TP) {
-      const int t = t0 + threadIdx.x;
-      int pd = -1;
-      if (t < P) {
-        const int x = t % ex, y = (t / ex) % ey, z = t / (ex * ey);
-        pd = ((z + F.lo[2]) * F.dext[1] + (y + F.lo[1])) * F.dext[0] + x + F.lo[0];
-      }
-      pds[threadIdx.x] = pd;
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < TP * m; e += blockDim.x) {
-      const int pp = e / m, k = e - pp * m;
-      const int pd = pds[pp];
-      const long long a = F.off + (long long)pd * F.ld + k;
-      ys[e] = pd >= 0 ? Y[a] : (T)0;
-      hs[e] = pd >= 0 ? HY[a] : (T)0;
-    }
-    __syncthreads();
-    if (active) {
-      for (int pp = g; pp < TP; pp += G) {
-        const int pd = pds[pp];
-        if (pd < 0) continue;
-        T x = 0, hx = 0;
-        if (j < r) {
-          const T* yr = ys + pp * m;
-          const T* hr = hs + pp * m;
-          for (int k = 0; k < m; ++k) {
-            const T cc = Cs[k * m + j];
-            x += yr[k] * cc;
-            hx += hr[k] * cc;
-          }
-        } else {
-          const unsigned long long key = ((unsigned long long)f << 44) ^ ((unsigned long long)j << 32) ^ (unsigned long long)pd;
-          const unsigned long long rr = splitmix64(key + s0);
-          x = (T)(((double)(rr >> 11) * (2.0 / 9007199254740992.0) - 1.0) / sqrt((double)P));
+  const T inv_sqrt_p = (T)(1.0 / sqrt((double)P));
+  // column blocks of JB columns (one for m <= JB); the tile rows are staged
+  // again for each block
+  for (int jb = 0; jb < m; jb += JB) {
+    const int jn = min(JB, m - jb);
+    // residual partial sums of the block's columns, in shared memory
+    if (tid < JB) rs[tid] = T(0);
+    for (int t0 = blockIdx.x * RT; t0 < P; t0 += gridDim.x * RT) {
+      __syncthreads();   // previous tile fully written out
+      if (tid < RT) {
+        const int t = t0 + tid;
+        int pd = -1;
+        if (t < P) {
+          const int x = t % ex, y = (t / ex) % ey, z = t / (ex * ey);
+          pd = ((z + F.lo[2]) * F.dext[1] + (y + F.lo[1])) * F.dext[0] + x + F.lo[0];
         }
-        const long long a = F.off + (long long)pd * F.ld + j;
-        Xo[a] = x;
-        HXo[a] = hx;
-        const T d = hx - th * x;
-        racc += d * d;
+        pds[tid] = pd;
+      }
+      __syncthreads();
+      // stage the tile's rows: warp w takes points w, w + 8, ..., lanes along the row
+      for (int pp = warp; pp < RT; pp += 8) {
+        const int pd = pds[pp];
+        const long long a = F.off + (long long)max(pd, 0) * F.ld;
+        for (int k = lane; k < m; k += 32) {
+          ys[pp * ms + k] = pd >= 0 ? Y[a + k] : T(0);
+          hs[pp * ms + k] = pd >= 0 ? HY[a + k] : T(0);
+        }
+      }
+      __syncthreads();
+      T x[RJ], hx[RJ];
+#pragma unroll
+      for (int i = 0; i < RJ; ++i) {
+        x[i] = T(0);
+        hx[i] = T(0);
+      }
+      for (int k = 0; k < m; ++k) {
+        const T yv = ys[pl * ms + k], hv = hs[pl * ms + k];
+        const T* crow = Cs + k * m + jb + jg;
+#pragma unroll
+        for (int i = 0; i < RJ; ++i) {
+          if (jg + 4 * i < jn) {
+            const T cc = crow[4 * i];
+            x[i] += yv * cc;
+            hx[i] += hv * cc;
+          }
+        }
+      }
+      __syncthreads();   // every thread has read the staged rows
+      const int pd = pds[pl];
+      // results of the block into the staged rows' columns jb .. jb + jn - 1
+#pragma unroll
+      for (int i = 0; i < RJ; ++i) {
+        const int c = jg + 4 * i;
+        if (c >= jn) continue;
+        const int j = jb + c;
+        T xv = x[i], hv = hx[i];
+        if (j >= r) {   // dropped direction: a fresh random vector, H X left zero
+          hv = T(0);
+          xv = T(0);
+          if (pd >= 0) {
+            const unsigned long long key =
+                ((unsigned long long)f << 44) ^ ((unsigned long long)j << 32) ^ (unsigned long long)pd;
+            const unsigned long long rr = splitmix64(key + s0);
+            xv = (T)((double)(rr >> 11) * (2.0 / 9007199254740992.0) - 1.0) * inv_sqrt_p;
+          }
+        }
+        ys[pl * ms + j] = xv;
+        hs[pl * ms + j] = hv;
+        // residual of this output, summed over the warp's 32 points by
+        // shuffles, then one shared-memory atomic per warp and column
+        const T d = pd >= 0 ? hv - (T)theta[toff[f] + j] * xv : T(0);
+        T v = d * d;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) atomicAdd(&rs[c], v);
+      }
+      __syncthreads();
+      // coalesced row writes
+      for (int pp = warp; pp < RT; pp += 8) {
+        const int pdo = pds[pp];
+        if (pdo < 0) continue;
+        const long long a = F.off + (long long)pdo * F.ld;
+        for (int k = jb + lane; k < jb + jn; k += 32) {
+          Xo[a + k] = ys[pp * ms + k];
+          HXo[a + k] = hs[pp * ms + k];
+        }
       }
     }
-  }
-  __syncthreads();
-  red[threadIdx.x] = (double)racc;
-  __syncthreads();
-  if (threadIdx.x < m) {
-    double s = 0.0;
-    for (int gg = 0; gg < G; ++gg) s += red[gg * m + threadIdx.x];
-    partial[((long long)f * gridDim.x + blockIdx.x) * mstride + threadIdx.x] = s;
+    __syncthreads();
+    if (tid < jn) partial[((long long)f * gridDim.x + blockIdx.x) * mstride + jb + tid] = (double)rs[tid];
+    __syncthreads();
   }
 }
 
-// res = sqrt(sum of the per-block partials), fixed order.
 __global__ void residual_reduce_kernel(const DevFrag* efr, const double* partial, int nblocks,
                                        int mstride, const long long* toff, double* res) {
   const int f = blockIdx.x;
@@ -780,9 +819,10 @@ static ofm_status eig_setup(ofm_ctx* c, int guard_opt) {
   OFM_CUDA(c, cudaStreamSynchronize(s));
   long long maxP = 0;
   for (auto& E : w->efr) maxP = std::max<long long>(maxP, (long long)E.ext[0] * E.ext[1] * E.ext[2]);
-  w->rot_blocks = (int)std::min<long long>((maxP + 31) / 32, 64);
+  w->rot_blocks = (int)std::min<long long>((maxP + RT - 1) / RT, 64);
   OFM_TRY(ofm_ensure(c, w->rpart, sizeof(double) * (size_t)nf * w->rot_blocks * w->mmax, "residual partials"));
-  w->rot_smem = 256 * sizeof(double) + 32 * sizeof(int) + ((size_t)w->mmax * w->mmax + 64 * (size_t)w->mmax) * es;
+  w->rot_smem = 16 * ((RT * sizeof(int) + 15) / 16) +
+                (4 * RJ + (size_t)w->mmax * w->mmax + 2 * (size_t)RT * (w->mmax + 1)) * es;
   if (w->rot_smem > 227 * 1024) return ofm_fail(c, OFM_ERR_INVALID, "block size too large for the rotation kernel");
   if (fp64) OFM_CUDA(c, cudaFuncSetAttribute(rotate_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w->rot_smem));
   else OFM_CUDA(c, cudaFuncSetAttribute(rotate_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w->rot_smem));
