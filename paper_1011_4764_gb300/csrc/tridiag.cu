@@ -3,12 +3,13 @@
 //
 // 1. Householder reduction of A to tridiagonal form in ONE persistent
 //    cooperative kernel: per column k, every CTA forms the Householder
-//    vector itself, the CTAs compute p = tau A22 v by rows, meet at a grid
-//    barrier and apply A22 -= v w^T + w v^T (w = p - (tau/2)(v^T p) v) by
-//    rows.  With the matrix rows resident in shared memory one barrier per
-//    column suffices (the next column travels with p as a published row);
-//    the global-memory fallback meets twice.  The barrier spins a bounded
-//    number of times and reports a timeout instead of hanging.
+//    vector itself, the CTAs compute p = tau A22 v by rows, exchange p and
+//    apply A22 -= v w^T + w v^T (w = p - (tau/2)(v^T p) v) by rows.  With the
+//    matrix rows resident in shared memory the exchange is a set of
+//    generation-tagged published values (no barrier; the next column travels
+//    as a published row); the global-memory fallback meets at a grid barrier
+//    twice per column.  Every wait spins a bounded number of times and
+//    reports a timeout instead of hanging.
 // 2. Eigenvalues by index with multisection: one CTA of one to four warps
 //    per wanted eigenvalue; each thread counts the eigenvalues below one of
 //    32-128 points of the current interval (Sturm sequence of T - x I
@@ -75,24 +76,6 @@ __device__ __forceinline__ double block_sum(double s, double* red) {
   }
   __syncthreads();
   return red[32];
-}
-
-// Sum over the first four warps (one per SM sub-partition; their partial
-// sums cover the whole range), in a fixed order.  Fewer warps than the whole
-// CTA because each FP64 instruction of a warp occupies a sub-partition's
-// FP64 pipe for many cycles: sixteen warps' shuffle trees cost more than
-// the additions they save.
-__device__ __forceinline__ double sum4(double s, double* red, double scale = 1.0) {
-  if (threadIdx.x < 128) {
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  }
-  __syncthreads();
-  // one thread adds the four partials (the SM's FP64 unit is shared: the
-  // same three additions in every warp would queue behind each other)
-  if (threadIdx.x == 0) red[4] = scale * ((red[0] + red[1]) + (red[2] + red[3]));
-  __syncthreads();
-  return red[4];
 }
 
 __global__ void __launch_bounds__(512) tridiag_persistent_kernel(double* A, int n, double* d,
@@ -195,126 +178,293 @@ __global__ void __launch_bounds__(512) tridiag_persistent_kernel(double* A, int 
   }
 }
 
-// The same reduction with the matrix resident in shared memory and ONE
-// grid barrier per column.  CTA b owns the rows i = b, b + nb, b + 2 nb, ...
-// for the whole reduction.  At step k every CTA holds the whole column k of
-// A_k and forms v itself; it computes p_i = tau (A_k v)_i for its rows, and
-// the owner of row k+1 also publishes that row of A_k.  After the barrier
-// every CTA has p and row k+1, forms w = p - (tau/2)(v.p) v, updates its own
-// rows, and obtains column k+1 of A_{k+1} from row k+1 by symmetry:
-//     A_{k+1}[k+1, i] = A_k[k+1, i] - v_{k+1} w_i - w_{k+1} v_i,
-// the same expression (same rounding) the owner applies to its copy of the
-// row.  So the next Householder vector needs no second exchange.  p and the
-// published row are double-buffered by the parity of k: a CTA that runs
-// ahead into step k+1 writes the other half while slower CTAs still read.
-__global__ void __launch_bounds__(512) tridiag_smem_kernel(double* A, int n, double* d, double* e,
-                                                           double* tau, double* xbuf,
-                                                           GridBar* bar) {
+// The same reduction with the matrix resident in shared memory and no grid
+// barrier inside the column loop.  CTA b owns the rows i = b, b + nb, ... for
+// the whole reduction, and every CTA keeps the whole current column k of A_k
+// (the Householder vector v is that column with v_{k+1} = x0 - alpha).
+//
+// Exchange.  The values a CTA needs from the others at column k are p_j =
+// tau (A_k v)_j for every j > k and row k+1 of A_k.  Each is published as two
+// 64-bit words, each holding 32 bits of the value and the column's generation
+// k+1 in the other 32 (an aligned 64-bit store is single-copy atomic), so a
+// reader that sees both words with the current generation has the value: no
+// counter, no barrier, one L2 round trip between the last writer and the
+// readers.  The slots are double-buffered by the parity of k.  A CTA writes
+// column k+2's values into a slot only after it has read every p of column
+// k+1, and each CTA that still reads column k's values writes some p of
+// column k+1 only after that read, so no slot is overwritten while read.
+// CTAs whose rows are all done leave the loop.
+//
+// Work per column, warp-specialised (warps 0-11 own matrix rows, warps 12-15
+// the vector work):
+//   rows:   p_i = tau (A_k col)_i - tau alpha A_k[i, k+1] (v differs from the
+//           column only in entry k+1, so the product starts before alpha and
+//           tau exist); after the exchange, pass 1 of the rank-2 update
+//           A -= v p^T while the vector warps form K; then pass 2,
+//           A -= c v^T with c = p - 2 K v, fused with the next column's
+//           product.  Together: A -= v w^T + w v^T with w = p - K v.
+//   vector: K = (tau/2) v.p, column k+1 of A_{k+1} from the published row,
+//           A_{k+1}[k+1, i] = A_k[k+1, i] - v_{k+1} w_i - w_{k+1} v_i,
+//           its norm, and the next alpha, tau (one thread: the FP64 square
+//           root and division run while the row warps compute).
+namespace {
+
+constexpr int TRI_THREADS = 512;
+constexpr int TRI_ROW_WARPS = 12;           // warps 0..11
+constexpr int TRI_VEC0 = 32 * TRI_ROW_WARPS;  // threads 384..511
+constexpr int TRI_PMAX = 8;                 // published entries polled per thread, at most
+constexpr int TRI_RMAX = 16;                // rows per CTA, at most
+
+struct __align__(16) Pub {
+  unsigned long long a, b;
+};
+
+__device__ __forceinline__ void pub_put(Pub* dst, double x, unsigned int gen) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const unsigned long long g = (unsigned long long)gen << 32;
+  const unsigned long long lo = (bits & 0xffffffffull) | g, hi = (bits >> 32) | g;
+  asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(dst), "l"(lo), "l"(hi)
+               : "memory");
+}
+
+__device__ __forceinline__ void pub_get(const Pub* src, unsigned long long& lo,
+                                        unsigned long long& hi) {
+  asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(lo), "=l"(hi) : "l"(src)
+               : "memory");
+}
+
+__device__ __forceinline__ void named_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void named_arrive(int id, int count) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ double warp_allsum(double s) {
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+// alpha, tau, v0, tau/2 of the reflector that maps (x0, x_rest) to
+// (alpha, 0), with sig = |x_rest|^2 (the sign of alpha opposite to x0's).
+__device__ __forceinline__ void house_scalars(double x0, double sig, double* hh) {
+  if (sig == 0.0) {
+    hh[0] = x0;
+    hh[1] = 0.0;
+    hh[2] = 1.0;
+  } else {
+    const double nrm = sqrt(fma(x0, x0, sig));
+    const double al = (x0 > 0.0) ? -nrm : nrm;
+    const double vv = x0 - al;
+    hh[0] = al;
+    hh[1] = 2.0 / fma(vv, vv, sig);
+    hh[2] = vv;
+  }
+  hh[3] = 0.5 * hh[1];
+}
+
+// Polls the published p_j and A_k[k+1, j] (j = k+1 .. n-1) into pw and rk.
+// Returns false when the wait exceeded its bound or another CTA gave up.
+__device__ __forceinline__ bool poll_column(const Pub* P, const Pub* Rw, int k, int n,
+                                            unsigned int gen, double* pw, double* rk,
+                                            GridBar* bar) {
+  const int m1 = n - k - 1, tot = 2 * m1, tid = threadIdx.x;
+  unsigned int pend = 0;
+#pragma unroll
+  for (int q = 0; q < TRI_PMAX; ++q)
+    if (tid + q * TRI_THREADS < tot) pend |= 1u << q;
+  unsigned int spins = 0;
+  while (pend) {
+    unsigned long long lo[TRI_PMAX], hi[TRI_PMAX];
+#pragma unroll
+    for (int q = 0; q < TRI_PMAX; ++q)
+      if ((pend >> q) & 1u) {
+        const int e = tid + q * TRI_THREADS;
+        pub_get(e < m1 ? P + (k + 1 + e) : Rw + (k + 1 + e - m1), lo[q], hi[q]);
+      }
+#pragma unroll
+    for (int q = 0; q < TRI_PMAX; ++q)
+      if (((pend >> q) & 1u) && (unsigned int)(lo[q] >> 32) == gen &&
+          (unsigned int)(hi[q] >> 32) == gen) {
+        const int e = tid + q * TRI_THREADS;
+        const double x =
+            __longlong_as_double((long long)(((hi[q] & 0xffffffffull) << 32) | (lo[q] & 0xffffffffull)));
+        if (e < m1)
+          pw[k + 1 + e] = x;
+        else
+          rk[k + 1 + e - m1] = x;
+        pend &= ~(1u << q);
+      }
+    if (pend) {
+      ++spins;
+      if (spins > (1u << 22) || ((spins & 255u) == 0 && *(volatile int*)&bar->err != 0)) {
+        atomicExch(&bar->err, 1);
+        return false;
+      }
+      if (spins > 8) __nanosleep(32);
+    }
+  }
+  return true;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(TRI_THREADS) tridiag_smem_kernel(double* A, int n, double* d,
+                                                                   double* e, double* tau,
+                                                                   Pub* pub, GridBar* bar) {
   extern __shared__ double sm[];
   const int nb = (int)gridDim.x, b = (int)blockIdx.x;
-  const int R = (n - b + nb - 1) / nb;      // rows owned by this CTA
+  const int R = (n - b + nb - 1) / nb;        // rows owned by this CTA (nb < n: R >= 1)
   const int Rmax = (n + nb - 1) / nb;
-  double* rows = sm;                        // Rmax x n
-  double* v = rows + (size_t)Rmax * n;      // n: Householder vector (indices k+1..n-1)
-  double* w = v + n;                        // n: p, then w
-  double* col = w + n;                      // n: column k of A_k (indices k+1..n-1)
-  double* rk = col + n;                     // n: row k+1 of A_k (indices k+1..n-1)
-  __shared__ double red[40];
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
-  for (int e2 = tid; e2 < R * n; e2 += nt) {
+  const int ilast = b + (R - 1) * nb;         // last owned row
+  double* rows = sm;                          // Rmax x n
+  double* cb0 = rows + (size_t)Rmax * n;      // columns k (even k) ...
+  double* cb1 = cb0 + n;                      // ... and k (odd k)
+  double* pw = cb1 + n;                       // p of the current column
+  double* rk = pw + n;                        // published row k+1 of A_k
+  __shared__ double redq[4], reds[4], us[TRI_RMAX], rs[TRI_RMAX];
+  __shared__ double hh[4];   // alpha, tau, v0, tau / 2 of the current column
+  __shared__ double Ks;      // (tau / 2) v.p of the last completed column
+  __shared__ int s_err;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool vecw = tid >= TRI_VEC0;
+  const int vt = tid - TRI_VEC0;
+  for (int e2 = tid; e2 < R * n; e2 += TRI_THREADS) {
     const int li = e2 / n, j = e2 - li * n;
     rows[(size_t)li * n + j] = A[(size_t)(b + li * nb) * n + j];
   }
-  for (int j = tid; j < n; j += nt) col[j] = A[j];   // column 0 = row 0 (A is symmetric)
-  // nobody reads A after this barrier; CTA 0 then stores the Householder vectors in it
-  if (!grid_sync(bar, nb)) return;
-  __shared__ double hh[4];   // alpha, tau, v0, tau / 2 of the current column
-  for (int k = 0; k + 2 < n; ++k) {
-    double s = 0.0;
-    if (tid < 128)
-      for (int i = k + 2 + tid; i < n; i += 128) s += col[i] * col[i];
-    const double sig = sum4(s, red);
-    // the scalar part once (FP64 square root and division are long
-    // sequences), broadcast through shared memory
-    if (tid == 0) {
-      const double x0 = col[k + 1];
-      if (sig == 0.0) {
-        hh[0] = x0;
-        hh[1] = 0.0;
-        hh[2] = 1.0;
-      } else {
-        const double nrm = sqrt(x0 * x0 + sig);
-        const double al = (x0 > 0.0) ? -nrm : nrm;
-        const double vv = x0 - al;
-        hh[0] = al;
-        hh[1] = 2.0 / (vv * vv + sig);
-        hh[2] = vv;
-      }
-      hh[3] = 0.5 * hh[1];
-    }
-    __syncthreads();
-    const double alpha = hh[0], t = hh[1], v0 = hh[2];
-    for (int i = k + 1 + tid; i < n; i += nt) {
-      const double vi = (i == k + 1) ? v0 : col[i];
-      v[i] = vi;
-      if (b == 0) A[(size_t)k * n + i] = vi;   // kept for back-transformation
-    }
-    if (tid == 0) {
-      if (k % nb == b) d[k] = rows[(size_t)(k / nb) * n + k];
-      if (b == 0) {
-        e[k] = alpha;
-        tau[k] = t;
-      }
-    }
-    __syncthreads();
-    double* pb = xbuf + (size_t)(k & 1) * n;
-    double* rb = xbuf + 2 * (size_t)n + (size_t)(k & 1) * n;
-    // p_i = t sum_j A_ij v_j for the owned rows i > k, one warp per row
-    const int li0 = (k + 1 - b + nb - 1) / nb;   // first owned row index > k
-    for (int li = li0 + warp; li < R; li += nwarps) {
-      const double* row = rows + (size_t)li * n;
-      double acc = 0.0;
-      for (int j = k + 1 + lane; j < n; j += 32) acc += row[j] * v[j];
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-      if (lane == 0) pb[b + li * nb] = t * acc;
-    }
-    if ((k + 1) % nb == b) {
-      const double* row = rows + (size_t)((k + 1) / nb) * n;
-      for (int j = k + 1 + tid; j < n; j += nt) rb[j] = row[j];
-    }
-    if (!grid_sync(bar, nb)) return;
-    for (int j = k + 1 + tid; j < n; j += nt) {
-      w[j] = __ldcg(&pb[j]);
-      rk[j] = __ldcg(&rb[j]);
-    }
-    __syncthreads();
-    double q = 0.0;
-    if (tid < 128)
-      for (int j = k + 1 + tid; j < n; j += 128) q += v[j] * w[j];
-    const double K = sum4(q, red, hh[3]);   // (tau / 2) v.p
-    for (int j = k + 1 + tid; j < n; j += nt) w[j] = fma(-K, v[j], w[j]);
-    __syncthreads();
-    // rank-2 update of the owned rows i > k
-    for (int li = li0 + warp; li < R; li += nwarps) {
-      const int i = b + li * nb;
-      double* row = rows + (size_t)li * n;
-      const double vi = v[i], wi = w[i];
-      for (int j = k + 1 + lane; j < n; j += 32) row[j] = fma(-vi, w[j], fma(-wi, v[j], row[j]));
-    }
-    // column k+1 of A_{k+1} from row k+1 (same expression as the owner's update)
-    {
-      const double vk = v[k + 1], wk = w[k + 1];
-      for (int i = k + 2 + tid; i < n; i += nt) col[i] = fma(-vk, w[i], fma(-wk, v[i], rk[i]));
-    }
-    __syncthreads();
+  for (int j = tid; j < n; j += TRI_THREADS) {
+    cb0[j] = A[j];   // column 0 = row 0 (A is symmetric)
+    cb1[j] = 0.0;    // no update precedes column 0
   }
   if (tid == 0) {
-    if (n >= 2) {
-      if ((n - 2) % nb == b) d[n - 2] = rows[(size_t)((n - 2) / nb) * n + n - 2];
-      if ((n - 1) % nb == b) e[n - 2] = rows[(size_t)((n - 1) / nb) * n + n - 2];
+    s_err = 0;
+    Ks = 0.0;
+    if (b == 0) d[0] = A[0];
+  }
+  // nobody reads A after this barrier; the Householder vectors go into it
+  if (!grid_sync(bar, nb)) return;
+  if (vecw) {   // reflector of column 0
+    double s = 0.0;
+    for (int i = 2 + vt; i < n; i += 128) s = fma(cb0[i], cb0[i], s);
+    s = warp_allsum(s);
+    if (lane == 0) reds[warp - TRI_ROW_WARPS] = s;
+    __syncwarp();
+    named_sync(1, 128);
+    if (vt == 0) house_scalars(cb0[1], (reds[0] + reds[1]) + (reds[2] + reds[3]), hh);
+  }
+  for (int k = 0; k + 2 < n; ++k) {
+    double* cur = (k & 1) ? cb1 : cb0;   // column k of A_k
+    double* prv = (k & 1) ? cb0 : cb1;   // v of column k-1, then column k+1
+    Pub* P = pub + (size_t)(k & 1) * 2 * n;
+    Pub* Rw = P + n;
+    const unsigned int gen = (unsigned int)k + 1u;
+    const int la = (k + 1 - b + nb - 1) / nb;   // first owned row > k
+    if (!vecw) {
+      // pass 2 of column k-1 fused with u_i = (A_k col)_i for the owned rows
+      // i > k, one warp per row
+      const double K2 = 2.0 * Ks;
+      for (int li = la + warp; li < R; li += TRI_ROW_WARPS) {
+        const int i = b + li * nb;
+        double* row = rows + (size_t)li * n;
+        const double ci = (k > 0) ? fma(-K2, prv[i], pw[i]) : 0.0;
+        // two independent chains per lane
+        double acc0 = 0.0, acc1 = 0.0;
+        int j = k + 1 + lane;
+        for (; j + 32 < n; j += 64) {
+          const double ra = fma(-ci, prv[j], row[j]);
+          const double rb = fma(-ci, prv[j + 32], row[j + 32]);
+          row[j] = ra;
+          row[j + 32] = rb;
+          acc0 = fma(ra, cur[j], acc0);
+          acc1 = fma(rb, cur[j + 32], acc1);
+        }
+        if (j < n) {
+          const double ra = fma(-ci, prv[j], row[j]);
+          row[j] = ra;
+          acc0 = fma(ra, cur[j], acc0);
+        }
+        const double acc = warp_allsum(acc0 + acc1);
+        __syncwarp();
+        if (i == k + 1)   // row k+1 of A_k for every CTA (each lane its own entries)
+          for (int jj = k + 1 + lane; jj < n; jj += 32) pub_put(Rw + jj, row[jj], gen);
+        if (lane == 0) {
+          us[li] = acc;
+          rs[li] = row[k + 1];
+        }
+      }
     }
-    if ((n - 1) % nb == b) d[n - 1] = rows[(size_t)((n - 1) / nb) * n + n - 1];
+    __syncthreads();   // reflector of column k and the row products complete
+    {
+      const double al = hh[0], t = hh[1];
+      for (int li = la + tid; li < R; li += TRI_THREADS)
+        pub_put(P + (b + li * nb), t * fma(-al, rs[li], us[li]), gen);
+    }
+    if (b == (k + 1) % nb && vecw) {   // owner of row k+1 keeps the reflector
+      for (int j = k + 1 + vt; j < n; j += 128) A[(size_t)k * n + j] = (j == k + 1) ? hh[2] : cur[j];
+      if (vt == 0) {
+        e[k] = hh[0];
+        tau[k] = hh[1];
+      }
+    }
+    if (ilast < k + 2) break;   // every owned row is finished
+    if (!poll_column(P, Rw, k, n, gen, pw, rk, bar)) s_err = 1;
+    __syncthreads();   // p and row k+1 of A_k are here
+    if (s_err) return;
+    if (vecw) {
+      // column k+1 of A_{k+1}:  A_k[k+1, i] - v_{k+1} w_i - w_{k+1} v_i
+      //   = (A_k[k+1, i] - v0 p_i) + (2 v0 K - p_{k+1}) v_i,
+      // the first part formed while K is being reduced
+      const double v0 = hh[2], hk = hh[3];
+      double q = (vt == 0) ? v0 * pw[k + 1] : 0.0;
+      for (int j = k + 2 + vt; j < n; j += 128) {
+        q = fma(cur[j], pw[j], q);
+        prv[j] = fma(-v0, pw[j], rk[j]);
+      }
+      q = warp_allsum(q);
+      if (lane == 0) redq[warp - TRI_ROW_WARPS] = q;
+      __syncwarp();
+      named_sync(1, 128);
+      const double K = hk * ((redq[0] + redq[1]) + (redq[2] + redq[3]));
+      const double wk1 = fma(-K, v0, pw[k + 1]);
+      const double beta = fma(2.0 * v0, K, -pw[k + 1]);
+      double s = 0.0;
+      for (int i = k + 2 + vt; i < n; i += 128) {
+        const double x = fma(beta, cur[i], prv[i]);
+        prv[i] = x;
+        if (i > k + 2) s = fma(x, x, s);
+      }
+      if (vt == 0) {
+        Ks = K;
+        if (b == (k + 2) % nb) d[k + 1] = fma(-2.0 * v0, wk1, rk[k + 1]);
+      }
+      __syncwarp();
+      named_arrive(2, TRI_THREADS);   // K and column k+1 are ready
+      s = warp_allsum(s);
+      if (lane == 0) reds[warp - TRI_ROW_WARPS] = s;
+      __syncwarp();
+      named_sync(1, 128);
+      if (vt == 0) house_scalars(prv[k + 2], (reds[0] + reds[1]) + (reds[2] + reds[3]), hh);
+    } else {
+      // pass 1 of column k on the owned rows i > k+1: A_ij -= v_i p_j
+      const int lb = (k + 2 - b + nb - 1) / nb;
+      for (int li = lb + warp; li < R; li += TRI_ROW_WARPS) {
+        double* row = rows + (size_t)li * n;
+        const double vi = cur[b + li * nb];
+        for (int j = k + 2 + lane; j < n; j += 32) row[j] = fma(-vi, pw[j], row[j]);
+      }
+      named_sync(2, TRI_THREADS);
+    }
+  }
+  __syncthreads();
+  if (tid == 0 && b == (n - 1) % nb) {
+    // last row: pass 2 of column n-3 on its diagonal, and the last off-diagonal
+    const double* v = (((n - 3) & 1) ? cb1 : cb0);
+    const double* cl = (((n - 2) & 1) ? cb1 : cb0);
+    const double c = fma(-2.0 * Ks, v[n - 1], pw[n - 1]);
+    d[n - 1] = fma(-c, v[n - 1], rows[(size_t)((n - 1) / nb) * n + n - 1]);
+    e[n - 2] = cl[n - 1];
   }
 }
 
@@ -480,28 +630,33 @@ ofm_status ofm_tridiag_persistent(ofm_ctx* c, double* A, int n, double* d, doubl
   if (!coop) return OFM_ERR_INVALID;
   // shared-memory-resident variant when every CTA's rows fit (one CTA per SM)
   {
-    const int nbs = sms;
+    // nbs < n: every CTA owns a row below row 0
+    const int nbs = std::min(sms, n - 1);
     const size_t rmax = (size_t)(n + nbs - 1) / nbs;
     const size_t smem2 = (rmax * n + 4 * (size_t)n) * sizeof(double);
+    const size_t pub_bytes = 4 * (size_t)n * sizeof(Pub);   // p and row k+1, two slots each
     int per_sm2 = 0;
-    if (smem2 <= 200 * 1024 &&
+    if (smem2 <= 200 * 1024 && rmax <= (size_t)TRI_RMAX &&
+        2 * (size_t)n <= (size_t)TRI_PMAX * TRI_THREADS &&
         cudaFuncSetAttribute(tridiag_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem2) == cudaSuccess &&
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, tridiag_smem_kernel, 512, smem2) ==
-            cudaSuccess &&
-        per_sm2 >= 1 && c->w_eval.cap >= 4 * (size_t)n * sizeof(double)) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, tridiag_smem_kernel, TRI_THREADS,
+                                                      smem2) == cudaSuccess &&
+        per_sm2 >= 1 && c->w_eval.cap >= pub_bytes) {
       OFM_TRY(ofm_ensure(c, c->w_bar, sizeof(GridBar), "grid barrier"));
       OFM_CUDA(c, cudaMemsetAsync(c->w_bar.p, 0, sizeof(GridBar), c->stream));
+      // generation 0 in every slot: no column's value yet
+      OFM_CUDA(c, cudaMemsetAsync(c->w_eval.p, 0, pub_bytes, c->stream));
       GridBar* bar = (GridBar*)c->w_bar.p;
-      double* xbuf = (double*)c->w_eval.p;   // p and the published row, two halves each
+      Pub* pub = (Pub*)c->w_eval.p;
       int nn = n;
-      void* args[] = {&A, &nn, &d, &e, &tau, &xbuf, &bar};
-      OFM_CUDA(c, cudaLaunchCooperativeKernel((const void*)tridiag_smem_kernel, dim3(nbs), dim3(512),
-                                              args, smem2, c->stream));
+      void* args[] = {&A, &nn, &d, &e, &tau, &pub, &bar};
+      OFM_CUDA(c, cudaLaunchCooperativeKernel((const void*)tridiag_smem_kernel, dim3(nbs),
+                                              dim3(TRI_THREADS), args, smem2, c->stream));
       GridBar hb{};
       OFM_CUDA(c, cudaMemcpyAsync(&hb, bar, sizeof(GridBar), cudaMemcpyDeviceToHost, c->stream));
       OFM_CUDA(c, cudaStreamSynchronize(c->stream));
-      if (hb.err) return ofm_fail(c, OFM_ERR_TIMEOUT, "tridiagonal reduction: grid barrier wait exceeded its bound");
+      if (hb.err) return ofm_fail(c, OFM_ERR_TIMEOUT, "tridiagonal reduction: a wait for another CTA exceeded its bound");
       return OFM_OK;
     }
     cudaGetLastError();
