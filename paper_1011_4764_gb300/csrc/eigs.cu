@@ -54,6 +54,7 @@ struct EigWork {
   double vlim[2] = {0.0, 0.0};        // max V, min V
   size_t rr_smem = 0, rot_smem = 0;   // dynamic shared memory of the two kernels
   int rot_blocks = 1;
+  bool rot4 = false;                    // FP32 register-tiled rotation
   ApplyGrid fgrid;                    // launch shape of the filter steps
   struct TcPlan* gtc = nullptr;       // Gram on tensor cores (TF32 hi+lo), FP32 storage
   bool ready = false;
@@ -612,6 +613,213 @@ __global__ void __launch_bounds__(256) rotate_kernel(const DevFrag* efr, const T
   }
 }
 
+// The same rotation for FP32 blocks with a larger register tile: a CTA takes
+// tiles of RT4 = 256 points, staged TRANSPOSED in shared memory (one row per
+// column k, the tile's points contiguous), and thread (point group pg,
+// column group jg) accumulates 4 points x RJ columns of both products.  Per
+// k a thread loads its 4 points of Y and of H Y with one 16-byte load each
+// and its RJ coefficients with RJ/2 8-byte loads (warp broadcasts), and
+// issues 8 RJ FMAs: the loop is FMA-bound, not shared-memory-bound.  The
+// residual partial sums stay in registers across the CTA's tiles.
+constexpr int RT4 = 256;   // points per tile (one per thread when staging)
+constexpr int RJB = 4 * RJ;  // columns per column block
+constexpr int RM4 = 52;      // widest block (m) this form takes
+
+__global__ void __launch_bounds__(256, 2) rotate4_kernel(const DevFrag* efr, const float* Y, float* Xo,
+                                                         const float* HY, float* HXo,
+                                                         const double* Cm, long long cstride,
+                                                         const int* rank, const double* theta,
+                                                         const long long* toff, double* partial,
+                                                         int mstride, unsigned long long salt) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ float red[8][RJ];
+  const int f = blockIdx.y;
+  const DevFrag F = efr[f];
+  const int m = F.n;
+  const int mcs = (m + RJB - 1) / RJB * RJB;   // coefficient row stride (zero-padded)
+  const int r = rank[f];
+  const int ex = F.ext[0], ey = F.ext[1];
+  const int P = F.ext[0] * F.ext[1] * F.ext[2];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int pg = tid & 63, jg = tid >> 6;
+  int* pds = reinterpret_cast<int*>(smem_raw);                      // RT4
+  float* Cs = reinterpret_cast<float*>(smem_raw + RT4 * sizeof(int));  // m x mcs
+  float* ys = Cs + (size_t)m * mcs;                                 // m x RT4, transposed
+  float* hs = ys + (size_t)m * RT4;                                 // m x RT4, transposed
+  // coefficients: every load of a thread issued before its stores (one
+  // round trip, not one per element)
+  for (int e0 = 0; e0 < m * mcs; e0 += 8 * 256) {
+    double cv[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * 256 + tid;
+      const int k = e / mcs, j = e - k * mcs;
+      cv[u] = (e < m * mcs && j < m) ? Cm[f * cstride + (long long)k * m + j] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * 256 + tid;
+      if (e < m * mcs) Cs[e] = (float)cv[u];
+    }
+  }
+  const unsigned long long s0 = splitmix64(salt);
+  const float inv_sqrt_p = (float)(1.0 / sqrt((double)P));
+  for (int jb = 0; jb < m; jb += RJB) {
+    const int jn = min(RJB, m - jb);
+    float rsum[RJ];
+#pragma unroll
+    for (int i = 0; i < RJ; ++i) rsum[i] = 0.f;
+    for (int t0 = blockIdx.x * RT4; t0 < P; t0 += gridDim.x * RT4) {
+      __syncthreads();   // previous tile written out (and the coefficients staged)
+      // stage: thread tid takes point t0 + tid, its row in 16-byte pieces
+      int pd = -1;
+      {
+        const int t = t0 + tid;
+        if (t < P) {
+          const int x = t % ex, y = (t / ex) % ey, z = t / (ex * ey);
+          pd = ((z + F.lo[2]) * F.dext[1] + (y + F.lo[1])) * F.dext[0] + x + F.lo[0];
+        }
+        pds[tid] = pd;
+        const long long a = F.off + (long long)max(pd, 0) * F.ld;
+        // the whole row (at most RM4 columns) in flight at once; ld is a
+        // multiple of 4, so every 16-byte piece stays inside the row
+        float4 yv[RM4 / 4], hv[RM4 / 4];
+#pragma unroll
+        for (int u = 0; u < RM4 / 4; ++u) {
+          yv[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+          hv[u] = yv[u];
+          if (pd >= 0 && 4 * u < m) {
+            yv[u] = *reinterpret_cast<const float4*>(Y + a + 4 * u);
+            hv[u] = *reinterpret_cast<const float4*>(HY + a + 4 * u);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < RM4 / 4; ++u) {
+          const int k = 4 * u;
+          if (k < m) {
+            ys[(size_t)k * RT4 + tid] = yv[u].x;
+            hs[(size_t)k * RT4 + tid] = hv[u].x;
+          }
+          if (k + 1 < m) {
+            ys[(size_t)(k + 1) * RT4 + tid] = yv[u].y;
+            hs[(size_t)(k + 1) * RT4 + tid] = hv[u].y;
+          }
+          if (k + 2 < m) {
+            ys[(size_t)(k + 2) * RT4 + tid] = yv[u].z;
+            hs[(size_t)(k + 2) * RT4 + tid] = hv[u].z;
+          }
+          if (k + 3 < m) {
+            ys[(size_t)(k + 3) * RT4 + tid] = yv[u].w;
+            hs[(size_t)(k + 3) * RT4 + tid] = hv[u].w;
+          }
+        }
+      }
+      __syncthreads();
+      float ax[4][RJ], ah[4][RJ];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int i = 0; i < RJ; ++i) {
+          ax[q][i] = 0.f;
+          ah[q][i] = 0.f;
+        }
+      const float* cp = Cs + jb + RJ * jg;
+      for (int k = 0; k < m; ++k) {
+        const float4 y4 = *reinterpret_cast<const float4*>(ys + (size_t)k * RT4 + 4 * pg);
+        const float4 h4 = *reinterpret_cast<const float4*>(hs + (size_t)k * RT4 + 4 * pg);
+        float cc[RJ];
+#pragma unroll
+        for (int i = 0; i < RJ / 2; ++i) {
+          const float2 c2 = *reinterpret_cast<const float2*>(cp + (size_t)k * mcs + 2 * i);
+          cc[2 * i] = c2.x;
+          cc[2 * i + 1] = c2.y;
+        }
+#pragma unroll
+        for (int i = 0; i < RJ; ++i) {
+          ax[0][i] = fmaf(y4.x, cc[i], ax[0][i]);
+          ax[1][i] = fmaf(y4.y, cc[i], ax[1][i]);
+          ax[2][i] = fmaf(y4.z, cc[i], ax[2][i]);
+          ax[3][i] = fmaf(y4.w, cc[i], ax[3][i]);
+          ah[0][i] = fmaf(h4.x, cc[i], ah[0][i]);
+          ah[1][i] = fmaf(h4.y, cc[i], ah[1][i]);
+          ah[2][i] = fmaf(h4.z, cc[i], ah[2][i]);
+          ah[3][i] = fmaf(h4.w, cc[i], ah[3][i]);
+        }
+      }
+      __syncthreads();   // every thread has read the staged tile
+      int pq[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) pq[q] = pds[4 * pg + q];
+#pragma unroll
+      for (int i = 0; i < RJ; ++i) {
+        const int c = RJ * jg + i;
+        if (c >= jn) continue;
+        const int j = jb + c;
+        const float th = (float)theta[toff[f] + j];
+        float xo[4], ho[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          float xv = ax[q][i], hv = ah[q][i];
+          if (j >= r) {   // dropped direction: a fresh random vector, H X left zero
+            hv = 0.f;
+            xv = 0.f;
+            if (pq[q] >= 0) {
+              const unsigned long long key = ((unsigned long long)f << 44) ^
+                                             ((unsigned long long)j << 32) ^ (unsigned long long)pq[q];
+              const unsigned long long rr = splitmix64(key + s0);
+              xv = (float)((double)(rr >> 11) * (2.0 / 9007199254740992.0) - 1.0) * inv_sqrt_p;
+            }
+          }
+          if (pq[q] >= 0) {
+            const float d = hv - th * xv;
+            rsum[i] = fmaf(d, d, rsum[i]);
+          }
+          xo[q] = xv;
+          ho[q] = hv;
+        }
+        *reinterpret_cast<float4*>(ys + (size_t)j * RT4 + 4 * pg) = make_float4(xo[0], xo[1], xo[2], xo[3]);
+        *reinterpret_cast<float4*>(hs + (size_t)j * RT4 + 4 * pg) = make_float4(ho[0], ho[1], ho[2], ho[3]);
+      }
+      __syncthreads();
+      // write the block's columns of point t0 + tid back, 16 bytes at a time
+      if (pd >= 0) {
+        const long long a = F.off + (long long)pd * F.ld;
+        const int je = jb + jn;
+        for (int k = jb; k < je; k += 4) {
+          if (k + 3 < je) {
+            *reinterpret_cast<float4*>(Xo + a + k) =
+                make_float4(ys[(size_t)k * RT4 + tid], ys[(size_t)(k + 1) * RT4 + tid],
+                            ys[(size_t)(k + 2) * RT4 + tid], ys[(size_t)(k + 3) * RT4 + tid]);
+            *reinterpret_cast<float4*>(HXo + a + k) =
+                make_float4(hs[(size_t)k * RT4 + tid], hs[(size_t)(k + 1) * RT4 + tid],
+                            hs[(size_t)(k + 2) * RT4 + tid], hs[(size_t)(k + 3) * RT4 + tid]);
+          } else {
+            for (int kk = k; kk < je; ++kk) {
+              Xo[a + kk] = ys[(size_t)kk * RT4 + tid];
+              HXo[a + kk] = hs[(size_t)kk * RT4 + tid];
+            }
+          }
+        }
+      }
+    }
+    // residual partials of the block's columns: over the 64 point groups of
+    // column group jg (warps 2 jg and 2 jg + 1)
+#pragma unroll
+    for (int i = 0; i < RJ; ++i) {
+      float v = rsum[i];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) red[warp][i] = v;
+    }
+    __syncthreads();
+    if (tid < jn) {
+      const int g = tid / RJ, i = tid - g * RJ;
+      partial[((long long)f * gridDim.x + blockIdx.x) * mstride + jb + tid] =
+          (double)red[2 * g][i] + (double)red[2 * g + 1][i];
+    }
+    __syncthreads();
+  }
+}
+
 __global__ void residual_reduce_kernel(const DevFrag* efr, const double* partial, int nblocks,
                                        int mstride, const long long* toff, double* res) {
   const int f = blockIdx.x;
@@ -819,12 +1027,25 @@ static ofm_status eig_setup(ofm_ctx* c, int guard_opt) {
   OFM_CUDA(c, cudaStreamSynchronize(s));
   long long maxP = 0;
   for (auto& E : w->efr) maxP = std::max<long long>(maxP, (long long)E.ext[0] * E.ext[1] * E.ext[2]);
-  w->rot_blocks = (int)std::min<long long>((maxP + RT - 1) / RT, 64);
+  // FP32 blocks take the 256-point register-tiled rotation when two CTAs fit
+  // on an SM; FP64 blocks and very wide ones the 64-point form
+  {
+    const size_t mcs = (size_t)(w->mmax + RJB - 1) / RJB * RJB;
+    const size_t smem4 = RT4 * sizeof(int) + ((size_t)w->mmax * mcs + 2 * (size_t)w->mmax * RT4) * sizeof(float);
+    w->rot4 = !fp64 && w->mmax <= RM4 && smem4 <= 110 * 1024;
+    if (w->rot4) {
+      w->rot_smem = smem4;
+      w->rot_blocks = (int)std::min<long long>((maxP + RT4 - 1) / RT4, 64);
+    } else {
+      w->rot_smem = 16 * ((RT * sizeof(int) + 15) / 16) +
+                    (4 * RJ + (size_t)w->mmax * w->mmax + 2 * (size_t)RT * (w->mmax + 1)) * es;
+      w->rot_blocks = (int)std::min<long long>((maxP + RT - 1) / RT, 64);
+    }
+  }
   OFM_TRY(ofm_ensure(c, w->rpart, sizeof(double) * (size_t)nf * w->rot_blocks * w->mmax, "residual partials"));
-  w->rot_smem = 16 * ((RT * sizeof(int) + 15) / 16) +
-                (4 * RJ + (size_t)w->mmax * w->mmax + 2 * (size_t)RT * (w->mmax + 1)) * es;
   if (w->rot_smem > 227 * 1024) return ofm_fail(c, OFM_ERR_INVALID, "block size too large for the rotation kernel");
-  if (fp64) OFM_CUDA(c, cudaFuncSetAttribute(rotate_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w->rot_smem));
+  if (w->rot4) OFM_CUDA(c, cudaFuncSetAttribute(rotate4_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w->rot_smem));
+  else if (fp64) OFM_CUDA(c, cudaFuncSetAttribute(rotate_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w->rot_smem));
   else OFM_CUDA(c, cudaFuncSetAttribute(rotate_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w->rot_smem));
   const size_t rr = (3 * (size_t)w->mmax * (w->mmax + 1) + 3 * (size_t)w->mmax) * es;
   w->rr_smem = rr <= 200 * 1024 ? rr : 0;
@@ -875,6 +1096,13 @@ static ofm_status eig_rr(ofm_ctx* c, int y, int hy, int xo, int hxo, unsigned lo
     rotate_kernel<double><<<g, 256, w->rot_smem, s>>>((const DevFrag*)w->d_efr.p, (const double*)w->buf[y].p,
                                                (double*)w->buf[xo].p, (const double*)w->buf[hy].p,
                                                (double*)w->buf[hxo].p, (const double*)w->Cm.p, mm,
+                                               (const int*)w->d_rank.p, (const double*)w->theta.p,
+                                               (const long long*)w->d_toff.p, (double*)w->rpart.p,
+                                               w->mmax, salt);
+  else if (w->rot4)
+    rotate4_kernel<<<g, 256, w->rot_smem, s>>>((const DevFrag*)w->d_efr.p, (const float*)w->buf[y].p,
+                                               (float*)w->buf[xo].p, (const float*)w->buf[hy].p,
+                                               (float*)w->buf[hxo].p, (const double*)w->Cm.p, mm,
                                                (const int*)w->d_rank.p, (const double*)w->theta.p,
                                                (const long long*)w->d_toff.p, (double*)w->rpart.p,
                                                w->mmax, salt);
