@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
+#include <vector>
 
 #include "ofm_internal.h"
 #include "ptx_util.h"
@@ -441,6 +442,194 @@ void launch_apply_filter(const DevFrag* d_fr, int nfrag, const ApplyGrid& g, con
                          const int gn[3], double h, bool fp64, int* flag, cudaStream_t s) {
   if (fp64) zmarch<double, true>(g, nfrag, d_fr, V, in, prev, out, coef, gn, h, flag, s);
   else zmarch<float, true>(g, nfrag, d_fr, V, in, prev, out, coef, gn, h, flag, s);
+}
+
+// ------------------------------------------------ whole filter on chip ----
+//
+// The whole degree-d Chebyshev filter of one fragment and ONE state column
+// in one CTA (FP32 storage, interior box EX x EY x EZ fixed at compile
+// time): the column's box is loaded once, every step runs between registers
+// and shared memory, and the filtered column Y = p(H_f) X and H_f Y leave
+// once.  The stencil acts on each state column independently, so the CTAs
+// of a fragment's columns share nothing.  Against one launch per degree
+// (three blocks through HBM per step) the HBM traffic of a filter drops from
+// ~3 d blocks to ~3 blocks; a step is bound by shared memory (four in-plane
+// neighbour loads and one store per point) and instruction issue.
+//   - two threads own each interior column (x, y), the lower and the upper
+//     half of its z range, and keep their half of the current iterate in
+//     registers; z neighbours come from registers (the two middle and the
+//     wrap-around ones from shared memory), in-plane neighbours from the
+//     shared copy of the current iterate;
+//   - the shared copy is the interior box ([z][y][x], unpadded: the two rows
+//     of 16 points a warp covers are 32 consecutive words, conflict-free) in
+//     two buffers: a step reads one and writes the next iterate over the
+//     previous one in the other (each point is read and rewritten by its own
+//     thread), one barrier per step.  c0 + V of every point sits in a third
+//     area;
+//   - a missing in-plane neighbour (non-periodic edge) reads the point itself
+//     with weight 0 and a periodic one reads the wrapped point, exactly as in
+//     apply_zmarch_kernel's filter mode, whose arithmetic and order are kept:
+//     both forms give the same values.
+template <int EX, int EY, int EZ>
+struct CfBox {
+  static constexpr int NXY = EX * EY;                 // points per plane (unpadded)
+  static constexpr int ZH = EZ / 2, NT = 2 * NXY;     // two threads per z-column
+  // two copies of the iterate, then c0 + V of every interior point
+  static constexpr size_t smem = 3 * (size_t)EZ * NXY * sizeof(float);
+};
+
+// One step for the ZH planes of a thread.  src holds the current iterate
+// (also in cur), dst the previous one; the next iterate replaces the
+// previous one in dst point by point (only this thread reads those points
+// of dst during the step) and replaces cur.  nb[i], w[i]: in-plane
+// neighbour offsets and 0/1 weights (x+1, x-1, y+1, y-1; a missing
+// neighbour reads the point itself with weight 0, as in the HBM form); ob /
+// oa: offsets of the planes just below / above the thread's range (-1:
+// zero there).  With write = false (the final H Y) the result goes to cur
+// only and dst is untouched.
+template <int EX, int EY, int EZ>
+__device__ __forceinline__ void cf_step(const float* __restrict__ src, float* __restrict__ dst,
+                                        int own, int ob, int oa, const int (&nb)[4],
+                                        const float (&w)[4], float (&cur)[CfBox<EX, EY, EZ>::ZH],
+                                        const float* __restrict__ vc, float c1, float al, float be,
+                                        float sh, bool has_prev, bool write) {
+  using B = CfBox<EX, EY, EZ>;
+  float below = ob >= 0 ? src[ob] : 0.f;
+  const float edge_a = oa >= 0 ? src[oa] : 0.f;
+  const float* p0 = src + nb[0];
+  const float* p1 = src + nb[1];
+  const float* p2 = src + nb[2];
+  const float* p3 = src + nb[3];
+  float* d = dst + own;
+#pragma unroll
+  for (int z = 0; z < B::ZH; ++z) {
+    const float above = (z + 1 < B::ZH) ? cur[z + 1] : edge_a;
+    float sum = below + above;
+    sum = fmaf(w[0], p0[z * B::NXY], sum);
+    sum = fmaf(w[1], p1[z * B::NXY], sum);
+    sum = fmaf(w[2], p2[z * B::NXY], sum);
+    sum = fmaf(w[3], p3[z * B::NXY], sum);
+    float h = fmaf(vc[z * B::NXY] - sh, cur[z], 0.f);
+    h = fmaf(-c1, sum, h);
+    float o = fmaf(al, h, 0.f);
+    if (has_prev) o = fmaf(be, d[z * B::NXY], o);
+    below = cur[z];   // the old value is the next point's lower neighbour
+    cur[z] = o;
+    if (write) d[z * B::NXY] = o;
+  }
+}
+
+template <int EX, int EY, int EZ>
+__global__ void __launch_bounds__(2 * EX * EY, 1) cheb_filter_kernel(
+    const DevFrag* __restrict__ fr, const float* __restrict__ V, const float* __restrict__ X,
+    float* __restrict__ Y, float* __restrict__ HY, const double* __restrict__ coef, int nsteps,
+    int nfrag, int gx, int gy, int gz, float c0, float c1) {
+  using B = CfBox<EX, EY, EZ>;
+  constexpr int ZH = B::ZH;
+  extern __shared__ float cf_box[];
+  const int f = blockIdx.y, j = blockIdx.x;
+  const DevFrag F = fr[f];
+  if (j >= F.n) return;   // uniform over the CTA
+  const int t = threadIdx.x;
+  const int c = t % B::NXY, half = t / B::NXY;
+  const int x = c % EX, y = c / EX, z0 = half * ZH;
+  const bool fz = F.full[2] != 0;
+  const int own = z0 * B::NXY + c;
+  const int ob = z0 > 0 ? own - B::NXY : (fz ? (EZ - 1) * B::NXY + c : -1);
+  const int oa = z0 + ZH < EZ ? own + ZH * B::NXY : (fz ? c : -1);
+  // in-plane neighbours within the interior plane (full dimensions wrap)
+  int nb[4];
+  float w[4];
+  {
+    const int xp = x + 1 < EX ? c + 1 : (F.full[0] ? c + 1 - EX : -1);
+    const int xm = x > 0 ? c - 1 : (F.full[0] ? c - 1 + EX : -1);
+    const int yp = y + 1 < EY ? c + EX : (F.full[1] ? c + EX - B::NXY : -1);
+    const int ym = y > 0 ? c - EX : (F.full[1] ? c - EX + B::NXY : -1);
+    const int q[4] = {xp, xm, yp, ym};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      w[i] = q[i] >= 0 ? 1.f : 0.f;
+      nb[i] = (q[i] >= 0 ? q[i] : c) + z0 * B::NXY;
+    }
+  }
+  const long long pstride = (long long)F.dext[0] * F.dext[1];   // storage points per plane
+  const long long p0 =
+      ((long long)(F.lo[2] + z0) * F.dext[1] + (F.lo[1] + y)) * F.dext[0] + F.lo[0] + x;
+  float* vcs = cf_box + 2 * EZ * B::NXY + own;   // c0 + V, plane stride NXY
+  {
+    const float* Vrow = V + (long long)((F.doff[1] + F.lo[1] + y) % gy) * gx + (F.doff[0] + F.lo[0] + x) % gx;
+    const long long vstride = (long long)gx * gy;
+#pragma unroll
+    for (int z = 0; z < ZH; ++z)
+      vcs[z * B::NXY] = c0 + Vrow[(long long)((F.doff[2] + F.lo[2] + z0 + z) % gz) * vstride];
+  }
+  float cur[ZH];
+#pragma unroll
+  for (int z = 0; z < ZH; ++z) cur[z] = X[F.off + (p0 + z * pstride) * F.ld + j];
+#pragma unroll
+  for (int z = 0; z < ZH; ++z) cf_box[own + z * B::NXY] = cur[z];
+  __syncthreads();
+  float* b0 = cf_box;
+  float* b1 = cf_box + EZ * B::NXY;
+  const double* cf = coef + 3 * (size_t)f;
+  float* src = b0;
+  float* dst = b1;
+  for (int k = 0; k < nsteps; ++k) {
+    const double* ca = cf + 3 * (size_t)k * nfrag;
+    cf_step<EX, EY, EZ>(src, dst, own, ob, oa, nb, w, cur, vcs, c1, (float)ca[0], (float)ca[1],
+                        (float)ca[2], k > 0, true);
+    __syncthreads();
+    float* tmp = src;
+    src = dst;
+    dst = tmp;
+  }
+  // cur holds the filtered column Y (also in src); H_f Y (alpha 1, beta 0,
+  // shift 0) goes to the registers of a second pass, Y straight out first
+  if (Y) {
+#pragma unroll
+    for (int z = 0; z < ZH; ++z) Y[F.off + (p0 + z * pstride) * F.ld + j] = cur[z];
+  }
+  cf_step<EX, EY, EZ>(src, dst, own, ob, oa, nb, w, cur, vcs, c1, 1.f, 0.f, 0.f, false, false);
+#pragma unroll
+  for (int z = 0; z < ZH; ++z) HY[F.off + (p0 + z * pstride) * F.ld + j] = cur[z];
+}
+
+// Box shapes with an on-chip filter: every fragment must have this interior
+// shape, and a full dimension must coincide with the storage box.
+static bool cf_shape(const std::vector<DevFrag>& frags, int ex, int ey, int ez) {
+  for (const DevFrag& F : frags) {
+    if (F.ext[0] != ex || F.ext[1] != ey || F.ext[2] != ez) return false;
+    for (int d = 0; d < 3; ++d)
+      if (F.full[d] && (F.ext[d] != F.dext[d] || F.lo[d] != 0)) return false;
+  }
+  return !frags.empty();
+}
+
+// Dynamic shared memory of the on-chip filter for these fragments, or 0 when
+// it does not apply (FP64 storage, or a box shape without a compiled form).
+size_t cheb_filter_smem(const std::vector<DevFrag>& frags, bool fp64) {
+  if (fp64) return 0;
+  if (cf_shape(frags, 16, 32, 32)) return CfBox<16, 32, 32>::smem;
+  return 0;
+}
+
+// One launch per filter: CTA (state j, fragment f) for every j < m_f.  Y may
+// be null (only H X wanted: nsteps = 0).
+void launch_cheb_filter(const DevFrag* d_fr, int nfrag, int mmax, size_t smem, const void* V,
+                        const void* X, void* Y, void* HY, const double* coef, int nsteps,
+                        const int gn[3], double h, cudaStream_t s) {
+  const double c0 = 3.0 / (h * h), c1 = 0.5 / (h * h);
+  if (smem == CfBox<16, 32, 32>::smem) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(cheb_filter_kernel<16, 32, 32>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      attr = true;
+    }
+    cheb_filter_kernel<16, 32, 32><<<dim3(mmax, nfrag), CfBox<16, 32, 32>::NT, smem, s>>>(
+        d_fr, (const float*)V, (const float*)X, (float*)Y, (float*)HY, coef, nsteps, nfrag,
+        gn[0], gn[1], gn[2], (float)c0, (float)c1);
+  }
 }
 
 // ------------------------------------------------------------ conversions --

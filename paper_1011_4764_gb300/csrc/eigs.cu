@@ -55,6 +55,8 @@ struct EigWork {
   size_t rr_smem = 0, rot_smem = 0;   // dynamic shared memory of the two kernels
   int rot_blocks = 1;
   bool rot4 = false;                    // FP32 register-tiled rotation
+  size_t cf_smem = 0;                   // on-chip filter: shared memory per CTA (0: off)
+  double cf_bytes0 = 0, cf_bytes = 0, cf_flops_step = 0;
   ApplyGrid fgrid;                    // launch shape of the filter steps
   struct TcPlan* gtc = nullptr;       // Gram on tensor cores (TF32 hi+lo), FP32 storage
   bool ready = false;
@@ -955,6 +957,17 @@ static ofm_status eig_setup(ofm_ctx* c, int guard_opt) {
   }
   w->total_ctas = (int)ctas;
   w->fgrid = apply_grid(w->efr, fp64, true);
+  // on-chip filter (one launch per filter) where every fragment fits
+  w->cf_smem = cheb_filter_smem(w->efr, fp64);
+  w->cf_bytes0 = w->cf_bytes = w->cf_flops_step = 0.0;
+  for (const DevFrag& E : w->efr) {
+    const double P = (double)E.ext[0] * E.ext[1] * E.ext[2];
+    // HBM: X in (and V), Y and H Y out; flops: 7-point stencil, shift, scale
+    // and the recurrence, ten per point and state per step
+    w->cf_bytes0 += P * (2.0 * E.n + 1.0) * es;
+    w->cf_bytes += P * (3.0 * E.n + 1.0) * es;
+    w->cf_flops_step += 10.0 * P * E.n;
+  }
   w->filter_b2 =w->filter_b3 = w->gram_bytes = w->gram_flops = w->rot_bytes = w->rot_flops = 0;
   for (const DevFrag& E : w->efr) {
     const double P = (double)E.ext[0] * E.ext[1] * E.ext[2];
@@ -1177,7 +1190,13 @@ extern "C" ofm_status ofm_fragment_eigs(ofm_ctx* c, const ofm_eig_opts* opts, do
   OFM_CUDA(c, cudaMemcpyAsync(w->coef.p, coef.data(), sizeof(double) * coef.size(), cudaMemcpyHostToDevice, s));
 
   // initial Rayleigh-Ritz of the random block
-  apply_block(c, 0, -1, 3, d_plain);
+  if (w->cf_smem) {
+    KTimer kt(c, KC_FILTER, 1, w->cf_bytes0, w->cf_flops_step);
+    launch_cheb_filter((const DevFrag*)w->d_efr.p, nf, w->mmax, w->cf_smem, c->V.p, w->buf[0].p,
+                       nullptr, w->buf[3].p, d_coef, 0, c->grid.n, c->grid.h, s);
+  } else {
+    apply_block(c, 0, -1, 3, d_plain);
+  }
   OFM_TRY(eig_rr(c, 0, 3, 1, 2, 0x1234ULL + o.seed));
   int xb = 1;
   std::vector<double> th(w->tsum), rs(w->tsum);
@@ -1258,15 +1277,26 @@ extern "C" ofm_status ofm_fragment_eigs(ofm_ctx* c, const ofm_eig_opts* opts, do
       }
     }
     OFM_CUDA(c, cudaMemcpyAsync(w->coef.p, coef.data(), sizeof(double) * 3 * nf * deg, cudaMemcpyHostToDevice, s));
-    int prev = -1, cur = xb;
-    for (int k = 0; k < deg; ++k) {
-      const int nxt = other(prev, cur);
-      apply_block(c, cur, prev, nxt, d_coef + 3 * (size_t)k * nf);
-      prev = cur;
-      cur = nxt;
+    int cur, hy;
+    if (w->cf_smem) {
+      // the whole filter and H Y in one launch, on chip
+      cur = other(xb, -1);
+      hy = other(xb, cur);
+      KTimer kt(c, KC_FILTER, 1, w->cf_bytes, (deg + 1) * w->cf_flops_step);
+      launch_cheb_filter((const DevFrag*)w->d_efr.p, nf, w->mmax, w->cf_smem, c->V.p, w->buf[xb].p,
+                         w->buf[cur].p, w->buf[hy].p, d_coef, deg, c->grid.n, c->grid.h, s);
+    } else {
+      int prev = -1;
+      cur = xb;
+      for (int k = 0; k < deg; ++k) {
+        const int nxt = other(prev, cur);
+        apply_block(c, cur, prev, nxt, d_coef + 3 * (size_t)k * nf);
+        prev = cur;
+        cur = nxt;
+      }
+      hy = other(cur, -1);
+      apply_block(c, cur, -1, hy, d_plain);
     }
-    const int hy = other(cur, -1);
-    apply_block(c, cur, -1, hy, d_plain);
     const int xo = other(cur, hy);
     const int hxo = other(cur, hy, xo);
     OFM_TRY(eig_rr(c, cur, hy, xo, hxo, 0x9876ULL * (it + 1) + o.seed));

@@ -104,6 +104,10 @@ void launch_import_states(const DevFrag* d_fr, int a, const DevFrag& fa, const d
                           void* states, bool fp64, cudaStream_t s);
 void launch_export_states(const DevFrag& fa, const void* states, double* dst, bool fp64,
                           bool dilated_hphi, cudaStream_t s);
+size_t cheb_filter_smem(const std::vector<DevFrag>& frags, bool fp64);
+void launch_cheb_filter(const DevFrag* d_fr, int nfrag, int mmax, size_t smem, const void* V,
+                        const void* X, void* Y, void* HY, const double* coef, int nsteps,
+                        const int gn[3], double h, cudaStream_t s);
 void launch_apply_filter(const DevFrag* d_fr, int nfrag, const ApplyGrid& g, const void* V,
                          const void* in, const void* prev, void* out, const double* coef,
                          const int gn[3], double h, bool fp64, int* flag, cudaStream_t s);
