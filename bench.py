@@ -57,6 +57,7 @@ def parse_args():
 # 152 * 2 * 2 * 2.07e9 = 1.26e12 flop/s, the recipe's 1.25 TFLOP/s.
 FP64_PEAK_TFLOPS = 1.25
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e-3   # CUDA-core FMA lanes x clock
+SMEM_PEAK_GBS = 152 * 128 * 2.07             # shared-memory bytes per clock per SM x clock
 HBM_CLASSES = {"filter", "apply", "convert", "eig_export", "eig_init", "finalize", "scatter"}
 FP64_CLASSES = {"cholesky", "reduce", "tridiag", "bisect"}
 
@@ -70,6 +71,18 @@ def roofline_for(name, s, pk, precision):
         per = s["bytes"] / max(1, s["launches"])
         r.update(bound="hbm", unit="GB/s", achieved=per / (ms * 1e-3) / 1e9, peak=pk["hbm_gbs"],
                  peak_source=pk["source"] + " copy bandwidth", algorithmic_bytes_per_launch=per)
+        if name == "filter" and s["flops"] > 0:
+            # on-chip form: the HBM bytes are one block in and two out per
+            # filter; each step runs from shared memory (4 in-plane
+            # neighbours, c0 + V and the previous iterate read, the next
+            # iterate written: 28 bytes per point, state and step, which
+            # the 10 flops per point, state and step count)
+            smem = s["flops"] / 10.0 * 28.0 / max(1, s["launches"])
+            r["shared_memory"] = {"bytes_per_launch": smem,
+                                  "achieved_gbs": smem / (ms * 1e-3) / 1e9,
+                                  "peak_gbs": SMEM_PEAK_GBS,
+                                  "frac": smem / (ms * 1e-3) / 1e9 / SMEM_PEAK_GBS,
+                                  "peak_source": "128 B per clock per SM x 152 SMs x max clock"}
     elif name in FP64_CLASSES:
         per = s["flops"] / max(1, s["launches"])
         r.update(bound="alu", unit="TFLOP/s", achieved=per / (ms * 1e-3) / 1e12,

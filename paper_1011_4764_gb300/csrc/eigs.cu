@@ -53,6 +53,7 @@ struct EigWork {
       d_gitems, d_toff, d_rank, d_vmax, rpart;
   double vlim[2] = {0.0, 0.0};        // max V, min V
   size_t rr_smem = 0, rot_smem = 0;   // dynamic shared memory of the two kernels
+  int rr_threads = 256;                 // Rayleigh-Ritz CTA size
   int rot_blocks = 1;
   bool rot4 = false;                    // FP32 register-tiled rotation
   size_t cf_smem = 0;                   // on-chip filter: shared memory per CTA (0: off)
@@ -271,6 +272,11 @@ __device__ void cta_jacobi(T* A, T* V, int n, int lda, int* perm, T* cs, double*
   }
 }
 
+// One warp per rotation pair of a Jacobi round (m/2 pairs), so a round's
+// row and column phases take one pass; at least 256 and at most
+// RR_MAX_THREADS threads (the reduction scratch holds 32 warps' partials).
+constexpr int RR_MAX_THREADS = 640;
+
 // Inputs: blocks of the self pair of fragment f, [K | G] with K = Y^T H Y
 // and G = Y^T Y (m x m each, symmetrised).  Outputs: C (m x m row-major,
 // columns = Ritz vectors in the Y basis, ascending Ritz values; dropped
@@ -279,7 +285,7 @@ __device__ void cta_jacobi(T* A, T* V, int n, int lda, int* perm, T* cs, double*
 // Work matrices A, U, W (row stride ld) and vectors D, sig, idx live in
 // dynamic shared memory (ld = m + 1) or, for large m, in `work` (ld = m).
 template <typename T>
-__global__ void __launch_bounds__(256) rayleigh_ritz_kernel(const DevFrag* efr, const DevPair* gp,
+__global__ void __launch_bounds__(RR_MAX_THREADS) rayleigh_ritz_kernel(const DevFrag* efr, const DevPair* gp,
                                                             const double* blocks, T* work,
                                                             long long wstride, double* Cm,
                                                             long long cstride, double* theta,
@@ -1060,6 +1066,7 @@ static ofm_status eig_setup(ofm_ctx* c, int guard_opt) {
   if (w->rot4) OFM_CUDA(c, cudaFuncSetAttribute(rotate4_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w->rot_smem));
   else if (fp64) OFM_CUDA(c, cudaFuncSetAttribute(rotate_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w->rot_smem));
   else OFM_CUDA(c, cudaFuncSetAttribute(rotate_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w->rot_smem));
+  w->rr_threads = std::min(RR_MAX_THREADS, std::max(256, 32 * ((w->mmax + 1) / 2)));
   const size_t rr = (3 * (size_t)w->mmax * (w->mmax + 1) + 3 * (size_t)w->mmax) * es;
   w->rr_smem = rr <= 200 * 1024 ? rr : 0;
   if (w->rr_smem) {
@@ -1093,12 +1100,12 @@ static ofm_status eig_rr(ofm_ctx* c, int y, int hy, int xo, int hxo, unsigned lo
   const long long mm = (long long)w->mmax * w->mmax;
   { KTimer kt(c, KC_RR);
   if (fp64)
-    rayleigh_ritz_kernel<double><<<nf, 256, w->rr_smem, s>>>(
+    rayleigh_ritz_kernel<double><<<nf, w->rr_threads, w->rr_smem, s>>>(
         (const DevFrag*)w->d_efr.p, (const DevPair*)w->d_gpairs.p, (const double*)w->blocks.p,
         (double*)w->work.p, 3 * mm + 3 * w->mmax + 8, (double*)w->Cm.p, mm, (double*)w->theta.p,
         (const long long*)w->d_toff.p, 1e-13, (int*)w->d_rank.p, w->rr_smem > 0 ? 1 : 0);
   else
-    rayleigh_ritz_kernel<float><<<nf, 256, w->rr_smem, s>>>(
+    rayleigh_ritz_kernel<float><<<nf, w->rr_threads, w->rr_smem, s>>>(
         (const DevFrag*)w->d_efr.p, (const DevPair*)w->d_gpairs.p, (const double*)w->blocks.p,
         (float*)w->work.p, 3 * mm + 3 * w->mmax + 8, (double*)w->Cm.p, mm, (double*)w->theta.p,
         (const long long*)w->d_toff.p, 1e-5, (int*)w->d_rank.p, w->rr_smem > 0 ? 1 : 0);

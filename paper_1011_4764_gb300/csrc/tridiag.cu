@@ -12,10 +12,11 @@
 //    reports a timeout instead of hanging.
 // 2. Eigenvalues by index with multisection: one CTA of one to four warps
 //    per wanted eigenvalue; each thread counts the eigenvalues below one of
-//    32-128 points of the current interval (Sturm sequence of T - x I
-//    written as the three-term recurrence of the leading principal minors,
-//    rescaled by powers of two, so a step needs no division), and the
-//    interval shrinks 33- to 129-fold per round.
+//    32-128 points of the current interval, and the interval shrinks 33- to
+//    129-fold per round.  FP32 counts (LDL^T pivots) narrow it first; FP64
+//    counts (Sturm sequence of T - x I written as the three-term recurrence
+//    of the leading principal minors, rescaled by powers of two, so a step
+//    needs no division) check the bracket and finish.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -536,6 +537,25 @@ __global__ void count_below_kernel(const double* d, const double* e, int n, doub
   }
 }
 
+// Number of eigenvalues of the tridiagonal below x in FP32 (pivots of the
+// LDL^T factorisation of T - x I: q_0 = d_0 - x, q_i = (d_i - x) -
+// e2_{i-1} / q_{i-1}, counted when negative; a pivot below pivmin in
+// magnitude becomes -pivmin).  Only used to narrow a bracket that FP64
+// counts then check, so the fast division is enough.
+__device__ __forceinline__ int sturm_count_f32(const float* __restrict__ d,
+                                               const float* __restrict__ e2, int n, float x,
+                                               float pivmin) {
+  float q = d[0] - x;
+  if (fabsf(q) < pivmin) q = -pivmin;
+  int c = q < 0.f ? 1 : 0;
+  for (int i = 1; i < n; ++i) {
+    q = (d[i] - x) - __fdividef(e2[i - 1], q);
+    if (fabsf(q) < pivmin) q = -pivmin;
+    c += q < 0.f ? 1 : 0;
+  }
+  return c;
+}
+
 // Multisection: one CTA of MS_W warps per wanted eigenvalue index; thread j
 // counts the eigenvalues below the shift x_j = lo + (hi - lo)(j + 1)/(S + 1)
 // (S = 32 MS_W shifts), and the interval shrinks to the (S + 1)-th part
@@ -544,8 +564,14 @@ __global__ void count_below_kernel(const double* d, const double* e, int n, doub
 // instruction about every 19 cycles: up to four warps per SM cost little
 // more time per round than one, beyond that time grows with the warp
 // count.  So few wanted eigenvalues take four warps each (129-section,
-// fewest rounds); many take one (33-section, least work).  d and e^2 are
-// staged in shared memory.
+// fewest rounds); many take one (33-section, least work).
+// Two phases: FP32 counts (fast: FP32 issues every cycle) narrow the
+// Gershgorin interval to about 2e-5 of the spectrum's scale; the bracket,
+// widened by 1e-5 of the scale (far above the FP32 counts' error), is
+// checked by the first FP64 round, whose shifts include both ends, and FP64
+// rounds finish.  A bracket that misses the eigenvalue sends the search back
+// to the Gershgorin interval.  d and e^2 (both precisions) are staged in
+// shared memory.
 template <int MS_W>
 __global__ void __launch_bounds__(32 * MS_W) multisection_kernel(const double* __restrict__ d,
                                                                  const double* __restrict__ e,
@@ -557,6 +583,8 @@ __global__ void __launch_bounds__(32 * MS_W) multisection_kernel(const double* _
   __shared__ double gl[2 * MS_W];
   double* ds = ms_smem;
   double* e2s = ms_smem + n;
+  float* dsf = reinterpret_cast<float*>(ms_smem + 2 * (size_t)n);
+  float* e2f = dsf + n;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int t = blockIdx.x;
   if (t >= m) return;   // uniform over the CTA
@@ -564,8 +592,11 @@ __global__ void __launch_bounds__(32 * MS_W) multisection_kernel(const double* _
   // staged d, e^2 and the Gershgorin interval
   double a = DBL_MAX, b = -DBL_MAX;
   for (int i = tid; i < n; i += blockDim.x) {
+    const double e2 = (i < n - 1) ? e[i] * e[i] : 0.0;
     ds[i] = d[i];
-    e2s[i] = (i < n - 1) ? e[i] * e[i] : 0.0;
+    e2s[i] = e2;
+    dsf[i] = (float)d[i];
+    e2f[i] = (float)e2;
     const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < n - 1 ? fabs(e[i]) : 0.0);
     a = fmin(a, d[i] - r);
     b = fmax(b, d[i] + r);
@@ -584,21 +615,21 @@ __global__ void __launch_bounds__(32 * MS_W) multisection_kernel(const double* _
     b = fmax(b, gl[MS_W + w]);
   }
   const double wdt = fmax(fabs(a), fabs(b));
-  double lo = a - 2.0 * DBL_EPSILON * wdt - DBL_MIN;
-  double hi = b + 2.0 * DBL_EPSILON * wdt + DBL_MIN;
-  for (int it = 0; it < 64; ++it) {
-    if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + 4.0 * DBL_MIN) break;
-    double x[1];
-    int cnt[1];
-    x[0] = lo + (hi - lo) * (double)(tid + 1) / (MS_S + 1);
-    sturm_counts<1>(ds, e2s, n, x, cnt);
-    const unsigned ball = __ballot_sync(0xffffffffu, cnt[0] > idx);
+  const double lo0 = a - 2.0 * DBL_EPSILON * wdt - DBL_MIN;
+  const double hi0 = b + 2.0 * DBL_EPSILON * wdt + DBL_MIN;
+  double lo = lo0, hi = hi0;
+  // index (0..S) of the first shift with more than idx eigenvalues below
+  auto first_above = [&](int cnt) -> int {
+    const unsigned ball = __ballot_sync(0xffffffffu, cnt > idx);
     if (lane == 0) firstw[warp] = ball ? __ffs(ball) - 1 : 32;
     __syncthreads();
-    int j = MS_S;   // first shift with more than idx eigenvalues below
+    int j = MS_S;
     for (int w = MS_W - 1; w >= 0; --w)
       if (firstw[w] < 32) j = w * 32 + firstw[w];
     __syncthreads();   // firstw is rewritten next round
+    return j;
+  };
+  auto shrink = [&](int j) -> bool {   // false: no progress at this precision
     double nlo, nhi;
     if (j == MS_S) {   // above every shift
       nlo = lo + (hi - lo) * (double)MS_S / (MS_S + 1);
@@ -607,9 +638,48 @@ __global__ void __launch_bounds__(32 * MS_W) multisection_kernel(const double* _
       nhi = lo + (hi - lo) * (double)(j + 1) / (MS_S + 1);
       nlo = (j > 0) ? lo + (hi - lo) * (double)j / (MS_S + 1) : lo;
     }
-    if (nhi == hi && nlo == lo) break;   // no progress at this precision
+    if (nhi == hi && nlo == lo) return false;
     lo = nlo;
     hi = nhi;
+    return true;
+  };
+  // phase 1: FP32 counts
+  const float pivmin = 1e-30f;
+  bool narrowed = false;
+  if (wdt > 0.0 && wdt < 1e30) {
+    for (int it = 0; it < 32; ++it) {
+      if (hi - lo <= 2e-5 * wdt) break;
+      const double x = lo + (hi - lo) * (double)(tid + 1) / (MS_S + 1);
+      if (!shrink(first_above(sturm_count_f32(dsf, e2f, n, (float)x, pivmin)))) break;
+      narrowed = true;
+    }
+  }
+  if (narrowed) {
+    // widen, then one FP64 round whose shifts include both ends
+    lo = fmax(lo - 1e-5 * wdt, lo0);
+    hi = fmin(hi + 1e-5 * wdt, hi0);
+    const double x = (tid == MS_S - 1) ? hi : lo + (hi - lo) * (double)tid / (MS_S - 1);
+    double xs[1] = {x};
+    int cnt[1];
+    sturm_counts<1>(ds, e2s, n, xs, cnt);
+    const int j = first_above(cnt[0]);
+    if (j == 0 || j == MS_S) {   // the eigenvalue is outside: start over
+      lo = lo0;
+      hi = hi0;
+    } else {
+      const double xj = (j == MS_S - 1) ? hi : lo + (hi - lo) * (double)j / (MS_S - 1);
+      lo = lo + (hi - lo) * (double)(j - 1) / (MS_S - 1);
+      hi = xj;
+    }
+  }
+  // phase 2: FP64 counts to full precision
+  for (int it = 0; it < 64; ++it) {
+    if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + 4.0 * DBL_MIN) break;
+    double x[1];
+    int cnt[1];
+    x[0] = lo + (hi - lo) * (double)(tid + 1) / (MS_S + 1);
+    sturm_counts<1>(ds, e2s, n, x, cnt);
+    if (!shrink(first_above(cnt[0]))) break;
   }
   if (tid == 0) out[t] = 0.5 * (lo + hi);
 }
@@ -696,7 +766,8 @@ void launch_count_below(const double* d, const double* e, int n, double x0, doub
 // (the caller then bisects from global memory).
 bool launch_multisection(const double* d, const double* e, int n, int i_lo, int m, double* out,
                          cudaStream_t s) {
-  const size_t smem = 2 * (size_t)n * sizeof(double);
+  // d and e^2 in FP64 and in FP32
+  const size_t smem = 2 * (size_t)n * (sizeof(double) + sizeof(float));
   if (smem > 200 * 1024) return false;
   static bool attr_set = false;
   if (!attr_set) {
