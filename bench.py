@@ -284,12 +284,15 @@ def run_ours(args):
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     def window_of(c):
+        # A window that starts AT an eigenvalue includes it: its computed
+        # value may round a few ulps above the exact one, so the lower end
+        # passed to the count sits 1e-9 Ha below it
         if rule.kind == "above_gap":
-            lo = float(c.eigs_by_index(rule.n_occ, rule.n_occ + 1)[0])
-            hi = lo + rule.width
+            e0 = float(c.eigs_by_index(rule.n_occ, rule.n_occ + 1)[0])
+            lo, hi = e0 - 1e-9, e0 + rule.width
         elif rule.kind == "from_lowest":
-            lo = float(c.eigs_by_index(0, 1)[0])
-            hi = lo + rule.width
+            e0 = float(c.eigs_by_index(0, 1)[0])
+            lo, hi = e0 - 1e-9, e0 + rule.width
         else:
             e = c.eigs_by_index(rule.n_occ - 1, rule.n_occ + 1)
             lo, hi = float(e[0]) - rule.width, float(e[1]) + rule.width

@@ -26,40 +26,54 @@ constexpr int NB = 32;
 // ---------------------------------------------------------------- Cholesky --
 
 // Factor the kb x kb diagonal block at (k0, k0) in place (lower triangle).
-// The pivot's reciprocal square root is formed once per column (one call;
-// L_jj = piv / sqrt(piv)), so the column is scaled by a multiplication (FP64
-// division and square root are long instruction sequences on a part with
-// few FP64 units).
+// Column j of the working copy stays unscaled; its pivot's reciprocal square
+// root r_j and r_j^2 are formed by ONE thread (an FP64 square root and a
+// division are long instruction sequences on a part with few FP64 units):
+// the thread that applies column j's update to the next pivot forms the
+// next r right away, while the other rows finish their updates, so each
+// column costs one barrier and no serial scalar step of its own.  The
+// update is a_yx -= a_yj (a_xj r_j^2); the scaling L_yj = a_yj r_j is applied
+// on the way out (L_jj = piv r_j).
 __global__ void potrf_diag_kernel(double* W, int n, int k0, int kb, int* fail_col) {
   __shared__ double a[NB][NB + 1];
-  __shared__ double rinv;
+  __shared__ double rinv[NB], r2[NB];
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 32
   if (tx < kb && ty < kb) a[ty][tx] = W[(long long)(k0 + ty) * n + k0 + tx];
   __syncthreads();
+  // r of the pivot at (j, j), which no later update of this block touches
+  auto pivot = [&](int j) {
+    double piv = a[j][j];
+    if (!(piv > 0.0)) {
+      atomicCAS(fail_col, -1, k0 + j);
+      piv = 1.0;  // keep going with finite numbers; the call reports failure
+      a[j][j] = 1.0;
+    }
+    const double r = rsqrt(piv);
+    rinv[j] = r;
+    r2[j] = r * r;
+  };
+  if (tx == 0 && ty == 0) pivot(0);
+  __syncthreads();
   for (int j = 0; j < kb; ++j) {
-    if (tx == 0 && ty == 0) {
-      double piv = a[j][j];
-      if (!(piv > 0.0)) {
-        atomicCAS(fail_col, -1, k0 + j);
-        piv = 1.0;  // keep going with finite numbers; the call reports failure
-      }
-      const double ri = rsqrt(piv);   // one call instead of a square root and a division
-      a[j][j] = piv * ri;
-      rinv = ri;
+    if (ty > j && ty < kb && tx > j && tx <= ty) {
+      a[ty][tx] = fma(-a[ty][j], a[tx][j] * r2[j], a[ty][tx]);
+      if (tx == j + 1 && ty == j + 1) pivot(j + 1);
     }
     __syncthreads();
-    if (tx == 0 && ty > j && ty < kb) a[ty][j] *= rinv;
-    __syncthreads();
-    if (ty > j && ty < kb && tx > j && tx <= ty) a[ty][tx] -= a[ty][j] * a[tx][j];
-    __syncthreads();
   }
-  if (tx < kb && ty < kb && tx <= ty) W[(long long)(k0 + ty) * n + k0 + tx] = a[ty][tx];
+  if (tx < kb && ty < kb && tx <= ty) W[(long long)(k0 + ty) * n + k0 + tx] = a[ty][tx] * rinv[tx];
 }
 
-// Rows i >= k0+kb of the panel: L21 = W21 L11^-T (forward substitution per row).
-__global__ void trsm_panel_kernel(double* W, int n, int k0, int kb) {
+// Rows i >= k0+kb of the panel: L21 = W21 L11^-T (forward substitution per
+// row).  Four lanes share a row (lane = 4 row + phase), each summing every
+// fourth term of x_j = (w_j - sum_{t<j} x_t L_jt) / L_jj, combined by two
+// shuffle levels: one warp issues an FP64 instruction every 64 cycles at
+// best, so a row's ~kb^2/2 products are split four ways rather than chained
+// in one lane.  8 rows per warp, 4 warps per CTA.
+__global__ void __launch_bounds__(128) trsm_panel_kernel(double* W, int n, int k0, int kb) {
   __shared__ double l[NB][NB + 1];
   __shared__ double dinv[NB];
+  __shared__ double xs[32][NB + 1];   // solved entries of the CTA's 32 rows
   for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
     int r = e / NB, cc = e % NB;
     l[r][cc] = (r < kb && cc <= r) ? W[(long long)(k0 + r) * n + k0 + cc] : 0.0;
@@ -67,21 +81,22 @@ __global__ void trsm_panel_kernel(double* W, int n, int k0, int kb) {
   __syncthreads();
   for (int j = threadIdx.x; j < kb; j += blockDim.x) dinv[j] = 1.0 / l[j][j];
   __syncthreads();
-  const int i = k0 + kb + blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  double x[NB];
-  double* row = W + (long long)i * n + k0;
-#pragma unroll
-  for (int j = 0; j < NB; ++j) {
-    if (j < kb) {
-      double s = row[j];
-      for (int t = 0; t < j; ++t) s -= x[t] * l[j][t];
-      x[j] = s * dinv[j];
-    }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int rl = warp * 8 + (lane >> 2), ph = lane & 3;   // row within the CTA, phase
+  const int i = k0 + kb + blockIdx.x * 32 + rl;
+  const bool live = i < n;
+  double* row = W + (long long)(live ? i : k0) * n + k0;
+  double* x = xs[rl];
+  for (int j = 0; j < kb; ++j) {
+    double s = 0.0;
+    for (int t = ph; t < j; t += 4) s = fma(x[t], l[j][t], s);
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    s += __shfl_xor_sync(0xffffffffu, s, 2);
+    if (ph == 0) x[j] = live ? (row[j] - s) * dinv[j] : 0.0;
+    __syncwarp();
   }
-#pragma unroll
-  for (int j = 0; j < NB; ++j)
-    if (j < kb) row[j] = x[j];
+  if (live)
+    for (int j = ph; j < kb; j += 4) row[j] = x[j];
 }
 
 // Trailing update of the lower triangle: W22 -= L21 L21^T (32x32 tiles).
@@ -419,7 +434,7 @@ ofm_status ofm_window_factor(ofm_ctx* c) {
     potrf_diag_kernel<<<1, dim3(32, 32), 0, s>>>(L, n, k0, kb, flag);
     const int rows = n - k0 - kb;
     if (rows > 0) {
-      trsm_panel_kernel<<<(rows + 31) / 32, 32, 0, s>>>(L, n, k0, kb);
+      trsm_panel_kernel<<<(rows + 31) / 32, 128, 0, s>>>(L, n, k0, kb);
       const int tb = (rows + NB - 1) / NB;
       syrk_update_kernel<<<dim3(tb, tb), dim3(32, 32), 0, s>>>(L, n, k0, kb);
       kt.add(2);
