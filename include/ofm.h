@@ -153,6 +153,23 @@ ofm_status ofm_get_fragment_states(ofm_ctx* ctx, int a, double* phi_out, ofm_loc
  * storage.  Enqueued on the context stream; does not synchronise. */
 ofm_status ofm_assemble_HS(ofm_ctx* ctx, ofm_precision prec, const ofm_assemble_opts* opts);
 
+/* Distance cutoff on the pair list (Sec. III.C, "Choice of the distance
+ * cutoff": a pair of fragments is included when the minimal distance between
+ * an atom of one and an atom of the other is below d_cut).  The atoms of
+ * fragment a are atom_xyz[3*i .. 3*i+2] for frag_atom_off[a] <= i <
+ * frag_atom_off[a+1] (host arrays: n_frag + 1 non-decreasing offsets from 0;
+ * positions in bohr, in the periodic box of n[d] * h; distances are minimum
+ * image).  A pair (a, b), a != b, whose boxes meet is kept when that
+ * distance is below d_cut; a self pair is always kept; a fragment without
+ * atoms keeps only its self pair.  Dropped pairs give zero blocks (in
+ * ofm_get_block and in the dense pencil).  atom_xyz == NULL or d_cut <= 0
+ * restores the geometric pair list.  Needs ofm_build_fragments first; the
+ * arrays are read during the call only.  Re-plans the contraction and
+ * discards any assembled blocks; synchronises the context stream.
+ * OFM_ERR_INVALID: bad offsets; OFM_ERR_STATE: no fragments built. */
+ofm_status ofm_set_pair_cutoff(ofm_ctx* ctx, const double* atom_xyz, const int* frag_atom_off,
+                               double d_cut);
+
 /* The pair list: *n_pairs always; pair_ab (2*n_pairs ints, a then b, a<=b,
  * sorted by a then b) when not NULL. */
 ofm_status ofm_get_pairs(ofm_ctx* ctx, int* n_pairs, int* pair_ab);

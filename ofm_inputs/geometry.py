@@ -79,6 +79,26 @@ class Workload:
     def basis_size(self) -> int:
         return int(sum(f.n_states for f in self.frags))
 
+    def fragment_atoms(self) -> list:
+        """The atoms of each fragment: the centres (bohr) of the wells that
+        lie inside its box (periodic), one (k, 3) array per fragment.  This
+        is what the distance cutoff between fragments is measured on."""
+        return fragment_atoms(self.grid, self.frags, self.wells)
+
+
+def fragment_atoms(grid: Grid, frags, wells) -> list:
+    """Well centres inside each periodic box off + [0, ext) (grid points of
+    spacing h), as one (k, 3) array per box."""
+    xyz = np.asarray(wells, dtype=np.float64).reshape(-1, 5)[:, :3] if len(wells) else np.zeros((0, 3))
+    out = []
+    for f in frags:
+        inside = np.ones(len(xyz), dtype=bool)
+        for d in range(3):
+            u = np.mod(xyz[:, d] / grid.h - f.off[d], grid.n[d])
+            inside &= u < f.ext[d]
+        out.append(xyz[inside].copy())
+    return out
+
 
 def gaussian_potential(grid: Grid, wells: np.ndarray,
                        cutoff: float = WELL_CUTOFF_WIDTHS) -> np.ndarray:

@@ -188,6 +188,30 @@ def pair_list(grid, frags):
     return out
 
 
+def fragment_distance(grid, atoms_a, atoms_b):
+    """Sec. III.C: the distance between two fragments is the minimal distance
+    between an atom of one and an atom of the other (minimum image in the
+    periodic box of n[d] * h bohr).  Infinite when either has no atoms."""
+    L = [grid.n[d] * grid.h for d in range(3)]
+    best = math.inf
+    for ra in np.asarray(atoms_a, dtype=np.float64).reshape(-1, 3):
+        for rb in np.asarray(atoms_b, dtype=np.float64).reshape(-1, 3):
+            s = 0.0
+            for d in range(3):
+                x = ra[d] - rb[d]
+                x -= L[d] * round(x / L[d])
+                s += x * x
+            best = min(best, math.sqrt(s))
+    return best
+
+
+def cutoff_pairs(grid, frags, atoms, d_cut):
+    """Sec. III.C: the pair list restricted to fragments closer than d_cut
+    (self pairs always kept); atoms[a] holds fragment a's atom positions."""
+    return [(a, b) for (a, b) in pair_list(grid, frags)
+            if a == b or fragment_distance(grid, atoms[a], atoms[b]) < d_cut]
+
+
 def overlap_points(grid, offa, exta, offb, extb):
     """Number of grid points shared by two periodic boxes."""
     cnt = 1

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -195,6 +196,16 @@ static ofm_status plan_contraction(ofm_ctx* c) {
   return ofm_plan_extra(c);
 }
 
+// Overlap counts and flops of the current pair list.
+static void pair_totals(ofm_ctx* c) {
+  c->flops = c->ks = c->kh = 0;
+  for (auto& p : c->pairs) {
+    c->ks += p.ks;
+    c->kh += p.kh;
+    c->flops += 2LL * c->frags[p.a].n * c->frags[p.b].n * (p.ks + p.kh);
+  }
+}
+
 extern "C" ofm_status ofm_build_fragments(ofm_ctx* c, const ofm_grid* grid, const double* V,
                                           ofm_location v_loc, const ofm_fragment* frags,
                                           int n_frag, ofm_storage storage) {
@@ -220,12 +231,7 @@ extern "C" ofm_status ofm_build_fragments(ofm_ctx* c, const ofm_grid* grid, cons
     c->basis += f.n;
     c->apply_points += f.Pd * f.n;
   }
-  c->flops = c->ks = c->kh = 0;
-  for (auto& p : c->pairs) {
-    c->ks += p.ks;
-    c->kh += p.kh;
-    c->flops += 2LL * c->frags[p.a].n * c->frags[p.b].n * (p.ks + p.kh);
-  }
+  pair_totals(c);
   c->frag_set.assign(n_frag, 0);
 
   const size_t es = elem_size(c);
@@ -268,6 +274,50 @@ extern "C" ofm_status ofm_build_fragments(ofm_ctx* c, const ofm_grid* grid, cons
   OFM_TRY(sync(c, "build_fragments"));
   c->built = true;
   return OFM_OK;
+}
+
+// Sec. III.C: pairs whose fragments' atoms are all at least d_cut apart are
+// left out.  The geometric list (boxes that meet) is made again and
+// filtered; self pairs stay.
+extern "C" ofm_status ofm_set_pair_cutoff(ofm_ctx* c, const double* atom_xyz,
+                                          const int* frag_atom_off, double d_cut) {
+  if (!c) return OFM_ERR_INVALID;
+  if (!c->built) return ofm_fail(c, OFM_ERR_STATE, "ofm_build_fragments must come first");
+  const bool cut = atom_xyz != nullptr && d_cut > 0.0;
+  if (cut) {
+    if (!frag_atom_off || frag_atom_off[0] != 0)
+      return ofm_fail(c, OFM_ERR_INVALID, "frag_atom_off must start at 0");
+    for (int a = 0; a < c->nfrag; ++a)
+      if (frag_atom_off[a + 1] < frag_atom_off[a])
+        return ofm_fail(c, OFM_ERR_INVALID, "frag_atom_off must not decrease");
+  }
+  make_pairs(c->grid, c->frags, c->pairs);
+  if (cut) {
+    double L[3];
+    for (int d = 0; d < 3; ++d) L[d] = c->grid.n[d] * c->grid.h;
+    const double dc2 = d_cut * d_cut;
+    auto near = [&](int a, int b) {
+      for (int i = frag_atom_off[a]; i < frag_atom_off[a + 1]; ++i)
+        for (int j = frag_atom_off[b]; j < frag_atom_off[b + 1]; ++j) {
+          double r2 = 0.0;
+          for (int d = 0; d < 3; ++d) {
+            double x = atom_xyz[3 * i + d] - atom_xyz[3 * j + d];
+            x -= L[d] * std::nearbyint(x / L[d]);   // minimum image
+            r2 += x * x;
+          }
+          if (r2 < dc2) return true;
+        }
+      return false;
+    };
+    std::vector<HostPair> kept;
+    for (auto& p : c->pairs)
+      if (p.a == p.b || near(p.a, p.b)) kept.push_back(std::move(p));
+    c->pairs.swap(kept);
+  }
+  pair_totals(c);
+  c->assembled = c->dense_ready = c->factored = false;
+  OFM_TRY(plan_contraction(c));
+  return sync(c, "set_pair_cutoff");
 }
 
 // ------------------------------------------------------------- states ------

@@ -28,7 +28,7 @@ EXPORTS = [
     "ofm_assemble_HS", "ofm_get_pairs", "ofm_get_plan_info", "ofm_get_block",
     "ofm_get_dense_HS", "ofm_get_hphi", "ofm_window_eigs", "ofm_eigs_by_index",
     "ofm_set_dense_HS", "ofm_plan_pairs", "ofm_set_profiling", "ofm_get_kernel_stats",
-    "ofm_pair_blocks_noalloc",
+    "ofm_pair_blocks_noalloc", "ofm_set_pair_cutoff",
 ]
 
 
@@ -100,6 +100,7 @@ def load_library(path: str = LIB_PATH):
         "ofm_pair_blocks_noalloc": ([C.POINTER(ofm_grid), C.POINTER(ofm_fragment),
                                      C.POINTER(ofm_fragment), P, P, P, P, P], I),
         "ofm_get_kernel_stats": ([P, C.POINTER(ofm_kernel_stat), I, IP], I),
+        "ofm_set_pair_cutoff": ([P, DP, IP, D], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -262,6 +263,23 @@ class Context:
     def assemble(self, precision="fp32", chunk_points=0, use_graph=True):
         o = ofm_assemble_opts(chunk_points, 1 if use_graph else 0)
         self._check(self.lib.ofm_assemble_HS(self.h, PREC[precision], C.byref(o)))
+
+    # -- ofm_set_pair_cutoff
+    def set_pair_cutoff(self, atoms, d_cut):
+        """atoms: one (k_a, 3) array of positions (bohr) per fragment, or
+        None (with any d_cut) to restore the geometric pair list."""
+        if atoms is None or d_cut is None or d_cut <= 0:
+            self._check(self.lib.ofm_set_pair_cutoff(self.h, None, None, 0.0))
+            return
+        if len(atoms) != len(self.frags):
+            raise ValueError("one atom array per fragment")
+        xyz = np.ascontiguousarray(np.concatenate(
+            [np.asarray(a, dtype=np.float64).reshape(-1, 3) for a in atoms]), dtype=np.float64)
+        off = np.zeros(len(atoms) + 1, dtype=np.int32)
+        off[1:] = np.cumsum([np.asarray(a).reshape(-1, 3).shape[0] for a in atoms])
+        if xyz.size == 0:
+            xyz = np.zeros(3)
+        self._check(self.lib.ofm_set_pair_cutoff(self.h, _dptr(xyz), _iptr(off), float(d_cut)))
 
     def pairs(self):
         n = C.c_int()

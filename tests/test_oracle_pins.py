@@ -404,3 +404,48 @@ def test_tiny_workload_matches_stored_oracle_output(repo_root):
     # variational bound on the stored numbers themselves
     assert np.all(np.array(g["ofm_spectrum"]) >= np.array(g["exact_lowest"]) - 1e-10)
     assert g["S_min_eig"] > 0
+
+
+# ------------------------------------------------ Sec. III.C distance cutoff --
+
+def test_fragment_distance_minimum_image_and_empty():
+    """Two atoms 0.3 bohr apart across the periodic edge of a 5 bohr box (not
+    4.7 apart), the smallest pair wins, and a fragment without atoms is
+    infinitely far from every other."""
+    grid = Grid((10, 10, 10), 0.5)
+    a = np.array([[0.2, 1.0, 1.0], [2.5, 2.5, 2.5]])
+    b = np.array([[4.9, 1.0, 1.0]])
+    assert abs(O.fragment_distance(grid, a, b) - 0.3) < 1e-12
+    c = np.array([[2.5, 2.5, 4.5]])              # 2.0 from a[1] along z
+    assert abs(O.fragment_distance(grid, a, c) - 2.0) < 1e-12
+    assert O.fragment_distance(grid, a, np.zeros((0, 3))) == math.inf
+
+
+def test_cutoff_pairs_limits():
+    """A cutoff above every distance keeps the geometric list; one below
+    every distance keeps the self pairs only; in between, exactly the pairs
+    closer than the cutoff stay (a ring of four boxes, fragment 2's atom
+    moved so that its two neighbours sit 3.5 and 2.5 bohr away)."""
+    grid = Grid((24, 8, 8), 0.5)
+    frags = [Fragment((6 * a, 0, 0), (8, 8, 8), 2) for a in range(4)]
+    atoms = [np.array([[(6 * a + 4) * 0.5, 2.0, 2.0]]) for a in range(4)]   # 3 bohr apart
+    atoms[2] = atoms[2] + np.array([[0.5, 0.0, 0.0]])
+    full = O.pair_list(grid, frags)
+    assert full == [(0, 0), (0, 1), (0, 3), (1, 1), (1, 2), (2, 2), (2, 3), (3, 3)]
+    assert O.cutoff_pairs(grid, frags, atoms, 1e9) == full
+    assert O.cutoff_pairs(grid, frags, atoms, 2.0) == [(a, a) for a in range(4)]
+    assert O.cutoff_pairs(grid, frags, atoms, 3.2) == [(0, 0), (0, 1), (0, 3), (1, 1), (2, 2),
+                                                       (2, 3), (3, 3)]
+
+
+def test_self_pairs_only_give_the_fragment_spectra():
+    """With exact fragment eigenstates S_aa = I and H_aa = diag(eps_a), so a
+    pencil assembled from the self pairs alone has exactly the union of the
+    fragment energies as its spectrum."""
+    wl = make_workload("tiny")
+    H = O.hamiltonian(wl.grid, wl.V)
+    eps, Phis = zip(*[O.fragment_eigs(H, wl.grid, f) for f in wl.frags])
+    selfs = [(a, a) for a in range(len(wl.frags))]
+    Hd, Sd = O.assemble_dense(wl.frags, O.pair_blocks(H, wl.grid, wl.frags, list(Phis), selfs))
+    E = O.generalized_eigs(Hd, Sd)
+    assert np.max(np.abs(E - np.sort(np.concatenate(eps)))) < 1e-10
