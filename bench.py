@@ -533,6 +533,43 @@ def extras(args, ctx, ofm, wl, V_host, step, window_of, stream, storage, F, dev,
         ex["pair_cutoff"] = {"full_pairs": len(ctx.pairs()), "window_n": m, "study": study}
     except Exception as e:
         ex["pair_cutoff"] = {"error": str(e)}
+    # Sec. III basis of fragment HOMOs: the n highest occupied states of every
+    # fragment (occupied = one level per well inside the box), the
+    # occupation rule's HOMO / LUMO against the full basis' levels N_occ-1
+    # and N_occ, and the device time of the smaller assembly and solve
+    try:
+        atoms = wl.fragment_atoms()
+        n_occ = wl.window.n_occ
+        if n_occ > 0 and all(len(a) >= 1 for a in atoms):
+            ctx.assemble(args.precision)   # the cutoff study left the pencil unassembled
+            eh, el = (float(x) for x in ctx.eigs_by_index(n_occ - 1, n_occ + 1))
+            host = [ctx.get_fragment_states(a) for a in range(len(wl.frags))]
+            rows = []
+            for n_homo in (5, 2):
+                first = [len(a) - n_homo for a in atoms]
+                if min(first) < 0:
+                    continue
+                hc = ofm.Context(stream)
+                hc.build_fragments(wl.grid, V_host, wl.frags, storage=storage)
+                for a, P in enumerate(host):
+                    hc.set_fragment_states(a, P)
+                hc.select_states(first, n_homo)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                hc.assemble(args.precision)
+                e_ref, h, l, occ = hc.homo_lumo_gap(0.5 * (el - eh))
+                e1.record(stream)
+                e1.synchronize()
+                rows.append({"homos_per_fragment": n_homo, "basis": n_homo * len(wl.frags),
+                             "e_ref_ha": e_ref, "E_homo_ha": h, "E_lumo_ha": l, "n_occ": occ,
+                             "E_homo_minus_full_ha": h - eh, "E_lumo_minus_full_ha": l - el,
+                             "assemble_and_rule_ms": e0.elapsed_time(e1)})
+                hc.close()
+            ex["homo_basis"] = {"full_basis": nb, "full_E_homo_ha": eh, "full_E_lumo_ha": el,
+                                "gap_min_ha": 0.5 * (el - eh), "rows": rows}
+    except Exception as e:
+        ex["homo_basis"] = {"error": str(e)}
     return ex
 
 

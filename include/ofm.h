@@ -170,6 +170,35 @@ ofm_status ofm_assemble_HS(ofm_ctx* ctx, ofm_precision prec, const ofm_assemble_
 ofm_status ofm_set_pair_cutoff(ofm_ctx* ctx, const double* atom_xyz, const int* frag_atom_off,
                                double d_cut);
 
+/* Basis selection (Sec. III, "Choice of the number of basis states per
+ * fragment": e.g. only the n highest occupied states of every fragment, its
+ * HOMOs): keep states first[a] .. first[a] + count[a] - 1 (0-based, in the
+ * ascending order of the stored states) of every fragment a as its basis.
+ * The selected columns are copied on the device; the fragment table, the
+ * pair plans and the state and H phi storage are laid out again for the new
+ * state counts; the geometry, V and a distance cutoff stay.  Needs every
+ * fragment's states (ofm_fragment_eigs or ofm_set_fragment_states); first
+ * and count are host arrays of n_frag ints, read during the call only.
+ * Discards assembled blocks and the eigensolver's workspace (a later
+ * ofm_fragment_eigs computes count[a] states).  Synchronises the context
+ * stream.  OFM_ERR_INVALID: a range outside a fragment's states, NULL
+ * arrays; OFM_ERR_STATE: states not set. */
+ofm_status ofm_select_states(ofm_ctx* ctx, const int* first, const int* count);
+
+/* Occupation with a HOMO basis (Sec. III, end of "Choice of the number of
+ * basis states per fragment"): e_a = <HOMO_a|H|HOMO_a> with the whole-system
+ * H for every fragment (the last diagonal entry of the assembled H_aa, i.e.
+ * of the fragment's highest basis state), e_ref = max_a e_a, then the first
+ * spacing wider than gap_min (Ha) between consecutive eigenvalues of Eq. 2,
+ * scanning upward from the largest eigenvalue <= e_ref.  Outputs: *e_ref
+ * (may be NULL), the eigenvalues *E_homo < *E_lumo bounding that spacing and
+ * *n_occ, the number of eigenvalues <= *E_homo (the occupied states).  Needs
+ * ofm_assemble_HS; solves Eq. 2 like ofm_eigs_by_index.  OFM_ERR_INVALID:
+ * gap_min <= 0, NULL outputs, or no such spacing; OFM_ERR_STATE: nothing
+ * assembled. */
+ofm_status ofm_homo_lumo_gap(ofm_ctx* ctx, double gap_min, double* e_ref, double* E_homo,
+                             double* E_lumo, int* n_occ);
+
 /* The pair list: *n_pairs always; pair_ab (2*n_pairs ints, a then b, a<=b,
  * sorted by a then b) when not NULL. */
 ofm_status ofm_get_pairs(ofm_ctx* ctx, int* n_pairs, int* pair_ab);

@@ -29,6 +29,10 @@ systems", Sec. II):
 5. The generalized eigenproblem sum_mn (H - E S) C = 0 of Eq. 2 on the dense
    assembled matrices (LAPACK through scipy.linalg.eigh, as the paper uses
    standard LAPACK routines), and the eigenvalues inside an energy window.
+6. Variants of Sec. III: the distance cutoff on the pair list ("Choice of the
+   distance cutoff"), and, for a basis of fragment HOMOs ("Choice of the
+   number of basis states per fragment"), e_i = <i|H|i> and the first gap of
+   the spectrum above it.
 
 Readings of the paper where it is silent are listed in the repository's
 design notes (fragment Hamiltonian = principal submatrix; the H_ab sum runs
@@ -356,6 +360,29 @@ def window_vectors(Hd, Sd, E_lo, E_hi):
 
 
 # ------------------------------------------------------------- pipeline -----
+
+def homo_expectations(H, grid, frags, Phis):
+    """Sec. III (occupation with a HOMO basis): e_a = <i|H|i> with the
+    whole-system H, |i> the highest basis state of fragment a."""
+    out = []
+    for f, P in zip(frags, Phis):
+        v = np.asarray(zero_extend(grid, f, P[:, -1:]).todense()).ravel()
+        out.append(float(v @ (H @ v)))
+    return out
+
+
+def first_gap(E, e_ref, gap_min):
+    """Sec. III: the first gap in the spectrum above e_ref, read as the first
+    spacing wider than gap_min between consecutive eigenvalues, starting from
+    the largest eigenvalue <= e_ref.  Returns (E_homo, E_lumo, n_occ) with
+    n_occ the number of eigenvalues <= E_homo."""
+    E = np.sort(np.asarray(E, dtype=np.float64))
+    k = max(int(np.sum(E <= e_ref)) - 1, 0)
+    for i in range(k, len(E) - 1):
+        if E[i + 1] - E[i] > gap_min:
+            return float(E[i]), float(E[i + 1]), i + 1
+    raise ValueError("no spacing wider than gap_min at or above e_ref")
+
 
 def run_ofm(workload, Phis=None, pairs=None):
     """Whole method on one workload: fragment eigensolves (unless states are

@@ -206,6 +206,86 @@ static void pair_totals(ofm_ctx* c) {
   }
 }
 
+// The pair list of the current fragments: boxes that meet, then (when a
+// distance cutoff is set, Sec. III.C) only the pairs whose fragments have
+// atoms closer than d_cut; self pairs always stay.
+static void plan_pairs(ofm_ctx* c) {
+  make_pairs(c->grid, c->frags, c->pairs);
+  if (!(c->cut_d > 0.0)) return;
+  const std::vector<int>& off = c->cut_off;
+  const std::vector<double>& xyz = c->cut_xyz;
+  double L[3];
+  for (int d = 0; d < 3; ++d) L[d] = c->grid.n[d] * c->grid.h;
+  const double dc2 = c->cut_d * c->cut_d;
+  auto near = [&](int a, int b) {
+    for (int i = off[a]; i < off[a + 1]; ++i)
+      for (int j = off[b]; j < off[b + 1]; ++j) {
+        double r2 = 0.0;
+        for (int d = 0; d < 3; ++d) {
+          double x = xyz[3 * i + d] - xyz[3 * j + d];
+          x -= L[d] * std::nearbyint(x / L[d]);   // minimum image
+          r2 += x * x;
+        }
+        if (r2 < dc2) return true;
+      }
+    return false;
+  };
+  std::vector<HostPair> kept;
+  for (auto& p : c->pairs)
+    if (p.a == p.b || near(p.a, p.b)) kept.push_back(std::move(p));
+  c->pairs.swap(kept);
+}
+
+// Everything that follows from the fragment list c->in_frags (geometry and
+// state counts): fragment table, pairs, traffic figures, zeroed state and
+// H phi storage, the device fragment table, launch shapes and contraction
+// plans.  The eigensolver's workspace, sized for the old table, is dropped.
+static ofm_status layout_fragments(ofm_ctx* c) {
+  const int n_frag = c->nfrag;
+  // the eigensolver's workspace is kept while the layout it was made for
+  // (grid, storage, boxes and state counts) stays
+  bool same = c->laid_storage == (int)c->storage && c->laid_frags.size() == c->in_frags.size() &&
+              c->laid_grid.h == c->grid.h;
+  for (int d = 0; d < 3; ++d) same = same && c->laid_grid.n[d] == c->grid.n[d];
+  for (size_t a = 0; same && a < c->in_frags.size(); ++a)
+    same = std::memcmp(&c->laid_frags[a], &c->in_frags[a], sizeof(ofm_fragment)) == 0;
+  if (!same) ofm_eig_free(c);
+  c->laid_frags = c->in_frags;
+  c->laid_grid = c->grid;
+  c->laid_storage = (int)c->storage;
+  make_frag_table(c->grid, c->in_frags.data(), n_frag, c->frags, c->state_elems);
+  plan_pairs(c);
+  c->basis = 0;
+  c->apply_points = 0;
+  for (auto& f : c->frags) {
+    c->basis += f.n;
+    c->apply_points += f.Pd * f.n;
+  }
+  pair_totals(c);
+  c->frag_set.assign(n_frag, 0);
+  const size_t es = elem_size(c);
+  // algorithmic traffic: the H apply reads every state and V once and writes
+  // H phi once on the dilated boxes; the contraction at its minimum reads
+  // states and H phi once.
+  c->apply_bytes = 0;
+  for (auto& f : c->frags) c->apply_bytes += (double)f.Pd * (2.0 * f.n + 1.0) * es;
+  c->contract_bytes = 0;
+  for (auto& f : c->frags) c->contract_bytes += (double)f.Pd * 2.0 * f.n * es;
+  OFM_TRY(ofm_ensure(c, c->states, c->state_elems * es, "fragment states"));
+  OFM_TRY(ofm_ensure(c, c->hphi, c->state_elems * es, "H phi"));
+  OFM_CUDA(c, cudaMemsetAsync(c->states.p, 0, c->state_elems * es, c->stream));
+  OFM_CUDA(c, cudaMemsetAsync(c->hphi.p, 0, c->state_elems * es, c->stream));
+  OFM_TRY(ofm_ensure(c, c->d_frags, sizeof(DevFrag) * n_frag, "fragment table"));
+  OFM_CUDA(c, cudaMemcpyAsync(c->d_frags.p, c->frags.data(), sizeof(DevFrag) * n_frag,
+                              cudaMemcpyHostToDevice, c->stream));
+  // H-apply launch: 2-D grid (chunks of the largest fragment x fragments)
+  c->agrid = apply_grid(c->frags, es == 8, false);
+  c->asm_chunk = 0;
+  OFM_TRY(plan_contraction(c));
+  // host copies of tables are read back by later calls: wait for the uploads
+  return sync(c, "fragment layout");
+}
+
 extern "C" ofm_status ofm_build_fragments(ofm_ctx* c, const ofm_grid* grid, const double* V,
                                           ofm_location v_loc, const ofm_fragment* frags,
                                           int n_frag, ofm_storage storage) {
@@ -217,31 +297,18 @@ extern "C" ofm_status ofm_build_fragments(ofm_ctx* c, const ofm_grid* grid, cons
     return ofm_fail(c, OFM_ERR_INVALID, "unknown V location");
   std::string msg;
   if (!validate_geometry(*grid, frags, n_frag, msg)) return ofm_fail(c, OFM_ERR_INVALID, msg);
+  if (n_frag > 65535) return ofm_fail(c, OFM_ERR_INVALID, "at most 65535 fragments");
 
   c->built = c->have_states = c->assembled = c->dense_ready = c->factored = false;
   c->grid = *grid;
   c->storage = storage;
   c->nfrag = n_frag;
   c->in_frags.assign(frags, frags + n_frag);
-  make_frag_table(*grid, frags, n_frag, c->frags, c->state_elems);
-  make_pairs(*grid, c->frags, c->pairs);
-  c->basis = 0;
-  c->apply_points = 0;
-  for (auto& f : c->frags) {
-    c->basis += f.n;
-    c->apply_points += f.Pd * f.n;
-  }
-  pair_totals(c);
-  c->frag_set.assign(n_frag, 0);
+  c->cut_d = 0.0;   // a distance cutoff belongs to the previous fragments
+  c->cut_xyz.clear();
+  c->cut_off.clear();
 
   const size_t es = elem_size(c);
-  // algorithmic traffic: the H apply reads every state and V once and writes
-  // H phi once on the dilated boxes; the contraction at its minimum reads
-  // states and H phi once.
-  c->apply_bytes = 0;
-  for (auto& f : c->frags) c->apply_bytes += (double)f.Pd * (2.0 * f.n + 1.0) * es;
-  c->contract_bytes = 0;
-  for (auto& f : c->frags) c->contract_bytes += (double)f.Pd * 2.0 * f.n * es;
   const long long npts = (long long)grid->n[0] * grid->n[1] * grid->n[2];
   OFM_TRY(ofm_ensure(c, c->V, npts * es, "potential"));
   if (v_loc == OFM_HOST) {
@@ -255,30 +322,14 @@ extern "C" ofm_status ofm_build_fragments(ofm_ctx* c, const ofm_grid* grid, cons
     launch_convert_V(V, c->V.p, npts, es == 8, c->stream);
   }
   OFM_TRY(check_launch(c, "convert V"));
-
-  OFM_TRY(ofm_ensure(c, c->states, c->state_elems * es, "fragment states"));
-  OFM_TRY(ofm_ensure(c, c->hphi, c->state_elems * es, "H phi"));
-  OFM_CUDA(c, cudaMemsetAsync(c->states.p, 0, c->state_elems * es, c->stream));
-  OFM_CUDA(c, cudaMemsetAsync(c->hphi.p, 0, c->state_elems * es, c->stream));
-  OFM_TRY(ofm_ensure(c, c->d_frags, sizeof(DevFrag) * n_frag, "fragment table"));
-  OFM_CUDA(c, cudaMemcpyAsync(c->d_frags.p, c->frags.data(), sizeof(DevFrag) * n_frag,
-                              cudaMemcpyHostToDevice, c->stream));
-
-  // H-apply launch: 2-D grid (chunks of the largest fragment x fragments)
-  if (n_frag > 65535) return ofm_fail(c, OFM_ERR_INVALID, "at most 65535 fragments");
-  c->agrid = apply_grid(c->frags, es == 8, false);
-
-  c->asm_chunk = 0;
-  OFM_TRY(plan_contraction(c));
-  // host copies of tables are read back by later calls: wait for the uploads
-  OFM_TRY(sync(c, "build_fragments"));
+  OFM_TRY(layout_fragments(c));
   c->built = true;
   return OFM_OK;
 }
 
 // Sec. III.C: pairs whose fragments' atoms are all at least d_cut apart are
-// left out.  The geometric list (boxes that meet) is made again and
-// filtered; self pairs stay.
+// left out.  The cutoff and the atoms are kept for later re-plans (a state
+// selection); a new ofm_build_fragments clears them.
 extern "C" ofm_status ofm_set_pair_cutoff(ofm_ctx* c, const double* atom_xyz,
                                           const int* frag_atom_off, double d_cut) {
   if (!c) return OFM_ERR_INVALID;
@@ -290,34 +341,55 @@ extern "C" ofm_status ofm_set_pair_cutoff(ofm_ctx* c, const double* atom_xyz,
     for (int a = 0; a < c->nfrag; ++a)
       if (frag_atom_off[a + 1] < frag_atom_off[a])
         return ofm_fail(c, OFM_ERR_INVALID, "frag_atom_off must not decrease");
+    c->cut_off.assign(frag_atom_off, frag_atom_off + c->nfrag + 1);
+    c->cut_xyz.assign(atom_xyz, atom_xyz + 3 * (size_t)frag_atom_off[c->nfrag]);
+    c->cut_d = d_cut;
+  } else {
+    c->cut_d = 0.0;
+    c->cut_xyz.clear();
+    c->cut_off.clear();
   }
-  make_pairs(c->grid, c->frags, c->pairs);
-  if (cut) {
-    double L[3];
-    for (int d = 0; d < 3; ++d) L[d] = c->grid.n[d] * c->grid.h;
-    const double dc2 = d_cut * d_cut;
-    auto near = [&](int a, int b) {
-      for (int i = frag_atom_off[a]; i < frag_atom_off[a + 1]; ++i)
-        for (int j = frag_atom_off[b]; j < frag_atom_off[b + 1]; ++j) {
-          double r2 = 0.0;
-          for (int d = 0; d < 3; ++d) {
-            double x = atom_xyz[3 * i + d] - atom_xyz[3 * j + d];
-            x -= L[d] * std::nearbyint(x / L[d]);   // minimum image
-            r2 += x * x;
-          }
-          if (r2 < dc2) return true;
-        }
-      return false;
-    };
-    std::vector<HostPair> kept;
-    for (auto& p : c->pairs)
-      if (p.a == p.b || near(p.a, p.b)) kept.push_back(std::move(p));
-    c->pairs.swap(kept);
-  }
+  plan_pairs(c);
   pair_totals(c);
   c->assembled = c->dense_ready = c->factored = false;
   OFM_TRY(plan_contraction(c));
   return sync(c, "set_pair_cutoff");
+}
+
+// Sec. III, "Choice of the number of basis states per fragment": a sub-range
+// of each fragment's states (e.g. its highest occupied ones) as the basis.
+// The selected columns are copied on the device into the layout for the new
+// state counts.
+extern "C" ofm_status ofm_select_states(ofm_ctx* c, const int* first, const int* count) {
+  if (!c) return OFM_ERR_INVALID;
+  if (!c->built || !c->have_states)
+    return ofm_fail(c, OFM_ERR_STATE, "fragment states are not set (ofm_fragment_eigs or ofm_set_fragment_states)");
+  if (!first || !count) return ofm_fail(c, OFM_ERR_INVALID, "first and count must not be NULL");
+  for (int a = 0; a < c->nfrag; ++a)
+    if (first[a] < 0 || count[a] < 1 || first[a] + count[a] > c->frags[a].n) {
+      char buf[128];
+      snprintf(buf, sizeof buf, "fragment %d: states [%d, %d) outside its %d states", a, first[a],
+               first[a] + count[a], c->frags[a].n);
+      return ofm_fail(c, OFM_ERR_INVALID, buf);
+    }
+  const size_t es = elem_size(c);
+  const std::vector<DevFrag> old = c->frags;
+  OFM_TRY(ofm_ensure(c, c->staging, c->state_elems * es, "staging"));
+  OFM_CUDA(c, cudaMemcpyAsync(c->staging.p, c->states.p, c->state_elems * es,
+                              cudaMemcpyDeviceToDevice, c->stream));
+  for (int a = 0; a < c->nfrag; ++a) c->in_frags[a].n_states = count[a];
+  OFM_TRY(layout_fragments(c));   // zeroed storage, new plans; the cutoff stays
+  {
+    KTimer t(c, KC_CONVERT);
+    for (int a = 0; a < c->nfrag; ++a)
+      launch_select_states(old[a], c->frags[a], first[a], c->staging.p, c->states.p, es == 8,
+                           c->stream);
+  }
+  OFM_TRY(check_launch(c, "select states"));
+  c->frag_set.assign(c->nfrag, 1);
+  c->have_states = true;
+  c->assembled = c->dense_ready = c->factored = false;
+  return sync(c, "select_states");
 }
 
 // ------------------------------------------------------------- states ------
@@ -612,4 +684,50 @@ extern "C" ofm_status ofm_eigs_by_index(ofm_ctx* c, int i_lo, int i_hi, double* 
   if (!c->factored) OFM_TRY(ofm_window_factor(c));
   if (i_hi > i_lo) OFM_TRY(ofm_window_bisect(c, i_lo, i_hi, E_out));
   return OFM_OK;
+}
+
+// Sec. III, occupation with a HOMO basis: e_a = <HOMO_a|H|HOMO_a> with the
+// whole-system H (the last diagonal entry of the assembled H_aa: the
+// fragment's highest basis state), e_ref = max_a e_a, then the first spacing
+// wider than gap_min between consecutive eigenvalues of Eq. 2, scanning up
+// from the largest eigenvalue <= e_ref (the spacing that holds e_ref counts).
+extern "C" ofm_status ofm_homo_lumo_gap(ofm_ctx* c, double gap_min, double* e_ref_out,
+                                        double* E_homo, double* E_lumo, int* n_occ) {
+  if (!c) return OFM_ERR_INVALID;
+  if (!c->assembled) return ofm_fail(c, OFM_ERR_STATE, "ofm_assemble_HS must come first");
+  if (!(gap_min > 0.0) || !E_homo || !E_lumo || !n_occ)
+    return ofm_fail(c, OFM_ERR_INVALID, "gap_min must be positive and the outputs not NULL");
+  OFM_TRY(ofm_wait_status(c));
+  std::vector<double> e(c->nfrag);
+  for (int a = 0; a < c->nfrag; ++a) {
+    const int p = find_pair(c, a, a);
+    const long long n = c->frags[a].n;
+    if (p < 0) return ofm_fail(c, OFM_ERR_STATE, "a self pair is missing");
+    OFM_CUDA(c, cudaMemcpyAsync(&e[a], (const double*)c->blocks.p + c->simt_pairs[p].blk_off + n * n - 1,
+                                sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  }
+  OFM_TRY(sync(c, "homo_lumo_gap"));
+  const double e_ref = *std::max_element(e.begin(), e.end());
+  if (e_ref_out) *e_ref_out = e_ref;
+  if (!c->dense_ready) OFM_TRY(ofm_make_dense(c));
+  if (!c->factored) OFM_TRY(ofm_window_factor(c));
+  int below = 0, upto = 0;
+  OFM_TRY(ofm_window_count(c, e_ref, e_ref, &below, &upto));   // upto: eigenvalues <= e_ref
+  const int n = c->dense_n;
+  int k = std::max(upto - 1, 0);
+  const int chunk = 64;
+  std::vector<double> E(chunk + 1);
+  while (k + 1 < n) {
+    const int m = std::min(chunk + 1, n - k);   // E_k .. E_{k+m-1}
+    OFM_TRY(ofm_window_bisect(c, k, k + m, E.data()));
+    for (int i = 0; i + 1 < m; ++i)
+      if (E[i + 1] - E[i] > gap_min) {
+        *E_homo = E[i];
+        *E_lumo = E[i + 1];
+        *n_occ = k + i + 1;
+        return OFM_OK;
+      }
+    k += m - 1;
+  }
+  return ofm_fail(c, OFM_ERR_INVALID, "no spacing wider than gap_min at or above e_ref");
 }

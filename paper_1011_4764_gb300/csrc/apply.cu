@@ -634,6 +634,28 @@ void launch_cheb_filter(const DevFrag* d_fr, int nfrag, int mmax, size_t smem, c
 
 // ------------------------------------------------------------ conversions --
 
+// Columns [first, first + Fn.n) of one fragment's stored states (every
+// storage point, halo included) into the layout Fn; pad columns zero.
+template <typename T>
+__global__ void select_states_kernel(DevFrag Fo, DevFrag Fn, int first, const T* __restrict__ src,
+                                     T* __restrict__ dst) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Fn.Pd * Fn.ld) return;
+  const long long p = i / Fn.ld;
+  const int j = (int)(i - p * Fn.ld);
+  dst[Fn.off + i] = (j < Fn.n) ? src[Fo.off + p * Fo.ld + first + j] : T(0);
+}
+
+void launch_select_states(const DevFrag& Fo, const DevFrag& Fn, int first, const void* src,
+                          void* dst, bool fp64, cudaStream_t s) {
+  const long long n = Fn.Pd * Fn.ld;
+  const int blocks = (int)((n + 255) / 256);
+  if (fp64)
+    select_states_kernel<double><<<blocks, 256, 0, s>>>(Fo, Fn, first, (const double*)src, (double*)dst);
+  else
+    select_states_kernel<float><<<blocks, 256, 0, s>>>(Fo, Fn, first, (const float*)src, (float*)dst);
+}
+
 template <typename T>
 __global__ void convert_V_kernel(const double* __restrict__ src, T* __restrict__ dst, long long n) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;

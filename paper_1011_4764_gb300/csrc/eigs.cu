@@ -900,18 +900,22 @@ __global__ void __launch_bounds__(1024) export_states_kernel(const DevFrag* efr,
   }
 }
 
-// out[0] = max V, out[1] = min V
+constexpr int VMAX_BLOCKS = 152;
+
+// max and min of V: per-block partials in the storage type (FP32 compares
+// are cheap, FP64 ones are not on this part), then one block combines them
+// into out[0] = max, out[1] = min; part holds 2 * VMAX_BLOCKS doubles.
 template <typename T>
-__global__ void vmax_kernel(const T* V, long long n, double* out) {
-  __shared__ double red[32], redm[32];
-  double m = -DBL_MAX, mn = DBL_MAX;
-  for (long long i = threadIdx.x; i < n; i += blockDim.x) {
-    m = fmax(m, (double)V[i]);
-    mn = fmin(mn, (double)V[i]);
+__global__ void __launch_bounds__(256) vmax_partial_kernel(const T* V, long long n, double* part) {
+  __shared__ T red[8], redm[8];
+  T m = V[0], mn = V[0];
+  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += 256LL * gridDim.x) {
+    m = max(m, V[i]);
+    mn = min(mn, V[i]);
   }
   for (int o = 16; o > 0; o >>= 1) {
-    m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
-    mn = fmin(mn, __shfl_down_sync(0xffffffffu, mn, o));
+    m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
   }
   if ((threadIdx.x & 31) == 0) {
     red[threadIdx.x >> 5] = m;
@@ -919,17 +923,46 @@ __global__ void vmax_kernel(const T* V, long long n, double* out) {
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t = -DBL_MAX, tm = DBL_MAX;
-    for (int w = 0; w < (int)blockDim.x / 32; ++w) {
-      t = fmax(t, red[w]);
-      tm = fmin(tm, redm[w]);
+    for (int w = 1; w < 8; ++w) {
+      m = max(m, red[w]);
+      mn = min(mn, redm[w]);
     }
-    out[0] = t;
-    out[1] = tm;
+    part[2 * blockIdx.x] = (double)m;
+    part[2 * blockIdx.x + 1] = (double)mn;
   }
 }
 
+__global__ void vmax_final_kernel(const double* part, int nb, double* out) {
+  if (threadIdx.x != 0) return;
+  double m = part[0], mn = part[1];
+  for (int b = 1; b < nb; ++b) {
+    m = fmax(m, part[2 * b]);
+    mn = fmin(mn, part[2 * b + 1]);
+  }
+  out[0] = m;
+  out[1] = mn;
+}
+
 }  // namespace
+
+// Range of V (max, min) for the filter's bounds: taken at every solve,
+// since V may change while the fragment layout (and the workspace) stays.
+static ofm_status eig_vlim(ofm_ctx* c) {
+  EigWork* w = c->eig;
+  cudaStream_t s = c->stream;
+  const long long npts = (long long)c->grid.n[0] * c->grid.n[1] * c->grid.n[2];
+  KTimer kt(c, KC_EIG_INIT);
+  double* part = (double*)w->d_vmax.p + 2;
+  if (c->storage == OFM_STORE_FP64)
+    vmax_partial_kernel<double><<<VMAX_BLOCKS, 256, 0, s>>>((const double*)c->V.p, npts, part);
+  else
+    vmax_partial_kernel<float><<<VMAX_BLOCKS, 256, 0, s>>>((const float*)c->V.p, npts, part);
+  vmax_final_kernel<<<1, 32, 0, s>>>(part, VMAX_BLOCKS, (double*)w->d_vmax.p);
+  OFM_CUDA(c, cudaGetLastError());
+  OFM_CUDA(c, cudaMemcpyAsync(w->vlim, w->d_vmax.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  OFM_CUDA(c, cudaStreamSynchronize(s));
+  return OFM_OK;
+}
 
 static ofm_status eig_setup(ofm_ctx* c, int guard_opt) {
   if (!c->eig) c->eig = new EigWork();
@@ -1021,7 +1054,7 @@ static ofm_status eig_setup(ofm_ctx* c, int guard_opt) {
   OFM_TRY(ofm_ensure(c, w->theta, sizeof(double) * w->tsum, "Ritz values"));
   OFM_TRY(ofm_ensure(c, w->res, sizeof(double) * w->tsum, "residuals"));
   OFM_TRY(ofm_ensure(c, w->d_rank, sizeof(int) * nf, "ranks"));
-  OFM_TRY(ofm_ensure(c, w->d_vmax, 2 * sizeof(double), "max and min V"));
+  OFM_TRY(ofm_ensure(c, w->d_vmax, (2 + 2 * VMAX_BLOCKS) * sizeof(double), "max and min V"));
   const long long mm = (long long)w->mmax * w->mmax;
   OFM_TRY(ofm_ensure(c, w->Cm, sizeof(double) * mm * nf, "Ritz coefficients"));
   OFM_TRY(ofm_ensure(c, w->work, sizeof(double) * (3 * mm + 3 * w->mmax + 8) * nf, "Rayleigh-Ritz work"));
@@ -1037,13 +1070,6 @@ static ofm_status eig_setup(ofm_ctx* c, int guard_opt) {
   OFM_CUDA(c, cudaMemcpyAsync(w->d_gpairs.p, w->gpairs.data(), sizeof(DevPair) * w->gpairs.size(), cudaMemcpyHostToDevice, s));
   OFM_CUDA(c, cudaMemcpyAsync(w->d_gpieces.p, w->gpieces.data(), sizeof(Piece) * w->gpieces.size(), cudaMemcpyHostToDevice, s));
   OFM_CUDA(c, cudaMemcpyAsync(w->d_gitems.p, w->gitems.data(), sizeof(WorkItem) * w->gitems.size(), cudaMemcpyHostToDevice, s));
-  const long long npts = (long long)c->grid.n[0] * c->grid.n[1] * c->grid.n[2];
-  KTimer kt(c, KC_EIG_INIT);
-  if (fp64) vmax_kernel<double><<<1, 1024, 0, s>>>((const double*)c->V.p, npts, (double*)w->d_vmax.p);
-  else vmax_kernel<float><<<1, 1024, 0, s>>>((const float*)c->V.p, npts, (double*)w->d_vmax.p);
-  OFM_CUDA(c, cudaGetLastError());
-  OFM_CUDA(c, cudaMemcpyAsync(w->vlim, w->d_vmax.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
-  OFM_CUDA(c, cudaStreamSynchronize(s));
   long long maxP = 0;
   for (auto& E : w->efr) maxP = std::max<long long>(maxP, (long long)E.ext[0] * E.ext[1] * E.ext[2]);
   // FP32 blocks take the 256-point register-tiled rotation when two CTAs fit
@@ -1172,6 +1198,7 @@ extern "C" ofm_status ofm_fragment_eigs(ofm_ctx* c, const ofm_eig_opts* opts, do
   if (!c->eig || !c->eig->ready || c->eig->efr.size() != (size_t)c->nfrag || o.extra_states > 0) {
     OFM_TRY(eig_setup(c, o.extra_states));
   }
+  OFM_TRY(eig_vlim(c));
   EigWork* w = c->eig;
   const int nf = c->nfrag;
   cudaStream_t s = c->stream;

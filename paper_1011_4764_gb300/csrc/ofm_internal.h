@@ -105,6 +105,8 @@ void launch_import_states(const DevFrag* d_fr, int a, const DevFrag& fa, const d
 void launch_export_states(const DevFrag& fa, const void* states, double* dst, bool fp64,
                           bool dilated_hphi, cudaStream_t s);
 size_t cheb_filter_smem(const std::vector<DevFrag>& frags, bool fp64);
+void launch_select_states(const DevFrag& Fo, const DevFrag& Fn, int first, const void* src,
+                          void* dst, bool fp64, cudaStream_t s);
 void launch_cheb_filter(const DevFrag* d_fr, int nfrag, int mmax, size_t smem, const void* V,
                         const void* X, void* Y, void* HY, const double* coef, int nsteps,
                         const int gn[3], double h, cudaStream_t s);
@@ -169,8 +171,16 @@ struct ofm_ctx {
   int nfrag = 0;
   int basis = 0;
   std::vector<ofm_fragment> in_frags;
+  // layout the eigensolver's workspace was made for
+  std::vector<ofm_fragment> laid_frags;
+  ofm_grid laid_grid{};
+  int laid_storage = -1;
   std::vector<ofm::DevFrag> frags;
   std::vector<ofm::HostPair> pairs;
+  // distance cutoff on the pair list (Sec. III.C); cut_d <= 0: none
+  double cut_d = 0.0;
+  std::vector<double> cut_xyz;   // atom positions, 3 per atom, grouped by fragment
+  std::vector<int> cut_off;      // nfrag + 1 offsets into the atoms
   long long state_elems = 0;
   long long flops = 0, ks = 0, kh = 0, apply_points = 0;
 

@@ -7,6 +7,7 @@ raises.  PyTorch is used only to hand device pointers and streams across.
 """
 from __future__ import annotations
 
+import collections
 import ctypes as C
 import os
 
@@ -28,8 +29,12 @@ EXPORTS = [
     "ofm_assemble_HS", "ofm_get_pairs", "ofm_get_plan_info", "ofm_get_block",
     "ofm_get_dense_HS", "ofm_get_hphi", "ofm_window_eigs", "ofm_eigs_by_index",
     "ofm_set_dense_HS", "ofm_plan_pairs", "ofm_set_profiling", "ofm_get_kernel_stats",
-    "ofm_pair_blocks_noalloc", "ofm_set_pair_cutoff",
+    "ofm_pair_blocks_noalloc", "ofm_set_pair_cutoff", "ofm_select_states", "ofm_homo_lumo_gap",
 ]
+
+
+# fragment geometry with the state count of the current basis
+_Frag = collections.namedtuple("_Frag", "off ext n_states")
 
 
 class ofm_grid(C.Structure):
@@ -101,6 +106,8 @@ def load_library(path: str = LIB_PATH):
                                      C.POINTER(ofm_fragment), P, P, P, P, P], I),
         "ofm_get_kernel_stats": ([P, C.POINTER(ofm_kernel_stat), I, IP], I),
         "ofm_set_pair_cutoff": ([P, DP, IP, D], I),
+        "ofm_select_states": ([P, IP, IP], I),
+        "ofm_homo_lumo_gap": ([P, D, DP, DP, DP, IP], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -280,6 +287,24 @@ class Context:
         if xyz.size == 0:
             xyz = np.zeros(3)
         self._check(self.lib.ofm_set_pair_cutoff(self.h, _dptr(xyz), _iptr(off), float(d_cut)))
+
+    # -- ofm_select_states
+    def select_states(self, first, count):
+        """Keep states first[a] .. first[a] + count[a] - 1 of every fragment
+        (ints or per-fragment sequences) as the basis."""
+        nf = len(self.frags)
+        f = np.ascontiguousarray(np.broadcast_to(np.asarray(first, dtype=np.int32), (nf,)))
+        n = np.ascontiguousarray(np.broadcast_to(np.asarray(count, dtype=np.int32), (nf,)))
+        self._check(self.lib.ofm_select_states(self.h, _iptr(f), _iptr(n)))
+        self.frags = [_Frag(tuple(fr.off), tuple(fr.ext), int(n[a])) for a, fr in enumerate(self.frags)]
+
+    # -- ofm_homo_lumo_gap
+    def homo_lumo_gap(self, gap_min):
+        """(e_ref, E_homo, E_lumo, n_occ) of the HOMO-basis occupation rule."""
+        e_ref, eh, el, n = C.c_double(), C.c_double(), C.c_double(), C.c_int()
+        self._check(self.lib.ofm_homo_lumo_gap(self.h, float(gap_min), C.byref(e_ref), C.byref(eh),
+                                               C.byref(el), C.byref(n)))
+        return e_ref.value, eh.value, el.value, n.value
 
     def pairs(self):
         n = C.c_int()

@@ -449,3 +449,33 @@ def test_self_pairs_only_give_the_fragment_spectra():
     Hd, Sd = O.assemble_dense(wl.frags, O.pair_blocks(H, wl.grid, wl.frags, list(Phis), selfs))
     E = O.generalized_eigs(Hd, Sd)
     assert np.max(np.abs(E - np.sort(np.concatenate(eps)))) < 1e-10
+
+
+# ------------------------------------- Sec. III basis selection and occupation --
+
+def test_first_gap_by_hand():
+    """Spectrum 0, .1, .2 | .9, 1.0 | 2.0 with gap_min 0.5: the first wide
+    spacing at or above the reference is (0.2, 0.9) whether the reference
+    sits below the spectrum, inside the cluster or inside that gap; a
+    smaller gap_min finds the first spacing that exceeds it."""
+    E = [1.0, 0.0, 2.0, 0.1, 0.9, 0.2]
+    for e_ref in (-1.0, 0.15, 0.5):
+        assert O.first_gap(E, e_ref, 0.5) == (0.2, 0.9, 3)
+    assert O.first_gap(E, 0.95, 0.5) == (1.0, 2.0, 5)
+    assert O.first_gap(E, 0.0, 0.09) == (0.0, 0.1, 1)
+    with pytest.raises(ValueError):
+        O.first_gap(E, 0.0, 5.0)
+
+
+def test_homo_expectation_is_the_fragment_energy():
+    """phi_HOMO vanishes outside its box, so <phi|H|phi> with the
+    whole-system H equals the quadratic form of the box's principal
+    submatrix: the fragment's HOMO energy, for exact eigenstates."""
+    wl = make_workload("tiny")
+    H = O.hamiltonian(wl.grid, wl.V)
+    eps, Phis = zip(*[O.fragment_eigs(H, wl.grid, f) for f in wl.frags])
+    e = O.homo_expectations(H, wl.grid, wl.frags, list(Phis))
+    assert np.max(np.abs(np.array(e) - np.array([w[-1] for w in eps]))) < 1e-12
+    top2 = [P[:, -2:] for P in Phis]
+    e2 = O.homo_expectations(H, wl.grid, wl.frags, top2)
+    assert e2 == e
