@@ -570,6 +570,42 @@ def extras(args, ctx, ofm, wl, V_host, step, window_of, stream, storage, F, dev,
                                 "gap_min_ha": 0.5 * (el - eh), "rows": rows}
     except Exception as e:
         ex["homo_basis"] = {"error": str(e)}
+    # fragment-size study (Sec. III "Choice of fragments": monomer / dimer /
+    # trimer-like boxes of 1, 2, 3 wells on the tiny grid, FP64): error of the
+    # bound levels against the full-grid diagonalisation, which is the
+    # library's own eigensolve of one fragment spanning the grid
+    try:
+        from ofm_inputs import Fragment, tiny_fragments_of
+        base = tiny_fragments_of(1)
+        whole = ofm.Context(stream)
+        whole.build_fragments(base.grid, base.V, [Fragment((0, 0, 0), tuple(base.grid.n), 8)],
+                              storage="fp64")
+        full, _, _ = whole.fragment_eigs()
+        whole.close()
+        rows = []
+        for s in (1, 2, 3):
+            wl_s = tiny_fragments_of(s)
+            c_s = ofm.Context(stream)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            c_s.build_fragments(wl_s.grid, wl_s.V, wl_s.frags, storage="fp64")
+            c_s.fragment_eigs()
+            c_s.assemble("fp64")
+            lv = c_s.eigs_by_index(0, 8)
+            e1.record(stream)
+            e1.synchronize()
+            bound = full < 0
+            rows.append({"wells_per_fragment": s, "basis": 8 * s,
+                         "max_err_bound_levels_ha": float(np.max(lv[bound] - full[bound])),
+                         "lowest_level_err_ha": float(lv[0] - full[0]),
+                         "min_err_ha": float(np.min(lv - full)),
+                         "method_ms": e0.elapsed_time(e1)})
+            c_s.close()
+        ex["fragment_size"] = {"workload": "tiny grid 32x12x12, 8 wells", "full_grid_levels_ha":
+                               [float(x) for x in full], "rows": rows}
+    except Exception as e:
+        ex["fragment_size"] = {"error": str(e)}
     return ex
 
 

@@ -147,6 +147,19 @@ def _tiny(seed: int = 0) -> Workload:
                     "8 Gaussian wells (D=1 Ha, w=1 bohr), 4 boxes 16x12x12, 6 states")
 
 
+def tiny_fragments_of(n_wells: int, seed: int = 0) -> Workload:
+    """The tiny workload's grid and wells with fragments of n_wells
+    consecutive wells (monomer-, dimer-, trimer-like for 1, 2, 3): one box per
+    starting well (periodic), 4n + 4 points wide with 2 bohr of margin on each
+    side, one state per well."""
+    base = _tiny(seed)
+    s = int(n_wells)
+    frags = [Fragment(((4 * i - 2) % base.grid.n[0], 0, 0), (4 * s + 4, 12, 12), s) for i in range(8)]
+    return Workload(f"tiny_{s}wells", base.grid, base.wells, frags,
+                    WindowRule("from_lowest", 0.5), "f64",
+                    f"tiny grid and wells, 8 boxes of {s} consecutive wells, {s} states each")
+
+
 def _alkane_chain(seed: int = 0) -> Workload:
     """256x32x32 grid, zig-zag chain of 64 C-like and 128 H-like wells."""
     grid = Grid((256, 32, 32), 0.5)
