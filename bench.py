@@ -8,8 +8,8 @@ the potential resident in device memory:
   a0  batched fragment eigensolve                                ofm_fragment_eigs
   a1  H phi on the dilated boxes, a3/a4 pair contraction,
   a5  symmetrise into blocks                                     ofm_assemble_HS
-  a6  FP64 window solve (index of the gap level, then the
-      eigenvalues in [E_gap, E_gap + 0.3 Ha])                    ofm_eigs_by_index, ofm_window_eigs
+  a6  FP64 window solve: the first empty level E_gap and the
+      eigenvalues in [E_gap, E_gap + 0.3 Ha]                      ofm_window_from_index
 The metric is the pair-block rate: algorithmic pair-block flops of one step
 (sum over pairs a<=b of 2 n_a n_b (|B_a∩B_b| + |B_a∩B_b+|)) times the steps,
 over the device time of the steps.  Per-row device times, the assembly-only
@@ -284,18 +284,15 @@ def run_ours(args):
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     def window_of(c):
-        # A window that starts AT an eigenvalue includes it: its computed
-        # value may round a few ulps above the exact one, so the lower end
-        # passed to the count sits 1e-9 Ha below it
-        if rule.kind == "above_gap":
-            e0 = float(c.eigs_by_index(rule.n_occ, rule.n_occ + 1)[0])
-            lo, hi = e0 - 1e-9, e0 + rule.width
-        elif rule.kind == "from_lowest":
-            e0 = float(c.eigs_by_index(0, 1)[0])
-            lo, hi = e0 - 1e-9, e0 + rule.width
-        else:
-            e = c.eigs_by_index(rule.n_occ - 1, rule.n_occ + 1)
-            lo, hi = float(e[0]) - rule.width, float(e[1]) + rule.width
+        # a window that starts AT an eigenvalue (the first empty level, or the
+        # lowest) is one index-anchored call: E_i and the levels up to
+        # E_i + width
+        if rule.kind in ("above_gap", "from_lowest"):
+            i0 = rule.n_occ if rule.kind == "above_gap" else 0
+            E, n = c.window_from_index(i0, rule.width)
+            return E, float(E[0]), float(E[0]) + rule.width
+        e = c.eigs_by_index(rule.n_occ - 1, rule.n_occ + 1)
+        lo, hi = float(e[0]) - rule.width, float(e[1]) + rule.width
         E, n = c.window_eigs(lo, hi)
         return E, lo, hi
 

@@ -231,6 +231,18 @@ ofm_status ofm_window_eigs(ofm_ctx* ctx, double E_lo, double E_hi, int max_out,
  * an energy window relative to a gap. */
 ofm_status ofm_eigs_by_index(ofm_ctx* ctx, int i_lo, int i_hi, double* E_out);
 
+/* A window of Eq. 2 anchored at an index: E_{i_lo} and every later
+ * eigenvalue E_j <= E_{i_lo} + width (width in Ha, >= 0), ascending, e.g.
+ * the levels within 0.3 Ha above the first empty one.  *n_out is the window
+ * size; E_out (host) receives min(*n_out, max_out) values.  The same set as
+ * ofm_eigs_by_index for E_{i_lo} followed by ofm_window_eigs on
+ * [E_{i_lo}, E_{i_lo} + width], in one multisection launch sized by an FP32
+ * estimate (extended when short), so the anchor's own search is not a
+ * separate serial step.  OFM_ERR_INVALID: i_lo outside the spectrum, width <
+ * 0, NULL outputs. */
+ofm_status ofm_window_from_index(ofm_ctx* ctx, int i_lo, double width, int max_out, double* E_out,
+                                 int* n_out);
+
 /* Eq. 2 for caller-supplied dense n x n row-major H (symmetric) and S
  * (symmetric positive definite), host pointers, solved by the same device
  * path as ofm_window_eigs (replaces the assembled matrices). */

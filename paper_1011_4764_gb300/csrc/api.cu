@@ -686,6 +686,39 @@ extern "C" ofm_status ofm_eigs_by_index(ofm_ctx* c, int i_lo, int i_hi, double* 
   return OFM_OK;
 }
 
+// A window anchored at an index: E_{i_lo} and every later eigenvalue up to
+// E_{i_lo} + width.  An FP32 estimate of the window's size sizes ONE
+// multisection launch over [i_lo, i_lo + estimate + pad); the FP64
+// eigenvalues then decide the window exactly (more are computed when the
+// last one is still inside).
+extern "C" ofm_status ofm_window_from_index(ofm_ctx* c, int i_lo, double width, int max_out,
+                                            double* E_out, int* n_out) {
+  if (!c) return OFM_ERR_INVALID;
+  if (!n_out || (max_out > 0 && !E_out) || max_out < 0 || !(width >= 0.0))
+    return ofm_fail(c, OFM_ERR_INVALID, "bad window arguments");
+  if (!c->dense_ready) OFM_TRY(ofm_make_dense(c));
+  if (!c->factored) OFM_TRY(ofm_window_factor(c));
+  const int n = c->dense_n;
+  if (i_lo < 0 || i_lo >= n) return ofm_fail(c, OFM_ERR_INVALID, "i_lo outside the spectrum");
+  int est = n;
+  OFM_TRY(ofm_window_size_estimate(c, i_lo, width, &est));
+  int i_hi = std::min(n, std::max(i_lo + 1, est + 8));
+  std::vector<double> E(i_hi - i_lo);
+  OFM_TRY(ofm_window_bisect(c, i_lo, i_hi, E.data()));
+  const double top = E[0] + width;
+  while (E.back() <= top && i_hi < n) {   // the estimate fell short: extend
+    const int more = std::min(n, i_hi + std::max(64, i_hi - i_lo)) - i_hi;
+    E.resize(E.size() + more);
+    OFM_TRY(ofm_window_bisect(c, i_hi, i_hi + more, E.data() + (i_hi - i_lo)));
+    i_hi += more;
+  }
+  int cnt = 0;
+  while (cnt < (int)E.size() && E[cnt] <= top) ++cnt;
+  *n_out = cnt;
+  if (max_out > 0) std::copy(E.begin(), E.begin() + std::min(cnt, max_out), E_out);
+  return OFM_OK;
+}
+
 // Sec. III, occupation with a HOMO basis: e_a = <HOMO_a|H|HOMO_a> with the
 // whole-system H (the last diagonal entry of the assembled H_aa: the
 // fragment's highest basis state), e_ref = max_a e_a, then the first spacing

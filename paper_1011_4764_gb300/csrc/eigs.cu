@@ -858,15 +858,46 @@ __global__ void __launch_bounds__(1024) export_states_kernel(const DevFrag* efr,
   const int P = F.ext[0] * F.ext[1] * F.ext[2];
   T best = T(-1);
   int besti = 0;
+  // the warp's points t = warp, warp + nw, ... walked by stepping (x, y, z)
+  // with carries: no integer division per point
+  const int sx = nw % ex, sy = (nw / ex) % ey, sz = nw / (ex * ey);
+  auto start = [&](int& x, int& y, int& z) {
+    x = warp % ex;
+    y = (warp / ex) % ey;
+    z = warp / (ex * ey);
+  };
+  auto step = [&](int& x, int& y, int& z) {
+    x += sx;
+    int cy = 0;
+    if (x >= ex) { x -= ex; cy = 1; }
+    y += sy + cy;
+    int cz = 0;
+    if (y >= ey) { y -= ey; cz = 1; }
+    z += sz + cz;
+  };
+  // eight loads in flight per warp: a load, its compare and then the next
+  // load would pay an L2 round trip per point
+  constexpr int U = 8;
   if (col < F.n) {
-    for (int t = warp; t < P; t += nw) {
-      const int x = t % ex, y = (t / ex) % ey, z = t / (ex * ey);
-      const int pd = ((z + E.lo[2]) * E.dext[1] + (y + E.lo[1])) * E.dext[0] + x + E.lo[0];
-      const T a = fabs(X[E.off + (long long)pd * E.ld + col]);
-      if (a > best) {  // strictly greater: the lowest index wins within a warp's stream
-        best = a;
-        besti = t;
+    int x, y, z;
+    start(x, y, z);
+    for (int t0 = warp; t0 < P; t0 += U * nw) {
+      T a[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        a[u] = T(-1);
+        if (t0 + u * nw < P) {
+          const int pd = ((z + E.lo[2]) * E.dext[1] + (y + E.lo[1])) * E.dext[0] + x + E.lo[0];
+          a[u] = fabs(X[E.off + (long long)pd * E.ld + col]);
+          step(x, y, z);
+        }
       }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (a[u] > best) {  // strictly greater, in stream order: the lowest index wins
+          best = a[u];
+          besti = t0 + u * nw;
+        }
     }
   }
   bv[warp][lane] = best;
@@ -892,11 +923,24 @@ __global__ void __launch_bounds__(1024) export_states_kernel(const DevFrag* efr,
   __syncthreads();
   if (col >= F.n) return;
   const T s = sgn[lane];
-  for (int t = warp; t < P; t += nw) {
-    const int x = t % ex, y = (t / ex) % ey, z = t / (ex * ey);
-    const int pe = ((z + E.lo[2]) * E.dext[1] + (y + E.lo[1])) * E.dext[0] + x + E.lo[0];
-    const int pf = ((z + F.lo[2]) * F.dext[1] + (y + F.lo[1])) * F.dext[0] + x + F.lo[0];
-    states[F.off + (long long)pf * F.ld + col] = s * X[E.off + (long long)pe * E.ld + col];
+  int x, y, z;
+  start(x, y, z);
+  for (int t0 = warp; t0 < P; t0 += U * nw) {
+    T v[U];
+    int pf[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      pf[u] = -1;
+      if (t0 + u * nw < P) {
+        const int pe = ((z + E.lo[2]) * E.dext[1] + (y + E.lo[1])) * E.dext[0] + x + E.lo[0];
+        pf[u] = ((z + F.lo[2]) * F.dext[1] + (y + F.lo[1])) * F.dext[0] + x + F.lo[0];
+        v[u] = X[E.off + (long long)pe * E.ld + col];
+        step(x, y, z);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (pf[u] >= 0) states[F.off + (long long)pf[u] * F.ld + col] = s * v[u];
   }
 }
 

@@ -255,11 +255,14 @@ ofm_status ofm_window_factor(ofm_ctx* c);
 // eigenvalues below lo and below-or-at hi of the factored pencil
 ofm_status ofm_window_count(ofm_ctx* c, double lo, double hi, int* count_lo, int* count_hi);
 ofm_status ofm_window_bisect(ofm_ctx* c, int i_lo, int i_hi, double* E_out);
+ofm_status ofm_window_size_estimate(ofm_ctx* c, int i_lo, double width, int* i_end);
 // eigenvectors for the m eigenvalues E (host, ascending) of the last bisection
 ofm_status ofm_window_vectors(ofm_ctx* c, int m, const double* E, double* C_out);
 ofm_status ofm_tridiag_persistent(ofm_ctx* c, double* A, int n, double* d, double* e, double* tau,
                                   double* pg);
 void launch_count_below(const double* d, const double* e, int n, double x0, double x1, int* out,
+                        cudaStream_t s);
+bool launch_window_size(const double* d, const double* e, int n, int i_lo, double width, int* out,
                         cudaStream_t s);
 bool launch_multisection(const double* d, const double* e, int n, int i_lo, int m, double* out,
                          cudaStream_t s);

@@ -683,6 +683,66 @@ __global__ void __launch_bounds__(32 * MS_W) multisection_kernel(const double* _
   }
   if (tid == 0) out[t] = 0.5 * (lo + hi);
 }
+// Size estimate of a window anchored at an index: FP32 multisection (one CTA
+// of 4 warps, 129 shifts per round) narrows eigenvalue i_lo to about 2e-5 of
+// the spectrum's scale, then one FP32 count at the bracket's top + width +
+// 4e-5 scale gives out[0] = an upper estimate of the index one past the
+// window.  FP32 counts can be off near eigenvalues, so the caller treats the
+// number as a guess and checks it in FP64.
+__global__ void __launch_bounds__(128) window_size_kernel(const double* __restrict__ d,
+                                                          const double* __restrict__ e, int n,
+                                                          int i_lo, double width, int* out) {
+  extern __shared__ float ws_smem[];
+  float* dsf = ws_smem;
+  float* e2f = ws_smem + n;
+  __shared__ int firstw[4];
+  __shared__ double gl[8];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double a = DBL_MAX, b = -DBL_MAX;
+  for (int i = tid; i < n; i += 128) {
+    const double e2 = (i < n - 1) ? e[i] * e[i] : 0.0;
+    dsf[i] = (float)d[i];
+    e2f[i] = (float)e2;
+    const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < n - 1 ? fabs(e[i]) : 0.0);
+    a = fmin(a, d[i] - r);
+    b = fmax(b, d[i] + r);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a = fmin(a, __shfl_xor_sync(0xffffffffu, a, o));
+    b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+  }
+  if (lane == 0) {
+    gl[warp] = a;
+    gl[4 + warp] = b;
+  }
+  __syncthreads();
+  a = fmin(fmin(gl[0], gl[1]), fmin(gl[2], gl[3]));
+  b = fmax(fmax(gl[4], gl[5]), fmax(gl[6], gl[7]));
+  const double wdt = fmax(fabs(a), fabs(b));
+  double lo = a - 1e-5 * wdt, hi = b + 1e-5 * wdt;
+  const float pivmin = 1e-30f;
+  for (int it = 0; it < 32 && hi - lo > 2e-5 * wdt; ++it) {
+    const double x = lo + (hi - lo) * (double)(tid + 1) / 129.0;
+    const int cnt = sturm_count_f32(dsf, e2f, n, (float)x, pivmin);
+    const unsigned ball = __ballot_sync(0xffffffffu, cnt > i_lo);
+    if (lane == 0) firstw[warp] = ball ? __ffs(ball) - 1 : 32;
+    __syncthreads();
+    int j = 128;
+    for (int w = 3; w >= 0; --w)
+      if (firstw[w] < 32) j = w * 32 + firstw[w];
+    __syncthreads();
+    const double nhi = (j == 128) ? hi : lo + (hi - lo) * (double)(j + 1) / 129.0;
+    const double nlo = (j == 128) ? lo + (hi - lo) * 128.0 / 129.0 : (j > 0 ? lo + (hi - lo) * (double)j / 129.0 : lo);
+    if (nlo == lo && nhi == hi) break;
+    lo = nlo;
+    hi = nhi;
+  }
+  if (tid == 0) {
+    const double top = hi + width + 4e-5 * wdt;
+    out[0] = (top >= b) ? n : sturm_count_f32(dsf, e2f, n, (float)top, pivmin);
+  }
+}
+
 }  // namespace ofm
 
 using namespace ofm;
@@ -792,5 +852,24 @@ bool launch_multisection(const double* d, const double* e, int n, int i_lo, int 
     multisection_kernel<2><<<m, 64, smem, s>>>(d, e, n, i_lo, m, out);
   else
     multisection_kernel<1><<<m, 32, smem, s>>>(d, e, n, i_lo, m, out);
+  return true;
+}
+
+// Estimate (see window_size_kernel) of one past the last index of the window
+// [E_{i_lo}, E_{i_lo} + width]; false when the tridiagonal is too long.
+bool launch_window_size(const double* d, const double* e, int n, int i_lo, double width, int* out,
+                        cudaStream_t s) {
+  const size_t smem = 2 * (size_t)n * sizeof(float);
+  if (smem > 200 * 1024) return false;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(window_size_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    attr = true;
+  }
+  window_size_kernel<<<1, 128, smem, s>>>(d, e, n, i_lo, width, out);
   return true;
 }

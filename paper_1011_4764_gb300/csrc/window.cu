@@ -518,6 +518,21 @@ ofm_status ofm_window_count(ofm_ctx* c, double lo, double hi, int* count_lo, int
   return OFM_OK;
 }
 
+// Upper estimate of one past the last index of [E_{i_lo}, E_{i_lo} + width]
+// from FP32 counts (a guess; the caller checks it with FP64 eigenvalues).
+ofm_status ofm_window_size_estimate(ofm_ctx* c, int i_lo, double width, int* i_end) {
+  int* dv = (int*)c->flag.p + 4;   // after the pivot flag and the two counts
+  KTimer kt(c, KC_BISECT);
+  if (!launch_window_size((const double*)c->w_d.p, (const double*)c->w_e.p, c->dense_n, i_lo,
+                          width, dv, c->stream)) {
+    *i_end = c->dense_n;   // too long to stage: take everything above i_lo
+    return OFM_OK;
+  }
+  OFM_CUDA(c, cudaGetLastError());
+  OFM_CUDA(c, cudaMemcpyAsync(i_end, dv, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  return sync_ctx(c, "window size estimate");
+}
+
 ofm_status ofm_window_bisect(ofm_ctx* c, int i_lo, int i_hi, double* E_out) {
   const int m = i_hi - i_lo;
   double* out = (double*)c->w_tmp.p;  // 2n doubles, m <= n

@@ -30,6 +30,7 @@ EXPORTS = [
     "ofm_get_dense_HS", "ofm_get_hphi", "ofm_window_eigs", "ofm_eigs_by_index",
     "ofm_set_dense_HS", "ofm_plan_pairs", "ofm_set_profiling", "ofm_get_kernel_stats",
     "ofm_pair_blocks_noalloc", "ofm_set_pair_cutoff", "ofm_select_states", "ofm_homo_lumo_gap",
+    "ofm_window_from_index",
 ]
 
 
@@ -108,6 +109,7 @@ def load_library(path: str = LIB_PATH):
         "ofm_set_pair_cutoff": ([P, DP, IP, D], I),
         "ofm_select_states": ([P, IP, IP], I),
         "ofm_homo_lumo_gap": ([P, D, DP, DP, DP, IP], I),
+        "ofm_window_from_index": ([P, I, D, I, DP, IP], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -287,6 +289,17 @@ class Context:
         if xyz.size == 0:
             xyz = np.zeros(3)
         self._check(self.lib.ofm_set_pair_cutoff(self.h, _dptr(xyz), _iptr(off), float(d_cut)))
+
+    # -- ofm_window_from_index
+    def window_from_index(self, i_lo, width, max_out=None):
+        """(E, n): E_{i_lo} and the later eigenvalues up to E_{i_lo} + width."""
+        if max_out is None:
+            max_out = sum(f.n_states for f in self.frags) or 1
+        out = np.zeros(max(1, max_out))
+        n = C.c_int()
+        self._check(self.lib.ofm_window_from_index(self.h, int(i_lo), float(width), int(max_out),
+                                                   _dptr(out), C.byref(n)))
+        return out[:min(n.value, max_out)].copy(), n.value
 
     # -- ofm_select_states
     def select_states(self, first, count):

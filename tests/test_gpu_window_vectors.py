@@ -93,3 +93,28 @@ def test_alkane_fp32_window_vectors_residual(ofm):
     scale = np.abs(Hd).max()
     assert np.max(np.abs(Hd @ C - Sd @ C * E)) < 1e-9 * scale
     assert np.max(np.abs(C.T @ Sd @ C - np.eye(m))) < 1e-9
+
+
+def test_window_from_index_matches_two_step_window(ofm):
+    """The index-anchored window equals E_i from ofm_eigs_by_index followed by
+    ofm_window_eigs on [E_i, E_i + width] (same multisection per index, so
+    the same values), for a narrow, a medium and a whole-spectrum width."""
+    wl = make_workload("tiny")
+    r = O.run_ofm(wl)
+    ctx = ofm.Context()
+    ctx.build_fragments(wl.grid, wl.V, wl.frags, storage="fp64")
+    for a, P in enumerate(r["Phis"]):
+        ctx.set_fragment_states(a, P)
+    ctx.assemble("fp64")
+    n = len(r["E"])
+    for i_lo, width in ((3, 0.05), (1, 0.5), (0, 1e3)):
+        e0 = ctx.eigs_by_index(i_lo, i_lo + 1)[0]
+        want, m = ctx.window_eigs(e0 - 1e-9, e0 + width)
+        got, k = ctx.window_from_index(i_lo, width)
+        assert k == m and k >= 1
+        assert np.array_equal(got, want)
+        ref = r["E"][i_lo:][r["E"][i_lo:] <= r["E"][i_lo] + width]
+        assert len(ref) == k and np.max(np.abs(got - ref)) < 1e-9
+    assert ctx.window_from_index(0, 1e3)[1] == n
+    with pytest.raises(ofm.OFMError):
+        ctx.window_from_index(n, 0.1)
