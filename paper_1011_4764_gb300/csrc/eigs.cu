@@ -50,7 +50,7 @@ struct EigWork {
   long long gpart = 0;
   long long gblk = 0;
   DevBuf d_efr, d_cta, buf[4], coef, theta, res, Cm, work, blocks, partials, d_gpairs, d_gpieces,
-      d_gitems, d_toff, d_rank, d_vmax, rpart;
+      d_gitems, d_toff, d_rank, d_vmax, rpart, xpart;
   double vlim[2] = {0.0, 0.0};        // max V, min V
   size_t rr_smem = 0, rot_smem = 0;   // dynamic shared memory of the two kernels
   int rr_threads = 256;                 // Rayleigh-Ritz CTA size
@@ -73,7 +73,7 @@ void ofm_eig_free(ofm_ctx* c) {
   DevBuf* bufs[] = {&w->d_efr, &w->d_cta, &w->buf[0], &w->buf[1], &w->buf[2], &w->buf[3],
                     &w->coef, &w->theta, &w->res, &w->Cm, &w->work, &w->blocks, &w->partials,
                     &w->d_gpairs, &w->d_gpieces, &w->d_gitems, &w->d_toff, &w->d_rank, &w->d_vmax,
-                    &w->rpart};
+                    &w->rpart, &w->xpart};
   for (DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   ofm_tc_plan_free(w->gtc);
@@ -839,103 +839,142 @@ __global__ void residual_reduce_kernel(const DevFrag* efr, const double* partial
   }
 }
 
-// First n columns of the block -> state storage, sign gauge applied.
-// 32 warps stride over the points; lanes are states.
+// Export of the first n_a Ritz vectors with the sign gauge (largest
+// |component| positive, ties to the lowest point index), in two launches over
+// (fragment, 32 columns, EXP_CHUNKS chunks of points): partial maxima per
+// chunk, then each CTA combines its columns' partials in chunk order (the
+// same winner as one pass over all points) and copies its chunk with the sign.
+// Coordinates are stepped without divisions and eight loads are in flight per
+// warp.
+constexpr int EXP_CHUNKS = 8;
+
+struct PointWalk {   // points t = t0, t0 + nw, ... of an ex x ey x ez box
+  int x, y, z, sx, sy, sz, ex, ey;
+  __device__ PointWalk(int t0, int nw, int ex_, int ey_) : ex(ex_), ey(ey_) {
+    x = t0 % ex;
+    y = (t0 / ex) % ey;
+    z = t0 / (ex * ey);
+    sx = nw % ex;
+    sy = (nw / ex) % ey;
+    sz = nw / (ex * ey);
+  }
+  __device__ void step() {
+    x += sx;
+    int c = 0;
+    if (x >= ex) { x -= ex; c = 1; }
+    y += sy + c;
+    c = 0;
+    if (y >= ey) { y -= ey; c = 1; }
+    z += sz + c;
+  }
+  __device__ int at(const DevFrag& D) const {
+    return ((z + D.lo[2]) * D.dext[1] + (y + D.lo[1])) * D.dext[0] + x + D.lo[0];
+  }
+};
+
 template <typename T>
-__global__ void __launch_bounds__(1024) export_states_kernel(const DevFrag* efr, const DevFrag* fr,
-                                                             const T* X, T* states) {
+__global__ void __launch_bounds__(256) export_max_kernel(const DevFrag* efr, const DevFrag* fr,
+                                                         const T* X, T* pmax, int* pidx, int mstride) {
   // magnitudes compared in the storage type: the same order as in FP64
-  __shared__ T bv[32][32];
-  __shared__ int bi[32][32];
-  __shared__ T sgn[32];
-  const int f = blockIdx.x;
+  __shared__ T bv[8][32];
+  __shared__ int bi[8][32];
+  const int f = blockIdx.x, chunk = blockIdx.z;
   const DevFrag E = efr[f];
   const DevFrag F = fr[f];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nw = (int)(blockDim.x >> 5);   // <= 32 warps (launch bound 1024)
   const int col = blockIdx.y * 32 + lane;
-  const int ex = F.ext[0], ey = F.ext[1];
   const int P = F.ext[0] * F.ext[1] * F.ext[2];
+  const int per = (P + EXP_CHUNKS - 1) / EXP_CHUNKS;
+  const int p0 = chunk * per, p1 = min(P, p0 + per);
   T best = T(-1);
-  int besti = 0;
-  // the warp's points t = warp, warp + nw, ... walked by stepping (x, y, z)
-  // with carries: no integer division per point
-  const int sx = nw % ex, sy = (nw / ex) % ey, sz = nw / (ex * ey);
-  auto start = [&](int& x, int& y, int& z) {
-    x = warp % ex;
-    y = (warp / ex) % ey;
-    z = warp / (ex * ey);
-  };
-  auto step = [&](int& x, int& y, int& z) {
-    x += sx;
-    int cy = 0;
-    if (x >= ex) { x -= ex; cy = 1; }
-    y += sy + cy;
-    int cz = 0;
-    if (y >= ey) { y -= ey; cz = 1; }
-    z += sz + cz;
-  };
-  // eight loads in flight per warp: a load, its compare and then the next
-  // load would pay an L2 round trip per point
-  constexpr int U = 8;
-  if (col < F.n) {
-    int x, y, z;
-    start(x, y, z);
-    for (int t0 = warp; t0 < P; t0 += U * nw) {
+  int besti = 0x7fffffff;
+  if (col < F.n && p0 + warp < p1) {
+    constexpr int U = 8;
+    PointWalk w(p0 + warp, 8, F.ext[0], F.ext[1]);
+    for (int t0 = p0 + warp; t0 < p1; t0 += U * 8) {
       T a[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         a[u] = T(-1);
-        if (t0 + u * nw < P) {
-          const int pd = ((z + E.lo[2]) * E.dext[1] + (y + E.lo[1])) * E.dext[0] + x + E.lo[0];
-          a[u] = fabs(X[E.off + (long long)pd * E.ld + col]);
-          step(x, y, z);
+        if (t0 + u * 8 < p1) {
+          a[u] = fabs(X[E.off + (long long)w.at(E) * E.ld + col]);
+          w.step();
         }
       }
 #pragma unroll
       for (int u = 0; u < U; ++u)
-        if (a[u] > best) {  // strictly greater, in stream order: the lowest index wins
+        if (a[u] > best) {  // strictly greater in stream order: the lowest index wins
           best = a[u];
-          besti = t0 + u * nw;
+          besti = t0 + u * 8;
         }
     }
   }
   bv[warp][lane] = best;
   bi[warp][lane] = besti;
   __syncthreads();
-  if (warp == 0) {
+  if (warp == 0 && col < F.n) {
     T b = bv[0][lane];
     int ib = bi[0][lane];
-    for (int w = 1; w < nw; ++w) {
-      if (bv[w][lane] > b || (bv[w][lane] == b && bi[w][lane] < ib)) {
-        b = bv[w][lane];
-        ib = bi[w][lane];
+    for (int v = 1; v < 8; ++v)
+      if (bv[v][lane] > b || (bv[v][lane] == b && bi[v][lane] < ib)) {
+        b = bv[v][lane];
+        ib = bi[v][lane];
       }
-    }
+    const long long o = ((long long)f * mstride + col) * EXP_CHUNKS + chunk;
+    pmax[o] = b;
+    pidx[o] = ib;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) export_copy_kernel(const DevFrag* efr, const DevFrag* fr,
+                                                          const T* X, const T* pmax,
+                                                          const int* pidx, int mstride, T* states) {
+  __shared__ T sgn[32];
+  const int f = blockIdx.x, chunk = blockIdx.z;
+  const DevFrag E = efr[f];
+  const DevFrag F = fr[f];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int col = blockIdx.y * 32 + lane;
+  const int ex = F.ext[0], ey = F.ext[1];
+  const int P = ex * ey * F.ext[2];
+  if (warp == 0) {
     T sg = T(1);
-    if (col < F.n && ib >= 0 && ib < P) {
-      const int x = ib % ex, y = (ib / ex) % ey, z = ib / (ex * ey);
-      const int pd = ((z + E.lo[2]) * E.dext[1] + (y + E.lo[1])) * E.dext[0] + x + E.lo[0];
-      sg = X[E.off + (long long)pd * E.ld + col] < T(0) ? T(-1) : T(1);
+    if (col < F.n) {
+      const long long o = ((long long)f * mstride + col) * EXP_CHUNKS;
+      T b = pmax[o];
+      int ib = pidx[o];
+      for (int k = 1; k < EXP_CHUNKS; ++k)
+        if (pmax[o + k] > b || (pmax[o + k] == b && pidx[o + k] < ib)) {
+          b = pmax[o + k];
+          ib = pidx[o + k];
+        }
+      if (ib >= 0 && ib < P) {
+        const int x = ib % ex, y = (ib / ex) % ey, z = ib / (ex * ey);
+        const int pd = ((z + E.lo[2]) * E.dext[1] + (y + E.lo[1])) * E.dext[0] + x + E.lo[0];
+        sg = X[E.off + (long long)pd * E.ld + col] < T(0) ? T(-1) : T(1);
+      }
     }
     sgn[lane] = sg;
   }
   __syncthreads();
   if (col >= F.n) return;
   const T s = sgn[lane];
-  int x, y, z;
-  start(x, y, z);
-  for (int t0 = warp; t0 < P; t0 += U * nw) {
+  const int per = (P + EXP_CHUNKS - 1) / EXP_CHUNKS;
+  const int p0 = chunk * per, p1 = min(P, p0 + per);
+  if (p0 + warp >= p1) return;
+  constexpr int U = 8;
+  PointWalk w(p0 + warp, 8, ex, ey);
+  for (int t0 = p0 + warp; t0 < p1; t0 += U * 8) {
     T v[U];
     int pf[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       pf[u] = -1;
-      if (t0 + u * nw < P) {
-        const int pe = ((z + E.lo[2]) * E.dext[1] + (y + E.lo[1])) * E.dext[0] + x + E.lo[0];
-        pf[u] = ((z + F.lo[2]) * F.dext[1] + (y + F.lo[1])) * F.dext[0] + x + F.lo[0];
-        v[u] = X[E.off + (long long)pe * E.ld + col];
-        step(x, y, z);
+      if (t0 + u * 8 < p1) {
+        v[u] = X[E.off + (long long)w.at(E) * E.ld + col];
+        pf[u] = w.at(F);
+        w.step();
       }
     }
 #pragma unroll
@@ -1381,14 +1420,24 @@ extern "C" ofm_status ofm_fragment_eigs(ofm_ctx* c, const ofm_eig_opts* opts, do
     xb = xo;
   }
   // export the first n_a Ritz vectors with the sign gauge
-  dim3 eg(nf, (w->mmax + 31) / 32);
-  { KTimer kt(c, KC_EXPORT);
-  if (fp64)
-    export_states_kernel<double><<<eg, 1024, 0, s>>>((const DevFrag*)w->d_efr.p, (const DevFrag*)c->d_frags.p,
-                                                    (const double*)w->buf[xb].p, (double*)c->states.p);
-  else
-    export_states_kernel<float><<<eg, 1024, 0, s>>>((const DevFrag*)w->d_efr.p, (const DevFrag*)c->d_frags.p,
-                                                   (const float*)w->buf[xb].p, (float*)c->states.p); }
+  dim3 eg(nf, (w->mmax + 31) / 32, EXP_CHUNKS);
+  { KTimer kt(c, KC_EXPORT, 2);
+  const size_t pe = (size_t)nf * w->mmax * EXP_CHUNKS;
+  OFM_TRY(ofm_ensure(c, w->xpart, pe * (sizeof(double) + sizeof(int)), "export partials"));
+  int* pidx = (int*)((double*)w->xpart.p + pe);
+  const DevFrag* ef = (const DevFrag*)w->d_efr.p;
+  const DevFrag* cf = (const DevFrag*)c->d_frags.p;
+  if (fp64) {
+    double* pm = (double*)w->xpart.p;
+    export_max_kernel<double><<<eg, 256, 0, s>>>(ef, cf, (const double*)w->buf[xb].p, pm, pidx, w->mmax);
+    export_copy_kernel<double><<<eg, 256, 0, s>>>(ef, cf, (const double*)w->buf[xb].p, pm, pidx,
+                                                  w->mmax, (double*)c->states.p);
+  } else {
+    float* pm = (float*)w->xpart.p;
+    export_max_kernel<float><<<eg, 256, 0, s>>>(ef, cf, (const float*)w->buf[xb].p, pm, pidx, w->mmax);
+    export_copy_kernel<float><<<eg, 256, 0, s>>>(ef, cf, (const float*)w->buf[xb].p, pm, pidx,
+                                                 w->mmax, (float*)c->states.p);
+  } }
   OFM_CUDA(c, cudaGetLastError());
   OFM_CUDA(c, cudaStreamSynchronize(s));
   double worst = 0.0;
