@@ -306,6 +306,14 @@ def run_ours(args):
     ctx.build_fragments(grid, V_dev, frags, storage=storage)
     info = ctx.plan_info()
     F = info["pair_flops"]
+    step(V_dev)
+    # measured choice of the assembly schedule (stencil form x points per
+    # work item), kept by the library for the steps below (same layout)
+    t_chunk, t_form, t_ms, t_times = ctx.autotune_assembly(args.precision, reps=3)
+    schedule = {"chunk_points": t_chunk, "stencil_form": ["register", "staged"][t_form - 1],
+                "assembly_ms": t_ms,
+                "candidates_ms": {"register": [round(float(t), 4) for t in t_times[0]],
+                                  "staged": [round(float(t), 4) for t in t_times[1]]}}
     for _ in range(args.warmup):
         step(V_dev)
 
@@ -400,6 +408,7 @@ def run_ours(args):
         "kernels": {k: {"row": s["row"], "launches": s["launches"] // K, "ms": s["ms"] / K}
                     for k, s in sorted(stats.items())},
         "assembly": {"ms": asm_ms, "tflops": F / (asm_ms * 1e-3) / 1e12 if asm_ms > 0 else None},
+        "assembly_schedule": schedule,
         "wall_s": wall,
         "gpu_launches": launches,
         "roofline": roof,

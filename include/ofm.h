@@ -153,6 +153,31 @@ ofm_status ofm_get_fragment_states(ofm_ctx* ctx, int a, double* phi_out, ofm_loc
  * storage.  Enqueued on the context stream; does not synchronise. */
 ofm_status ofm_assemble_HS(ofm_ctx* ctx, ofm_precision prec, const ofm_assemble_opts* opts);
 
+/* Result of ofm_autotune_assembly. */
+typedef struct {
+  int chunk_points;      /* chosen points per contraction work item */
+  int stencil_form;      /* chosen form of the H apply: 1 register, 2 staged (shared-memory planes) */
+  double ms;             /* its mean assembly time over the timed runs, milliseconds */
+  int n_tried;           /* candidates timed */
+} ofm_tune_result;
+
+/* Measuring autotuner of the assembly schedule of ofm_assemble_HS (the same
+ * computation in every candidate: the schedule moves work between launches
+ * and changes the order of the FP32/FP64 partial sums, nothing else).  Each
+ * candidate (stencil form 1 or 2) x (points per work item) is planned, run
+ * once, then run `reps` times between two CUDA events on the context stream;
+ * the fastest becomes the context's schedule, used by later ofm_assemble_HS
+ * calls whose chunk_points is 0, until ofm_build_fragments changes the layout
+ * (boxes, state counts, grid or storage).  chunks: n_chunks candidate sizes
+ * (> 0), or NULL for five: the planner's own size for this precision's
+ * contraction times 1/4, 1/2, 1, 2 and 4.  times_ms (host, nullable) gets
+ * 2 x n_cand mean times, form-major, -1 where the staged form does not fit.
+ * out (nullable) gets the choice.  Ends with one assembly of the chosen
+ * schedule and synchronises the stream.  Needs states; profiling must be off
+ * (OFM_ERR_STATE); reps >= 1 (OFM_ERR_INVALID). */
+ofm_status ofm_autotune_assembly(ofm_ctx* ctx, ofm_precision prec, const int* chunks, int n_chunks,
+                                 int reps, double* times_ms, ofm_tune_result* out);
+
 /* Distance cutoff on the pair list (Sec. III.C, "Choice of the distance
  * cutoff": a pair of fragments is included when the minimal distance between
  * an atom of one and an atom of the other is below d_cut).  The atoms of

@@ -170,11 +170,14 @@ extern "C" const char* ofm_last_error(const ofm_ctx* c) {
 // with work items of about c->asm_chunk points (0: the planner's choice,
 // about 8 items per SM on CUDA cores, 4 per SM on tensor cores).  Any
 // captured assembly graph refers to the old plan and is dropped.
+static long long planner_chunk(const ofm_ctx* c) {
+  return std::min<long long>(std::max<long long>(256, c->kh / (8 * 152)), 16384);
+}
+
 static ofm_status plan_contraction(ofm_ctx* c) {
   drop_graphs(c);
   const size_t es = elem_size(c);
-  long long chunk = c->asm_chunk > 0 ? c->asm_chunk : std::max<long long>(256, c->kh / (8 * 152));
-  if (c->asm_chunk <= 0) chunk = std::min<long long>(chunk, 16384);
+  const long long chunk = c->asm_chunk > 0 ? c->asm_chunk : planner_chunk(c);
   c->simt_chunk = chunk;
   make_items_simt(c->frags, c->pairs, c->simt_tile, chunk, c->simt_pairs, c->simt_pieces,
                   c->simt_items, c->simt_partial_elems);
@@ -249,7 +252,11 @@ static ofm_status layout_fragments(ofm_ctx* c) {
   for (int d = 0; d < 3; ++d) same = same && c->laid_grid.n[d] == c->grid.n[d];
   for (size_t a = 0; same && a < c->in_frags.size(); ++a)
     same = std::memcmp(&c->laid_frags[a], &c->in_frags[a], sizeof(ofm_fragment)) == 0;
-  if (!same) ofm_eig_free(c);
+  if (!same) {
+    ofm_eig_free(c);
+    c->stencil_form = 0;
+    c->tuned_chunk = 0;
+  }
   c->laid_frags = c->in_frags;
   c->laid_grid = c->grid;
   c->laid_storage = (int)c->storage;
@@ -279,8 +286,8 @@ static ofm_status layout_fragments(ofm_ctx* c) {
   OFM_CUDA(c, cudaMemcpyAsync(c->d_frags.p, c->frags.data(), sizeof(DevFrag) * n_frag,
                               cudaMemcpyHostToDevice, c->stream));
   // H-apply launch: 2-D grid (chunks of the largest fragment x fragments)
-  c->agrid = apply_grid(c->frags, es == 8, false);
-  c->asm_chunk = 0;
+  c->agrid = apply_grid(c->frags, es == 8, false, c->stencil_form);
+  c->asm_chunk = c->tuned_chunk;
   OFM_TRY(plan_contraction(c));
   // host copies of tables are read back by later calls: wait for the uploads
   return sync(c, "fragment layout");
@@ -524,9 +531,10 @@ extern "C" ofm_status ofm_assemble_HS(ofm_ctx* c, ofm_precision prec, const ofm_
   if (prec < OFM_PREC_FP64 || prec > OFM_PREC_BF16X3) return ofm_fail(c, OFM_ERR_INVALID, "unknown precision");
   if (prec != OFM_PREC_FP64 && c->storage == OFM_STORE_FP64)
     return ofm_fail(c, OFM_ERR_INVALID, "FP32 and tensor-core contractions need FP32 storage");
-  const long long chunk = opts ? opts->chunk_points : 0;
+  long long chunk = opts ? opts->chunk_points : 0;
   const bool use_graph = opts ? opts->use_graph != 0 : true;
   if (chunk < 0) return ofm_fail(c, OFM_ERR_INVALID, "chunk_points must be >= 0");
+  if (chunk == 0) chunk = c->tuned_chunk;
   if (chunk != c->asm_chunk) {
     c->asm_chunk = chunk;
     OFM_TRY(plan_contraction(c));
@@ -550,6 +558,102 @@ extern "C" ofm_status ofm_assemble_HS(ofm_ctx* c, ofm_precision prec, const ofm_
   OFM_TRY(enqueue_assembly(c, prec));
   c->assembled = true;
   return OFM_OK;
+}
+
+// Measuring autotuner of the assembly schedule: every (stencil form, points
+// per work item) candidate is planned, run once (which captures its graph)
+// and then timed over `reps` runs with CUDA events on the ctx stream; the
+// fastest becomes the ctx's schedule.  The blocks are recomputed with it at
+// the end, so the ctx holds an assembly of the chosen plan.
+extern "C" ofm_status ofm_autotune_assembly(ofm_ctx* c, ofm_precision prec, const int* chunks,
+                                            int n_chunks, int reps, double* times_ms,
+                                            ofm_tune_result* out) {
+  if (!c) return OFM_ERR_INVALID;
+  if (!c->built) return ofm_fail(c, OFM_ERR_STATE, "ofm_build_fragments must come first");
+  if (!c->have_states) return ofm_fail(c, OFM_ERR_STATE, "fragment states are not set (ofm_fragment_eigs or ofm_set_fragment_states)");
+  if (c->prof.on) return ofm_fail(c, OFM_ERR_STATE, "turn profiling off while tuning");
+  if (reps < 1) return ofm_fail(c, OFM_ERR_INVALID, "reps must be >= 1");
+  if (chunks && n_chunks < 1) return ofm_fail(c, OFM_ERR_INVALID, "n_chunks must be >= 1");
+  std::vector<long long> cand;
+  if (chunks) {
+    for (int i = 0; i < n_chunks; ++i) {
+      if (chunks[i] <= 0) return ofm_fail(c, OFM_ERR_INVALID, "chunk candidates must be > 0");
+      cand.push_back(chunks[i]);
+    }
+  } else {
+    // the planner's own size for this contraction, and 1/4 .. 4 times it
+    const bool tc = prec >= OFM_PREC_TF32;
+    const long long base = tc ? std::max<long long>(1024, c->kh / (4 * 152)) : planner_chunk(c);
+    for (int m = -2; m <= 2; ++m)
+      cand.push_back(std::max<long long>(64, m < 0 ? base >> -m : base << m));
+  }
+  const int nc = (int)cand.size();
+  const size_t es = elem_size(c);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  OFM_CUDA(c, cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return ofm_cuda_check(c, cudaGetLastError(), "cudaEventCreate");
+  }
+  double best = -1.0;
+  int best_form = 1;
+  long long best_chunk = cand[0];
+  int tried = 0;
+  ofm_status st = OFM_OK;
+  ofm_assemble_opts o{};
+  o.use_graph = 1;
+  for (int form = 1; form <= 2 && st == OFM_OK; ++form) {
+    const ApplyGrid g = apply_grid(c->frags, es == 8, false, form);
+    const bool fits = form == 1 || g.staged;
+    for (int i = 0; i < nc && st == OFM_OK; ++i) {
+      if (times_ms) times_ms[(form - 1) * nc + i] = -1.0;
+      if (!fits) continue;
+      drop_graphs(c);
+      c->agrid = g;
+      c->stencil_form = form;
+      o.chunk_points = (int)cand[i];
+      st = ofm_assemble_HS(c, prec, &o);   // plans, captures and runs once
+      if (st != OFM_OK) break;
+      if ((st = ofm_wait_status(c)) != OFM_OK) break;
+      if (cudaEventRecord(e0, c->stream) != cudaSuccess) { st = ofm_cuda_check(c, cudaGetLastError(), "event"); break; }
+      for (int r = 0; r < reps && st == OFM_OK; ++r) st = ofm_assemble_HS(c, prec, &o);
+      if (st != OFM_OK) break;
+      if (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+        st = ofm_cuda_check(c, cudaGetLastError(), "autotune timing");
+        break;
+      }
+      if ((st = ofm_wait_status(c)) != OFM_OK) break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      const double t = (double)ms / reps;
+      if (times_ms) times_ms[(form - 1) * nc + i] = t;
+      ++tried;
+      if (best < 0.0 || t < best) {
+        best = t;
+        best_form = form;
+        best_chunk = cand[i];
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  // the chosen schedule (the default one after a failure), then one assembly
+  // with it
+  drop_graphs(c);
+  c->stencil_form = st == OFM_OK ? best_form : 0;
+  c->tuned_chunk = st == OFM_OK ? best_chunk : 0;
+  c->agrid = apply_grid(c->frags, es == 8, false, c->stencil_form);
+  c->asm_chunk = -1;   // re-plan at the next assembly
+  if (st != OFM_OK) return st;
+  OFM_TRY(ofm_assemble_HS(c, prec, nullptr));
+  OFM_TRY(ofm_wait_status(c));
+  if (out) {
+    out->chunk_points = (int)best_chunk;
+    out->stencil_form = best_form;
+    out->ms = best;
+    out->n_tried = tried;
+  }
+  return sync(c, "autotuned assembly");
 }
 
 extern "C" ofm_status ofm_get_pairs(ofm_ctx* c, int* n_pairs, int* pair_ab) {

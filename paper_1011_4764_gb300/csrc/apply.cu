@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(STG_THREADS) apply_staged_kernel(
 // SM, else one) and at most STG_EPT elements per thread, and the chunk count
 // fills about two resident waves of the GB300 (152 SMs).  Register form (fallback when even one row does not fit):
 // x covers the (x, y, column group) elements of the largest plane.
-ApplyGrid apply_grid(const std::vector<DevFrag>& fr, bool fp64, bool filter) {
+ApplyGrid apply_grid(const std::vector<DevFrag>& fr, bool fp64, bool filter, int form) {
   const int vn = fp64 ? 2 : 4;
   const int es = fp64 ? 8 : 4;
   const int sms = 152;
@@ -357,9 +357,11 @@ ApplyGrid apply_grid(const std::vector<DevFrag>& fr, bool fp64, bool filter) {
     rowQ = std::max(rowQ, (long long)(filter ? f.ext[0] : f.dext[0]) * (f.ld / vn));
   }
   ApplyGrid g;
-  // staged form, where OFM_STENCIL=staged asks for it
-  const char* form = std::getenv("OFM_STENCIL");
-  const bool try_staged = form != nullptr && std::strcmp(form, "staged") == 0;
+  // staged form where the caller (form 2), or with form 0 OFM_STENCIL=staged,
+  // asks for it
+  const char* env = std::getenv("OFM_STENCIL");
+  const bool try_staged =
+      form == 2 || (form == 0 && env != nullptr && std::strcmp(env, "staged") == 0);
   const long long budgets[2] = {110 * 1024, 200 * 1024};
   for (int bi = 0; bi < 2 && try_staged && !g.staged; ++bi) {
     int best = 0;

@@ -95,7 +95,9 @@ struct ApplyGrid {
   bool staged = false;
   int x = 1, z = 1, zc = 1, ty = 1, smem = 0;
 };
-ApplyGrid apply_grid(const std::vector<DevFrag>& fr, bool fp64, bool filter);
+// form: 0 register form unless OFM_STENCIL=staged, 1 register form, 2 staged
+// form where it fits (else the register form)
+ApplyGrid apply_grid(const std::vector<DevFrag>& fr, bool fp64, bool filter, int form = 0);
 // flag: set to 1 when a bounded wait of the staged form gives up
 void launch_apply_global(const DevFrag* d_fr, int nfrag, const ApplyGrid& g, const void* V,
                          const void* states, void* hphi, const int gn[3], double h, bool fp64,
@@ -195,6 +197,10 @@ struct ofm_ctx {
   std::vector<long long> blk_off;   // per pair
   long long blk_elems = 0;
   ofm::ApplyGrid agrid;                // launch shape of the a1 stencil
+  // assembly schedule chosen by ofm_autotune_assembly (kept while the layout
+  // stays): stencil form (0: default) and points per work item (0: planner)
+  int stencil_form = 0;
+  long long tuned_chunk = 0;
 
   // device buffers
   ofm::DevBuf V, states, hphi, d_frags, d_pairs, d_pieces, d_items, partials,

@@ -30,7 +30,7 @@ EXPORTS = [
     "ofm_get_dense_HS", "ofm_get_hphi", "ofm_window_eigs", "ofm_eigs_by_index",
     "ofm_set_dense_HS", "ofm_plan_pairs", "ofm_set_profiling", "ofm_get_kernel_stats",
     "ofm_pair_blocks_noalloc", "ofm_set_pair_cutoff", "ofm_select_states", "ofm_homo_lumo_gap",
-    "ofm_window_from_index",
+    "ofm_window_from_index", "ofm_autotune_assembly",
 ]
 
 
@@ -53,6 +53,11 @@ class ofm_eig_opts(C.Structure):
 
 class ofm_assemble_opts(C.Structure):
     _fields_ = [("chunk_points", C.c_int), ("use_graph", C.c_int)]
+
+
+class ofm_tune_result(C.Structure):
+    _fields_ = [("chunk_points", C.c_int), ("stencil_form", C.c_int), ("ms", C.c_double),
+                ("n_tried", C.c_int)]
 
 
 class ofm_plan_info(C.Structure):
@@ -110,6 +115,7 @@ def load_library(path: str = LIB_PATH):
         "ofm_select_states": ([P, IP, IP], I),
         "ofm_homo_lumo_gap": ([P, D, DP, DP, DP, IP], I),
         "ofm_window_from_index": ([P, I, D, I, DP, IP], I),
+        "ofm_autotune_assembly": ([P, I, IP, I, I, DP, C.POINTER(ofm_tune_result)], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -272,6 +278,20 @@ class Context:
     def assemble(self, precision="fp32", chunk_points=0, use_graph=True):
         o = ofm_assemble_opts(chunk_points, 1 if use_graph else 0)
         self._check(self.lib.ofm_assemble_HS(self.h, PREC[precision], C.byref(o)))
+
+    # -- ofm_autotune_assembly
+    def autotune_assembly(self, precision="fp32", chunks=None, reps=3):
+        """Times every (stencil form, chunk) candidate and keeps the fastest.
+        Returns (chunk_points, stencil_form, ms, times) with times a
+        (2, n_candidates) array of mean milliseconds (-1: form does not fit)."""
+        cand = None if chunks is None else np.ascontiguousarray(chunks, dtype=np.int32)
+        nc = 5 if cand is None else len(cand)
+        times = np.full(2 * nc, -1.0)
+        r = ofm_tune_result()
+        self._check(self.lib.ofm_autotune_assembly(
+            self.h, PREC[precision], None if cand is None else _iptr(cand), nc, int(reps),
+            _dptr(times), C.byref(r)))
+        return r.chunk_points, r.stencil_form, r.ms, times.reshape(2, nc)
 
     # -- ofm_set_pair_cutoff
     def set_pair_cutoff(self, atoms, d_cut):
