@@ -506,7 +506,7 @@ constexpr int RJ = 10;   // columns per thread and column block (4 groups x 10 =
 
 template <typename T>
 __global__ void __launch_bounds__(256) rotate_kernel(const DevFrag* efr, const T* Y, T* Xo,
-                                                     const T* HY, T* HXo, const double* Cm,
+                                                     const T* HY, const double* Cm,
                                                      long long cstride, const int* rank,
                                                      const double* theta, const long long* toff,
                                                      double* partial, int mstride,
@@ -595,7 +595,6 @@ __global__ void __launch_bounds__(256) rotate_kernel(const DevFrag* efr, const T
           }
         }
         ys[pl * ms + j] = xv;
-        hs[pl * ms + j] = hv;
         // residual of this output, summed over the warp's 32 points by
         // shuffles, then one shared-memory atomic per warp and column
         const T d = pd >= 0 ? hv - (T)theta[toff[f] + j] * xv : T(0);
@@ -609,10 +608,7 @@ __global__ void __launch_bounds__(256) rotate_kernel(const DevFrag* efr, const T
         const int pdo = pds[pp];
         if (pdo < 0) continue;
         const long long a = F.off + (long long)pdo * F.ld;
-        for (int k = jb + lane; k < jb + jn; k += 32) {
-          Xo[a + k] = ys[pp * ms + k];
-          HXo[a + k] = hs[pp * ms + k];
-        }
+        for (int k = jb + lane; k < jb + jn; k += 32) Xo[a + k] = ys[pp * ms + k];
       }
     }
     __syncthreads();
@@ -634,7 +630,7 @@ constexpr int RJB = 4 * RJ;  // columns per column block
 constexpr int RM4 = 52;      // widest block (m) this form takes
 
 __global__ void __launch_bounds__(256, 2) rotate4_kernel(const DevFrag* efr, const float* Y, float* Xo,
-                                                         const float* HY, float* HXo,
+                                                         const float* HY,
                                                          const double* Cm, long long cstride,
                                                          const int* rank, const double* theta,
                                                          const long long* toff, double* partial,
@@ -764,7 +760,7 @@ __global__ void __launch_bounds__(256, 2) rotate4_kernel(const DevFrag* efr, con
         if (c >= jn) continue;
         const int j = jb + c;
         const float th = (float)theta[toff[f] + j];
-        float xo[4], ho[4];
+        float xo[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           float xv = ax[q][i], hv = ah[q][i];
@@ -783,10 +779,8 @@ __global__ void __launch_bounds__(256, 2) rotate4_kernel(const DevFrag* efr, con
             rsum[i] = fmaf(d, d, rsum[i]);
           }
           xo[q] = xv;
-          ho[q] = hv;
         }
         *reinterpret_cast<float4*>(ys + (size_t)j * RT4 + 4 * pg) = make_float4(xo[0], xo[1], xo[2], xo[3]);
-        *reinterpret_cast<float4*>(hs + (size_t)j * RT4 + 4 * pg) = make_float4(ho[0], ho[1], ho[2], ho[3]);
       }
       __syncthreads();
       // write the block's columns of point t0 + tid back, 16 bytes at a time
@@ -798,14 +792,8 @@ __global__ void __launch_bounds__(256, 2) rotate4_kernel(const DevFrag* efr, con
             *reinterpret_cast<float4*>(Xo + a + k) =
                 make_float4(ys[(size_t)k * RT4 + tid], ys[(size_t)(k + 1) * RT4 + tid],
                             ys[(size_t)(k + 2) * RT4 + tid], ys[(size_t)(k + 3) * RT4 + tid]);
-            *reinterpret_cast<float4*>(HXo + a + k) =
-                make_float4(hs[(size_t)k * RT4 + tid], hs[(size_t)(k + 1) * RT4 + tid],
-                            hs[(size_t)(k + 2) * RT4 + tid], hs[(size_t)(k + 3) * RT4 + tid]);
           } else {
-            for (int kk = k; kk < je; ++kk) {
-              Xo[a + kk] = ys[(size_t)kk * RT4 + tid];
-              HXo[a + kk] = hs[(size_t)kk * RT4 + tid];
-            }
+            for (int kk = k; kk < je; ++kk) Xo[a + kk] = ys[(size_t)kk * RT4 + tid];
           }
         }
       }
@@ -1097,7 +1085,7 @@ static ofm_status eig_setup(ofm_ctx* c, int guard_opt) {
     w->filter_b3 += P * (3.0 * E.n + 1.0) * es;
     w->gram_bytes += P * 2.0 * E.n * es;
     w->gram_flops += 2.0 * P * E.n * 2.0 * E.n;
-    w->rot_bytes += P * 4.0 * E.n * es;
+    w->rot_bytes += P * 3.0 * E.n * es;   // Y and H Y in, X out
     w->rot_flops += 2.0 * 2.0 * P * E.n * E.n;
   }
   // Gram plan: self pairs over the interior box, chunks of ~1024 points
@@ -1186,8 +1174,11 @@ static ofm_status eig_setup(ofm_ctx* c, int guard_opt) {
   return OFM_OK;
 }
 
-// Gram blocks of (Y, HY), Rayleigh-Ritz, rotation into (xo, hxo), residuals.
-static ofm_status eig_rr(ofm_ctx* c, int y, int hy, int xo, int hxo, unsigned long long salt) {
+// Gram blocks of (Y, HY), Rayleigh-Ritz, rotation of Y into xo, residuals.
+// H X = (H Y) C is formed only for the residual norms, in registers: the
+// next filter starts from X alone and the export reads X, so it is never
+// stored.
+static ofm_status eig_rr(ofm_ctx* c, int y, int hy, int xo, unsigned long long salt) {
   EigWork* w = c->eig;
   const bool fp64 = c->storage == OFM_STORE_FP64;
   const int nf = c->nfrag;
@@ -1224,21 +1215,21 @@ static ofm_status eig_rr(ofm_ctx* c, int y, int hy, int xo, int hxo, unsigned lo
   if (fp64)
     rotate_kernel<double><<<g, 256, w->rot_smem, s>>>((const DevFrag*)w->d_efr.p, (const double*)w->buf[y].p,
                                                (double*)w->buf[xo].p, (const double*)w->buf[hy].p,
-                                               (double*)w->buf[hxo].p, (const double*)w->Cm.p, mm,
+                                               (const double*)w->Cm.p, mm,
                                                (const int*)w->d_rank.p, (const double*)w->theta.p,
                                                (const long long*)w->d_toff.p, (double*)w->rpart.p,
                                                w->mmax, salt);
   else if (w->rot4)
     rotate4_kernel<<<g, 256, w->rot_smem, s>>>((const DevFrag*)w->d_efr.p, (const float*)w->buf[y].p,
                                                (float*)w->buf[xo].p, (const float*)w->buf[hy].p,
-                                               (float*)w->buf[hxo].p, (const double*)w->Cm.p, mm,
+                                               (const double*)w->Cm.p, mm,
                                                (const int*)w->d_rank.p, (const double*)w->theta.p,
                                                (const long long*)w->d_toff.p, (double*)w->rpart.p,
                                                w->mmax, salt);
   else
     rotate_kernel<float><<<g, 256, w->rot_smem, s>>>((const DevFrag*)w->d_efr.p, (const float*)w->buf[y].p,
                                               (float*)w->buf[xo].p, (const float*)w->buf[hy].p,
-                                              (float*)w->buf[hxo].p, (const double*)w->Cm.p, mm,
+                                              (const double*)w->Cm.p, mm,
                                               (const int*)w->d_rank.p, (const double*)w->theta.p,
                                               (const long long*)w->d_toff.p, (double*)w->rpart.p,
                                               w->mmax, salt);
@@ -1314,7 +1305,7 @@ extern "C" ofm_status ofm_fragment_eigs(ofm_ctx* c, const ofm_eig_opts* opts, do
   } else {
     apply_block(c, 0, -1, 3, d_plain);
   }
-  OFM_TRY(eig_rr(c, 0, 3, 1, 2, 0x1234ULL + o.seed));
+  OFM_TRY(eig_rr(c, 0, 3, 1, 0x1234ULL + o.seed));
   int xb = 1;
   std::vector<double> th(w->tsum), rs(w->tsum);
   const double bup = 6.0 / (c->grid.h * c->grid.h) + w->vlim[0];
@@ -1415,8 +1406,7 @@ extern "C" ofm_status ofm_fragment_eigs(ofm_ctx* c, const ofm_eig_opts* opts, do
       apply_block(c, cur, -1, hy, d_plain);
     }
     const int xo = other(cur, hy);
-    const int hxo = other(cur, hy, xo);
-    OFM_TRY(eig_rr(c, cur, hy, xo, hxo, 0x9876ULL * (it + 1) + o.seed));
+    OFM_TRY(eig_rr(c, cur, hy, xo, 0x9876ULL * (it + 1) + o.seed));
     xb = xo;
   }
   // export the first n_a Ritz vectors with the sign gauge
