@@ -255,6 +255,23 @@ def run_reference(args):
 
 # ---------------------------------------------------------------- our arm --
 
+def job_time_ms(t_ms, dist, device):
+    """The slowest rank's timed-region milliseconds (every rank calls this;
+    dist None: one process)."""
+    if dist is None:
+        return float(t_ms)
+    import torch
+    t = torch.tensor([float(t_ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, flops_per_step, steps, t_ms):
+    """Whole-job TFLOP/s: the pair flops every rank's replica computed in its
+    K steps over the slowest rank's time."""
+    return world * flops_per_step * steps / (t_ms * 1e-3) / 1e12
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -360,14 +377,10 @@ def run_ours(args):
     barrier()
     prof_ms, _, stats, _ = timed_steps(True)
     barrier()
-    t_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([t_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_ms = float(t.item())
+    t_ms = job_time_ms(sum(step_ms), dist, dev)
     K = args.steps
     ms_per_step = t_ms / K
-    value = world * F * K / (t_ms * 1e-3) / 1e12
+    value = job_value(world, F, K, t_ms)
 
     rows = {}
     for name, s in stats.items():
@@ -400,7 +413,7 @@ def run_ours(args):
                    "window": f"{rule.kind} width {rule.width} Ha",
                    "l2": "flushed by a 512 MiB device write before every step (untimed)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "value_profiled": world * F * K / (sum(prof_ms) * 1e-3) / 1e12,
+        "value_profiled": job_value(world, F, K, sum(prof_ms)),
         "profile_pass": "rows_ms, kernels, roofline and rooflines come from a second pass of the same "
                         "K steps with per-class CUDA events (value_profiled is its throughput); value "
                         "and gpu_launches come from the unprofiled timed pass",

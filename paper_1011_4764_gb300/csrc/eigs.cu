@@ -152,16 +152,6 @@ __global__ void init_random_kernel(const DevFrag* fr, const int* cta_start, int 
 // Round-robin schedule (circle method): index ne-1 stays, the others
 // rotate; round r pairs (r, ne-1) and ((r+k) mod (ne-1), (r-k) mod (ne-1)).
 // Every pair meets once per sweep and the pairs of a round are disjoint.
-__device__ __forceinline__ void rr_pair(int r, int k, int ne, int& p, int& q) {
-  const int M = ne - 1;
-  if (k == 0) {
-    p = r;
-    q = M;
-  } else {
-    p = (r + k) % M;
-    q = (r - k + M) % M;
-  }
-}
 
 template <typename T> struct Eps;
 template <> struct Eps<float> { static constexpr double v = 6.0e-8; };
@@ -170,8 +160,9 @@ template <> struct Eps<double> { static constexpr double v = 1.1e-16; };
 // Cyclic parallel Jacobi on the symmetric n x n matrix A (leading dim lda),
 // accumulating the rotations into V (which must hold the identity or a
 // start basis).  Round-robin pairing: n_even/2 disjoint rotations per round.
-// A and V live in shared memory when they fit, so a round costs three CTA
-// barriers and no global-memory round trips.  Stops when the off-diagonal
+// A and V live in shared memory when they fit, so a round costs two CTA
+// barriers (after the rows, after the columns) and no global-memory round
+// trips.  Stops when the off-diagonal
 // mass is at the rounding level of an n x n matrix or a sweep rotated
 // nothing (elements below rounding relative to their diagonal pair are
 // left alone).
@@ -219,32 +210,47 @@ __device__ void cta_jacobi(T* A, T* V, int n, int lda, int* perm, T* cs, double*
     if (done) break;
     const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
     for (int r = 0; r < ne - 1; ++r) {
-      // angles of the round's disjoint pairs; the pairs go to perm[] so the
-      // updates below need no index arithmetic
-      for (int k = tid; k < half; k += nt) {
+      // rows p, q: one warp per pair.  The warp forms its pair's angle itself
+      // (every lane the same arithmetic) and goes on to the row update, so
+      // the angle needs no phase or barrier of its own; perm[] and cs[] carry
+      // the pairs and angles to the column phase.  With d = a_qq - a_pp,
+      //   t = sgn(d) 2 a_pq / (|d| + sqrt(d^2 + 4 a_pq^2))
+      // is the smaller root of t^2 + 2 theta t - 1 = 0, theta = d / (2 a_pq)
+      // (the classical cyclic-Jacobi tangent), with one division and one
+      // square root fewer than forming theta first.
+      for (int k = warp; k < half; k += nwarps) {
         int p, q;
-        rr_pair(r, k, ne, p, q);
-        perm[k] = p | (q << 16);
+        {   // the round-robin pairing without integer division
+          const int M = ne - 1;
+          if (k == 0) {
+            p = r;
+            q = M;
+          } else {
+            p = r + k;
+            if (p >= M) p -= M;
+            q = r - k;
+            if (q < 0) q += M;
+          }
+        }
         T c = 1, s = 0;
         if (p < n && q < n) {
           const T apq = A[p * lda + q];
           const T app = A[p * lda + p], aqq = A[q * lda + q];
-          if (fabs(apq) > fmax(T(2) * eps_t * sqrt(fabs(app * aqq)), floor_t)) {
-            red[65] = 1.0;
-            const T th = (aqq - app) / (T(2) * apq);
-            const T t = (th >= T(0) ? T(1) : T(-1)) / (fabs(th) + sqrt(th * th + T(1)));
+          const T thr = fmax(T(4) * eps_t * eps_t * fabs(app * aqq), floor_t * floor_t);
+          if (apq * apq > thr) {
+            if (lane == 0) red[65] = 1.0;
+            const T d = aqq - app;
+            const T t = (d >= T(0) ? T(2) : T(-2)) * apq / (fabs(d) + sqrt(d * d + T(4) * apq * apq));
             c = T(1) / sqrt(t * t + T(1));
             s = t * c;
           }
         }
-        cs[2 * k] = c;
-        cs[2 * k + 1] = s;
-      }
-      __syncthreads();
-      // rows p, q: one warp per pair, lanes along the row
-      for (int k = warp; k < half; k += nwarps) {
-        const int pq = perm[k], p = pq & 0xffff, q = pq >> 16;
-        const T c = cs[2 * k], s = cs[2 * k + 1];
+        if (lane == 0) {
+          perm[k] = p | (q << 16);
+          cs[2 * k] = c;
+          cs[2 * k + 1] = s;
+        }
+        __syncwarp();   // every lane has read a_pq, a_pp, a_qq before the rows change
         if (p >= n || q >= n || s == T(0)) continue;   // uniform over the warp
         for (int j = lane; j < n; j += 32) {
           const T ap = A[p * lda + j], aq = A[q * lda + j];
@@ -1250,9 +1256,9 @@ static void apply_block(ofm_ctx* c, int in, int prev, int out, const double* coe
   c->stencil_check = true;
 }
 
-static int other(int a, int b, int c2 = -1) {
+static int other(int a, int b) {
   for (int i = 0; i < 4; ++i)
-    if (i != a && i != b && i != c2) return i;
+    if (i != a && i != b) return i;
   return -1;
 }
 
