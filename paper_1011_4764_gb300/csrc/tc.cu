@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1) tc_contract_kernel(
       const int npts = (it.r1 - it.r0) * lenx;
       for (int k0 = 0; k0 < npts; k0 += span, ++gr) {
         const int s = gr % nraw, u = gr / nraw;
-        if (u > 0) {   // lane 0 waits; the verdict is the warp's (uniform control flow)
+        if (u > 0) {   // lane 0 waits; the outcome is the warp's (uniform control flow)
           bool w = true;
           if (lane == 0) w = wait(&raw_empty[s], (uint32_t)((u - 1) & 1));
           ok = __shfl_sync(0xffffffffu, w ? 1 : 0, 0) != 0;
@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1) tc_contract_kernel(
       const float inv_a = 1.0f / (float)A.n, inv_n = 1.0f / (float)N;
       for (int k0 = 0; k0 < npts && ok; k0 += span, ++gr) {
         const int s = gr % nraw, u = gr / nraw;
-        // every lane waits (it reads the copied data); the verdict is the warp's
+        // every lane waits (it reads the copied data); the outcome is the warp's
         ok = __all_sync(0xffffffffu, wait(&raw_full[s], (uint32_t)(u & 1)));
         if (!ok) break;
         const int nkr = min(span, npts - k0);
