@@ -28,6 +28,7 @@
 
 #include <algorithm>
 #include <cfloat>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <vector>
@@ -289,7 +290,8 @@ constexpr int RR_MAX_THREADS = 640;
 // directions give zero columns), theta (m; dropped directions repeat the
 // largest kept value), rank (number of kept directions).
 // Work matrices A, U, W (row stride ld) and vectors D, sig, idx live in
-// dynamic shared memory (ld = m + 1) or, for large m, in `work` (ld = m).
+// dynamic shared memory (ld = the odd one of m + 1, m + 2: column walks across
+// the warp hit distinct banks) or, for large m, in `work` (ld = m).
 template <typename T>
 __global__ void __launch_bounds__(RR_MAX_THREADS) rayleigh_ritz_kernel(const DevFrag* efr, const DevPair* gp,
                                                             const double* blocks, T* work,
@@ -307,7 +309,7 @@ __global__ void __launch_bounds__(RR_MAX_THREADS) rayleigh_ritz_kernel(const Dev
   const int tid = threadIdx.x, nt = blockDim.x;
   const double* Kb = blocks + gp[f].blk_off;
   const double* Gb = Kb + (long long)m * m;
-  const int ld = use_smem ? m + 1 : m;
+  const int ld = use_smem ? m + 1 + (m & 1) : m;
   T* A = use_smem ? reinterpret_cast<T*>(rr_raw) : work + f * wstride;
   T* U = A + (long long)m * ld;
   T* W = U + (long long)m * ld;
@@ -502,7 +504,8 @@ __global__ void __launch_bounds__(RR_MAX_THREADS) rayleigh_ritz_kernel(const Dev
 // get fresh random values and H X = 0), plus per-block partial sums of
 // (HX_new - theta X_new)^2 per column for the residual norms.
 // A CTA takes tiles of RT points: their rows of Y and H Y are staged in
-// shared memory (row stride m + 1: conflict-free column reads); thread
+// shared memory (row stride m + 1 or m + 2, whichever is odd: conflict-free
+// column reads); thread
 // (point lane pl, column group jg) accumulates the columns j = jb + jg + 4 i
 // (i < RJ) of its point in registers, so each coefficient read is a warp
 // broadcast and feeds two FMAs per point.  Results go back through shared
@@ -520,7 +523,7 @@ __global__ void __launch_bounds__(256) rotate_kernel(const DevFrag* efr, const T
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int f = blockIdx.y;
   const DevFrag F = efr[f];
-  const int m = F.n, ms = m + 1;
+  const int m = F.n, ms = m + 1 + (m & 1);
   const int r = rank[f];
   const int ex = F.ext[0], ey = F.ext[1];
   const int P = F.ext[0] * F.ext[1] * F.ext[2];
@@ -1055,10 +1058,36 @@ static ofm_status eig_setup(ofm_ctx* c, int guard_opt) {
   w->tsum = 0;
   w->cta_start.resize(nf);
   long long ctas = 0;
+  // The on-chip filter runs one CTA per (fragment, vector), one CTA per SM
+  // (the box takes most of the shared memory), so a filter takes
+  // ceil(m_max nfrag / SMs) waves.  With the default guard counts, one or two
+  // guard vectors fewer per fragment (never below four) are taken when that
+  // saves a whole wave.
+  int trim = 0;
+  if (guard_opt <= 0 && cheb_filter_smem(c->frags, fp64) > 0) {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || sms < 1) {
+      cudaGetLastError();
+      sms = 152;
+    }
+    auto waves = [&](int t) -> long long {
+      int mm = 0;
+      for (const DevFrag& F : c->frags) {
+        const int g = std::max(4, F.n / 4) - t;
+        if (g < 4) return LLONG_MAX;
+        const long long P = (long long)F.ext[0] * F.ext[1] * F.ext[2];
+        mm = std::max(mm, (int)std::min<long long>(std::min<long long>((long long)F.n + g, P - 1), 256));
+      }
+      return ((long long)mm * nf + sms - 1) / sms;
+    };
+    const long long w0 = waves(0);
+    for (int t = 1; t <= 2 && trim == 0; ++t)
+      if (waves(t) < w0) trim = t;
+  }
   for (int a = 0; a < nf; ++a) {
     DevFrag& E = w->efr[a];
     const long long P = (long long)E.ext[0] * E.ext[1] * E.ext[2];
-    int g = guard_opt > 0 ? guard_opt : std::max(4, E.n / 4);
+    int g = guard_opt > 0 ? guard_opt : std::max(4, E.n / 4) - trim;
     int m = (int)std::min<long long>((long long)E.n + g, P - 1);
     m = std::min(m, 256);
     E.n = m;
@@ -1160,7 +1189,7 @@ static ofm_status eig_setup(ofm_ctx* c, int guard_opt) {
       w->rot_blocks = (int)std::min<long long>((maxP + RT4 - 1) / RT4, 64);
     } else {
       w->rot_smem = 16 * ((RT * sizeof(int) + 15) / 16) +
-                    (4 * RJ + (size_t)w->mmax * w->mmax + 2 * (size_t)RT * (w->mmax + 1)) * es;
+                    (4 * RJ + (size_t)w->mmax * w->mmax + 2 * (size_t)RT * (w->mmax + 1 + (w->mmax & 1))) * es;
       w->rot_blocks = (int)std::min<long long>((maxP + RT - 1) / RT, 64);
     }
   }
@@ -1170,7 +1199,7 @@ static ofm_status eig_setup(ofm_ctx* c, int guard_opt) {
   else if (fp64) OFM_CUDA(c, cudaFuncSetAttribute(rotate_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w->rot_smem));
   else OFM_CUDA(c, cudaFuncSetAttribute(rotate_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w->rot_smem));
   w->rr_threads = std::min(RR_MAX_THREADS, std::max(256, 32 * ((w->mmax + 1) / 2)));
-  const size_t rr = (3 * (size_t)w->mmax * (w->mmax + 1) + 3 * (size_t)w->mmax) * es;
+  const size_t rr = (3 * (size_t)w->mmax * (w->mmax + 1 + (w->mmax & 1)) + 3 * (size_t)w->mmax) * es;
   w->rr_smem = rr <= 200 * 1024 ? rr : 0;
   if (w->rr_smem) {
     if (fp64) OFM_CUDA(c, cudaFuncSetAttribute(rayleigh_ritz_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w->rr_smem));
