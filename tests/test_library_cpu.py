@@ -95,3 +95,20 @@ def test_planner_rejects_invalid_geometry(lib, bad):
 def test_planner_rejects_bad_spacing(lib):
     with pytest.raises(lib.OFMError):
         lib.plan_pairs(Grid((8, 8, 8), 0.0), [Fragment((0, 0, 0), (4, 4, 4), 1)])
+
+
+def test_missing_library_raises(lib, monkeypatch, tmp_path):
+    """No CPU fallback: without libofm.so the binding refuses to load."""
+    monkeypatch.setattr(lib, "_LIB", None)
+    with pytest.raises(RuntimeError):
+        lib.load_library(str(tmp_path / "libofm.so"))
+
+
+def test_no_device_is_an_error_not_a_fallback(lib):
+    """Without a CUDA device a context cannot be created: the call reports
+    the CUDA failure (there is no host path to fall back to)."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    with pytest.raises(lib.OFMError):
+        lib.Context()
