@@ -242,6 +242,21 @@ ofm_status ofm_get_dense_HS(ofm_ctx* ctx, double* H, double* S, ofm_location loc
  * doubles (host), available after ofm_assemble_HS. */
 ofm_status ofm_get_hphi(ofm_ctx* ctx, int b, double* hphi_out);
 
+/* Block-sparse product with the assembled pencil of Eq. 2, without forming
+ * the dense matrices: Y = M X with M = H (which = 0) or M = S (which = 1),
+ * summed over the pair blocks (the stored block a <= b, its transpose for
+ * b > a; blocks of pairs outside the pair list are zero), FP64, in basis
+ * order.  X and Y are DEVICE arrays of k columns, column-major: column c of
+ * X starts at X + c * ldx, ldx and ldy >= basis_size; Y is written, X only
+ * read, and the two must not overlap.  The caller owns both.  Enqueued on
+ * the context stream (X must be ready there); does not synchronise.  Each
+ * output is summed in a fixed order (deterministic).
+ * OFM_ERR_STATE before ofm_assemble_HS; OFM_ERR_INVALID for which not 0/1,
+ * NULL pointers, k < 1, leading dimensions < basis_size, or X and Y
+ * overlapping. */
+ofm_status ofm_pencil_apply(ofm_ctx* ctx, int which, const double* X, long long ldx, double* Y,
+                            long long ldy, int k);
+
 /* Eq. 2 restricted to an energy window, FP64 on the device: Cholesky
  * S = L L^T, A = L^-1 H L^-T, Householder tridiagonalisation, Sturm-count
  * bisection for the eigenvalues in [E_lo, E_hi] (inclusive).  E_out: host,

@@ -152,7 +152,7 @@ extern "C" void ofm_destroy(ofm_ctx* c) {
   DevBuf* bufs[] = {&c->V, &c->states, &c->hphi, &c->d_frags, &c->d_pairs,
                     &c->d_pieces, &c->d_items, &c->partials, &c->blocks, &c->dense_H,
                     &c->dense_S, &c->staging, &c->flag, &c->w_A, &c->w_L, &c->w_d, &c->w_e,
-                    &c->w_tau, &c->w_tmp, &c->w_eval, &c->w_bar, &c->w_Q};
+                    &c->w_tau, &c->w_tmp, &c->w_eval, &c->w_bar, &c->w_Q, &c->sp_rowptr, &c->sp_ents};
   for (DevBuf* b : bufs) free_buf(*b);
   ofm_free_extra(c);
   if (c->own_stream) cudaStreamDestroy(c->stream);

@@ -133,7 +133,8 @@ void launch_scatter_dense(const DevFrag* d_fr, const DevPair* d_pairs, int npair
 namespace ofm {
 enum KClass {
   KC_CONVERT, KC_APPLY, KC_CONTRACT, KC_FINALIZE, KC_SCATTER, KC_EIG_INIT, KC_FILTER, KC_GRAM,
-  KC_RR, KC_ROTATE, KC_EXPORT, KC_CHOL, KC_REDUCE, KC_TRIDIAG, KC_BISECT, KC_VECTORS, KC_COUNT
+  KC_RR, KC_ROTATE, KC_EXPORT, KC_CHOL, KC_REDUCE, KC_TRIDIAG, KC_BISECT, KC_VECTORS, KC_PENCIL,
+  KC_COUNT
 };
 struct KStat {
   long long launches = 0;
@@ -206,6 +207,7 @@ struct ofm_ctx {
   ofm::DevBuf V, states, hphi, d_frags, d_pairs, d_pieces, d_items, partials,
       blocks, dense_H, dense_S, staging, flag;
   ofm::DevBuf w_A, w_L, w_d, w_e, w_tau, w_tmp, w_eval, w_bar, w_Q;   // window-solver workspaces
+  ofm::DevBuf sp_rowptr, sp_ents;   // block rows of the pencil for ofm_pencil_apply
   int dense_n = 0;
   int window_fail_col = -1;
   std::vector<char> frag_set;       // per fragment: states imported or computed

@@ -12,13 +12,13 @@ const char* kclass_name(int k) {
   static const char* names[KC_COUNT] = {
       "convert",  "apply",  "contract", "finalize", "scatter", "eig_init", "filter", "gram",
       "rayleigh_ritz", "rotate", "eig_export", "cholesky", "reduce", "tridiag", "bisect",
-      "vectors"};
+      "vectors", "pencil"};
   return (k >= 0 && k < KC_COUNT) ? names[k] : "?";
 }
 
 const char* kclass_row(int k) {
   static const char* rows[KC_COUNT] = {"a2", "a1", "a4", "a5", "a5", "a0", "a0", "a0",
-                                       "a0", "a0", "a0", "a6", "a6", "a6", "a6", "a6"};
+                                       "a0", "a0", "a0", "a6", "a6", "a6", "a6", "a6", "a6"};
   return (k >= 0 && k < KC_COUNT) ? rows[k] : "?";
 }
 

@@ -30,7 +30,7 @@ EXPORTS = [
     "ofm_get_dense_HS", "ofm_get_hphi", "ofm_window_eigs", "ofm_eigs_by_index",
     "ofm_set_dense_HS", "ofm_plan_pairs", "ofm_set_profiling", "ofm_get_kernel_stats",
     "ofm_pair_blocks_noalloc", "ofm_set_pair_cutoff", "ofm_select_states", "ofm_homo_lumo_gap",
-    "ofm_window_from_index", "ofm_autotune_assembly",
+    "ofm_window_from_index", "ofm_autotune_assembly", "ofm_pencil_apply",
 ]
 
 
@@ -116,6 +116,7 @@ def load_library(path: str = LIB_PATH):
         "ofm_homo_lumo_gap": ([P, D, DP, DP, DP, IP], I),
         "ofm_window_from_index": ([P, I, D, I, DP, IP], I),
         "ofm_autotune_assembly": ([P, I, IP, I, I, DP, C.POINTER(ofm_tune_result)], I),
+        "ofm_pencil_apply": ([P, I, P, C.c_longlong, P, C.c_longlong, I], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -292,6 +293,19 @@ class Context:
             self.h, PREC[precision], None if cand is None else _iptr(cand), nc, int(reps),
             _dptr(times), C.byref(r)))
         return r.chunk_points, r.stencil_form, r.ms, times.reshape(2, nc)
+
+    # -- ofm_pencil_apply
+    def pencil_apply(self, which, X, out=None):
+        """Y = H X (which "H") or S X (which "S") with the assembled blocks.
+        X: CUDA float64 torch tensor of shape (k, basis), contiguous (its rows
+        are the k columns); returns Y of the same shape (enqueued on the
+        context stream)."""
+        assert _is_torch(X) and X.is_cuda and str(X.dtype) == "torch.float64" and X.is_contiguous()
+        k, n = X.shape
+        Y = out if out is not None else X.new_empty((k, n))
+        self._check(self.lib.ofm_pencil_apply(self.h, {"H": 0, "S": 1}[which], C.c_void_p(X.data_ptr()),
+                                              n, C.c_void_p(Y.data_ptr()), n, k))
+        return Y
 
     # -- ofm_set_pair_cutoff
     def set_pair_cutoff(self, atoms, d_cut):
