@@ -13,11 +13,14 @@
 //      Ritz value (the scaled three-term recurrence, one fused stencil step
 //      per degree, every fragment in one launch);
 //   3. Rayleigh-Ritz: G = Y^T Y and K = Y^T H Y (one batched contraction),
-//      then per fragment, in FP64: diagonal scaling, Jacobi eigen-
-//      decomposition of G, canonical orthogonalisation (directions with
-//      relative Gram eigenvalue below a threshold are dropped), Jacobi
-//      eigendecomposition of the projected K -> Ritz values and C;
-//   4. X <- Y C, HX <- (HY) C, residual norms ||HX_i - theta_i X_i||;
+//      then per fragment, in the storage precision: diagonal scaling,
+//      Cholesky of the scaled G and Jacobi on L^-1 K L^-T when G is well
+//      conditioned, else Jacobi eigendecomposition of G, canonical
+//      orthogonalisation (directions with relative Gram eigenvalue below a
+//      threshold are dropped) and Jacobi on the projected K -> Ritz values
+//      and C;
+//   4. X <- Y C, and residual norms ||(HY) C_i - theta_i X_i|| with (HY) C
+//      formed on the fly (never stored: the next filter starts from X);
 //   5. b_lo <- largest Ritz value, repeat until every wanted residual is
 //      below tol.
 // The Gershgorin bound b_up = 6/h^2 + max V holds for every fragment
@@ -500,9 +503,10 @@ __global__ void __launch_bounds__(RR_MAX_THREADS) rayleigh_ritz_kernel(const Dev
   if (tid == 0) rank_out[f] = r;
 }
 
-// X_new = Y C and HX_new = HY C over the interior points (columns >= rank
-// get fresh random values and H X = 0), plus per-block partial sums of
-// (HX_new - theta X_new)^2 per column for the residual norms.
+// X_new = Y C over the interior points (columns >= rank get fresh random
+// values), plus per-block partial sums of ((HY) C - theta X_new)^2 per
+// column for the residual norms, with (HY) C formed on the fly and not
+// stored (a dropped direction's H X counts as zero).
 // A CTA takes tiles of RT points: their rows of Y and H Y are staged in
 // shared memory (row stride m + 1 or m + 2, whichever is odd: conflict-free
 // column reads); thread
