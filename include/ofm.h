@@ -94,6 +94,16 @@ typedef struct {
                             profiling is off (per-launch timing needs separate launches)
                             and on a stream that can be captured (not the legacy default
                             stream); 0 launches the kernels one by one */
+  int schedule;          /* tensor-core precisions only: [0] the context's schedule (the one
+                            ofm_autotune_assembly chose, else "region" wherever its plan
+                            applies, else "pair"); 1 "pair": H phi in the states' layout,
+                            then one GEMM per pair (M = n_a padded to 128); 2 "region":
+                            the grid is cut into coverage regions (products of the
+                            segments between dilated-box boundaries) and every region's
+                            fragments are stacked into one GEMM (M = sum of their
+                            n_a), with the H apply writing MMA-ready operands
+                            (OFM_ERR_INVALID where that plan does not apply: more than
+                            128 states per fragment, or partial sums beyond 16 GB) */
 } ofm_assemble_opts;
 
 /* Counts describing the planned work (after ofm_build_fragments). */
@@ -156,10 +166,13 @@ ofm_status ofm_assemble_HS(ofm_ctx* ctx, ofm_precision prec, const ofm_assemble_
 
 /* Result of ofm_autotune_assembly. */
 typedef struct {
-  int chunk_points;      /* chosen points per contraction work item */
+  int chunk_points;      /* chosen points per contraction work item (pair schedule) */
   int stencil_form;      /* chosen form of the H apply: 1 register, 2 staged (shared-memory planes) */
   double ms;             /* its mean assembly time over the timed runs, milliseconds */
   int n_tried;           /* candidates timed */
+  int schedule;          /* chosen schedule: 1 pair, 2 region */
+  double region_ms;      /* mean time of the region schedule, -1 where it does not apply
+                            or for the CUDA-core precisions */
 } ofm_tune_result;
 
 /* Measuring autotuner of the assembly schedule of ofm_assemble_HS (the same
@@ -169,7 +182,9 @@ typedef struct {
  * once, then run `reps` times between two CUDA events on the context stream;
  * the fastest becomes the context's schedule, used by later ofm_assemble_HS
  * calls whose chunk_points is 0, until ofm_build_fragments changes the layout
- * (boxes, state counts, grid or storage).  chunks: n_chunks candidate sizes
+ * (boxes, state counts, grid or storage).  For the tensor-core precisions
+ * the region schedule (ofm_assemble_opts.schedule) is timed too and kept
+ * when it is the fastest.  chunks: n_chunks candidate sizes
  * (> 0), or NULL for five: the planner's own size for this precision's
  * contraction times 1/4, 1/2, 1, 2 and 4.  times_ms (host, nullable) gets
  * 2 x n_cand mean times, form-major, -1 where the staged form does not fit.
@@ -317,6 +332,22 @@ ofm_status ofm_get_kernel_stats(ofm_ctx* ctx, ofm_kernel_stat* out, int max, int
 ofm_status ofm_plan_pairs(const ofm_grid* grid, const ofm_fragment* frags, int n_frag,
                           int* n_pairs, int* pair_ab, long long* counts, int max_pairs,
                           long long* pair_flops);
+
+/* Host-only query of the region plan of the tensor-core assembly (needs no
+ * GPU and no context), for the pair list of ofm_plan_pairs.  Sec. II sums
+ * H_ab and S_ab over the grid points two fragments share; the region plan
+ * cuts the grid into coverage regions (per dimension, the segments between
+ * dilated-box boundaries, merged while shorter than w_min points; products
+ * of three segments) and sums every pair over the regions whose cover set
+ * holds both fragments.  stats (8 long longs, nullable): plan applies (0/1),
+ * regions, region parts (K splits), work items, operand-plane bytes,
+ * partial-slot bytes, MMA flops of one product pass, the segment width
+ * used.  pair_points (nullable, max_pairs entries, pair-list order): for
+ * each pair, the points of B_a ∩ B_b+ that the regions holding both
+ * fragments cover, counted point by point (equal to |B_a ∩ B_b+| when the
+ * plan is right).  OFM_ERR_INVALID for a bad geometry. */
+ofm_status ofm_plan_regions(const ofm_grid* grid, const ofm_fragment* frags, int n_frag,
+                            int w_min, long long* stats, long long* pair_points, int max_pairs);
 
 /* Allocation-free pair blocks.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory when they need

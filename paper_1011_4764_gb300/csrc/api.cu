@@ -47,6 +47,13 @@ ofm_status ofm_ensure(ofm_ctx* c, DevBuf& b, size_t bytes, const char* what) {
   return OFM_OK;
 }
 
+ofm_status ofm_ensure_big(ofm_ctx* c, DevBuf& b, size_t bytes, const char* what) {
+  const ofm_status st = ofm_ensure(c, b, bytes, what);
+  if (st != OFM_ERR_OOM || !c->eig) return st;
+  ofm_eig_free(c);   // the largest reclaimable buffers; the next eigensolve re-makes them
+  return ofm_ensure(c, b, bytes, what);
+}
+
 static void free_buf(DevBuf& b) {
   if (b.p) cudaFree(b.p);
   b.p = nullptr;
@@ -92,6 +99,7 @@ static int find_pair(const ofm_ctx* c, int a, int b) {
 void ofm_free_extra(ofm_ctx* c) {
   ofm_eig_free(c);
   ofm_tc_free(c);
+  ofm_region_free(c);
 }
 
 // ------------------------------------------------------------- lifecycle ---
@@ -185,7 +193,6 @@ static ofm_status plan_contraction(ofm_ctx* c) {
   OFM_TRY(ofm_ensure(c, c->d_pairs, sizeof(DevPair) * std::max(1, np), "pair table"));
   OFM_TRY(ofm_ensure(c, c->d_pieces, sizeof(Piece) * std::max<size_t>(1, c->simt_pieces.size()), "piece table"));
   OFM_TRY(ofm_ensure(c, c->d_items, sizeof(WorkItem) * std::max<size_t>(1, c->simt_items.size()), "work items"));
-  OFM_TRY(ofm_ensure(c, c->partials, sizeof(double) * c->simt_partial_elems, "partials"));
   OFM_CUDA(c, cudaMemcpyAsync(c->d_pairs.p, c->simt_pairs.data(), sizeof(DevPair) * np,
                               cudaMemcpyHostToDevice, c->stream));
   OFM_CUDA(c, cudaMemcpyAsync(c->d_pieces.p, c->simt_pieces.data(),
@@ -196,6 +203,7 @@ static ofm_status plan_contraction(ofm_ctx* c) {
   for (auto& p : c->simt_pairs) c->blk_elems = std::max<long long>(c->blk_elems, p.blk_off + 2LL * c->frags[p.a].n * c->frags[p.b].n);
   OFM_TRY(ofm_ensure(c, c->blocks, sizeof(double) * c->blk_elems, "blocks"));
   c->finalize_bytes = (double)c->simt_partial_elems * (es == 8 ? 8 : 4) + 8.0 * c->blk_elems;
+  c->region_stale = true;
   return ofm_plan_extra(c);
 }
 
@@ -256,6 +264,7 @@ static ofm_status layout_fragments(ofm_ctx* c) {
     ofm_eig_free(c);
     c->stencil_form = 0;
     c->tuned_chunk = 0;
+    c->schedule = 0;
   }
   c->laid_frags = c->in_frags;
   c->laid_grid = c->grid;
@@ -278,10 +287,22 @@ static ofm_status layout_fragments(ofm_ctx* c) {
   for (auto& f : c->frags) c->apply_bytes += (double)f.Pd * (2.0 * f.n + 1.0) * es;
   c->contract_bytes = 0;
   for (auto& f : c->frags) c->contract_bytes += (double)f.Pd * 2.0 * f.n * es;
+  // the region path's traffic: the apply + pack reads the states once and
+  // writes phi and H phi as operands (8 bytes per point-state for BF16 hi+lo
+  // and TF32, 4 for BF16); the contraction reads those operands once
+  for (int k = 0; k < 3; ++k) {
+    const double ob = k == 1 ? 2.0 : 4.0;
+    c->pack_bytes[k] = 0;
+    c->region_bytes[k] = 0;
+    for (auto& f : c->frags) {
+      c->pack_bytes[k] += (double)f.Pd * f.n * (4.0 + 2.0 * ob) + (double)f.Pd * 4.0;
+      c->region_bytes[k] += (double)f.Pd * f.n * 2.0 * ob;
+    }
+  }
   OFM_TRY(ofm_ensure(c, c->states, c->state_elems * es, "fragment states"));
-  OFM_TRY(ofm_ensure(c, c->hphi, c->state_elems * es, "H phi"));
   OFM_CUDA(c, cudaMemsetAsync(c->states.p, 0, c->state_elems * es, c->stream));
-  OFM_CUDA(c, cudaMemsetAsync(c->hphi.p, 0, c->state_elems * es, c->stream));
+  // H phi (every element written by the apply) is allocated on first use
+  c->hphi_ready = c->hphi.cap >= (size_t)(c->state_elems * es);
   OFM_TRY(ofm_ensure(c, c->d_frags, sizeof(DevFrag) * n_frag, "fragment table"));
   OFM_CUDA(c, cudaMemcpyAsync(c->d_frags.p, c->frags.data(), sizeof(DevFrag) * n_frag,
                               cudaMemcpyHostToDevice, c->stream));
@@ -399,6 +420,14 @@ extern "C" ofm_status ofm_select_states(ofm_ctx* c, const int* first, const int*
   return sync(c, "select_states");
 }
 
+// The H phi buffer of the current layout (outside any stream capture).
+static ofm_status ensure_hphi(ofm_ctx* c) {
+  if (c->hphi_ready) return OFM_OK;
+  OFM_TRY(ofm_ensure_big(c, c->hphi, c->state_elems * elem_size(c), "H phi"));
+  c->hphi_ready = true;
+  return OFM_OK;
+}
+
 // ------------------------------------------------------------- states ------
 
 extern "C" ofm_status ofm_set_fragment_states(ofm_ctx* c, int a, const double* phi, ofm_location loc) {
@@ -451,6 +480,9 @@ extern "C" ofm_status ofm_get_hphi(ofm_ctx* c, int b, double* out) {
   const DevFrag& F = c->frags[b];
   const long long cnt = F.Pd * F.n;
   OFM_TRY(ofm_ensure(c, c->staging, cnt * sizeof(double), "staging"));
+  // the region path never stores H phi in the states' layout: apply H here
+  OFM_TRY(ensure_hphi(c));
+  OFM_TRY(ofm_apply_h(c));
   launch_export_states(F, c->hphi.p, (double*)c->staging.p, c->storage == OFM_STORE_FP64, true, c->stream);
   OFM_TRY(check_launch(c, "export H phi"));
   OFM_CUDA(c, cudaMemcpyAsync(out, c->staging.p, cnt * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -460,6 +492,7 @@ extern "C" ofm_status ofm_get_hphi(ofm_ctx* c, int b, double* out) {
 // ------------------------------------------------------------- assembly ----
 
 ofm_status ofm_apply_h(ofm_ctx* c) {
+  if (!c->hphi_ready) return ofm_fail(c, OFM_ERR_STATE, "H phi buffer not allocated");
   KTimer t(c, KC_APPLY, 1, c->apply_bytes);
   launch_apply_global((const DevFrag*)c->d_frags.p, c->nfrag, c->agrid, c->V.p,
                       c->states.p, c->hphi.p, c->grid.n, c->grid.h,
@@ -468,10 +501,40 @@ ofm_status ofm_apply_h(ofm_ctx* c) {
   return check_launch(c, "apply H");
 }
 
+// Whether a tensor-core assembly of this precision takes the region-stacked
+// schedule: requested (2), or by default (0) wherever its plan applies.
+static bool region_schedule(const ofm_ctx* c, ofm_precision prec, int sched) {
+  if (prec == OFM_PREC_FP64 || prec == OFM_PREC_FP32) return false;
+  if (sched == 1) return false;
+  return ofm_region_ok(c);
+}
+
+// Plans and buffers an assembly needs, made before any capture: the region
+// plan (host tables after a re-plan), or the H phi buffer and the CUDA-core
+// partial sums.
+static ofm_status prepare_assembly(ofm_ctx* c, ofm_precision prec, int sched) {
+  if (prec != OFM_PREC_FP64 && prec != OFM_PREC_FP32 && sched != 1 && c->region_stale) {
+    OFM_TRY(ofm_region_plan(c));
+    c->region_stale = false;
+  }
+  if (sched == 2 && !region_schedule(c, prec, sched))
+    return ofm_fail(c, OFM_ERR_INVALID, std::string("region schedule unavailable: ") + ofm_region_why(c));
+  if (region_schedule(c, prec, sched)) return ofm_region_prepare(c);   // tables and buffers
+  OFM_TRY(ensure_hphi(c));
+  if (prec == OFM_PREC_FP64 || prec == OFM_PREC_FP32)
+    OFM_TRY(ofm_ensure_big(c, c->partials, sizeof(double) * c->simt_partial_elems, "partials"));
+  return OFM_OK;
+}
+
 // The launches of one assembly (a1 apply, a3/a4 contraction, a5 blocks) on
 // the context stream; no host synchronisation, so it can be captured.
-static ofm_status enqueue_assembly(ofm_ctx* c, ofm_precision prec) {
+static ofm_status enqueue_assembly(ofm_ctx* c, ofm_precision prec, int sched) {
+  if (region_schedule(c, prec, sched)) {
+    c->last_schedule = 2;
+    return ofm_region_run(c, prec);
+  }
   OFM_TRY(ofm_apply_h(c));
+  if (prec != OFM_PREC_FP64 && prec != OFM_PREC_FP32) c->last_schedule = 1;
   if (prec == OFM_PREC_FP64 || prec == OFM_PREC_FP32) {
     { KTimer t(c, KC_CONTRACT, 1, c->contract_bytes, (double)c->flops);
     launch_contract_simt(prec, c->storage == OFM_STORE_FP64, (const DevFrag*)c->d_frags.p,
@@ -493,7 +556,7 @@ static ofm_status enqueue_assembly(ofm_ctx* c, ofm_precision prec) {
 // Captures enqueue_assembly for `prec` as a CUDA graph.  A stream that cannot
 // be captured (the legacy default stream, for one) turns graphs off for the
 // context; the assembly is then launched directly.
-static ofm_status capture_assembly(ofm_ctx* c, ofm_precision prec) {
+static ofm_status capture_assembly(ofm_ctx* c, ofm_precision prec, int sched) {
   ofm::KStat before[KC_COUNT];
   for (int k = 0; k < KC_COUNT; ++k) before[k] = c->prof.st[k];
   if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
@@ -501,7 +564,7 @@ static ofm_status capture_assembly(ofm_ctx* c, ofm_precision prec) {
     c->graphs_off = true;
     return OFM_OK;
   }
-  const ofm_status st = enqueue_assembly(c, prec);
+  const ofm_status st = enqueue_assembly(c, prec, sched);
   cudaGraph_t g = nullptr;
   const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
   // nothing ran yet: the counters take what one replay adds
@@ -512,6 +575,7 @@ static ofm_status capture_assembly(ofm_ctx* c, ofm_precision prec) {
     c->prof.st[k] = before[k];
   }
   c->asm_tc[prec] = c->tc_check;
+  c->asm_sched[prec] = sched;
   c->tc_check = false;
   c->stencil_check = false;
   if (st != OFM_OK || e != cudaSuccess || !g ||
@@ -533,15 +597,23 @@ extern "C" ofm_status ofm_assemble_HS(ofm_ctx* c, ofm_precision prec, const ofm_
     return ofm_fail(c, OFM_ERR_INVALID, "FP32 and tensor-core contractions need FP32 storage");
   long long chunk = opts ? opts->chunk_points : 0;
   const bool use_graph = opts ? opts->use_graph != 0 : true;
+  int sched = opts ? opts->schedule : 0;
   if (chunk < 0) return ofm_fail(c, OFM_ERR_INVALID, "chunk_points must be >= 0");
+  if (sched < 0 || sched > 2) return ofm_fail(c, OFM_ERR_INVALID, "schedule must be 0, 1 or 2");
+  if (sched == 0) sched = c->schedule;
   if (chunk == 0) chunk = c->tuned_chunk;
   if (chunk != c->asm_chunk) {
     c->asm_chunk = chunk;
     OFM_TRY(plan_contraction(c));
   }
   c->assembled = c->dense_ready = c->factored = false;
+  OFM_TRY(prepare_assembly(c, prec, sched));
+  if (c->asm_exec[prec] && c->asm_sched[prec] != sched) {
+    cudaGraphExecDestroy(c->asm_exec[prec]);
+    c->asm_exec[prec] = nullptr;
+  }
   if (use_graph && !c->prof.on && !c->graphs_off) {
-    if (!c->asm_exec[prec]) OFM_TRY(capture_assembly(c, prec));
+    if (!c->asm_exec[prec]) OFM_TRY(capture_assembly(c, prec, sched));
     if (c->asm_exec[prec]) {
       OFM_CUDA(c, cudaGraphLaunch(c->asm_exec[prec], c->stream));
       for (int k = 0; k < KC_COUNT; ++k) {
@@ -549,13 +621,14 @@ extern "C" ofm_status ofm_assemble_HS(ofm_ctx* c, ofm_precision prec, const ofm_
         c->prof.st[k].bytes += c->asm_cost[prec][k].bytes;
         c->prof.st[k].flops += c->asm_cost[prec][k].flops;
       }
-      c->stencil_check = true;
+      c->stencil_check = !region_schedule(c, prec, sched);
       if (c->asm_tc[prec]) c->tc_check = true;
+      if (prec != OFM_PREC_FP64 && prec != OFM_PREC_FP32) c->last_schedule = sched == 0 ? (ofm_region_ok(c) ? 2 : 1) : sched;
       c->assembled = true;
       return OFM_OK;
     }
   }
-  OFM_TRY(enqueue_assembly(c, prec));
+  OFM_TRY(enqueue_assembly(c, prec, sched));
   c->assembled = true;
   return OFM_OK;
 }
@@ -602,6 +675,8 @@ extern "C" ofm_status ofm_autotune_assembly(ofm_ctx* c, ofm_precision prec, cons
   ofm_status st = OFM_OK;
   ofm_assemble_opts o{};
   o.use_graph = 1;
+  o.schedule = 1;
+  const bool tcp = prec >= OFM_PREC_TF32;
   for (int form = 1; form <= 2 && st == OFM_OK; ++form) {
     const ApplyGrid g = apply_grid(c->frags, es == 8, false, form);
     const bool fits = form == 1 || g.staged;
@@ -635,6 +710,35 @@ extern "C" ofm_status ofm_autotune_assembly(ofm_ctx* c, ofm_precision prec, cons
       }
     }
   }
+  // the region schedule (tensor-core precisions, where its plan applies)
+  double region_ms = -1.0;
+  int best_sched = 1;
+  if (st == OFM_OK && tcp) {
+    if (c->region_stale) {
+      st = ofm_region_plan(c);
+      c->region_stale = false;
+    }
+    if (st == OFM_OK && ofm_region_ok(c)) {
+      o.schedule = 2;
+      st = ofm_assemble_HS(c, prec, &o);
+      if (st == OFM_OK) st = ofm_wait_status(c);
+      if (st == OFM_OK && cudaEventRecord(e0, c->stream) != cudaSuccess) st = ofm_cuda_check(c, cudaGetLastError(), "event");
+      for (int r = 0; r < reps && st == OFM_OK; ++r) st = ofm_assemble_HS(c, prec, &o);
+      if (st == OFM_OK && (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+        st = ofm_cuda_check(c, cudaGetLastError(), "autotune timing");
+      if (st == OFM_OK) st = ofm_wait_status(c);
+      if (st == OFM_OK) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        region_ms = (double)ms / reps;
+        ++tried;
+        if (best < 0.0 || region_ms < best) {
+          best = region_ms;
+          best_sched = 2;
+        }
+      }
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   // the chosen schedule (the default one after a failure), then one assembly
@@ -642,6 +746,7 @@ extern "C" ofm_status ofm_autotune_assembly(ofm_ctx* c, ofm_precision prec, cons
   drop_graphs(c);
   c->stencil_form = st == OFM_OK ? best_form : 0;
   c->tuned_chunk = st == OFM_OK ? best_chunk : 0;
+  c->schedule = st == OFM_OK && tcp ? best_sched : 0;
   c->agrid = apply_grid(c->frags, es == 8, false, c->stencil_form);
   c->asm_chunk = -1;   // re-plan at the next assembly
   if (st != OFM_OK) return st;
@@ -652,6 +757,8 @@ extern "C" ofm_status ofm_autotune_assembly(ofm_ctx* c, ofm_precision prec, cons
     out->stencil_form = best_form;
     out->ms = best;
     out->n_tried = tried;
+    out->schedule = best_sched;
+    out->region_ms = region_ms;
   }
   return sync(c, "autotuned assembly");
 }

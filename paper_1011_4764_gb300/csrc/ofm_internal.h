@@ -221,11 +221,24 @@ struct ofm_ctx {
   cudaGraphExec_t asm_exec[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   ofm::KStat asm_cost[5][ofm::KC_COUNT];
   bool asm_tc[5] = {false, false, false, false, false};
+  int asm_sched[5] = {0, 0, 0, 0, 0};   // schedule each graph was captured with
   bool graphs_off = false;          // capture failed once on this stream: launch directly
   bool tc_check = false;            // a tensor-core launch's timeout flag is unread
   bool stencil_check = false;       // a stencil launch's timeout flag is unread
   struct EigWork* eig = nullptr;    // fragment-eigensolver buffers and plan
-  struct TcPlan* tc = nullptr;      // tensor-core contraction plan
+  struct TcPlan* tc = nullptr;      // tensor-core contraction plan (one GEMM per pair)
+  // region-stacked tensor-core contraction: plan (built on first use after a
+  // re-plan), its segment coarsening, and the schedule of the tensor-core
+  // assembly (0: region where its plan applies, else per pair; 1: per pair;
+  // 2: region)
+  struct RegionPlan* region = nullptr;
+  bool region_stale = true;
+  int region_wmin = 1;
+  int schedule = 0;                 // the tuned or caller-set default schedule
+  int last_schedule = 0;            // schedule of the last tensor-core assembly (1 or 2)
+  bool hphi_ready = false;          // the FP32/FP64 H phi buffer is allocated
+  double pack_bytes[3] = {0, 0, 0};     // algorithmic bytes of the apply + pack, per kind
+  double region_bytes[3] = {0, 0, 0};   // algorithmic bytes of the region contraction, per kind
 };
 
 // words of the context's 16-int flag buffer: 0 pivot flag and 2..3 window
@@ -238,6 +251,10 @@ constexpr int OFM_FLAG_TC = 9;
 ofm_status ofm_fail(ofm_ctx* c, ofm_status s, const std::string& msg);
 ofm_status ofm_cuda_check(ofm_ctx* c, cudaError_t e, const char* what);
 ofm_status ofm_ensure(ofm_ctx* c, ofm::DevBuf& b, size_t bytes, const char* what);
+// ofm_ensure for the large lazily-sized buffers: when the device is out of
+// memory it releases the fragment eigensolver's workspace (re-made by the next
+// ofm_fragment_eigs) and tries once more
+ofm_status ofm_ensure_big(ofm_ctx* c, ofm::DevBuf& b, size_t bytes, const char* what);
 
 // cross-translation-unit steps
 ofm_status ofm_apply_h(ofm_ctx* c);
@@ -258,7 +275,15 @@ ofm_status ofm_tc_run(ofm_ctx* c, struct TcPlan* t, int kind, const ofm::DevFrag
                       int kclass_finalize, double bytes, double flops);
 bool ofm_tc_plan_ok(const struct TcPlan* t, int kind);   // the kind's staging fits
 void ofm_tc_plan_free(struct TcPlan* t);
-ofm_status ofm_wait_status(ofm_ctx* c);       // OFM_ERR_TIMEOUT if a bounded wait gave up
+ofm_status ofm_wait_status(ofm_ctx* c);
+// region-stacked contraction (region.cu)
+ofm_status ofm_region_plan(ofm_ctx* c);
+bool ofm_region_ok(const ofm_ctx* c);
+const char* ofm_region_why(const ofm_ctx* c);
+ofm_status ofm_region_prepare(ofm_ctx* c);   // device tables and buffers of the plan
+ofm_status ofm_region_run(ofm_ctx* c, ofm_precision prec);
+void ofm_region_free(ofm_ctx* c);
+void ofm_region_stats(const ofm_ctx* c, long long* out);       // OFM_ERR_TIMEOUT if a bounded wait gave up
 ofm_status ofm_window_factor(ofm_ctx* c);
 // eigenvalues below lo and below-or-at hi of the factored pencil
 ofm_status ofm_window_count(ofm_ctx* c, double lo, double hi, int* count_lo, int* count_hi);

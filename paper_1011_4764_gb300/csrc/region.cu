@@ -1,0 +1,1123 @@
+// Region-stacked pair contraction on the tcgen05 tensor cores (Sec. II, the
+// H_ab / S_ab dot products over the shared grid points).
+//
+// The grid is cut into coverage regions: per dimension, the boundaries of all
+// dilated boxes split the periodic axis into segments, and a region is a
+// product of three segments.  Every fragment whose dilated box meets a region
+// is in its cover set C(R).  Over one region, the blocks of every pair in
+// C(R) come from ONE stacked product
+//     D = Phi_C[R]^T [Phi_C[R] | HPhi_C[R]],   Phi_C = [Phi_f0 | Phi_f1 | ...],
+// with M = sum of the cover's (padded) state counts, so the 128-row MMA
+// tiles are full whatever n_a is, and each fragment's states are read once
+// per region instead of once per pair.  The blocks a <= b of D are the
+// region's contribution to (H_ab, S_ab); the contributions of the regions
+// are summed in region order (deterministic).  Points of a region outside a
+// fragment's box carry zeros in that fragment's operands, so each pair's
+// sum runs exactly over B_a ∩ B_b+ (Phi_a vanishes outside B_a, H phi_b
+// outside B_b+).
+//
+// Three kernels:
+//   pack_kernel      a1: H phi with the whole-system H (7-point stencil + V)
+//                    and the operand planes: for each (fragment, region) the
+//                    states and H phi of the region's points, already in the
+//                    K-major canonical MMA layout (core matrices of 8 rows x
+//                    16 bytes) as BF16 hi/lo, BF16 or TF32 -- the contraction
+//                    then copies tiles with no conversion;
+//   region_kernel    a3/a4: persistent, warp-specialised: a producer warp
+//                    issues one bulk copy per (fragment piece, plane, K
+//                    chunk) into a ring of stages, one thread issues the
+//                    MMAs into two alternating TMEM accumulators, four warps
+//                    drain an accumulator into the FP32 partial slot of each
+//                    (pair, region part) it covers;
+//   rfinalize_kernel a5: FP64 sum of each pair's slots in region order,
+//                    symmetrised diagonal blocks.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <unordered_map>
+#include <vector>
+
+#include "ofm_internal.h"
+#include "ptx_util.h"
+
+using namespace ofm;
+using namespace ofm::ptx;
+
+namespace {
+
+// ----------------------------------------------------------- tables -------
+
+// Pack work: one (fragment, region) block of the plane arena.
+struct RUnit {
+  int frag;
+  int s0[3];          // region start (global grid coordinates)
+  int L[3];           // region extent
+  int npts;           // |R|
+  long long tile0;    // first global pack tile of this unit
+  long long base;     // byte offset of the block in the plane arena
+};
+
+// One contraction work item: an M tile x N tile of one region part.
+struct RItem {
+  int tile0, ntiles;  // K range of the part in 64-point tiles of the region
+  int n_cols;         // MMA N (multiple of 16, <= 256)
+  int pa0, npa;       // A pieces
+  int pb0, npb;       // B pieces
+  int rs0, nrs;       // row segments of the epilogue
+  int cs0, ncs;       // column segments of the epilogue
+  int ncf;            // column fragments (slot-table width)
+  long long st0;      // slot table (nrs x ncf)
+};
+
+// A run of 8-row groups of one fragment's operand plane for one K chunk.
+struct RPiece {
+  long long base;     // byte offset of chunk 0 of the hi plane, first group
+  long long lo;       // byte offset hi plane -> lo plane (BF16 hi+lo)
+  int cb;             // bytes per K chunk of this fragment (rows_pad * 64)
+  int bytes;          // groups * 512
+  int dst;            // byte offset in the operand tile
+  int pad;
+};
+
+struct RRowSeg { int r0, nr, i0, na; };              // tile rows [r0, r0+nr) = states i0.. (n_a = na)
+struct RColSeg { int c0, nc, j0, nb, part, cf; };    // tile cols [c0, c0+nc) = states j0.. of part
+                                                     // (0 phi, 1 H phi) of column fragment cf
+// Finalize: one pair's slots.
+struct RPair {
+  int a, b, na, nb;
+  int nslot;
+  long long slot0;    // first slot (floats); slot q at slot0 + q * na * 2 nb
+  long long blk_off;  // [H_ab | S_ab] in the block arena
+};
+
+// operand kinds of the region path (same numbering as the pair path)
+enum { RK_TF32 = 0, RK_BF16 = 1, RK_BF16X3 = 2 };
+
+constexpr int RS_THREADS = 192;    // warp 0 copies, 1 MMA, 2-5 epilogue
+constexpr int RS_NSTAGE = 4;
+constexpr int RS_ACOLS = 256;      // TMEM columns per accumulator (two accumulators)
+constexpr int RS_ATILE = 128 * 64; // bytes of an A chunk tile (128 rows x 64 B)
+constexpr int RS_BTILE = 256 * 64; // bytes of a B chunk tile (256 rows x 64 B)
+constexpr int RS_STAGE = 48 * 1024;
+constexpr int RS_SMEM = RS_NSTAGE * RS_STAGE;
+constexpr int RS_MAXROWS = 128;    // padded states per fragment this path takes
+constexpr int PK_THREADS = 256;
+
+template <int K> struct KindT;
+template <> struct KindT<RK_TF32> {
+  static constexpr int esz = 4, KC = 16, CPT = 4, NPL = 1, SC = 2, FMT = 2;
+};
+template <> struct KindT<RK_BF16> {
+  static constexpr int esz = 2, KC = 32, CPT = 2, NPL = 1, SC = 2, FMT = 1;
+};
+template <> struct KindT<RK_BF16X3> {
+  static constexpr int esz = 2, KC = 32, CPT = 2, NPL = 2, SC = 1, FMT = 1;
+};
+
+__device__ __forceinline__ uint64_t rdesc(uint32_t saddr) {
+  // K-major, no swizzle: K-adjacent core matrices 128 bytes apart (LBO),
+  // 8-row groups 512 bytes apart (SBO), descriptor version 1
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((128u >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((512u >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+__host__ __device__ constexpr uint32_t ridesc(uint32_t fmt, uint32_t M, uint32_t N) {
+  // FP32 accumulator, A/B format, both K-major, N >> 3, M >> 4
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+template <int FMT>
+__device__ __forceinline__ void rmma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                     uint32_t accum) {
+  if constexpr (FMT == 2) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accum)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accum)
+        : "memory");
+  }
+}
+
+__device__ __forceinline__ void rcommit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+               : "memory");
+}
+
+__device__ __forceinline__ void rtmem_ld8(uint32_t taddr, float* v) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t rtf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+// ------------------------------------------------------------- a1: pack ---
+
+// One CTA per 64-point tile of a (fragment, region) unit, in two phases.
+//   1. Threads take (point k, 4-state group q) items with q fastest, so a
+//      warp's loads of phi and of each neighbour are contiguous runs of the
+//      point-major FP32 storage (zero outside the dilated storage box; a
+//      full-span dimension wraps), and form
+//          H phi = (3/h^2 + V) phi - (1/(2h^2)) sum_neighbours phi;
+//      phi and H phi go to shared memory as [k][state] FP32 rows with an odd
+//      row stride.
+//   2. Each thread writes 16-byte units of the operand planes in the
+//      canonical layout (memory order, coalesced): 8 (BF16) or 4 (TF32)
+//      consecutive points of one state, read down a column of the shared
+//      rows (conflict-free with the odd stride), rounded to TF32, BF16, or
+//      split into BF16 hi and lo.
+// Points of the region outside the fragment's dilated box, the tile's
+// padding points and the state rows beyond n (up to the multiple of 8) are
+// zeros.
+template <int KIND>
+__global__ void __launch_bounds__(PK_THREADS) pack_kernel(
+    const RUnit* __restrict__ units, int nunits, const DevFrag* __restrict__ fr,
+    const float* __restrict__ V, const float* __restrict__ states, unsigned char* __restrict__ planes,
+    int gx, int gy, int gz, float c0, float c1) {
+  using KT = KindT<KIND>;
+  constexpr int ESZ = KT::esz;
+  extern __shared__ __align__(16) float pk_smem[];
+  __shared__ RUnit U;
+  __shared__ DevFrag F;
+  __shared__ int s_p[64], s_nb[64][6];
+  __shared__ float s_v[64];
+  const long long T = blockIdx.x;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    int lo = 0, hi = nunits - 1;   // last unit with tile0 <= T
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (units[mid].tile0 <= T) lo = mid; else hi = mid - 1;
+    }
+    U = units[lo];
+    F = fr[U.frag];
+  }
+  __syncthreads();
+  const int t = (int)(T - U.tile0);
+  const int rows = (F.n + 7) / 8 * 8;
+  const int RS = rows + (ESZ == 4 ? 2 : 1);   // shared row stride (words)
+  float* sPh = pk_smem;
+  float* sHp = pk_smem + 64 * RS;
+  if (tid < 64) {
+    // point tid of the tile: region-local index -> fragment-local coordinates
+    const int e = t * 64 + tid;
+    bool in = e < U.npts;
+    int l[3] = {0, 0, 0}, gi[3] = {0, 0, 0};
+    if (in) {
+      const int ii[3] = {e % U.L[0], (e / U.L[0]) % U.L[1], e / (U.L[0] * U.L[1])};
+      const int gn[3] = {gx, gy, gz};
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        int g = U.s0[d] + ii[d];
+        if (g >= gn[d]) g -= gn[d];
+        gi[d] = g;
+        int ld = g - F.doff[d];
+        if (ld < 0) ld += gn[d];
+        l[d] = ld;
+        in = in && ld < F.dext[d];
+      }
+    }
+    const int ex = F.dext[0], exy = F.dext[0] * F.dext[1];
+    const int p = l[0] + ex * l[1] + exy * l[2];
+    const int st[3] = {1, ex, exy};
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int sd = 0; sd < 2; ++sd) {
+        const int c = l[d] + (sd ? -1 : 1);
+        int q = -1;
+        if (c >= 0 && c < F.dext[d]) q = p + (c - l[d]) * st[d];
+        else if (F.full[d]) q = p + (((c + F.dext[d]) % F.dext[d]) - l[d]) * st[d];
+        s_nb[tid][2 * d + sd] = in ? q : -1;
+      }
+    s_p[tid] = in ? p : -1;
+    s_v[tid] = in ? V[(long long)gi[0] + (long long)gx * (gi[1] + (long long)gy * gi[2])] : 0.f;
+  }
+  __syncthreads();
+  const float4* S4 = reinterpret_cast<const float4*>(states + F.off);
+  const int qpp = F.ld / 4;
+  const int nq = rows / 4;
+  for (int it = tid; it < 64 * nq; it += PK_THREADS) {
+    const int k = it / nq, q = it - k * nq;
+    const int p = s_p[k];
+    float4 ph = make_float4(0.f, 0.f, 0.f, 0.f), hp = ph;
+    if (p >= 0 && q < qpp) {
+      ph = S4[(long long)p * qpp + q];
+      float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        const int nb = s_nb[k][j];
+        if (nb >= 0) {
+          const float4 w = S4[(long long)nb * qpp + q];
+          sum.x += w.x; sum.y += w.y; sum.z += w.z; sum.w += w.w;
+        }
+      }
+      const float dv = c0 + s_v[k];
+      hp.x = fmaf(-c1, sum.x, dv * ph.x);
+      hp.y = fmaf(-c1, sum.y, dv * ph.y);
+      hp.z = fmaf(-c1, sum.z, dv * ph.z);
+      hp.w = fmaf(-c1, sum.w, dv * ph.w);
+    }
+    const float pv[4] = {ph.x, ph.y, ph.z, ph.w};
+    const float hv[4] = {hp.x, hp.y, hp.z, hp.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int row = 4 * q + i;
+      const bool ok = row < F.n;
+      sPh[k * RS + row] = ok ? pv[i] : 0.f;
+      sHp[k * RS + row] = ok ? hv[i] : 0.f;
+    }
+  }
+  __syncthreads();
+  // write-out: 16-byte unit (array A: phi / H phi, chunk cc, 8-row group g,
+  // core kc, row r) of plane(A, hi|lo) at
+  //   base + part(A) [+ lo] + (t*CPT + cc)*cb + g*512 + kc*128 + r*16
+  const long long cb = (long long)rows * 64;
+  const long long npl = (long long)((U.npts + 63) / 64) * 128 * rows;   // one 2-byte plane
+  constexpr int KPU = 16 / ESZ;                                         // points per unit
+  const int upc = rows * 4;                                             // units per chunk and plane
+  const int nunit = 2 * KT::CPT * upc;
+  unsigned char* blk = planes + U.base;
+  for (int w = tid; w < nunit; w += PK_THREADS) {
+    const int A = w / (KT::CPT * upc);
+    int u = w - A * (KT::CPT * upc);
+    const int cc = u / upc;
+    u -= cc * upc;
+    const int r = u & 7, kc = (u >> 3) & 3, g = u >> 5;
+    const int row = 8 * g + r;
+    const int k0 = cc * KT::KC + kc * KPU;
+    const float* src = (A ? sHp : sPh) + k0 * RS + row;
+    float x[KPU];
+#pragma unroll
+    for (int j = 0; j < KPU; ++j) x[j] = src[j * RS];
+    const long long off = (long long)(t * KT::CPT + cc) * cb + g * 512 + kc * 128 + r * 16;
+    if constexpr (KIND == RK_TF32) {
+      const uint4 v = make_uint4(rtf32(x[0]), rtf32(x[1]), rtf32(x[2]), rtf32(x[3]));
+      *reinterpret_cast<uint4*>(blk + A * 2 * npl + off) = v;
+    } else {
+      uint32_t hw[4], lw[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(x[2 * j], x[2 * j + 1]);
+        hw[j] = *reinterpret_cast<const uint32_t*>(&h2);
+        if constexpr (KIND == RK_BF16X3) {
+          const float2 hf = __bfloat1622float2(h2);
+          const __nv_bfloat162 l2 = __floats2bfloat162_rn(x[2 * j] - hf.x, x[2 * j + 1] - hf.y);
+          lw[j] = *reinterpret_cast<const uint32_t*>(&l2);
+        }
+      }
+      *reinterpret_cast<uint4*>(blk + A * 2 * npl + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+      if constexpr (KIND == RK_BF16X3)
+        *reinterpret_cast<uint4*>(blk + A * 2 * npl + npl + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+    }
+  }
+}
+
+// -------------------------------------------------------- a3/a4: contract --
+
+template <int KIND>
+__global__ void __launch_bounds__(RS_THREADS, 1) region_kernel(
+    const RItem* __restrict__ items, int nitems, const RPiece* __restrict__ pieces,
+    const RRowSeg* __restrict__ rsegs, const RColSeg* __restrict__ csegs,
+    const long long* __restrict__ stab, const unsigned char* __restrict__ planes,
+    float* __restrict__ slots, int* flag) {
+  using KT = KindT<KIND>;
+  extern __shared__ __align__(1024) unsigned char rsm[];
+  __shared__ __align__(8) unsigned long long full[RS_NSTAGE], empty[RS_NSTAGE], acc_full[2], acc_empty[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_s, issued_s, mma_steps_s;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // stage s: for chunk cc < SC: A planes then B planes
+  auto atile = [&](int s, int cc, int pl) {
+    return rsm + (size_t)s * RS_STAGE + (size_t)cc * KT::NPL * (RS_ATILE + RS_BTILE) + (size_t)pl * RS_ATILE;
+  };
+  auto btile = [&](int s, int cc, int pl) {
+    return rsm + (size_t)s * RS_STAGE + (size_t)cc * KT::NPL * (RS_ATILE + RS_BTILE) +
+           (size_t)KT::NPL * RS_ATILE + (size_t)pl * RS_BTILE;
+  };
+  if (tid == 0) {
+    for (int i = 0; i < RS_NSTAGE; ++i) {
+      mbar_init(smem_u32(&full[i]), 1);
+      mbar_init(smem_u32(&empty[i]), 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(smem_u32(&acc_full[i]), 1);
+      mbar_init(smem_u32(&acc_empty[i]), 4);
+    }
+    fence_mbar_init();
+    abort_s = 0;
+    issued_s = 0;
+    mma_steps_s = 0;
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(2 * RS_ACOLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+
+  auto wait = [&](unsigned long long* bar, uint32_t parity) -> bool {
+    const uint32_t a = smem_u32(bar);
+    for (int i = 0; i < (1 << 20); ++i) {
+      if (mbar_try(a, parity)) return true;
+      if (*(volatile int*)&abort_s) return false;
+    }
+    atomicExch(flag, 1);
+    *(volatile int*)&abort_s = 1;
+    return false;
+  };
+
+  if (warp == 0) {
+    // ---------------------------------------------------------- producer
+    int g = 0;
+    bool ok = true;
+    for (int ii = blockIdx.x; ii < nitems && ok; ii += gridDim.x) {
+      const RItem it = items[ii];
+      const int npc = it.npa + it.npb;
+      // stage bytes (every lane computes the same sum)
+      uint32_t sbytes = 0;
+      for (int j = 0; j < npc; ++j)
+        sbytes += (uint32_t)pieces[(j < it.npa ? it.pa0 + j : it.pb0 + j - it.npa)].bytes;
+      sbytes *= (uint32_t)(KT::SC * KT::NPL);
+      const int nst = it.ntiles * KT::CPT / KT::SC;
+      const long long c00 = (long long)it.tile0 * KT::CPT;
+      for (int st = 0; st < nst; ++st, ++g) {
+        const int s = g % RS_NSTAGE, u = g / RS_NSTAGE;
+        if (u > 0) {
+          bool w = true;
+          if (lane == 0) w = wait(&empty[s], (uint32_t)((u - 1) & 1));
+          ok = __shfl_sync(0xffffffffu, w ? 1 : 0, 0) != 0;
+          if (!ok) break;
+        }
+        const uint32_t mb = smem_u32(&full[s]);
+        if (lane == 0) mbar_arrive_expect(mb, sbytes);
+        __syncwarp();
+        for (int j = lane; j < npc; j += 32) {
+          const bool isA = j < it.npa;
+          const RPiece pc = pieces[isA ? it.pa0 + j : it.pb0 + j - it.npa];
+#pragma unroll
+          for (int cc = 0; cc < KT::SC; ++cc) {
+            const long long c = c00 + (long long)st * KT::SC + cc;
+            const unsigned char* src = planes + pc.base + c * pc.cb;
+#pragma unroll
+            for (int pl = 0; pl < KT::NPL; ++pl) {
+              unsigned char* dst = (isA ? atile(s, cc, pl) : btile(s, cc, pl)) + pc.dst;
+              bulk_g2s(smem_u32(dst), src + (pl ? pc.lo : 0), (uint32_t)pc.bytes, mb);
+            }
+          }
+        }
+        if (lane == 0) *(volatile int*)&issued_s = g + 1;
+      }
+    }
+  } else if (warp == 1) {
+    // --------------------------------------------------------------- MMA
+    if (lane == 0) {
+      int g = 0, item_no = 0;
+      bool ok = true;
+      for (int ii = blockIdx.x; ii < nitems && ok; ii += gridDim.x, ++item_no) {
+        const RItem it = items[ii];
+        const int b = item_no & 1, ub = item_no >> 1;
+        if (ub > 0 && !(ok = wait(&acc_empty[b], (uint32_t)((ub - 1) & 1)))) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t idesc = ridesc((uint32_t)KT::FMT, 128, (uint32_t)it.n_cols);
+        const uint32_t dacc = tmem + (uint32_t)(b * RS_ACOLS);
+        const int nst = it.ntiles * KT::CPT / KT::SC;
+        for (int st = 0; st < nst; ++st, ++g) {
+          const int s = g % RS_NSTAGE, u = g / RS_NSTAGE;
+          if (!(ok = wait(&full[s], (uint32_t)(u & 1)))) break;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+          for (int cc = 0; cc < KT::SC; ++cc) {
+            const uint64_t a0 = rdesc(smem_u32(atile(s, cc, 0)));
+            const uint64_t b0 = rdesc(smem_u32(btile(s, cc, 0)));
+            uint64_t a1 = 0, b1 = 0;
+            if constexpr (KT::NPL == 2) {
+              a1 = rdesc(smem_u32(atile(s, cc, 1)));
+              b1 = rdesc(smem_u32(btile(s, cc, 1)));
+            }
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {   // 32 bytes of K per MMA: two core columns
+              const uint64_t o = (uint64_t)((ks * 256) >> 4);
+              rmma<KT::FMT>(dacc, a0 + o, b0 + o, idesc, (st > 0 || cc > 0 || ks > 0) ? 1u : 0u);
+              if constexpr (KT::NPL == 2) {
+                rmma<KT::FMT>(dacc, a0 + o, b1 + o, idesc, 1u);
+                rmma<KT::FMT>(dacc, a1 + o, b0 + o, idesc, 1u);
+              }
+            }
+          }
+          rcommit(smem_u32(&empty[s]));
+          *(volatile int*)&mma_steps_s = g + 1;
+        }
+        if (!ok) break;
+        rcommit(smem_u32(&acc_full[b]));
+      }
+    }
+  } else {
+    // ---------------------------------------------------------- epilogue
+    const int q = warp & 3;   // TMEM lane quadrant
+    const int row = q * 32 + lane;
+    int item_no = 0;
+    bool ok = true;
+    for (int ii = blockIdx.x; ii < nitems && ok; ii += gridDim.x, ++item_no) {
+      const RItem it = items[ii];
+      const int b = item_no & 1, ub = item_no >> 1;
+      ok = __all_sync(0xffffffffu, wait(&acc_full[b], (uint32_t)(ub & 1)));
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      // this lane's row segment
+      int rs = -1, i = 0, na = 0;
+      for (int r = 0; r < it.nrs; ++r) {
+        const RRowSeg sg = rsegs[it.rs0 + r];
+        if (row >= sg.r0 && row < sg.r0 + sg.nr) {
+          rs = r;
+          i = sg.i0 + row - sg.r0;
+          na = sg.na;
+        }
+      }
+      const bool rok = rs >= 0 && i < na;
+      for (int c = 0; c < it.ncs; ++c) {
+        const RColSeg cs = csegs[it.cs0 + c];
+        const long long slot = rok ? stab[it.st0 + (long long)rs * it.ncf + cs.cf] : -1;
+        const int nbb = cs.nb;
+        for (int c0 = cs.c0; c0 < cs.c0 + cs.nc; c0 += 8) {
+          float v[8];
+          rtmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * RS_ACOLS + c0), v);
+          if (slot >= 0) {
+            float* o = slots + slot + (long long)i * 2 * nbb + cs.part * nbb;
+            const int j0 = cs.j0 + c0 - cs.c0;
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj)
+              if (j0 + jj < nbb) o[j0 + jj] = v[jj];
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&acc_empty[b]));
+    }
+  }
+
+  __syncthreads();
+  if (abort_s && tid == 0) {
+    // drain the copies of the last issued stages and the MMAs of the last
+    // committed stage before shared and tensor memory are released
+    auto drain = [&](unsigned long long* bar, uint32_t parity) {
+      const uint32_t a = smem_u32(bar);
+      for (int i = 0; i < (1 << 24) && !mbar_test(a, parity); ++i)
+        if (i > 64) __nanosleep(64);
+    };
+    const int issued = issued_s;
+    for (int g = max(0, issued - RS_NSTAGE); g < issued; ++g)
+      drain(&full[g % RS_NSTAGE], (uint32_t)((g / RS_NSTAGE) & 1));
+    const int ms = mma_steps_s;
+    if (ms > 0) drain(&empty[(ms - 1) % RS_NSTAGE], (uint32_t)(((ms - 1) / RS_NSTAGE) & 1));
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * RS_ACOLS)
+                 : "memory");
+}
+
+// ------------------------------------------------------------ a5: blocks ---
+
+// Pair p = blockIdx.x: S_ab and H_ab as sums of its slots in region order
+// ([i][S_j | H_j] rows of 2 n_b floats), accumulated error-free in FP32
+// (two-sum: the rounding error of every addition is carried in a second
+// FP32 word, so the result is the FP64 value of the FP32 terms' sum to
+// about 2^-44 relative, without FP64 arithmetic per term); a diagonal block
+// is symmetrised, (X + X^T) / 2.
+__device__ __forceinline__ void two_sum(float& s, float& e, float x) {
+  const float t = s + x;
+  const float bp = t - s;
+  e += (s - (t - bp)) + (x - bp);
+  s = t;
+}
+
+__global__ void rfinalize_kernel(const RPair* __restrict__ prs, const float* __restrict__ slots,
+                                 double* __restrict__ blocks) {
+  const RPair pr = prs[blockIdx.x];
+  const int na = pr.na, nb = pr.nb;
+  const long long ss = (long long)na * 2 * nb;
+  double* Hblk = blocks + pr.blk_off;
+  double* Sblk = Hblk + (long long)na * nb;
+  auto sum = [&](int i, int c) {
+    float s = 0.f, e = 0.f;
+    const float* p = slots + pr.slot0 + (long long)i * 2 * nb + c;
+    for (int k = 0; k < pr.nslot; ++k) two_sum(s, e, p[k * ss]);
+    return (double)s + (double)e;
+  };
+  for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < na * nb; e += gridDim.y * blockDim.x) {
+    const int i = e / nb, m = e - (e / nb) * nb;
+    double s = sum(i, m), h = sum(i, nb + m);
+    if (pr.a == pr.b) {
+      s = 0.5 * (s + sum(m, i));
+      h = 0.5 * (h + sum(m, nb + i));
+    }
+    Sblk[e] = s;
+    Hblk[e] = h;
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- planner ----
+
+struct RegionPlan {
+  std::vector<RUnit> units;
+  std::vector<RItem> items;
+  std::vector<RPiece> pieces;
+  std::vector<RRowSeg> rsegs;
+  std::vector<RColSeg> csegs;
+  std::vector<long long> stab;
+  std::vector<RPair> rpairs;
+  long long plane_bytes = 0, slot_elems = 0, total_tiles = 0;
+  double mma_flops = 0.0;     // MMA work per 64-point tile summed (M 128 x N), for one product
+  int nregions = 0, nparts = 0, w_min = 1;
+  DevBuf d_units, d_items, d_pieces, d_rsegs, d_csegs, d_stab, d_rpairs, planes, slots;
+  bool ok = false;
+  bool uploaded = false;
+  std::string why;
+};
+
+namespace {
+
+struct Seg { int s0, len; };
+
+// Segments of one periodic dimension cut at every dilated-box boundary;
+// segments shorter than w_min are merged into a neighbour.
+std::vector<Seg> dim_segments(int n, const std::vector<DevFrag>& fr, int d, int w_min) {
+  std::vector<int> bp;
+  for (const DevFrag& f : fr)
+    if (!f.full[d]) {
+      bp.push_back(f.doff[d] % n);
+      bp.push_back((f.doff[d] + f.dext[d]) % n);
+    }
+  std::sort(bp.begin(), bp.end());
+  bp.erase(std::unique(bp.begin(), bp.end()), bp.end());
+  std::vector<Seg> s;
+  if (bp.empty()) {
+    s.push_back({0, n});
+    return s;
+  }
+  const int m = (int)bp.size();
+  for (int i = 0; i < m; ++i) {
+    const int a = bp[i], b = i + 1 < m ? bp[i + 1] : bp[0] + n;
+    s.push_back({a, b - a});
+  }
+  // merge short segments into the shorter neighbour (cyclic)
+  while (s.size() > 1) {
+    int k = -1;
+    for (int i = 0; i < (int)s.size(); ++i)
+      if (s[i].len < w_min && (k < 0 || s[i].len < s[k].len)) k = i;
+    if (k < 0) break;
+    const int ns = (int)s.size();
+    const int l = (k + ns - 1) % ns, r = (k + 1) % ns;
+    if (s[l].len <= s[r].len) {
+      s[l].len += s[k].len;
+      s.erase(s.begin() + k);
+    } else {
+      s[r].s0 = s[k].s0;
+      s[r].len += s[k].len;
+      s.erase(s.begin() + k);
+    }
+  }
+  for (auto& x : s) x.s0 %= n;
+  return s;
+}
+
+bool meets(int n, int s0, int len, int d0, int dl) {
+  if (dl >= n || len >= n) return true;
+  const int a = ((s0 - d0) % n + n) % n;   // segment start relative to the interval
+  const int b = ((d0 - s0) % n + n) % n;   // interval start relative to the segment
+  return a < dl || b < len;
+}
+
+}  // namespace
+
+// Builds the region plan: returns OFM_OK with plan->ok false (and why) when
+// this path does not apply (more than 128 states, too many slots).
+// pair_pts (nullable): per pair, the points of B_a ∩ B_b+ inside the
+// regions that hold both fragments, counted point by point (a check of the
+// cover sets).
+static void region_plan_build(const int gn[3], RegionPlan* P, const std::vector<DevFrag>& fr,
+                              const std::vector<HostPair>& prs, const std::vector<long long>& blk_off,
+                              int w_min_req, long long slot_budget_bytes,
+                              std::vector<long long>* pair_pts = nullptr) {
+  P->units.clear(); P->items.clear(); P->pieces.clear(); P->rsegs.clear(); P->csegs.clear();
+  P->stab.clear(); P->rpairs.clear();
+  P->ok = false;
+  P->uploaded = false;
+  P->mma_flops = 0.0;
+  const int nf = (int)fr.size();
+  for (const DevFrag& f : fr)
+    if ((f.n + 7) / 8 * 8 > RS_MAXROWS) {
+      P->why = "region contraction takes at most 128 states per fragment";
+      return;
+    }
+  // segments, coarsened until the (fragment, region) incidences stay bounded
+  std::vector<Seg> seg[3];
+  std::vector<std::vector<int>> fseg[3];   // per dim, per fragment: segment indices it meets
+  int w_min = std::max(1, w_min_req);
+  for (;;) {
+    long long inc = 0;
+    for (int d = 0; d < 3; ++d) {
+      seg[d] = dim_segments(gn[d], fr, d, w_min);
+      fseg[d].assign(nf, {});
+      for (int a = 0; a < nf; ++a)
+        for (int i = 0; i < (int)seg[d].size(); ++i)
+          if (fr[a].full[d] || meets(gn[d], seg[d][i].s0, seg[d][i].len, fr[a].doff[d], fr[a].dext[d]))
+            fseg[d][a].push_back(i);
+    }
+    for (int a = 0; a < nf; ++a)
+      inc += (long long)fseg[0][a].size() * fseg[1][a].size() * fseg[2][a].size();
+    if (inc <= 4000000 || w_min >= 64) break;
+    w_min *= 2;
+  }
+  P->w_min = w_min;
+  const long long nsx = seg[0].size(), nsy = seg[1].size(), nsz = seg[2].size();
+  // cover sets (fragments in increasing order)
+  std::unordered_map<long long, std::vector<int>> cover;
+  for (int a = 0; a < nf; ++a)
+    for (int k : fseg[2][a])
+      for (int j : fseg[1][a])
+        for (int i : fseg[0][a]) cover[i + nsx * (j + nsy * (long long)k)].push_back(a);
+  std::vector<long long> keys;
+  keys.reserve(cover.size());
+  for (auto& kv : cover) keys.push_back(kv.first);
+  std::sort(keys.begin(), keys.end());
+  P->nregions = (int)keys.size();
+  std::unordered_map<long long, int> pidx;
+  pidx.reserve(prs.size() * 2);
+  for (int p = 0; p < (int)prs.size(); ++p) pidx[(long long)prs[p].a * nf + prs[p].b] = p;
+  std::vector<int> rows(nf);
+  for (int a = 0; a < nf; ++a) rows[a] = (fr[a].n + 7) / 8 * 8;
+
+  // plane arena: one block per (fragment, region), 8 bytes per (point, padded state)
+  struct RInfo { long long key; int ix, iy, iz, npts, ntiles; };
+  std::vector<RInfo> regs(keys.size());
+  std::vector<std::unordered_map<long long, long long>> fbase(nf);
+  long long arena = 0, tiles = 0, total_work = 0;
+  for (size_t r = 0; r < keys.size(); ++r) {
+    const long long key = keys[r];
+    RInfo& R = regs[r];
+    R.key = key;
+    R.ix = (int)(key % nsx);
+    R.iy = (int)((key / nsx) % nsy);
+    R.iz = (int)(key / (nsx * nsy));
+    R.npts = seg[0][R.ix].len * seg[1][R.iy].len * seg[2][R.iz].len;
+    R.ntiles = (R.npts + 63) / 64;
+    long long M = 0;
+    for (int a : cover[key]) {
+      RUnit u;
+      u.frag = a;
+      u.s0[0] = seg[0][R.ix].s0; u.s0[1] = seg[1][R.iy].s0; u.s0[2] = seg[2][R.iz].s0;
+      u.L[0] = seg[0][R.ix].len; u.L[1] = seg[1][R.iy].len; u.L[2] = seg[2][R.iz].len;
+      u.npts = R.npts;
+      u.tile0 = tiles;
+      u.base = arena;
+      fbase[a][key] = arena;
+      arena += (long long)R.ntiles * 64 * rows[a] * 8;
+      tiles += R.ntiles;
+      P->units.push_back(u);
+      M += rows[a];
+    }
+    // work in (tile x N-tile x M-tile) units, for the K split below
+    const long long mt = (M + 127) / 128;
+    total_work += (long long)R.ntiles * mt * ((2 * M + 255) / 256);
+  }
+  P->plane_bytes = arena;
+  P->total_tiles = tiles;
+  // K split: about six items of equal work per SM, parts of at least 4 tiles
+  const long long target = std::max<long long>(4, total_work / (6 * 152));
+
+  // slots: count per pair first
+  std::vector<int> nslot(prs.size(), 0);
+  struct PartInfo { int r, t0, nt; };
+  std::vector<PartInfo> parts;
+  for (size_t r = 0; r < regs.size(); ++r) {
+    const std::vector<int>& C = cover[regs[r].key];
+    long long M = 0;
+    for (int a : C) M += rows[a];
+    const long long per_tile = ((M + 127) / 128) * ((2 * M + 255) / 256);
+    const int nt = regs[r].ntiles;
+    int nsplit = (int)std::min<long long>(std::max<long long>(1, nt / 4),
+                                          std::max<long long>(1, (nt * per_tile + target - 1) / target));
+    for (int s = 0; s < nsplit; ++s) {
+      const int t0 = (int)((long long)nt * s / nsplit), t1 = (int)((long long)nt * (s + 1) / nsplit);
+      if (t1 > t0) parts.push_back({(int)r, t0, t1 - t0});
+    }
+    for (size_t x = 0; x < C.size(); ++x)
+      for (size_t y = x; y < C.size(); ++y) {
+        auto it = pidx.find((long long)C[x] * nf + C[y]);
+        if (it != pidx.end()) nslot[it->second] += nsplit;
+      }
+  }
+  P->nparts = (int)parts.size();
+  P->rpairs.resize(prs.size());
+  long long se = 0;
+  for (size_t p = 0; p < prs.size(); ++p) {
+    RPair& q = P->rpairs[p];
+    q.a = prs[p].a;
+    q.b = prs[p].b;
+    q.na = fr[q.a].n;
+    q.nb = fr[q.b].n;
+    q.nslot = nslot[p];
+    q.slot0 = se;
+    q.blk_off = blk_off[p];
+    se += (long long)nslot[p] * q.na * 2 * q.nb;
+  }
+  P->slot_elems = se;
+  if (se * 4 > slot_budget_bytes) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "region contraction needs %.1f GB of partial slots (budget %.1f GB)",
+             se * 4e-9, slot_budget_bytes * 1e-9);
+    P->why = buf;
+    return;
+  }
+  if (pair_pts) {
+    // |R ∩ B_a ∩ B_b+| per dimension by walking the segment's points
+    pair_pts->assign(prs.size(), 0);
+    auto count = [&](int d, const Seg& sg, const DevFrag& A, const DevFrag& B) {
+      long long k = 0;
+      for (int t = 0; t < sg.len; ++t) {
+        const int g = (sg.s0 + t) % gn[d];
+        const int la = ((g - A.doff[d]) % gn[d] + gn[d]) % gn[d];
+        const int lb = ((g - B.doff[d]) % gn[d] + gn[d]) % gn[d];
+        if (la >= A.lo[d] && la < A.lo[d] + A.ext[d] && lb < B.dext[d]) ++k;
+      }
+      return k;
+    };
+    for (const RInfo& R : regs) {
+      const std::vector<int>& C = cover[R.key];
+      for (size_t x = 0; x < C.size(); ++x)
+        for (size_t y = x; y < C.size(); ++y) {
+          auto it = pidx.find((long long)C[x] * nf + C[y]);
+          if (it == pidx.end()) continue;
+          const DevFrag &A = fr[C[x]], &B = fr[C[y]];
+          (*pair_pts)[it->second] += count(0, seg[0][R.ix], A, B) * count(1, seg[1][R.iy], A, B) *
+                                     count(2, seg[2][R.iz], A, B);
+        }
+    }
+  }
+  std::vector<int> used(prs.size(), 0);
+
+  // items
+  for (const PartInfo& pt : parts) {
+    const RInfo& R = regs[pt.r];
+    const std::vector<int>& C = cover[R.key];
+    const int nc = (int)C.size();
+    std::vector<int> r0(nc + 1, 0);
+    for (int x = 0; x < nc; ++x) r0[x + 1] = r0[x] + rows[C[x]];
+    const int M = r0[nc];
+    // this part's slot of every pair in the cover
+    std::vector<long long> slot(nc * nc, -1);
+    for (int x = 0; x < nc; ++x)
+      for (int y = x; y < nc; ++y) {
+        auto it = pidx.find((long long)C[x] * nf + C[y]);
+        if (it == pidx.end()) continue;
+        const int p = it->second;
+        const RPair& q = P->rpairs[p];
+        slot[x * nc + y] = q.slot0 + (long long)used[p]++ * q.na * 2 * q.nb;
+      }
+    for (int m0 = 0; m0 < M; m0 += 128) {
+      const int m1 = std::min(M, m0 + 128);
+      int xlo = 0;
+      while (r0[xlo + 1] <= m0) ++xlo;
+      for (int n0 = 2 * r0[xlo]; n0 < 2 * M; n0 += 256) {
+        const int n1 = std::min(2 * M, n0 + 256);
+        RItem it;
+        it.tile0 = pt.t0;
+        it.ntiles = pt.nt;
+        it.n_cols = n1 - n0;
+        it.pa0 = (int)P->pieces.size();
+        it.rs0 = (int)P->rsegs.size();
+        std::vector<int> rfr;   // cover index of each row segment
+        for (int x = xlo; x < nc && r0[x] < m1; ++x) {
+          const int lo = std::max(m0, r0[x]), hi = std::min(m1, r0[x + 1]);
+          if (hi <= lo) continue;
+          const long long base = fbase[C[x]][R.key];
+          RPiece pc;
+          pc.cb = rows[C[x]] * 64;
+          pc.base = base + (long long)((lo - r0[x]) / 8) * 512;
+          pc.lo = (long long)R.ntiles * 64 * rows[C[x]] * 2;
+          pc.bytes = (hi - lo) / 8 * 512;
+          pc.dst = (lo - m0) / 8 * 512;
+          pc.pad = 0;
+          P->pieces.push_back(pc);
+          RRowSeg rs;
+          rs.r0 = lo - m0;
+          rs.nr = hi - lo;
+          rs.i0 = lo - r0[x];
+          rs.na = fr[C[x]].n;
+          P->rsegs.push_back(rs);
+          rfr.push_back(x);
+        }
+        it.npa = (int)P->pieces.size() - it.pa0;
+        it.nrs = (int)P->rsegs.size() - it.rs0;
+        it.pb0 = (int)P->pieces.size();
+        it.cs0 = (int)P->csegs.size();
+        std::vector<int> cfr;   // cover index of each column fragment
+        for (int x = 0; x < nc; ++x) {
+          for (int part = 0; part < 2; ++part) {
+            const int cbeg = 2 * r0[x] + part * rows[C[x]], cend = cbeg + rows[C[x]];
+            const int lo = std::max(n0, cbeg), hi = std::min(n1, cend);
+            if (hi <= lo) continue;
+            const long long base = fbase[C[x]][R.key];
+            RPiece pc;
+            pc.cb = rows[C[x]] * 64;
+            const long long half = (long long)R.ntiles * 64 * rows[C[x]] * 4;
+            pc.base = base + part * half + (long long)((lo - cbeg) / 8) * 512;
+            pc.lo = (long long)R.ntiles * 64 * rows[C[x]] * 2;
+            pc.bytes = (hi - lo) / 8 * 512;
+            pc.dst = (lo - n0) / 8 * 512;
+            pc.pad = 0;
+            P->pieces.push_back(pc);
+            if (cfr.empty() || cfr.back() != x) cfr.push_back(x);
+            RColSeg cs;
+            cs.c0 = lo - n0;
+            cs.nc = hi - lo;
+            cs.j0 = lo - cbeg;
+            cs.nb = fr[C[x]].n;
+            cs.part = part;
+            cs.cf = (int)cfr.size() - 1;
+            P->csegs.push_back(cs);
+          }
+        }
+        it.npb = (int)P->pieces.size() - it.pb0;
+        it.ncs = (int)P->csegs.size() - it.cs0;
+        it.ncf = (int)cfr.size();
+        it.st0 = (long long)P->stab.size();
+        for (int x : rfr)
+          for (int y : cfr) P->stab.push_back(x <= y ? slot[x * nc + y] : -1);
+        P->mma_flops += 2.0 * 128 * it.n_cols * 64.0 * it.ntiles;
+        P->items.push_back(it);
+      }
+    }
+  }
+  P->ok = true;
+}
+
+// ------------------------------------------------------------- runtime ----
+
+template <typename T>
+static ofm_status upload(ofm_ctx* c, DevBuf& b, const std::vector<T>& v, const char* what) {
+  OFM_TRY(ofm_ensure(c, b, sizeof(T) * std::max<size_t>(1, v.size()), what));
+  if (!v.empty())
+    OFM_CUDA(c, cudaMemcpyAsync(b.p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, c->stream));
+  return OFM_OK;
+}
+
+void ofm_region_free(ofm_ctx* c) {
+  RegionPlan* P = c->region;
+  if (!P) return;
+  DevBuf* bufs[] = {&P->d_units, &P->d_items, &P->d_pieces, &P->d_rsegs, &P->d_csegs,
+                    &P->d_stab, &P->d_rpairs, &P->planes, &P->slots};
+  for (DevBuf* b : bufs)
+    if (b->p) cudaFree(b->p);
+  delete P;
+  c->region = nullptr;
+}
+
+// The region plan of the context's current fragments and pairs (host tables
+// only; device buffers on first use).
+ofm_status ofm_region_plan(ofm_ctx* c) {
+  if (!c->region) c->region = new RegionPlan();
+  RegionPlan* P = c->region;
+  if (c->storage != OFM_STORE_FP32) {
+    P->ok = false;
+    P->uploaded = false;
+    P->why = "region contraction needs FP32 storage";
+    return OFM_OK;
+  }
+  std::vector<long long> off(c->pairs.size());
+  for (size_t p = 0; p < c->pairs.size(); ++p) off[p] = c->simt_pairs[p].blk_off;
+  region_plan_build(c->grid.n, P, c->frags, c->pairs, off, c->region_wmin, 16LL << 30);
+  return OFM_OK;
+}
+
+bool ofm_region_ok(const ofm_ctx* c) { return c->region && c->region->ok; }
+
+const char* ofm_region_why(const ofm_ctx* c) {
+  return c->region ? c->region->why.c_str() : "no region plan";
+}
+
+ofm_status ofm_region_prepare(ofm_ctx* c) {
+  RegionPlan* P = c->region;
+  if (P->uploaded) return OFM_OK;
+  OFM_TRY(upload(c, P->d_units, P->units, "region units"));
+  OFM_TRY(upload(c, P->d_items, P->items, "region items"));
+  OFM_TRY(upload(c, P->d_pieces, P->pieces, "region pieces"));
+  OFM_TRY(upload(c, P->d_rsegs, P->rsegs, "region row segments"));
+  OFM_TRY(upload(c, P->d_csegs, P->csegs, "region column segments"));
+  OFM_TRY(upload(c, P->d_stab, P->stab, "region slot table"));
+  OFM_TRY(upload(c, P->d_rpairs, P->rpairs, "region pairs"));
+  OFM_TRY(ofm_ensure_big(c, P->planes, (size_t)P->plane_bytes, "operand planes"));
+  OFM_TRY(ofm_ensure_big(c, P->slots, sizeof(float) * (size_t)std::max<long long>(1, P->slot_elems),
+                         "partial slots"));
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(region_kernel<RK_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, RS_SMEM);
+    cudaFuncSetAttribute(region_kernel<RK_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, RS_SMEM);
+    cudaFuncSetAttribute(region_kernel<RK_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, RS_SMEM);
+    const int pk = 2 * 64 * (RS_MAXROWS + 2) * 4;   // phi and H phi, 64 points x (rows + pad) words
+    cudaFuncSetAttribute(pack_kernel<RK_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, pk);
+    cudaFuncSetAttribute(pack_kernel<RK_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, pk);
+    cudaFuncSetAttribute(pack_kernel<RK_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, pk);
+    OFM_CUDA(c, cudaGetLastError());
+    attr = true;
+  }
+  P->uploaded = true;
+  return OFM_OK;
+}
+
+// a1 (apply + pack), a3/a4 (region contraction) and a5 (blocks) for one
+// tensor-core precision, enqueued on the context stream.
+ofm_status ofm_region_run(ofm_ctx* c, ofm_precision prec) {
+  RegionPlan* P = c->region;
+  if (!P || !P->ok) return ofm_fail(c, OFM_ERR_INVALID, P ? P->why : "no region plan");
+  if (!P->uploaded) return ofm_fail(c, OFM_ERR_STATE, "region plan not prepared");
+  const int kind = prec == OFM_PREC_TF32 ? RK_TF32 : prec == OFM_PREC_BF16 ? RK_BF16 : RK_BF16X3;
+  int maxrows = 8;
+  for (const DevFrag& f : c->frags) maxrows = std::max(maxrows, (f.n + 7) / 8 * 8);
+  const double h = c->grid.h;
+  const float c0 = (float)(3.0 / (h * h)), c1 = (float)(0.5 / (h * h));
+  {
+    KTimer t(c, KC_APPLY, 1, c->pack_bytes[kind]);
+    if (P->total_tiles > 0) {
+      const int nu = (int)P->units.size();
+      const RUnit* u = (const RUnit*)P->d_units.p;
+      const DevFrag* f = (const DevFrag*)c->d_frags.p;
+      const float* V = (const float*)c->V.p;
+      const float* st = (const float*)c->states.p;
+      unsigned char* pl = (unsigned char*)P->planes.p;
+      const unsigned grid = (unsigned)P->total_tiles;
+      if (kind == RK_TF32)
+        pack_kernel<RK_TF32><<<grid, PK_THREADS, 2 * 64 * (maxrows + 2) * 4, c->stream>>>(
+            u, nu, f, V, st, pl, c->grid.n[0], c->grid.n[1], c->grid.n[2], c0, c1);
+      else if (kind == RK_BF16)
+        pack_kernel<RK_BF16><<<grid, PK_THREADS, 2 * 64 * (maxrows + 1) * 4, c->stream>>>(
+            u, nu, f, V, st, pl, c->grid.n[0], c->grid.n[1], c->grid.n[2], c0, c1);
+      else
+        pack_kernel<RK_BF16X3><<<grid, PK_THREADS, 2 * 64 * (maxrows + 1) * 4, c->stream>>>(
+            u, nu, f, V, st, pl, c->grid.n[0], c->grid.n[1], c->grid.n[2], c0, c1);
+    }
+    OFM_CUDA(c, cudaGetLastError());
+  }
+  int* fl = (int*)c->flag.p + OFM_FLAG_TC;
+  {
+    KTimer t(c, KC_CONTRACT, 1, c->region_bytes[kind], (double)c->flops);
+    const int ni = (int)P->items.size();
+    if (ni > 0) {
+      const int grid = std::min(ni, 152);
+      const RItem* it = (const RItem*)P->d_items.p;
+      const RPiece* pc = (const RPiece*)P->d_pieces.p;
+      const RRowSeg* rs = (const RRowSeg*)P->d_rsegs.p;
+      const RColSeg* cs = (const RColSeg*)P->d_csegs.p;
+      const long long* sb = (const long long*)P->d_stab.p;
+      const unsigned char* pl = (const unsigned char*)P->planes.p;
+      float* sl = (float*)P->slots.p;
+      if (kind == RK_TF32)
+        region_kernel<RK_TF32><<<grid, RS_THREADS, RS_SMEM, c->stream>>>(it, ni, pc, rs, cs, sb, pl, sl, fl);
+      else if (kind == RK_BF16)
+        region_kernel<RK_BF16><<<grid, RS_THREADS, RS_SMEM, c->stream>>>(it, ni, pc, rs, cs, sb, pl, sl, fl);
+      else
+        region_kernel<RK_BF16X3><<<grid, RS_THREADS, RS_SMEM, c->stream>>>(it, ni, pc, rs, cs, sb, pl, sl, fl);
+    }
+    OFM_CUDA(c, cudaGetLastError());
+  }
+  {
+    KTimer t(c, KC_FINALIZE, 1, (double)P->slot_elems * 4 + 16.0 * c->blk_elems);
+    int nmax = 1, amax = 1;
+    for (const RPair& q : P->rpairs) {
+      nmax = std::max(nmax, q.nb);
+      amax = std::max(amax, q.na);
+    }
+    const int chunks = std::max(1, (amax * nmax + 255) / 256);
+    if (!P->rpairs.empty())
+      rfinalize_kernel<<<dim3((unsigned)P->rpairs.size(), (unsigned)chunks), 256, 0, c->stream>>>(
+          (const RPair*)P->d_rpairs.p, (const float*)P->slots.p, (double*)c->blocks.p);
+    OFM_CUDA(c, cudaGetLastError());
+  }
+  c->tc_check = true;
+  return OFM_OK;
+}
+
+// Host statistics of the region plan (for the planner query).
+void ofm_region_stats(const ofm_ctx* c, long long* out) {
+  const RegionPlan* P = c->region;
+  if (!P) return;
+  out[0] = P->ok;
+  out[1] = P->nregions;
+  out[2] = P->nparts;
+  out[3] = (long long)P->items.size();
+  out[4] = P->plane_bytes;
+  out[5] = P->slot_elems * 4;
+  out[6] = (long long)P->mma_flops;
+  out[7] = P->w_min;
+}
+
+extern "C" ofm_status ofm_plan_regions(const ofm_grid* grid, const ofm_fragment* frags, int n_frag,
+                                       int w_min, long long* stats, long long* pair_points,
+                                       int max_pairs) {
+  if (!grid || !frags) return OFM_ERR_INVALID;
+  std::string err;
+  if (!validate_geometry(*grid, frags, n_frag, err)) return OFM_ERR_INVALID;
+  std::vector<DevFrag> fr;
+  long long tot = 0;
+  make_frag_table(*grid, frags, n_frag, fr, tot);
+  std::vector<HostPair> pairs;
+  make_pairs(*grid, fr, pairs);
+  std::vector<long long> off(pairs.size());
+  long long blk = 0;
+  for (size_t p = 0; p < pairs.size(); ++p) {
+    off[p] = blk;
+    blk += 2LL * fr[pairs[p].a].n * fr[pairs[p].b].n;
+  }
+  RegionPlan P;
+  std::vector<long long> pts;
+  region_plan_build(grid->n, &P, fr, pairs, off, w_min, 16LL << 30, pair_points ? &pts : nullptr);
+  if (stats) {
+    stats[0] = P.ok;
+    stats[1] = P.nregions;
+    stats[2] = P.nparts;
+    stats[3] = (long long)P.items.size();
+    stats[4] = P.plane_bytes;
+    stats[5] = P.slot_elems * 4;
+    stats[6] = (long long)P.mma_flops;
+    stats[7] = P.w_min;
+  }
+  if (pair_points)
+    for (int i = 0; i < (int)pts.size() && i < max_pairs; ++i) pair_points[i] = pts[i];
+  return OFM_OK;
+}

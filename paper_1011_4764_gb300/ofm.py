@@ -30,8 +30,9 @@ EXPORTS = [
     "ofm_get_dense_HS", "ofm_get_hphi", "ofm_window_eigs", "ofm_eigs_by_index",
     "ofm_set_dense_HS", "ofm_plan_pairs", "ofm_set_profiling", "ofm_get_kernel_stats",
     "ofm_pair_blocks_noalloc", "ofm_set_pair_cutoff", "ofm_select_states", "ofm_homo_lumo_gap",
-    "ofm_window_from_index", "ofm_autotune_assembly", "ofm_pencil_apply",
+    "ofm_window_from_index", "ofm_autotune_assembly", "ofm_pencil_apply", "ofm_plan_regions",
 ]
+SCHEDULE = {"auto": 0, "pair": 1, "region": 2}
 
 
 # fragment geometry with the state count of the current basis
@@ -52,12 +53,12 @@ class ofm_eig_opts(C.Structure):
 
 
 class ofm_assemble_opts(C.Structure):
-    _fields_ = [("chunk_points", C.c_int), ("use_graph", C.c_int)]
+    _fields_ = [("chunk_points", C.c_int), ("use_graph", C.c_int), ("schedule", C.c_int)]
 
 
 class ofm_tune_result(C.Structure):
     _fields_ = [("chunk_points", C.c_int), ("stencil_form", C.c_int), ("ms", C.c_double),
-                ("n_tried", C.c_int)]
+                ("n_tried", C.c_int), ("schedule", C.c_int), ("region_ms", C.c_double)]
 
 
 class ofm_plan_info(C.Structure):
@@ -117,6 +118,8 @@ def load_library(path: str = LIB_PATH):
         "ofm_window_from_index": ([P, I, D, I, DP, IP], I),
         "ofm_autotune_assembly": ([P, I, IP, I, I, DP, C.POINTER(ofm_tune_result)], I),
         "ofm_pencil_apply": ([P, I, P, C.c_longlong, P, C.c_longlong, I], I),
+        "ofm_plan_regions": ([C.POINTER(ofm_grid), C.POINTER(ofm_fragment), I, I,
+                              C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), I], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -172,6 +175,23 @@ def plan_pairs(grid, frags):
     lib.ofm_plan_pairs(C.byref(g), fa, len(frags), C.byref(n), _iptr(ab),
                        cnt.ctypes.data_as(C.POINTER(C.c_longlong)), n.value, C.byref(F))
     return [tuple(map(int, ab[2 * i:2 * i + 2])) for i in range(n.value)], cnt.reshape(-1, 2), F.value
+
+
+def plan_regions(grid, frags, w_min=1):
+    """Host-only query of the region plan: (stats dict, per-pair points of
+    B_a ∩ B_b+ covered by the regions holding both fragments)."""
+    lib = load_library()
+    g, fa = _c_geometry(grid, frags)
+    pairs, _, _ = plan_pairs(grid, frags)
+    st = np.zeros(8, dtype=np.int64)
+    pts = np.zeros(max(1, len(pairs)), dtype=np.int64)
+    LP = C.POINTER(C.c_longlong)
+    s = lib.ofm_plan_regions(C.byref(g), fa, len(frags), int(w_min), st.ctypes.data_as(LP),
+                             pts.ctypes.data_as(LP), len(pairs))
+    if s != OFM_OK:
+        raise OFMError(s, "invalid geometry")
+    keys = ("ok", "regions", "parts", "items", "plane_bytes", "slot_bytes", "mma_flops", "w_min")
+    return dict(zip(keys, map(int, st))), pts[:len(pairs)]
 
 
 def pair_blocks_noalloc(grid, fa, fb, phi_a, phi_b, hphi_b, out, stream=0):
@@ -276,15 +296,19 @@ class Context:
         return out.T
 
     # -- ofm_assemble_HS
-    def assemble(self, precision="fp32", chunk_points=0, use_graph=True):
-        o = ofm_assemble_opts(chunk_points, 1 if use_graph else 0)
+    def assemble(self, precision="fp32", chunk_points=0, use_graph=True, schedule="auto"):
+        """schedule (tensor-core precisions): "auto" (the context's choice),
+        "pair" (one GEMM per pair) or "region" (coverage regions stacked)."""
+        o = ofm_assemble_opts(chunk_points, 1 if use_graph else 0, SCHEDULE[schedule])
         self._check(self.lib.ofm_assemble_HS(self.h, PREC[precision], C.byref(o)))
 
     # -- ofm_autotune_assembly
     def autotune_assembly(self, precision="fp32", chunks=None, reps=3):
-        """Times every (stencil form, chunk) candidate and keeps the fastest.
-        Returns (chunk_points, stencil_form, ms, times) with times a
-        (2, n_candidates) array of mean milliseconds (-1: form does not fit)."""
+        """Times every (stencil form, chunk) candidate of the pair schedule and,
+        for the tensor-core precisions, the region schedule, and keeps the
+        fastest.  Returns (chunk_points, stencil_form, ms, times) with times a
+        (2, n_candidates) array of mean milliseconds (-1: form does not fit);
+        self.tuned holds the schedule chosen and the region time."""
         cand = None if chunks is None else np.ascontiguousarray(chunks, dtype=np.int32)
         nc = 5 if cand is None else len(cand)
         times = np.full(2 * nc, -1.0)
@@ -292,6 +316,8 @@ class Context:
         self._check(self.lib.ofm_autotune_assembly(
             self.h, PREC[precision], None if cand is None else _iptr(cand), nc, int(reps),
             _dptr(times), C.byref(r)))
+        self.tuned = {"schedule": {1: "pair", 2: "region"}.get(r.schedule, "pair"),
+                      "region_ms": r.region_ms}
         return r.chunk_points, r.stencil_form, r.ms, times.reshape(2, nc)
 
     # -- ofm_pencil_apply

@@ -1,5 +1,7 @@
 """Tensor-core (tcgen05) pair contraction in TF32, BF16 and BF16 hi+lo
-against the FP64 oracle on the same FP32 states.
+against the FP64 oracle on the same FP32 states, in both schedules: one GEMM
+per pair, and coverage regions with their fragments stacked into one GEMM
+(the region sums are FP32 over each region's points, FP64 across regions).
 
 Per-entry bound (Higham's inner-product bound with rounded inputs):
     |err| <= (2 u_in + 2 K u_32) sum_r |phi_a(r)| |phi_b(r)|
@@ -68,9 +70,10 @@ def check_blocks(ctx, wl, Phis, H, pairs, prec):
     return worst
 
 
+@pytest.mark.parametrize("sched", ["pair", "region"])
 @pytest.mark.parametrize("prec", ["tf32", "bf16", "bf16x3"])
 @pytest.mark.parametrize("geom", sorted(GEOMS))
-def test_tensor_core_blocks_within_bounds(ofm, geom, prec):
+def test_tensor_core_blocks_within_bounds(ofm, geom, prec, sched):
     grid, frags = GEOMS[geom]
     wl = small_workload(grid_n=grid.n, h=grid.h, frags=frags, seed=3)
     Phis = fp32_states(grid, frags, 500)
@@ -79,12 +82,18 @@ def test_tensor_core_blocks_within_bounds(ofm, geom, prec):
     ctx.build_fragments(grid, wl.V, frags, storage="fp32")
     for a, P in enumerate(Phis):
         ctx.set_fragment_states(a, P)
-    ctx.assemble(prec)
+    ctx.assemble(prec, schedule=sched)
     check_blocks(ctx, wl, Phis, H, O.pair_list(grid, frags), prec)
+    # a second assembly (captured graph replay) gives the same blocks bit for bit
+    H01 = ctx.block(0, 1)
+    ctx.assemble(prec, schedule=sched)
+    H01b = ctx.block(0, 1)
+    assert np.array_equal(H01[0], H01b[0]) and np.array_equal(H01[1], H01b[1])
 
 
+@pytest.mark.parametrize("sched", ["pair", "region"])
 @pytest.mark.parametrize("prec", ["tf32", "bf16x3"])
-def test_tensor_core_alkane_full_size_sampled(ofm, prec):
+def test_tensor_core_alkane_full_size_sampled(ofm, prec, sched):
     wl = make_workload("alkane")
     Phis = fp32_states(wl.grid, wl.frags, 900)
     H = O.hamiltonian(wl.grid, wl.V)
@@ -92,12 +101,14 @@ def test_tensor_core_alkane_full_size_sampled(ofm, prec):
     ctx.build_fragments(wl.grid, wl.V, wl.frags, storage="fp32")
     for a, P in enumerate(Phis):
         ctx.set_fragment_states(a, P)
-    ctx.assemble(prec)
-    check_blocks(ctx, wl, Phis, H, [(0, 0), (0, 1), (0, 30), (14, 15), (15, 17), (30, 30)], prec)
+    ctx.assemble(prec, schedule=sched)
+    check_blocks(ctx, wl, Phis, H, [(0, 0), (0, 1), (0, 2), (0, 30), (14, 15), (15, 17), (30, 30)],
+                 prec)
 
 
+@pytest.mark.parametrize("sched", ["pair", "region"])
 @pytest.mark.parametrize("prec,tol", [("tf32", 1e-4), ("bf16x3", 1e-5), ("bf16", 5e-3)])
-def test_tensor_core_window_on_shared_states(ofm, prec, tol):
+def test_tensor_core_window_on_shared_states(ofm, prec, tol, sched):
     """Tiny workload, the oracle's eigenstates (rounded to FP32) imported:
     window eigenvalues of the mixed-precision path against the oracle's."""
     wl = make_workload("tiny")
@@ -111,7 +122,7 @@ def test_tensor_core_window_on_shared_states(ofm, prec, tol):
     ctx.build_fragments(wl.grid, wl.V, wl.frags, storage="fp32")
     for a, P in enumerate(Phis32):
         ctx.set_fragment_states(a, P)
-    ctx.assemble(prec)
+    ctx.assemble(prec, schedule=sched)
     m = int(np.sum((E >= lo) & (E <= hi)))
     got = ctx.eigs_by_index(0, m)
     assert np.max(np.abs(got - E[:m])) < tol, (prec, np.max(np.abs(got - E[:m])))
