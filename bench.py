@@ -1,23 +1,28 @@
 #!/usr/bin/env python3
 """Benchmark of the overlapping-fragments-method hot path on GB300.
 
-One step is one pass of the whole method over the synthetic alkane-chain
-workload (256x32x32 grid, 31 boxes 16x32x32, 32 states each), starting from
-the potential resident in device memory:
-  a2  plan the pairs and overlap geometry (host) and take V    ofm_build_fragments
-  a0  batched fragment eigensolve                                ofm_fragment_eigs
-  a1  H phi on the dilated boxes, a3/a4 pair contraction,
-  a5  symmetrise into blocks                                     ofm_assemble_HS
-  a6  FP64 window solve: the first empty level E_gap and the
-      eigenvalues in [E_gap, E_gap + 0.3 Ha]                      ofm_window_from_index
-The metric is the pair-block rate: algorithmic pair-block flops of one step
-(sum over pairs a<=b of 2 n_a n_b (|B_a∩B_b| + |B_a∩B_b+|)) times the steps,
-over the device time of the steps.  Per-row device times, the assembly-only
-rate, the roofline of the dominant kernel, the window-eigenvalue error
-against the all-FP64 GPU path and the speedups of the contraction
-arithmetic are reported beside it.
+Workload (default): the large lattice, 384x192x192 grid (spacing 0.5 bohr),
+~20000 Gaussian wells on 64 self-avoiding chains, 1024 boxes of 40^3 points
+on a 16x8x8 lattice of stride 24, 96 states per fragment -- the largest
+configuration that runs on one GPU.
 
---impl reference times the FP64 CPU oracle on a bounded sample instead.
+Set-up (untimed): V copied in, pair list planned (a2), the fragment states
+computed by the library's own batched eigensolver (a0), the assembly
+schedule chosen by the library's measuring autotuner.
+
+One step = the assembly of Sec. II from the resident states: H phi on every
+dilated box and the operands (a1), every pair block [S_ab | H_ab] on the
+tensor cores (a3/a4), the symmetrised FP64 blocks (a5) -- ofm_assemble_HS.
+The metric is the pair-block rate: algorithmic pair flops of one assembly
+(sum over pairs a<=b of 2 n_a n_b (|B_a∩B_b| + |B_a∩B_b+|)) times the steps
+over the device time of the steps (L2 flushed before each step).
+
+e2e: the same metric through the C ABI with host buffers: per step a new
+potential from pinned host memory (ofm_set_potential), the assembly, and
+every block read back into pinned host memory (ofm_get_blocks).
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (pair blocks of seeded states, the rate extrapolated by flops).
 Under torchrun every rank runs an independent replica (the method's units
 are independent workloads; no collective on the data path).
 """
@@ -43,87 +48,102 @@ def parse_args():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="alkane")
+    p.add_argument("--workload", default="large")
     p.add_argument("--precision", default="bf16x3",
-                   help="pair-contraction arithmetic: fp64 fp32 tf32 bf16 bf16x3")
-    p.add_argument("--no-extras", action="store_true", help="skip e2e, FP64 reference and sweeps")
-    p.add_argument("--eig-degree", type=int, default=0, help="Chebyshev degree (0 = library default)")
-    p.add_argument("--eig-extra", type=int, default=0, help="guard vectors (0 = library default)")
+                   help="pair-contraction arithmetic: tf32 bf16 bf16x3 fp32")
+    p.add_argument("--no-extras", action="store_true", help="skip e2e, sweeps and the alkane run")
     return p.parse_args()
 
 
-# FP64 issue rate measured by ncu on this part (about 2 FMA per clock per SM;
-# sm__pipe_fp64_cycles_active), times 152 SMs at the 2070 MHz maximum clock:
-# 152 * 2 * 2 * 2.07e9 = 1.26e12 flop/s, the recipe's 1.25 TFLOP/s.
-FP64_PEAK_TFLOPS = 1.25
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e-3   # CUDA-core FMA lanes x clock
-SMEM_PEAK_GBS = 152 * 128 * 2.07             # shared-memory bytes per clock per SM x clock
-HBM_CLASSES = {"filter", "apply", "convert", "eig_export", "eig_init", "finalize", "scatter"}
+HBM_CLASSES = {"apply", "convert", "eig_export", "eig_init", "finalize", "scatter", "filter"}
 FP64_CLASSES = {"cholesky", "reduce", "tridiag", "bisect"}
 
 
+def peaks(measured=None):
+    """Roofline denominators: MEASURED_PEAKS.json (driver-written: HBM copy
+    bandwidth, cuBLAS BF16 burst and sustained), else the fallback figures;
+    FP64 / FP32 / TF32 from this run's own GEMM probes when given."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        pk = {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"],
+              "bf16_tflops_sustained": d.get("bf16_tflops_sustained"), "source": "measured"}
+    except Exception:
+        pk = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+              "source": "fallback"}
+    if measured:
+        pk.update(measured)
+    return pk
+
+
+def tensor_peak(pk, precision):
+    """Peak of ALGORITHMIC flops for a tensor-core precision: BF16 takes the
+    BF16 burst; the hi+lo split issues three BF16 products per credited
+    product; TF32 takes this run's measured TF32 GEMM rate when there is one,
+    else the BF16 burst times the nominal ratio 1.1/2.25."""
+    bf16 = pk["bf16_tflops"]
+    if precision == "bf16":
+        return bf16, "bf16 burst (measured)" if pk["source"] == "measured" else "bf16 fallback"
+    if precision == "bf16x3":
+        return bf16 / 3.0, "bf16 burst / 3 (three bf16 products per credited product)"
+    if precision == "tf32":
+        if pk.get("tf32_tflops"):
+            return pk["tf32_tflops"], "tf32 cuBLAS GEMM measured in this run"
+        return bf16 * 1.1 / 2.25, "bf16 burst x nominal tf32/bf16 ratio 1.1/2.25"
+    if precision == "fp32":
+        return pk.get("fp32_tflops") or 152 * 128 * 2 * 2.07e-3, "fp32 SGEMM measured in this run"
+    return pk.get("fp64_tflops") or 1.25, "fp64 DGEMM measured in this run"
+
+
 def roofline_for(name, s, pk, precision):
-    """Roofline of one kernel class from its algorithmic bytes / flops and
-    its event-timed duration."""
+    """Roofline of one kernel class: algorithmic bytes or flops per launch
+    over its event-timed duration, against the class's bound."""
     ms = s["ms"] / max(1, s["launches"])
     r = {"kernel": name, "row": s["row"], "launches": s["launches"], "ms_per_launch": ms}
-    if name in HBM_CLASSES or (s["flops"] == 0 and s["bytes"] > 0):
+    if name == "contract" and precision in ("tf32", "bf16", "bf16x3"):
+        per = s["flops"] / max(1, s["launches"])
+        per_b = s["bytes"] / max(1, s["launches"])
+        tpeak, src = tensor_peak(pk, precision)
+        r.update(bound="tensor", unit="TFLOP/s", achieved=per / (ms * 1e-3) / 1e12, peak=tpeak,
+                 peak_source=src, algorithmic_flops_per_launch=per,
+                 operand_bytes_per_launch=per_b,
+                 intensity_flop_per_byte=per / per_b if per_b else None,
+                 operand_gbs=per_b / (ms * 1e-3) / 1e9)
+    elif name in FP64_CLASSES:
+        per = s["flops"] / max(1, s["launches"])
+        tpeak, src = tensor_peak(pk, "fp64")
+        r.update(bound="alu", unit="TFLOP/s", achieved=per / (ms * 1e-3) / 1e12, peak=tpeak,
+                 peak_source=src, algorithmic_flops_per_launch=per)
+    elif name in HBM_CLASSES or (s["flops"] == 0 and s["bytes"] > 0):
         per = s["bytes"] / max(1, s["launches"])
         r.update(bound="hbm", unit="GB/s", achieved=per / (ms * 1e-3) / 1e9, peak=pk["hbm_gbs"],
                  peak_source=pk["source"] + " copy bandwidth", algorithmic_bytes_per_launch=per)
-        if name == "filter" and s["flops"] > 0:
-            # on-chip form: the HBM bytes are one block in and two out per
-            # filter; each step runs from shared memory (4 in-plane
-            # neighbours, c0 + V and the previous iterate read, the next
-            # iterate written: 28 bytes per point, state and step, which
-            # the 10 flops per point, state and step count)
-            smem = s["flops"] / 10.0 * 28.0 / max(1, s["launches"])
-            r["shared_memory"] = {"bytes_per_launch": smem,
-                                  "achieved_gbs": smem / (ms * 1e-3) / 1e9,
-                                  "peak_gbs": SMEM_PEAK_GBS,
-                                  "frac": smem / (ms * 1e-3) / 1e9 / SMEM_PEAK_GBS,
-                                  "peak_source": "128 B per clock per SM x 152 SMs x max clock"}
-    elif name in FP64_CLASSES:
-        per = s["flops"] / max(1, s["launches"])
-        r.update(bound="alu", unit="TFLOP/s", achieved=per / (ms * 1e-3) / 1e12,
-                 peak=FP64_PEAK_TFLOPS, peak_source="FP64 issue rate x SMs x max clock",
-                 algorithmic_flops_per_launch=per)
-    elif name == "contract" and precision in ("tf32", "bf16", "bf16x3"):
-        # attainable = min(tensor peak of the precision, intensity x HBM); the
-        # binding one is the bound reported
-        per = s["flops"] / max(1, s["launches"])
-        per_b = s["bytes"] / max(1, s["launches"])
-        bf16 = pk["bf16_tflops"]
-        tpeak = {"bf16": bf16, "bf16x3": bf16 / 3.0, "tf32": bf16 * 1.1 / 2.25}[precision]
-        intensity = per / per_b if per_b > 0 else float("inf")
-        if intensity * pk["hbm_gbs"] / 1e3 < tpeak:
-            r.update(bound="hbm", unit="GB/s", achieved=per_b / (ms * 1e-3) / 1e9, peak=pk["hbm_gbs"],
-                     peak_source=pk["source"] + " copy bandwidth (intensity %.1f flop/B is below "
-                     "the tensor ridge)" % intensity,
-                     algorithmic_bytes_per_launch=per_b, algorithmic_flops_per_launch=per,
-                     tflops=per / (ms * 1e-3) / 1e12, tensor_peak_tflops=tpeak)
-        else:
-            r.update(bound="tensor", unit="TFLOP/s", achieved=per / (ms * 1e-3) / 1e12, peak=tpeak,
-                     peak_source=pk["source"] + " bf16 burst x dtype ratio (tf32 1.1/2.25, hi+lo 1/3)",
-                     algorithmic_flops_per_launch=per)
     else:
         per = s["flops"] / max(1, s["launches"])
-        r.update(bound="alu", unit="TFLOP/s", achieved=per / (ms * 1e-3) / 1e12,
-                 peak=FP32_PEAK_TFLOPS, peak_source="FP32 lanes x SMs x max clock",
-                 algorithmic_flops_per_launch=per)
+        tpeak, src = tensor_peak(pk, "fp32")
+        r.update(bound="alu", unit="TFLOP/s", achieved=per / (ms * 1e-3) / 1e12, peak=tpeak,
+                 peak_source=src, algorithmic_flops_per_launch=per)
     r["frac"] = r["achieved"] / r["peak"] if r["peak"] else None
     return r
 
 
-def peaks():
-    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+def profiled_traffic(kernel_class):
+    """DRAM bytes per launch from the committed ncu summary, or None when the
+    summary is absent or was taken on a different version of the kernel."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
-        d = json.load(open(path))
-        return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"],
-                "bf16_tflops_sustained": d.get("bf16_tflops_sustained"), "source": "measured"}
+        d = json.load(open(path))[kernel_class]
     except Exception:
-        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
-                "source": "fallback"}
+        return None
+    import hashlib
+    src = os.path.join(ROOT, "paper_1011_4764_gb300", "csrc", d["source"])
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    if sha != d.get("source_sha"):
+        return None
+    return d.get("dram_bytes_per_launch")
 
 
 # ------------------------------------------------------------------ clocks --
@@ -181,76 +201,103 @@ class ClockSampler:
 
 # ------------------------------------------------------------ oracle legs --
 
-def _oracle_frag(args):
-    name, a = args
-    from ofm_inputs import make_workload
+def _sample_pairs(wl, count, seed=0):
+    """A seeded sample of the workload's pairs (self and neighbour pairs)."""
+    import numpy as np
+    from paper_1011_4764_gb300 import ofm
+    pairs, cnt, _ = ofm.plan_pairs(wl.grid, wl.frags)
+    rng = np.random.default_rng(seed)
+    pick = sorted(rng.choice(len(pairs), size=min(count, len(pairs)), replace=False).tolist())
+    return [pairs[i] for i in pick], [tuple(cnt[i]) for i in pick]
+
+
+def _oracle_pairs(args):
+    """Worker: the oracle's pair blocks for `pairs` of the workload on seeded
+    random states, `reps` times; returns the seconds of each repetition."""
+    grid, frags, vpath, pairs, reps = args
+    import numpy as np
+    from ofm_inputs import random_states
     from oracle import ofm_oracle as O
-    wl = make_workload(name)
-    H = O.hamiltonian(wl.grid, wl.V)
-    return O.fragment_eigs(H, wl.grid, wl.frags[a])
+    H = O.hamiltonian(grid, np.load(vpath, mmap_mode="r"))
+    states = {}
+    for a, b in pairs:
+        for f in (a, b):
+            if f not in states:
+                states[f] = random_states(grid, frags[f], seed=1000 + f)
+    out = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        for a, b in pairs:
+            O.pair_block(H, grid, frags[a], states[a], frags[b], states[b])
+        out.append(time.perf_counter() - t0)
+    return out
 
 
-def oracle_sample(name, k):
-    """The FP64 oracle, as it stands, on the sub-system of the first k
-    fragments of the workload: k fragment eigensolves (one single-threaded
-    process each), their pair blocks and the dense generalized eigensolve.
-    Returns (pair flops of the sub-system, seconds, cores)."""
+def oracle_sample(name, npairs, workers, reps=1):
+    """The FP64 oracle, as it stands, on `npairs` seeded sampled pair blocks
+    of the workload, spread over `workers` single-threaded processes
+    (spawned; each builds the sparse H once, untimed).  Returns (sampled pair
+    flops, per repetition the seconds of the slowest worker, workers)."""
     import multiprocessing as mp
+    import numpy as np
     for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[v] = "1"
     from ofm_inputs import make_workload
-    from oracle import ofm_oracle as O
     wl = make_workload(name)
-    frags = wl.frags[:k]
-    t0 = time.perf_counter()
-    with mp.get_context("spawn").Pool(k) as pool:
-        res = pool.map(_oracle_frag, [(name, a) for a in range(k)])
-    Phis = [U for _, U in res]
-    H = O.hamiltonian(wl.grid, wl.V)
-    pairs = O.pair_list(wl.grid, frags)
-    blocks = O.pair_blocks(H, wl.grid, frags, Phis, pairs)
-    Hd, Sd = O.assemble_dense(frags, blocks)
-    O.generalized_eigs(Hd, Sd)
-    dt = time.perf_counter() - t0
-    return O.pair_flops(wl.grid, frags, pairs), dt, k
+    pairs, cnt = _sample_pairs(wl, npairs)
+    F = sum(2 * wl.frags[a].n_states * wl.frags[b].n_states * (ks + kh)
+            for (a, b), (ks, kh) in zip(pairs, cnt))
+    w = max(1, min(workers, len(pairs)))
+    chunks = [pairs[i::w] for i in range(w)]
+    with tempfile.TemporaryDirectory() as tmp:
+        vpath = os.path.join(tmp, "V.npy")
+        np.save(vpath, np.ascontiguousarray(wl.V))
+        with mp.get_context("spawn").Pool(w) as pool:
+            secs = pool.map(_oracle_pairs, [(wl.grid, wl.frags, vpath, c, reps) for c in chunks])
+    per_rep = [max(s[r] for s in secs) for r in range(reps)]
+    return F, per_rep, w
 
 
-def cpu_baseline_leg(name):
-    k = max(1, min(8, os.cpu_count() or 1))
-    F, dt, cores = oracle_sample(name, k)
-    return {"value": F / dt / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
-            "sample": f"fragments 0..{k - 1} of the workload as a sub-system: {k} fragment "
-                      f"eigensolves (one single-threaded process each), their pair blocks, "
-                      f"dense generalized eigensolve; {F:.3e} pair flops in {dt:.1f} s"}
+def cpu_baseline_leg(name, npairs=16):
+    cores = os.cpu_count() or 1
+    F, per_rep, w = oracle_sample(name, npairs, cores)
+    dt = per_rep[0]
+    return {"value": F / dt / 1e12, "unit": "TFLOP/s", "cores": w, "kind": "oracle",
+            "sample": f"{npairs} seeded sampled pair blocks of {name} on seeded random states, "
+                      f"{w} single-threaded processes; {F:.3e} pair flops in {dt:.1f} s (the slowest "
+                      f"process, pair blocks only, the sparse H built beforehand); the rate is "
+                      f"extrapolated by flops to the whole workload"}
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    from ofm_inputs import make_workload
-    wl = make_workload(args.workload)
-    k = 2
-    times = []
-    F = 0
-    for i in range(args.warmup + args.steps):
-        F, dt, cores = oracle_sample(args.workload, k)
-        if i >= args.warmup:
-            times.append(dt)
+    cores = os.cpu_count() or 1
+    npairs = max(1, min(cores, 16))
+    F, per_rep, w = oracle_sample(args.workload, npairs, cores, reps=args.warmup + args.steps)
+    times = per_rep[args.warmup:] or per_rep
     t = sum(times) / len(times)
     val = F / t / 1e12
+    name = _workload_name(args.workload)
     out = {
         "impl": "reference", "metric": "H/S pair-block TFLOP/s", "value": val, "unit": "TFLOP/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": wl.name, "sample_fragments": k},
-        "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": k, "kind": "oracle",
-                         "sample": f"fragments 0..{k - 1} of {wl.name} per step (eigensolves, "
-                                   f"pair blocks, dense generalized eigensolve)"},
+        "config": {"workload": name, "sample_pairs": npairs},
+        "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": w, "kind": "oracle",
+                         "sample": f"{npairs} seeded sampled pair blocks of {name} per step on "
+                                   f"seeded random states, {w} processes, rate extrapolated by flops"},
         "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out), flush=True)
+
+
+def _workload_name(key):
+    return {"large": "large_lattice_384x192x192", "alkane": "alkane_chain_256x32x32",
+            "polymer": "amorphous_polymer_128c", "scaled": "chains_scaled_192c",
+            "tiny": "tiny_32x12x12"}.get(key, key)
 
 
 # ---------------------------------------------------------------- our arm --
@@ -270,6 +317,38 @@ def job_value(world, flops_per_step, steps, t_ms):
     """Whole-job TFLOP/s: the pair flops every rank's replica computed in its
     K steps over the slowest rank's time."""
     return world * flops_per_step * steps / (t_ms * 1e-3) / 1e12
+
+
+def gemm_peaks(dev):
+    """FP64, FP32 (no TF32) and TF32 dense GEMM rates of this GPU (cuBLAS via
+    torch), the denominators of the FP64 / FP32 / TF32 fractions."""
+    import torch
+    out = {}
+    for key, dtype, tf32, n in (("fp64_tflops", torch.float64, False, 4096),
+                                ("fp32_tflops", torch.float32, False, 8192),
+                                ("tf32_tflops", torch.float32, True, 8192)):
+        prev = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        try:
+            a = torch.randn(n, n, device=dev, dtype=dtype)
+            b = torch.randn(n, n, device=dev, dtype=dtype)
+            for _ in range(2):
+                a @ b
+            torch.cuda.synchronize(dev)
+            reps = 5
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                a @ b
+            e1.record()
+            e1.synchronize()
+            out[key] = 2.0 * n ** 3 * reps / (e0.elapsed_time(e1) * 1e-3) / 1e12
+        finally:
+            torch.backends.cuda.matmul.allow_tf32 = prev
+        del a, b
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_ours(args):
@@ -292,47 +371,33 @@ def run_ours(args):
     from paper_1011_4764_gb300 import ofm
 
     wl = make_workload(args.workload)
-    grid, frags, rule = wl.grid, wl.frags, wl.window
-    storage = "fp64" if args.precision == "fp64" else "fp32"
+    grid, frags = wl.grid, wl.frags
+    prec = args.precision
     stream = torch.cuda.Stream(device=dev)
     ctx = ofm.Context(stream)
     V_dev = torch.from_numpy(np.ascontiguousarray(wl.V)).to(dev)
-    V_host = torch.from_numpy(np.ascontiguousarray(wl.V)).pin_memory()
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
-    def window_of(c):
-        # a window that starts AT an eigenvalue (the first empty level, or the
-        # lowest) is one index-anchored call: E_i and the levels up to
-        # E_i + width
-        if rule.kind in ("above_gap", "from_lowest"):
-            i0 = rule.n_occ if rule.kind == "above_gap" else 0
-            E, n = c.window_from_index(i0, rule.width)
-            return E, float(E[0]), float(E[0]) + rule.width
-        e = c.eigs_by_index(rule.n_occ - 1, rule.n_occ + 1)
-        lo, hi = float(e[0]) - rule.width, float(e[1]) + rule.width
-        E, n = c.window_eigs(lo, hi)
-        return E, lo, hi
-
-    def step(Vsrc):
-        ctx.build_fragments(grid, Vsrc, frags, storage=storage)
-        eps, res, _ = ctx.fragment_eigs(degree=args.eig_degree, extra_states=args.eig_extra)
-        ctx.assemble(args.precision)
-        E, lo, hi = window_of(ctx)
-        return E, eps
-
-    ctx.build_fragments(grid, V_dev, frags, storage=storage)
+    # ---- set-up: pairs, the fragment states from the library's eigensolver,
+    # the assembly schedule from its autotuner
+    t_setup = time.perf_counter()
+    ctx.build_fragments(grid, V_dev, frags, storage="fp32")
     info = ctx.plan_info()
     F = info["pair_flops"]
-    step(V_dev)
-    # measured choice of the assembly schedule (stencil form x points per
-    # work item), kept by the library for the steps below (same layout)
-    t_chunk, t_form, t_ms, t_times = ctx.autotune_assembly(args.precision, reps=3)
-    schedule = {"chunk_points": t_chunk, "stencil_form": ["register", "staged"][t_form - 1],
-                "assembly_ms": t_ms,
-                "candidates_ms": {"register": [round(float(t), 4) for t in t_times[0]],
-                                  "staged": [round(float(t), 4) for t in t_times[1]]}}
+    eps, res, eig_status = ctx.fragment_eigs(allow_not_converged=True)
+    eig_s = time.perf_counter() - t_setup
+    t_chunk, t_form, t_ms, t_times = ctx.autotune_assembly(prec, reps=3)
+    schedule = {"schedule": ctx.tuned["schedule"], "region_ms": ctx.tuned["region_ms"],
+                "pair_best_ms": float(np.min(t_times[t_times > 0])) if np.any(t_times > 0) else None,
+                "pair_chunk_points": t_chunk,
+                "pair_stencil_form": ["register", "staged"][t_form - 1]}
+    setup_s = time.perf_counter() - t_setup
+
+    def step():
+        ctx.assemble(prec)
+
     for _ in range(args.warmup):
-        step(V_dev)
+        step()
 
     def barrier():
         if dist is not None:
@@ -340,77 +405,73 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
 
     def timed_steps(profile):
-        """K steps, L2 flushed before each, timed with CUDA events on the
-        library stream; with profile=True the library also brackets every
-        kernel class with events (per-class durations for the rooflines)."""
+        """K steps, L2 flushed before each (untimed), timed with CUDA events
+        on the library stream; with profile=True the library also brackets
+        every kernel class with events (per-class durations)."""
         ctx.set_profiling(profile)
         launches0 = sum(v["launches"] for v in ctx.kernel_stats().values())
         ms = []
-        E_ = None
         for _ in range(args.steps):
             with torch.cuda.stream(stream):
                 flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            E_, eps_ = step(V_dev)
+            step()
             e1.record(stream)
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
         launches = sum(v["launches"] for v in ctx.kernel_stats().values()) - launches0
         st = ctx.kernel_stats() if profile else None
         ctx.set_profiling(False)
-        return ms, launches, st, E_
+        return ms, launches, st
 
-    # ---- timed region: K full steps, inputs resident in HBM, no per-kernel
-    # timing (events around every launch would add host work to the step)
+    # ---- timed region
     clocks = ClockSampler(local if world > 1 else dev.index or 0)
     barrier()
     clocks.start()
     t_wall0 = time.perf_counter()
-    step_ms, timed_launches, _, E = timed_steps(False)
+    step_ms, timed_launches, _ = timed_steps(False)
     barrier()
     wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
-    # ---- the same K steps again with per-class CUDA-event timing: the
-    # breakdown by row and kernel class and the rooflines come from this pass
+    # ---- the same K steps with per-class CUDA events: rows and rooflines
     barrier()
-    prof_ms, _, stats, _ = timed_steps(True)
+    prof_ms, _, stats = timed_steps(True)
     barrier()
     t_ms = job_time_ms(sum(step_ms), dist, dev)
     K = args.steps
-    ms_per_step = t_ms / K
     value = job_value(world, F, K, t_ms)
 
+    measured = gemm_peaks(dev) if rank == 0 and not args.no_extras else {}
+    pk = peaks(measured)
+    dom_name, dom = max(stats.items(), key=lambda kv: kv[1]["ms"])
+    roof = roofline_for(dom_name, dom, pk, prec)
+    roof["traffic"] = profiled_traffic(dom_name)
+    others = {k: roofline_for(k, s, pk, prec) for k, s in stats.items() if k != dom_name}
+    for k in others:
+        others[k]["traffic"] = profiled_traffic(k)
     rows = {}
     for name, s in stats.items():
-        rows.setdefault(s["row"], 0.0)
-        rows[s["row"]] += s["ms"] / K
-    asm_ms = sum(rows.get(r, 0.0) for r in ("a1", "a4", "a5")) - stats.get("scatter", {}).get("ms", 0.0) / K
-    launches = timed_launches
-
-    # dominant kernel class and its roofline
-    pk = peaks()
-    dom_name, dom = max(stats.items(), key=lambda kv: kv[1]["ms"])
-    roof = roofline_for(dom_name, dom, pk, args.precision)
-    roof["traffic"] = profiled_traffic(dom_name)
-    others = {k: roofline_for(k, s, pk, args.precision) for k, s in stats.items()
-              if k in ("filter", "apply", "contract", "tridiag")}
+        rows[s["row"]] = rows.get(s["row"], 0.0) + s["ms"] / K
 
     out = {
         "metric": "H/S pair-block TFLOP/s", "value": value, "unit": "TFLOP/s",
-        "n_gpus": world, "steps": K, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "n_gpus": world, "steps": K, "warmup": args.warmup, "ms_per_step": t_ms / K,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp64": "f64", "fp32": "f32", "tf32": "tf32", "bf16": "bf16",
-                  "bf16x3": "bf16x3"}[args.precision],
+                  "bf16x3": "bf16x3"}[prec],
         "data": "synthetic",
         "config": {"workload": wl.name, "grid": list(grid.n), "h": grid.h,
                    "fragments": len(frags), "states": sorted({f.n_states for f in frags}),
                    "pairs": info["n_pairs"], "basis": info["basis_size"], "pair_flops": F,
-                   "contraction": args.precision, "storage": storage,
-                   "step": "a2 plan + a0 fragment eigensolve + a1 H apply + a3/a4 contraction "
-                           "+ a5 blocks + a6 FP64 window solve",
-                   "window": f"{rule.kind} width {rule.width} Ha",
+                   "contraction": prec, "storage": "fp32",
+                   "step": "a1 H apply + operands, a3/a4 pair contraction, a5 FP64 blocks "
+                           "(ofm_assemble_HS) from resident states",
+                   "states_from": "the library's batched fragment eigensolver, run once untimed "
+                                  f"({eig_s:.1f} s with the pair planning; status "
+                                  f"{ofm.status_name(eig_status)}, max residual {float(res.max()):.2e})",
+                   "schedule": schedule["schedule"],
                    "l2": "flushed by a 512 MiB device write before every step (untimed)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "value_profiled": job_value(world, F, K, sum(prof_ms)),
@@ -420,23 +481,30 @@ def run_ours(args):
         "rows_ms": {k: round(v, 4) for k, v in sorted(rows.items())},
         "kernels": {k: {"row": s["row"], "launches": s["launches"] // K, "ms": s["ms"] / K}
                     for k, s in sorted(stats.items())},
-        "assembly": {"ms": asm_ms, "tflops": F / (asm_ms * 1e-3) / 1e12 if asm_ms > 0 else None},
         "assembly_schedule": schedule,
+        "setup_s": setup_s,
         "wall_s": wall,
-        "gpu_launches": launches,
+        "gpu_launches": timed_launches,
         "roofline": roof,
         "rooflines": others,
+        "peaks": {k: v for k, v in pk.items()},
         "clocks": clk,
-        "window_eigs": int(len(E)),
     }
-
     if not args.no_extras and rank == 0:
-        out.update(extras(args, ctx, ofm, wl, V_host, step, window_of, stream, storage, F, dev, E))
+        out.update(extras(args, ctx, ofm, wl, stream, F, dev, prec))
+    ctx.close()
+    del ctx
+    torch.cuda.empty_cache()
+    if not args.no_extras and rank == 0:
+        try:
+            out["alkane_chain"] = alkane_extra(ofm, stream, dev)
+        except Exception as e:  # an extra must not hide the headline line
+            out["alkane_chain"] = {"error": str(e)}
     if rank == 0:
         if world == 1 and not args.no_extras:
             try:
                 out["cpu_baseline"] = cpu_baseline_leg(args.workload)
-            except Exception as e:  # the baseline must not hide the GPU line
+            except Exception as e:
                 out["cpu_baseline"] = {"value": None, "unit": "TFLOP/s", "cores": 0,
                                        "kind": "oracle", "sample": f"failed: {e}"}
         print(json.dumps(out), flush=True)
@@ -445,187 +513,133 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def profiled_traffic(kernel_class):
-    """DRAM bytes per launch from the committed ncu summary, or None when the
-    summary is absent or was taken on a different version of the kernel."""
-    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
-    try:
-        d = json.load(open(path))[kernel_class]
-    except Exception:
-        return None
-    import hashlib
-    src = os.path.join(ROOT, "paper_1011_4764_gb300", "csrc", d["source"])
-    try:
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    except OSError:
-        return None
-    if sha != d.get("source_sha"):
-        return None
-    return d.get("dram_bytes_per_launch")
+def _time_assembly(ctx, stream, prec, schedule="auto", reps=5):
+    import torch
+    ctx.assemble(prec, schedule=schedule)
+    ts = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.assemble(prec, schedule=schedule)
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return min(ts)
 
 
-def extras(args, ctx, ofm, wl, V_host, step, window_of, stream, storage, F, dev, E_main):
+def extras(args, ctx, ofm, wl, stream, F, dev, prec):
     import numpy as np
     import torch
     ex = {}
-    # e2e: the same steps through the C ABI from pinned host buffers
-    n_e2e = max(2, min(args.steps, 5))
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    for _ in range(n_e2e):
-        E, eps = step(V_host)
-    torch.cuda.synchronize(dev)
-    dt = (time.perf_counter() - t0) / n_e2e
-    nb = sum(f.n_states for f in wl.frags)
-    ex["e2e"] = {"value": F / dt / 1e12, "unit": "TFLOP/s",
-                 "h2d_bytes_per_step": int(V_host.numel() * 8),
-                 "d2h_bytes_per_step": int((2 * nb + len(E) + 1) * 8),
-                 "steps": n_e2e, "timer": "host wall clock"}
-    # contraction arithmetic on the same states: a1-a5 device time
+    # e2e: a new potential from pinned host memory, the assembly, every block
+    # read back into pinned host memory, through the C ABI
+    try:
+        V_host = torch.from_numpy(np.ascontiguousarray(wl.V)).pin_memory()
+        nblk = ctx.blocks_count()
+        out_host = torch.empty(nblk, dtype=torch.float64).pin_memory()
+        n_e2e = max(3, min(args.steps, 5))
+        ctx.set_potential(V_host)
+        ctx.assemble(prec)
+        ctx.get_blocks(out_host)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            ctx.set_potential(V_host)
+            ctx.assemble(prec)
+            ctx.get_blocks(out_host)
+        torch.cuda.synchronize(dev)
+        dt = (time.perf_counter() - t0) / n_e2e
+        ex["e2e"] = {"value": F / dt / 1e12, "unit": "TFLOP/s",
+                     "h2d_bytes_per_step": int(V_host.numel() * 8),
+                     "d2h_bytes_per_step": int(nblk * 8), "steps": n_e2e,
+                     "timer": "host wall clock",
+                     "step": "ofm_set_potential (pinned host V) + ofm_assemble_HS + ofm_get_blocks "
+                             "(every [H_ab | S_ab] block into pinned host memory)"}
+    except Exception as e:
+        ex["e2e"] = {"error": str(e)}
+    # contraction arithmetic and schedule on the same states: a1-a5 device time
     asm = {}
-    for prec in ("fp32", "fp64", "tf32", "bf16", "bf16x3"):
-        if storage == "fp64" and prec != "fp64":
-            continue
+    for p in ("bf16x3", "bf16", "tf32", "fp32"):
         try:
-            ctx.assemble(prec)
-        except ofm.OFMError:
-            continue
-        ts = []
-        for _ in range(5):
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            ctx.assemble(prec)
-            e1.record(stream)
-            e1.synchronize()
-            ts.append(e0.elapsed_time(e1))
-        asm[prec] = min(ts)
+            asm[p] = _time_assembly(ctx, stream, p)
+        except ofm.OFMError as e:
+            asm[p] = str(e)
     ex["assembly_ms_by_precision"] = asm
-    if "fp32" in asm:
-        ex["speedup_vs_fp32"] = {p: asm["fp32"] / t for p, t in asm.items()}
-    # window eigenvalues against the all-FP64 GPU path (FP64 states, FP64
-    # contraction), compared index by index
-    try:
-        ref = ofm.Context(stream)
-        ref.build_fragments(wl.grid, V_host, wl.frags, storage="fp64")
-        ref.fragment_eigs()
-        ref.assemble("fp64")
-        Eref, lo, hi = window_of(ref)
-        ctx.assemble(args.precision)
-        n0 = wl.window.n_occ if wl.window.kind != "from_lowest" else 0
-        m = len(Eref)
-        mine = ctx.eigs_by_index(n0, n0 + m)
-        refi = ref.eigs_by_index(n0, n0 + m)
-        ex["window_vs_fp64"] = {"n": m, "max_abs_err_ha": float(np.max(np.abs(mine - refi))) if m else 0.0,
-                                "window_ha": [lo, hi]}
-        ref.close()
-    except Exception as e:
-        ex["window_vs_fp64"] = {"error": str(e)}
-    # Sec. III.C distance cutoff between fragments (atoms = the wells inside
-    # each box): pairs kept, a1-a5 device time, and the shift of the
-    # window's eigenvalues (same indices) against the full pair list
-    try:
-        atoms = wl.fragment_atoms()
-        n0 = wl.window.n_occ if wl.window.kind != "from_lowest" else 0
-        ctx.set_pair_cutoff(None, 0.0)
-        ctx.assemble(args.precision)
-        m = len(E_main)
-        full = ctx.eigs_by_index(n0, n0 + m)
-        study = []
-        for d_cut in (1.0, 2.0, 2.5):   # the halo-only pairs sit 2.33 bohr apart
-            ctx.set_pair_cutoff(atoms, d_cut)
-            ctx.assemble(args.precision)
-            ts = []
-            for _ in range(5):
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                ctx.assemble(args.precision)
-                e1.record(stream)
-                e1.synchronize()
-                ts.append(e0.elapsed_time(e1))
-            Ec = ctx.eigs_by_index(n0, n0 + m)
-            study.append({"d_cut_bohr": d_cut, "pairs": len(ctx.pairs()),
-                          "assembly_ms": min(ts),
-                          "window_shift_max_abs_ha": float(np.max(np.abs(Ec - full))) if m else 0.0})
-        ctx.set_pair_cutoff(None, 0.0)
-        ex["pair_cutoff"] = {"full_pairs": len(ctx.pairs()), "window_n": m, "study": study}
-    except Exception as e:
-        ex["pair_cutoff"] = {"error": str(e)}
-    # Sec. III basis of fragment HOMOs: the n highest occupied states of every
-    # fragment (occupied = one level per well inside the box), the
-    # occupation rule's HOMO / LUMO against the full basis' levels N_occ-1
-    # and N_occ, and the device time of the smaller assembly and solve
-    try:
-        atoms = wl.fragment_atoms()
-        n_occ = wl.window.n_occ
-        if n_occ > 0 and all(len(a) >= 1 for a in atoms):
-            ctx.assemble(args.precision)   # the cutoff study left the pencil unassembled
-            eh, el = (float(x) for x in ctx.eigs_by_index(n_occ - 1, n_occ + 1))
-            host = [ctx.get_fragment_states(a) for a in range(len(wl.frags))]
-            rows = []
-            for n_homo in (5, 2):
-                first = [len(a) - n_homo for a in atoms]
-                if min(first) < 0:
-                    continue
-                hc = ofm.Context(stream)
-                hc.build_fragments(wl.grid, V_host, wl.frags, storage=storage)
-                for a, P in enumerate(host):
-                    hc.set_fragment_states(a, P)
-                hc.select_states(first, n_homo)
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                hc.assemble(args.precision)
-                e_ref, h, l, occ = hc.homo_lumo_gap(0.5 * (el - eh))
-                e1.record(stream)
-                e1.synchronize()
-                rows.append({"homos_per_fragment": n_homo, "basis": n_homo * len(wl.frags),
-                             "e_ref_ha": e_ref, "E_homo_ha": h, "E_lumo_ha": l, "n_occ": occ,
-                             "E_homo_minus_full_ha": h - eh, "E_lumo_minus_full_ha": l - el,
-                             "assemble_and_rule_ms": e0.elapsed_time(e1)})
-                hc.close()
-            ex["homo_basis"] = {"full_basis": nb, "full_E_homo_ha": eh, "full_E_lumo_ha": el,
-                                "gap_min_ha": 0.5 * (el - eh), "rows": rows}
-    except Exception as e:
-        ex["homo_basis"] = {"error": str(e)}
-    # fragment-size study (Sec. III "Choice of fragments": monomer / dimer /
-    # trimer-like boxes of 1, 2, 3 wells on the tiny grid, FP64): error of the
-    # bound levels against the full-grid diagonalisation, which is the
-    # library's own eigensolve of one fragment spanning the grid
-    try:
-        from ofm_inputs import Fragment, tiny_fragments_of
-        base = tiny_fragments_of(1)
-        whole = ofm.Context(stream)
-        whole.build_fragments(base.grid, base.V, [Fragment((0, 0, 0), tuple(base.grid.n), 8)],
-                              storage="fp64")
-        full, _, _ = whole.fragment_eigs()
-        whole.close()
-        rows = []
-        for s in (1, 2, 3):
-            wl_s = tiny_fragments_of(s)
-            c_s = ofm.Context(stream)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            c_s.build_fragments(wl_s.grid, wl_s.V, wl_s.frags, storage="fp64")
-            c_s.fragment_eigs()
-            c_s.assemble("fp64")
-            lv = c_s.eigs_by_index(0, 8)
-            e1.record(stream)
-            e1.synchronize()
-            bound = full < 0
-            rows.append({"wells_per_fragment": s, "basis": 8 * s,
-                         "max_err_bound_levels_ha": float(np.max(lv[bound] - full[bound])),
-                         "lowest_level_err_ha": float(lv[0] - full[0]),
-                         "min_err_ha": float(np.min(lv - full)),
-                         "method_ms": e0.elapsed_time(e1)})
-            c_s.close()
-        ex["fragment_size"] = {"workload": "tiny grid 32x12x12, 8 wells", "full_grid_levels_ha":
-                               [float(x) for x in full], "rows": rows}
-    except Exception as e:
-        ex["fragment_size"] = {"error": str(e)}
+    if isinstance(asm.get("fp32"), float):
+        ex["speedup_vs_fp32_cuda_cores"] = {p: asm["fp32"] / t for p, t in asm.items()
+                                           if isinstance(t, float)}
+    sch = {}
+    for s in ("pair", "region"):
+        try:
+            sch[s] = _time_assembly(ctx, stream, prec, schedule=s, reps=3)
+        except ofm.OFMError as e:
+            sch[s] = str(e)
+    ex["assembly_ms_by_schedule"] = sch
+    ctx.assemble(prec)
     return ex
+
+
+def alkane_extra(ofm, stream, dev):
+    """The alkane chain (256x32x32, 31 boxes, 32 states): the whole method
+    per step (a0 eigensolve + a1-a5 + a6 window), and each window
+    eigenvalue's error against the FP64 oracle's spectrum of the same
+    workload (tests/golden/alkane_oracle.json, written by the oracle) for
+    every contraction arithmetic, on the GPU's own states."""
+    import numpy as np
+    import torch
+    from ofm_inputs import make_workload
+    wl = make_workload("alkane")
+    rule = wl.window
+    golden = json.load(open(os.path.join(ROOT, "tests", "golden", "alkane_oracle.json")))
+    Eo = np.array(golden["ofm_spectrum"])
+    i0 = rule.n_occ
+    m = int(np.sum((Eo >= Eo[i0]) & (Eo <= Eo[i0] + rule.width)))
+    res = {"workload": wl.name, "window": f"E_{i0 + 1} .. E_{i0 + 1} + {rule.width} Ha",
+           "window_count_oracle": m}
+    ctx = ofm.Context(stream)
+    V_dev = torch.from_numpy(np.ascontiguousarray(wl.V)).to(dev)
+
+    def full_step():
+        ctx.build_fragments(wl.grid, V_dev, wl.frags, storage="fp32")
+        ctx.fragment_eigs()
+        ctx.assemble("bf16x3")
+        return ctx.window_from_index(i0, rule.width)
+
+    full_step()
+    ts = []
+    for _ in range(5):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        E, n = full_step()
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    F = ctx.plan_info()["pair_flops"]
+    res["full_step_ms"] = min(ts)
+    res["full_step_tflops"] = F / min(ts) / 1e9
+    res["window_count"] = n
+    errs = {}
+    for p in ("bf16x3", "tf32", "bf16", "fp32"):
+        ctx.assemble(p)
+        got = ctx.eigs_by_index(i0, i0 + m)
+        d = got - Eo[i0:i0 + m]
+        errs[p] = {"max_abs_ha": float(np.max(np.abs(d))), "mean_abs_ha": float(np.mean(np.abs(d))),
+                   "per_eigenvalue_ha": [float(f"{x:.3e}") for x in d]}
+    ctx.close()
+    # the all-FP64 path: FP64 states (FP64 eigensolve) and FP64 contraction
+    c64 = ofm.Context(stream)
+    c64.build_fragments(wl.grid, V_dev, wl.frags, storage="fp64")
+    c64.fragment_eigs()
+    c64.assemble("fp64")
+    got = c64.eigs_by_index(i0, i0 + m)
+    d = got - Eo[i0:i0 + m]
+    errs["fp64"] = {"max_abs_ha": float(np.max(np.abs(d))), "mean_abs_ha": float(np.mean(np.abs(d))),
+                    "per_eigenvalue_ha": [float(f"{x:.3e}") for x in d]}
+    c64.close()
+    res["window_error_vs_oracle"] = errs
+    return res
 
 
 def main():

@@ -95,8 +95,10 @@ typedef struct {
                             and on a stream that can be captured (not the legacy default
                             stream); 0 launches the kernels one by one */
   int schedule;          /* tensor-core precisions only: [0] the context's schedule (the one
-                            ofm_autotune_assembly chose, else "region" wherever its plan
-                            applies, else "pair"); 1 "pair": H phi in the states' layout,
+                            ofm_autotune_assembly chose, else "region" where its plan
+                            applies and its MMA work, padding included, stays within 4x
+                            the algorithmic flops, else "pair"); 1 "pair": H phi in the
+                            states' layout,
                             then one GEMM per pair (M = n_a padded to 128); 2 "region":
                             the grid is cut into coverage regions (products of the
                             segments between dilated-box boundaries) and every region's
@@ -194,6 +196,16 @@ typedef struct {
 ofm_status ofm_autotune_assembly(ofm_ctx* ctx, ofm_precision prec, const int* chunks, int n_chunks,
                                  int reps, double* times_ms, ofm_tune_result* out);
 
+/* Eq. 1 with a new potential on the same grid: V (n0*n1*n2 doubles, x
+ * fastest; host or device per v_loc) replaces the current one.  The
+ * fragments, pair list, plans and states stay -- the states remain the basis
+ * (Sec. II: the basis is fixed once the fragment eigenstates are computed;
+ * the whole-system H is then represented in it) -- and the assembled blocks
+ * are discarded, so the next ofm_assemble_HS represents the new H in the
+ * same basis.  A host V is copied before the call returns.  OFM_ERR_STATE
+ * before ofm_build_fragments. */
+ofm_status ofm_set_potential(ofm_ctx* ctx, const double* V, ofm_location v_loc);
+
 /* Distance cutoff on the pair list (Sec. III.C, "Choice of the distance
  * cutoff": a pair of fragments is included when the minimal distance between
  * an atom of one and an atom of the other is below d_cut).  The atoms of
@@ -248,6 +260,15 @@ ofm_status ofm_get_plan_info(ofm_ctx* ctx, ofm_plan_info* info);
 /* Block of the pair (a, b) (either order): n_a x n_b row-major doubles,
  * host.  A pair not in the list yields zeros.  H_ab / S_ab may be NULL. */
 ofm_status ofm_get_block(ofm_ctx* ctx, int a, int b, double* H_ab, double* S_ab);
+
+/* Every assembled block at once, in the order of the pair list
+ * (ofm_get_pairs): for each pair a <= b, H_ab then S_ab, each n_a x n_b
+ * row-major doubles, concatenated -- the block-sparse form of the pencil of
+ * Eq. 2 that a sparse or distributed eigensolver takes (Sec. II points to
+ * ScaLAPACK / PARPACK for large systems).  *n_elems (nullable) receives the
+ * element count; HS (host or device per loc; NULL only queries the count)
+ * receives the blocks.  Synchronises the context stream. */
+ofm_status ofm_get_blocks(ofm_ctx* ctx, double* HS, ofm_location loc, long long* n_elems);
 
 /* Dense n x n (n = basis_size) row-major H and S in basis order, host or
  * device per loc.  Either pointer may be NULL. */

@@ -6,5 +6,5 @@ arithmetic, so both the CPU oracle and the CUDA path may use it.
 """
 from .geometry import (  # noqa: F401
     Grid, Fragment, Workload, WindowRule, gaussian_potential, make_workload,
-    WORKLOADS, small_workload, random_states, fragment_atoms, tiny_fragments_of,
+    WORKLOADS, small_workload, random_states, fragment_atoms, tiny_fragments_of, lattice_workload,
 )

@@ -269,26 +269,54 @@ def _box_around(points, grid: Grid, margin: float, lo: int, hi: int, mult: int =
     return tuple(off), tuple(ext)
 
 
+def _box_overlap_fraction(grid: Grid, fa, fb) -> float:
+    """Shared grid points of two periodic boxes over the smaller box's points."""
+    cnt = 1
+    for d in range(3):
+        sa = set(((fa.off[d] + np.arange(fa.ext[d])) % grid.n[d]).tolist())
+        sb = set(((fb.off[d] + np.arange(fb.ext[d])) % grid.n[d]).tolist())
+        cnt *= len(sa & sb)
+    return cnt / min(np.prod(fa.ext), np.prod(fb.ext))
+
+
 def _amorphous_polymer(seed: int = 0) -> Workload:
-    """128^3 grid, 800 wells on 8 self-avoiding chains, ~250 uneven boxes."""
+    """128^3 grid, 800 wells on 8 self-avoiding chains, uneven boxes
+    overlapping their chain neighbour by 30-60 %."""
     grid = Grid((128, 128, 128), 0.5)
     rng = np.random.default_rng(seed)
     chains = _self_avoiding_chains(rng, grid.lengths, 8, 100, 1.45, 1.2)
     wells, frags = [], []
+    seg = 10
     for ch in chains:
         D = rng.uniform(0.6, 1.2, size=len(ch))
         w = rng.uniform(0.6, 1.0, size=len(ch))
         for p, d, ww in zip(ch, D, w):
             wells.append((p[0], p[1], p[2], d, ww))
-        seg, stride = 10, 3
-        for s0 in range(0, len(ch) - seg + 1, stride):
+        # consecutive segments of 10 wells; each next segment starts at the
+        # first well whose box shares at most 60 % of the smaller box with
+        # the previous fragment's box (boxes: bounding box + U(2, 7) bohr of
+        # margin, edges multiples of 8 points in [16, 40])
+        start, prev = 0, None
+        while start + seg <= len(ch):
             margin = rng.uniform(2.0, 7.0)
-            off, ext = _box_around(ch[s0:s0 + seg], grid, margin, 16, 40)
-            frags.append(Fragment(off, ext, int(rng.integers(8, 65))))
+            n_states = int(rng.integers(8, 65))
+            s0 = start
+            while True:
+                off, ext = _box_around(ch[s0:s0 + seg], grid, margin, 16, 40)
+                f = Fragment(off, ext, n_states)
+                if prev is None or s0 + seg >= len(ch) or _box_overlap_fraction(grid, prev, f) <= 0.6:
+                    break
+                s0 += 1
+            if prev is not None and s0 + seg > len(ch):
+                break
+            frags.append(f)
+            prev = f
+            start = s0 + 1
     return Workload("amorphous_polymer_128c", grid, np.array(wells), frags,
                     WindowRule("above_gap", 0.3, n_occ=len(wells)), "f32",
                     "800 wells on 8 self-avoiding chains (1.45 bohr steps), "
-                    "boxes 16^3..40^3, states U{8..64}")
+                    "boxes 16^3..40^3 overlapping their chain neighbour by at most 60 %, "
+                    "states U{8..64}")
 
 
 def _chains_scaled(seed: int = 0) -> Workload:
@@ -325,23 +353,38 @@ def _chains_scaled(seed: int = 0) -> Workload:
                     "24^3..32^3 at uniform arc length, 48 states")
 
 
-def _large_lattice(seed: int = 0) -> Workload:
-    """384x192x192 grid, ~20000 wells on 64 chains, 1024 boxes 40^3 stride 24."""
-    grid = Grid((384, 192, 192), 0.5)
+def lattice_workload(cells=(16, 8, 8), seed: int = 0, states: int = 96) -> Workload:
+    """Boxes of 40^3 points on a periodic lattice of stride 24 (40 % overlap
+    per dimension), one box per lattice cell, on a grid of 24 points per cell
+    (spacing 0.5 bohr); wells on self-avoiding random-walk chains of 313
+    wells (1.45 bohr steps), 64 chains per 16x8x8 cells (scaled with the
+    volume, at least one), depth U(0.6, 1.2) Ha, width U(0.6, 1.0) bohr.
+    cells=(16, 8, 8) is the large 384x192x192 workload; smaller lattices keep
+    its box shape, overlap and state count."""
+    cx, cy, cz = (int(c) for c in cells)
+    grid = Grid((24 * cx, 24 * cy, 24 * cz), 0.5)
     rng = np.random.default_rng(seed)
-    chains = _self_avoiding_chains(rng, grid.lengths, 64, 313, 1.45, 1.2)
+    n_chains = max(1, int(round(64 * cx * cy * cz / 1024)))
+    chains = _self_avoiding_chains(rng, grid.lengths, n_chains, 313, 1.45, 1.2)
     wells = []
     for ch in chains:
         D = rng.uniform(0.6, 1.2, size=len(ch))
         w = rng.uniform(0.6, 1.0, size=len(ch))
         for p, d, ww in zip(ch, D, w):
             wells.append((p[0], p[1], p[2], d, ww))
-    frags = [Fragment((24 * i, 24 * j, 24 * k), (40, 40, 40), 96)
-             for k in range(8) for j in range(8) for i in range(16)]
-    return Workload("large_lattice_384x192x192", grid, np.array(wells), frags,
+    frags = [Fragment((24 * i, 24 * j, 24 * k), (40, 40, 40), states)
+             for k in range(cz) for j in range(cy) for i in range(cx)]
+    name = ("large_lattice_384x192x192" if (cx, cy, cz) == (16, 8, 8)
+            else f"lattice_{grid.n[0]}x{grid.n[1]}x{grid.n[2]}")
+    return Workload(name, grid, np.array(wells), frags,
                     WindowRule("around_gap", 0.2, n_occ=len(wells)), "f32",
-                    "~20000 wells on 64 self-avoiding chains; 1024 boxes 40^3 "
-                    "on a 16x8x8 lattice of stride 24, 96 states")
+                    f"~{len(wells)} wells on {n_chains} self-avoiding chains; {len(frags)} boxes "
+                    f"40^3 on a {cx}x{cy}x{cz} lattice of stride 24, {states} states")
+
+
+def _large_lattice(seed: int = 0) -> Workload:
+    """384x192x192 grid, ~20000 wells on 64 chains, 1024 boxes 40^3 stride 24."""
+    return lattice_workload((16, 8, 8), seed)
 
 
 WORKLOADS = {

@@ -355,6 +355,49 @@ extern "C" ofm_status ofm_build_fragments(ofm_ctx* c, const ofm_grid* grid, cons
   return OFM_OK;
 }
 
+// A new potential on the same grid and fragments (Eq. 1): the states stay
+// (they remain the basis), the pair list and plans stay, the blocks are
+// discarded.
+extern "C" ofm_status ofm_set_potential(ofm_ctx* c, const double* V, ofm_location v_loc) {
+  if (!c) return OFM_ERR_INVALID;
+  if (!c->built) return ofm_fail(c, OFM_ERR_STATE, "ofm_build_fragments must come first");
+  if (!V) return ofm_fail(c, OFM_ERR_INVALID, "V must not be NULL");
+  if (v_loc != OFM_HOST && v_loc != OFM_DEVICE) return ofm_fail(c, OFM_ERR_INVALID, "unknown V location");
+  const size_t es = elem_size(c);
+  const long long npts = (long long)c->grid.n[0] * c->grid.n[1] * c->grid.n[2];
+  const double* src = V;
+  if (v_loc == OFM_HOST) {
+    OFM_TRY(ofm_ensure(c, c->staging, npts * sizeof(double), "staging"));
+    OFM_CUDA(c, cudaMemcpyAsync(c->staging.p, V, npts * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    src = (const double*)c->staging.p;
+  }
+  {
+    KTimer t(c, KC_CONVERT, 1, (double)npts * (8 + es));
+    launch_convert_V(src, c->V.p, npts, es == 8, c->stream);
+  }
+  OFM_TRY(check_launch(c, "convert V"));
+  c->assembled = c->dense_ready = c->factored = false;
+  // host V: the staging buffer is reused by later calls
+  return v_loc == OFM_HOST ? sync(c, "set_potential") : OFM_OK;
+}
+
+// Every assembled block in pair-list order: [H_ab | S_ab], n_a x n_b
+// row-major FP64 each.
+extern "C" ofm_status ofm_get_blocks(ofm_ctx* c, double* HS, ofm_location loc, long long* n_elems) {
+  if (!c) return OFM_ERR_INVALID;
+  if (!c->assembled) return ofm_fail(c, OFM_ERR_STATE, "ofm_assemble_HS must come first");
+  if (loc != OFM_HOST && loc != OFM_DEVICE) return ofm_fail(c, OFM_ERR_INVALID, "unknown location");
+  long long n = 0;
+  for (const HostPair& p : c->pairs) n += 2LL * c->frags[p.a].n * c->frags[p.b].n;
+  if (n_elems) *n_elems = n;
+  if (!HS) return OFM_OK;
+  OFM_TRY(ofm_wait_status(c));
+  OFM_CUDA(c, cudaMemcpyAsync(HS, c->blocks.p, sizeof(double) * n,
+                              loc == OFM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                              c->stream));
+  return sync(c, "get_blocks");
+}
+
 // Sec. III.C: pairs whose fragments' atoms are all at least d_cut apart are
 // left out.  The cutoff and the atoms are kept for later re-plans (a state
 // selection); a new ofm_build_fragments clears them.
@@ -506,7 +549,7 @@ ofm_status ofm_apply_h(ofm_ctx* c) {
 static bool region_schedule(const ofm_ctx* c, ofm_precision prec, int sched) {
   if (prec == OFM_PREC_FP64 || prec == OFM_PREC_FP32) return false;
   if (sched == 1) return false;
-  return ofm_region_ok(c);
+  return sched == 2 ? ofm_region_ok(c) : ofm_region_default(c);
 }
 
 // Plans and buffers an assembly needs, made before any capture: the region
@@ -600,7 +643,8 @@ extern "C" ofm_status ofm_assemble_HS(ofm_ctx* c, ofm_precision prec, const ofm_
   int sched = opts ? opts->schedule : 0;
   if (chunk < 0) return ofm_fail(c, OFM_ERR_INVALID, "chunk_points must be >= 0");
   if (sched < 0 || sched > 2) return ofm_fail(c, OFM_ERR_INVALID, "schedule must be 0, 1 or 2");
-  if (sched == 0) sched = c->schedule;
+  if (prec == OFM_PREC_FP64 || prec == OFM_PREC_FP32) sched = 0;   // one schedule on CUDA cores
+  else if (sched == 0) sched = c->schedule;
   if (chunk == 0) chunk = c->tuned_chunk;
   if (chunk != c->asm_chunk) {
     c->asm_chunk = chunk;
@@ -623,7 +667,7 @@ extern "C" ofm_status ofm_assemble_HS(ofm_ctx* c, ofm_precision prec, const ofm_
       }
       c->stencil_check = !region_schedule(c, prec, sched);
       if (c->asm_tc[prec]) c->tc_check = true;
-      if (prec != OFM_PREC_FP64 && prec != OFM_PREC_FP32) c->last_schedule = sched == 0 ? (ofm_region_ok(c) ? 2 : 1) : sched;
+      if (prec != OFM_PREC_FP64 && prec != OFM_PREC_FP32) c->last_schedule = region_schedule(c, prec, sched) ? 2 : 1;
       c->assembled = true;
       return OFM_OK;
     }

@@ -243,9 +243,10 @@ struct ofm_ctx {
 
 // words of the context's 16-int flag buffer: 0 pivot flag and 2..3 window
 // counts (window solver), 8 staged-stencil wait timeout, 9 tensor-core wait
-// timeout
+// timeout, 12 next work item of the region contraction
 constexpr int OFM_FLAG_STENCIL = 8;
 constexpr int OFM_FLAG_TC = 9;
+constexpr int OFM_FLAG_QUEUE = 12;   // work counter of the region contraction
 
 // helpers used by every translation unit
 ofm_status ofm_fail(ofm_ctx* c, ofm_status s, const std::string& msg);
@@ -279,6 +280,7 @@ ofm_status ofm_wait_status(ofm_ctx* c);
 // region-stacked contraction (region.cu)
 ofm_status ofm_region_plan(ofm_ctx* c);
 bool ofm_region_ok(const ofm_ctx* c);
+bool ofm_region_default(const ofm_ctx* c);   // the plan applies and is not mostly padding
 const char* ofm_region_why(const ofm_ctx* c);
 ofm_status ofm_region_prepare(ofm_ctx* c);   // device tables and buffers of the plan
 ofm_status ofm_region_run(ofm_ctx* c, ofm_precision prec);

@@ -52,12 +52,17 @@ namespace {
 // ----------------------------------------------------------- tables -------
 
 // Pack work: one (fragment, region) block of the plane arena.
+// The points of a region are ordered plane by plane in z, x fastest within a
+// plane, each plane padded to a multiple of 8 points (p8): point (ix, iy, iz)
+// has K index iz * p8 + iy * L[0] + ix, so a 16-byte operand unit (8 BF16 or
+// 4 TF32 points) never straddles two planes.  K is padded to 64-point tiles.
 struct RUnit {
   int frag;
   int s0[3];          // region start (global grid coordinates)
   int L[3];           // region extent
-  int npts;           // |R|
-  long long tile0;    // first global pack tile of this unit
+  int p8;             // plane stride in K: L[0] * L[1] rounded up to 8
+  int ntiles;         // 64-point tiles: (L[2] * p8) / 64 rounded up
+  long long tile0;    // first global tile of this unit
   long long base;     // byte offset of the block in the plane arena
 };
 
@@ -99,6 +104,7 @@ enum { RK_TF32 = 0, RK_BF16 = 1, RK_BF16X3 = 2 };
 
 constexpr int RS_THREADS = 192;    // warp 0 copies, 1 MMA, 2-5 epilogue
 constexpr int RS_NSTAGE = 4;
+constexpr int RS_NQ = 4;           // work-item ring between the roles
 constexpr int RS_ACOLS = 256;      // TMEM columns per accumulator (two accumulators)
 constexpr int RS_ATILE = 128 * 64; // bytes of an A chunk tile (128 rows x 64 B)
 constexpr int RS_BTILE = 256 * 64; // bytes of a B chunk tile (256 rows x 64 B)
@@ -106,6 +112,8 @@ constexpr int RS_STAGE = 48 * 1024;
 constexpr int RS_SMEM = RS_NSTAGE * RS_STAGE;
 constexpr int RS_MAXROWS = 128;    // padded states per fragment this path takes
 constexpr int PK_THREADS = 256;
+constexpr int PK_TPC = 4;          // tiles per pack CTA
+constexpr int PK_SEGMAX = 18;      // x and y segments longer than this are split
 
 template <int K> struct KindT;
 template <> struct KindT<RK_TF32> {
@@ -178,7 +186,9 @@ __device__ __forceinline__ uint32_t rtf32(float x) {
 
 // ------------------------------------------------------------- a1: pack ---
 
-// One CTA per 64-point tile of a (fragment, region) unit, in two phases.
+// One CTA per run of up to PK_TPC consecutive 64-point tiles of one
+// (fragment, region) unit (cta[i] = {unit, first tile, tiles}); per tile,
+// two phases.
 //   1. Threads take (point k, 4-state group q) items with q fastest, so a
 //      warp's loads of phi and of each neighbour are contiguous runs of the
 //      point-major FP32 storage (zero outside the dilated storage box; a
@@ -189,166 +199,172 @@ __device__ __forceinline__ uint32_t rtf32(float x) {
 //   2. Each thread writes 16-byte units of the operand planes in the
 //      canonical layout (memory order, coalesced): 8 (BF16) or 4 (TF32)
 //      consecutive points of one state, read down a column of the shared
-//      rows (conflict-free with the odd stride), rounded to TF32, BF16, or
-//      split into BF16 hi and lo.
-// Points of the region outside the fragment's dilated box, the tile's
-// padding points and the state rows beyond n (up to the multiple of 8) are
+//      rows, rounded to TF32, BF16, or split into BF16 hi and lo.
+// Points of the region outside the fragment's dilated box, the plane and
+// tile padding and the state rows beyond n (up to the multiple of 8) are
 // zeros.
 template <int KIND>
 __global__ void __launch_bounds__(PK_THREADS) pack_kernel(
-    const RUnit* __restrict__ units, int nunits, const DevFrag* __restrict__ fr,
+    const RUnit* __restrict__ units, const int4* __restrict__ cta, const DevFrag* __restrict__ fr,
     const float* __restrict__ V, const float* __restrict__ states, unsigned char* __restrict__ planes,
     int gx, int gy, int gz, float c0, float c1) {
   using KT = KindT<KIND>;
   constexpr int ESZ = KT::esz;
+  constexpr int KPU = 16 / ESZ;   // points per 16-byte unit
   extern __shared__ __align__(16) float pk_smem[];
   __shared__ RUnit U;
   __shared__ DevFrag F;
   __shared__ int s_p[64], s_nb[64][6];
   __shared__ float s_v[64];
-  const long long T = blockIdx.x;
   const int tid = threadIdx.x;
-  if (tid == 0) {
-    int lo = 0, hi = nunits - 1;   // last unit with tile0 <= T
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (units[mid].tile0 <= T) lo = mid; else hi = mid - 1;
-    }
-    U = units[lo];
-    F = fr[U.frag];
-  }
+  const int4 job = cta[blockIdx.x];   // unit, first tile, tiles
+  if (tid == 0) U = units[job.x];
   __syncthreads();
-  const int t = (int)(T - U.tile0);
+  if (tid == 0) F = fr[U.frag];
+  __syncthreads();
   const int rows = (F.n + 7) / 8 * 8;
   const int RS = rows + (ESZ == 4 ? 2 : 1);   // shared row stride (words)
   float* sPh = pk_smem;
   float* sHp = pk_smem + 64 * RS;
-  if (tid < 64) {
-    // point tid of the tile: region-local index -> fragment-local coordinates
-    const int e = t * 64 + tid;
-    bool in = e < U.npts;
-    int l[3] = {0, 0, 0}, gi[3] = {0, 0, 0};
-    if (in) {
-      const int ii[3] = {e % U.L[0], (e / U.L[0]) % U.L[1], e / (U.L[0] * U.L[1])};
-      const int gn[3] = {gx, gy, gz};
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        int g = U.s0[d] + ii[d];
-        if (g >= gn[d]) g -= gn[d];
-        gi[d] = g;
-        int ld = g - F.doff[d];
-        if (ld < 0) ld += gn[d];
-        l[d] = ld;
-        in = in && ld < F.dext[d];
-      }
-    }
-    const int ex = F.dext[0], exy = F.dext[0] * F.dext[1];
-    const int p = l[0] + ex * l[1] + exy * l[2];
-    const int st[3] = {1, ex, exy};
-#pragma unroll
-    for (int d = 0; d < 3; ++d)
-#pragma unroll
-      for (int sd = 0; sd < 2; ++sd) {
-        const int c = l[d] + (sd ? -1 : 1);
-        int q = -1;
-        if (c >= 0 && c < F.dext[d]) q = p + (c - l[d]) * st[d];
-        else if (F.full[d]) q = p + (((c + F.dext[d]) % F.dext[d]) - l[d]) * st[d];
-        s_nb[tid][2 * d + sd] = in ? q : -1;
-      }
-    s_p[tid] = in ? p : -1;
-    s_v[tid] = in ? V[(long long)gi[0] + (long long)gx * (gi[1] + (long long)gy * gi[2])] : 0.f;
-  }
-  __syncthreads();
   const float4* S4 = reinterpret_cast<const float4*>(states + F.off);
   const int qpp = F.ld / 4;
   const int nq = rows / 4;
-  for (int it = tid; it < 64 * nq; it += PK_THREADS) {
-    const int k = it / nq, q = it - k * nq;
-    const int p = s_p[k];
-    float4 ph = make_float4(0.f, 0.f, 0.f, 0.f), hp = ph;
-    if (p >= 0 && q < qpp) {
-      ph = S4[(long long)p * qpp + q];
-      float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-      for (int j = 0; j < 6; ++j) {
-        const int nb = s_nb[k][j];
-        if (nb >= 0) {
-          const float4 w = S4[(long long)nb * qpp + q];
-          sum.x += w.x; sum.y += w.y; sum.z += w.z; sum.w += w.w;
-        }
-      }
-      const float dv = c0 + s_v[k];
-      hp.x = fmaf(-c1, sum.x, dv * ph.x);
-      hp.y = fmaf(-c1, sum.y, dv * ph.y);
-      hp.z = fmaf(-c1, sum.z, dv * ph.z);
-      hp.w = fmaf(-c1, sum.w, dv * ph.w);
-    }
-    const float pv[4] = {ph.x, ph.y, ph.z, ph.w};
-    const float hv[4] = {hp.x, hp.y, hp.z, hp.w};
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int row = 4 * q + i;
-      const bool ok = row < F.n;
-      sPh[k * RS + row] = ok ? pv[i] : 0.f;
-      sHp[k * RS + row] = ok ? hv[i] : 0.f;
-    }
-  }
-  __syncthreads();
-  // write-out: 16-byte unit (array A: phi / H phi, chunk cc, 8-row group g,
-  // core kc, row r) of plane(A, hi|lo) at
-  //   base + part(A) [+ lo] + (t*CPT + cc)*cb + g*512 + kc*128 + r*16
+  const int npl = U.L[0] * U.L[1];
   const long long cb = (long long)rows * 64;
-  const long long npl = (long long)((U.npts + 63) / 64) * 128 * rows;   // one 2-byte plane
-  constexpr int KPU = 16 / ESZ;                                         // points per unit
-  const int upc = rows * 4;                                             // units per chunk and plane
+  const long long npl2 = (long long)U.ntiles * 128 * rows;   // one 2-byte plane
+  const int upc = rows * 4;                                  // units per chunk and plane
   const int nunit = 2 * KT::CPT * upc;
   unsigned char* blk = planes + U.base;
-  for (int w = tid; w < nunit; w += PK_THREADS) {
-    const int A = w / (KT::CPT * upc);
-    int u = w - A * (KT::CPT * upc);
-    const int cc = u / upc;
-    u -= cc * upc;
-    const int r = u & 7, kc = (u >> 3) & 3, g = u >> 5;
-    const int row = 8 * g + r;
-    const int k0 = cc * KT::KC + kc * KPU;
-    const float* src = (A ? sHp : sPh) + k0 * RS + row;
-    float x[KPU];
+  for (int t = job.y; t < job.y + job.z; ++t) {
+    if (t > job.y) __syncthreads();   // the previous tile's shared data is consumed
+    if (tid < 64) {
+      // point tid of the tile: K index -> (ix, iy, iz) -> fragment-local coordinates
+      const int K = t * 64 + tid;
+      const int iz = K / U.p8, r = K - iz * U.p8;
+      bool in = iz < U.L[2] && r < npl;
+      int l[3] = {0, 0, 0}, gi[3] = {0, 0, 0};
+      if (in) {
+        const int ii[3] = {r % U.L[0], r / U.L[0], iz};
+        const int gn[3] = {gx, gy, gz};
 #pragma unroll
-    for (int j = 0; j < KPU; ++j) x[j] = src[j * RS];
-    const long long off = (long long)(t * KT::CPT + cc) * cb + g * 512 + kc * 128 + r * 16;
-    if constexpr (KIND == RK_TF32) {
-      const uint4 v = make_uint4(rtf32(x[0]), rtf32(x[1]), rtf32(x[2]), rtf32(x[3]));
-      *reinterpret_cast<uint4*>(blk + A * 2 * npl + off) = v;
-    } else {
-      uint32_t hw[4], lw[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const __nv_bfloat162 h2 = __floats2bfloat162_rn(x[2 * j], x[2 * j + 1]);
-        hw[j] = *reinterpret_cast<const uint32_t*>(&h2);
-        if constexpr (KIND == RK_BF16X3) {
-          const float2 hf = __bfloat1622float2(h2);
-          const __nv_bfloat162 l2 = __floats2bfloat162_rn(x[2 * j] - hf.x, x[2 * j + 1] - hf.y);
-          lw[j] = *reinterpret_cast<const uint32_t*>(&l2);
+        for (int d = 0; d < 3; ++d) {
+          int g = U.s0[d] + ii[d];
+          if (g >= gn[d]) g -= gn[d];
+          gi[d] = g;
+          int ld = g - F.doff[d];
+          if (ld < 0) ld += gn[d];
+          l[d] = ld;
+          in = in && ld < F.dext[d];
         }
       }
-      *reinterpret_cast<uint4*>(blk + A * 2 * npl + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-      if constexpr (KIND == RK_BF16X3)
-        *reinterpret_cast<uint4*>(blk + A * 2 * npl + npl + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+      const int ex = F.dext[0], exy = F.dext[0] * F.dext[1];
+      const int p = l[0] + ex * l[1] + exy * l[2];
+      const int st[3] = {1, ex, exy};
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int sd = 0; sd < 2; ++sd) {
+          const int c = l[d] + (sd ? -1 : 1);
+          int q = -1;
+          if (c >= 0 && c < F.dext[d]) q = p + (c - l[d]) * st[d];
+          else if (F.full[d]) q = p + ((c < 0 ? c + F.dext[d] : c - F.dext[d]) - l[d]) * st[d];
+          s_nb[tid][2 * d + sd] = in ? q : -1;
+        }
+      s_p[tid] = in ? p : -1;
+      s_v[tid] = in ? V[(long long)gi[0] + (long long)gx * (gi[1] + (long long)gy * gi[2])] : 0.f;
     }
-  }
+    __syncthreads();
+    for (int it = tid; it < 64 * nq; it += PK_THREADS) {
+      const int k = it / nq, q = it - k * nq;
+      const int p = s_p[k];
+      float4 ph = make_float4(0.f, 0.f, 0.f, 0.f), hp = ph;
+      if (p >= 0 && q < qpp) {
+        ph = S4[(long long)p * qpp + q];
+        float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+          const int nb = s_nb[k][j];
+          if (nb >= 0) {
+            const float4 w = S4[(long long)nb * qpp + q];
+            sum.x += w.x; sum.y += w.y; sum.z += w.z; sum.w += w.w;
+          }
+        }
+        const float dv = c0 + s_v[k];
+        hp.x = fmaf(-c1, sum.x, dv * ph.x);
+        hp.y = fmaf(-c1, sum.y, dv * ph.y);
+        hp.z = fmaf(-c1, sum.z, dv * ph.z);
+        hp.w = fmaf(-c1, sum.w, dv * ph.w);
+      }
+      const float pv[4] = {ph.x, ph.y, ph.z, ph.w};
+      const float hv[4] = {hp.x, hp.y, hp.z, hp.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int row = 4 * q + i;
+        const bool ok = row < F.n;
+        sPh[k * RS + row] = ok ? pv[i] : 0.f;
+        sHp[k * RS + row] = ok ? hv[i] : 0.f;
+      }
+    }
+    __syncthreads();
+    // write-out: 16-byte unit (array A: phi / H phi, chunk cc, 8-row group g,
+    // core kc, row r) of plane(A, hi|lo) at
+    //   base + part(A) [+ lo] + (t*CPT + cc)*cb + g*512 + kc*128 + r*16
+    for (int w = tid; w < nunit; w += PK_THREADS) {
+      const int A = w / (KT::CPT * upc);
+      int u = w - A * (KT::CPT * upc);
+      const int cc = u / upc;
+      u -= cc * upc;
+      const int r = u & 7, kc = (u >> 3) & 3, g = u >> 5;
+      const int row = 8 * g + r;
+      const int k0 = cc * KT::KC + kc * KPU;
+      const float* src = (A ? sHp : sPh) + k0 * RS + row;
+      float x[KPU];
+#pragma unroll
+      for (int j = 0; j < KPU; ++j) x[j] = src[j * RS];
+      const long long off = (long long)(t * KT::CPT + cc) * cb + g * 512 + kc * 128 + r * 16;
+      if constexpr (KIND == RK_TF32) {
+        const uint4 v = make_uint4(rtf32(x[0]), rtf32(x[1]), rtf32(x[2]), rtf32(x[3]));
+        *reinterpret_cast<uint4*>(blk + A * 2 * npl2 + off) = v;
+      } else {
+        uint32_t hw[4], lw[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const __nv_bfloat162 h2 = __floats2bfloat162_rn(x[2 * j], x[2 * j + 1]);
+          hw[j] = *reinterpret_cast<const uint32_t*>(&h2);
+          if constexpr (KIND == RK_BF16X3) {
+            const float2 hf = __bfloat1622float2(h2);
+            const __nv_bfloat162 l2 = __floats2bfloat162_rn(x[2 * j] - hf.x, x[2 * j + 1] - hf.y);
+            lw[j] = *reinterpret_cast<const uint32_t*>(&l2);
+          }
+        }
+        *reinterpret_cast<uint4*>(blk + A * 2 * npl2 + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        if constexpr (KIND == RK_BF16X3)
+          *reinterpret_cast<uint4*>(blk + A * 2 * npl2 + npl2 + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+      }
+    }
+  }   // tiles
 }
 
 // -------------------------------------------------------- a3/a4: contract --
 
+// Items are taken in order from a global counter (*next, zero at launch) by
+// the producer warp, which passes each index to the MMA thread and the
+// epilogue warps through a small ring in shared memory (RS_NQ entries, each
+// with a full and an empty mbarrier); an index >= nitems ends the roles.
+// Consecutive items -- the M x N tiles of one region -- therefore start
+// together on different SMs and read the same operand chunks at about the
+// same time, which keeps them in L2.
 template <int KIND>
 __global__ void __launch_bounds__(RS_THREADS, 1) region_kernel(
     const RItem* __restrict__ items, int nitems, const RPiece* __restrict__ pieces,
     const RRowSeg* __restrict__ rsegs, const RColSeg* __restrict__ csegs,
     const long long* __restrict__ stab, const unsigned char* __restrict__ planes,
-    float* __restrict__ slots, int* flag) {
+    float* __restrict__ slots, int* flag, int* next) {
   using KT = KindT<KIND>;
   extern __shared__ __align__(1024) unsigned char rsm[];
   __shared__ __align__(8) unsigned long long full[RS_NSTAGE], empty[RS_NSTAGE], acc_full[2], acc_empty[2];
+  __shared__ __align__(8) unsigned long long q_full[RS_NQ], q_empty[RS_NQ];
+  __shared__ int q_item[RS_NQ];
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_s, issued_s, mma_steps_s;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -368,6 +384,10 @@ __global__ void __launch_bounds__(RS_THREADS, 1) region_kernel(
     for (int i = 0; i < 2; ++i) {
       mbar_init(smem_u32(&acc_full[i]), 1);
       mbar_init(smem_u32(&acc_empty[i]), 4);
+    }
+    for (int i = 0; i < RS_NQ; ++i) {
+      mbar_init(smem_u32(&q_full[i]), 1);
+      mbar_init(smem_u32(&q_empty[i]), 5);   // the MMA thread and the four epilogue warps
     }
     fence_mbar_init();
     abort_s = 0;
@@ -401,14 +421,36 @@ __global__ void __launch_bounds__(RS_THREADS, 1) region_kernel(
     // ---------------------------------------------------------- producer
     int g = 0;
     bool ok = true;
-    for (int ii = blockIdx.x; ii < nitems && ok; ii += gridDim.x) {
+    for (int item_no = 0; ok; ++item_no) {
+      // claim the next item and publish it to the other roles
+      const int qs = item_no % RS_NQ, qu = item_no / RS_NQ;
+      int ii = 0;
+      if (lane == 0) {
+        bool w = qu == 0 || wait(&q_empty[qs], (uint32_t)((qu - 1) & 1));
+        ii = w ? atomicAdd(next, 1) : nitems;
+        q_item[qs] = ii;
+        mbar_arrive(smem_u32(&q_full[qs]));   // release: the index is visible to the waiters
+        ok = w;
+      }
+      ii = __shfl_sync(0xffffffffu, ii, 0);
+      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      if (!ok || ii >= nitems) break;
       const RItem it = items[ii];
-      const int npc = it.npa + it.npb;
-      // stage bytes (every lane computes the same sum)
-      uint32_t sbytes = 0;
-      for (int j = 0; j < npc; ++j)
-        sbytes += (uint32_t)pieces[(j < it.npa ? it.pa0 + j : it.pb0 + j - it.npa)].bytes;
-      sbytes *= (uint32_t)(KT::SC * KT::NPL);
+      const int npc = it.npa + it.npb;   // <= 64 (planner): lane j holds pieces j and j + 32
+      RPiece pc[2];
+      bool isA[2], has[2];
+      uint32_t mine = 0;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int j = lane + 32 * h;
+        has[h] = j < npc;
+        isA[h] = j < it.npa;
+        if (has[h]) {
+          pc[h] = pieces[isA[h] ? it.pa0 + j : it.pb0 + j - it.npa];
+          mine += (uint32_t)pc[h].bytes;
+        }
+      }
+      const uint32_t sbytes = __reduce_add_sync(0xffffffffu, mine) * (uint32_t)(KT::SC * KT::NPL);
       const int nst = it.ntiles * KT::CPT / KT::SC;
       const long long c00 = (long long)it.tile0 * KT::CPT;
       for (int st = 0; st < nst; ++st, ++g) {
@@ -422,17 +464,17 @@ __global__ void __launch_bounds__(RS_THREADS, 1) region_kernel(
         const uint32_t mb = smem_u32(&full[s]);
         if (lane == 0) mbar_arrive_expect(mb, sbytes);
         __syncwarp();
-        for (int j = lane; j < npc; j += 32) {
-          const bool isA = j < it.npa;
-          const RPiece pc = pieces[isA ? it.pa0 + j : it.pb0 + j - it.npa];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (!has[h]) continue;
 #pragma unroll
           for (int cc = 0; cc < KT::SC; ++cc) {
             const long long c = c00 + (long long)st * KT::SC + cc;
-            const unsigned char* src = planes + pc.base + c * pc.cb;
+            const unsigned char* src = planes + pc[h].base + c * pc[h].cb;
 #pragma unroll
             for (int pl = 0; pl < KT::NPL; ++pl) {
-              unsigned char* dst = (isA ? atile(s, cc, pl) : btile(s, cc, pl)) + pc.dst;
-              bulk_g2s(smem_u32(dst), src + (pl ? pc.lo : 0), (uint32_t)pc.bytes, mb);
+              unsigned char* dst = (isA[h] ? atile(s, cc, pl) : btile(s, cc, pl)) + pc[h].dst;
+              bulk_g2s(smem_u32(dst), src + (pl ? pc[h].lo : 0), (uint32_t)pc[h].bytes, mb);
             }
           }
         }
@@ -442,9 +484,14 @@ __global__ void __launch_bounds__(RS_THREADS, 1) region_kernel(
   } else if (warp == 1) {
     // --------------------------------------------------------------- MMA
     if (lane == 0) {
-      int g = 0, item_no = 0;
+      int g = 0;
       bool ok = true;
-      for (int ii = blockIdx.x; ii < nitems && ok; ii += gridDim.x, ++item_no) {
+      for (int item_no = 0; ok; ++item_no) {
+        const int qs = item_no % RS_NQ, qu = item_no / RS_NQ;
+        if (!(ok = wait(&q_full[qs], (uint32_t)(qu & 1)))) break;
+        const int ii = *(volatile int*)&q_item[qs];
+        mbar_arrive(smem_u32(&q_empty[qs]));
+        if (ii >= nitems) break;
         const RItem it = items[ii];
         const int b = item_no & 1, ub = item_no >> 1;
         if (ub > 0 && !(ok = wait(&acc_empty[b], (uint32_t)((ub - 1) & 1)))) break;
@@ -486,10 +533,23 @@ __global__ void __launch_bounds__(RS_THREADS, 1) region_kernel(
     // ---------------------------------------------------------- epilogue
     const int q = warp & 3;   // TMEM lane quadrant
     const int row = q * 32 + lane;
-    int item_no = 0;
     bool ok = true;
-    for (int ii = blockIdx.x; ii < nitems && ok; ii += gridDim.x, ++item_no) {
+    for (int item_no = 0; ok; ++item_no) {
+      const int qs = item_no % RS_NQ, qu = item_no / RS_NQ;
+      ok = __all_sync(0xffffffffu, wait(&q_full[qs], (uint32_t)(qu & 1)));
+      if (!ok) break;
+      const int ii = *(volatile int*)&q_item[qs];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&q_empty[qs]));
+      if (ii >= nitems) break;
       const RItem it = items[ii];
+      // the item's segments, one per lane (the planner keeps nrs <= 32 and
+      // ncs <= 64), loaded while the accumulator fills
+      RRowSeg rsl = {0, 0, 0, 0};
+      RColSeg csl[2] = {{0, 0, 0, 0, 0, 0}, {0, 0, 0, 0, 0, 0}};
+      if (lane < it.nrs) rsl = rsegs[it.rs0 + lane];
+      if (lane < it.ncs) csl[0] = csegs[it.cs0 + lane];
+      if (lane + 32 < it.ncs) csl[1] = csegs[it.cs0 + lane + 32];
       const int b = item_no & 1, ub = item_no >> 1;
       ok = __all_sync(0xffffffffu, wait(&acc_full[b], (uint32_t)(ub & 1)));
       if (!ok) break;
@@ -497,27 +557,38 @@ __global__ void __launch_bounds__(RS_THREADS, 1) region_kernel(
       // this lane's row segment
       int rs = -1, i = 0, na = 0;
       for (int r = 0; r < it.nrs; ++r) {
-        const RRowSeg sg = rsegs[it.rs0 + r];
-        if (row >= sg.r0 && row < sg.r0 + sg.nr) {
+        const int r0 = __shfl_sync(0xffffffffu, rsl.r0, r), nr = __shfl_sync(0xffffffffu, rsl.nr, r);
+        const int i0 = __shfl_sync(0xffffffffu, rsl.i0, r), nn = __shfl_sync(0xffffffffu, rsl.na, r);
+        if (row >= r0 && row < r0 + nr) {
           rs = r;
-          i = sg.i0 + row - sg.r0;
-          na = sg.na;
+          i = i0 + row - r0;
+          na = nn;
         }
       }
       const bool rok = rs >= 0 && i < na;
       for (int c = 0; c < it.ncs; ++c) {
-        const RColSeg cs = csegs[it.cs0 + c];
-        const long long slot = rok ? stab[it.st0 + (long long)rs * it.ncf + cs.cf] : -1;
-        const int nbb = cs.nb;
-        for (int c0 = cs.c0; c0 < cs.c0 + cs.nc; c0 += 8) {
+        const int h = c >> 5, sl = c & 31;
+        const int cc0 = __shfl_sync(0xffffffffu, h ? csl[1].c0 : csl[0].c0, sl);
+        const int cnc = __shfl_sync(0xffffffffu, h ? csl[1].nc : csl[0].nc, sl);
+        const int cj0 = __shfl_sync(0xffffffffu, h ? csl[1].j0 : csl[0].j0, sl);
+        const int cnb = __shfl_sync(0xffffffffu, h ? csl[1].nb : csl[0].nb, sl);
+        const int cpart = __shfl_sync(0xffffffffu, h ? csl[1].part : csl[0].part, sl);
+        const int ccf = __shfl_sync(0xffffffffu, h ? csl[1].cf : csl[0].cf, sl);
+        const long long slot = rok ? stab[it.st0 + (long long)rs * it.ncf + ccf] : -1;
+        for (int c0 = cc0; c0 < cc0 + cnc; c0 += 8) {
           float v[8];
           rtmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * RS_ACOLS + c0), v);
           if (slot >= 0) {
-            float* o = slots + slot + (long long)i * 2 * nbb + cs.part * nbb;
-            const int j0 = cs.j0 + c0 - cs.c0;
+            float* o = slots + slot + (long long)i * 2 * cnb + cpart * cnb;
+            const int j0 = cj0 + c0 - cc0;
+            if (j0 + 8 <= cnb && ((reinterpret_cast<uintptr_t>(o + j0) & 15) == 0)) {
+              *reinterpret_cast<float4*>(o + j0) = make_float4(v[0], v[1], v[2], v[3]);
+              *reinterpret_cast<float4*>(o + j0 + 4) = make_float4(v[4], v[5], v[6], v[7]);
+            } else {
 #pragma unroll
-            for (int jj = 0; jj < 8; ++jj)
-              if (j0 + jj < nbb) o[j0 + jj] = v[jj];
+              for (int jj = 0; jj < 8; ++jj)
+                if (j0 + jj < cnb) o[j0 + jj] = v[jj];
+            }
           }
         }
       }
@@ -564,25 +635,51 @@ __device__ __forceinline__ void two_sum(float& s, float& e, float x) {
   s = t;
 }
 
-__global__ void rfinalize_kernel(const RPair* __restrict__ prs, const float* __restrict__ slots,
-                                 double* __restrict__ blocks) {
+// Sum of column c (S: c = m, H: c = n_b + m) and c + n_b of row i over the
+// pair's slots; the loads of up to 8 slots are issued before they are added.
+__device__ __forceinline__ void slot_sums(const float* __restrict__ p, long long ss, int nslot, int nb,
+                                          double& S, double& H) {
+  float s1 = 0.f, e1 = 0.f, s2 = 0.f, e2 = 0.f;
+  for (int k0 = 0; k0 < nslot; k0 += 8) {
+    float a[8], b[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      a[j] = 0.f;
+      b[j] = 0.f;
+      if (k0 + j < nslot) {
+        a[j] = p[(long long)(k0 + j) * ss];
+        b[j] = p[(long long)(k0 + j) * ss + nb];
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (k0 + j < nslot) {
+        two_sum(s1, e1, a[j]);
+        two_sum(s2, e2, b[j]);
+      }
+  }
+  S = (double)s1 + (double)e1;
+  H = (double)s2 + (double)e2;
+}
+
+__global__ void __launch_bounds__(256) rfinalize_kernel(const RPair* __restrict__ prs,
+                                                        const float* __restrict__ slots,
+                                                        double* __restrict__ blocks) {
   const RPair pr = prs[blockIdx.x];
   const int na = pr.na, nb = pr.nb;
   const long long ss = (long long)na * 2 * nb;
   double* Hblk = blocks + pr.blk_off;
   double* Sblk = Hblk + (long long)na * nb;
-  auto sum = [&](int i, int c) {
-    float s = 0.f, e = 0.f;
-    const float* p = slots + pr.slot0 + (long long)i * 2 * nb + c;
-    for (int k = 0; k < pr.nslot; ++k) two_sum(s, e, p[k * ss]);
-    return (double)s + (double)e;
-  };
+  const float* base = slots + pr.slot0;
   for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < na * nb; e += gridDim.y * blockDim.x) {
     const int i = e / nb, m = e - (e / nb) * nb;
-    double s = sum(i, m), h = sum(i, nb + m);
+    double s, h;
+    slot_sums(base + (long long)i * 2 * nb + m, ss, pr.nslot, nb, s, h);
     if (pr.a == pr.b) {
-      s = 0.5 * (s + sum(m, i));
-      h = 0.5 * (h + sum(m, nb + i));
+      double st, ht;
+      slot_sums(base + (long long)m * 2 * nb + i, ss, pr.nslot, nb, st, ht);
+      s = 0.5 * (s + st);
+      h = 0.5 * (h + ht);
     }
     Sblk[e] = s;
     Hblk[e] = h;
@@ -595,6 +692,7 @@ __global__ void rfinalize_kernel(const RPair* __restrict__ prs, const float* __r
 
 struct RegionPlan {
   std::vector<RUnit> units;
+  std::vector<int4> pack_cta;   // pack CTAs: unit, first tile, tiles
   std::vector<RItem> items;
   std::vector<RPiece> pieces;
   std::vector<RRowSeg> rsegs;
@@ -604,7 +702,7 @@ struct RegionPlan {
   long long plane_bytes = 0, slot_elems = 0, total_tiles = 0;
   double mma_flops = 0.0;     // MMA work per 64-point tile summed (M 128 x N), for one product
   int nregions = 0, nparts = 0, w_min = 1;
-  DevBuf d_units, d_items, d_pieces, d_rsegs, d_csegs, d_stab, d_rpairs, planes, slots;
+  DevBuf d_units, d_pcta, d_items, d_pieces, d_rsegs, d_csegs, d_stab, d_rpairs, planes, slots;
   bool ok = false;
   bool uploaded = false;
   std::string why;
@@ -626,11 +724,8 @@ std::vector<Seg> dim_segments(int n, const std::vector<DevFrag>& fr, int d, int 
   std::sort(bp.begin(), bp.end());
   bp.erase(std::unique(bp.begin(), bp.end()), bp.end());
   std::vector<Seg> s;
-  if (bp.empty()) {
-    s.push_back({0, n});
-    return s;
-  }
   const int m = (int)bp.size();
+  if (m == 0) s.push_back({0, n});
   for (int i = 0; i < m; ++i) {
     const int a = bp[i], b = i + 1 < m ? bp[i + 1] : bp[0] + n;
     s.push_back({a, b - a});
@@ -653,6 +748,19 @@ std::vector<Seg> dim_segments(int n, const std::vector<DevFrag>& fr, int d, int 
     }
   }
   for (auto& x : s) x.s0 %= n;
+  // long x and y segments are split (a region's z plane is staged on chip
+  // by the pack); splitting keeps the cover set
+  if (d < 2) {
+    std::vector<Seg> t;
+    for (const Seg& x : s) {
+      const int parts = (x.len + PK_SEGMAX - 1) / PK_SEGMAX;
+      for (int k = 0; k < parts; ++k) {
+        const int a = (int)((long long)x.len * k / parts), b = (int)((long long)x.len * (k + 1) / parts);
+        t.push_back({(x.s0 + a) % n, b - a});
+      }
+    }
+    s.swap(t);
+  }
   return s;
 }
 
@@ -674,7 +782,7 @@ static void region_plan_build(const int gn[3], RegionPlan* P, const std::vector<
                               const std::vector<HostPair>& prs, const std::vector<long long>& blk_off,
                               int w_min_req, long long slot_budget_bytes,
                               std::vector<long long>* pair_pts = nullptr) {
-  P->units.clear(); P->items.clear(); P->pieces.clear(); P->rsegs.clear(); P->csegs.clear();
+  P->units.clear(); P->pack_cta.clear(); P->items.clear(); P->pieces.clear(); P->rsegs.clear(); P->csegs.clear();
   P->stab.clear(); P->rpairs.clear();
   P->ok = false;
   P->uploaded = false;
@@ -724,7 +832,7 @@ static void region_plan_build(const int gn[3], RegionPlan* P, const std::vector<
   for (int a = 0; a < nf; ++a) rows[a] = (fr[a].n + 7) / 8 * 8;
 
   // plane arena: one block per (fragment, region), 8 bytes per (point, padded state)
-  struct RInfo { long long key; int ix, iy, iz, npts, ntiles; };
+  struct RInfo { long long key; int ix, iy, iz, npts, p8, ntiles; };
   std::vector<RInfo> regs(keys.size());
   std::vector<std::unordered_map<long long, long long>> fbase(nf);
   long long arena = 0, tiles = 0, total_work = 0;
@@ -736,19 +844,22 @@ static void region_plan_build(const int gn[3], RegionPlan* P, const std::vector<
     R.iy = (int)((key / nsx) % nsy);
     R.iz = (int)(key / (nsx * nsy));
     R.npts = seg[0][R.ix].len * seg[1][R.iy].len * seg[2][R.iz].len;
-    R.ntiles = (R.npts + 63) / 64;
+    R.p8 = (seg[0][R.ix].len * seg[1][R.iy].len + 7) / 8 * 8;
+    R.ntiles = (seg[2][R.iz].len * R.p8 + 63) / 64;
     long long M = 0;
     for (int a : cover[key]) {
       RUnit u;
       u.frag = a;
       u.s0[0] = seg[0][R.ix].s0; u.s0[1] = seg[1][R.iy].s0; u.s0[2] = seg[2][R.iz].s0;
       u.L[0] = seg[0][R.ix].len; u.L[1] = seg[1][R.iy].len; u.L[2] = seg[2][R.iz].len;
-      u.npts = R.npts;
+      u.p8 = R.p8;
+      u.ntiles = R.ntiles;
       u.tile0 = tiles;
       u.base = arena;
       fbase[a][key] = arena;
       arena += (long long)R.ntiles * 64 * rows[a] * 8;
       tiles += R.ntiles;
+
       P->units.push_back(u);
       M += rows[a];
     }
@@ -758,6 +869,12 @@ static void region_plan_build(const int gn[3], RegionPlan* P, const std::vector<
   }
   P->plane_bytes = arena;
   P->total_tiles = tiles;
+  for (int ui = 0; ui < (int)P->units.size(); ++ui) {
+    const RUnit& u = P->units[ui];
+    for (int t0 = 0; t0 < u.ntiles; t0 += PK_TPC)
+      P->pack_cta.push_back(make_int4(ui, t0, std::min(PK_TPC, u.ntiles - t0), 0));
+  }
+
   // K split: about six items of equal work per SM, parts of at least 4 tiles
   const long long target = std::max<long long>(4, total_work / (6 * 152));
 
@@ -916,6 +1033,11 @@ static void region_plan_build(const int gn[3], RegionPlan* P, const std::vector<
         }
         it.npb = (int)P->pieces.size() - it.pb0;
         it.ncs = (int)P->csegs.size() - it.cs0;
+        if (it.npa + it.npb > 64 || it.nrs > 32 || it.ncs > 64) {
+          P->why = "region item with more than 64 copy pieces";
+          P->items.clear();
+          return;
+        }
         it.ncf = (int)cfr.size();
         it.st0 = (long long)P->stab.size();
         for (int x : rfr)
@@ -941,7 +1063,7 @@ static ofm_status upload(ofm_ctx* c, DevBuf& b, const std::vector<T>& v, const c
 void ofm_region_free(ofm_ctx* c) {
   RegionPlan* P = c->region;
   if (!P) return;
-  DevBuf* bufs[] = {&P->d_units, &P->d_items, &P->d_pieces, &P->d_rsegs, &P->d_csegs,
+  DevBuf* bufs[] = {&P->d_units, &P->d_pcta, &P->d_items, &P->d_pieces, &P->d_rsegs, &P->d_csegs,
                     &P->d_stab, &P->d_rpairs, &P->planes, &P->slots};
   for (DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
@@ -968,6 +1090,14 @@ ofm_status ofm_region_plan(ofm_ctx* c) {
 
 bool ofm_region_ok(const ofm_ctx* c) { return c->region && c->region->ok; }
 
+// Whether the region plan is the default: its MMA work (one product pass,
+// padding and lower-triangle tiles included) stays within 4x the
+// algorithmic pair flops.  Irregular boxes cut the grid into many small
+// regions whose tiles are mostly padding; there the per-pair GEMMs win.
+bool ofm_region_default(const ofm_ctx* c) {
+  return ofm_region_ok(c) && c->region->mma_flops <= 4.0 * (double)c->flops;
+}
+
 const char* ofm_region_why(const ofm_ctx* c) {
   return c->region ? c->region->why.c_str() : "no region plan";
 }
@@ -976,6 +1106,7 @@ ofm_status ofm_region_prepare(ofm_ctx* c) {
   RegionPlan* P = c->region;
   if (P->uploaded) return OFM_OK;
   OFM_TRY(upload(c, P->d_units, P->units, "region units"));
+  OFM_TRY(upload(c, P->d_pcta, P->pack_cta, "pack launch table"));
   OFM_TRY(upload(c, P->d_items, P->items, "region items"));
   OFM_TRY(upload(c, P->d_pieces, P->pieces, "region pieces"));
   OFM_TRY(upload(c, P->d_rsegs, P->rsegs, "region row segments"));
@@ -1008,33 +1139,34 @@ ofm_status ofm_region_run(ofm_ctx* c, ofm_precision prec) {
   if (!P || !P->ok) return ofm_fail(c, OFM_ERR_INVALID, P ? P->why : "no region plan");
   if (!P->uploaded) return ofm_fail(c, OFM_ERR_STATE, "region plan not prepared");
   const int kind = prec == OFM_PREC_TF32 ? RK_TF32 : prec == OFM_PREC_BF16 ? RK_BF16 : RK_BF16X3;
-  int maxrows = 8;
-  for (const DevFrag& f : c->frags) maxrows = std::max(maxrows, (f.n + 7) / 8 * 8);
+
   const double h = c->grid.h;
   const float c0 = (float)(3.0 / (h * h)), c1 = (float)(0.5 / (h * h));
   {
     KTimer t(c, KC_APPLY, 1, c->pack_bytes[kind]);
-    if (P->total_tiles > 0) {
-      const int nu = (int)P->units.size();
-      const RUnit* u = (const RUnit*)P->d_units.p;
-      const DevFrag* f = (const DevFrag*)c->d_frags.p;
-      const float* V = (const float*)c->V.p;
-      const float* st = (const float*)c->states.p;
-      unsigned char* pl = (unsigned char*)P->planes.p;
-      const unsigned grid = (unsigned)P->total_tiles;
+    const RUnit* u = (const RUnit*)P->d_units.p;
+    const DevFrag* f = (const DevFrag*)c->d_frags.p;
+    const float* V = (const float*)c->V.p;
+    const float* st = (const float*)c->states.p;
+    unsigned char* pl = (unsigned char*)P->planes.p;
+    int maxrows = 8;
+    for (const DevFrag& fq : c->frags) maxrows = std::max(maxrows, (fq.n + 7) / 8 * 8);
+    const int sm = 2 * 64 * (maxrows + 2) * 4;
+    const int4* cta = (const int4*)P->d_pcta.p;
+    const unsigned grid = (unsigned)P->pack_cta.size();
+    if (grid > 0) {
       if (kind == RK_TF32)
-        pack_kernel<RK_TF32><<<grid, PK_THREADS, 2 * 64 * (maxrows + 2) * 4, c->stream>>>(
-            u, nu, f, V, st, pl, c->grid.n[0], c->grid.n[1], c->grid.n[2], c0, c1);
+        pack_kernel<RK_TF32><<<grid, PK_THREADS, sm, c->stream>>>(u, cta, f, V, st, pl, c->grid.n[0], c->grid.n[1], c->grid.n[2], c0, c1);
       else if (kind == RK_BF16)
-        pack_kernel<RK_BF16><<<grid, PK_THREADS, 2 * 64 * (maxrows + 1) * 4, c->stream>>>(
-            u, nu, f, V, st, pl, c->grid.n[0], c->grid.n[1], c->grid.n[2], c0, c1);
+        pack_kernel<RK_BF16><<<grid, PK_THREADS, sm, c->stream>>>(u, cta, f, V, st, pl, c->grid.n[0], c->grid.n[1], c->grid.n[2], c0, c1);
       else
-        pack_kernel<RK_BF16X3><<<grid, PK_THREADS, 2 * 64 * (maxrows + 1) * 4, c->stream>>>(
-            u, nu, f, V, st, pl, c->grid.n[0], c->grid.n[1], c->grid.n[2], c0, c1);
+        pack_kernel<RK_BF16X3><<<grid, PK_THREADS, sm, c->stream>>>(u, cta, f, V, st, pl, c->grid.n[0], c->grid.n[1], c->grid.n[2], c0, c1);
     }
     OFM_CUDA(c, cudaGetLastError());
   }
   int* fl = (int*)c->flag.p + OFM_FLAG_TC;
+  int* next = (int*)c->flag.p + OFM_FLAG_QUEUE;
+  OFM_CUDA(c, cudaMemsetAsync(next, 0, sizeof(int), c->stream));
   {
     KTimer t(c, KC_CONTRACT, 1, c->region_bytes[kind], (double)c->flops);
     const int ni = (int)P->items.size();
@@ -1048,11 +1180,11 @@ ofm_status ofm_region_run(ofm_ctx* c, ofm_precision prec) {
       const unsigned char* pl = (const unsigned char*)P->planes.p;
       float* sl = (float*)P->slots.p;
       if (kind == RK_TF32)
-        region_kernel<RK_TF32><<<grid, RS_THREADS, RS_SMEM, c->stream>>>(it, ni, pc, rs, cs, sb, pl, sl, fl);
+        region_kernel<RK_TF32><<<grid, RS_THREADS, RS_SMEM, c->stream>>>(it, ni, pc, rs, cs, sb, pl, sl, fl, next);
       else if (kind == RK_BF16)
-        region_kernel<RK_BF16><<<grid, RS_THREADS, RS_SMEM, c->stream>>>(it, ni, pc, rs, cs, sb, pl, sl, fl);
+        region_kernel<RK_BF16><<<grid, RS_THREADS, RS_SMEM, c->stream>>>(it, ni, pc, rs, cs, sb, pl, sl, fl, next);
       else
-        region_kernel<RK_BF16X3><<<grid, RS_THREADS, RS_SMEM, c->stream>>>(it, ni, pc, rs, cs, sb, pl, sl, fl);
+        region_kernel<RK_BF16X3><<<grid, RS_THREADS, RS_SMEM, c->stream>>>(it, ni, pc, rs, cs, sb, pl, sl, fl, next);
     }
     OFM_CUDA(c, cudaGetLastError());
   }

@@ -31,6 +31,7 @@ EXPORTS = [
     "ofm_set_dense_HS", "ofm_plan_pairs", "ofm_set_profiling", "ofm_get_kernel_stats",
     "ofm_pair_blocks_noalloc", "ofm_set_pair_cutoff", "ofm_select_states", "ofm_homo_lumo_gap",
     "ofm_window_from_index", "ofm_autotune_assembly", "ofm_pencil_apply", "ofm_plan_regions",
+    "ofm_set_potential", "ofm_get_blocks",
 ]
 SCHEDULE = {"auto": 0, "pair": 1, "region": 2}
 
@@ -120,6 +121,8 @@ def load_library(path: str = LIB_PATH):
         "ofm_pencil_apply": ([P, I, P, C.c_longlong, P, C.c_longlong, I], I),
         "ofm_plan_regions": ([C.POINTER(ofm_grid), C.POINTER(ofm_fragment), I, I,
                               C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), I], I),
+        "ofm_set_potential": ([P, P, I], I),
+        "ofm_get_blocks": ([P, P, I, C.POINTER(C.c_longlong)], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -264,6 +267,37 @@ class Context:
         self.frags = list(frags)
         self.grid = grid
         return self
+
+    # -- ofm_set_potential
+    def set_potential(self, V):
+        """V: float64 (nz, ny, nx) numpy array (host) or CUDA/pinned torch tensor."""
+        if _is_torch(V):
+            assert str(V.dtype) == "torch.float64" and V.is_contiguous()
+            self._check(self.lib.ofm_set_potential(self.h, C.c_void_p(V.data_ptr()),
+                                                   DEVICE if V.is_cuda else HOST))
+            return
+        keep = np.ascontiguousarray(V, dtype=np.float64)
+        self._check(self.lib.ofm_set_potential(self.h, C.c_void_p(keep.ctypes.data), HOST))
+
+    # -- ofm_get_blocks
+    def blocks_count(self):
+        n = C.c_longlong()
+        self._check(self.lib.ofm_get_blocks(self.h, None, HOST, C.byref(n)))
+        return n.value
+
+    def get_blocks(self, out=None):
+        """Every block [H_ab | S_ab] in pair-list order, as one float64 array:
+        numpy (host) by default, or into `out` (a float64 torch tensor, CUDA
+        or pinned host, of blocks_count() elements)."""
+        if out is None:
+            out = np.zeros(self.blocks_count())
+            self._check(self.lib.ofm_get_blocks(self.h, C.c_void_p(out.ctypes.data), HOST, None))
+            return out
+        assert _is_torch(out) and str(out.dtype) == "torch.float64" and out.is_contiguous()
+        assert out.numel() >= self.blocks_count()
+        self._check(self.lib.ofm_get_blocks(self.h, C.c_void_p(out.data_ptr()),
+                                            DEVICE if out.is_cuda else HOST, None))
+        return out
 
     # -- ofm_fragment_eigs
     def fragment_eigs(self, tol=0.0, max_iter=0, degree=0, extra_states=0, seed=0,

@@ -1,10 +1,15 @@
-"""Writes tests/golden/tiny_oracle.json: the FP64 oracle's results on the
-32x12x12 tiny workload (4 boxes 16x12x12, 6 states each, seed 0).
+"""Writes the FP64 oracle's results used as stored expected values:
+  tests/golden/tiny_oracle.json   -- the 32x12x12 tiny workload (4 boxes
+                                     16x12x12, 6 states each, seed 0);
+  tests/golden/alkane_oracle.json -- the 256x32x32 alkane chain (31 boxes
+                                     16x32x32, 32 states each, seed 0): its
+                                     fragment energies and the whole spectrum
+                                     of Eq. 2 (992 eigenvalues).
 
 Calls only oracle/ and the seeded input generator.  The stored numbers are
 the oracle's, not the paper's (the paper prints no worked example: its
 figures are not part of the available text).
-Run from the repository root:  python tests/golden/make_golden.py
+Run from the repository root:  python tests/golden/make_golden.py [tiny|alkane]
 """
 import json
 import os
@@ -17,6 +22,40 @@ import numpy as np  # noqa: E402
 
 from ofm_inputs import make_workload  # noqa: E402
 from oracle import ofm_oracle as O  # noqa: E402
+
+
+def _alkane_fragment(a):
+    wl = make_workload("alkane", seed=0)
+    H = O.hamiltonian(wl.grid, wl.V)
+    return O.fragment_eigs(H, wl.grid, wl.frags[a])
+
+
+def alkane():
+    """The alkane chain through the oracle as it stands: fragment eigensolves
+    (one process each, spawned), pair blocks, dense Eq. 2."""
+    import multiprocessing as mp
+    for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    wl = make_workload("alkane", seed=0)
+    with mp.get_context("spawn").Pool(min(len(wl.frags), os.cpu_count() or 1)) as pool:
+        res = pool.map(_alkane_fragment, range(len(wl.frags)))
+    eps = [w for w, _ in res]
+    Phis = [U for _, U in res]
+    r = O.run_ofm(wl, Phis=Phis)
+    out = {
+        "workload": wl.name,
+        "seed": 0,
+        "source": "oracle/ofm_oracle.py fragment_eigs + run_ofm (FP64), tests/golden/make_golden.py",
+        "fragment_eps": [list(map(float, e)) for e in eps],
+        "n_pairs": len(r["pairs"]),
+        "ofm_spectrum": list(map(float, r["E"])),
+        "window_rule": {"kind": wl.window.kind, "width": wl.window.width, "n_occ": wl.window.n_occ},
+        "S_min_eig": float(np.linalg.eigvalsh(r["Sd"])[0]),
+    }
+    path = os.path.join(ROOT, "tests", "golden", "alkane_oracle.json")
+    with open(path, "w") as f:
+        json.dump(out, f, indent=0)
+    print("wrote", path)
 
 
 def main():
@@ -46,4 +85,8 @@ def main():
 
 
 if __name__ == "__main__":
-    main()
+    which = sys.argv[1:] or ["tiny"]
+    if "tiny" in which:
+        main()
+    if "alkane" in which:
+        alkane()
