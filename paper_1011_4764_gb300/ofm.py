@@ -231,6 +231,7 @@ class Context:
         self.h = h
         self.frags = []
         self.grid = None
+        self._dense_n = 0
 
     def close(self):
         if getattr(self, "h", None):
@@ -388,7 +389,7 @@ class Context:
     def window_from_index(self, i_lo, width, max_out=None):
         """(E, n): E_{i_lo} and the later eigenvalues up to E_{i_lo} + width."""
         if max_out is None:
-            max_out = sum(f.n_states for f in self.frags) or 1
+            max_out = sum(f.n_states for f in self.frags) or self._dense_n or 1
         out = np.zeros(max(1, max_out))
         n = C.c_int()
         self._check(self.lib.ofm_window_from_index(self.h, int(i_lo), float(width), int(max_out),
@@ -458,7 +459,7 @@ class Context:
     # -- ofm_window_eigs / ofm_eigs_by_index / ofm_set_dense_HS
     def window_eigs(self, E_lo, E_hi, max_out=None, vectors=False, n_basis=None):
         if max_out is None:
-            max_out = n_basis or sum(f.n_states for f in self.frags) or 1
+            max_out = n_basis or sum(f.n_states for f in self.frags) or self._dense_n or 1
         E = np.zeros(max(1, max_out))
         nout = C.c_int()
         Cv = None
@@ -495,3 +496,4 @@ class Context:
         H = np.ascontiguousarray(H, dtype=np.float64)
         S = np.ascontiguousarray(S, dtype=np.float64)
         self._check(self.lib.ofm_set_dense_HS(self.h, H.shape[0], _dptr(H), _dptr(S)))
+        self._dense_n = H.shape[0]

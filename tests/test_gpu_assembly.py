@@ -241,3 +241,44 @@ def test_status_codes_for_bad_calls(ofm):
         ctx.assemble("fp32")          # FP32 arithmetic needs FP32 storage
     assert e.value.status == ofm.OFM_ERR_INVALID
     ctx.assemble("fp64")
+
+
+def test_set_potential_and_get_blocks(ofm):
+    """A new potential in the same basis (ofm_set_potential): with V -> V + c
+    the whole-system H gains c I, so every H_ab gains c S_ab while S_ab stays
+    (Eq. 1); the blocks equal the oracle's for the shifted potential.  The
+    block export (ofm_get_blocks) is the pair list's [H_ab | S_ab] blocks
+    concatenated, bit for bit those of ofm_get_block."""
+    import torch
+    wl = make_workload("tiny")
+    r = O.run_ofm(wl)
+    ctx = run_gpu(ofm, wl, r["Phis"], "fp64", "fp64")
+    all0 = ctx.get_blocks()
+    off = 0
+    for a, b in ctx.pairs():
+        na, nb = wl.frags[a].n_states, wl.frags[b].n_states
+        Hg, Sg = ctx.block(a, b)
+        assert np.array_equal(all0[off:off + na * nb].reshape(na, nb), Hg)
+        assert np.array_equal(all0[off + na * nb:off + 2 * na * nb].reshape(na, nb), Sg)
+        off += 2 * na * nb
+    assert off == len(all0) == ctx.blocks_count()
+    c = 0.37
+    ctx.set_potential(wl.V + c)
+    with pytest.raises(ofm.OFMError):
+        ctx.block(0, 1)            # blocks of the old H are gone
+    ctx.assemble("fp64")
+    H2 = O.hamiltonian(wl.grid, wl.V + c)
+    for (a, b), (Hab, Sab) in r["blocks"].items():
+        Hg, Sg = ctx.block(a, b)
+        Ho, So = O.pair_block(H2, wl.grid, wl.frags[a], r["Phis"][a], wl.frags[b], r["Phis"][b])
+        if a == b:
+            Ho = 0.5 * (Ho + Ho.T)
+        assert np.max(np.abs(Hg - (Hab + c * Sab))) < 1e-12
+        assert np.max(np.abs(Hg - Ho)) < 1e-12 and np.max(np.abs(Sg - Sab)) < 1e-13
+    # device output and a pinned host output give the same blocks
+    dev = torch.empty(ctx.blocks_count(), dtype=torch.float64, device="cuda")
+    pin = torch.empty(ctx.blocks_count(), dtype=torch.float64).pin_memory()
+    ctx.get_blocks(dev)
+    ctx.get_blocks(pin)
+    assert np.array_equal(dev.cpu().numpy(), pin.numpy())
+    assert np.array_equal(pin.numpy(), ctx.get_blocks())

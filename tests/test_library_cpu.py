@@ -112,3 +112,40 @@ def test_no_device_is_an_error_not_a_fallback(lib):
         pytest.skip("a CUDA device is present")
     with pytest.raises(lib.OFMError):
         lib.Context()
+
+
+@pytest.mark.parametrize("name", ["tiny", "alkane", "polymer"])
+def test_region_plan_covers_every_pair_exactly(name):
+    """The region plan of the tensor-core assembly (coverage regions: products
+    of the segments between dilated-box boundaries) sums each pair over the
+    regions that hold both fragments; those regions must contain exactly the
+    points of B_a ∩ B_b+ that the oracle counts, for every pair."""
+    from paper_1011_4764_gb300 import ofm
+    wl = make_workload(name)
+    stats, pts = ofm.plan_regions(wl.grid, wl.frags)
+    pairs = O.pair_list(wl.grid, wl.frags)
+    want = []
+    for a, b in pairs:
+        doff, dext = O.dilated_box(wl.grid, wl.frags[b])
+        want.append(O.overlap_points(wl.grid, wl.frags[a].off, wl.frags[a].ext, doff, dext))
+    assert stats["regions"] > 0
+    assert list(pts) == want
+
+
+def test_region_plan_on_wrapping_uneven_boxes():
+    """Boxes that wrap the periodic boundary, span whole dimensions, and have
+    uneven state counts: the same exact coverage, and the plan applies."""
+    from paper_1011_4764_gb300 import ofm
+    grid = Grid((20, 9, 8), 0.45)
+    frags = [Fragment((15, 0, 0), (9, 9, 5), 5), Fragment((3, 2, 4), (7, 5, 8), 7),
+             Fragment((9, 7, 6), (6, 4, 6), 3), Fragment((0, 0, 0), (20, 9, 8), 9),
+             Fragment((18, 5, 2), (4, 9, 3), 2)]
+    stats, pts = ofm.plan_regions(grid, frags)
+    want = []
+    for a, b in O.pair_list(grid, frags):
+        doff, dext = O.dilated_box(grid, frags[b])
+        want.append(O.overlap_points(grid, frags[a].off, frags[a].ext, doff, dext))
+    assert stats["ok"] == 1 and list(pts) == want
+    # segments merged to at least 4 points: regions coarser, coverage unchanged
+    s4, p4 = ofm.plan_regions(grid, frags, w_min=4)
+    assert s4["regions"] <= stats["regions"] and list(p4) == want
