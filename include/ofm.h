@@ -343,6 +343,29 @@ typedef struct {
 ofm_status ofm_set_profiling(ofm_ctx* ctx, int on);
 ofm_status ofm_get_kernel_stats(ofm_ctx* ctx, ofm_kernel_stat* out, int max, int* n);
 
+/* Test hook of the failure detection (for tests, not for production use).
+ * Every device-side wait of the library is bounded: when it runs out, the
+ * kernel records the failure, waits (bounded) for its own copies in flight,
+ * frees what it holds and returns, and the call returns OFM_ERR_TIMEOUT with
+ * the context still usable.  This hook makes one such wait run out, on
+ * purpose and without any fault: what = 1 arms the next region-schedule
+ * contraction launch of ofm_assemble_HS, whose producer then withholds every
+ * operand copy (the tensor cores' first wait gives up; that assembly is
+ * launched directly, not from a captured graph); what = 2 arms the next
+ * tridiagonal reduction of Eq. 2, one of whose CTAs withholds its first
+ * grid-barrier arrival.  bound: polls before the held wait gives up (0: the
+ * usual bound, about a second).  what = 0 disarms.  The timeout is reported
+ * by the call that reads the device status (ofm_get_block etc. after an
+ * assembly; the window call itself for Eq. 2).
+ * Host-side injection, which never touches the device: the environment
+ * variable OFM_FAULT, read by ofm_create, makes that context report
+ * OFM_ERR_OOM for its allocations of 4 KiB or more (oom), OFM_ERR_TIMEOUT when
+ * it reads the device status after an assembly (timeout),
+ * OFM_ERR_NOT_CONVERGED from ofm_fragment_eigs with every output filled
+ * (nonconv), or OFM_ERR_NOT_POSDEF from the factorisation of Eq. 2
+ * (notposdef). */
+ofm_status ofm_test_hold_wait(ofm_ctx* ctx, int what, int bound);
+
 /* Host-only planner query (needs no GPU and no context): validates the
  * geometry like ofm_build_fragments and returns the pair list (Sec. II,
  * pairs of fragments that share grid points through the stencil) with the

@@ -6,6 +6,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <cstdlib>
+#include <string>
 #include <new>
 
 #include "ofm_internal.h"
@@ -29,6 +31,11 @@ ofm_status ofm_cuda_check(ofm_ctx* c, cudaError_t e, const char* what) {
 ofm_status ofm_ensure(ofm_ctx* c, DevBuf& b, size_t bytes, const char* what) {
   if (bytes == 0) bytes = 16;
   if (b.cap >= bytes) return OFM_OK;
+  if (c && c->fault == OFM_FAULT_OOM && bytes >= 4096) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "cudaMalloc of %zu bytes for %s failed (injected by OFM_FAULT=oom)", bytes, what);
+    return ofm_fail(c, OFM_ERR_OOM, buf);
+  }
   if (b.p) {
     cudaError_t e = cudaFree(b.p);
     b.p = nullptr;
@@ -128,6 +135,11 @@ extern "C" ofm_status ofm_create(ofm_ctx** out, void* cuda_stream) {
     delete c;
     cudaGetLastError();
     return OFM_ERR_CUDA;
+  }
+  if (const char* f = std::getenv("OFM_FAULT")) {
+    const std::string k(f);
+    c->fault = k == "oom" ? OFM_FAULT_OOM : k == "timeout" ? OFM_FAULT_TIMEOUT
+             : k == "nonconv" ? OFM_FAULT_NONCONV : k == "notposdef" ? OFM_FAULT_NOTPOSDEF : OFM_FAULT_NONE;
   }
   if (cuda_stream) {
     c->stream = (cudaStream_t)cuda_stream;
@@ -398,6 +410,18 @@ extern "C" ofm_status ofm_get_blocks(ofm_ctx* c, double* HS, ofm_location loc, l
   return sync(c, "get_blocks");
 }
 
+// Test hook of the failure detection: the next launch of the chosen bounded
+// device wait runs out (its producer withholds what it waits for), nothing
+// faults or hangs, and the status reports OFM_ERR_TIMEOUT.
+extern "C" ofm_status ofm_test_hold_wait(ofm_ctx* c, int what, int bound) {
+  if (!c) return OFM_ERR_INVALID;
+  if (what < 0 || what > 2 || bound < 0) return ofm_fail(c, OFM_ERR_INVALID, "what must be 0, 1 or 2 and bound >= 0");
+  c->hold_tc = what == 1;
+  c->hold_tri = what == 2;
+  c->hold_bound = bound;
+  return OFM_OK;
+}
+
 // Sec. III.C: pairs whose fragments' atoms are all at least d_cut apart are
 // left out.  The cutoff and the atoms are kept for later re-plans (a state
 // selection); a new ofm_build_fragments clears them.
@@ -633,6 +657,7 @@ static ofm_status capture_assembly(ofm_ctx* c, ofm_precision prec, int sched) {
 
 extern "C" ofm_status ofm_assemble_HS(ofm_ctx* c, ofm_precision prec, const ofm_assemble_opts* opts) {
   if (!c) return OFM_ERR_INVALID;
+  c->fault_due = c->fault == OFM_FAULT_TIMEOUT;   // host-side injection: the next status read
   if (!c->built) return ofm_fail(c, OFM_ERR_STATE, "ofm_build_fragments must come first");
   if (!c->have_states) return ofm_fail(c, OFM_ERR_STATE, "fragment states are not set (ofm_fragment_eigs or ofm_set_fragment_states)");
   if (prec < OFM_PREC_FP64 || prec > OFM_PREC_BF16X3) return ofm_fail(c, OFM_ERR_INVALID, "unknown precision");
@@ -652,11 +677,12 @@ extern "C" ofm_status ofm_assemble_HS(ofm_ctx* c, ofm_precision prec, const ofm_
   }
   c->assembled = c->dense_ready = c->factored = false;
   OFM_TRY(prepare_assembly(c, prec, sched));
+  const bool held = c->hold_tc && region_schedule(c, prec, sched);   // one direct launch
   if (c->asm_exec[prec] && c->asm_sched[prec] != sched) {
     cudaGraphExecDestroy(c->asm_exec[prec]);
     c->asm_exec[prec] = nullptr;
   }
-  if (use_graph && !c->prof.on && !c->graphs_off) {
+  if (use_graph && !c->prof.on && !c->graphs_off && !held) {
     if (!c->asm_exec[prec]) OFM_TRY(capture_assembly(c, prec, sched));
     if (c->asm_exec[prec]) {
       OFM_CUDA(c, cudaGraphLaunch(c->asm_exec[prec], c->stream));

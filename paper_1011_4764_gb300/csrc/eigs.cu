@@ -1480,10 +1480,16 @@ extern "C" ofm_status ofm_fragment_eigs(ofm_ctx* c, const ofm_eig_opts* opts, do
   std::fill(c->frag_set.begin(), c->frag_set.end(), 1);
   c->have_states = true;
   c->last_eig_iters = it;
+  const bool injected = c->fault == OFM_FAULT_NONCONV;
+  if (injected) converged = false;
   if (!converged) {
-    char buf[160];
-    snprintf(buf, sizeof buf, "fragment eigensolver: largest residual %.3e > tol %.3e after %d iterations",
-             worst, tol, it);
+    char buf[192];
+    if (injected)
+      snprintf(buf, sizeof buf, "fragment eigensolver: not converged (injected by OFM_FAULT=nonconv; "
+               "largest residual %.3e after %d iterations)", worst, it);
+    else
+      snprintf(buf, sizeof buf, "fragment eigensolver: largest residual %.3e > tol %.3e after %d iterations",
+               worst, tol, it);
     return ofm_fail(c, OFM_ERR_NOT_CONVERGED, buf);
   }
   return OFM_OK;

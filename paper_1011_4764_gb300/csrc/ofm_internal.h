@@ -237,6 +237,12 @@ struct ofm_ctx {
   int schedule = 0;                 // the tuned or caller-set default schedule
   int last_schedule = 0;            // schedule of the last tensor-core assembly (1 or 2)
   bool hphi_ready = false;          // the FP32/FP64 H phi buffer is allocated
+  // failure injection: host-side (OFM_FAULT at ofm_create; never touches the
+  // device) and the test hook that makes one bounded device wait run out
+  int fault = 0;                    // OFM_FAULT_*
+  bool fault_due = false;           // an injected timeout waits for the next status read
+  int hold_tc = 0, hold_tri = 0;    // armed for the next launch
+  int hold_bound = 0;               // polls before the held wait gives up (0: usual bound)
   double pack_bytes[3] = {0, 0, 0};     // algorithmic bytes of the apply + pack, per kind
   double region_bytes[3] = {0, 0, 0};   // algorithmic bytes of the region contraction, per kind
 };
@@ -247,6 +253,10 @@ struct ofm_ctx {
 constexpr int OFM_FLAG_STENCIL = 8;
 constexpr int OFM_FLAG_TC = 9;
 constexpr int OFM_FLAG_QUEUE = 12;   // work counter of the region contraction
+
+// host-side fault injection (environment variable OFM_FAULT read by ofm_create)
+enum { OFM_FAULT_NONE = 0, OFM_FAULT_OOM = 1, OFM_FAULT_TIMEOUT = 2, OFM_FAULT_NONCONV = 3,
+       OFM_FAULT_NOTPOSDEF = 4 };
 
 // helpers used by every translation unit
 ofm_status ofm_fail(ofm_ctx* c, ofm_status s, const std::string& msg);

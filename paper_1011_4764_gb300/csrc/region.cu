@@ -347,6 +347,10 @@ __global__ void __launch_bounds__(PK_THREADS) pack_kernel(
 
 // -------------------------------------------------------- a3/a4: contract --
 
+// hold (a test of the failure detection): the producer publishes its first
+// item and then withholds every copy, so the MMA thread's wait for the first
+// stage runs out after wait_iters polls (no copy in flight), the roles give
+// up, and the launch reports a timeout through *flag.
 // Items are taken in order from a global counter (*next, zero at launch) by
 // the producer warp, which passes each index to the MMA thread and the
 // epilogue warps through a small ring in shared memory (RS_NQ entries, each
@@ -359,7 +363,7 @@ __global__ void __launch_bounds__(RS_THREADS, 1) region_kernel(
     const RItem* __restrict__ items, int nitems, const RPiece* __restrict__ pieces,
     const RRowSeg* __restrict__ rsegs, const RColSeg* __restrict__ csegs,
     const long long* __restrict__ stab, const unsigned char* __restrict__ planes,
-    float* __restrict__ slots, int* flag, int* next) {
+    float* __restrict__ slots, int* flag, int* next, int hold, int wait_iters) {
   using KT = KindT<KIND>;
   extern __shared__ __align__(1024) unsigned char rsm[];
   __shared__ __align__(8) unsigned long long full[RS_NSTAGE], empty[RS_NSTAGE], acc_full[2], acc_empty[2];
@@ -408,7 +412,7 @@ __global__ void __launch_bounds__(RS_THREADS, 1) region_kernel(
 
   auto wait = [&](unsigned long long* bar, uint32_t parity) -> bool {
     const uint32_t a = smem_u32(bar);
-    for (int i = 0; i < (1 << 20); ++i) {
+    for (int i = 0; i < wait_iters; ++i) {
       if (mbar_try(a, parity)) return true;
       if (*(volatile int*)&abort_s) return false;
     }
@@ -434,7 +438,7 @@ __global__ void __launch_bounds__(RS_THREADS, 1) region_kernel(
       }
       ii = __shfl_sync(0xffffffffu, ii, 0);
       ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-      if (!ok || ii >= nitems) break;
+      if (!ok || ii >= nitems || hold) break;
       const RItem it = items[ii];
       const int npc = it.npa + it.npb;   // <= 64 (planner): lane j holds pieces j and j + 32
       RPiece pc[2];
@@ -1179,12 +1183,15 @@ ofm_status ofm_region_run(ofm_ctx* c, ofm_precision prec) {
       const long long* sb = (const long long*)P->d_stab.p;
       const unsigned char* pl = (const unsigned char*)P->planes.p;
       float* sl = (float*)P->slots.p;
+      const int hold = c->hold_tc;   // armed by the test hook for one launch
+      const int wi = hold && c->hold_bound > 0 ? c->hold_bound : (1 << 20);
+      c->hold_tc = 0;
       if (kind == RK_TF32)
-        region_kernel<RK_TF32><<<grid, RS_THREADS, RS_SMEM, c->stream>>>(it, ni, pc, rs, cs, sb, pl, sl, fl, next);
+        region_kernel<RK_TF32><<<grid, RS_THREADS, RS_SMEM, c->stream>>>(it, ni, pc, rs, cs, sb, pl, sl, fl, next, hold, wi);
       else if (kind == RK_BF16)
-        region_kernel<RK_BF16><<<grid, RS_THREADS, RS_SMEM, c->stream>>>(it, ni, pc, rs, cs, sb, pl, sl, fl, next);
+        region_kernel<RK_BF16><<<grid, RS_THREADS, RS_SMEM, c->stream>>>(it, ni, pc, rs, cs, sb, pl, sl, fl, next, hold, wi);
       else
-        region_kernel<RK_BF16X3><<<grid, RS_THREADS, RS_SMEM, c->stream>>>(it, ni, pc, rs, cs, sb, pl, sl, fl, next);
+        region_kernel<RK_BF16X3><<<grid, RS_THREADS, RS_SMEM, c->stream>>>(it, ni, pc, rs, cs, sb, pl, sl, fl, next, hold, wi);
     }
     OFM_CUDA(c, cudaGetLastError());
   }

@@ -746,6 +746,11 @@ ofm_status ofm_contract_tc(ofm_ctx* c, ofm_precision prec) {
 // Reports a bounded-wait timeout of an earlier tensor-core or staged-stencil
 // launch (each sets its flag word; the flags are read once and cleared).
 ofm_status ofm_wait_status(ofm_ctx* c) {
+  if (c->fault_due) {
+    c->fault_due = false;
+    c->tc_check = c->stencil_check = false;
+    return ofm_fail(c, OFM_ERR_TIMEOUT, "a bounded device wait exceeded its bound (injected by OFM_FAULT=timeout)");
+  }
   if (c->tc_check) {
     int h = 0;
     int* f = (int*)c->flag.p + OFM_FLAG_TC;

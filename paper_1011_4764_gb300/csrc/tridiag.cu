@@ -33,7 +33,9 @@ namespace ofm {
 struct GridBar {
   unsigned int count;
   int err;
-  unsigned int pad[30];
+  unsigned int hold;    // test of the failure detection: CTA 0 withholds its first arrival
+  unsigned int limit;   // polls before a wait gives up (0: 2^24)
+  unsigned int pad[28];
 };
 
 // All CTAs of a cooperative launch meet here: one release atomic per CTA
@@ -44,16 +46,21 @@ __device__ bool grid_sync(GridBar* bar, unsigned int nblocks) {
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile int* verr = &bar->err;
-    unsigned int old;
-    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], 1;" : "=r"(old) : "l"(&bar->count) : "memory");
+    // a held arrival (test hook, CTA 0 once): nobody reaches the target, every
+    // CTA's wait runs out
+    const bool skip = blockIdx.x == 0 && atomicExch(&bar->hold, 0u) != 0u;
+    unsigned int old = 0;
+    if (!skip)
+      asm volatile("atom.add.release.gpu.global.u32 %0, [%1], 1;" : "=r"(old) : "l"(&bar->count) : "memory");
     const unsigned int target = (old / nblocks + 1u) * nblocks;
+    const unsigned int lim = *(volatile unsigned int*)&bar->limit ? *(volatile unsigned int*)&bar->limit : (1u << 24);
     ok = 1;
     unsigned int spins = 0;
     while (true) {
       unsigned int cur;
       asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(&bar->count) : "memory");
       if ((int)(cur - target) >= 0) break;
-      if (*verr != 0 || ++spins > (1u << 24)) {
+      if (*verr != 0 || ++spins > lim) {
         atomicExch(&bar->err, 1);
         ok = 0;
         break;
@@ -747,6 +754,19 @@ __global__ void __launch_bounds__(128) window_size_kernel(const double* __restri
 
 using namespace ofm;
 
+// The test hook's held arrival for the next reduction (one launch): the
+// barrier's hold word and a short poll limit, written after its reset.
+static ofm_status arm_hold(ofm_ctx* c) {
+  if (!c->hold_tri) return OFM_OK;
+  static GridBar h{};   // pageable source of a stream-ordered copy: kept alive
+  h = GridBar{};
+  h.hold = 1;
+  h.limit = c->hold_bound > 0 ? (unsigned int)c->hold_bound : 0u;
+  c->hold_tri = 0;
+  OFM_CUDA(c, cudaMemcpyAsync(c->w_bar.p, &h, sizeof(GridBar), cudaMemcpyHostToDevice, c->stream));
+  return OFM_OK;
+}
+
 // Returns OFM_OK when the persistent reduction ran; OFM_ERR_INVALID when it
 // cannot be used here (the caller then takes the per-column launch path).
 ofm_status ofm_tridiag_persistent(ofm_ctx* c, double* A, int n, double* d, double* e, double* tau,
@@ -775,6 +795,7 @@ ofm_status ofm_tridiag_persistent(ofm_ctx* c, double* A, int n, double* d, doubl
         per_sm2 >= 1 && c->w_eval.cap >= pub_bytes) {
       OFM_TRY(ofm_ensure(c, c->w_bar, sizeof(GridBar), "grid barrier"));
       OFM_CUDA(c, cudaMemsetAsync(c->w_bar.p, 0, sizeof(GridBar), c->stream));
+      OFM_TRY(arm_hold(c));
       // generation 0 in every slot: no column's value yet
       OFM_CUDA(c, cudaMemsetAsync(c->w_eval.p, 0, pub_bytes, c->stream));
       GridBar* bar = (GridBar*)c->w_bar.p;
@@ -801,6 +822,7 @@ ofm_status ofm_tridiag_persistent(ofm_ctx* c, double* A, int n, double* d, doubl
   const int nb = std::max(1, std::min(sms * per_sm, sms));
   OFM_TRY(ofm_ensure(c, c->w_bar, sizeof(GridBar), "grid barrier"));
   OFM_CUDA(c, cudaMemsetAsync(c->w_bar.p, 0, sizeof(GridBar), c->stream));
+  OFM_TRY(arm_hold(c));
   GridBar* bar = (GridBar*)c->w_bar.p;
   void* args[] = {&A, &n, &d, &e, &tau, &pg, &bar};
   OFM_CUDA(c, cudaLaunchCooperativeKernel((const void*)tridiag_persistent_kernel, dim3(nb),

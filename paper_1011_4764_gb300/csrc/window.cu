@@ -413,6 +413,10 @@ static void trsm_lower_left(const double* Q, double* B, double* X, int n, cudaSt
 
 ofm_status ofm_window_factor(ofm_ctx* c) {
   const int n = c->dense_n;
+  if (c->fault == OFM_FAULT_NOTPOSDEF) {
+    c->window_fail_col = 0;
+    return ofm_fail(c, OFM_ERR_NOT_POSDEF, "S is not positive definite: Cholesky pivot 0 is not positive (injected by OFM_FAULT=notposdef)");
+  }
   const size_t bytes = sizeof(double) * (size_t)n * n;
   OFM_TRY(ofm_ensure(c, c->w_L, bytes, "window L"));
   OFM_TRY(ofm_ensure(c, c->w_A, bytes, "window A"));

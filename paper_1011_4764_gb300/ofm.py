@@ -31,7 +31,7 @@ EXPORTS = [
     "ofm_set_dense_HS", "ofm_plan_pairs", "ofm_set_profiling", "ofm_get_kernel_stats",
     "ofm_pair_blocks_noalloc", "ofm_set_pair_cutoff", "ofm_select_states", "ofm_homo_lumo_gap",
     "ofm_window_from_index", "ofm_autotune_assembly", "ofm_pencil_apply", "ofm_plan_regions",
-    "ofm_set_potential", "ofm_get_blocks",
+    "ofm_set_potential", "ofm_get_blocks", "ofm_test_hold_wait",
 ]
 SCHEDULE = {"auto": 0, "pair": 1, "region": 2}
 
@@ -123,6 +123,7 @@ def load_library(path: str = LIB_PATH):
                               C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), I], I),
         "ofm_set_potential": ([P, P, I], I),
         "ofm_get_blocks": ([P, P, I, C.POINTER(C.c_longlong)], I),
+        "ofm_test_hold_wait": ([P, I, I], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -268,6 +269,13 @@ class Context:
         self.frags = list(frags)
         self.grid = grid
         return self
+
+    # -- ofm_test_hold_wait (failure-detection tests)
+    def test_hold_wait(self, what, bound=0):
+        """Arm one bounded device wait to run out: "contract" (the next region
+        contraction) or "tridiag" (the next reduction of Eq. 2); None disarms."""
+        self._check(self.lib.ofm_test_hold_wait(self.h, {None: 0, "contract": 1, "tridiag": 2}[what],
+                                                int(bound)))
 
     # -- ofm_set_potential
     def set_potential(self, V):
