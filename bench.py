@@ -620,6 +620,27 @@ def alkane_extra(ofm, stream, dev):
     res["full_step_ms"] = min(ts)
     res["full_step_tflops"] = F / min(ts) / 1e9
     res["window_count"] = n
+    # the block-sparse pencil product Y = H X (ofm_pencil_apply) with one
+    # column per window eigenvalue: device time and achieved bandwidth
+    try:
+        nb = ctx.plan_info()["basis_size"]
+        with torch.cuda.stream(stream):
+            X = torch.randn((max(1, m), nb), dtype=torch.float64, device=dev)
+            Y = torch.empty_like(X)
+        stream.synchronize()
+        ctx.pencil_apply("H", X, Y)
+        ctx.set_profiling(True)
+        for _ in range(5):
+            ctx.pencil_apply("H", X, Y)
+        st = ctx.kernel_stats()["pencil"]
+        ctx.set_profiling(False)
+        ms = st["ms"] / st["launches"]
+        res["pencil_apply"] = {"columns": int(X.shape[0]), "ms": ms,
+                               "achieved_gbs": st["bytes"] / st["launches"] / (ms * 1e-3) / 1e9,
+                               "achieved_tflops_fp64": st["flops"] / st["launches"] / (ms * 1e-3) / 1e12,
+                               "bytes_per_launch": st["bytes"] / st["launches"]}
+    except Exception as e:
+        res["pencil_apply"] = {"error": str(e)}
     errs = {}
     for p in ("bf16x3", "tf32", "bf16", "fp32"):
         ctx.assemble(p)

@@ -415,9 +415,12 @@ ofm_status ofm_plan_regions(const ofm_grid* grid, const ofm_fragment* frags, int
  * is made.  The first call on a device looks up that array's address and
  * should come before any stream capture.  Calls share the array: calls
  * whose GPU work overlaps race.  Work is enqueued on cuda_stream (NULL =
- * legacy default stream) and not synchronised.  Returns OFM_ERR_INVALID for
- * bad geometry or pointers, or when the pair's work tables and partial
- * tiles do not fit the scratch; OFM_ERR_CUDA when a runtime call fails. */
+ * legacy default stream; otherwise a stream of the current device) and not
+ * synchronised.  Returns OFM_ERR_INVALID for bad geometry or pointers, when
+ * the pair's work tables and partial tiles do not fit the scratch, when
+ * cuda_stream belongs to another device, or when cuda_stream is being
+ * captured (the work tables are staged from host memory that lives only
+ * for the call); OFM_ERR_CUDA when a runtime call fails. */
 #define OFM_NOALLOC_SCRATCH (32u * 1024u * 1024u)
 ofm_status ofm_pair_blocks_noalloc(const ofm_grid* grid, const ofm_fragment* fa,
                                    const ofm_fragment* fb, const float* phi_a,

@@ -216,6 +216,7 @@ static ofm_status plan_contraction(ofm_ctx* c) {
   OFM_TRY(ofm_ensure(c, c->blocks, sizeof(double) * c->blk_elems, "blocks"));
   c->finalize_bytes = (double)c->simt_partial_elems * (es == 8 ? 8 : 4) + 8.0 * c->blk_elems;
   c->region_stale = true;
+  c->sp_stale = true;
   return ofm_plan_extra(c);
 }
 

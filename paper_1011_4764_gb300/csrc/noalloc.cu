@@ -17,9 +17,13 @@
 // exits.  In host code the array's name is only a host-side stand-in, not a
 // device address; the first call on each device (with that device current)
 // looks up the real address with cudaGetSymbolAddress and caches it.  That
-// first call should happen before any stream capture.  Every call shares
-// the array, so calls whose GPU work overlaps (other streams, other host
-// threads) race on it.  The partial tiles need no clearing: every work item
+// first call should happen before any stream capture.  The work tables are
+// staged from host memory that lives only for the call, so a call made
+// while its stream is being captured returns OFM_ERR_INVALID (the captured
+// copy would read that memory after the call).  The stream must belong to
+// the current device (the cached address is the current device's).  Every
+// call shares the array, so calls whose GPU work overlaps (other streams,
+// other host threads) race on it.  The partial tiles need no clearing: every work item
 // overwrites its whole tile before the reduction reads it.
 #include <cuda_runtime.h>
 
@@ -71,6 +75,26 @@ extern "C" ofm_status ofm_pair_blocks_noalloc(const ofm_grid* grid, const ofm_fr
   std::string err;
   if (!validate_geometry(*grid, two, 2, err)) return OFM_ERR_INVALID;
   cudaStream_t s = (cudaStream_t)cuda_stream;
+  {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+      cudaGetLastError();
+      return OFM_ERR_CUDA;
+    }
+    if (cs != cudaStreamCaptureStatusNone) return OFM_ERR_INVALID;
+    int cur = 0, sdev = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess) {
+      cudaGetLastError();
+      return OFM_ERR_CUDA;
+    }
+    if (s != nullptr) {
+      if (cudaStreamGetDevice(s, &sdev) != cudaSuccess) {
+        cudaGetLastError();
+        return OFM_ERR_CUDA;
+      }
+      if (sdev != cur) return OFM_ERR_INVALID;
+    }
+  }
   const bool same = std::memcmp(fa, fb, sizeof(ofm_fragment)) == 0 && phi_a == phi_b;
 
   // fragment table: the caller's buffers are addressed relative to phi_a

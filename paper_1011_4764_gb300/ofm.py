@@ -209,6 +209,16 @@ def pair_blocks_noalloc(grid, fa, fb, phi_a, phi_b, hphi_b, out, stream=0):
     for t in (phi_a, phi_b, hphi_b):
         assert t.is_cuda and str(t.dtype) == "torch.float32" and t.is_contiguous()
     assert out.is_cuda and str(out.dtype) == "torch.float64" and out.is_contiguous()
+
+    def stored(f):   # floats of the storage layout: dilated-box points x ld
+        Pd = 1
+        for d in range(3):
+            Pd *= f.ext[d] + 2 if f.ext[d] < grid.n[d] else f.ext[d]
+        return Pd * ((f.n_states + 3) // 4 * 4)
+    assert phi_a.numel() >= stored(fa), "phi_a is shorter than fragment a's storage layout"
+    assert phi_b.numel() >= stored(fb) and hphi_b.numel() >= stored(fb), \
+        "phi_b / hphi_b are shorter than fragment b's storage layout"
+    assert out.numel() == 2 * fa.n_states * fb.n_states, "out must hold 2 n_a n_b doubles"
     s = lib.ofm_pair_blocks_noalloc(C.byref(g), C.byref(fab[0]), C.byref(fab[1]),
                                     C.c_void_p(phi_a.data_ptr()), C.c_void_p(phi_b.data_ptr()),
                                     C.c_void_p(hphi_b.data_ptr()), C.c_void_p(out.data_ptr()),
@@ -233,6 +243,7 @@ class Context:
         self.frags = []
         self.grid = None
         self._dense_n = 0
+        self.stream_obj = stream if (stream is not None and not isinstance(stream, int)) else None
 
     def close(self):
         if getattr(self, "h", None):
@@ -367,11 +378,19 @@ class Context:
     def pencil_apply(self, which, X, out=None):
         """Y = H X (which "H") or S X (which "S") with the assembled blocks.
         X: CUDA float64 torch tensor of shape (k, basis), contiguous (its rows
-        are the k columns); returns Y of the same shape (enqueued on the
-        context stream)."""
+        are the k columns), ready on the context stream; returns Y of the
+        same shape, written on the context stream (use it there, or
+        synchronise)."""
         assert _is_torch(X) and X.is_cuda and str(X.dtype) == "torch.float64" and X.is_contiguous()
         k, n = X.shape
+        assert n == self.plan_info()["basis_size"], "X must have basis_size columns per row"
+        if out is not None:
+            assert (_is_torch(out) and out.is_cuda and out.device == X.device and out.is_contiguous()
+                    and str(out.dtype) == "torch.float64" and tuple(out.shape) == (k, n)), \
+                "out must be a contiguous CUDA float64 tensor of X's shape on X's device"
         Y = out if out is not None else X.new_empty((k, n))
+        if self.stream_obj is not None and hasattr(Y, "record_stream"):
+            Y.record_stream(self.stream_obj)   # written on the context stream
         self._check(self.lib.ofm_pencil_apply(self.h, {"H": 0, "S": 1}[which], C.c_void_p(X.data_ptr()),
                                               n, C.c_void_p(Y.data_ptr()), n, k))
         return Y

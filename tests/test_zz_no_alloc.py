@@ -1,10 +1,13 @@
-"""The allocation-free pair-block entry point against the regular assembly.
+"""The allocation-free pair-block entry point against the oracle and the
+regular assembly.
 
 ofm_pair_blocks_noalloc serves callers that cannot allocate device memory
 when they need a block (device memory owned by another framework's pool,
 latency-critical paths where cudaMalloc/cudaFree may block, sandboxed code
-handed ready-made buffers).  It must give the same blocks as
-ofm_assemble_HS + ofm_get_block.  Two calls in a row exercise the shared
+handed ready-made buffers).  Its inputs here are the oracle's: seeded states
+and H phi from the oracle's H apply.  It must give the oracle's blocks
+within the FP32 inner-product bound, and the blocks of ofm_assemble_HS +
+ofm_get_block within the same bound.  Two calls in a row exercise the shared
 fixed scratch; the file is collected last so that a failure here comes
 after every other test has run.
 """
@@ -58,15 +61,15 @@ def test_noalloc_pair_blocks_match_the_assembly():
     wl = small_workload(grid_n=grid.n, h=grid.h, frags=frags, seed=5)
     Phis = [random_states(grid, f, seed=700 + a).astype(np.float32).astype(np.float64)
             for a, f in enumerate(frags)]
+    H = O.hamiltonian(grid, wl.V)
     ctx = ofm.Context()
     ctx.build_fragments(grid, wl.V, frags, storage="fp32")
     for a, P in enumerate(Phis):
         ctx.set_fragment_states(a, P)
     ctx.assemble("fp32")
-    H = O.hamiltonian(grid, wl.V)
     dev = [torch.tensor(storage_from_box(grid, f, Phis[a]), device="cuda")
            for a, f in enumerate(frags)]
-    hdev = [torch.tensor(storage_from_dilated(grid, f, ctx.hphi(a)), device="cuda")
+    hdev = [torch.tensor(storage_from_dilated(grid, f, O.apply_h(H, grid, f, Phis[a])), device="cuda")
             for a, f in enumerate(frags)]
     stream = torch.cuda.current_stream().cuda_stream
     # two calls in a row on the shared scratch: an off-diagonal and a diagonal pair
@@ -78,15 +81,21 @@ def test_noalloc_pair_blocks_match_the_assembly():
         got = out.cpu().numpy()
         Hg, Sg = got[:na * nb].reshape(na, nb), got[na * nb:].reshape(na, nb)
         Hr, Sr = ctx.block(a, b)
-        # FP32 sums: per-entry bound 2 K u |a|.|b| (K = points of box a)
+        Ho, So = O.pair_block(H, grid, frags[a], Phis[a], frags[b], Phis[b])
+        if a == b:
+            Ho, So = 0.5 * (Ho + Ho.T), 0.5 * (So + So.T)
+        # FP32 sums: per-entry bound 2 K u |a|.|b| (K = points of box a); the
+        # H phi input is rounded to FP32 too (u |H| |phi_b|)
         Ea = O.zero_extend(grid, frags[a], Phis[a])
         Eb = O.zero_extend(grid, frags[b], Phis[b])
         K = int(np.prod(frags[a].ext))
         bS = 2 * K * U32 * (abs(Ea).T @ abs(Eb)).toarray() + 1e-30
         bH = (2 * K + 8) * U32 * (abs(Ea).T @ (abs(H) @ abs(Eb))).toarray() + 1e-30
         assert np.all(np.isfinite(Hg)) and np.all(np.isfinite(Sg))
-        assert np.all(np.abs(Sg - Sr) <= bS), (a, b)
-        assert np.all(np.abs(Hg - Hr) <= bH), (a, b)
+        assert np.all(np.abs(Sg - So) <= bS), (a, b)
+        assert np.all(np.abs(Hg - Ho) <= bH), (a, b)
+        assert np.all(np.abs(Sg - Sr) <= 2 * bS), (a, b)
+        assert np.all(np.abs(Hg - Hr) <= 2 * bH), (a, b)
     # a pair whose boxes never meet gives zeros
     na, nb = frags[0].n_states, frags[3].n_states
     far = Fragment((30, 0, 0), (12, 10, 10), nb)
@@ -94,3 +103,25 @@ def test_noalloc_pair_blocks_match_the_assembly():
     ofm.pair_blocks_noalloc(grid, frags[0], far, dev[0], dev[3], hdev[3], out, stream)
     torch.cuda.synchronize()
     assert torch.all(out == 0)
+
+
+def test_noalloc_refuses_a_capturing_stream():
+    """The work tables are staged from host memory that lives only for the
+    call, so a call on a stream under capture is refused (nothing is
+    captured)."""
+    ofm = gpu_lib()
+    import torch
+
+    grid = Grid((48, 10, 10), 0.5)
+    fa = Fragment((0, 0, 0), (12, 10, 10), 6)
+    fb = Fragment((6, 0, 0), (12, 10, 10), 6)
+    dev = torch.zeros(14 * 10 * 10 * 8, dtype=torch.float32, device="cuda")
+    out = torch.zeros(2 * 36, dtype=torch.float64, device="cuda")
+    s = torch.cuda.Stream()
+    ofm.pair_blocks_noalloc(grid, fa, fb, dev, dev, dev, out, s.cuda_stream)   # look-up before capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with pytest.raises(ofm.OFMError) as e:
+        with torch.cuda.graph(g, stream=s):
+            ofm.pair_blocks_noalloc(grid, fa, fb, dev, dev, dev, out, s.cuda_stream)
+    assert e.value.status == ofm.OFM_ERR_INVALID
