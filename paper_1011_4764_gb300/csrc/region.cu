@@ -639,54 +639,92 @@ __device__ __forceinline__ void two_sum(float& s, float& e, float x) {
   s = t;
 }
 
-// Sum of column c (S: c = m, H: c = n_b + m) and c + n_b of row i over the
-// pair's slots; the loads of up to 8 slots are issued before they are added.
-__device__ __forceinline__ void slot_sums(const float* __restrict__ p, long long ss, int nslot, int nb,
-                                          double& S, double& H) {
-  float s1 = 0.f, e1 = 0.f, s2 = 0.f, e2 = 0.f;
-  for (int k0 = 0; k0 < nslot; k0 += 8) {
-    float a[8], b[8];
+// One CTA per (pair, 32 x 32 tile of the block): thread (ty, tx) sums rows
+// ty, ty + 8, ty + 16, ty + 24 of the tile at column tx over the pair's
+// slots in region order, S and H; every load is a coalesced row of a slot,
+// up to 8 slots in flight.  A diagonal block also sums the mirrored tile
+// (rows and columns exchanged, read as rows) into shared memory and writes
+// (X + X^T) / 2.  Sums are FP32 two-sum pairs (the rounding error of each
+// addition carried in a second word), converted to FP64 at the end.
+__device__ __forceinline__ void tile_sums(const float* __restrict__ base, long long ss, int nslot,
+                                          int nb, int r0, int c0, int nr, int nc, int ty, int tx,
+                                          double S[4], double H[4]) {
+  float s1[4], e1[4], s2[4], e2[4];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      a[j] = 0.f;
-      b[j] = 0.f;
-      if (k0 + j < nslot) {
-        a[j] = p[(long long)(k0 + j) * ss];
-        b[j] = p[(long long)(k0 + j) * ss + nb];
-      }
-    }
+  for (int r = 0; r < 4; ++r) s1[r] = e1[r] = s2[r] = e2[r] = 0.f;
+  const int c = c0 + tx;
+  for (int k0 = 0; k0 < nslot; k0 += 4) {
+    float a[4][4], b[4][4];
 #pragma unroll
-    for (int j = 0; j < 8; ++j)
-      if (k0 + j < nslot) {
-        two_sum(s1, e1, a[j]);
-        two_sum(s2, e2, b[j]);
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int i = r0 + ty + 8 * r;
+        a[j][r] = 0.f;
+        b[j][r] = 0.f;
+        if (k0 + j < nslot && i < r0 + nr && c < c0 + nc) {
+          const float* p = base + (long long)(k0 + j) * ss + (long long)i * 2 * nb + c;
+          a[j][r] = p[0];
+          b[j][r] = p[nb];
+        }
       }
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (k0 + j < nslot)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          two_sum(s1[r], e1[r], a[j][r]);
+          two_sum(s2[r], e2[r], b[j][r]);
+        }
   }
-  S = (double)s1 + (double)e1;
-  H = (double)s2 + (double)e2;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    S[r] = (double)s1[r] + (double)e1[r];
+    H[r] = (double)s2[r] + (double)e2[r];
+  }
 }
 
 __global__ void __launch_bounds__(256) rfinalize_kernel(const RPair* __restrict__ prs,
                                                         const float* __restrict__ slots,
                                                         double* __restrict__ blocks) {
+  __shared__ double tS[32][33], tH[32][33];
   const RPair pr = prs[blockIdx.x];
   const int na = pr.na, nb = pr.nb;
+  const int tcol = (nb + 31) / 32;
+  const int ti = blockIdx.y / tcol, tm = blockIdx.y - (blockIdx.y / tcol) * tcol;
+  const int r0 = 32 * ti, c0 = 32 * tm;
+  if (r0 >= na) return;
+  const int nr = min(32, na - r0), nc = min(32, nb - c0);
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const long long ss = (long long)na * 2 * nb;
+  const float* base = slots + pr.slot0;
+  double S[4], H[4];
+  tile_sums(base, ss, pr.nslot, nb, r0, c0, nr, nc, ty, tx, S, H);
+  if (pr.a == pr.b) {
+    // the mirrored tile: rows c0.., columns r0.. (n_a = n_b)
+    double St[4], Ht[4];
+    tile_sums(base, ss, pr.nslot, nb, c0, r0, nc, nr, ty, tx, St, Ht);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      tS[ty + 8 * r][tx] = St[r];
+      tH[ty + 8 * r][tx] = Ht[r];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      S[r] = 0.5 * (S[r] + tS[tx][ty + 8 * r]);
+      H[r] = 0.5 * (H[r] + tH[tx][ty + 8 * r]);
+    }
+  }
   double* Hblk = blocks + pr.blk_off;
   double* Sblk = Hblk + (long long)na * nb;
-  const float* base = slots + pr.slot0;
-  for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < na * nb; e += gridDim.y * blockDim.x) {
-    const int i = e / nb, m = e - (e / nb) * nb;
-    double s, h;
-    slot_sums(base + (long long)i * 2 * nb + m, ss, pr.nslot, nb, s, h);
-    if (pr.a == pr.b) {
-      double st, ht;
-      slot_sums(base + (long long)m * 2 * nb + i, ss, pr.nslot, nb, st, ht);
-      s = 0.5 * (s + st);
-      h = 0.5 * (h + ht);
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int i = r0 + ty + 8 * r, m = c0 + tx;
+    if (i < r0 + nr && m < c0 + nc) {
+      Sblk[(long long)i * nb + m] = S[r];
+      Hblk[(long long)i * nb + m] = H[r];
     }
-    Sblk[e] = s;
-    Hblk[e] = h;
   }
 }
 
@@ -1202,7 +1240,7 @@ ofm_status ofm_region_run(ofm_ctx* c, ofm_precision prec) {
       nmax = std::max(nmax, q.nb);
       amax = std::max(amax, q.na);
     }
-    const int chunks = std::max(1, (amax * nmax + 255) / 256);
+    const int chunks = ((amax + 31) / 32) * ((nmax + 31) / 32);   // 32 x 32 tiles of the largest block
     if (!P->rpairs.empty())
       rfinalize_kernel<<<dim3((unsigned)P->rpairs.size(), (unsigned)chunks), 256, 0, c->stream>>>(
           (const RPair*)P->d_rpairs.p, (const float*)P->slots.p, (double*)c->blocks.p);
