@@ -387,12 +387,19 @@ def _large_lattice(seed: int = 0) -> Workload:
     return lattice_workload((16, 8, 8), seed)
 
 
+def _lattice_4x4x4(seed: int = 0) -> Workload:
+    """96^3 grid: 4x4x4 cells of the large lattice (64 boxes 40^3, stride 24,
+    96 states), a few-GB case of the same kernels' shapes."""
+    return lattice_workload((4, 4, 4), seed)
+
+
 WORKLOADS = {
     "tiny": _tiny,
     "alkane": _alkane_chain,
     "polymer": _amorphous_polymer,
     "scaled": _chains_scaled,
     "large": _large_lattice,
+    "lattice4": _lattice_4x4x4,
 }
 
 
