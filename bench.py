@@ -258,15 +258,15 @@ def oracle_sample(name, npairs, workers, reps=1):
     return F, per_rep, w
 
 
-def cpu_baseline_leg(name, npairs=16):
+def cpu_baseline_leg(name, npairs=64):
     cores = os.cpu_count() or 1
     F, per_rep, w = oracle_sample(name, npairs, cores)
     dt = per_rep[0]
     return {"value": F / dt / 1e12, "unit": "TFLOP/s", "cores": w, "kind": "oracle",
             "sample": f"{npairs} seeded sampled pair blocks of {name} on seeded random states, "
                       f"{w} single-threaded processes; {F:.3e} pair flops in {dt:.1f} s (the slowest "
-                      f"process, pair blocks only, the sparse H built beforehand); the rate is "
-                      f"extrapolated by flops to the whole workload"}
+                      f"process, pair blocks only, the sparse H built beforehand); extrapolated: "
+                      f"the rate is carried by flops to the whole workload"}
 
 
 def run_reference(args):
@@ -560,15 +560,18 @@ def extras(args, ctx, ofm, wl, stream, F, dev, prec):
         ex["e2e"] = {"error": str(e)}
     # contraction arithmetic and schedule on the same states: a1-a5 device time
     asm = {}
-    for p in ("bf16x3", "bf16", "tf32", "fp32"):
+    # (the FP32 / FP64 plain forms on the CUDA cores take the same region
+    # plan; FP64 last, it doubles the operand planes and partial slots)
+    for p in ("bf16x3", "bf16", "tf32", "fp32", "fp64"):
         try:
-            asm[p] = _time_assembly(ctx, stream, p)
+            asm[p] = _time_assembly(ctx, stream, p, reps=1 if p == "fp64" else 5)
         except ofm.OFMError as e:
             asm[p] = str(e)
     ex["assembly_ms_by_precision"] = asm
-    if isinstance(asm.get("fp32"), float):
-        ex["speedup_vs_fp32_cuda_cores"] = {p: asm["fp32"] / t for p, t in asm.items()
-                                           if isinstance(t, float)}
+    for plain in ("fp32", "fp64"):
+        if isinstance(asm.get(plain), float):
+            ex[f"speedup_vs_{plain}_cuda_cores"] = {p: asm[plain] / t for p, t in asm.items()
+                                                   if isinstance(t, float)}
     sch = {}
     for s in ("pair", "region"):
         try:

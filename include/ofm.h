@@ -94,18 +94,21 @@ typedef struct {
                             profiling is off (per-launch timing needs separate launches)
                             and on a stream that can be captured (not the legacy default
                             stream); 0 launches the kernels one by one */
-  int schedule;          /* tensor-core precisions only: [0] the context's schedule (the one
-                            ofm_autotune_assembly chose, else "region" where its plan
-                            applies and its MMA work, padding included, stays within 4x
-                            the algorithmic flops, else "pair"); 1 "pair": H phi in the
-                            states' layout,
+  int schedule;          /* [0] the default: for the tensor-core precisions the context's
+                            schedule (the one ofm_autotune_assembly chose), else, and for
+                            FP32 / FP64, "region" where its plan applies and its MMA
+                            work, padding included, stays within 4x the algorithmic
+                            flops, else "pair"; 1 "pair": H phi in the states' layout,
                             then one GEMM per pair (M = n_a padded to 128); 2 "region":
                             the grid is cut into coverage regions (products of the
                             segments between dilated-box boundaries) and every region's
                             fragments are stacked into one GEMM (M = sum of their
-                            n_a), with the H apply writing MMA-ready operands
-                            (OFM_ERR_INVALID where that plan does not apply: more than
-                            128 states per fragment, or partial sums beyond 16 GB) */
+                            n_a), with the H apply writing the operands (OFM_ERR_INVALID
+                            where that plan does not apply: FP64 storage, more than
+                            128 states per fragment, or partial sums beyond 16 GB).
+                            FP32 and FP64 run both schedules on the CUDA cores; the
+                            FP64 region form forms H phi in FP64 from the FP32 states
+                            and needs twice the operand and partial-sum memory */
 } ofm_assemble_opts;
 
 /* Counts describing the planned work (after ofm_build_fragments). */
@@ -120,6 +123,9 @@ typedef struct {
   long long state_bytes;          /* device bytes of the fragment states (one copy) */
   long long hphi_bytes;           /* device bytes of H phi */
   long long apply_points;         /* sum_a |B_a+| * n_a (point-states written by the H apply) */
+  int last_schedule;              /* schedule of the last ofm_assemble_HS: 1 pair, 2 region,
+                                     0 none yet */
+  int pad_;
 } ofm_plan_info;
 
 typedef struct ofm_ctx ofm_ctx;

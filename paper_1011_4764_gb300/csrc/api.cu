@@ -303,8 +303,8 @@ static ofm_status layout_fragments(ofm_ctx* c) {
   // the region path's traffic: the apply + pack reads the states once and
   // writes phi and H phi as operands (8 bytes per point-state for BF16 hi+lo
   // and TF32, 4 for BF16); the contraction reads those operands once
-  for (int k = 0; k < 3; ++k) {
-    const double ob = k == 1 ? 2.0 : 4.0;
+  for (int k = 0; k < 5; ++k) {   // TF32, BF16, BF16 hi+lo, FP32, FP64 operands
+    const double ob = k == 1 ? 2.0 : k == 4 ? 8.0 : 4.0;
     c->pack_bytes[k] = 0;
     c->region_bytes[k] = 0;
     for (auto& f : c->frags) {
@@ -569,10 +569,11 @@ ofm_status ofm_apply_h(ofm_ctx* c) {
   return check_launch(c, "apply H");
 }
 
-// Whether a tensor-core assembly of this precision takes the region-stacked
-// schedule: requested (2), or by default (0) wherever its plan applies.
+// Whether an assembly takes the region-stacked schedule: requested (2), or
+// by default (0) wherever its plan applies (FP32 storage; the CUDA-core
+// precisions then run the plain region form).
 static bool region_schedule(const ofm_ctx* c, ofm_precision prec, int sched) {
-  if (prec == OFM_PREC_FP64 || prec == OFM_PREC_FP32) return false;
+  (void)prec;
   if (sched == 1) return false;
   return sched == 2 ? ofm_region_ok(c) : ofm_region_default(c);
 }
@@ -581,13 +582,13 @@ static bool region_schedule(const ofm_ctx* c, ofm_precision prec, int sched) {
 // plan (host tables after a re-plan), or the H phi buffer and the CUDA-core
 // partial sums.
 static ofm_status prepare_assembly(ofm_ctx* c, ofm_precision prec, int sched) {
-  if (prec != OFM_PREC_FP64 && prec != OFM_PREC_FP32 && sched != 1 && c->region_stale) {
+  if (sched != 1 && c->region_stale) {
     OFM_TRY(ofm_region_plan(c));
     c->region_stale = false;
   }
   if (sched == 2 && !region_schedule(c, prec, sched))
     return ofm_fail(c, OFM_ERR_INVALID, std::string("region schedule unavailable: ") + ofm_region_why(c));
-  if (region_schedule(c, prec, sched)) return ofm_region_prepare(c);   // tables and buffers
+  if (region_schedule(c, prec, sched)) return ofm_region_prepare(c, prec);   // tables and buffers
   OFM_TRY(ensure_hphi(c));
   if (prec == OFM_PREC_FP64 || prec == OFM_PREC_FP32)
     OFM_TRY(ofm_ensure_big(c, c->partials, sizeof(double) * c->simt_partial_elems, "partials"));
@@ -602,7 +603,7 @@ static ofm_status enqueue_assembly(ofm_ctx* c, ofm_precision prec, int sched) {
     return ofm_region_run(c, prec);
   }
   OFM_TRY(ofm_apply_h(c));
-  if (prec != OFM_PREC_FP64 && prec != OFM_PREC_FP32) c->last_schedule = 1;
+  c->last_schedule = 1;
   if (prec == OFM_PREC_FP64 || prec == OFM_PREC_FP32) {
     { KTimer t(c, KC_CONTRACT, 1, c->contract_bytes, (double)c->flops);
     launch_contract_simt(prec, c->storage == OFM_STORE_FP64, (const DevFrag*)c->d_frags.p,
@@ -669,8 +670,9 @@ extern "C" ofm_status ofm_assemble_HS(ofm_ctx* c, ofm_precision prec, const ofm_
   int sched = opts ? opts->schedule : 0;
   if (chunk < 0) return ofm_fail(c, OFM_ERR_INVALID, "chunk_points must be >= 0");
   if (sched < 0 || sched > 2) return ofm_fail(c, OFM_ERR_INVALID, "schedule must be 0, 1 or 2");
-  if (prec == OFM_PREC_FP64 || prec == OFM_PREC_FP32) sched = 0;   // one schedule on CUDA cores
-  else if (sched == 0) sched = c->schedule;
+  // the autotuned schedule is the tensor-core one; the CUDA-core precisions
+  // take the plan's default unless one is requested
+  if (sched == 0 && prec != OFM_PREC_FP64 && prec != OFM_PREC_FP32) sched = c->schedule;
   if (chunk == 0) chunk = c->tuned_chunk;
   if (chunk != c->asm_chunk) {
     c->asm_chunk = chunk;
@@ -678,7 +680,8 @@ extern "C" ofm_status ofm_assemble_HS(ofm_ctx* c, ofm_precision prec, const ofm_
   }
   c->assembled = c->dense_ready = c->factored = false;
   OFM_TRY(prepare_assembly(c, prec, sched));
-  const bool held = c->hold_tc && region_schedule(c, prec, sched);   // one direct launch
+  const bool held = c->hold_tc && region_schedule(c, prec, sched) && prec != OFM_PREC_FP64 &&
+                    prec != OFM_PREC_FP32;   // one direct launch
   if (c->asm_exec[prec] && c->asm_sched[prec] != sched) {
     cudaGraphExecDestroy(c->asm_exec[prec]);
     c->asm_exec[prec] = nullptr;
@@ -694,7 +697,7 @@ extern "C" ofm_status ofm_assemble_HS(ofm_ctx* c, ofm_precision prec, const ofm_
       }
       c->stencil_check = !region_schedule(c, prec, sched);
       if (c->asm_tc[prec]) c->tc_check = true;
-      if (prec != OFM_PREC_FP64 && prec != OFM_PREC_FP32) c->last_schedule = region_schedule(c, prec, sched) ? 2 : 1;
+      c->last_schedule = region_schedule(c, prec, sched) ? 2 : 1;
       c->assembled = true;
       return OFM_OK;
     }
@@ -861,6 +864,8 @@ extern "C" ofm_status ofm_get_plan_info(ofm_ctx* c, ofm_plan_info* info) {
   info->state_bytes = c->state_elems * (long long)elem_size(c);
   info->hphi_bytes = c->state_elems * (long long)elem_size(c);
   info->apply_points = c->apply_points;
+  info->last_schedule = c->last_schedule;
+  info->pad_ = 0;
   return OFM_OK;
 }
 

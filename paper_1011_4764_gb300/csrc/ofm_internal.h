@@ -237,7 +237,7 @@ struct ofm_ctx {
   bool region_stale = true;
   int region_wmin = 1;
   int schedule = 0;                 // the tuned or caller-set default schedule
-  int last_schedule = 0;            // schedule of the last tensor-core assembly (1 or 2)
+  int last_schedule = 0;            // schedule of the last assembly (1 pair, 2 region)
   bool hphi_ready = false;          // the FP32/FP64 H phi buffer is allocated
   // failure injection: host-side (OFM_FAULT at ofm_create; never touches the
   // device) and the test hook that makes one bounded device wait run out
@@ -245,8 +245,8 @@ struct ofm_ctx {
   bool fault_due = false;           // an injected timeout waits for the next status read
   int hold_tc = 0, hold_tri = 0;    // armed for the next launch
   int hold_bound = 0;               // polls before the held wait gives up (0: usual bound)
-  double pack_bytes[3] = {0, 0, 0};     // algorithmic bytes of the apply + pack, per kind
-  double region_bytes[3] = {0, 0, 0};   // algorithmic bytes of the region contraction, per kind
+  double pack_bytes[5] = {0, 0, 0, 0, 0};     // algorithmic bytes of the apply + pack, per kind
+  double region_bytes[5] = {0, 0, 0, 0, 0};   // algorithmic bytes of the region contraction, per kind
 };
 
 // words of the context's 16-int flag buffer: 0 pivot flag and 2..3 window
@@ -294,7 +294,7 @@ ofm_status ofm_region_plan(ofm_ctx* c);
 bool ofm_region_ok(const ofm_ctx* c);
 bool ofm_region_default(const ofm_ctx* c);   // the plan applies and is not mostly padding
 const char* ofm_region_why(const ofm_ctx* c);
-ofm_status ofm_region_prepare(ofm_ctx* c);   // device tables and buffers of the plan
+ofm_status ofm_region_prepare(ofm_ctx* c, ofm_precision prec);   // device tables and buffers
 ofm_status ofm_region_run(ofm_ctx* c, ofm_precision prec);
 void ofm_region_free(ofm_ctx* c);
 void ofm_region_stats(const ofm_ctx* c, long long* out);       // OFM_ERR_TIMEOUT if a bounded wait gave up

@@ -31,10 +31,15 @@
 //                    (pair, region part) it covers;
 //   rfinalize_kernel a5: FP64 sum of each pair's slots in region order,
 //                    symmetrised diagonal blocks.
+// The plain forms on the CUDA cores (FP32 and FP64 arithmetic) take the same
+// plan: the pack writes FP32 or FP64 operand planes in the same layout (all
+// byte offsets doubled for FP64), region_simt_kernel forms the same tiles
+// with register-tiled FMAs, and the FP64 form keeps FP64 partial slots.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -99,8 +104,9 @@ struct RPair {
   long long blk_off;  // [H_ab | S_ab] in the block arena
 };
 
-// operand kinds of the region path (same numbering as the pair path)
-enum { RK_TF32 = 0, RK_BF16 = 1, RK_BF16X3 = 2 };
+// operand kinds of the region path (the tensor-core ones numbered as in the
+// pair path); RK_F32 and RK_F64 are the plain forms on the CUDA cores
+enum { RK_TF32 = 0, RK_BF16 = 1, RK_BF16X3 = 2, RK_F32 = 3, RK_F64 = 4 };
 
 constexpr int RS_THREADS = 192;    // warp 0 copies, 1 MMA, 2-5 epilogue
 constexpr int RS_NSTAGE = 4;
@@ -125,6 +131,15 @@ template <> struct KindT<RK_BF16> {
 template <> struct KindT<RK_BF16X3> {
   static constexpr int esz = 2, KC = 32, CPT = 2, NPL = 2, SC = 1, FMT = 1;
 };
+// plain forms: a chunk is 16 points (64 bytes a row in FP32, 128 in FP64)
+template <> struct KindT<RK_F32> {
+  static constexpr int esz = 4, KC = 16, CPT = 4;
+};
+template <> struct KindT<RK_F64> {
+  static constexpr int esz = 8, KC = 16, CPT = 4;
+};
+// byte scale of a kind's plane layout against the plan's offsets (FP64: 2)
+__host__ __device__ constexpr int kind_scale(int k) { return k == RK_F64 ? 2 : 1; }
 
 __device__ __forceinline__ uint64_t rdesc(uint32_t saddr) {
   // K-major, no swizzle: K-adjacent core matrices 128 bytes apart (LBO),
@@ -207,11 +222,18 @@ template <int KIND>
 __global__ void __launch_bounds__(PK_THREADS) pack_kernel(
     const RUnit* __restrict__ units, const int4* __restrict__ cta, const DevFrag* __restrict__ fr,
     const float* __restrict__ V, const float* __restrict__ states, unsigned char* __restrict__ planes,
-    int gx, int gy, int gz, float c0, float c1) {
+    int gx, int gy, int gz, double c0d, double c1d) {
   using KT = KindT<KIND>;
   constexpr int ESZ = KT::esz;
-  constexpr int KPU = 16 / ESZ;   // points per 16-byte unit
-  extern __shared__ __align__(16) float pk_smem[];
+  constexpr int KPU = 16 / ESZ;            // points per 16-byte unit
+  constexpr int NCORE = KT::KC / KPU;      // 16-byte core columns per chunk
+  constexpr int SCL = kind_scale(KIND);
+  // the staged values: FP64 for the FP64 form (H phi formed in FP64 from the
+  // FP32 states and potential), FP32 otherwise
+  using ST = typename std::conditional<KIND == RK_F64, double, float>::type;
+  const ST c0 = (ST)c0d, c1 = (ST)c1d;
+  extern __shared__ __align__(16) unsigned char pk_raw[];
+  ST* pk_smem = reinterpret_cast<ST*>(pk_raw);
   __shared__ RUnit U;
   __shared__ DevFrag F;
   __shared__ int s_p[64], s_nb[64][6];
@@ -223,18 +245,19 @@ __global__ void __launch_bounds__(PK_THREADS) pack_kernel(
   if (tid == 0) F = fr[U.frag];
   __syncthreads();
   const int rows = (F.n + 7) / 8 * 8;
-  const int RS = rows + (ESZ == 4 ? 2 : 1);   // shared row stride (words)
-  float* sPh = pk_smem;
-  float* sHp = pk_smem + 64 * RS;
+  const int RS = rows + (ESZ == 4 ? 2 : 1);   // shared row stride (elements)
+  ST* sPh = pk_smem;
+  ST* sHp = pk_smem + 64 * RS;
   const float4* S4 = reinterpret_cast<const float4*>(states + F.off);
   const int qpp = F.ld / 4;
   const int nq = rows / 4;
   const int npl = U.L[0] * U.L[1];
-  const long long cb = (long long)rows * 64;
+  const long long cb = (long long)rows * 64 * SCL;
   const long long npl2 = (long long)U.ntiles * 128 * rows;   // one 2-byte plane
-  const int upc = rows * 4;                                  // units per chunk and plane
+  const long long half = 2 * npl2 * SCL;                     // phi planes -> H phi planes
+  const int upc = rows * NCORE;                              // units per chunk and plane
   const int nunit = 2 * KT::CPT * upc;
-  unsigned char* blk = planes + U.base;
+  unsigned char* blk = planes + U.base * SCL;
   for (int t = job.y; t < job.y + job.z; ++t) {
     if (t > job.y) __syncthreads();   // the previous tile's shared data is consumed
     if (tid < 64) {
@@ -277,32 +300,29 @@ __global__ void __launch_bounds__(PK_THREADS) pack_kernel(
     for (int it = tid; it < 64 * nq; it += PK_THREADS) {
       const int k = it / nq, q = it - k * nq;
       const int p = s_p[k];
-      float4 ph = make_float4(0.f, 0.f, 0.f, 0.f), hp = ph;
+      ST pv[4] = {0, 0, 0, 0}, hv[4] = {0, 0, 0, 0};
       if (p >= 0 && q < qpp) {
-        ph = S4[(long long)p * qpp + q];
-        float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 ph = S4[(long long)p * qpp + q];
+        ST sum[4] = {0, 0, 0, 0};
 #pragma unroll
         for (int j = 0; j < 6; ++j) {
           const int nb = s_nb[k][j];
           if (nb >= 0) {
             const float4 w = S4[(long long)nb * qpp + q];
-            sum.x += w.x; sum.y += w.y; sum.z += w.z; sum.w += w.w;
+            sum[0] += (ST)w.x; sum[1] += (ST)w.y; sum[2] += (ST)w.z; sum[3] += (ST)w.w;
           }
         }
-        const float dv = c0 + s_v[k];
-        hp.x = fmaf(-c1, sum.x, dv * ph.x);
-        hp.y = fmaf(-c1, sum.y, dv * ph.y);
-        hp.z = fmaf(-c1, sum.z, dv * ph.z);
-        hp.w = fmaf(-c1, sum.w, dv * ph.w);
+        const ST dv = c0 + (ST)s_v[k];
+        pv[0] = ph.x; pv[1] = ph.y; pv[2] = ph.z; pv[3] = ph.w;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) hv[i] = fma(-c1, sum[i], dv * pv[i]);
       }
-      const float pv[4] = {ph.x, ph.y, ph.z, ph.w};
-      const float hv[4] = {hp.x, hp.y, hp.z, hp.w};
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const int row = 4 * q + i;
         const bool ok = row < F.n;
-        sPh[k * RS + row] = ok ? pv[i] : 0.f;
-        sHp[k * RS + row] = ok ? hv[i] : 0.f;
+        sPh[k * RS + row] = ok ? pv[i] : (ST)0;
+        sHp[k * RS + row] = ok ? hv[i] : (ST)0;
       }
     }
     __syncthreads();
@@ -314,17 +334,21 @@ __global__ void __launch_bounds__(PK_THREADS) pack_kernel(
       int u = w - A * (KT::CPT * upc);
       const int cc = u / upc;
       u -= cc * upc;
-      const int r = u & 7, kc = (u >> 3) & 3, g = u >> 5;
+      const int r = u & 7, kc = (u >> 3) % NCORE, g = u / (8 * NCORE);
       const int row = 8 * g + r;
       const int k0 = cc * KT::KC + kc * KPU;
-      const float* src = (A ? sHp : sPh) + k0 * RS + row;
-      float x[KPU];
+      const ST* src = (A ? sHp : sPh) + k0 * RS + row;
+      ST x[KPU];
 #pragma unroll
       for (int j = 0; j < KPU; ++j) x[j] = src[j * RS];
-      const long long off = (long long)(t * KT::CPT + cc) * cb + g * 512 + kc * 128 + r * 16;
+      const long long off = (long long)(t * KT::CPT + cc) * cb + g * (NCORE * 128) + kc * 128 + r * 16;
       if constexpr (KIND == RK_TF32) {
         const uint4 v = make_uint4(rtf32(x[0]), rtf32(x[1]), rtf32(x[2]), rtf32(x[3]));
-        *reinterpret_cast<uint4*>(blk + A * 2 * npl2 + off) = v;
+        *reinterpret_cast<uint4*>(blk + A * half + off) = v;
+      } else if constexpr (KIND == RK_F32) {
+        *reinterpret_cast<float4*>(blk + A * half + off) = make_float4(x[0], x[1], x[2], x[3]);
+      } else if constexpr (KIND == RK_F64) {
+        *reinterpret_cast<double2*>(blk + A * half + off) = make_double2(x[0], x[1]);
       } else {
         uint32_t hw[4], lw[4];
 #pragma unroll
@@ -337,9 +361,9 @@ __global__ void __launch_bounds__(PK_THREADS) pack_kernel(
             lw[j] = *reinterpret_cast<const uint32_t*>(&l2);
           }
         }
-        *reinterpret_cast<uint4*>(blk + A * 2 * npl2 + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        *reinterpret_cast<uint4*>(blk + A * half + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
         if constexpr (KIND == RK_BF16X3)
-          *reinterpret_cast<uint4*>(blk + A * 2 * npl2 + npl2 + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+          *reinterpret_cast<uint4*>(blk + A * half + npl2 + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
       }
     }
   }   // tiles
@@ -624,6 +648,231 @@ __global__ void __launch_bounds__(RS_THREADS, 1) region_kernel(
                  : "memory");
 }
 
+
+// ------------------------------------------- a3/a4: plain, CUDA cores ----
+
+// The same items, pieces and slots as region_kernel, on the CUDA cores in
+// FP32 or FP64 arithmetic: the plain forms the tensor-core precisions are
+// measured against.  A persistent CTA takes items from the global counter;
+// per item and pass of NP columns it streams the 16-point K chunks of the A
+// pieces (128 stacked state rows) and of the B pieces clipped to the pass
+// into a ring of shared-memory stages with 16-byte asynchronous copies, and
+// each thread accumulates an 8-row x TN-column register tile.  Thread
+// (tr, tc) takes rows 8 (2i + tr/8) + tr%8 and columns 8 (2j + tc/8) + tc%8,
+// so the eight lanes of a quarter warp read one 16-byte unit of A (a
+// broadcast) and eight adjacent units of B (no bank conflict).  Each output
+// is a sum in K order with one FMA per point; the FP32 form stores FP32
+// partial slots (finalized like the tensor-core ones), the FP64 form FP64
+// slots.
+constexpr int SR_THREADS = 256;
+constexpr int SR_NSTAGE = 3;
+
+template <typename T> struct SimtT;
+template <> struct SimtT<float> {
+  static constexpr int S = 1, NP = 256, TN = 16, NCORE = 4;
+  using V = float4;
+};
+template <> struct SimtT<double> {
+  static constexpr int S = 2, NP = 128, TN = 8, NCORE = 8;
+  using V = double2;
+};
+template <typename T>
+constexpr int simt_smem() {
+  return SR_NSTAGE * (16 + SimtT<T>::NP / 8) * 512 * SimtT<T>::S;
+}
+
+__device__ __forceinline__ void cpa16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst),
+               "l"((unsigned long long)__cvta_generic_to_global(src))
+               : "memory");
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cpa_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ void fma_unit(float& acc, const float4& a, const float4& b) {
+  acc = fmaf(a.x, b.x, acc);
+  acc = fmaf(a.y, b.y, acc);
+  acc = fmaf(a.z, b.z, acc);
+  acc = fmaf(a.w, b.w, acc);
+}
+__device__ __forceinline__ void fma_unit(double& acc, const double2& a, const double2& b) {
+  acc = fma(a.x, b.x, acc);
+  acc = fma(a.y, b.y, acc);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(SR_THREADS, 1) region_simt_kernel(
+    const RItem* __restrict__ items, int nitems, const RPiece* __restrict__ pieces,
+    const RRowSeg* __restrict__ rsegs, const RColSeg* __restrict__ csegs,
+    const long long* __restrict__ stab, const unsigned char* __restrict__ planes,
+    T* __restrict__ slots, int* next) {
+  using C = SimtT<T>;
+  using V = typename C::V;
+  constexpr int G = 512 * C::S;   // bytes of one 8-row group of a chunk
+  constexpr int ABYTES = 16 * G, STAGE = ABYTES + (C::NP / 8) * G;
+  constexpr int HT = C::TN / 2;
+  extern __shared__ __align__(16) unsigned char ssm[];
+  __shared__ long long s_src[64], s_cb[64];
+  __shared__ int s_bytes[64], s_dst[64];
+  __shared__ int s_rrs[128], s_ri[128];
+  __shared__ int s_ccf[C::NP], s_cpart[C::NP], s_cj[C::NP], s_cnb[C::NP];
+  __shared__ int s_item, s_npc, s_aend;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tc = lane & 15, tr = (lane >> 4) + 2 * warp;
+  for (;;) {
+    __syncthreads();   // the previous item's tables and stages are consumed
+    if (tid == 0) s_item = atomicAdd(next, 1);
+    __syncthreads();
+    const int ii = s_item;
+    if (ii >= nitems) break;
+    const RItem it = items[ii];
+    for (int r = tid; r < 128; r += SR_THREADS) {
+      int rs = -1, i = 0;
+      for (int q = 0; q < it.nrs; ++q) {
+        const RRowSeg g = rsegs[it.rs0 + q];
+        if (r >= g.r0 && r < g.r0 + g.nr) {
+          i = g.i0 + r - g.r0;
+          rs = i < g.na ? q : -1;
+        }
+      }
+      s_rrs[r] = rs;
+      s_ri[r] = i;
+    }
+    const int nch = it.ntiles * 4;   // 16-point chunks of the part
+    for (int c0 = 0; c0 < it.n_cols; c0 += C::NP) {
+      const int ncp = min(C::NP, it.n_cols - c0);
+      if (c0 > 0) __syncthreads();   // the previous pass's tables and stages are consumed
+      for (int ci = tid; ci < C::NP; ci += SR_THREADS) {
+        int cf = -1, part = 0, j = 0, nb = 0;
+        const int col = c0 + ci;
+        if (ci < ncp)
+          for (int q = 0; q < it.ncs; ++q) {
+            const RColSeg g = csegs[it.cs0 + q];
+            if (col >= g.c0 && col < g.c0 + g.nc) {
+              j = g.j0 + col - g.c0;
+              cf = j < g.nb ? g.cf : -1;
+              part = g.part;
+              nb = g.nb;
+            }
+          }
+        s_ccf[ci] = cf;
+        s_cpart[ci] = part;
+        s_cj[ci] = j;
+        s_cnb[ci] = nb;
+      }
+      if (tid == 0) {
+        // A pieces whole; B pieces clipped to the pass's column groups
+        // (plan offsets are those of 4-byte operands: 512 bytes per group)
+        int n = 0, aend = 0;
+        for (int q = 0; q < it.npa; ++q) {
+          const RPiece pc = pieces[it.pa0 + q];
+          s_src[n] = pc.base * C::S;
+          s_cb[n] = (long long)pc.cb * C::S;
+          s_bytes[n] = pc.bytes * C::S;
+          s_dst[n] = pc.dst * C::S;
+          aend = max(aend, (pc.dst + pc.bytes) * C::S);
+          ++n;
+        }
+        for (int q = 0; q < it.npb; ++q) {
+          const RPiece pc = pieces[it.pb0 + q];
+          const int g0 = pc.dst / 512, ng = pc.bytes / 512;
+          const int lo = max(g0, c0 / 8), hi = min(g0 + ng, (c0 + C::NP) / 8);
+          if (hi <= lo) continue;
+          s_src[n] = (pc.base + (long long)(lo - g0) * 512) * C::S;
+          s_cb[n] = (long long)pc.cb * C::S;
+          s_bytes[n] = (hi - lo) * G;
+          s_dst[n] = ABYTES + (lo - c0 / 8) * G;
+          ++n;
+        }
+        s_npc = n;
+        s_aend = aend;
+      }
+      __syncthreads();
+      // rows and columns no piece covers read zeros
+      {
+        const int aend = s_aend, bend = ABYTES + (ncp / 8) * G;
+        for (int st = 0; st < SR_NSTAGE; ++st) {
+          unsigned char* b = ssm + (size_t)st * STAGE;
+          for (int o = aend + 16 * tid; o < ABYTES; o += 16 * SR_THREADS)
+            *reinterpret_cast<uint4*>(b + o) = make_uint4(0, 0, 0, 0);
+          for (int o = bend + 16 * tid; o < STAGE; o += 16 * SR_THREADS)
+            *reinterpret_cast<uint4*>(b + o) = make_uint4(0, 0, 0, 0);
+        }
+      }
+      const int npc = s_npc;
+      auto issue = [&](int ch) {
+        if (ch < nch) {
+          unsigned char* st = ssm + (size_t)(ch % SR_NSTAGE) * STAGE;
+          const long long cg = (long long)it.tile0 * 4 + ch;   // chunk index in the unit
+          for (int q = 0; q < npc; ++q) {
+            const unsigned char* src = planes + s_src[q] + cg * s_cb[q];
+            const int nu = s_bytes[q] >> 4;
+            const uint32_t dst = smem_u32(st + s_dst[q]);
+            for (int u = tid; u < nu; u += SR_THREADS) cpa16(dst + 16 * u, src + 16 * u);
+          }
+        }
+        cpa_commit();
+      };
+      T acc[8][C::TN];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < C::TN; ++j) acc[i][j] = (T)0;
+#pragma unroll
+      for (int ch = 0; ch < SR_NSTAGE - 1; ++ch) issue(ch);
+      for (int ch = 0; ch < nch; ++ch) {
+        issue(ch + SR_NSTAGE - 1);   // into the stage consumed in the previous iteration
+        cpa_wait<SR_NSTAGE - 1>();
+        __syncthreads();
+        const unsigned char* As = ssm + (size_t)(ch % SR_NSTAGE) * STAGE;
+        const unsigned char* Bs = As + ABYTES;
+#pragma unroll
+        for (int kc = 0; kc < C::NCORE; ++kc) {
+          V a[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+            a[i] = *reinterpret_cast<const V*>(As + (2 * i + (tr >> 3)) * G + kc * 128 + (tr & 7) * 16);
+#pragma unroll
+          for (int jh = 0; jh < 2; ++jh) {
+            V b[HT];
+#pragma unroll
+            for (int j = 0; j < HT; ++j)
+              b[j] = *reinterpret_cast<const V*>(Bs + (2 * (jh * HT + j) + (tc >> 3)) * G + kc * 128 +
+                                                 (tc & 7) * 16);
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+              for (int j = 0; j < HT; ++j) fma_unit(acc[i][jh * HT + j], a[i], b[j]);
+          }
+        }
+        __syncthreads();
+      }
+      cpa_wait<0>();
+      // epilogue: each valid (row, column) into its pair's slot
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int row = 8 * (2 * i + (tr >> 3)) + (tr & 7);
+        const int rs = s_rrs[row];
+        if (rs < 0) continue;
+        const int si = s_ri[row];
+#pragma unroll
+        for (int j = 0; j < C::TN; ++j) {
+          const int ci = 8 * (2 * j + (tc >> 3)) + (tc & 7);
+          const int cf = s_ccf[ci];
+          if (cf < 0) continue;
+          const long long slot = stab[it.st0 + (long long)rs * it.ncf + cf];
+          if (slot < 0) continue;
+          const int nb = s_cnb[ci];
+          slots[slot + (long long)si * 2 * nb + s_cpart[ci] * nb + s_cj[ci]] = acc[i][j];
+        }
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------ a5: blocks ---
 
 // Pair p = blockIdx.x: S_ab and H_ab as sums of its slots in region order
@@ -684,8 +933,28 @@ __device__ __forceinline__ void tile_sums(const float* __restrict__ base, long l
   }
 }
 
+// FP64 slots (the FP64 plain form): plain FP64 sums in region order.
+__device__ __forceinline__ void tile_sums(const double* __restrict__ base, long long ss, int nslot,
+                                          int nb, int r0, int c0, int nr, int nc, int ty, int tx,
+                                          double S[4], double H[4]) {
+#pragma unroll
+  for (int r = 0; r < 4; ++r) S[r] = H[r] = 0.0;
+  const int c = c0 + tx;
+  for (int k = 0; k < nslot; ++k)
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int i = r0 + ty + 8 * r;
+      if (i < r0 + nr && c < c0 + nc) {
+        const double* p = base + (long long)k * ss + (long long)i * 2 * nb + c;
+        S[r] += p[0];
+        H[r] += p[nb];
+      }
+    }
+}
+
+template <typename T>
 __global__ void __launch_bounds__(256) rfinalize_kernel(const RPair* __restrict__ prs,
-                                                        const float* __restrict__ slots,
+                                                        const T* __restrict__ slots,
                                                         double* __restrict__ blocks) {
   __shared__ double tS[32][33], tH[32][33];
   const RPair pr = prs[blockIdx.x];
@@ -697,7 +966,7 @@ __global__ void __launch_bounds__(256) rfinalize_kernel(const RPair* __restrict_
   const int nr = min(32, na - r0), nc = min(32, nb - c0);
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const long long ss = (long long)na * 2 * nb;
-  const float* base = slots + pr.slot0;
+  const T* base = slots + pr.slot0;
   double S[4], H[4];
   tile_sums(base, ss, pr.nslot, nb, r0, c0, nr, nc, ty, tx, S, H);
   if (pr.a == pr.b) {
@@ -1144,9 +1413,15 @@ const char* ofm_region_why(const ofm_ctx* c) {
   return c->region ? c->region->why.c_str() : "no region plan";
 }
 
-ofm_status ofm_region_prepare(ofm_ctx* c) {
+ofm_status ofm_region_prepare(ofm_ctx* c, ofm_precision prec) {
   RegionPlan* P = c->region;
-  if (P->uploaded) return OFM_OK;
+  // the FP64 plain form doubles the planes and keeps FP64 slots
+  const int scl = prec == OFM_PREC_FP64 ? 2 : 1;
+  if (P->uploaded) {
+    OFM_TRY(ofm_ensure_big(c, P->planes, (size_t)P->plane_bytes * scl, "operand planes"));
+    return ofm_ensure_big(c, P->slots, 4 * scl * (size_t)std::max<long long>(1, P->slot_elems),
+                          "partial slots");
+  }
   OFM_TRY(upload(c, P->d_units, P->units, "region units"));
   OFM_TRY(upload(c, P->d_pcta, P->pack_cta, "pack launch table"));
   OFM_TRY(upload(c, P->d_items, P->items, "region items"));
@@ -1155,8 +1430,8 @@ ofm_status ofm_region_prepare(ofm_ctx* c) {
   OFM_TRY(upload(c, P->d_csegs, P->csegs, "region column segments"));
   OFM_TRY(upload(c, P->d_stab, P->stab, "region slot table"));
   OFM_TRY(upload(c, P->d_rpairs, P->rpairs, "region pairs"));
-  OFM_TRY(ofm_ensure_big(c, P->planes, (size_t)P->plane_bytes, "operand planes"));
-  OFM_TRY(ofm_ensure_big(c, P->slots, sizeof(float) * (size_t)std::max<long long>(1, P->slot_elems),
+  OFM_TRY(ofm_ensure_big(c, P->planes, (size_t)P->plane_bytes * scl, "operand planes"));
+  OFM_TRY(ofm_ensure_big(c, P->slots, 4 * scl * (size_t)std::max<long long>(1, P->slot_elems),
                          "partial slots"));
   static bool attr = false;
   if (!attr) {
@@ -1167,6 +1442,12 @@ ofm_status ofm_region_prepare(ofm_ctx* c) {
     cudaFuncSetAttribute(pack_kernel<RK_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, pk);
     cudaFuncSetAttribute(pack_kernel<RK_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, pk);
     cudaFuncSetAttribute(pack_kernel<RK_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, pk);
+    cudaFuncSetAttribute(pack_kernel<RK_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, pk);
+    cudaFuncSetAttribute(pack_kernel<RK_F64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * pk);
+    cudaFuncSetAttribute(region_simt_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         simt_smem<float>());
+    cudaFuncSetAttribute(region_simt_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         simt_smem<double>());
     OFM_CUDA(c, cudaGetLastError());
     attr = true;
   }
@@ -1175,15 +1456,20 @@ ofm_status ofm_region_prepare(ofm_ctx* c) {
 }
 
 // a1 (apply + pack), a3/a4 (region contraction) and a5 (blocks) for one
-// tensor-core precision, enqueued on the context stream.
+// precision, enqueued on the context stream.
 ofm_status ofm_region_run(ofm_ctx* c, ofm_precision prec) {
   RegionPlan* P = c->region;
   if (!P || !P->ok) return ofm_fail(c, OFM_ERR_INVALID, P ? P->why : "no region plan");
   if (!P->uploaded) return ofm_fail(c, OFM_ERR_STATE, "region plan not prepared");
-  const int kind = prec == OFM_PREC_TF32 ? RK_TF32 : prec == OFM_PREC_BF16 ? RK_BF16 : RK_BF16X3;
+  const int kind = prec == OFM_PREC_TF32   ? RK_TF32
+                   : prec == OFM_PREC_BF16 ? RK_BF16
+                   : prec == OFM_PREC_FP32 ? RK_F32
+                   : prec == OFM_PREC_FP64 ? RK_F64
+                                           : RK_BF16X3;
+  const bool f64 = kind == RK_F64;
 
   const double h = c->grid.h;
-  const float c0 = (float)(3.0 / (h * h)), c1 = (float)(0.5 / (h * h));
+  const double c0 = 3.0 / (h * h), c1 = 0.5 / (h * h);
   {
     KTimer t(c, KC_APPLY, 1, c->pack_bytes[kind]);
     const RUnit* u = (const RUnit*)P->d_units.p;
@@ -1193,7 +1479,7 @@ ofm_status ofm_region_run(ofm_ctx* c, ofm_precision prec) {
     unsigned char* pl = (unsigned char*)P->planes.p;
     int maxrows = 8;
     for (const DevFrag& fq : c->frags) maxrows = std::max(maxrows, (fq.n + 7) / 8 * 8);
-    const int sm = 2 * 64 * (maxrows + 2) * 4;
+    const int sm = 2 * 64 * (maxrows + 2) * (f64 ? 8 : 4);
     const int4* cta = (const int4*)P->d_pcta.p;
     const unsigned grid = (unsigned)P->pack_cta.size();
     if (grid > 0) {
@@ -1201,6 +1487,10 @@ ofm_status ofm_region_run(ofm_ctx* c, ofm_precision prec) {
         pack_kernel<RK_TF32><<<grid, PK_THREADS, sm, c->stream>>>(u, cta, f, V, st, pl, c->grid.n[0], c->grid.n[1], c->grid.n[2], c0, c1);
       else if (kind == RK_BF16)
         pack_kernel<RK_BF16><<<grid, PK_THREADS, sm, c->stream>>>(u, cta, f, V, st, pl, c->grid.n[0], c->grid.n[1], c->grid.n[2], c0, c1);
+      else if (kind == RK_F32)
+        pack_kernel<RK_F32><<<grid, PK_THREADS, sm, c->stream>>>(u, cta, f, V, st, pl, c->grid.n[0], c->grid.n[1], c->grid.n[2], c0, c1);
+      else if (kind == RK_F64)
+        pack_kernel<RK_F64><<<grid, PK_THREADS, sm, c->stream>>>(u, cta, f, V, st, pl, c->grid.n[0], c->grid.n[1], c->grid.n[2], c0, c1);
       else
         pack_kernel<RK_BF16X3><<<grid, PK_THREADS, sm, c->stream>>>(u, cta, f, V, st, pl, c->grid.n[0], c->grid.n[1], c->grid.n[2], c0, c1);
     }
@@ -1221,32 +1511,44 @@ ofm_status ofm_region_run(ofm_ctx* c, ofm_precision prec) {
       const long long* sb = (const long long*)P->d_stab.p;
       const unsigned char* pl = (const unsigned char*)P->planes.p;
       float* sl = (float*)P->slots.p;
-      const int hold = c->hold_tc;   // armed by the test hook for one launch
-      const int wi = hold && c->hold_bound > 0 ? c->hold_bound : (1 << 20);
-      c->hold_tc = 0;
-      if (kind == RK_TF32)
-        region_kernel<RK_TF32><<<grid, RS_THREADS, RS_SMEM, c->stream>>>(it, ni, pc, rs, cs, sb, pl, sl, fl, next, hold, wi);
-      else if (kind == RK_BF16)
-        region_kernel<RK_BF16><<<grid, RS_THREADS, RS_SMEM, c->stream>>>(it, ni, pc, rs, cs, sb, pl, sl, fl, next, hold, wi);
-      else
-        region_kernel<RK_BF16X3><<<grid, RS_THREADS, RS_SMEM, c->stream>>>(it, ni, pc, rs, cs, sb, pl, sl, fl, next, hold, wi);
+      if (kind == RK_F32) {
+        region_simt_kernel<float><<<grid, SR_THREADS, simt_smem<float>(), c->stream>>>(
+            it, ni, pc, rs, cs, sb, pl, sl, next);
+      } else if (kind == RK_F64) {
+        region_simt_kernel<double><<<grid, SR_THREADS, simt_smem<double>(), c->stream>>>(
+            it, ni, pc, rs, cs, sb, pl, (double*)P->slots.p, next);
+      } else {
+        const int hold = c->hold_tc;   // armed by the test hook for one launch
+        const int wi = hold && c->hold_bound > 0 ? c->hold_bound : (1 << 20);
+        c->hold_tc = 0;
+        if (kind == RK_TF32)
+          region_kernel<RK_TF32><<<grid, RS_THREADS, RS_SMEM, c->stream>>>(it, ni, pc, rs, cs, sb, pl, sl, fl, next, hold, wi);
+        else if (kind == RK_BF16)
+          region_kernel<RK_BF16><<<grid, RS_THREADS, RS_SMEM, c->stream>>>(it, ni, pc, rs, cs, sb, pl, sl, fl, next, hold, wi);
+        else
+          region_kernel<RK_BF16X3><<<grid, RS_THREADS, RS_SMEM, c->stream>>>(it, ni, pc, rs, cs, sb, pl, sl, fl, next, hold, wi);
+      }
     }
     OFM_CUDA(c, cudaGetLastError());
   }
   {
-    KTimer t(c, KC_FINALIZE, 1, (double)P->slot_elems * 4 + 16.0 * c->blk_elems);
+    KTimer t(c, KC_FINALIZE, 1, (double)P->slot_elems * (f64 ? 8 : 4) + 16.0 * c->blk_elems);
     int nmax = 1, amax = 1;
     for (const RPair& q : P->rpairs) {
       nmax = std::max(nmax, q.nb);
       amax = std::max(amax, q.na);
     }
     const int chunks = ((amax + 31) / 32) * ((nmax + 31) / 32);   // 32 x 32 tiles of the largest block
-    if (!P->rpairs.empty())
-      rfinalize_kernel<<<dim3((unsigned)P->rpairs.size(), (unsigned)chunks), 256, 0, c->stream>>>(
-          (const RPair*)P->d_rpairs.p, (const float*)P->slots.p, (double*)c->blocks.p);
+    const dim3 fg((unsigned)P->rpairs.size(), (unsigned)chunks);
+    if (!P->rpairs.empty() && f64)
+      rfinalize_kernel<double><<<fg, 256, 0, c->stream>>>((const RPair*)P->d_rpairs.p,
+                                                          (const double*)P->slots.p, (double*)c->blocks.p);
+    else if (!P->rpairs.empty())
+      rfinalize_kernel<float><<<fg, 256, 0, c->stream>>>((const RPair*)P->d_rpairs.p,
+                                                         (const float*)P->slots.p, (double*)c->blocks.p);
     OFM_CUDA(c, cudaGetLastError());
   }
-  c->tc_check = true;
+  c->tc_check = kind <= RK_BF16X3;
   return OFM_OK;
 }
 

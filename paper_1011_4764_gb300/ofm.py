@@ -67,7 +67,7 @@ class ofm_plan_info(C.Structure):
                 ("n_work_items", C.c_int), ("pair_flops", C.c_longlong),
                 ("overlap_points_s", C.c_longlong), ("overlap_points_h", C.c_longlong),
                 ("state_bytes", C.c_longlong), ("hphi_bytes", C.c_longlong),
-                ("apply_points", C.c_longlong)]
+                ("apply_points", C.c_longlong), ("last_schedule", C.c_int), ("pad_", C.c_int)]
 
 
 class ofm_kernel_stat(C.Structure):
@@ -351,8 +351,9 @@ class Context:
 
     # -- ofm_assemble_HS
     def assemble(self, precision="fp32", chunk_points=0, use_graph=True, schedule="auto"):
-        """schedule (tensor-core precisions): "auto" (the context's choice),
-        "pair" (one GEMM per pair) or "region" (coverage regions stacked)."""
+        """schedule: "auto" (the context's choice; for FP32 / FP64 the plan's
+        default), "pair" (one GEMM per pair) or "region" (coverage regions
+        stacked); FP32 and FP64 run either on the CUDA cores."""
         o = ofm_assemble_opts(chunk_points, 1 if use_graph else 0, SCHEDULE[schedule])
         self._check(self.lib.ofm_assemble_HS(self.h, PREC[precision], C.byref(o)))
 
@@ -452,6 +453,10 @@ class Context:
         info = ofm_plan_info()
         self._check(self.lib.ofm_get_plan_info(self.h, C.byref(info)))
         return {k: getattr(info, k) for k, _ in ofm_plan_info._fields_}
+
+    def last_schedule(self):
+        """Schedule of the last assembly: "pair", "region" or None."""
+        return {1: "pair", 2: "region"}.get(self.plan_info()["last_schedule"])
 
     def block(self, a, b):
         na, nb = self.frags[a].n_states, self.frags[b].n_states
