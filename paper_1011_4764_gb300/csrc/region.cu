@@ -207,14 +207,14 @@ __device__ __forceinline__ uint32_t rtf32(float x) {
 //   1. Threads take (point k, 4-state group q) items with q fastest, so a
 //      warp's loads of phi and of each neighbour are contiguous runs of the
 //      point-major FP32 storage (zero outside the dilated storage box; a
-//      full-span dimension wraps), and form
+//      full-span dimension wraps), two items (14 loads) at a time, and form
 //          H phi = (3/h^2 + V) phi - (1/(2h^2)) sum_neighbours phi;
-//      phi and H phi go to shared memory as [k][state] FP32 rows with an odd
-//      row stride.
-//   2. Each thread writes 16-byte units of the operand planes in the
-//      canonical layout (memory order, coalesced): 8 (BF16) or 4 (TF32)
-//      consecutive points of one state, read down a column of the shared
-//      rows, rounded to TF32, BF16, or split into BF16 hi and lo.
+//      phi and H phi go to shared memory as [k][state] rows.
+//   2. Each thread writes 16-byte units of one (array, K chunk) of the
+//      operand planes in the canonical layout (memory order, coalesced):
+//      8 (BF16), 4 (TF32, FP32) or 2 (FP64) consecutive points of one
+//      state, read down a column of the shared rows, rounded to TF32, BF16,
+//      or split into BF16 hi and lo.
 // Points of the region outside the fragment's dilated box, the plane and
 // tile padding and the state rows beyond n (up to the multiple of 8) are
 // zeros.
@@ -245,7 +245,14 @@ __global__ void __launch_bounds__(PK_THREADS) pack_kernel(
   if (tid == 0) F = fr[U.frag];
   __syncthreads();
   const int rows = (F.n + 7) / 8 * 8;
-  const int RS = rows + (ESZ == 4 ? 2 : 1);   // shared row stride (elements)
+  // shared rows [k][state]: FP32 kinds take a row stride of 4 mod 32 words
+  // and an XOR swizzle of the state index by the 16-byte core column of k,
+  // (k / KPU) % 4, in steps of 8 states, so phase 1 stores 4 states of a
+  // point as one 16-byte word and phase 2 reads a column (8 rows x 4 cores
+  // per warp) without bank conflicts; FP64 takes an odd stride.
+  constexpr bool SWZ = sizeof(ST) == 4;
+  const int RS = SWZ ? (rows + 31) / 32 * 32 + 4 : rows + 1;
+  auto sw = [](int k, int row) { return SWZ ? row ^ (((k / KPU) & 3) << 3) : row; };
   ST* sPh = pk_smem;
   ST* sHp = pk_smem + 64 * RS;
   const float4* S4 = reinterpret_cast<const float4*>(states + F.off);
@@ -256,8 +263,19 @@ __global__ void __launch_bounds__(PK_THREADS) pack_kernel(
   const long long npl2 = (long long)U.ntiles * 128 * rows;   // one 2-byte plane
   const long long half = 2 * npl2 * SCL;                     // phi planes -> H phi planes
   const int upc = rows * NCORE;                              // units per chunk and plane
-  const int nunit = 2 * KT::CPT * upc;
   unsigned char* blk = planes + U.base * SCL;
+  // phase 1 items (k, q): thread tid starts at item tid and steps by two
+  // items of PK_THREADS each (incremental division by nq)
+  const int k1s = tid / nq, q1s = tid - k1s * nq;
+  const int dk = PK_THREADS / nq, dq = PK_THREADS - dk * nq;
+  int k2s = k1s + dk, q2s = q1s + dq;
+  if (q2s >= nq) { q2s -= nq; ++k2s; }
+  const int dk2 = (2 * PK_THREADS) / nq, dq2 = 2 * PK_THREADS - dk2 * nq;
+  // phase 2: thread tid writes the units of one (array, chunk) combination
+  constexpr int NCOMBO = 2 * KT::CPT;
+  constexpr int TPCB = PK_THREADS / NCOMBO;
+  const int combo = tid / TPCB, lic = tid % TPCB;
+  const int A = combo / KT::CPT, cc = combo % KT::CPT;
   for (int t = job.y; t < job.y + job.z; ++t) {
     if (t > job.y) __syncthreads();   // the previous tile's shared data is consumed
     if (tid < 64) {
@@ -297,58 +315,94 @@ __global__ void __launch_bounds__(PK_THREADS) pack_kernel(
       s_v[tid] = in ? V[(long long)gi[0] + (long long)gx * (gi[1] + (long long)gy * gi[2])] : 0.f;
     }
     __syncthreads();
-    for (int it = tid; it < 64 * nq; it += PK_THREADS) {
-      const int k = it / nq, q = it - k * nq;
-      const int p = s_p[k];
-      ST pv[4] = {0, 0, 0, 0}, hv[4] = {0, 0, 0, 0};
-      if (p >= 0 && q < qpp) {
-        const float4 ph = S4[(long long)p * qpp + q];
-        ST sum[4] = {0, 0, 0, 0};
+    // phase 1: two items per step, their 14 loads issued together (absent
+    // points and neighbours load a row of the fragment itself and are
+    // masked, so no load depends on a branch)
+    for (int k1 = k1s, q1 = q1s, k2 = k2s, q2 = q2s; k1 < 64;) {
+      const int kk[2] = {k1, k2 < 64 ? k2 : k1};
+      const int qq[2] = {q1, q2};
+      float4 w[2][7];
+      bool use[2][7];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int p = s_p[kk[h]];
+        const bool ok = p >= 0 && qq[h] < qpp;
+        const int qc = min(qq[h], qpp - 1);
+        const int pc = p >= 0 ? p : 0;
+        use[h][0] = ok;
+        w[h][0] = S4[(long long)pc * qpp + qc];
 #pragma unroll
         for (int j = 0; j < 6; ++j) {
-          const int nb = s_nb[k][j];
-          if (nb >= 0) {
-            const float4 w = S4[(long long)nb * qpp + q];
-            sum[0] += (ST)w.x; sum[1] += (ST)w.y; sum[2] += (ST)w.z; sum[3] += (ST)w.w;
+          const int nb = s_nb[kk[h]][j];
+          use[h][j + 1] = ok && nb >= 0;
+          w[h][j + 1] = S4[(long long)(nb >= 0 ? nb : pc) * qpp + qc];
+        }
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (h == 1 && k2 >= 64) break;
+        const int k = kk[h], q = qq[h];
+        ST pv[4] = {0, 0, 0, 0}, hv[4] = {0, 0, 0, 0};
+        if (use[h][0]) {
+          ST sum[4] = {0, 0, 0, 0};
+#pragma unroll
+          for (int j = 1; j < 7; ++j)
+            if (use[h][j]) {
+              sum[0] += (ST)w[h][j].x; sum[1] += (ST)w[h][j].y;
+              sum[2] += (ST)w[h][j].z; sum[3] += (ST)w[h][j].w;
+            }
+          const ST dv = c0 + (ST)s_v[k];
+          pv[0] = w[h][0].x; pv[1] = w[h][0].y; pv[2] = w[h][0].z; pv[3] = w[h][0].w;
+#pragma unroll
+          for (int i = 0; i < 4; ++i) hv[i] = fma(-c1, sum[i], dv * pv[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (4 * q + i >= F.n) pv[i] = hv[i] = (ST)0;
+        if constexpr (SWZ) {
+          const int o = k * RS + sw(k, 4 * q);
+          *reinterpret_cast<float4*>(sPh + o) = make_float4(pv[0], pv[1], pv[2], pv[3]);
+          *reinterpret_cast<float4*>(sHp + o) = make_float4(hv[0], hv[1], hv[2], hv[3]);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            sPh[k * RS + 4 * q + i] = pv[i];
+            sHp[k * RS + 4 * q + i] = hv[i];
           }
         }
-        const ST dv = c0 + (ST)s_v[k];
-        pv[0] = ph.x; pv[1] = ph.y; pv[2] = ph.z; pv[3] = ph.w;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) hv[i] = fma(-c1, sum[i], dv * pv[i]);
       }
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int row = 4 * q + i;
-        const bool ok = row < F.n;
-        sPh[k * RS + row] = ok ? pv[i] : (ST)0;
-        sHp[k * RS + row] = ok ? hv[i] : (ST)0;
-      }
+      k1 += dk2; q1 += dq2;
+      if (q1 >= nq) { q1 -= nq; ++k1; }
+      k2 += dk2; q2 += dq2;
+      if (q2 >= nq) { q2 -= nq; ++k2; }
     }
     __syncthreads();
-    // write-out: 16-byte unit (array A: phi / H phi, chunk cc, 8-row group g,
-    // core kc, row r) of plane(A, hi|lo) at
-    //   base + part(A) [+ lo] + (t*CPT + cc)*cb + g*512 + kc*128 + r*16
-    for (int w = tid; w < nunit; w += PK_THREADS) {
-      const int A = w / (KT::CPT * upc);
-      int u = w - A * (KT::CPT * upc);
-      const int cc = u / upc;
-      u -= cc * upc;
-      const int r = u & 7, kc = (u >> 3) % NCORE, g = u / (8 * NCORE);
+    // phase 2, write-out: 16-byte unit (array A: phi / H phi, chunk cc,
+    // 8-row group g, core kc, row r) of plane(A, hi|lo) at
+    //   base + part(A) [+ lo] + (t*CPT + cc)*cb + g*(NCORE*128) + kc*128 + r*16
+    // (the units of one (A, cc) are consecutive in memory: coalesced)
+    const ST* srcA = A ? sHp : sPh;
+    // not unrolled: the unrolled loop measured 15 % slower on the large lattice
+#pragma unroll 1
+    for (int u = lic; u < upc; u += TPCB) {
+      const int r = u & 7, kc = (u >> 3) & (NCORE - 1), g = u / (8 * NCORE);
       const int row = 8 * g + r;
       const int k0 = cc * KT::KC + kc * KPU;
-      const ST* src = (A ? sHp : sPh) + k0 * RS + row;
+      const ST* src = srcA + k0 * RS + sw(k0, row);
       ST x[KPU];
 #pragma unroll
       for (int j = 0; j < KPU; ++j) x[j] = src[j * RS];
       const long long off = (long long)(t * KT::CPT + cc) * cb + g * (NCORE * 128) + kc * 128 + r * 16;
+      // streaming stores: the planes are read by the next kernel, long after
+      // they would have left L2, and keeping them out of L2 leaves it to the
+      // states' neighbour rows
       if constexpr (KIND == RK_TF32) {
         const uint4 v = make_uint4(rtf32(x[0]), rtf32(x[1]), rtf32(x[2]), rtf32(x[3]));
-        *reinterpret_cast<uint4*>(blk + A * half + off) = v;
+        __stcs(reinterpret_cast<uint4*>(blk + A * half + off), v);
       } else if constexpr (KIND == RK_F32) {
-        *reinterpret_cast<float4*>(blk + A * half + off) = make_float4(x[0], x[1], x[2], x[3]);
+        __stcs(reinterpret_cast<float4*>(blk + A * half + off), make_float4(x[0], x[1], x[2], x[3]));
       } else if constexpr (KIND == RK_F64) {
-        *reinterpret_cast<double2*>(blk + A * half + off) = make_double2(x[0], x[1]);
+        __stcs(reinterpret_cast<double2*>(blk + A * half + off), make_double2(x[0], x[1]));
       } else {
         uint32_t hw[4], lw[4];
 #pragma unroll
@@ -361,9 +415,9 @@ __global__ void __launch_bounds__(PK_THREADS) pack_kernel(
             lw[j] = *reinterpret_cast<const uint32_t*>(&l2);
           }
         }
-        *reinterpret_cast<uint4*>(blk + A * half + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        __stcs(reinterpret_cast<uint4*>(blk + A * half + off), make_uint4(hw[0], hw[1], hw[2], hw[3]));
         if constexpr (KIND == RK_BF16X3)
-          *reinterpret_cast<uint4*>(blk + A * half + npl2 + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+          __stcs(reinterpret_cast<uint4*>(blk + A * half + npl2 + off), make_uint4(lw[0], lw[1], lw[2], lw[3]));
       }
     }
   }   // tiles
@@ -1438,7 +1492,7 @@ ofm_status ofm_region_prepare(ofm_ctx* c, ofm_precision prec) {
     cudaFuncSetAttribute(region_kernel<RK_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, RS_SMEM);
     cudaFuncSetAttribute(region_kernel<RK_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, RS_SMEM);
     cudaFuncSetAttribute(region_kernel<RK_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, RS_SMEM);
-    const int pk = 2 * 64 * (RS_MAXROWS + 2) * 4;   // phi and H phi, 64 points x (rows + pad) words
+    const int pk = 2 * 64 * (RS_MAXROWS + 4) * 4;   // phi and H phi, 64 points x (rows + pad) words
     cudaFuncSetAttribute(pack_kernel<RK_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, pk);
     cudaFuncSetAttribute(pack_kernel<RK_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, pk);
     cudaFuncSetAttribute(pack_kernel<RK_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, pk);
@@ -1479,7 +1533,7 @@ ofm_status ofm_region_run(ofm_ctx* c, ofm_precision prec) {
     unsigned char* pl = (unsigned char*)P->planes.p;
     int maxrows = 8;
     for (const DevFrag& fq : c->frags) maxrows = std::max(maxrows, (fq.n + 7) / 8 * 8);
-    const int sm = 2 * 64 * (maxrows + 2) * (f64 ? 8 : 4);
+    const int sm = f64 ? 2 * 64 * (maxrows + 1) * 8 : 2 * 64 * ((maxrows + 31) / 32 * 32 + 4) * 4;
     const int4* cta = (const int4*)P->d_pcta.p;
     const unsigned grid = (unsigned)P->pack_cta.size();
     if (grid > 0) {

@@ -4,12 +4,15 @@
   tests/golden/alkane_oracle.json -- the 256x32x32 alkane chain (31 boxes
                                      16x32x32, 32 states each, seed 0): its
                                      fragment energies and the whole spectrum
-                                     of Eq. 2 (992 eigenvalues).
+                                     of Eq. 2 (992 eigenvalues);
+  tests/golden/polymer_oracle.json -- the 128^3 amorphous polymer (56 uneven
+                                     boxes, 8-64 states, seed 0): the same
+                                     (2033 eigenvalues).
 
 Calls only oracle/ and the seeded input generator.  The stored numbers are
 the oracle's, not the paper's (the paper prints no worked example: its
 figures are not part of the available text).
-Run from the repository root:  python tests/golden/make_golden.py [tiny|alkane]
+Run from the repository root:  python tests/golden/make_golden.py [tiny|alkane|polymer]
 """
 import json
 import os
@@ -24,21 +27,22 @@ from ofm_inputs import make_workload  # noqa: E402
 from oracle import ofm_oracle as O  # noqa: E402
 
 
-def _alkane_fragment(a):
-    wl = make_workload("alkane", seed=0)
+def _fragment(args):
+    key, a = args
+    wl = make_workload(key, seed=0)
     H = O.hamiltonian(wl.grid, wl.V)
     return O.fragment_eigs(H, wl.grid, wl.frags[a])
 
 
-def alkane():
-    """The alkane chain through the oracle as it stands: fragment eigensolves
-    (one process each, spawned), pair blocks, dense Eq. 2."""
+def alkane(key="alkane"):
+    """A workload through the oracle as it stands: fragment eigensolves (one
+    process each, spawned), pair blocks, dense Eq. 2."""
     import multiprocessing as mp
     for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[v] = "1"
-    wl = make_workload("alkane", seed=0)
+    wl = make_workload(key, seed=0)
     with mp.get_context("spawn").Pool(min(len(wl.frags), os.cpu_count() or 1)) as pool:
-        res = pool.map(_alkane_fragment, range(len(wl.frags)))
+        res = pool.map(_fragment, [(key, a) for a in range(len(wl.frags))])
     eps = [w for w, _ in res]
     Phis = [U for _, U in res]
     r = O.run_ofm(wl, Phis=Phis)
@@ -52,7 +56,7 @@ def alkane():
         "window_rule": {"kind": wl.window.kind, "width": wl.window.width, "n_occ": wl.window.n_occ},
         "S_min_eig": float(np.linalg.eigvalsh(r["Sd"])[0]),
     }
-    path = os.path.join(ROOT, "tests", "golden", "alkane_oracle.json")
+    path = os.path.join(ROOT, "tests", "golden", f"{key}_oracle.json")
     with open(path, "w") as f:
         json.dump(out, f, indent=0)
     print("wrote", path)
@@ -90,3 +94,5 @@ if __name__ == "__main__":
         main()
     if "alkane" in which:
         alkane()
+    if "polymer" in which:
+        alkane("polymer")

@@ -406,6 +406,27 @@ def test_tiny_workload_matches_stored_oracle_output(repo_root):
     assert g["S_min_eig"] > 0
 
 
+@pytest.mark.parametrize("key", ["alkane", "polymer"])
+def test_stored_spectra_match_the_generator_and_the_oracle(repo_root, key):
+    """The stored FP64 oracle runs (tests/golden/{alkane,polymer}_oracle.json)
+    belong to the workload the generator makes today: one entry per basis
+    function, fragment energies in ascending order per fragment, and the
+    smallest fragment's energies recomputed by the oracle now."""
+    import json
+    import os
+    g = json.load(open(os.path.join(repo_root, "tests", "golden", f"{key}_oracle.json")))
+    wl = make_workload(key, seed=0)
+    assert g["workload"] == wl.name
+    assert len(g["ofm_spectrum"]) == sum(f.n_states for f in wl.frags)
+    assert [len(e) for e in g["fragment_eps"]] == [f.n_states for f in wl.frags]
+    assert all(np.all(np.diff(e) >= 0) for e in g["fragment_eps"])
+    assert np.all(np.diff(g["ofm_spectrum"]) >= 0) and g["S_min_eig"] > 0
+    a = min(range(len(wl.frags)), key=lambda i: (np.prod(wl.frags[i].ext), wl.frags[i].n_states))
+    H = O.hamiltonian(wl.grid, wl.V)
+    eps, _ = O.fragment_eigs(H, wl.grid, wl.frags[a])
+    assert np.max(np.abs(eps - np.array(g["fragment_eps"][a]))) < 1e-9
+
+
 # ------------------------------------------------ Sec. III.C distance cutoff --
 
 def test_fragment_distance_minimum_image_and_empty():
