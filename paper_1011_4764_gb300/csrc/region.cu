@@ -71,10 +71,14 @@ struct RUnit {
   long long base;     // byte offset of the block in the plane arena
 };
 
-// One contraction work item: an M tile x N tile of one region part.
+// One contraction work item: up to 256 rows (two 128-row halves sharing the
+// B operand) x an N tile of one region part.
 struct RItem {
   int tile0, ntiles;  // K range of the part in 64-point tiles of the region
   int n_cols;         // MMA N (multiple of 16, <= 256)
+  int nh;             // row halves (1 or 2)
+  int cskip;          // half 1 skips columns [0, cskip): fragments before its
+                      // first one (lower-triangle blocks), a multiple of 16
   int pa0, npa;       // A pieces
   int pb0, npb;       // B pieces
   int rs0, nrs;       // row segments of the epilogue
@@ -109,12 +113,12 @@ struct RPair {
 enum { RK_TF32 = 0, RK_BF16 = 1, RK_BF16X3 = 2, RK_F32 = 3, RK_F64 = 4 };
 
 constexpr int RS_THREADS = 192;    // warp 0 copies, 1 MMA, 2-5 epilogue
-constexpr int RS_NSTAGE = 4;
+constexpr int RS_NSTAGE = 3;
 constexpr int RS_NQ = 4;           // work-item ring between the roles
-constexpr int RS_ACOLS = 256;      // TMEM columns per accumulator (two accumulators)
-constexpr int RS_ATILE = 128 * 64; // bytes of an A chunk tile (128 rows x 64 B)
+constexpr int RS_ACOLS = 256;      // TMEM columns per accumulator (one per row half)
+constexpr int RS_ATILE = 256 * 64; // bytes of an A chunk tile (256 rows x 64 B)
 constexpr int RS_BTILE = 256 * 64; // bytes of a B chunk tile (256 rows x 64 B)
-constexpr int RS_STAGE = 48 * 1024;
+constexpr int RS_STAGE = 64 * 1024;
 constexpr int RS_SMEM = RS_NSTAGE * RS_STAGE;
 constexpr int RS_MAXROWS = 128;    // padded states per fragment this path takes
 constexpr int PK_THREADS = 256;
@@ -438,6 +442,10 @@ __global__ void __launch_bounds__(PK_THREADS, 3) pack_kernel(
 // Consecutive items -- the M x N tiles of one region -- therefore start
 // together on different SMs and read the same operand chunks at about the
 // same time, which keeps them in L2.
+// An item's two row halves share each B chunk (one accumulator of 256 TMEM
+// columns per half): a third less operand traffic from L2 than 128-row
+// items.  The accumulators are not double-buffered across items (an item
+// runs for milliseconds, its drain for microseconds).
 template <int KIND>
 __global__ void __launch_bounds__(RS_THREADS, 1) region_kernel(
     const RItem* __restrict__ items, int nitems, const RPiece* __restrict__ pieces,
@@ -446,7 +454,7 @@ __global__ void __launch_bounds__(RS_THREADS, 1) region_kernel(
     float* __restrict__ slots, int* flag, int* next, int hold, int wait_iters) {
   using KT = KindT<KIND>;
   extern __shared__ __align__(1024) unsigned char rsm[];
-  __shared__ __align__(8) unsigned long long full[RS_NSTAGE], empty[RS_NSTAGE], acc_full[2], acc_empty[2];
+  __shared__ __align__(8) unsigned long long full[RS_NSTAGE], empty[RS_NSTAGE], acc_full[1], acc_empty[1];
   __shared__ __align__(8) unsigned long long q_full[RS_NQ], q_empty[RS_NQ];
   __shared__ int q_item[RS_NQ];
   __shared__ uint32_t tmem_slot;
@@ -465,10 +473,8 @@ __global__ void __launch_bounds__(RS_THREADS, 1) region_kernel(
       mbar_init(smem_u32(&full[i]), 1);
       mbar_init(smem_u32(&empty[i]), 1);
     }
-    for (int i = 0; i < 2; ++i) {
-      mbar_init(smem_u32(&acc_full[i]), 1);
-      mbar_init(smem_u32(&acc_empty[i]), 4);
-    }
+    mbar_init(smem_u32(&acc_full[0]), 1);
+    mbar_init(smem_u32(&acc_empty[0]), 4);
     for (int i = 0; i < RS_NQ; ++i) {
       mbar_init(smem_u32(&q_full[i]), 1);
       mbar_init(smem_u32(&q_empty[i]), 5);   // the MMA thread and the four epilogue warps
@@ -577,11 +583,15 @@ __global__ void __launch_bounds__(RS_THREADS, 1) region_kernel(
         mbar_arrive(smem_u32(&q_empty[qs]));
         if (ii >= nitems) break;
         const RItem it = items[ii];
-        const int b = item_no & 1, ub = item_no >> 1;
-        if (ub > 0 && !(ok = wait(&acc_empty[b], (uint32_t)((ub - 1) & 1)))) break;
+        if (item_no > 0 && !(ok = wait(&acc_empty[0], (uint32_t)((item_no - 1) & 1)))) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t idesc = ridesc((uint32_t)KT::FMT, 128, (uint32_t)it.n_cols);
-        const uint32_t dacc = tmem + (uint32_t)(b * RS_ACOLS);
+        // half 0: all n_cols columns; half 1: columns [cskip, n_cols)
+        const bool two = it.nh > 1 && it.n_cols - it.cskip >= 16;
+        const uint32_t id0 = ridesc((uint32_t)KT::FMT, 128, (uint32_t)it.n_cols);
+        const uint32_t id1 = ridesc((uint32_t)KT::FMT, 128, (uint32_t)(two ? it.n_cols - it.cskip : 16));
+        const uint32_t d0 = tmem, d1 = tmem + (uint32_t)(RS_ACOLS + it.cskip);
+        const uint64_t aoff = (uint64_t)((128 * 64) >> 4);             // rows 128.. of the A tile
+        const uint64_t boff = (uint64_t)(((it.cskip / 8) * 512) >> 4);  // columns cskip.. of B
         const int nst = it.ntiles * KT::CPT / KT::SC;
         for (int st = 0; st < nst; ++st, ++g) {
           const int s = g % RS_NSTAGE, u = g / RS_NSTAGE;
@@ -599,10 +609,18 @@ __global__ void __launch_bounds__(RS_THREADS, 1) region_kernel(
 #pragma unroll
             for (int ks = 0; ks < 2; ++ks) {   // 32 bytes of K per MMA: two core columns
               const uint64_t o = (uint64_t)((ks * 256) >> 4);
-              rmma<KT::FMT>(dacc, a0 + o, b0 + o, idesc, (st > 0 || cc > 0 || ks > 0) ? 1u : 0u);
+              const uint32_t acc = (st > 0 || cc > 0 || ks > 0) ? 1u : 0u;
+              rmma<KT::FMT>(d0, a0 + o, b0 + o, id0, acc);
               if constexpr (KT::NPL == 2) {
-                rmma<KT::FMT>(dacc, a0 + o, b1 + o, idesc, 1u);
-                rmma<KT::FMT>(dacc, a1 + o, b0 + o, idesc, 1u);
+                rmma<KT::FMT>(d0, a0 + o, b1 + o, id0, 1u);
+                rmma<KT::FMT>(d0, a1 + o, b0 + o, id0, 1u);
+              }
+              if (two) {
+                rmma<KT::FMT>(d1, a0 + aoff + o, b0 + boff + o, id1, acc);
+                if constexpr (KT::NPL == 2) {
+                  rmma<KT::FMT>(d1, a0 + aoff + o, b1 + boff + o, id1, 1u);
+                  rmma<KT::FMT>(d1, a1 + aoff + o, b0 + boff + o, id1, 1u);
+                }
               }
             }
           }
@@ -610,13 +628,12 @@ __global__ void __launch_bounds__(RS_THREADS, 1) region_kernel(
           *(volatile int*)&mma_steps_s = g + 1;
         }
         if (!ok) break;
-        rcommit(smem_u32(&acc_full[b]));
+        rcommit(smem_u32(&acc_full[0]));
       }
     }
   } else {
     // ---------------------------------------------------------- epilogue
     const int q = warp & 3;   // TMEM lane quadrant
-    const int row = q * 32 + lane;
     bool ok = true;
     for (int item_no = 0; ok; ++item_no) {
       const int qs = item_no % RS_NQ, qu = item_no / RS_NQ;
@@ -628,57 +645,63 @@ __global__ void __launch_bounds__(RS_THREADS, 1) region_kernel(
       if (ii >= nitems) break;
       const RItem it = items[ii];
       // the item's segments, one per lane (the planner keeps nrs <= 32 and
-      // ncs <= 64), loaded while the accumulator fills
+      // ncs <= 64), loaded while the accumulators fill
       RRowSeg rsl = {0, 0, 0, 0};
       RColSeg csl[2] = {{0, 0, 0, 0, 0, 0}, {0, 0, 0, 0, 0, 0}};
       if (lane < it.nrs) rsl = rsegs[it.rs0 + lane];
       if (lane < it.ncs) csl[0] = csegs[it.cs0 + lane];
       if (lane + 32 < it.ncs) csl[1] = csegs[it.cs0 + lane + 32];
-      const int b = item_no & 1, ub = item_no >> 1;
-      ok = __all_sync(0xffffffffu, wait(&acc_full[b], (uint32_t)(ub & 1)));
+      ok = __all_sync(0xffffffffu, wait(&acc_full[0], (uint32_t)(item_no & 1)));
       if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      // this lane's row segment
-      int rs = -1, i = 0, na = 0;
-      for (int r = 0; r < it.nrs; ++r) {
-        const int r0 = __shfl_sync(0xffffffffu, rsl.r0, r), nr = __shfl_sync(0xffffffffu, rsl.nr, r);
-        const int i0 = __shfl_sync(0xffffffffu, rsl.i0, r), nn = __shfl_sync(0xffffffffu, rsl.na, r);
-        if (row >= r0 && row < r0 + nr) {
-          rs = r;
-          i = i0 + row - r0;
-          na = nn;
+      const int nh = it.nh > 1 && it.n_cols - it.cskip >= 16 ? 2 : 1;
+      for (int hh = 0; hh < nh; ++hh) {
+        // this lane's row of half hh and its row segment (half 1's columns
+        // below cskip were not formed; they belong to pairs b < a, which
+        // have no slot)
+        const int row = hh * 128 + q * 32 + lane;
+        int rs = -1, i = 0, na = 0;
+        for (int r = 0; r < it.nrs; ++r) {
+          const int r0 = __shfl_sync(0xffffffffu, rsl.r0, r), nr = __shfl_sync(0xffffffffu, rsl.nr, r);
+          const int i0 = __shfl_sync(0xffffffffu, rsl.i0, r), nn = __shfl_sync(0xffffffffu, rsl.na, r);
+          if (row >= r0 && row < r0 + nr) {
+            rs = r;
+            i = i0 + row - r0;
+            na = nn;
+          }
         }
-      }
-      const bool rok = rs >= 0 && i < na;
-      for (int c = 0; c < it.ncs; ++c) {
-        const int h = c >> 5, sl = c & 31;
-        const int cc0 = __shfl_sync(0xffffffffu, h ? csl[1].c0 : csl[0].c0, sl);
-        const int cnc = __shfl_sync(0xffffffffu, h ? csl[1].nc : csl[0].nc, sl);
-        const int cj0 = __shfl_sync(0xffffffffu, h ? csl[1].j0 : csl[0].j0, sl);
-        const int cnb = __shfl_sync(0xffffffffu, h ? csl[1].nb : csl[0].nb, sl);
-        const int cpart = __shfl_sync(0xffffffffu, h ? csl[1].part : csl[0].part, sl);
-        const int ccf = __shfl_sync(0xffffffffu, h ? csl[1].cf : csl[0].cf, sl);
-        const long long slot = rok ? stab[it.st0 + (long long)rs * it.ncf + ccf] : -1;
-        for (int c0 = cc0; c0 < cc0 + cnc; c0 += 8) {
-          float v[8];
-          rtmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * RS_ACOLS + c0), v);
-          if (slot >= 0) {
-            float* o = slots + slot + (long long)i * 2 * cnb + cpart * cnb;
-            const int j0 = cj0 + c0 - cc0;
-            if (j0 + 8 <= cnb && ((reinterpret_cast<uintptr_t>(o + j0) & 15) == 0)) {
-              *reinterpret_cast<float4*>(o + j0) = make_float4(v[0], v[1], v[2], v[3]);
-              *reinterpret_cast<float4*>(o + j0 + 4) = make_float4(v[4], v[5], v[6], v[7]);
-            } else {
+        const bool rok = rs >= 0 && i < na;
+        for (int c = 0; c < it.ncs; ++c) {
+          const int h = c >> 5, sl = c & 31;
+          const int cc0 = __shfl_sync(0xffffffffu, h ? csl[1].c0 : csl[0].c0, sl);
+          const int cnc = __shfl_sync(0xffffffffu, h ? csl[1].nc : csl[0].nc, sl);
+          const int cj0 = __shfl_sync(0xffffffffu, h ? csl[1].j0 : csl[0].j0, sl);
+          const int cnb = __shfl_sync(0xffffffffu, h ? csl[1].nb : csl[0].nb, sl);
+          const int cpart = __shfl_sync(0xffffffffu, h ? csl[1].part : csl[0].part, sl);
+          const int ccf = __shfl_sync(0xffffffffu, h ? csl[1].cf : csl[0].cf, sl);
+          if (hh == 1 && cc0 + cnc <= it.cskip) continue;   // not formed, no slot
+          const long long slot = rok ? stab[it.st0 + (long long)rs * it.ncf + ccf] : -1;
+          for (int c0 = cc0; c0 < cc0 + cnc; c0 += 8) {
+            float v[8];
+            rtmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(hh * RS_ACOLS + c0), v);
+            if (slot >= 0) {
+              float* o = slots + slot + (long long)i * 2 * cnb + cpart * cnb;
+              const int j0 = cj0 + c0 - cc0;
+              if (j0 + 8 <= cnb && ((reinterpret_cast<uintptr_t>(o + j0) & 15) == 0)) {
+                *reinterpret_cast<float4*>(o + j0) = make_float4(v[0], v[1], v[2], v[3]);
+                *reinterpret_cast<float4*>(o + j0 + 4) = make_float4(v[4], v[5], v[6], v[7]);
+              } else {
 #pragma unroll
-              for (int jj = 0; jj < 8; ++jj)
-                if (j0 + jj < cnb) o[j0 + jj] = v[jj];
+                for (int jj = 0; jj < 8; ++jj)
+                  if (j0 + jj < cnb) o[j0 + jj] = v[jj];
+              }
             }
           }
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&acc_empty[b]));
+      if (lane == 0) mbar_arrive(smem_u32(&acc_empty[0]));
     }
   }
 
@@ -773,7 +796,7 @@ __global__ void __launch_bounds__(SR_THREADS, 1) region_simt_kernel(
   extern __shared__ __align__(16) unsigned char ssm[];
   __shared__ long long s_src[64], s_cb[64];
   __shared__ int s_bytes[64], s_dst[64];
-  __shared__ int s_rrs[128], s_ri[128];
+  __shared__ int s_rrs[256], s_ri[256];
   __shared__ int s_ccf[C::NP], s_cpart[C::NP], s_cj[C::NP], s_cnb[C::NP];
   __shared__ int s_item, s_npc, s_aend;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -785,7 +808,7 @@ __global__ void __launch_bounds__(SR_THREADS, 1) region_simt_kernel(
     const int ii = s_item;
     if (ii >= nitems) break;
     const RItem it = items[ii];
-    for (int r = tid; r < 128; r += SR_THREADS) {
+    for (int r = tid; r < 256; r += SR_THREADS) {
       int rs = -1, i = 0;
       for (int q = 0; q < it.nrs; ++q) {
         const RRowSeg g = rsegs[it.rs0 + q];
@@ -798,9 +821,11 @@ __global__ void __launch_bounds__(SR_THREADS, 1) region_simt_kernel(
       s_ri[r] = i;
     }
     const int nch = it.ntiles * 4;   // 16-point chunks of the part
-    for (int c0 = 0; c0 < it.n_cols; c0 += C::NP) {
+    // passes: row half hh (128 rows; half 1 from column cskip on) x NP columns
+    for (int hh = 0; hh < it.nh; ++hh)
+    for (int c0 = hh ? it.cskip : 0; c0 < it.n_cols; c0 += C::NP) {
       const int ncp = min(C::NP, it.n_cols - c0);
-      if (c0 > 0) __syncthreads();   // the previous pass's tables and stages are consumed
+      __syncthreads();   // the previous pass's tables and stages are consumed
       for (int ci = tid; ci < C::NP; ci += SR_THREADS) {
         int cf = -1, part = 0, j = 0, nb = 0;
         const int col = c0 + ci;
@@ -823,13 +848,16 @@ __global__ void __launch_bounds__(SR_THREADS, 1) region_simt_kernel(
         // A pieces whole; B pieces clipped to the pass's column groups
         // (plan offsets are those of 4-byte operands: 512 bytes per group)
         int n = 0, aend = 0;
-        for (int q = 0; q < it.npa; ++q) {
+        for (int q = 0; q < it.npa; ++q) {   // clipped to the half's 16 row groups
           const RPiece pc = pieces[it.pa0 + q];
-          s_src[n] = pc.base * C::S;
+          const int g0 = pc.dst / 512, ng = pc.bytes / 512;
+          const int lo = max(g0, 16 * hh), hi = min(g0 + ng, 16 * hh + 16);
+          if (hi <= lo) continue;
+          s_src[n] = (pc.base + (long long)(lo - g0) * 512) * C::S;
           s_cb[n] = (long long)pc.cb * C::S;
-          s_bytes[n] = pc.bytes * C::S;
-          s_dst[n] = pc.dst * C::S;
-          aend = max(aend, (pc.dst + pc.bytes) * C::S);
+          s_bytes[n] = (hi - lo) * G;
+          s_dst[n] = (lo - 16 * hh) * G;
+          aend = max(aend, s_dst[n] + s_bytes[n]);
           ++n;
         }
         for (int q = 0; q < it.npb; ++q) {
@@ -910,7 +938,7 @@ __global__ void __launch_bounds__(SR_THREADS, 1) region_simt_kernel(
       // epilogue: each valid (row, column) into its pair's slot
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
-        const int row = 8 * (2 * i + (tr >> 3)) + (tr & 7);
+        const int row = 128 * hh + 8 * (2 * i + (tr >> 3)) + (tr & 7);
         const int rs = s_rrs[row];
         if (rs < 0) continue;
         const int si = s_ri[row];
@@ -1334,16 +1362,26 @@ static void region_plan_build(const int gn[3], RegionPlan* P, const std::vector<
         const RPair& q = P->rpairs[p];
         slot[x * nc + y] = q.slot0 + (long long)used[p]++ * q.na * 2 * q.nb;
       }
-    for (int m0 = 0; m0 < M; m0 += 128) {
-      const int m1 = std::min(M, m0 + 128);
+    for (int m0 = 0; m0 < M; m0 += 256) {
+      const int m1 = std::min(M, m0 + 256);
       int xlo = 0;
       while (r0[xlo + 1] <= m0) ++xlo;
+      int xlo1 = xlo;   // first fragment of the second half
+      while (m1 > m0 + 128 && r0[xlo1 + 1] <= m0 + 128) ++xlo1;
       for (int n0 = 2 * r0[xlo]; n0 < 2 * M; n0 += 256) {
         const int n1 = std::min(2 * M, n0 + 256);
         RItem it;
         it.tile0 = pt.t0;
         it.ntiles = pt.nt;
         it.n_cols = n1 - n0;
+        // the second half needs the columns of its own fragments onward
+        it.nh = m1 > m0 + 128 ? 2 : 1;
+        it.cskip = 0;
+        if (it.nh == 2) {
+          const int need = std::max(0, 2 * r0[xlo1] - n0);
+          if (need >= it.n_cols) it.nh = 1;   // no block of half 1 in this N tile
+          else it.cskip = need / 16 * 16;
+        }
         it.pa0 = (int)P->pieces.size();
         it.rs0 = (int)P->rsegs.size();
         std::vector<int> rfr;   // cover index of each row segment
@@ -1409,7 +1447,7 @@ static void region_plan_build(const int gn[3], RegionPlan* P, const std::vector<
         it.st0 = (long long)P->stab.size();
         for (int x : rfr)
           for (int y : cfr) P->stab.push_back(x <= y ? slot[x * nc + y] : -1);
-        P->mma_flops += 2.0 * 128 * it.n_cols * 64.0 * it.ntiles;
+        P->mma_flops += 2.0 * 128 * (it.n_cols + (it.nh == 2 ? it.n_cols - it.cskip : 0)) * 64.0 * it.ntiles;
         P->items.push_back(it);
       }
     }
