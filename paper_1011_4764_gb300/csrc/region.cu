@@ -1036,8 +1036,10 @@ __device__ __forceinline__ void tile_sums(const double* __restrict__ base, long 
     }
 }
 
+// Four CTAs per SM (64 registers): 2.35 ms against 3.05 ms at two (105
+// registers) on the large lattice.
 template <typename T>
-__global__ void __launch_bounds__(256) rfinalize_kernel(const RPair* __restrict__ prs,
+__global__ void __launch_bounds__(256, 4) rfinalize_kernel(const RPair* __restrict__ prs,
                                                         const T* __restrict__ slots,
                                                         double* __restrict__ blocks) {
   __shared__ double tS[32][33], tH[32][33];
