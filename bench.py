@@ -500,6 +500,10 @@ def run_ours(args):
             out["alkane_chain"] = alkane_extra(ofm, stream, dev)
         except Exception as e:  # an extra must not hide the headline line
             out["alkane_chain"] = {"error": str(e)}
+        try:
+            out["amorphous_polymer"] = polymer_extra(ofm, stream, dev)
+        except Exception as e:
+            out["amorphous_polymer"] = {"error": str(e)}
     if rank == 0:
         if world == 1 and not args.no_extras:
             try:
@@ -663,6 +667,71 @@ def alkane_extra(ofm, stream, dev):
                     "per_eigenvalue_ha": [float(f"{x:.3e}") for x in d]}
     c64.close()
     res["window_error_vs_oracle"] = errs
+    return res
+
+
+def _errs(got, ref):
+    import numpy as np
+    d = got - ref
+    return {"max_abs_ha": float(np.max(np.abs(d))), "mean_abs_ha": float(np.mean(np.abs(d))),
+            "per_eigenvalue_ha": [float(f"{x:.3e}") for x in d]}
+
+
+def polymer_extra(ofm, stream, dev):
+    """The amorphous polymer (128^3 grid, 56 uneven boxes 16^3..40^3, 8-64
+    states, basis 2033) end to end from the GPU's own states: FP64 storage,
+    eigensolve, assembly and window (timed, and each window eigenvalue
+    against the FP64 oracle's spectrum in tests/golden/polymer_oracle.json);
+    then every contraction arithmetic on FP32 states, where the pencil's
+    nearly singular S (lambda_min 2e-9 in the oracle) decides the outcome."""
+    import numpy as np
+    import torch
+    from ofm_inputs import make_workload
+    wl = make_workload("polymer")
+    rule = wl.window
+    golden = json.load(open(os.path.join(ROOT, "tests", "golden", "polymer_oracle.json")))
+    Eo = np.array(golden["ofm_spectrum"])
+    i0 = rule.n_occ
+    m = int(np.sum((Eo >= Eo[i0]) & (Eo <= Eo[i0] + rule.width)))
+    res = {"workload": wl.name, "boxes": len(wl.frags), "basis": int(len(Eo)),
+           "window": f"E_{i0 + 1} .. E_{i0 + 1} + {rule.width} Ha", "window_count_oracle": m,
+           "S_min_eig_oracle": golden["S_min_eig"]}
+    V_dev = torch.from_numpy(np.ascontiguousarray(wl.V)).to(dev)
+    ctx = ofm.Context(stream)
+
+    def full_step():
+        ctx.build_fragments(wl.grid, V_dev, wl.frags, storage="fp64")
+        ctx.fragment_eigs()
+        ctx.assemble("fp64")
+        return ctx.window_from_index(i0, rule.width, max_out=len(Eo))
+
+    full_step()
+    ts = []
+    for _ in range(3):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        E, n = full_step()
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    res["fp64_full_step_ms"] = min(ts)
+    res["window_count"] = int(n)
+    res["window_error_vs_oracle"] = {"fp64": _errs(ctx.eigs_by_index(i0, i0 + m), Eo[i0:i0 + m])}
+    ctx.close()
+    c32 = ofm.Context(stream)
+    c32.build_fragments(wl.grid, V_dev, wl.frags, storage="fp32")
+    _, r32, st32 = c32.fragment_eigs(allow_not_converged=True)
+    res["fp32_states"] = {"eigensolver_status": ofm.status_name(st32),
+                          "max_residual": float(r32.max())}
+    for p in ("bf16x3", "tf32", "bf16", "fp32", "fp64"):
+        try:
+            c32.assemble(p)
+            res["window_error_vs_oracle"][f"{p}_on_fp32_states"] = _errs(
+                c32.eigs_by_index(i0, i0 + m), Eo[i0:i0 + m])
+        except ofm.OFMError as e:
+            res["window_error_vs_oracle"][f"{p}_on_fp32_states"] = {"status": str(e)}
+    c32.close()
     return res
 
 
