@@ -52,6 +52,10 @@ def parse_args():
     p.add_argument("--precision", default="bf16x3",
                    help="pair-contraction arithmetic: tf32 bf16 bf16x3 fp32")
     p.add_argument("--no-extras", action="store_true", help="skip e2e, sweeps and the alkane run")
+    p.add_argument("--step", default="assembly", choices=["assembly", "full"],
+                   help="assembly: a1-a5 from resident states (the headline); full: the whole "
+                        "method per step (a2 build, a0 eigensolve, a1-a5, a6 window), for "
+                        "workloads whose basis the dense window solver takes")
     return p.parse_args()
 
 
@@ -91,8 +95,12 @@ def tensor_peak(pk, precision):
             return pk["tf32_tflops"], "tf32 cuBLAS GEMM measured in this run"
         return bf16 * 1.1 / 2.25, "bf16 burst x nominal tf32/bf16 ratio 1.1/2.25"
     if precision == "fp32":
-        return pk.get("fp32_tflops") or 152 * 128 * 2 * 2.07e-3, "fp32 SGEMM measured in this run"
-    return pk.get("fp64_tflops") or 1.25, "fp64 DGEMM measured in this run"
+        if pk.get("fp32_tflops"):
+            return pk["fp32_tflops"], "fp32 SGEMM measured in this run"
+        return None, "fp32 peak not measured"
+    if pk.get("fp64_tflops"):
+        return pk["fp64_tflops"], "fp64 DGEMM measured in this run"
+    return None, "fp64 peak not measured"
 
 
 def roofline_for(name, s, pk, precision):
@@ -127,13 +135,16 @@ def roofline_for(name, s, pk, precision):
     return r
 
 
-def profiled_traffic(kernel_class):
+def profiled_traffic(kernel_class, workload):
     """DRAM bytes per launch from the committed ncu summary, or None when the
-    summary is absent or was taken on a different version of the kernel."""
+    summary is absent, was taken on another workload, or on a different
+    version of the kernel."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         d = json.load(open(path))[kernel_class]
     except Exception:
+        return None
+    if d.get("workload") != workload:
         return None
     import hashlib
     src = os.path.join(ROOT, "paper_1011_4764_gb300", "csrc", d["source"])
@@ -393,8 +404,19 @@ def run_ours(args):
                 "pair_stencil_form": ["register", "staged"][t_form - 1]}
     setup_s = time.perf_counter() - t_setup
 
-    def step():
-        ctx.assemble(prec)
+    if args.step == "full":
+        rule = wl.window
+        if rule is None or rule.kind != "above_gap" or info["basis_size"] > 12800:
+            raise SystemExit("--step full needs an above-gap window and a basis of at most 12800")
+
+        def step():
+            ctx.build_fragments(grid, V_dev, frags, storage="fp32")
+            ctx.fragment_eigs()
+            ctx.assemble(prec)
+            ctx.window_from_index(rule.n_occ, rule.width)
+    else:
+        def step():
+            ctx.assemble(prec)
 
     for _ in range(args.warmup):
         step()
@@ -443,14 +465,14 @@ def run_ours(args):
     K = args.steps
     value = job_value(world, F, K, t_ms)
 
-    measured = gemm_peaks(dev) if rank == 0 and not args.no_extras else {}
+    measured = gemm_peaks(dev) if rank == 0 else {}
     pk = peaks(measured)
     dom_name, dom = max(stats.items(), key=lambda kv: kv[1]["ms"])
     roof = roofline_for(dom_name, dom, pk, prec)
-    roof["traffic"] = profiled_traffic(dom_name)
+    roof["traffic"] = profiled_traffic(dom_name, wl.name)
     others = {k: roofline_for(k, s, pk, prec) for k, s in stats.items() if k != dom_name}
     for k in others:
-        others[k]["traffic"] = profiled_traffic(k)
+        others[k]["traffic"] = profiled_traffic(k, wl.name)
     rows = {}
     for name, s in stats.items():
         rows[s["row"]] = rows.get(s["row"], 0.0) + s["ms"] / K
@@ -466,8 +488,10 @@ def run_ours(args):
                    "fragments": len(frags), "states": sorted({f.n_states for f in frags}),
                    "pairs": info["n_pairs"], "basis": info["basis_size"], "pair_flops": F,
                    "contraction": prec, "storage": "fp32",
-                   "step": "a1 H apply + operands, a3/a4 pair contraction, a5 FP64 blocks "
-                           "(ofm_assemble_HS) from resident states",
+                   "step": ("a1 H apply + operands, a3/a4 pair contraction, a5 FP64 blocks "
+                            "(ofm_assemble_HS) from resident states") if args.step == "assembly" else
+                           ("a2 build + a0 eigensolve + a1-a5 assembly + a6 window above the gap "
+                            "(the whole method)"),
                    "states_from": "the library's batched fragment eigensolver, run once untimed "
                                   f"({eig_s:.1f} s with the pair planning; status "
                                   f"{ofm.status_name(eig_status)}, max residual {float(res.max()):.2e})",
