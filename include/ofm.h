@@ -276,6 +276,20 @@ ofm_status ofm_get_block(ofm_ctx* ctx, int a, int b, double* H_ab, double* S_ab)
  * receives the blocks.  Synchronises the context stream. */
 ofm_status ofm_get_blocks(ofm_ctx* ctx, double* HS, ofm_location loc, long long* n_elems);
 
+/* The same blocks, read back without synchronising: the call enqueues a
+ * device copy of the blocks into a staging buffer on the context stream
+ * (ordered after the assembly) and their transfer to HS (host memory,
+ * pinned for the transfer to overlap; or device memory) on a stream of the
+ * context's own, and returns.  A later ofm_assemble_HS on the context stream
+ * runs while the blocks travel.  HS holds the blocks once ofm_sync_blocks
+ * returns OFM_OK; until then the caller must neither read nor free it.  A
+ * second call waits (on the device, not the host) for the first transfer
+ * before it overwrites the staging buffer.  *n_elems (nullable) receives the
+ * element count; HS NULL only queries it.  Device errors of the assembly are
+ * reported by ofm_sync_blocks. */
+ofm_status ofm_get_blocks_async(ofm_ctx* ctx, double* HS, long long* n_elems);
+ofm_status ofm_sync_blocks(ofm_ctx* ctx);
+
 /* Dense n x n (n = basis_size) row-major H and S in basis order, host or
  * device per loc.  Either pointer may be NULL. */
 ofm_status ofm_get_dense_HS(ofm_ctx* ctx, double* H, double* S, ofm_location loc);

@@ -169,13 +169,18 @@ extern "C" void ofm_destroy(ofm_ctx* c) {
   cudaStreamSynchronize(c->stream);
   drop_graphs(c);
   ofm_prof_release(c);
+  if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
   DevBuf* bufs[] = {&c->V, &c->states, &c->hphi, &c->d_frags, &c->d_pairs,
                     &c->d_pieces, &c->d_items, &c->partials, &c->blocks, &c->dense_H,
                     &c->dense_S, &c->staging, &c->flag, &c->w_A, &c->w_L, &c->w_d, &c->w_e,
-                    &c->w_tau, &c->w_tmp, &c->w_eval, &c->w_bar, &c->w_Q, &c->sp_rowptr, &c->sp_ents};
+                    &c->w_tau, &c->w_tmp, &c->w_eval, &c->w_bar, &c->w_Q, &c->sp_rowptr, &c->sp_ents,
+                    &c->blk_stage};
   for (DevBuf* b : bufs) free_buf(*b);
   ofm_free_extra(c);
   if (c->own_stream) cudaStreamDestroy(c->stream);
+  if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+  if (c->stage_ready) cudaEventDestroy(c->stage_ready);
+  if (c->copy_done) cudaEventDestroy(c->copy_done);
   delete c;
 }
 
@@ -409,6 +414,46 @@ extern "C" ofm_status ofm_get_blocks(ofm_ctx* c, double* HS, ofm_location loc, l
                               loc == OFM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
                               c->stream));
   return sync(c, "get_blocks");
+}
+
+// Asynchronous read-back: the blocks are copied device-to-device into a
+// staging buffer on the context stream (after the assembly), then to HS on
+// the copy stream, so the next assembly runs while they travel.  Before the
+// staging buffer is overwritten by a later call, the context stream waits
+// for the previous transfer.
+extern "C" ofm_status ofm_get_blocks_async(ofm_ctx* c, double* HS, long long* n_elems) {
+  if (!c) return OFM_ERR_INVALID;
+  if (!c->assembled) return ofm_fail(c, OFM_ERR_STATE, "ofm_assemble_HS must come first");
+  long long n = 0;
+  for (const HostPair& p : c->pairs) n += 2LL * c->frags[p.a].n * c->frags[p.b].n;
+  if (n_elems) *n_elems = n;
+  if (!HS) return OFM_OK;
+  if (!c->copy_stream) {
+    OFM_CUDA(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+    OFM_CUDA(c, cudaEventCreateWithFlags(&c->stage_ready, cudaEventDisableTiming));
+    OFM_CUDA(c, cudaEventCreateWithFlags(&c->copy_done, cudaEventDisableTiming));
+  }
+  if (c->copy_pending) OFM_CUDA(c, cudaStreamWaitEvent(c->stream, c->copy_done, 0));
+  OFM_TRY(ofm_ensure_big(c, c->blk_stage, sizeof(double) * (size_t)std::max<long long>(1, n),
+                         "block staging"));
+  OFM_CUDA(c, cudaMemcpyAsync(c->blk_stage.p, c->blocks.p, sizeof(double) * n,
+                              cudaMemcpyDeviceToDevice, c->stream));
+  OFM_CUDA(c, cudaEventRecord(c->stage_ready, c->stream));
+  OFM_CUDA(c, cudaStreamWaitEvent(c->copy_stream, c->stage_ready, 0));
+  OFM_CUDA(c, cudaMemcpyAsync(HS, c->blk_stage.p, sizeof(double) * n, cudaMemcpyDefault,
+                              c->copy_stream));
+  OFM_CUDA(c, cudaEventRecord(c->copy_done, c->copy_stream));
+  c->copy_pending = true;
+  return OFM_OK;
+}
+
+extern "C" ofm_status ofm_sync_blocks(ofm_ctx* c) {
+  if (!c) return OFM_ERR_INVALID;
+  if (c->copy_pending) {
+    OFM_CUDA(c, cudaEventSynchronize(c->copy_done));
+    c->copy_pending = false;
+  }
+  return ofm_wait_status(c);
 }
 
 // Test hook of the failure detection: the next launch of the chosen bounded

@@ -208,6 +208,12 @@ struct ofm_ctx {
       blocks, dense_H, dense_S, staging, flag;
   ofm::DevBuf w_A, w_L, w_d, w_e, w_tau, w_tmp, w_eval, w_bar, w_Q;   // window-solver workspaces
   ofm::DevBuf sp_rowptr, sp_ents;   // block rows of the pencil for ofm_pencil_apply
+  // asynchronous read-back of the blocks (ofm_get_blocks_async): a device
+  // staging copy, and the device-to-host copy on a stream of its own
+  ofm::DevBuf blk_stage;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t stage_ready = nullptr, copy_done = nullptr;
+  bool copy_pending = false;
   bool sp_stale = true;             // rebuilt after the pair list or the plan changes
   double sp_flops_per_col = 0.0, sp_bytes_fixed = 0.0;
   int dense_n = 0;

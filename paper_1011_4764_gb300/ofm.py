@@ -31,7 +31,8 @@ EXPORTS = [
     "ofm_set_dense_HS", "ofm_plan_pairs", "ofm_set_profiling", "ofm_get_kernel_stats",
     "ofm_pair_blocks_noalloc", "ofm_set_pair_cutoff", "ofm_select_states", "ofm_homo_lumo_gap",
     "ofm_window_from_index", "ofm_autotune_assembly", "ofm_pencil_apply", "ofm_plan_regions",
-    "ofm_set_potential", "ofm_get_blocks", "ofm_test_hold_wait",
+    "ofm_set_potential", "ofm_get_blocks", "ofm_get_blocks_async", "ofm_sync_blocks",
+    "ofm_test_hold_wait",
 ]
 SCHEDULE = {"auto": 0, "pair": 1, "region": 2}
 
@@ -102,6 +103,8 @@ def load_library(path: str = LIB_PATH):
         "ofm_get_pairs": ([P, IP, IP], I),
         "ofm_get_plan_info": ([P, C.POINTER(ofm_plan_info)], I),
         "ofm_get_block": ([P, I, I, DP, DP], I),
+        "ofm_get_blocks_async": ([P, P, C.POINTER(C.c_longlong)], I),
+        "ofm_sync_blocks": ([P], I),
         "ofm_get_dense_HS": ([P, P, P, I], I),
         "ofm_get_hphi": ([P, I, DP], I),
         "ofm_window_eigs": ([P, D, D, I, DP, IP, DP], I),
@@ -318,6 +321,18 @@ class Context:
         self._check(self.lib.ofm_get_blocks(self.h, C.c_void_p(out.data_ptr()),
                                             DEVICE if out.is_cuda else HOST, None))
         return out
+
+    def get_blocks_async(self, out):
+        """Starts the read-back of every block into `out` (a float64 torch
+        tensor, pinned host or CUDA, of blocks_count() elements) and returns;
+        `out` holds the blocks after sync_blocks()."""
+        assert _is_torch(out) and str(out.dtype) == "torch.float64" and out.is_contiguous()
+        assert out.numel() >= self.blocks_count()
+        self._check(self.lib.ofm_get_blocks_async(self.h, C.c_void_p(out.data_ptr()), None))
+        return out
+
+    def sync_blocks(self):
+        self._check(self.lib.ofm_sync_blocks(self.h))
 
     # -- ofm_fragment_eigs
     def fragment_eigs(self, tol=0.0, max_iter=0, degree=0, extra_states=0, seed=0,

@@ -282,3 +282,30 @@ def test_set_potential_and_get_blocks(ofm):
     ctx.get_blocks(pin)
     assert np.array_equal(dev.cpu().numpy(), pin.numpy())
     assert np.array_equal(pin.numpy(), ctx.get_blocks())
+
+
+def test_blocks_async_read_back(ofm):
+    """ofm_get_blocks_async: the blocks reach the caller's buffer (pinned host
+    or device) after ofm_sync_blocks, bit for bit those of ofm_get_blocks,
+    also when the next assemblies (another potential each) are enqueued while
+    the previous blocks travel; the last call's blocks are the ones held."""
+    import torch
+    wl = make_workload("tiny")
+    r = O.run_ofm(wl)
+    ctx = run_gpu(ofm, wl, r["Phis"], "fp64", "fp64")
+    n = ctx.blocks_count()
+    pin = torch.full((n,), -1.0, dtype=torch.float64).pin_memory()
+    dev = torch.full((n,), -1.0, dtype=torch.float64, device="cuda")
+    for k, c in enumerate((0.0, 0.21, -0.13)):
+        ctx.set_potential(wl.V + c)
+        ctx.assemble("fp64")
+        ctx.get_blocks_async(pin if k % 2 == 0 else dev)
+    ctx.sync_blocks()
+    last = ctx.get_blocks()
+    assert np.array_equal(pin.numpy(), last)           # the third assembly (k = 2)
+    ctx.set_potential(wl.V + 0.21)
+    ctx.assemble("fp64")
+    ref = ctx.get_blocks()
+    assert np.array_equal(dev.cpu().numpy(), ref)      # the second assembly (k = 1)
+    # the count query and the sync without a pending transfer
+    assert ctx.lib.ofm_sync_blocks(ctx.h) == ofm.OFM_OK
