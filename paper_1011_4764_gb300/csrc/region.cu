@@ -1272,8 +1272,10 @@ static void region_plan_build(const int gn[3], RegionPlan* P, const std::vector<
       P->pack_cta.push_back(make_int4(ui, t0, std::min(PK_TPC, u.ntiles - t0), 0));
   }
 
-  // K split: about six items of equal work per SM, parts of at least 4 tiles
-  const long long target = std::max<long long>(4, total_work / (6 * 152));
+  // K split: about two items of equal work per SM, parts of at least 4 tiles
+  // (more, shorter parts only multiply the partial slots: six per SM took
+  // the alkane chain's assembly from 170 to 204 us, nearly all of it in a5)
+  const long long target = std::max<long long>(4, total_work / (2 * 152));
 
   // slots: count per pair first
   std::vector<int> nslot(prs.size(), 0);
