@@ -242,8 +242,8 @@ __global__ void __launch_bounds__(PK_THREADS, 3) pack_kernel(
   ST* pk_smem = reinterpret_cast<ST*>(pk_raw);
   __shared__ RUnit U;
   __shared__ DevFrag F;
-  __shared__ int s_p[64], s_nb[64][6];
-  __shared__ float s_v[64];
+  __shared__ int s_p[PK_TPC * 64], s_nb[PK_TPC * 64][6];
+  __shared__ float s_v[PK_TPC * 64];
   const int tid = threadIdx.x;
   const int4 job = cta[blockIdx.x];   // unit, first tile, tiles
   if (tid == 0) U = units[job.x];
@@ -282,45 +282,48 @@ __global__ void __launch_bounds__(PK_THREADS, 3) pack_kernel(
   constexpr int TPCB = PK_THREADS / NCOMBO;
   const int combo = tid / TPCB, lic = tid % TPCB;
   const int A = combo / KT::CPT, cc = combo % KT::CPT;
-  for (int t = job.y; t < job.y + job.z; ++t) {
-    if (t > job.y) __syncthreads();   // the previous tile's shared data is consumed
-    if (tid < 64) {
-      // point tid of the tile: K index -> (ix, iy, iz) -> fragment-local coordinates
-      const int K = t * 64 + tid;
-      const int iz = K / U.p8, r = K - iz * U.p8;
-      bool in = iz < U.L[2] && r < npl;
-      int l[3] = {0, 0, 0}, gi[3] = {0, 0, 0};
-      if (in) {
-        const int ii[3] = {r % U.L[0], r / U.L[0], iz};
-        const int gn[3] = {gx, gy, gz};
+  // the coordinates, neighbours and potential of all the CTA's points at
+  // once, one point per thread (PK_TPC * 64 = PK_THREADS)
+  static_assert(PK_TPC * 64 == PK_THREADS, "one point per thread");
+  {
+    const int t = job.y + tid / 64;
+    const int K = t * 64 + tid % 64;
+    const int iz = K / U.p8, r = K - iz * U.p8;
+    bool in = t < job.y + job.z && iz < U.L[2] && r < npl;
+    int l[3] = {0, 0, 0}, gi[3] = {0, 0, 0};
+    if (in) {
+      const int ii[3] = {r % U.L[0], r / U.L[0], iz};
+      const int gn[3] = {gx, gy, gz};
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          int g = U.s0[d] + ii[d];
-          if (g >= gn[d]) g -= gn[d];
-          gi[d] = g;
-          int ld = g - F.doff[d];
-          if (ld < 0) ld += gn[d];
-          l[d] = ld;
-          in = in && ld < F.dext[d];
-        }
+      for (int d = 0; d < 3; ++d) {
+        int g = U.s0[d] + ii[d];
+        if (g >= gn[d]) g -= gn[d];
+        gi[d] = g;
+        int ld = g - F.doff[d];
+        if (ld < 0) ld += gn[d];
+        l[d] = ld;
+        in = in && ld < F.dext[d];
       }
-      const int ex = F.dext[0], exy = F.dext[0] * F.dext[1];
-      const int p = l[0] + ex * l[1] + exy * l[2];
-      const int st[3] = {1, ex, exy};
-#pragma unroll
-      for (int d = 0; d < 3; ++d)
-#pragma unroll
-        for (int sd = 0; sd < 2; ++sd) {
-          const int c = l[d] + (sd ? -1 : 1);
-          int q = -1;
-          if (c >= 0 && c < F.dext[d]) q = p + (c - l[d]) * st[d];
-          else if (F.full[d]) q = p + ((c < 0 ? c + F.dext[d] : c - F.dext[d]) - l[d]) * st[d];
-          s_nb[tid][2 * d + sd] = in ? q : -1;
-        }
-      s_p[tid] = in ? p : -1;
-      s_v[tid] = in ? V[(long long)gi[0] + (long long)gx * (gi[1] + (long long)gy * gi[2])] : 0.f;
     }
-    __syncthreads();
+    const int ex = F.dext[0], exy = F.dext[0] * F.dext[1];
+    const int p = l[0] + ex * l[1] + exy * l[2];
+    const int st[3] = {1, ex, exy};
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int sd = 0; sd < 2; ++sd) {
+        const int c = l[d] + (sd ? -1 : 1);
+        int q = -1;
+        if (c >= 0 && c < F.dext[d]) q = p + (c - l[d]) * st[d];
+        else if (F.full[d]) q = p + ((c < 0 ? c + F.dext[d] : c - F.dext[d]) - l[d]) * st[d];
+        s_nb[tid][2 * d + sd] = in ? q : -1;
+      }
+    s_p[tid] = in ? p : -1;
+    s_v[tid] = in ? V[(long long)gi[0] + (long long)gx * (gi[1] + (long long)gy * gi[2])] : 0.f;
+  }
+  for (int t = job.y; t < job.y + job.z; ++t) {
+    __syncthreads();   // the tables are written / the previous tile's shared rows are consumed
+    const int kb = (t - job.y) * 64;   // this tile's points in the tables
     // phase 1: two items per step, their 14 loads issued together (absent
     // points and neighbours load a row of the fragment itself and are
     // masked, so no load depends on a branch)
@@ -331,7 +334,7 @@ __global__ void __launch_bounds__(PK_THREADS, 3) pack_kernel(
       bool use[2][7];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const int p = s_p[kk[h]];
+        const int p = s_p[kb + kk[h]];
         const bool ok = p >= 0 && qq[h] < qpp;
         const int qc = min(qq[h], qpp - 1);
         const int pc = p >= 0 ? p : 0;
@@ -339,7 +342,7 @@ __global__ void __launch_bounds__(PK_THREADS, 3) pack_kernel(
         w[h][0] = S4[(long long)pc * qpp + qc];
 #pragma unroll
         for (int j = 0; j < 6; ++j) {
-          const int nb = s_nb[kk[h]][j];
+          const int nb = s_nb[kb + kk[h]][j];
           use[h][j + 1] = ok && nb >= 0;
           w[h][j + 1] = S4[(long long)(nb >= 0 ? nb : pc) * qpp + qc];
         }
@@ -357,7 +360,7 @@ __global__ void __launch_bounds__(PK_THREADS, 3) pack_kernel(
               sum[0] += (ST)w[h][j].x; sum[1] += (ST)w[h][j].y;
               sum[2] += (ST)w[h][j].z; sum[3] += (ST)w[h][j].w;
             }
-          const ST dv = c0 + (ST)s_v[k];
+          const ST dv = c0 + (ST)s_v[kb + k];
           pv[0] = w[h][0].x; pv[1] = w[h][0].y; pv[2] = w[h][0].z; pv[3] = w[h][0].w;
 #pragma unroll
           for (int i = 0; i < 4; ++i) hv[i] = fma(-c1, sum[i], dv * pv[i]);
