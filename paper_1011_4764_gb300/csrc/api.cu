@@ -335,6 +335,7 @@ static ofm_status layout_fragments(ofm_ctx* c) {
 extern "C" ofm_status ofm_build_fragments(ofm_ctx* c, const ofm_grid* grid, const double* V,
                                           ofm_location v_loc, const ofm_fragment* frags,
                                           int n_frag, ofm_storage storage) {
+  OFM_RANGE("ofm_build_fragments");
   if (!c) return OFM_ERR_INVALID;
   if (!grid || !V) return ofm_fail(c, OFM_ERR_INVALID, "grid and V must not be NULL");
   if (storage != OFM_STORE_FP32 && storage != OFM_STORE_FP64)
@@ -377,6 +378,7 @@ extern "C" ofm_status ofm_build_fragments(ofm_ctx* c, const ofm_grid* grid, cons
 // (they remain the basis), the pair list and plans stay, the blocks are
 // discarded.
 extern "C" ofm_status ofm_set_potential(ofm_ctx* c, const double* V, ofm_location v_loc) {
+  OFM_RANGE("ofm_set_potential");
   if (!c) return OFM_ERR_INVALID;
   if (!c->built) return ofm_fail(c, OFM_ERR_STATE, "ofm_build_fragments must come first");
   if (!V) return ofm_fail(c, OFM_ERR_INVALID, "V must not be NULL");
@@ -402,6 +404,7 @@ extern "C" ofm_status ofm_set_potential(ofm_ctx* c, const double* V, ofm_locatio
 // Every assembled block in pair-list order: [H_ab | S_ab], n_a x n_b
 // row-major FP64 each.
 extern "C" ofm_status ofm_get_blocks(ofm_ctx* c, double* HS, ofm_location loc, long long* n_elems) {
+  OFM_RANGE("ofm_get_blocks");
   if (!c) return OFM_ERR_INVALID;
   if (!c->assembled) return ofm_fail(c, OFM_ERR_STATE, "ofm_assemble_HS must come first");
   if (loc != OFM_HOST && loc != OFM_DEVICE) return ofm_fail(c, OFM_ERR_INVALID, "unknown location");
@@ -422,6 +425,7 @@ extern "C" ofm_status ofm_get_blocks(ofm_ctx* c, double* HS, ofm_location loc, l
 // staging buffer is overwritten by a later call, the context stream waits
 // for the previous transfer.
 extern "C" ofm_status ofm_get_blocks_async(ofm_ctx* c, double* HS, long long* n_elems) {
+  OFM_RANGE("ofm_get_blocks_async");
   if (!c) return OFM_ERR_INVALID;
   if (!c->assembled) return ofm_fail(c, OFM_ERR_STATE, "ofm_assemble_HS must come first");
   long long n = 0;
@@ -448,6 +452,7 @@ extern "C" ofm_status ofm_get_blocks_async(ofm_ctx* c, double* HS, long long* n_
 }
 
 extern "C" ofm_status ofm_sync_blocks(ofm_ctx* c) {
+  OFM_RANGE("ofm_sync_blocks");
   if (!c) return OFM_ERR_INVALID;
   if (c->copy_pending) {
     OFM_CUDA(c, cudaEventSynchronize(c->copy_done));
@@ -502,6 +507,7 @@ extern "C" ofm_status ofm_set_pair_cutoff(ofm_ctx* c, const double* atom_xyz,
 // The selected columns are copied on the device into the layout for the new
 // state counts.
 extern "C" ofm_status ofm_select_states(ofm_ctx* c, const int* first, const int* count) {
+  OFM_RANGE("ofm_select_states");
   if (!c) return OFM_ERR_INVALID;
   if (!c->built || !c->have_states)
     return ofm_fail(c, OFM_ERR_STATE, "fragment states are not set (ofm_fragment_eigs or ofm_set_fragment_states)");
@@ -544,6 +550,7 @@ static ofm_status ensure_hphi(ofm_ctx* c) {
 // ------------------------------------------------------------- states ------
 
 extern "C" ofm_status ofm_set_fragment_states(ofm_ctx* c, int a, const double* phi, ofm_location loc) {
+  OFM_RANGE("ofm_set_fragment_states");
   if (!c) return OFM_ERR_INVALID;
   if (!c->built) return ofm_fail(c, OFM_ERR_STATE, "ofm_build_fragments must come first");
   if (a < 0 || a >= c->nfrag || !phi) return ofm_fail(c, OFM_ERR_INVALID, "bad fragment index or NULL states");
@@ -568,6 +575,7 @@ extern "C" ofm_status ofm_set_fragment_states(ofm_ctx* c, int a, const double* p
 }
 
 extern "C" ofm_status ofm_get_fragment_states(ofm_ctx* c, int a, double* out, ofm_location loc) {
+  OFM_RANGE("ofm_get_fragment_states");
   if (!c) return OFM_ERR_INVALID;
   if (!c->built || !c->frag_set.size() || !c->frag_set[a < 0 || a >= c->nfrag ? 0 : a])
     return ofm_fail(c, OFM_ERR_STATE, "states of this fragment are not set");
@@ -587,6 +595,7 @@ extern "C" ofm_status ofm_get_fragment_states(ofm_ctx* c, int a, double* out, of
 }
 
 extern "C" ofm_status ofm_get_hphi(ofm_ctx* c, int b, double* out) {
+  OFM_RANGE("ofm_get_hphi");
   if (!c) return OFM_ERR_INVALID;
   if (!c->assembled) return ofm_fail(c, OFM_ERR_STATE, "ofm_assemble_HS must come first");
   if (b < 0 || b >= c->nfrag || !out) return ofm_fail(c, OFM_ERR_INVALID, "bad fragment index or NULL output");
@@ -703,6 +712,7 @@ static ofm_status capture_assembly(ofm_ctx* c, ofm_precision prec, int sched) {
 }
 
 extern "C" ofm_status ofm_assemble_HS(ofm_ctx* c, ofm_precision prec, const ofm_assemble_opts* opts) {
+  OFM_RANGE("ofm_assemble_HS");
   if (!c) return OFM_ERR_INVALID;
   c->fault_due = c->fault == OFM_FAULT_TIMEOUT;   // host-side injection: the next status read
   if (!c->built) return ofm_fail(c, OFM_ERR_STATE, "ofm_build_fragments must come first");
@@ -760,6 +770,7 @@ extern "C" ofm_status ofm_assemble_HS(ofm_ctx* c, ofm_precision prec, const ofm_
 extern "C" ofm_status ofm_autotune_assembly(ofm_ctx* c, ofm_precision prec, const int* chunks,
                                             int n_chunks, int reps, double* times_ms,
                                             ofm_tune_result* out) {
+  OFM_RANGE("ofm_autotune_assembly");
   if (!c) return OFM_ERR_INVALID;
   if (!c->built) return ofm_fail(c, OFM_ERR_STATE, "ofm_build_fragments must come first");
   if (!c->have_states) return ofm_fail(c, OFM_ERR_STATE, "fragment states are not set (ofm_fragment_eigs or ofm_set_fragment_states)");
@@ -915,6 +926,7 @@ extern "C" ofm_status ofm_get_plan_info(ofm_ctx* c, ofm_plan_info* info) {
 }
 
 extern "C" ofm_status ofm_get_block(ofm_ctx* c, int a, int b, double* H_ab, double* S_ab) {
+  OFM_RANGE("ofm_get_block");
   if (!c) return OFM_ERR_INVALID;
   if (!c->assembled) return ofm_fail(c, OFM_ERR_STATE, "ofm_assemble_HS must come first");
   if (a < 0 || b < 0 || a >= c->nfrag || b >= c->nfrag) return ofm_fail(c, OFM_ERR_INVALID, "bad fragment index");
@@ -965,6 +977,7 @@ ofm_status ofm_make_dense(ofm_ctx* c) {
 }
 
 extern "C" ofm_status ofm_get_dense_HS(ofm_ctx* c, double* H, double* S, ofm_location loc) {
+  OFM_RANGE("ofm_get_dense_HS");
   if (!c) return OFM_ERR_INVALID;
   if (!c->dense_ready) OFM_TRY(ofm_make_dense(c));
   const size_t bytes = sizeof(double) * (size_t)c->dense_n * c->dense_n;
@@ -975,6 +988,7 @@ extern "C" ofm_status ofm_get_dense_HS(ofm_ctx* c, double* H, double* S, ofm_loc
 }
 
 extern "C" ofm_status ofm_set_dense_HS(ofm_ctx* c, int n, const double* H, const double* S) {
+  OFM_RANGE("ofm_set_dense_HS");
   if (!c) return OFM_ERR_INVALID;
   if (n < 1 || !H || !S) return ofm_fail(c, OFM_ERR_INVALID, "need n >= 1 and non-NULL H, S");
   const size_t bytes = sizeof(double) * (size_t)n * n;
@@ -994,6 +1008,7 @@ extern "C" ofm_status ofm_set_dense_HS(ofm_ctx* c, int n, const double* H, const
 
 extern "C" ofm_status ofm_window_eigs(ofm_ctx* c, double E_lo, double E_hi, int max_out,
                                       double* E_out, int* n_out, double* C_out) {
+  OFM_RANGE("ofm_window_eigs");
   if (!c) return OFM_ERR_INVALID;
   if (!n_out || (max_out > 0 && !E_out) || max_out < 0 || !(E_lo <= E_hi))
     return ofm_fail(c, OFM_ERR_INVALID, "bad window arguments");
@@ -1009,6 +1024,7 @@ extern "C" ofm_status ofm_window_eigs(ofm_ctx* c, double E_lo, double E_hi, int 
 }
 
 extern "C" ofm_status ofm_eigs_by_index(ofm_ctx* c, int i_lo, int i_hi, double* E_out) {
+  OFM_RANGE("ofm_eigs_by_index");
   if (!c) return OFM_ERR_INVALID;
   if (!c->dense_ready) OFM_TRY(ofm_make_dense(c));
   if (i_lo < 0 || i_hi > c->dense_n || i_lo > i_hi || (!E_out && i_hi > i_lo))
@@ -1025,6 +1041,7 @@ extern "C" ofm_status ofm_eigs_by_index(ofm_ctx* c, int i_lo, int i_hi, double* 
 // last one is still inside).
 extern "C" ofm_status ofm_window_from_index(ofm_ctx* c, int i_lo, double width, int max_out,
                                             double* E_out, int* n_out) {
+  OFM_RANGE("ofm_window_from_index");
   if (!c) return OFM_ERR_INVALID;
   if (!n_out || (max_out > 0 && !E_out) || max_out < 0 || !(width >= 0.0))
     return ofm_fail(c, OFM_ERR_INVALID, "bad window arguments");
@@ -1058,6 +1075,7 @@ extern "C" ofm_status ofm_window_from_index(ofm_ctx* c, int i_lo, double width, 
 // from the largest eigenvalue <= e_ref (the spacing that holds e_ref counts).
 extern "C" ofm_status ofm_homo_lumo_gap(ofm_ctx* c, double gap_min, double* e_ref_out,
                                         double* E_homo, double* E_lumo, int* n_occ) {
+  OFM_RANGE("ofm_homo_lumo_gap");
   if (!c) return OFM_ERR_INVALID;
   if (!c->assembled) return ofm_fail(c, OFM_ERR_STATE, "ofm_assemble_HS must come first");
   if (!(gap_min > 0.0) || !E_homo || !E_lumo || !n_occ)

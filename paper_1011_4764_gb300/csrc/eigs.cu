@@ -1297,6 +1297,7 @@ static int other(int a, int b) {
 
 extern "C" ofm_status ofm_fragment_eigs(ofm_ctx* c, const ofm_eig_opts* opts, double* eps_out,
                                         double* resid_out) {
+  OFM_RANGE("ofm_fragment_eigs");
   if (!c) return OFM_ERR_INVALID;
   if (!c->built) return ofm_fail(c, OFM_ERR_STATE, "ofm_build_fragments must come first");
   if (!eps_out) return ofm_fail(c, OFM_ERR_INVALID, "eps_out must not be NULL");

@@ -8,9 +8,21 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "ofm.h"
 
 namespace ofm {
+
+// An NVTX range for the lifetime of a C-ABI call (visible in nsys/ncu
+// timelines; a no-op without a tool attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define OFM_RANGE(name) ::ofm::NvtxRange ofm_nvtx_range_(name)
 
 // ---------------------------------------------------------------- geometry --
 

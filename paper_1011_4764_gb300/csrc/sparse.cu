@@ -122,6 +122,7 @@ using namespace ofm;
 
 extern "C" ofm_status ofm_pencil_apply(ofm_ctx* c, int which, const double* X, long long ldx,
                                        double* Y, long long ldy, int k) {
+  OFM_RANGE("ofm_pencil_apply");
   if (!c) return OFM_ERR_INVALID;
   if (!c->assembled) return ofm_fail(c, OFM_ERR_STATE, "ofm_assemble_HS must come first");
   if (which != 0 && which != 1) return ofm_fail(c, OFM_ERR_INVALID, "which must be 0 (H) or 1 (S)");
