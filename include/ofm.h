@@ -54,7 +54,9 @@ typedef enum {
   OFM_ERR_NOT_CONVERGED = 4,  /* iteration cap reached (residuals reported) */
   OFM_ERR_NOT_POSDEF = 5,     /* Cholesky of S met a non-positive pivot */
   OFM_ERR_TIMEOUT = 6,        /* a bounded device-side wait gave up */
-  OFM_ERR_STATE = 7           /* call out of order */
+  OFM_ERR_STATE = 7,          /* call out of order */
+  OFM_ERR_CORRUPT = 8         /* check mode: a guard band was overwritten or a device
+                                 bounds check refused an access */
 } ofm_status;
 
 /* Arithmetic of the pair contraction (Sec. II, the H_ab / S_ab dot products). */
@@ -385,6 +387,28 @@ ofm_status ofm_get_kernel_stats(ofm_ctx* ctx, ofm_kernel_stat* out, int max, int
  * (nonconv), or OFM_ERR_NOT_POSDEF from the factorisation of Eq. 2
  * (notposdef). */
 ofm_status ofm_test_hold_wait(ofm_ctx* ctx, int what, int bound);
+/* The same hook tests the check mode below, again from the host and without
+ * any device fault: what = 3 overwrites one byte of the block arena's guard
+ * band (the next guard check reports it); what = 4 (check mode only) points
+ * the region plan's first copy piece just past its plane arena, for the next
+ * region-schedule assembly, whose checking producer refuses it. */
+
+/* Check mode (also on when the environment variable OFM_CHECK is set to 1
+ * when the context is created).  Every device buffer of the library carries
+ * a 256-byte guard band of the byte 0xA5 after its end, written when it is
+ * allocated.  With checks on:
+ *  - ofm_fragment_eigs, ofm_assemble_HS, the window calls, ofm_pencil_apply
+ *    and ofm_get_blocks end with ofm_check_guards (which synchronises);
+ *  - the region schedule's pack and contraction run forms that check every
+ *    gathered point index and every copied byte range against their buffers
+ *    and refuse (skip) an access outside them.
+ * A failure returns OFM_ERR_CORRUPT naming the buffer or the kernel.
+ * Checks cost time (a synchronisation per call, a bounds test per access);
+ * results are the same bit for bit. */
+ofm_status ofm_set_checks(ofm_ctx* ctx, int on);
+/* Reads every guard band of the context's buffers now: OFM_ERR_CORRUPT
+ * (naming the first overwritten buffer) or OFM_OK.  Synchronises. */
+ofm_status ofm_check_guards(ofm_ctx* ctx);
 
 /* Host-only planner query (needs no GPU and no context): validates the
  * geometry like ofm_build_fragments and returns the pair list (Sec. II,

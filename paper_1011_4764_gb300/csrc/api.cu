@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -42,8 +43,15 @@ ofm_status ofm_ensure(ofm_ctx* c, DevBuf& b, size_t bytes, const char* what) {
     b.cap = 0;
     if (e != cudaSuccess) return ofm_cuda_check(c, e, "cudaFree");
   }
-  cudaError_t e = cudaMalloc(&b.p, bytes);
+  // the buffer and its guard band (OFM_GUARD_BYTES of 0xA5 after the end)
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes + OFM_GUARD_BYTES);
+  if (e == cudaSuccess) {
+    b.p = p;
+    e = cudaMemsetAsync((char*)p + bytes, 0xA5, OFM_GUARD_BYTES, c ? c->stream : nullptr);
+  }
   if (e != cudaSuccess) {
+    if (b.p) cudaFree(b.p);
     b.p = nullptr;
     cudaGetLastError();
     char buf[160];
@@ -103,6 +111,80 @@ static int find_pair(const ofm_ctx* c, int a, int b) {
   return -1;
 }
 
+// ----------------------------------------------------- guard bands -------
+
+namespace {
+// One CTA per buffer: thread t reads byte t of the guard band; the smallest
+// index of a buffer with a byte other than 0xA5 goes to *bad.
+__global__ void guard_check_kernel(const GuardRef* tab, int* bad) {
+  const GuardRef g = tab[blockIdx.x];
+  const unsigned char v = static_cast<const unsigned char*>(g.p)[g.cap + threadIdx.x];
+  if (v != 0xA5) atomicMin(bad, (int)blockIdx.x);
+}
+}  // namespace
+
+static void ctx_guards(const ofm_ctx* c, std::vector<GuardRef>& out) {
+  const struct { const DevBuf* b; const char* n; } own[] = {
+      {&c->V, "V"}, {&c->states, "fragment states"}, {&c->hphi, "H phi"},
+      {&c->d_frags, "fragment table"}, {&c->d_pairs, "pair table"}, {&c->d_pieces, "piece table"},
+      {&c->d_items, "work items"}, {&c->partials, "partials"}, {&c->blocks, "blocks"},
+      {&c->dense_H, "dense H"}, {&c->dense_S, "dense S"}, {&c->staging, "staging"},
+      {&c->flag, "error flags"}, {&c->w_A, "window A"}, {&c->w_L, "window L"},
+      {&c->w_d, "window d"}, {&c->w_e, "window e"}, {&c->w_tau, "window tau"},
+      {&c->w_tmp, "window tmp"}, {&c->w_eval, "window eigenvalues"}, {&c->w_bar, "window barrier"},
+      {&c->w_Q, "window Q"}, {&c->sp_rowptr, "pencil rows"}, {&c->sp_ents, "pencil entries"},
+      {&c->blk_stage, "block staging"}};
+  for (const auto& o : own)
+    if (o.b->p) out.push_back({o.b->p, o.b->cap, o.n});
+  ofm_tc_guards(c->tc, out);
+  ofm_eig_guards(c, out);
+  ofm_region_guards(c, out);
+}
+
+// Reads every guard band (and the check-mode kernels' refusal flag):
+// OFM_ERR_CORRUPT naming the first overwritten buffer.  Synchronises.
+ofm_status ofm_check_guards_now(ofm_ctx* c, const char* after) {
+  std::vector<GuardRef> g;
+  ctx_guards(c, g);
+  OFM_TRY(ofm_ensure(c, c->guard_tab, sizeof(GuardRef) * (g.size() + 1), "guard table"));
+  g.push_back({c->guard_tab.p, c->guard_tab.cap, "guard table"});
+  OFM_CUDA(c, cudaMemcpyAsync(c->guard_tab.p, g.data(), sizeof(GuardRef) * g.size(),
+                              cudaMemcpyHostToDevice, c->stream));
+  int* flags = (int*)c->flag.p;
+  const int none = INT_MAX;
+  OFM_CUDA(c, cudaMemcpyAsync(flags + OFM_FLAG_GUARD, &none, sizeof(int), cudaMemcpyHostToDevice,
+                              c->stream));
+  guard_check_kernel<<<(unsigned)g.size(), (unsigned)OFM_GUARD_BYTES, 0, c->stream>>>(
+      (const GuardRef*)c->guard_tab.p, flags + OFM_FLAG_GUARD);
+  OFM_CUDA(c, cudaGetLastError());
+  int res[2] = {0, 0};
+  OFM_CUDA(c, cudaMemcpyAsync(res, flags + OFM_FLAG_GUARD, 2 * sizeof(int), cudaMemcpyDeviceToHost,
+                              c->stream));
+  OFM_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (res[1]) {
+    cudaMemsetAsync(flags + OFM_FLAG_BOUNDS, 0, sizeof(int), c->stream);
+    return ofm_fail(c, OFM_ERR_CORRUPT, std::string("a check-mode kernel refused an access outside its buffer (after ") + after + ")");
+  }
+  if (res[0] != none)
+    return ofm_fail(c, OFM_ERR_CORRUPT, std::string("the guard band of ") + g[res[0]].name +
+                                            " was overwritten (found after " + after + ")");
+  return OFM_OK;
+}
+
+extern "C" ofm_status ofm_set_checks(ofm_ctx* c, int on) {
+  if (!c) return OFM_ERR_INVALID;
+  c->checks = on != 0;
+  drop_graphs(c);          // the captured assemblies use the other kernel forms
+  c->region_stale = true;  // and a fresh region plan drops anything a test hook changed
+  return OFM_OK;
+}
+
+extern "C" ofm_status ofm_check_guards(ofm_ctx* c) {
+  if (!c) return OFM_ERR_INVALID;
+  OFM_RANGE("ofm_check_guards");
+  return ofm_check_guards_now(c, "ofm_check_guards");
+}
+
 void ofm_free_extra(ofm_ctx* c) {
   ofm_eig_free(c);
   ofm_tc_free(c);
@@ -121,6 +203,7 @@ extern "C" const char* ofm_status_string(ofm_status s) {
     case OFM_ERR_NOT_POSDEF: return "OFM_ERR_NOT_POSDEF";
     case OFM_ERR_TIMEOUT: return "OFM_ERR_TIMEOUT";
     case OFM_ERR_STATE: return "OFM_ERR_STATE";
+    case OFM_ERR_CORRUPT: return "OFM_ERR_CORRUPT";
   }
   return "OFM_ERR_UNKNOWN";
 }
@@ -141,6 +224,7 @@ extern "C" ofm_status ofm_create(ofm_ctx** out, void* cuda_stream) {
     c->fault = k == "oom" ? OFM_FAULT_OOM : k == "timeout" ? OFM_FAULT_TIMEOUT
              : k == "nonconv" ? OFM_FAULT_NONCONV : k == "notposdef" ? OFM_FAULT_NOTPOSDEF : OFM_FAULT_NONE;
   }
+  if (const char* k = std::getenv("OFM_CHECK")) c->checks = std::string(k) == "1";
   if (cuda_stream) {
     c->stream = (cudaStream_t)cuda_stream;
   } else {
@@ -403,7 +487,7 @@ extern "C" ofm_status ofm_set_potential(ofm_ctx* c, const double* V, ofm_locatio
 
 // Every assembled block in pair-list order: [H_ab | S_ab], n_a x n_b
 // row-major FP64 each.
-extern "C" ofm_status ofm_get_blocks(ofm_ctx* c, double* HS, ofm_location loc, long long* n_elems) {
+static ofm_status ofm_get_blocks_impl(ofm_ctx* c, double* HS, ofm_location loc, long long* n_elems) {
   OFM_RANGE("ofm_get_blocks");
   if (!c) return OFM_ERR_INVALID;
   if (!c->assembled) return ofm_fail(c, OFM_ERR_STATE, "ofm_assemble_HS must come first");
@@ -417,6 +501,12 @@ extern "C" ofm_status ofm_get_blocks(ofm_ctx* c, double* HS, ofm_location loc, l
                               loc == OFM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
                               c->stream));
   return sync(c, "get_blocks");
+}
+
+extern "C" ofm_status ofm_get_blocks(ofm_ctx* c, double* HS, ofm_location loc, long long* n_elems) {
+  const ofm_status st = ofm_get_blocks_impl(c, HS, loc, n_elems);
+  if (st != OFM_OK || !c || !c->checks) return st;
+  return ofm_check_guards_now(c, "ofm_get_blocks");
 }
 
 // Asynchronous read-back: the blocks are copied device-to-device into a
@@ -466,7 +556,14 @@ extern "C" ofm_status ofm_sync_blocks(ofm_ctx* c) {
 // faults or hangs, and the status reports OFM_ERR_TIMEOUT.
 extern "C" ofm_status ofm_test_hold_wait(ofm_ctx* c, int what, int bound) {
   if (!c) return OFM_ERR_INVALID;
-  if (what < 0 || what > 2 || bound < 0) return ofm_fail(c, OFM_ERR_INVALID, "what must be 0, 1 or 2 and bound >= 0");
+  if (what < 0 || what > 4 || bound < 0) return ofm_fail(c, OFM_ERR_INVALID, "what must be 0..4 and bound >= 0");
+  if (what == 3) {
+    // one byte of the block arena's guard band overwritten from the host
+    if (!c->blocks.p) return ofm_fail(c, OFM_ERR_STATE, "no block arena yet");
+    OFM_CUDA(c, cudaMemsetAsync((char*)c->blocks.p + c->blocks.cap + 7, 0x5A, 1, c->stream));
+    return sync(c, "test_hold_wait");
+  }
+  if (what == 4) return ofm_region_test_corrupt(c);
   c->hold_tc = what == 1;
   c->hold_tri = what == 2;
   c->hold_bound = bound;
@@ -711,7 +808,7 @@ static ofm_status capture_assembly(ofm_ctx* c, ofm_precision prec, int sched) {
   return OFM_OK;
 }
 
-extern "C" ofm_status ofm_assemble_HS(ofm_ctx* c, ofm_precision prec, const ofm_assemble_opts* opts) {
+static ofm_status ofm_assemble_HS_impl(ofm_ctx* c, ofm_precision prec, const ofm_assemble_opts* opts) {
   OFM_RANGE("ofm_assemble_HS");
   if (!c) return OFM_ERR_INVALID;
   c->fault_due = c->fault == OFM_FAULT_TIMEOUT;   // host-side injection: the next status read
@@ -760,6 +857,12 @@ extern "C" ofm_status ofm_assemble_HS(ofm_ctx* c, ofm_precision prec, const ofm_
   OFM_TRY(enqueue_assembly(c, prec, sched));
   c->assembled = true;
   return OFM_OK;
+}
+
+extern "C" ofm_status ofm_assemble_HS(ofm_ctx* c, ofm_precision prec, const ofm_assemble_opts* opts) {
+  const ofm_status st = ofm_assemble_HS_impl(c, prec, opts);
+  if (st != OFM_OK || !c || !c->checks) return st;
+  return ofm_check_guards_now(c, "ofm_assemble_HS");
 }
 
 // Measuring autotuner of the assembly schedule: every (stencil form, points
@@ -1006,7 +1109,7 @@ extern "C" ofm_status ofm_set_dense_HS(ofm_ctx* c, int n, const double* H, const
 
 // ------------------------------------------------------------- Eq. 2 -------
 
-extern "C" ofm_status ofm_window_eigs(ofm_ctx* c, double E_lo, double E_hi, int max_out,
+static ofm_status ofm_window_eigs_impl(ofm_ctx* c, double E_lo, double E_hi, int max_out,
                                       double* E_out, int* n_out, double* C_out) {
   OFM_RANGE("ofm_window_eigs");
   if (!c) return OFM_ERR_INVALID;
@@ -1023,7 +1126,13 @@ extern "C" ofm_status ofm_window_eigs(ofm_ctx* c, double E_lo, double E_hi, int 
   return OFM_OK;
 }
 
-extern "C" ofm_status ofm_eigs_by_index(ofm_ctx* c, int i_lo, int i_hi, double* E_out) {
+extern "C" ofm_status ofm_window_eigs(ofm_ctx* c, double E_lo, double E_hi, int max_out, double* E_out, int* n_out, double* C_out) {
+  const ofm_status st = ofm_window_eigs_impl(c, E_lo, E_hi, max_out, E_out, n_out, C_out);
+  if (st != OFM_OK || !c || !c->checks) return st;
+  return ofm_check_guards_now(c, "ofm_window_eigs");
+}
+
+static ofm_status ofm_eigs_by_index_impl(ofm_ctx* c, int i_lo, int i_hi, double* E_out) {
   OFM_RANGE("ofm_eigs_by_index");
   if (!c) return OFM_ERR_INVALID;
   if (!c->dense_ready) OFM_TRY(ofm_make_dense(c));
@@ -1034,12 +1143,18 @@ extern "C" ofm_status ofm_eigs_by_index(ofm_ctx* c, int i_lo, int i_hi, double* 
   return OFM_OK;
 }
 
+extern "C" ofm_status ofm_eigs_by_index(ofm_ctx* c, int i_lo, int i_hi, double* E_out) {
+  const ofm_status st = ofm_eigs_by_index_impl(c, i_lo, i_hi, E_out);
+  if (st != OFM_OK || !c || !c->checks) return st;
+  return ofm_check_guards_now(c, "ofm_eigs_by_index");
+}
+
 // A window anchored at an index: E_{i_lo} and every later eigenvalue up to
 // E_{i_lo} + width.  An FP32 estimate of the window's size sizes ONE
 // multisection launch over [i_lo, i_lo + estimate + pad); the FP64
 // eigenvalues then decide the window exactly (more are computed when the
 // last one is still inside).
-extern "C" ofm_status ofm_window_from_index(ofm_ctx* c, int i_lo, double width, int max_out,
+static ofm_status ofm_window_from_index_impl(ofm_ctx* c, int i_lo, double width, int max_out,
                                             double* E_out, int* n_out) {
   OFM_RANGE("ofm_window_from_index");
   if (!c) return OFM_ERR_INVALID;
@@ -1066,6 +1181,12 @@ extern "C" ofm_status ofm_window_from_index(ofm_ctx* c, int i_lo, double width, 
   *n_out = cnt;
   if (max_out > 0) std::copy(E.begin(), E.begin() + std::min(cnt, max_out), E_out);
   return OFM_OK;
+}
+
+extern "C" ofm_status ofm_window_from_index(ofm_ctx* c, int i_lo, double width, int max_out, double* E_out, int* n_out) {
+  const ofm_status st = ofm_window_from_index_impl(c, i_lo, width, max_out, E_out, n_out);
+  if (st != OFM_OK || !c || !c->checks) return st;
+  return ofm_check_guards_now(c, "ofm_window_from_index");
 }
 
 // Sec. III, occupation with a HOMO basis: e_a = <HOMO_a|H|HOMO_a> with the

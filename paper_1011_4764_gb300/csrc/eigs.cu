@@ -71,6 +71,23 @@ struct EigWork {
          rot_flops = 0;
 };
 
+void ofm_eig_guards(const ofm_ctx* c, std::vector<GuardRef>& out) {
+  if (!c->eig) return;
+  const EigWork* w = c->eig;
+  const struct { const DevBuf* b; const char* n; } bufs[] = {
+      {&w->d_efr, "eigensolver fragment table"}, {&w->d_cta, "eigensolver CTA table"},
+      {&w->buf[0], "eigensolver block 0"}, {&w->buf[1], "eigensolver block 1"},
+      {&w->buf[2], "eigensolver block 2"}, {&w->buf[3], "eigensolver block 3"},
+      {&w->coef, "filter coefficients"}, {&w->theta, "Ritz values"}, {&w->res, "residuals"},
+      {&w->Cm, "Ritz coefficients"}, {&w->work, "Rayleigh-Ritz work"}, {&w->blocks, "Gram blocks"},
+      {&w->partials, "Gram partials"}, {&w->d_gpairs, "Gram pairs"}, {&w->d_gpieces, "Gram pieces"},
+      {&w->d_gitems, "Gram items"}, {&w->d_toff, "eigensolver offsets"}, {&w->d_rank, "ranks"},
+      {&w->d_vmax, "potential maxima"}, {&w->rpart, "residual partials"}, {&w->xpart, "export partials"}};
+  for (const auto& x : bufs)
+    if (x.b->p) out.push_back({x.b->p, x.b->cap, x.n});
+  ofm_tc_guards(w->gtc, out);
+}
+
 void ofm_eig_free(ofm_ctx* c) {
   if (!c->eig) return;
   EigWork* w = c->eig;
@@ -1295,7 +1312,7 @@ static int other(int a, int b) {
   return -1;
 }
 
-extern "C" ofm_status ofm_fragment_eigs(ofm_ctx* c, const ofm_eig_opts* opts, double* eps_out,
+static ofm_status ofm_fragment_eigs_impl(ofm_ctx* c, const ofm_eig_opts* opts, double* eps_out,
                                         double* resid_out) {
   OFM_RANGE("ofm_fragment_eigs");
   if (!c) return OFM_ERR_INVALID;
@@ -1494,4 +1511,11 @@ extern "C" ofm_status ofm_fragment_eigs(ofm_ctx* c, const ofm_eig_opts* opts, do
     return ofm_fail(c, OFM_ERR_NOT_CONVERGED, buf);
   }
   return OFM_OK;
+}
+
+extern "C" ofm_status ofm_fragment_eigs(ofm_ctx* c, const ofm_eig_opts* opts, double* eps_out, double* resid_out) {
+  const ofm_status st = ofm_fragment_eigs_impl(c, opts, eps_out, resid_out);
+  if ((st != OFM_OK && st != OFM_ERR_NOT_CONVERGED) || !c || !c->checks) return st;
+  const ofm_status g = ofm_check_guards_now(c, "ofm_fragment_eigs");
+  return g != OFM_OK ? g : st;
 }

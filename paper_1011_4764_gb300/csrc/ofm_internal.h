@@ -265,14 +265,35 @@ struct ofm_ctx {
   int hold_bound = 0;               // polls before the held wait gives up (0: usual bound)
   double pack_bytes[5] = {0, 0, 0, 0, 0};     // algorithmic bytes of the apply + pack, per kind
   double region_bytes[5] = {0, 0, 0, 0, 0};   // algorithmic bytes of the region contraction, per kind
+  // check mode (ofm_set_checks / OFM_CHECK): guard bands read after the
+  // calls, bounds-checking kernel forms on the region schedule
+  bool checks = false;
+  bool bounds_check = false;        // a check-mode launch may have set OFM_FLAG_BOUNDS
+  ofm::DevBuf guard_tab;            // device copy of the guard table
 };
 
 // words of the context's 16-int flag buffer: 0 pivot flag and 2..3 window
 // counts (window solver), 8 staged-stencil wait timeout, 9 tensor-core wait
-// timeout, 12 next work item of the region contraction
+// timeout, 12 next work item of the region contraction, 13 the guard check's
+// result, 14 a refused access of a check-mode kernel
 constexpr int OFM_FLAG_STENCIL = 8;
 constexpr int OFM_FLAG_TC = 9;
 constexpr int OFM_FLAG_QUEUE = 12;   // work counter of the region contraction
+constexpr int OFM_FLAG_GUARD = 13;   // first overwritten guard band (INT_MAX: none)
+constexpr int OFM_FLAG_BOUNDS = 14;  // a check-mode kernel refused an access
+constexpr size_t OFM_GUARD_BYTES = 256;   // guard band after every device buffer
+
+// A device buffer whose guard band the check reads.
+struct GuardRef {
+  const void* p;
+  size_t cap;
+  const char* name;
+};
+void ofm_eig_guards(const ofm_ctx* c, std::vector<GuardRef>& out);
+void ofm_region_guards(const ofm_ctx* c, std::vector<GuardRef>& out);
+void ofm_tc_guards(const struct TcPlan* t, std::vector<GuardRef>& out);
+ofm_status ofm_check_guards_now(ofm_ctx* c, const char* after);
+ofm_status ofm_region_test_corrupt(ofm_ctx* c);
 
 // host-side fault injection (environment variable OFM_FAULT read by ofm_create)
 enum { OFM_FAULT_NONE = 0, OFM_FAULT_OOM = 1, OFM_FAULT_TIMEOUT = 2, OFM_FAULT_NONCONV = 3,

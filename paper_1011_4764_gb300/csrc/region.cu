@@ -224,11 +224,15 @@ __device__ __forceinline__ uint32_t rtf32(float x) {
 // zeros.
 // Three CTAs per SM (80 registers): measured 20.1 ms against 24.0 ms at two
 // CTAs (97 registers) and 31.7 ms at four (64 registers, spills), large lattice.
-template <int KIND>
+// CHECK (check mode): every gathered point index is tested against the
+// fragment's dilated box and the states arena, every 16-byte store against
+// the plane arena; a failing access is skipped and *bounds set.
+template <int KIND, bool CHECK = false>
 __global__ void __launch_bounds__(PK_THREADS, 3) pack_kernel(
     const RUnit* __restrict__ units, const int4* __restrict__ cta, const DevFrag* __restrict__ fr,
     const float* __restrict__ V, const float* __restrict__ states, unsigned char* __restrict__ planes,
-    int gx, int gy, int gz, double c0d, double c1d) {
+    int gx, int gy, int gz, double c0d, double c1d, long long n_states, long long n_plane_bytes,
+    int* bounds) {
   using KT = KindT<KIND>;
   constexpr int ESZ = KT::esz;
   constexpr int KPU = 16 / ESZ;            // points per 16-byte unit
@@ -316,8 +320,21 @@ __global__ void __launch_bounds__(PK_THREADS, 3) pack_kernel(
         int q = -1;
         if (c >= 0 && c < F.dext[d]) q = p + (c - l[d]) * st[d];
         else if (F.full[d]) q = p + ((c < 0 ? c + F.dext[d] : c - F.dext[d]) - l[d]) * st[d];
+        if constexpr (CHECK) {
+          if (in && q >= 0 &&
+              (q >= F.Pd || F.off + ((long long)q + 1) * F.ld > n_states)) {
+            atomicExch(bounds, 1);
+            q = -1;
+          }
+        }
         s_nb[tid][2 * d + sd] = in ? q : -1;
       }
+    if constexpr (CHECK) {
+      if (in && (p < 0 || p >= F.Pd || F.off + ((long long)p + 1) * F.ld > n_states)) {
+        atomicExch(bounds, 1);
+        in = false;
+      }
+    }
     s_p[tid] = in ? p : -1;
     s_v[tid] = in ? V[(long long)gi[0] + (long long)gx * (gi[1] + (long long)gy * gi[2])] : 0.f;
   }
@@ -402,6 +419,13 @@ __global__ void __launch_bounds__(PK_THREADS, 3) pack_kernel(
 #pragma unroll
       for (int j = 0; j < KPU; ++j) x[j] = src[j * RS];
       const long long off = (long long)(t * KT::CPT + cc) * cb + g * (NCORE * 128) + kc * 128 + r * 16;
+      if constexpr (CHECK) {
+        const long long last = U.base * SCL + A * half + off + (KIND == RK_BF16X3 ? npl2 : 0) + 16;
+        if (last > n_plane_bytes || U.base < 0) {
+          atomicExch(bounds, 1);
+          continue;
+        }
+      }
       // streaming stores: the planes are read by the next kernel, long after
       // they would have left L2, and keeping them out of L2 leaves it to the
       // states' neighbour rows
@@ -449,12 +473,17 @@ __global__ void __launch_bounds__(PK_THREADS, 3) pack_kernel(
 // columns per half): a third less operand traffic from L2 than 128-row
 // items.  The accumulators are not double-buffered across items (an item
 // runs for milliseconds, its drain for microseconds).
-template <int KIND>
+// CHECK (check mode): the producer tests every copy's source range against
+// the plane arena and destination against its operand tile, the epilogue
+// every slot store against the slot arena; a failing copy ends the launch
+// (the roles give up at once), a failing store is skipped; *bounds is set.
+template <int KIND, bool CHECK = false>
 __global__ void __launch_bounds__(RS_THREADS, 1) region_kernel(
     const RItem* __restrict__ items, int nitems, const RPiece* __restrict__ pieces,
     const RRowSeg* __restrict__ rsegs, const RColSeg* __restrict__ csegs,
     const long long* __restrict__ stab, const unsigned char* __restrict__ planes,
-    float* __restrict__ slots, int* flag, int* next, int hold, int wait_iters) {
+    float* __restrict__ slots, int* flag, int* next, int hold, int wait_iters,
+    long long n_plane_bytes, long long n_slots, int* bounds) {
   using KT = KindT<KIND>;
   extern __shared__ __align__(1024) unsigned char rsm[];
   __shared__ __align__(8) unsigned long long full[RS_NSTAGE], empty[RS_NSTAGE], acc_full[1], acc_empty[1];
@@ -546,6 +575,26 @@ __global__ void __launch_bounds__(RS_THREADS, 1) region_kernel(
       const uint32_t sbytes = __reduce_add_sync(0xffffffffu, mine) * (uint32_t)(KT::SC * KT::NPL);
       const int nst = it.ntiles * KT::CPT / KT::SC;
       const long long c00 = (long long)it.tile0 * KT::CPT;
+      if constexpr (CHECK) {
+        // every chunk of every piece of the item, both planes, inside the
+        // arena; every destination inside its tile
+        bool bad = false;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (!has[h]) continue;
+          const long long first = pc[h].base, last = pc[h].base + (c00 + nst * KT::SC - 1) * pc[h].cb +
+                                                     (KT::NPL == 2 ? pc[h].lo : 0) + pc[h].bytes;
+          const int tile = isA[h] ? RS_ATILE : RS_BTILE;
+          bad = bad || first < 0 || last > n_plane_bytes || pc[h].dst < 0 || pc[h].dst + pc[h].bytes > tile;
+        }
+        if (__any_sync(0xffffffffu, bad)) {
+          if (lane == 0) {
+            atomicExch(bounds, 1);
+            *(volatile int*)&abort_s = 1;
+          }
+          break;
+        }
+      }
       for (int st = 0; st < nst; ++st, ++g) {
         const int s = g % RS_NSTAGE, u = g / RS_NSTAGE;
         if (u > 0) {
@@ -690,6 +739,13 @@ __global__ void __launch_bounds__(RS_THREADS, 1) region_kernel(
             if (slot >= 0) {
               float* o = slots + slot + (long long)i * 2 * cnb + cpart * cnb;
               const int j0 = cj0 + c0 - cc0;
+              if constexpr (CHECK) {
+                const long long e = slot + (long long)i * 2 * cnb + cpart * cnb + j0;
+                if (e < 0 || e + min(8, cnb - j0) > n_slots) {
+                  atomicExch(bounds, 1);
+                  continue;
+                }
+              }
               if (j0 + 8 <= cnb && ((reinterpret_cast<uintptr_t>(o + j0) & 15) == 0)) {
                 *reinterpret_cast<float4*>(o + j0) = make_float4(v[0], v[1], v[2], v[3]);
                 *reinterpret_cast<float4*>(o + j0 + 4) = make_float4(v[4], v[5], v[6], v[7]);
@@ -1472,6 +1528,30 @@ static ofm_status upload(ofm_ctx* c, DevBuf& b, const std::vector<T>& v, const c
   return OFM_OK;
 }
 
+// Test hook of the check mode: the host copy of the first copy piece now
+// points just past the plane arena, and the tables are uploaded again at the
+// next assembly, whose check-mode producer must refuse it.
+ofm_status ofm_region_test_corrupt(ofm_ctx* c) {
+  RegionPlan* P = c->region;
+  if (!c->checks) return ofm_fail(c, OFM_ERR_STATE, "the corruption hook needs check mode");
+  if (!P || !P->ok || P->pieces.empty()) return ofm_fail(c, OFM_ERR_STATE, "no region plan");
+  P->pieces[0].base = P->plane_bytes;
+  P->uploaded = false;
+  return OFM_OK;
+}
+
+void ofm_region_guards(const ofm_ctx* c, std::vector<GuardRef>& out) {
+  const RegionPlan* P = c->region;
+  if (!P) return;
+  const struct { const DevBuf* b; const char* n; } bufs[] = {
+      {&P->d_units, "region units"}, {&P->d_pcta, "pack launch table"}, {&P->d_items, "region items"},
+      {&P->d_pieces, "region pieces"}, {&P->d_rsegs, "region row segments"},
+      {&P->d_csegs, "region column segments"}, {&P->d_stab, "region slot table"},
+      {&P->d_rpairs, "region pairs"}, {&P->planes, "operand planes"}, {&P->slots, "partial slots"}};
+  for (const auto& x : bufs)
+    if (x.b->p) out.push_back({x.b->p, x.b->cap, x.n});
+}
+
 void ofm_region_free(ofm_ctx* c) {
   RegionPlan* P = c->region;
   if (!P) return;
@@ -1539,12 +1619,20 @@ ofm_status ofm_region_prepare(ofm_ctx* c, ofm_precision prec) {
     cudaFuncSetAttribute(region_kernel<RK_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, RS_SMEM);
     cudaFuncSetAttribute(region_kernel<RK_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, RS_SMEM);
     cudaFuncSetAttribute(region_kernel<RK_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, RS_SMEM);
+    cudaFuncSetAttribute(region_kernel<RK_TF32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, RS_SMEM);
+    cudaFuncSetAttribute(region_kernel<RK_BF16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, RS_SMEM);
+    cudaFuncSetAttribute(region_kernel<RK_BF16X3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, RS_SMEM);
     const int pk = 2 * 64 * (RS_MAXROWS + 4) * 4;   // phi and H phi, 64 points x (rows + pad) words
     cudaFuncSetAttribute(pack_kernel<RK_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, pk);
     cudaFuncSetAttribute(pack_kernel<RK_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, pk);
     cudaFuncSetAttribute(pack_kernel<RK_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, pk);
     cudaFuncSetAttribute(pack_kernel<RK_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, pk);
     cudaFuncSetAttribute(pack_kernel<RK_F64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * pk);
+    cudaFuncSetAttribute(pack_kernel<RK_TF32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, pk);
+    cudaFuncSetAttribute(pack_kernel<RK_BF16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, pk);
+    cudaFuncSetAttribute(pack_kernel<RK_BF16X3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, pk);
+    cudaFuncSetAttribute(pack_kernel<RK_F32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, pk);
+    cudaFuncSetAttribute(pack_kernel<RK_F64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * pk);
     cudaFuncSetAttribute(region_simt_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          simt_smem<float>());
     cudaFuncSetAttribute(region_simt_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1584,16 +1672,20 @@ ofm_status ofm_region_run(ofm_ctx* c, ofm_precision prec) {
     const int4* cta = (const int4*)P->d_pcta.p;
     const unsigned grid = (unsigned)P->pack_cta.size();
     if (grid > 0) {
-      if (kind == RK_TF32)
-        pack_kernel<RK_TF32><<<grid, PK_THREADS, sm, c->stream>>>(u, cta, f, V, st, pl, c->grid.n[0], c->grid.n[1], c->grid.n[2], c0, c1);
-      else if (kind == RK_BF16)
-        pack_kernel<RK_BF16><<<grid, PK_THREADS, sm, c->stream>>>(u, cta, f, V, st, pl, c->grid.n[0], c->grid.n[1], c->grid.n[2], c0, c1);
-      else if (kind == RK_F32)
-        pack_kernel<RK_F32><<<grid, PK_THREADS, sm, c->stream>>>(u, cta, f, V, st, pl, c->grid.n[0], c->grid.n[1], c->grid.n[2], c0, c1);
-      else if (kind == RK_F64)
-        pack_kernel<RK_F64><<<grid, PK_THREADS, sm, c->stream>>>(u, cta, f, V, st, pl, c->grid.n[0], c->grid.n[1], c->grid.n[2], c0, c1);
-      else
-        pack_kernel<RK_BF16X3><<<grid, PK_THREADS, sm, c->stream>>>(u, cta, f, V, st, pl, c->grid.n[0], c->grid.n[1], c->grid.n[2], c0, c1);
+      const long long nst = c->state_elems;
+      const long long npb = (long long)P->plane_bytes * (f64 ? 2 : 1);
+      int* bd = (int*)c->flag.p + OFM_FLAG_BOUNDS;
+#define OFM_PACK(K, CH)                                                                        \
+  pack_kernel<K, CH><<<grid, PK_THREADS, sm, c->stream>>>(u, cta, f, V, st, pl, c->grid.n[0],  \
+                                                         c->grid.n[1], c->grid.n[2], c0, c1, \
+                                                         nst, npb, bd)
+      const bool ch = c->checks;
+      if (kind == RK_TF32) { if (ch) OFM_PACK(RK_TF32, true); else OFM_PACK(RK_TF32, false); }
+      else if (kind == RK_BF16) { if (ch) OFM_PACK(RK_BF16, true); else OFM_PACK(RK_BF16, false); }
+      else if (kind == RK_F32) { if (ch) OFM_PACK(RK_F32, true); else OFM_PACK(RK_F32, false); }
+      else if (kind == RK_F64) { if (ch) OFM_PACK(RK_F64, true); else OFM_PACK(RK_F64, false); }
+      else { if (ch) OFM_PACK(RK_BF16X3, true); else OFM_PACK(RK_BF16X3, false); }
+#undef OFM_PACK
     }
     OFM_CUDA(c, cudaGetLastError());
   }
@@ -1622,12 +1714,16 @@ ofm_status ofm_region_run(ofm_ctx* c, ofm_precision prec) {
         const int hold = c->hold_tc;   // armed by the test hook for one launch
         const int wi = hold && c->hold_bound > 0 ? c->hold_bound : (1 << 20);
         c->hold_tc = 0;
-        if (kind == RK_TF32)
-          region_kernel<RK_TF32><<<grid, RS_THREADS, RS_SMEM, c->stream>>>(it, ni, pc, rs, cs, sb, pl, sl, fl, next, hold, wi);
-        else if (kind == RK_BF16)
-          region_kernel<RK_BF16><<<grid, RS_THREADS, RS_SMEM, c->stream>>>(it, ni, pc, rs, cs, sb, pl, sl, fl, next, hold, wi);
-        else
-          region_kernel<RK_BF16X3><<<grid, RS_THREADS, RS_SMEM, c->stream>>>(it, ni, pc, rs, cs, sb, pl, sl, fl, next, hold, wi);
+        const long long npb = P->plane_bytes, nsl = P->slot_elems;
+        int* bd = (int*)c->flag.p + OFM_FLAG_BOUNDS;
+#define OFM_REGION(K, CH)                                                                     \
+  region_kernel<K, CH><<<grid, RS_THREADS, RS_SMEM, c->stream>>>(it, ni, pc, rs, cs, sb, pl, sl, fl, \
+                                                                 next, hold, wi, npb, nsl, bd)
+        const bool ch = c->checks;
+        if (kind == RK_TF32) { if (ch) OFM_REGION(RK_TF32, true); else OFM_REGION(RK_TF32, false); }
+        else if (kind == RK_BF16) { if (ch) OFM_REGION(RK_BF16, true); else OFM_REGION(RK_BF16, false); }
+        else { if (ch) OFM_REGION(RK_BF16X3, true); else OFM_REGION(RK_BF16X3, false); }
+#undef OFM_REGION
       }
     }
     OFM_CUDA(c, cudaGetLastError());

@@ -120,7 +120,7 @@ static ofm_status pencil_tables(ofm_ctx* c) {
 
 using namespace ofm;
 
-extern "C" ofm_status ofm_pencil_apply(ofm_ctx* c, int which, const double* X, long long ldx,
+static ofm_status ofm_pencil_apply_impl(ofm_ctx* c, int which, const double* X, long long ldx,
                                        double* Y, long long ldy, int k) {
   OFM_RANGE("ofm_pencil_apply");
   if (!c) return OFM_ERR_INVALID;
@@ -154,4 +154,10 @@ extern "C" ofm_status ofm_pencil_apply(ofm_ctx* c, int which, const double* X, l
   }
   OFM_CUDA(c, cudaGetLastError());
   return OFM_OK;
+}
+
+extern "C" ofm_status ofm_pencil_apply(ofm_ctx* c, int which, const double* X, long long ldx, double* Y, long long ldy, int k) {
+  const ofm_status st = ofm_pencil_apply_impl(c, which, X, ldx, Y, ldy, k);
+  if (st != OFM_OK || !c || !c->checks) return st;
+  return ofm_check_guards_now(c, "ofm_pencil_apply");
 }

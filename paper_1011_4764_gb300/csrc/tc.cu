@@ -535,6 +535,15 @@ struct TcPlan {
   std::string why;
 };
 
+void ofm_tc_guards(const TcPlan* t, std::vector<GuardRef>& out) {
+  if (!t) return;
+  const struct { const DevBuf* b; const char* n; } bufs[] = {
+      {&t->d_pairs, "tensor-core pairs"}, {&t->d_items, "tensor-core items"},
+      {&t->d_pieces, "tensor-core pieces"}, {&t->partials, "tensor-core partials"}};
+  for (const auto& x : bufs)
+    if (x.b->p) out.push_back({x.b->p, x.b->cap, x.n});
+}
+
 void ofm_tc_plan_free(TcPlan* t) {
   if (!t) return;
   DevBuf* bufs[] = {&t->d_pairs, &t->d_items, &t->d_pieces, &t->partials};

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "libofm.so")
 
 OFM_OK, OFM_ERR_INVALID, OFM_ERR_OOM, OFM_ERR_CUDA = 0, 1, 2, 3
 OFM_ERR_NOT_CONVERGED, OFM_ERR_NOT_POSDEF, OFM_ERR_TIMEOUT, OFM_ERR_STATE = 4, 5, 6, 7
+OFM_ERR_CORRUPT = 8
 PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3, "bf16x3": 4}
 STORE = {"fp64": 0, "fp32": 1}
 HOST, DEVICE = 0, 1
@@ -32,7 +33,7 @@ EXPORTS = [
     "ofm_pair_blocks_noalloc", "ofm_set_pair_cutoff", "ofm_select_states", "ofm_homo_lumo_gap",
     "ofm_window_from_index", "ofm_autotune_assembly", "ofm_pencil_apply", "ofm_plan_regions",
     "ofm_set_potential", "ofm_get_blocks", "ofm_get_blocks_async", "ofm_sync_blocks",
-    "ofm_test_hold_wait",
+    "ofm_test_hold_wait", "ofm_set_checks", "ofm_check_guards",
 ]
 SCHEDULE = {"auto": 0, "pair": 1, "region": 2}
 
@@ -127,6 +128,8 @@ def load_library(path: str = LIB_PATH):
         "ofm_set_potential": ([P, P, I], I),
         "ofm_get_blocks": ([P, P, I, C.POINTER(C.c_longlong)], I),
         "ofm_test_hold_wait": ([P, I, I], I),
+        "ofm_set_checks": ([P, I], I),
+        "ofm_check_guards": ([P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -287,9 +290,19 @@ class Context:
     # -- ofm_test_hold_wait (failure-detection tests)
     def test_hold_wait(self, what, bound=0):
         """Arm one bounded device wait to run out: "contract" (the next region
-        contraction) or "tridiag" (the next reduction of Eq. 2); None disarms."""
-        self._check(self.lib.ofm_test_hold_wait(self.h, {None: 0, "contract": 1, "tridiag": 2}[what],
-                                                int(bound)))
+        contraction) or "tridiag" (the next reduction of Eq. 2); None disarms.
+        Check-mode tests: "guard" overwrites a byte of the block arena's guard
+        band, "piece" points the region plan's first copy piece past its
+        arena (check mode only)."""
+        self._check(self.lib.ofm_test_hold_wait(
+            self.h, {None: 0, "contract": 1, "tridiag": 2, "guard": 3, "piece": 4}[what], int(bound)))
+
+    # -- ofm_set_checks / ofm_check_guards
+    def set_checks(self, on=True):
+        self._check(self.lib.ofm_set_checks(self.h, 1 if on else 0))
+
+    def check_guards(self):
+        self._check(self.lib.ofm_check_guards(self.h))
 
     # -- ofm_set_potential
     def set_potential(self, V):
