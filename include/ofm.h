@@ -171,7 +171,9 @@ ofm_status ofm_get_fragment_states(ofm_ctx* ctx, int a, double* phi_out, ofm_loc
  * in the requested arithmetic, summed in a fixed order (deterministic), and
  * stored as FP64 blocks; a diagonal block is symmetrised as (X + X^T)/2.
  * FP64 arithmetic is allowed with either storage; the others need FP32
- * storage.  Enqueued on the context stream; does not synchronise. */
+ * storage.  The tensor-core precisions (TF32, BF16, BF16 hi+lo) take at most
+ * 128 states per fragment (OFM_ERR_INVALID beyond; FP32 and FP64 have no
+ * such limit).  Enqueued on the context stream; does not synchronise. */
 ofm_status ofm_assemble_HS(ofm_ctx* ctx, ofm_precision prec, const ofm_assemble_opts* opts);
 
 /* Result of ofm_autotune_assembly. */
