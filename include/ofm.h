@@ -165,6 +165,17 @@ ofm_status ofm_fragment_eigs(ofm_ctx* ctx, const ofm_eig_opts* opts,
 ofm_status ofm_set_fragment_states(ofm_ctx* ctx, int a, const double* phi, ofm_location loc);
 ofm_status ofm_get_fragment_states(ofm_ctx* ctx, int a, double* phi_out, ofm_location loc);
 
+/* Checkpoint of the basis: every fragment's states written to <path>.bin
+ * (raw little-endian values in the storage precision, fragment after
+ * fragment, each laid out as ofm_get_fragment_states returns it) with a
+ * JSON header <path>.json (format, grid, h, storage, the boxes and state
+ * counts).  ofm_load_basis reads them into a context built with the same
+ * grid, boxes, state counts and storage (OFM_ERR_INVALID otherwise, or for
+ * a file that cannot be read or has the wrong length) and marks them as the
+ * current basis: a run resumes after the eigensolve.  Both synchronise. */
+ofm_status ofm_save_basis(ofm_ctx* ctx, const char* path);
+ofm_status ofm_load_basis(ofm_ctx* ctx, const char* path);
+
 /* Sec. II, the main part of the calculation: H phi_b on every dilated box
  * (whole-system H), then for every pair a <= b
  *     S_ab = Phi_a^T Phi_b  over B_a ∩ B_b,   H_ab = Phi_a^T (H Phi_b) over B_a ∩ B_b+,

@@ -33,7 +33,8 @@ EXPORTS = [
     "ofm_pair_blocks_noalloc", "ofm_set_pair_cutoff", "ofm_select_states", "ofm_homo_lumo_gap",
     "ofm_window_from_index", "ofm_autotune_assembly", "ofm_pencil_apply", "ofm_plan_regions",
     "ofm_set_potential", "ofm_get_blocks", "ofm_get_blocks_async", "ofm_sync_blocks",
-    "ofm_test_hold_wait", "ofm_set_checks", "ofm_check_guards",
+    "ofm_test_hold_wait", "ofm_set_checks", "ofm_check_guards", "ofm_save_basis",
+    "ofm_load_basis",
 ]
 SCHEDULE = {"auto": 0, "pair": 1, "region": 2}
 
@@ -129,6 +130,8 @@ def load_library(path: str = LIB_PATH):
         "ofm_get_blocks": ([P, P, I, C.POINTER(C.c_longlong)], I),
         "ofm_test_hold_wait": ([P, I, I], I),
         "ofm_set_checks": ([P, I], I),
+        "ofm_save_basis": ([P, C.c_char_p], I),
+        "ofm_load_basis": ([P, C.c_char_p], I),
         "ofm_check_guards": ([P], I),
     }
     for name, (args, res) in sig.items():
@@ -296,6 +299,15 @@ class Context:
         arena (check mode only)."""
         self._check(self.lib.ofm_test_hold_wait(
             self.h, {None: 0, "contract": 1, "tridiag": 2, "guard": 3, "piece": 4}[what], int(bound)))
+
+    # -- ofm_save_basis / ofm_load_basis
+    def save_basis(self, path):
+        """Writes <path>.bin and <path>.json (the basis checkpoint)."""
+        self._check(self.lib.ofm_save_basis(self.h, os.fsencode(str(path))))
+
+    def load_basis(self, path):
+        """Reads a checkpoint written by save_basis for the same geometry."""
+        self._check(self.lib.ofm_load_basis(self.h, os.fsencode(str(path))))
 
     # -- ofm_set_checks / ofm_check_guards
     def set_checks(self, on=True):
