@@ -70,7 +70,6 @@ extern "C" ofm_status ofm_pair_blocks_noalloc(const ofm_grid* grid, const ofm_fr
                                               const ofm_fragment* fb, const float* phi_a,
                                               const float* phi_b, const float* hphi_b,
                                               double* HS_ab, void* cuda_stream) {
-  OFM_RANGE("ofm_pair_blocks_noalloc");
   if (!grid || !fa || !fb || !phi_a || !phi_b || !hphi_b || !HS_ab) return OFM_ERR_INVALID;
   const ofm_fragment two[2] = {*fa, *fb};
   std::string err;
