@@ -80,7 +80,7 @@ typedef struct { int off[3]; int ext[3]; int n_states; } ofm_fragment;
  * iteration with Rayleigh-Ritz).  Zero fields take the defaults in brackets. */
 typedef struct {
   double tol;            /* stop when every max_i ||H phi_i - eps_i phi_i|| <= tol [1e-5 FP32, 1e-9 FP64] */
-  int max_iter;          /* outer iterations [60] */
+  int max_iter;          /* outer iterations [240] */
   int degree;            /* Chebyshev degree per iteration [32] */
   int extra_states;      /* guard vectors beyond n_states [max(4, n/4), or one or two fewer
                             (at least 4) when that saves a wave of the on-chip filter] */

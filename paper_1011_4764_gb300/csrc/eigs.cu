@@ -1322,7 +1322,10 @@ static ofm_status ofm_fragment_eigs_impl(ofm_ctx* c, const ofm_eig_opts* opts, d
   if (opts) o = *opts;
   const bool fp64 = c->storage == OFM_STORE_FP64;
   const double tol = o.tol > 0 ? o.tol : (fp64 ? 1e-9 : 1e-5);
-  const int max_iter = o.max_iter > 0 ? o.max_iter : 60;
+  // 240: the polymer's FP32 blocks of 32-49 states in 16-24 point boxes need
+  // about 200 outer iterations (60 left residuals of 4e-5 against 1e-5);
+  // converged blocks stop early, so the bound costs nothing elsewhere
+  const int max_iter = o.max_iter > 0 ? o.max_iter : 240;
   const int degree = o.degree > 0 ? o.degree : 32;
   if (o.tol < 0 || o.max_iter < 0 || o.degree < 0 || o.extra_states < 0 || degree > 200)
     return ofm_fail(c, OFM_ERR_INVALID, "bad eigensolver options");
