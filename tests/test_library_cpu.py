@@ -41,8 +41,17 @@ def test_every_declared_symbol_is_exported(lib, repo_root):
 
 
 def test_status_strings(lib):
-    assert lib.status_name(0) == "OFM_OK"
-    assert lib.status_name(5) == "OFM_ERR_NOT_POSDEF"
+    """Every status the header defines has its name, and the binding's
+    constants carry the header's values."""
+    import re
+    text = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                             "include", "ofm.h")).read()
+    codes = dict((n, int(v)) for n, v in re.findall(r"\b(OFM_(?:OK|ERR_[A-Z_]+))\s*=\s*(\d+)", text))
+    assert codes["OFM_OK"] == 0 and len(codes) >= 9
+    for name, value in codes.items():
+        assert lib.status_name(value) == name
+        assert getattr(lib, name) == value
+    assert lib.status_name(99) == "OFM_ERR_UNKNOWN"
 
 
 @pytest.mark.parametrize("name", ["tiny", "alkane"])
